@@ -1,0 +1,167 @@
+"""FP64 CPU oracle for the Minimod acoustic isotropic constant-density propagator.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference leg of ``bench.py`` may import this package.  The CUDA
+library never calls it and shares no code with it; the product path fails
+loudly when its own extension is missing instead of falling back here.
+
+The arithmetic lives in ``oracle.c`` (plain C, FP64, OpenMP over z); this module
+only builds it with gcc and marshals numpy arrays through ctypes.  What each C
+function follows in the paper (Eq. 1, Eq. 5, the Sec. 3 Laplacian, Alg. 1 and
+Alg. 2) and the readings taken where the paper is silent are stated in the C
+file's header.
+
+Parity pins (tests/test_oracle_*.py): Taylor coefficients against the textbook
+closed form and the moment identities; Laplacian exact on polynomials of degree
+<= 9; the exact discrete standing wave (dispersion relation); discrete energy
+conservation (damping off) and decay (damping on); the 3-D homogeneous Green's
+function; a dense-matrix stepper on tiny grids; linearity, reciprocity and axis
+permutation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# -ffp-contract=off: no fused multiply-adds, so x86 and Arm hosts round alike.
+_CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off"]
+
+
+def build(force: bool = False, src: str = _SRC, out: str = _LIB) -> str:
+    """Compile the oracle's C source into a shared library (gcc, OpenMP)."""
+    with _lock:
+        if (not force and os.path.exists(out)
+                and os.path.getmtime(out) >= os.path.getmtime(src)):
+            return out
+        tmp = out + f".tmp{os.getpid()}"
+        cmd = ["gcc", *_CFLAGS, src, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, out)
+        return out
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Oracle:
+    """ctypes binding of one build of oracle.c (the default one, or a variant)."""
+
+    def __init__(self, path: str):
+        lib = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        I, D = ctypes.c_int, ctypes.c_double
+        lib.orc_fd_coeffs.argtypes = [I, P]
+        lib.orc_damping_profile.argtypes = [I, I, D, D, D, P]
+        lib.orc_laplacian.argtypes = [I, I, I, D, D, D, I, P, P]
+        lib.orc_forward.argtypes = [I, I, I, D, D, D, D, I, I, I, D, P,
+                                    I, P, P, I, P, P, P, P, P, P, I]
+        lib.orc_max_threads.argtypes = []
+        for f in (lib.orc_fd_coeffs, lib.orc_damping_profile, lib.orc_laplacian,
+                  lib.orc_forward, lib.orc_max_threads):
+            f.restype = ctypes.c_int
+        self.lib = lib
+        self.path = path
+
+    def max_threads(self) -> int:
+        return self.lib.orc_max_threads()
+
+    def fd_coeffs(self, order: int) -> np.ndarray:
+        """[c0, c1..cR]: centre weight and Taylor weights of Sec. 3 (unit spacing)."""
+        out = np.zeros(max(order // 2, 0) + 1, dtype=np.float64)
+        rc = self.lib.orc_fd_coeffs(order, _ptr(out))
+        if rc != 0:
+            raise ValueError(f"orc_fd_coeffs(order={order}) -> {rc}")
+        return out
+
+    def damping_profile(self, n: int, nbl: int, h: float, vmax: float, refl: float = 1e-3) -> np.ndarray:
+        """eta_a(i), i = 0..n-1, of the damping layers (reading R3)."""
+        out = np.zeros(n, dtype=np.float64)
+        rc = self.lib.orc_damping_profile(n, nbl, h, vmax, refl, _ptr(out))
+        if rc != 0:
+            raise ValueError(f"orc_damping_profile -> {rc}")
+        return out
+
+    def laplacian(self, u: np.ndarray, h, order: int = 8) -> np.ndarray:
+        """Sec. 3 Laplacian of u [nz][ny][nx] with u = 0 outside the grid."""
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        nz, ny, nx = u.shape
+        hx, hy, hz = h
+        out = np.empty_like(u)
+        rc = self.lib.orc_laplacian(nx, ny, nz, hx, hy, hz, order, _ptr(u), _ptr(out))
+        if rc != 0:
+            raise ValueError(f"orc_laplacian -> {rc}")
+        return out
+
+    def forward(self, vel: np.ndarray, h, dt: float, nt: int, *, order: int = 8, nbl: int = 0,
+                refl: float = 1e-3, src_ijk=None, wavelet=None, rec_ijk=None,
+                u_prev0=None, u_cur0=None, want_state: bool = False, nthreads: int = 0):
+        """Alg. 1 / Alg. 2 forward run in FP64.
+
+        vel: [nz][ny][nx] float32 m/s.  src_ijk: [nsrc][3] (i, j, k).  wavelet:
+        [nsrc][nt] float32.  rec_ijk: [nrec][3].  Returns traces [nt][nrec]
+        (FP64) and, with want_state, also (u^{nt-1}, u^{nt}).
+        """
+        vel = np.ascontiguousarray(vel, dtype=np.float32)
+        nz, ny, nx = vel.shape
+        hx, hy, hz = h
+        src = (np.zeros((0, 3), np.int32) if src_ijk is None
+               else np.ascontiguousarray(src_ijk, np.int32).reshape(-1, 3))
+        rec = (np.zeros((0, 3), np.int32) if rec_ijk is None
+               else np.ascontiguousarray(rec_ijk, np.int32).reshape(-1, 3))
+        nsrc, nrec = src.shape[0], rec.shape[0]
+        wav = np.ascontiguousarray(wavelet, np.float32).reshape(nsrc, nt) if nsrc else None
+        traces = np.zeros((nt, nrec), dtype=np.float64)
+        up0 = None if u_prev0 is None else np.ascontiguousarray(u_prev0, np.float64)
+        uc0 = None if u_cur0 is None else np.ascontiguousarray(u_cur0, np.float64)
+        upo = np.empty(vel.shape, np.float64) if want_state else None
+        uco = np.empty(vel.shape, np.float64) if want_state else None
+        rc = self.lib.orc_forward(nx, ny, nz, hx, hy, hz, dt, nt, order, nbl, refl, _ptr(vel),
+                                  nsrc, _ptr(src) if nsrc else None, _ptr(wav),
+                                  nrec, _ptr(rec) if nrec else None, _ptr(traces) if nrec else None,
+                                  _ptr(up0), _ptr(uc0), _ptr(upo), _ptr(uco), nthreads)
+        if rc != 0:
+            raise ValueError(f"orc_forward -> {rc}")
+        if want_state:
+            return traces, upo, uco
+        return traces
+
+
+def _default() -> Oracle:
+    global _lib
+    if _lib is None:
+        _lib = Oracle(build())
+    return _lib
+
+
+def max_threads() -> int:
+    return _default().max_threads()
+
+
+def fd_coeffs(order: int) -> np.ndarray:
+    return _default().fd_coeffs(order)
+
+
+def damping_profile(n: int, nbl: int, h: float, vmax: float, refl: float = 1e-3) -> np.ndarray:
+    return _default().damping_profile(n, nbl, h, vmax, refl)
+
+
+def laplacian(u: np.ndarray, h, order: int = 8) -> np.ndarray:
+    return _default().laplacian(u, h, order)
+
+
+def forward(vel, h, dt, nt, **kw):
+    return _default().forward(vel, h, dt, nt, **kw)
+
+
+forward.__doc__ = Oracle.forward.__doc__

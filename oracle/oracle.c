@@ -1,0 +1,303 @@
+/*
+ * FP64 CPU oracle for the Minimod acoustic isotropic constant-density
+ * propagator (arXiv 2007.06048).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is the plain, slow, obviously correct
+ * reference that the CUDA library is checked against.  Only the test suite,
+ * the smoke check and the benchmark's CPU-baseline / reference leg load it;
+ * the library never does.  The two share no code, header, table or constant.
+ *
+ * What it computes, by the paper's sections:
+ *   Eq. 1   (1/v^2) p_tt - lap p = f
+ *   Eq. 5   p^{n+1} - Q p^n + p^{n-1} = dt^2 v^2 f^n,   Q = 2 + dt^2 v^2 lap
+ *   Sec. 3  the 25-point star Laplacian  sum_m c_am [p(+m) + p(-m) - 2 p]  on
+ *           each axis a, with c_am from the order-2R Taylor expansion
+ *   Alg. 1  p^0 = 0; each step solves the left-hand side everywhere and then
+ *           adds the source term f^n
+ *   Alg. 2  an inner region updated with Eq. 5 and six damping regions
+ *           (left/right, back/front, top/bottom) around it
+ *
+ * Readings where the paper is silent (also listed in the design notes):
+ *   R2  u = 0 outside the grid (homogeneous Dirichlet).
+ *   R3  the damping regions solve u_tt + 2 eta u_t = v^2 (lap u + f), centred
+ *       in time, which gives
+ *          u^{n+1} = [2 u^n - (1 - eta dt) u^{n-1} + c lap u^n] / (1 + eta dt)
+ *       with c = dt^2 v^2, eta = eta_x(i) + eta_y(j) + eta_z(k),
+ *       eta_a(i) = eta_max,a (d/L)^2, d = max(L - i, i - (n_a - 1 - L), 0),
+ *       eta_max,a = 3 vmax ln(1/R) / (2 L h_a).  Where eta = 0 this is Eq. 5.
+ *   R4  the damping layers are part of the grid; the inner region is
+ *       [L, n_a - 1 - L] on every axis.
+ *   R5  a point source: the discrete f^n at x_s is w[n] / (hx hy hz), so the
+ *       add of Alg. 1 is  c(x_s) w[n] / (hx hy hz (1 + eta(x_s) dt)),  i.e.
+ *       the source sits inside the damped update's numerator.
+ *   R7  receivers record u^{n+1} at grid points after the add of step n.
+ *
+ * Index convention: i along x (fastest), j along y, k along z (depth, k = 0 at
+ * the surface); user arrays are [nz][ny][nx].
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_MAX_R 8
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3: second-derivative weights from the Taylor expansion.             */
+/*                                                                          */
+/*   f(x+mh) + f(x-mh) - 2 f(x) = sum_{p>=1} 2 (mh)^{2p} f^{(2p)}(x) / (2p)! */
+/*                                                                          */
+/* so  sum_m c_m [f(x+mh) + f(x-mh) - 2 f(x)] = h^2 f''(x) + O(h^{2R+2})    */
+/* exactly when  sum_m c_m m^2 = 1  and  sum_m c_m m^{2p} = 0, p = 2..R.    */
+/* The R x R system is solved by Gaussian elimination with partial pivots.  */
+/* Output: c[0] = -2 sum_m c_m (the centre weight), c[m] = c_m, m = 1..R.  */
+/* ------------------------------------------------------------------------ */
+int orc_fd_coeffs(int order, double *c)
+{
+    if (order < 2 || order % 2 != 0 || order / 2 > ORC_MAX_R || !c) return -1;
+    const int R = order / 2;
+    double A[ORC_MAX_R][ORC_MAX_R + 1];
+    for (int p = 1; p <= R; ++p) {
+        for (int m = 1; m <= R; ++m) A[p - 1][m - 1] = pow((double)m, 2.0 * p);
+        A[p - 1][R] = (p == 1) ? 1.0 : 0.0;
+    }
+    for (int col = 0; col < R; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < R; ++r)
+            if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
+        if (A[piv][col] == 0.0) return -2;
+        if (piv != col)
+            for (int q = 0; q <= R; ++q) { double t = A[col][q]; A[col][q] = A[piv][q]; A[piv][q] = t; }
+        for (int r = 0; r < R; ++r) {
+            if (r == col) continue;
+            const double f = A[r][col] / A[col][col];
+            for (int q = col; q <= R; ++q) A[r][q] -= f * A[col][q];
+        }
+    }
+    double sum = 0.0;
+    for (int m = 1; m <= R; ++m) { c[m] = A[m - 1][R] / A[m - 1][m - 1]; sum += c[m]; }
+    c[0] = -2.0 * sum;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Reading R3: damping profile along one axis of n cells, L = nbl.          */
+/* ------------------------------------------------------------------------ */
+int orc_damping_profile(int n, int nbl, double h, double vmax, double refl, double *eta)
+{
+    if (n < 1 || nbl < 0 || 2 * nbl > n || h <= 0 || !eta) return -1;
+    if (nbl == 0) { for (int i = 0; i < n; ++i) eta[i] = 0.0; return 0; }
+    if (!(refl > 0.0 && refl < 1.0) || vmax <= 0) return -1;
+    const double eta_max = 3.0 * vmax * log(1.0 / refl) / (2.0 * nbl * h);
+    for (int i = 0; i < n; ++i) {
+        int d = 0;
+        if (nbl - i > d) d = nbl - i;
+        if (i - (n - 1 - nbl) > d) d = i - (n - 1 - nbl);
+        const double s = (double)d / (double)nbl;
+        eta[i] = eta_max * s * s;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Wavefields live in a zero-padded copy: R extra cells on every side hold  */
+/* the u = 0 of reading R2 literally, so the stencil needs no bounds tests. */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int nx, ny, nz, R;
+    long px, py, pz;   /* padded extents */
+    long sy, sz;       /* strides of j and k in the padded array */
+} grid_t;
+
+static grid_t make_grid(int nx, int ny, int nz, int R)
+{
+    grid_t g;
+    g.nx = nx; g.ny = ny; g.nz = nz; g.R = R;
+    g.px = nx + 2L * R; g.py = ny + 2L * R; g.pz = nz + 2L * R;
+    g.sy = g.px; g.sz = g.px * g.py;
+    return g;
+}
+
+static inline long at(const grid_t *g, int i, int j, int k)
+{
+    return ((long)k + g->R) * g->sz + ((long)j + g->R) * g->sy + ((long)i + g->R);
+}
+
+static double *padded_zeros(const grid_t *g)
+{
+    return (double *)calloc((size_t)(g->px * g->py * g->pz), sizeof(double));
+}
+
+/* Sec. 3 Laplacian at one point: per axis  sum_m c_am [p(+m) + p(-m) - 2p]. */
+static inline double lap_at(const grid_t *g, const double *u, long o,
+                            const double *cx, const double *cy, const double *cz)
+{
+    const double p = u[o];
+    double lx = 0.0, ly = 0.0, lz = 0.0;
+    for (int m = 1; m <= g->R; ++m) {
+        lx += cx[m] * (u[o + m] + u[o - m] - 2.0 * p);
+        ly += cy[m] * (u[o + m * g->sy] + u[o - m * g->sy] - 2.0 * p);
+        lz += cz[m] * (u[o + m * g->sz] + u[o - m * g->sz] - 2.0 * p);
+    }
+    return lx + ly + lz;
+}
+
+static int axis_weights(int order, double hx, double hy, double hz,
+                        double *cx, double *cy, double *cz)
+{
+    double c[ORC_MAX_R + 1];
+    if (orc_fd_coeffs(order, c) != 0) return -1;
+    for (int m = 0; m <= order / 2; ++m) {
+        cx[m] = c[m] / (hx * hx);
+        cy[m] = c[m] / (hy * hy);
+        cz[m] = c[m] / (hz * hz);
+    }
+    return 0;
+}
+
+/* Sec. 3 Laplacian of a whole field u [nz][ny][nx] into out, u = 0 outside. */
+int orc_laplacian(int nx, int ny, int nz, double hx, double hy, double hz, int order,
+                  const double *u, double *out)
+{
+    if (nx < 1 || ny < 1 || nz < 1 || !u || !out) return -1;
+    double cx[ORC_MAX_R + 1], cy[ORC_MAX_R + 1], cz[ORC_MAX_R + 1];
+    if (axis_weights(order, hx, hy, hz, cx, cy, cz) != 0) return -1;
+    const grid_t g = make_grid(nx, ny, nz, order / 2);
+    double *pu = padded_zeros(&g);
+    if (!pu) return -3;
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i)
+                pu[at(&g, i, j, k)] = u[((long)k * ny + j) * nx + i];
+    #pragma omp parallel for collapse(2) schedule(static)
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i)
+                out[((long)k * ny + j) * nx + i] = lap_at(&g, pu, at(&g, i, j, k), cx, cy, cz);
+    free(pu);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Forward modelling: Alg. 1 with the wavefield solution step of Alg. 2.    */
+/*                                                                          */
+/* vel      [nz][ny][nx] FP32 velocities (m/s), promoted to FP64 here       */
+/* src_ijk  [nsrc][3] grid indices, wavelet [nsrc][nt] FP32                 */
+/* rec_ijk  [nrec][3] grid indices, traces [nt][nrec] FP64 output           */
+/* u_prev0, u_cur0   optional initial u^{-1}, u^0 ([nz][ny][nx]); NULL = 0  */
+/* u_prev_out, u_cur_out  optional final u^{nt-1}, u^{nt}                   */
+/* nthreads  OpenMP threads, 0 = runtime default                            */
+/* Returns 0, or a negative code for bad arguments / no memory.             */
+/* ------------------------------------------------------------------------ */
+int orc_forward(int nx, int ny, int nz, double hx, double hy, double hz,
+                double dt, int nt, int order, int nbl, double refl,
+                const float *vel,
+                int nsrc, const int *src_ijk, const float *wavelet,
+                int nrec, const int *rec_ijk, double *traces,
+                const double *u_prev0, const double *u_cur0,
+                double *u_prev_out, double *u_cur_out, int nthreads)
+{
+    if (nx < 1 || ny < 1 || nz < 1 || nt < 0 || dt <= 0 || !vel) return -1;
+    if (hx <= 0 || hy <= 0 || hz <= 0) return -1;
+    if (2 * nbl > nx || 2 * nbl > ny || 2 * nbl > nz || nbl < 0) return -1;
+    if (nsrc < 0 || nrec < 0 || (nsrc > 0 && (!src_ijk || !wavelet))) return -1;
+    if (nrec > 0 && (!rec_ijk || !traces)) return -1;
+    for (int s = 0; s < nsrc; ++s) {
+        const int *p = src_ijk + 3 * s;
+        if (p[0] < 0 || p[0] >= nx || p[1] < 0 || p[1] >= ny || p[2] < 0 || p[2] >= nz) return -1;
+    }
+    for (int r = 0; r < nrec; ++r) {
+        const int *p = rec_ijk + 3 * r;
+        if (p[0] < 0 || p[0] >= nx || p[1] < 0 || p[1] >= ny || p[2] < 0 || p[2] >= nz) return -1;
+    }
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    double cx[ORC_MAX_R + 1], cy[ORC_MAX_R + 1], cz[ORC_MAX_R + 1];
+    if (axis_weights(order, hx, hy, hz, cx, cy, cz) != 0) return -1;
+    const grid_t g = make_grid(nx, ny, nz, order / 2);
+    const long N = (long)nx * ny * nz;
+
+    /* c = dt^2 v^2 (Eq. 5) and the model maximum used by reading R3. */
+    double vmax = 0.0;
+    for (long q = 0; q < N; ++q) if ((double)vel[q] > vmax) vmax = (double)vel[q];
+    double *ex = (double *)malloc(sizeof(double) * nx);
+    double *ey = (double *)malloc(sizeof(double) * ny);
+    double *ez = (double *)malloc(sizeof(double) * nz);
+    double *C = padded_zeros(&g), *ua = padded_zeros(&g), *ub = padded_zeros(&g), *uc = padded_zeros(&g);
+    int rc = 0;
+    if (!ex || !ey || !ez || !C || !ua || !ub || !uc) { rc = -3; goto done; }
+    if (orc_damping_profile(nx, nbl, hx, vmax, refl, ex) || orc_damping_profile(ny, nbl, hy, vmax, refl, ey) ||
+        orc_damping_profile(nz, nbl, hz, vmax, refl, ez)) { rc = -1; goto done; }
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const long q = ((long)k * ny + j) * nx + i;
+                const double v = (double)vel[q];
+                C[at(&g, i, j, k)] = dt * dt * v * v;
+                if (u_prev0) ua[at(&g, i, j, k)] = u_prev0[q];
+                if (u_cur0) ub[at(&g, i, j, k)] = u_cur0[q];
+            }
+
+    /* Alg. 2 region bounds: inner = [x3,x4] x [y3,y4] x [z3,z4]. */
+    const int x3 = nbl, x4 = nx - 1 - nbl, y3 = nbl, y4 = ny - 1 - nbl, z3 = nbl, z4 = nz - 1 - nbl;
+    const double cell = hx * hy * hz;
+    double *up = ua, *ucur = ub, *un = uc;   /* u^{n-1}, u^n, u^{n+1} */
+
+    for (int n = 0; n < nt; ++n) {          /* Alg. 1 time loop */
+        #pragma omp parallel for collapse(2) schedule(static)
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    const long o = at(&g, i, j, k);
+                    const double L = lap_at(&g, ucur, o, cx, cy, cz);
+                    const int inner = i >= x3 && i <= x4 && j >= y3 && j <= y4 && k >= z3 && k <= z4;
+                    if (inner) {
+                        /* Eq. 5 solved for p^{n+1} (its right-hand side is added below). */
+                        un[o] = 2.0 * ucur[o] - up[o] + C[o] * L;
+                    } else {
+                        /* Damping regions of Alg. 2, reading R3. */
+                        const double e = (ex[i] + ey[j] + ez[k]) * dt;
+                        un[o] = (2.0 * ucur[o] - (1.0 - e) * up[o] + C[o] * L) / (1.0 + e);
+                    }
+                }
+        /* Alg. 1: add the source term of Eq. 5's right-hand side (reading R5). */
+        for (int s = 0; s < nsrc; ++s) {
+            const int *p = src_ijk + 3 * s;
+            const long o = at(&g, p[0], p[1], p[2]);
+            const double e = (ex[p[0]] + ey[p[1]] + ez[p[2]]) * dt;
+            un[o] += C[o] * (double)wavelet[(long)s * nt + n] / (cell * (1.0 + e));
+        }
+        /* Reading R7: receivers sample u^{n+1}. */
+        for (int r = 0; r < nrec; ++r) {
+            const int *p = rec_ijk + 3 * r;
+            traces[(long)n * nrec + r] = un[at(&g, p[0], p[1], p[2])];
+        }
+        double *t = up; up = ucur; ucur = un; un = t;
+    }
+
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const long q = ((long)k * ny + j) * nx + i;
+                if (u_prev_out) u_prev_out[q] = up[at(&g, i, j, k)];
+                if (u_cur_out) u_cur_out[q] = ucur[at(&g, i, j, k)];
+            }
+done:
+    free(ex); free(ey); free(ez); free(C); free(ua); free(ub); free(uc);
+    return rc;
+}
+
+/* Threads the OpenMP runtime would use (1 without OpenMP). */
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

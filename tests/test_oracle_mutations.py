@@ -1,0 +1,74 @@
+"""The pins have teeth: plant one plausible mistake at a time in a temporary
+copy of the oracle's C source (never in the committed file, always on the
+CPU), build it, and require that at least one pin rejects the result."""
+import os
+
+import pytest
+
+import oracle
+import test_oracle_bruteforce as BF
+import test_oracle_dynamics as DY
+import test_oracle_stencil as ST
+
+
+def _dense(orc):
+    BF.test_dense_stepper_agrees(orc, (11, 10, 12), 2, 8)
+    BF.test_dense_stepper_agrees(orc, (9, 12, 10), 3, 6)
+
+
+def _poly(orc):
+    ST.test_laplacian_exact_on_polynomials(orc, 8)
+
+
+def _coeffs(orc):
+    ST.test_coeffs_match_textbook_closed_form(orc, 8)
+
+
+def _energy(orc):
+    DY.test_energy_conserved_without_damping(orc)
+    DY.test_energy_decrement_with_damping_is_exact(orc)
+
+
+def _reciprocity(orc):
+    BF.test_reciprocity_heterogeneous_damped(orc)
+
+
+def _standing(orc):
+    DY.test_standing_wave_is_exact(orc, 8)
+
+
+MUTATIONS = [
+    ("damping drops (1 - eta dt) on u^{n-1}", "(1.0 - e) * up[o]", "up[o]", [_energy, _dense]),
+    ("damping sign flipped", "/ (1.0 + e);", "/ (1.0 - e);", [_energy, _dense]),
+    ("y axis uses the x weights", "ly += cy[m]", "ly += cx[m]", [_poly, _dense]),
+    ("z neighbour uses the y stride", "u[o - m * g->sz]", "u[o - m * g->sy]", [_poly, _dense, _energy]),
+    ("centre term dropped on x", "lx += cx[m] * (u[o + m] + u[o - m] - 2.0 * p)",
+     "lx += cx[m] * (u[o + m] + u[o - m] - p)", [_poly, _standing]),
+    ("Taylor right-hand side wrong", "(p == 1) ? 1.0 : 0.0", "(p == 1) ? 2.0 : 0.0", [_coeffs, _poly]),
+    ("source outside the (1 + eta dt) division", "(cell * (1.0 + e))", "cell", [_dense, _reciprocity]),
+    ("source sign flipped", "un[o] += C[o]", "un[o] -= C[o]", [_dense]),
+    ("receivers record u^n instead of u^{n+1}", "traces[(long)n * nrec + r] = un[", "traces[(long)n * nrec + r] = ucur[",
+     [_dense]),
+    ("damping profile shifted by one cell", "if (nbl - i > d) d = nbl - i;", "if (nbl - i - 1 > d) d = nbl - i - 1;",
+     [_dense]),
+    ("leapfrog uses 2 u^{n-1}", "un[o] = 2.0 * ucur[o] - up[o] + C[o] * L;",
+     "un[o] = 2.0 * ucur[o] - 2.0 * up[o] + C[o] * L;", [_standing, _dense]),
+]
+
+
+@pytest.mark.parametrize("name,old,new,pins", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_planted_mistake_is_caught(tmp_path, name, old, new, pins):
+    src = open(oracle._SRC).read()
+    assert src.count(old) == 1, f"mutation anchor not unique: {old!r}"
+    mut_src = tmp_path / "oracle_mut.c"
+    mut_src.write_text(src.replace(old, new))
+    lib = oracle.build(force=True, src=str(mut_src), out=str(tmp_path / "liboracle_mut.so"))
+    orc = oracle.Oracle(lib)
+    failures = []
+    for pin in pins:
+        try:
+            pin(orc)
+        except (AssertionError, ValueError) as e:  # the pin rejected the mutant
+            failures.append(f"{pin.__name__}: {type(e).__name__}")
+    assert failures, f"no pin caught: {name}"
+    assert os.path.exists(lib)
