@@ -1,0 +1,329 @@
+"""Throughput of the forward propagator in Gpoint-updates/s on one or more GPUs.
+
+One bench step = one mmod_forward: the whole hot path (interior and damping
+updates, source injection, receiver gather, the nt-step time loop) over the
+workload.  Default workload: 240^3 grid, 1000 steps, four-layer velocity model
+with a smoothed +-5% perturbation, 20-cell damping layers, Ricker 10 Hz source
+at depth 40 m, 240 x 240 surface receivers (synthetic, seeded).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mmod|reference]
+
+With N > 1 the script runs under torch.distributed.run; each rank advances its
+own replica of the workload on its own GPU (independent shots: weak scaling,
+no collective on the data path), and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gpoint-updates/s and % HBM roofline (fwd, adjoint, batched shots) at stated error"
+UNIT = "Gpoint-updates/s"
+BYTES_PER_POINT = 16      # read u^n, u^{n-1}, c; write u^{n+1} (FP32)
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def make_workload(name: str, nt: int | None):
+    import workloads as W
+    if name == "layered240":
+        return W.layered_240(nt or 1000)
+    if name == "homogeneous64":
+        return W.small_homogeneous(nt or 100)
+    if name == "gradient200":
+        return W.smooth_gradient_200(nt or 1000)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def describe(p, extra=None):
+    nz, ny, nx = p.vel.shape
+    cfg = {"workload": p.name, "grid": [nx, ny, nz], "h_m": list(p.h), "nt": p.nt, "dt_s": p.dt,
+           "nbl": p.nbl, "order": p.order, "nsrc": int(len(p.src_ijk)), "nrec": int(len(p.rec_ijk)),
+           "cache": "inputs larger than L2: each time step streams three %.1f MB FP32 volumes (> 129 MB L2)"
+                    % (nx * ny * nz * 4 / 1e6)}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), float(f[3]), f[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
+        sm = [r[0] for r in rows]
+        loaded = [r[0] for r in rows if r[2] > 200.0] or sm
+        return {"sm_mhz": float(np.median(loaded)), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "power_w_max": max(r[2] for r in rows), "reasons": reasons}
+
+
+def oracle_sample(p, seconds_target=20.0, max_steps=None):
+    """Time the FP64 oracle on the host cores on the first steps of the workload."""
+    import oracle
+    oracle.build()
+    threads = oracle.max_threads()
+    npts = p.npoints
+    probe = 2
+    t0 = time.perf_counter()
+    oracle.forward(p.vel, p.h, p.dt, probe, nbl=p.nbl, src_ijk=p.src_ijk, wavelet=p.wavelet[:, :probe],
+                   rec_ijk=p.rec_ijk)
+    per_step = (time.perf_counter() - t0) / probe
+    steps = int(max(2, min(p.nt, seconds_target / max(per_step, 1e-6))))
+    if max_steps:
+        steps = min(steps, max_steps)
+    t0 = time.perf_counter()
+    oracle.forward(p.vel, p.h, p.dt, steps, nbl=p.nbl, src_ijk=p.src_ijk, wavelet=p.wavelet[:, :steps],
+                   rec_ijk=p.rec_ijk)
+    dt = time.perf_counter() - t0
+    return {"value": npts * steps / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{p.name}: first {steps} of {p.nt} steps, FP64, OpenMP {threads} threads, "
+                      f"{dt:.1f} s"}, dt, steps
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    p = make_workload(args.workload, args.nt)
+    vals, secs = [], 0.0
+    for _ in range(args.warmup):
+        oracle_sample(p, seconds_target=2.0)
+    for _ in range(args.steps):
+        cb, dt, steps = oracle_sample(p, seconds_target=args.ref_seconds)
+        vals.append(cb["value"])
+        secs += dt
+    value = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": describe(p),
+            "cpu_baseline": {**cb, "value": value},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def traffic_from_profiles(kernel_tag: str):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    valid only while the kernel's source hash matches."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    src = os.path.join(ROOT, "paper_2007_06048_gb300", "csrc", rec.get("source", ""))
+    try:
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    if digest != rec.get("source_sha256_16") or rec.get("kernel") != kernel_tag:
+        return None
+    return rec
+
+
+def run_mmod(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2007_06048_gb300 as M
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    p = make_workload(args.workload, args.nt)
+    nz, ny, nx = p.vel.shape
+    npts = p.npoints
+    prop = M.Propagator.from_problem(p, device=local)
+    if args.kernel != "auto":
+        prop.set_kernel({"simple": M.KERNEL_SIMPLE, "tma": M.KERNEL_TMA}[args.kernel])
+    stream = torch.cuda.current_stream(dev)
+    vel_d = torch.from_numpy(p.vel).to(dev)
+    wav_d = torch.from_numpy(np.ascontiguousarray(p.wavelet)).to(dev)
+    tr_d = torch.empty((p.nt, len(p.rec_ijk)), device=dev)
+    prop.set_model(vel_d, stream)
+    kernel_tag = "tma" if (args.kernel in ("auto", "tma") and prop_uses_tma(prop)) else "simple"
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        prop.forward(wav_d, tr_d, None, stream)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    loop_ms = []
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            prop.forward(wav_d, tr_d, None, stream)
+            loop_ms.append(prop.loop_ms())     # CUDA events around the step loop, same stream
+        e1.record(stream)
+        barrier()
+    launches = prop.launches * args.steps
+    ms = e0.elapsed_time(e1)
+    ms_max = ms
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = ws * npts * p.nt * args.steps / (ms_max * 1e-3) / 1e9
+
+    # roofline of the dominant kernel: the step kernel, one launch per time step
+    peak, peak_kind = load_peaks()
+    step_ms = float(np.mean(loop_ms)) / p.nt
+    achieved = BYTES_PER_POINT * npts / (step_ms * 1e-3) / 1e9
+    tr_rec = traffic_from_profiles(kernel_tag)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"
+                if peak_kind == "measured" else "fallback 6.8 TB/s",
+                "kernel": f"step_{kernel_tag}", "bytes_per_point": BYTES_PER_POINT,
+                "launch_ms": step_ms,
+                "traffic": None if tr_rec is None else tr_rec["dram_bytes_per_launch"] * npts / tr_rec["npoints"]}
+
+    # end-to-end through the C ABI with host buffers (pinned), copies inside the timed region
+    vel_h = torch.from_numpy(p.vel).pin_memory()
+    wav_h = torch.from_numpy(np.ascontiguousarray(p.wavelet)).pin_memory()
+    tr_h = torch.empty((p.nt, len(p.rec_ijk)), pin_memory=True)
+    e2e_steps = max(1, min(args.steps, 5))
+    prop.set_model(vel_h, stream)
+    prop.forward(wav_h, tr_h, None, stream)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        prop.set_model(vel_h, stream)
+        prop.forward(wav_h, tr_h, None, stream)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": ws * npts * p.nt * e2e_steps / e2e_s / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": int(vel_h.numel() * 4 + wav_h.numel() * 4),
+           "d2h_bytes_per_step": int(tr_h.numel() * 4),
+           "api": "mmod_set_model + mmod_forward with pinned host buffers, wall clock"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu, _, _ = oracle_sample(p, seconds_target=args.ref_seconds)
+    clocks = clk.summary()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": describe(p, {"parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                                       "kernel": kernel_tag}),
+                "hbm_roofline_pct": 100.0 * BYTES_PER_POINT * value / ws / peak,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    prop.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def prop_uses_tma(prop) -> bool:
+    """True when the handle's automatic kernel choice is the TMA kernel."""
+    import paper_2007_06048_gb300 as M
+    try:
+        prop.set_kernel(M.KERNEL_TMA)
+    except M.MmodError:
+        return False
+    prop.set_kernel(M.KERNEL_AUTO)
+    return True
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["mmod", "reference"], default="mmod")
+    ap.add_argument("--workload", default="layered240")
+    ap.add_argument("--nt", type=int, default=None, help="override the workload's step count")
+    ap.add_argument("--kernel", choices=["auto", "simple", "tma"], default="auto")
+    ap.add_argument("--ref-seconds", type=float, default=20.0,
+                    help="CPU seconds per oracle sample (cpu_baseline / reference arm)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "mmod":
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_mmod(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,153 @@
+/*
+ * mmod.h — C ABI of the GB300 (sm_103a) acoustic propagator library.
+ *
+ * The library time-steps the acoustic isotropic constant-density wave
+ * equation of Minimod (arXiv 2007.06048):
+ *   Eq. 1   (1/v^2) p_tt - lap p = f
+ *   Eq. 5   p^{n+1} - Q p^n + p^{n-1} = dt^2 v^2 f^n,  Q = 2 + dt^2 v^2 lap
+ *   Sec. 3  lap as the 25-point star  sum_m c_am [p(+m) + p(-m) - 2 p],
+ *           order-8 Taylor weights (radius 4 per axis)
+ *   Alg. 1  p^0 = 0, then per step: solve for p^{n+1}, add the source term
+ *   Alg. 2  the inner region (Eq. 5) surrounded by six damping regions
+ * with damping layers, point sources and grid-point receivers.  The readings
+ * taken where the paper is silent are fixed by this ABI:
+ *   - u = 0 outside the grid;
+ *   - inside the layers the update is
+ *       u^{n+1} = [2u^n - (1 - e) u^{n-1} + c (lap u^n + s^n)] / (1 + e),
+ *     c = dt^2 v^2, e = dt (eta_x(i) + eta_y(j) + eta_z(k)),
+ *     eta_a(i) = eta_max,a (d/L)^2, d = max(L - i, i - (n_a - 1 - L), 0),
+ *     eta_max,a = 3 vmax ln(1/R) / (2 L h_a)   (e = 0 gives Eq. 5 exactly);
+ *   - a point source adds c(x_s) w[n] / (hx hy hz) to the numerator above;
+ *   - traces[n][r] = u^{n+1} at receiver r, after the source add of step n.
+ *
+ * Conventions.  Grid index (i, j, k) along (x, y, z); k = 0 is the surface.
+ * Volumes are FP32 [nz][ny][nx] (x fastest), dense, no padding.  The layers
+ * are part of the grid.  All arithmetic on the GPU is FP32.
+ *
+ * Pointers.  Every array argument may point to device memory or to host
+ * memory (pageable or pinned); the library detects which and stages host
+ * buffers through its own device buffers on the given stream.  The caller
+ * owns every pointer it passes; the handle owns its internal wavefields,
+ * coefficient volume, profiles and staging buffers.
+ *
+ * Streams.  `stream` is a cudaStream_t (NULL = the legacy default stream).
+ * Calls are stream-ordered; a call returns once its work is enqueued, except
+ * where a call says it synchronises.  With host output buffers the call
+ * synchronises the stream before returning so that the data is in place.
+ *
+ * Errors.  Every call returns an mmod_status; on failure nothing is enqueued
+ * (argument errors) or the CUDA error is latched in the handle and returned
+ * by this and every later call.  mmod_last_error() describes the last failure.
+ * A handle is not thread-safe: one host thread at a time.
+ */
+#ifndef MMOD_H
+#define MMOD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t, declared without the CUDA headers. */
+typedef struct CUstream_st *mmod_stream;
+
+typedef enum {
+    MMOD_OK = 0,
+    MMOD_ERR_ARG = -1,          /* invalid argument or configuration */
+    MMOD_ERR_UNSTABLE = -2,     /* dt too large for the model (CFL bound) */
+    MMOD_ERR_OOM = -3,          /* device allocation failed */
+    MMOD_ERR_CUDA = -4,         /* a CUDA call failed; see mmod_last_error */
+    MMOD_ERR_TIMEOUT = -5,      /* a bounded device-side wait gave up */
+    MMOD_ERR_STATE = -6,        /* call out of order (e.g. forward before set_model) */
+    MMOD_ERR_UNSUPPORTED = -7   /* valid for the oracle, not on this GPU path */
+} mmod_status;
+
+typedef struct mmod_handle mmod_handle;
+
+/* Problem description.  Mirrors the paper's run parameters (--ngrid,
+ * --dgrid, --nsteps; "stencil", "ndamping", "source_loc", "nreceivers" of
+ * the Sec. 5.3 printout). */
+typedef struct {
+    int nx, ny, nz;          /* grid points, damping layers included; each >= 1 and >= 2*nbl */
+    double hx, hy, hz;       /* grid spacing, metres, > 0 */
+    double dt;               /* time step, seconds, > 0 */
+    int nt;                  /* number of time steps, >= 0 */
+    int order;               /* spatial order; the GPU path supports 8 only */
+    int nbl;                 /* damping width in cells on all six faces, >= 0 */
+    double damp_R;           /* target reflection of the layers, 0 < R < 1 (1e-3 typical) */
+    int nsrc;                /* number of point sources, >= 0 */
+    const int *src_ijk;      /* host [nsrc][3] (i, j, k); copied by mmod_create */
+    int nrec;                /* number of receivers, >= 0 */
+    const int *rec_ijk;      /* host [nrec][3] (i, j, k); copied by mmod_create */
+} mmod_config;
+
+/* Create a handle on CUDA device `device`: validates the configuration,
+ * copies the source/receiver lists and allocates the wavefields and
+ * coefficient volume (about 3 * 4 * nx*ny*nz bytes, rows padded to 128 B).
+ * Errors: ARG (bad sizes, positions outside the grid, null lists with
+ * nonzero counts, order != 8 -> UNSUPPORTED), OOM, CUDA.  *out is NULL on
+ * failure. */
+mmod_status mmod_create(const mmod_config *cfg, int device, mmod_handle **out);
+
+/* Release everything the handle owns.  Synchronises the device work it
+ * enqueued.  NULL is accepted. */
+mmod_status mmod_destroy(mmod_handle *h);
+
+/* Load a velocity model vel [nz][ny][nx] (m/s, FP32, all > 0): computes
+ * c = dt^2 v^2 (rounded once from FP64 to FP32), the model maximum vmax and
+ * the damping profiles.  Synchronises `stream` (vmax is read back for the
+ * stability check).  Errors: ARG (null, non-positive or non-finite values),
+ * UNSTABLE when dt * vmax * sqrt(sum_a 6.5016 / h_a^2) > 2 (the order-8
+ * stencil's largest symbol magnitude is 6.5016 / h^2 per axis), CUDA. */
+mmod_status mmod_set_model(mmod_handle *h, const float *vel, mmod_stream stream);
+
+/* Forward modelling, Alg. 1: nt steps from u^{-1} = u^0 = 0 (or from the
+ * state given by mmod_set_state, consumed by this call).
+ *   wavelet  [nsrc][nt] FP32 source time functions w[n] (n = 0..nt-1);
+ *            may be NULL when nsrc == 0
+ *   traces   [nt][nrec] FP32 output, traces[n][r] = u^{n+1}(x_r); may be
+ *            NULL when nrec == 0
+ *   final_u  optional [nz][ny][nx] FP32 output u^{nt}
+ * Errors: STATE (no model), ARG, CUDA, TIMEOUT. */
+mmod_status mmod_forward(mmod_handle *h, const float *wavelet, float *traces,
+                         float *final_u, mmod_stream stream);
+
+/* Test hook: the next mmod_forward starts from u^{-1} = u_prev, u^0 = u_cur
+ * ([nz][ny][nx] FP32, either may be NULL for zeros) instead of zeros. */
+mmod_status mmod_set_state(mmod_handle *h, const float *u_prev, const float *u_cur,
+                           mmod_stream stream);
+
+/* Copy the last forward's final state u^{nt-1}, u^{nt} (either may be NULL). */
+mmod_status mmod_get_state(mmod_handle *h, float *u_prev, float *u_cur, mmod_stream stream);
+
+/* Kernel selection for validation: MMOD_KERNEL_AUTO (default) picks the
+ * TMA-pipelined kernel; MMOD_KERNEL_SIMPLE runs the plain one-thread-per-
+ * point kernel, which performs the identical FP32 operations per point. */
+enum { MMOD_KERNEL_AUTO = 0, MMOD_KERNEL_SIMPLE = 1, MMOD_KERNEL_TMA = 2 };
+mmod_status mmod_set_kernel(mmod_handle *h, int kernel);
+
+/* Number of kernel launches the last mmod_forward enqueued (all of this
+ * library's kernels, including set-up and gathers). */
+long long mmod_last_launch_count(const mmod_handle *h);
+
+/* Device time in milliseconds of the last mmod_forward's time loop (all
+ * step and gather kernels between two CUDA events recorded on the call's
+ * stream inside the captured graph).  Waits for that work to finish.
+ * Returns a negative value when no loop has run. */
+float mmod_last_loop_ms(mmod_handle *h);
+
+/* dt = cfl * hmin / vmax (the CFL reading of the workloads).  Returns a
+ * negative value for non-positive arguments. */
+double mmod_cfl_dt(double cfl, double hmin, double vmax);
+
+/* Human-readable description of the handle's last failure ("" if none).
+ * The string is owned by the handle and valid until its next call.  With
+ * h == NULL: the calling thread's last mmod_create failure. */
+const char *mmod_last_error(const mmod_handle *h);
+
+/* Library version string, e.g. "mmod-gb300 0.1 sm_103a". */
+const char *mmod_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MMOD_H */

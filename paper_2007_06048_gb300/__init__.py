@@ -1,0 +1,242 @@
+"""Python binding of the GB300 acoustic propagator library (include/mmod.h).
+
+Argument marshalling only: every step of the propagator runs in the CUDA
+kernels of ``libmmod.so``.  The functions keep the C names (``mmod_create``,
+``mmod_set_model``, ``mmod_forward`` ...); array arguments may be torch tensors
+(device or host), numpy arrays (host) or raw integer addresses, and streams are
+``torch.cuda.Stream`` objects, raw ``cudaStream_t`` integers or ``None`` (the
+current torch stream when torch has CUDA, else the legacy default stream).
+
+There is no CPU fallback: without a loadable library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+__all__ = ["MmodError", "build", "load", "mmod_create", "mmod_destroy", "mmod_set_model",
+           "mmod_forward", "mmod_set_state", "mmod_get_state", "mmod_set_kernel",
+           "mmod_last_error", "mmod_last_launch_count", "mmod_last_loop_ms", "mmod_cfl_dt",
+           "mmod_version", "Propagator", "STATUS", "EXPORTED"]
+
+STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_UNSTABLE", -3: "ERR_OOM", -4: "ERR_CUDA",
+          -5: "ERR_TIMEOUT", -6: "ERR_STATE", -7: "ERR_UNSUPPORTED"}
+KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_TMA = 0, 1, 2
+
+# Every symbol include/mmod.h declares (checked against the header by the tests).
+EXPORTED = ["mmod_create", "mmod_destroy", "mmod_set_model", "mmod_forward", "mmod_set_state",
+            "mmod_get_state", "mmod_set_kernel", "mmod_last_launch_count", "mmod_last_loop_ms",
+            "mmod_cfl_dt", "mmod_last_error", "mmod_version"]
+
+
+class MmodError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("hx", ctypes.c_double), ("hy", ctypes.c_double), ("hz", ctypes.c_double),
+                ("dt", ctypes.c_double), ("nt", ctypes.c_int), ("order", ctypes.c_int),
+                ("nbl", ctypes.c_int), ("damp_R", ctypes.c_double),
+                ("nsrc", ctypes.c_int), ("src_ijk", ctypes.c_void_p),
+                ("nrec", ctypes.c_int), ("rec_ijk", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile libmmod.so for sm_103a (nvcc) if missing or stale."""
+    return _build.build(force=force)
+
+
+def load():
+    """Load libmmod.so (building it first if needed) and declare signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if _build.is_stale():
+        _build.build()
+    lib = ctypes.CDLL(_build.LIB)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "mmod_create": ([ctypes.POINTER(_Config), I, ctypes.POINTER(P)], I),
+        "mmod_destroy": ([P], I),
+        "mmod_set_model": ([P, P, P], I),
+        "mmod_forward": ([P, P, P, P, P], I),
+        "mmod_set_state": ([P, P, P, P], I),
+        "mmod_get_state": ([P, P, P, P], I),
+        "mmod_set_kernel": ([P, I], I),
+        "mmod_last_launch_count": ([P], ctypes.c_longlong),
+        "mmod_last_loop_ms": ([P], ctypes.c_float),
+        "mmod_cfl_dt": ([D, D, D], D),
+        "mmod_last_error": ([P], ctypes.c_char_p),
+        "mmod_version": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _addr(x):
+    """Address of a tensor / array / int (None -> NULL).  Keeps no copies."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x).__name__}")
+
+
+def _stream(s):
+    if s is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(h, st: int):
+    if st != 0:
+        msg = load().mmod_last_error(h).decode() if h else ""
+        raise MmodError(st, msg)
+
+
+def mmod_cfl_dt(cfl: float, hmin: float, vmax: float) -> float:
+    return load().mmod_cfl_dt(cfl, hmin, vmax)
+
+
+def mmod_version() -> str:
+    return load().mmod_version().decode()
+
+
+def mmod_create(nx, ny, nz, h, dt, nt, *, nbl=0, src_ijk=None, rec_ijk=None, order=8,
+                damp_R=1e-3, device=0):
+    """Create a handle (ctypes void pointer).  src_ijk / rec_ijk: [n][3] int."""
+    src = np.ascontiguousarray(np.zeros((0, 3)) if src_ijk is None else src_ijk, np.int32).reshape(-1, 3)
+    rec = np.ascontiguousarray(np.zeros((0, 3)) if rec_ijk is None else rec_ijk, np.int32).reshape(-1, 3)
+    cfg = _Config(int(nx), int(ny), int(nz), float(h[0]), float(h[1]), float(h[2]), float(dt), int(nt),
+                  int(order), int(nbl), float(damp_R), len(src), src.ctypes.data if len(src) else None,
+                  len(rec), rec.ctypes.data if len(rec) else None)
+    out = ctypes.c_void_p()
+    st = load().mmod_create(ctypes.byref(cfg), int(device), ctypes.byref(out))
+    if st != 0:
+        raise MmodError(st, load().mmod_last_error(None).decode())
+    return out
+
+
+def mmod_destroy(h):
+    _check(None, load().mmod_destroy(h))
+
+
+def mmod_set_model(h, vel, stream=None):
+    _check(h, load().mmod_set_model(h, _addr(vel), _stream(stream)))
+
+
+def mmod_forward(h, wavelet, traces, final_u=None, stream=None):
+    _check(h, load().mmod_forward(h, _addr(wavelet), _addr(traces), _addr(final_u), _stream(stream)))
+
+
+def mmod_set_state(h, u_prev, u_cur, stream=None):
+    _check(h, load().mmod_set_state(h, _addr(u_prev), _addr(u_cur), _stream(stream)))
+
+
+def mmod_get_state(h, u_prev, u_cur, stream=None):
+    _check(h, load().mmod_get_state(h, _addr(u_prev), _addr(u_cur), _stream(stream)))
+
+
+def mmod_set_kernel(h, kernel: int):
+    _check(h, load().mmod_set_kernel(h, int(kernel)))
+
+
+def mmod_last_error(h) -> str:
+    return load().mmod_last_error(h).decode()
+
+
+def mmod_last_launch_count(h) -> int:
+    return int(load().mmod_last_launch_count(h))
+
+
+def mmod_last_loop_ms(h) -> float:
+    return float(load().mmod_last_loop_ms(h))
+
+
+class Propagator:
+    """Owning wrapper around one handle for a given problem geometry."""
+
+    def __init__(self, shape, h, dt, nt, *, nbl=0, src_ijk=None, rec_ijk=None, damp_R=1e-3,
+                 device=0, order=8):
+        nz, ny, nx = shape
+        self.shape = tuple(shape)
+        self.nt = int(nt)
+        self.nsrc = 0 if src_ijk is None else len(np.asarray(src_ijk).reshape(-1, 3))
+        self.nrec = 0 if rec_ijk is None else len(np.asarray(rec_ijk).reshape(-1, 3))
+        self.device = device
+        self.handle = mmod_create(nx, ny, nz, h, dt, nt, nbl=nbl, src_ijk=src_ijk, rec_ijk=rec_ijk,
+                                  order=order, damp_R=damp_R, device=device)
+
+    @classmethod
+    def from_problem(cls, p, device=0):
+        return cls(p.vel.shape, p.h, p.dt, p.nt, nbl=p.nbl, src_ijk=p.src_ijk, rec_ijk=p.rec_ijk,
+                   damp_R=p.refl, device=device, order=p.order)
+
+    def set_model(self, vel, stream=None):
+        mmod_set_model(self.handle, vel, stream)
+
+    def set_kernel(self, kernel: int):
+        mmod_set_kernel(self.handle, kernel)
+
+    def forward(self, wavelet, traces, final_u=None, stream=None):
+        mmod_forward(self.handle, wavelet, traces, final_u, stream)
+
+    def set_state(self, u_prev, u_cur, stream=None):
+        mmod_set_state(self.handle, u_prev, u_cur, stream)
+
+    def get_state(self, u_prev, u_cur, stream=None):
+        mmod_get_state(self.handle, u_prev, u_cur, stream)
+
+    @property
+    def launches(self) -> int:
+        return mmod_last_launch_count(self.handle)
+
+    def loop_ms(self) -> float:
+        return mmod_last_loop_ms(self.handle)
+
+    def close(self):
+        if self.handle is not None:
+            mmod_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

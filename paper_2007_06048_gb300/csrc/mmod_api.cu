@@ -1,0 +1,561 @@
+// C ABI of the propagator (include/mmod.h): validation, the handle, staging of
+// host buffers, the CUDA-graph-captured time loop (Alg. 1) and error latching.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "mmod_internal.h"
+#include "tma_plan.h"
+
+#define MMOD_API extern "C" __attribute__((visibility("default")))
+
+using namespace mmod;
+
+namespace {
+
+// Order-8 Taylor weights of the second derivative (Sec. 3):
+// c_1..c_4 = 8/5, -1/5, 8/315, -1/560.
+constexpr double kTaylor8[4] = {8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0};
+// Largest magnitude of the order-8 stencil's symbol (at k h = pi):
+// 4 (c_1 + c_3) = 2048 / 315; leapfrog is stable iff dt^2 v^2 sum_a K_a <= 4.
+constexpr double kSymbolMax8 = 2048.0 / 315.0;
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int d) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != d) cudaSetDevice(d);
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Message of the calling thread's last mmod_create failure.
+thread_local std::string g_create_err;
+
+}  // namespace
+
+struct mmod_handle {
+    mmod_config cfg{};
+    std::vector<int> src, rec;     // owned copies of the position lists
+    int device = 0;
+    int nxp = 0;
+    long long plane = 0, vol = 0;  // padded plane / volume, in floats
+    long long npts = 0;            // nx * ny * nz
+    Weights w{};
+
+    float *u[2] = {nullptr, nullptr};   // wavefields (padded)
+    float *c = nullptr;                 // dt^2 v^2 (padded)
+    float *eta = nullptr;               // dt * eta_x | dt * eta_y | dt * eta_z
+    int *src_kstart = nullptr, *src_i = nullptr, *src_j = nullptr, *src_k = nullptr,
+        *src_row = nullptr;
+    float *src_scale = nullptr;
+    long long *rec_off = nullptr;
+    unsigned int *vmax_bits = nullptr;
+    unsigned long long *bad = nullptr;
+
+    float *st_vol = nullptr;            // dense [nz][ny][nx] staging (lazy)
+    float *st_wav = nullptr;            // [nsrc][nt] staging (lazy)
+    float *st_tr = nullptr;             // [nt][nrec] staging (lazy)
+
+    cudaStream_t cap = nullptr;         // private stream used only for graph capture
+    cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;   // bracket the step loop
+    cudaGraphExec_t gexec = nullptr;
+    const float *g_wav = nullptr;
+    float *g_tr = nullptr;
+    int g_kernel = -1;
+    long long g_launches = 0;
+
+    TmaPlan plan{};
+    bool tma_ok = false;
+    CUtensorMap cur_map[2], prev_map[2], c_map;
+
+    bool model_set = false;
+    double vmax = 0.0;
+    bool state_pending = false;
+    bool ran = false;
+    int kernel = MMOD_KERNEL_AUTO;
+    long long last_launches = 0;
+    cudaError_t latched = cudaSuccess;
+    std::string err;
+};
+
+namespace {
+
+mmod_status fail(mmod_handle *h, mmod_status st, const std::string &msg) {
+    if (h) h->err = msg;
+    return st;
+}
+
+mmod_status fail_cuda(mmod_handle *h, cudaError_t e, const char *what) {
+    if (h) {
+        if (h->latched == cudaSuccess) h->latched = e;
+        h->err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    }
+    return e == cudaErrorMemoryAllocation ? MMOD_ERR_OOM : MMOD_ERR_CUDA;
+}
+
+#define CK(h, call)                                   \
+    do {                                              \
+        cudaError_t _e = (call);                      \
+        if (_e != cudaSuccess) return fail_cuda((h), _e, #call); \
+    } while (0)
+
+mmod_status check_latched(mmod_handle *h) {
+    if (h->latched != cudaSuccess) {
+        h->err = std::string("earlier CUDA failure: ") + cudaGetErrorName(h->latched);
+        return MMOD_ERR_CUDA;
+    }
+    return MMOD_OK;
+}
+
+bool in_grid(const mmod_config &c, const int *p) {
+    return p[0] >= 0 && p[0] < c.nx && p[1] >= 0 && p[1] < c.ny && p[2] >= 0 && p[2] < c.nz;
+}
+
+std::string validate(const mmod_config *c, mmod_status *st) {
+    *st = MMOD_ERR_ARG;
+    if (!c) return "null config";
+    if (c->nx < 1 || c->ny < 1 || c->nz < 1) return "grid sizes must be >= 1";
+    if ((long long)c->nx * c->ny * c->nz > (1LL << 36)) return "grid too large";
+    if (!(c->hx > 0 && c->hy > 0 && c->hz > 0) || !std::isfinite(c->hx) ||
+        !std::isfinite(c->hy) || !std::isfinite(c->hz))
+        return "grid spacings must be positive and finite";
+    if (!(c->dt > 0) || !std::isfinite(c->dt)) return "dt must be positive and finite";
+    if (c->nt < 0) return "nt must be >= 0";
+    if (c->nbl < 0 || 2LL * c->nbl > c->nx || 2LL * c->nbl > c->ny || 2LL * c->nbl > c->nz)
+        return "damping width must satisfy 0 <= 2*nbl <= n on every axis";
+    if (c->nbl > 0 && !(c->damp_R > 0 && c->damp_R < 1)) return "damp_R must be in (0, 1)";
+    if (c->nsrc < 0 || c->nrec < 0) return "negative source/receiver count";
+    if (c->nsrc > 0 && !c->src_ijk) return "null source list";
+    if (c->nrec > 0 && !c->rec_ijk) return "null receiver list";
+    for (int s = 0; s < c->nsrc; ++s)
+        if (!in_grid(*c, c->src_ijk + 3 * s)) return "source " + std::to_string(s) + " outside the grid";
+    for (int r = 0; r < c->nrec; ++r)
+        if (!in_grid(*c, c->rec_ijk + 3 * r)) return "receiver " + std::to_string(r) + " outside the grid";
+    if (c->order != 8) {
+        *st = MMOD_ERR_UNSUPPORTED;
+        return "the GPU path implements order 8 only";
+    }
+    *st = MMOD_OK;
+    return "";
+}
+
+void free_all(mmod_handle *h) {
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    for (float *p : {h->u[0], h->u[1], h->c, h->eta, h->src_scale, h->st_vol, h->st_wav, h->st_tr})
+        if (p) cudaFree(p);
+    for (int *p : {h->src_kstart, h->src_i, h->src_j, h->src_k, h->src_row})
+        if (p) cudaFree(p);
+    if (h->rec_off) cudaFree(h->rec_off);
+    if (h->vmax_bits) cudaFree(h->vmax_bits);
+    if (h->bad) cudaFree(h->bad);
+    if (h->ev_t0) cudaEventDestroy(h->ev_t0);
+    if (h->ev_t1) cudaEventDestroy(h->ev_t1);
+    if (h->cap) cudaStreamDestroy(h->cap);
+}
+
+// Damping profile of one axis (the ABI's reading of the layers), FP64 -> FP32
+// after multiplying by dt.
+void damping_profile(int n, int nbl, double h, double vmax, double R, double dt, float *out) {
+    if (nbl == 0) {
+        std::fill(out, out + n, 0.0f);
+        return;
+    }
+    const double eta_max = 1.5 * vmax * std::log(1.0 / R) / (nbl * h);
+    for (int i = 0; i < n; ++i) {
+        const int d = std::max({nbl - i, i - (n - 1 - nbl), 0});
+        const double s = (double)d / nbl;
+        out[i] = (float)(dt * eta_max * s * s);
+    }
+}
+
+StepArgs step_args(mmod_handle *h, const float *wavelet, float *traces, int n) {
+    StepArgs a{};
+    a.nx = h->cfg.nx; a.ny = h->cfg.ny; a.nz = h->cfg.nz;
+    a.nxp = h->nxp; a.plane = h->plane; a.nbl = h->cfg.nbl; a.nt = h->cfg.nt; a.n = n;
+    a.w = h->w;
+    a.ucur = h->u[(n + 1) & 1];
+    a.uprev = h->u[n & 1];
+    a.c = h->c;
+    a.ex = h->eta; a.ey = h->eta + h->cfg.nx; a.ez = h->eta + h->cfg.nx + h->cfg.ny;
+    a.src_kstart = h->src_kstart; a.src_i = h->src_i; a.src_j = h->src_j; a.src_row = h->src_row;
+    a.src_scale = h->src_scale; a.wavelet = wavelet;
+    a.nrec = h->cfg.nrec; a.rec_off = h->rec_off;
+    a.traces = (n >= 1 && traces) ? traces + (long long)(n - 1) * h->cfg.nrec : nullptr;
+    return a;
+}
+
+bool use_tma(const mmod_handle *h) {
+    return h->tma_ok && (h->kernel == MMOD_KERNEL_AUTO || h->kernel == MMOD_KERNEL_TMA);
+}
+
+// Enqueue the nt steps (and receiver gathers) on stream s.  Returns the
+// number of kernels launched.
+mmod_status enqueue_steps(mmod_handle *h, const float *wav, float *tr, cudaStream_t s, long long *nlaunch) {
+    const int nt = h->cfg.nt, nrec = h->cfg.nrec;
+    long long count = 0;
+    const bool tma = use_tma(h);
+    CK(h, cudaEventRecord(h->ev_t0, s));
+    for (int n = 0; n < nt; ++n) {
+        StepArgs a = step_args(h, wav, tr, n);
+        if (tma) {
+            CK(h, launch_step_tma(a, &h->cur_map[(n + 1) & 1], &h->prev_map[n & 1], &h->c_map, h->plan, s));
+            ++count;
+        } else {
+            a.traces = nullptr;   // the plain path gathers with a separate kernel
+            CK(h, launch_step_simple(a, s));
+            ++count;
+            if (nrec > 0 && tr) {
+                CK(h, launch_gather(h->u[n & 1], h->rec_off, nrec, tr + (long long)n * nrec, s));
+                ++count;
+            }
+        }
+    }
+    if (tma && nt > 0 && nrec > 0 && tr) {
+        // u^{nt} sits in u[(nt - 1) & 1]; the last step kernel had no successor
+        CK(h, launch_gather(h->u[(nt - 1) & 1], h->rec_off, nrec, tr + (long long)(nt - 1) * nrec, s));
+        ++count;
+    }
+    CK(h, cudaEventRecord(h->ev_t1, s));
+    *nlaunch = count;
+    return MMOD_OK;
+}
+
+}  // namespace
+
+MMOD_API double mmod_cfl_dt(double cfl, double hmin, double vmax) {
+    if (!(cfl > 0) || !(hmin > 0) || !(vmax > 0)) return -1.0;
+    return cfl * hmin / vmax;
+}
+
+MMOD_API const char *mmod_version(void) { return "mmod-gb300 0.1 sm_103a"; }
+
+MMOD_API const char *mmod_last_error(const mmod_handle *h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+MMOD_API long long mmod_last_launch_count(const mmod_handle *h) { return h ? h->last_launches : -1; }
+
+MMOD_API mmod_status mmod_create(const mmod_config *cfg, int device, mmod_handle **out) {
+    g_create_err.clear();
+    if (!out) {
+        g_create_err = "null output pointer";
+        return MMOD_ERR_ARG;
+    }
+    *out = nullptr;
+    mmod_status st;
+    const std::string why = validate(cfg, &st);
+    if (st != MMOD_OK) {
+        g_create_err = why;
+        return st;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        g_create_err = "CUDA device " + std::to_string(device) + " not available";
+        return MMOD_ERR_CUDA;
+    }
+    DeviceGuard guard(device);
+    mmod_handle *h = new (std::nothrow) mmod_handle();
+    if (!h) return MMOD_ERR_OOM;
+    h->cfg = *cfg;
+    h->device = device;
+    h->src.assign(cfg->src_ijk, cfg->src_ijk + 3 * (size_t)cfg->nsrc);
+    h->rec.assign(cfg->rec_ijk, cfg->rec_ijk + 3 * (size_t)cfg->nrec);
+    h->cfg.src_ijk = h->src.data();
+    h->cfg.rec_ijk = h->rec.data();
+    const int nx = cfg->nx, ny = cfg->ny, nz = cfg->nz;
+    h->nxp = (nx + 31) / 32 * 32;
+    h->plane = (long long)h->nxp * ny;
+    h->vol = h->plane * nz;
+    h->npts = (long long)nx * ny * nz;
+    for (int m = 0; m < kRadius; ++m) {
+        h->w.x[m] = (float)(kTaylor8[m] / (cfg->hx * cfg->hx));
+        h->w.y[m] = (float)(kTaylor8[m] / (cfg->hy * cfg->hy));
+        h->w.z[m] = (float)(kTaylor8[m] / (cfg->hz * cfg->hz));
+    }
+
+    auto bail = [&](cudaError_t e, const char *what) {
+        g_create_err = std::string(what) + ": " + cudaGetErrorString(e);
+        free_all(h);
+        delete h;
+        return e == cudaErrorMemoryAllocation ? MMOD_ERR_OOM : MMOD_ERR_CUDA;
+    };
+#define CKC(call)                                  \
+    do {                                           \
+        cudaError_t _e = (call);                   \
+        if (_e != cudaSuccess) return bail(_e, #call); \
+    } while (0)
+
+    const size_t vbytes = sizeof(float) * (size_t)h->vol;
+    CKC(cudaMalloc(&h->u[0], vbytes));
+    CKC(cudaMalloc(&h->u[1], vbytes));
+    CKC(cudaMalloc(&h->c, vbytes));
+    CKC(cudaMalloc(&h->eta, sizeof(float) * (size_t)(nx + ny + nz)));
+    CKC(cudaMemset(h->u[0], 0, vbytes));
+    CKC(cudaMemset(h->u[1], 0, vbytes));
+    CKC(cudaMemset(h->c, 0, vbytes));
+    CKC(cudaMemset(h->eta, 0, sizeof(float) * (size_t)(nx + ny + nz)));
+    CKC(cudaMalloc(&h->vmax_bits, sizeof(unsigned int)));
+    CKC(cudaMalloc(&h->bad, sizeof(unsigned long long)));
+
+    // Sources sorted by depth (stable: sources at one point keep their order).
+    const int nsrc = cfg->nsrc;
+    std::vector<int> order(nsrc);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return h->src[3 * a + 2] < h->src[3 * b + 2]; });
+    std::vector<int> kstart(nz + 1, 0), si(nsrc), sj(nsrc), sk(nsrc), srow(nsrc);
+    for (int t = 0; t < nsrc; ++t) {
+        const int s = order[t];
+        si[t] = h->src[3 * s]; sj[t] = h->src[3 * s + 1]; sk[t] = h->src[3 * s + 2]; srow[t] = s;
+        kstart[sk[t] + 1]++;
+    }
+    for (int k = 0; k < nz; ++k) kstart[k + 1] += kstart[k];
+    CKC(cudaMalloc(&h->src_kstart, sizeof(int) * (nz + 1)));
+    CKC(cudaMemcpy(h->src_kstart, kstart.data(), sizeof(int) * (nz + 1), cudaMemcpyHostToDevice));
+    const size_t sb = sizeof(int) * (size_t)std::max(nsrc, 1);
+    CKC(cudaMalloc(&h->src_i, sb));
+    CKC(cudaMalloc(&h->src_j, sb));
+    CKC(cudaMalloc(&h->src_k, sb));
+    CKC(cudaMalloc(&h->src_row, sb));
+    CKC(cudaMalloc(&h->src_scale, sizeof(float) * (size_t)std::max(nsrc, 1)));
+    if (nsrc) {
+        CKC(cudaMemcpy(h->src_i, si.data(), sizeof(int) * nsrc, cudaMemcpyHostToDevice));
+        CKC(cudaMemcpy(h->src_j, sj.data(), sizeof(int) * nsrc, cudaMemcpyHostToDevice));
+        CKC(cudaMemcpy(h->src_k, sk.data(), sizeof(int) * nsrc, cudaMemcpyHostToDevice));
+        CKC(cudaMemcpy(h->src_row, srow.data(), sizeof(int) * nsrc, cudaMemcpyHostToDevice));
+        CKC(cudaMemset(h->src_scale, 0, sizeof(float) * nsrc));
+    }
+    const int nrec = cfg->nrec;
+    std::vector<long long> roff(std::max(nrec, 1), 0);
+    for (int r = 0; r < nrec; ++r)
+        roff[r] = (long long)h->rec[3 * r + 2] * h->plane + (long long)h->rec[3 * r + 1] * h->nxp + h->rec[3 * r];
+    CKC(cudaMalloc(&h->rec_off, sizeof(long long) * roff.size()));
+    CKC(cudaMemcpy(h->rec_off, roff.data(), sizeof(long long) * roff.size(), cudaMemcpyHostToDevice));
+
+    CKC(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+    CKC(cudaEventCreate(&h->ev_t0));
+    CKC(cudaEventCreate(&h->ev_t1));
+    h->tma_ok = make_tma_plan(h->cfg, h->nxp, h->u, h->c, h->cur_map, h->prev_map, &h->c_map, &h->plan);
+#undef CKC
+    *out = h;
+    return MMOD_OK;
+}
+
+MMOD_API mmod_status mmod_destroy(mmod_handle *h) {
+    if (!h) return MMOD_OK;
+    {
+        DeviceGuard guard(h->device);
+        cudaDeviceSynchronize();
+        free_all(h);
+    }
+    delete h;
+    return MMOD_OK;
+}
+
+MMOD_API mmod_status mmod_set_kernel(mmod_handle *h, int kernel) {
+    if (!h) return MMOD_ERR_ARG;
+    if (kernel != MMOD_KERNEL_AUTO && kernel != MMOD_KERNEL_SIMPLE && kernel != MMOD_KERNEL_TMA)
+        return fail(h, MMOD_ERR_ARG, "unknown kernel id");
+    if (kernel == MMOD_KERNEL_TMA && !h->tma_ok)
+        return fail(h, MMOD_ERR_UNSUPPORTED, "TMA kernel unavailable for this grid");
+    h->kernel = kernel;
+    return MMOD_OK;
+}
+
+MMOD_API mmod_status mmod_set_model(mmod_handle *h, const float *vel, mmod_stream stream) {
+    if (!h) return MMOD_ERR_ARG;
+    if (!vel) return fail(h, MMOD_ERR_ARG, "null velocity");
+    if (mmod_status st = check_latched(h)) return st;
+    DeviceGuard guard(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const auto &c = h->cfg;
+    const float *dvel = vel;
+    if (!is_device_ptr(vel)) {
+        if (!h->st_vol) CK(h, cudaMalloc(&h->st_vol, sizeof(float) * (size_t)h->npts));
+        CK(h, cudaMemcpyAsync(h->st_vol, vel, sizeof(float) * (size_t)h->npts, cudaMemcpyHostToDevice, s));
+        dvel = h->st_vol;
+    }
+    CK(h, cudaMemsetAsync(h->vmax_bits, 0, sizeof(unsigned int), s));
+    CK(h, cudaMemsetAsync(h->bad, 0, sizeof(unsigned long long), s));
+    CK(h, launch_model_scan(dvel, h->npts, h->vmax_bits, h->bad, s));
+    unsigned int vbits = 0;
+    unsigned long long nbad = 0;
+    CK(h, cudaMemcpyAsync(&vbits, h->vmax_bits, sizeof(vbits), cudaMemcpyDeviceToHost, s));
+    CK(h, cudaMemcpyAsync(&nbad, h->bad, sizeof(nbad), cudaMemcpyDeviceToHost, s));
+    CK(h, cudaStreamSynchronize(s));
+    if (nbad) return fail(h, MMOD_ERR_ARG, std::to_string(nbad) + " velocities are not positive and finite");
+    float vmaxf;
+    std::memcpy(&vmaxf, &vbits, sizeof(vmaxf));
+    const double vmax = vmaxf;
+    const double ksum = kSymbolMax8 * (1.0 / (c.hx * c.hx) + 1.0 / (c.hy * c.hy) + 1.0 / (c.hz * c.hz));
+    if (c.dt * vmax * std::sqrt(ksum) > 2.0) {
+        h->model_set = false;
+        return fail(h, MMOD_ERR_UNSTABLE, "dt too large: dt*vmax*sqrt(sum 6.5016/h^2) = " +
+                                              std::to_string(c.dt * vmax * std::sqrt(ksum)) + " > 2");
+    }
+    CK(h, launch_model_fill(dvel, c.nx, c.ny, c.nz, h->nxp, c.dt, h->c, s));
+    CK(h, launch_source_scale(dvel, c.nx, c.ny, c.nsrc, h->src_i, h->src_j, h->src_k, c.dt,
+                              c.hx * c.hy * c.hz, h->src_scale, s));
+    std::vector<float> eta(c.nx + c.ny + c.nz);
+    damping_profile(c.nx, c.nbl, c.hx, vmax, c.damp_R, c.dt, eta.data());
+    damping_profile(c.ny, c.nbl, c.hy, vmax, c.damp_R, c.dt, eta.data() + c.nx);
+    damping_profile(c.nz, c.nbl, c.hz, vmax, c.damp_R, c.dt, eta.data() + c.nx + c.ny);
+    CK(h, cudaMemcpyAsync(h->eta, eta.data(), sizeof(float) * eta.size(), cudaMemcpyHostToDevice, s));
+    CK(h, cudaStreamSynchronize(s));   // eta lives on the host stack
+    h->vmax = vmax;
+    h->model_set = true;
+    return MMOD_OK;
+}
+
+MMOD_API mmod_status mmod_set_state(mmod_handle *h, const float *u_prev, const float *u_cur,
+                                    mmod_stream stream) {
+    if (!h) return MMOD_ERR_ARG;
+    if (mmod_status st = check_latched(h)) return st;
+    DeviceGuard guard(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const float *src[2] = {u_prev, u_cur};
+    for (int b = 0; b < 2; ++b) {
+        const float *d = src[b];
+        if (d && !is_device_ptr(d)) {
+            if (!h->st_vol) CK(h, cudaMalloc(&h->st_vol, sizeof(float) * (size_t)h->npts));
+            CK(h, cudaMemcpyAsync(h->st_vol, d, sizeof(float) * (size_t)h->npts, cudaMemcpyHostToDevice, s));
+            d = h->st_vol;
+        }
+        // buffer 0 holds u^{n-1}, buffer 1 holds u^n at step 0
+        CK(h, launch_pack(d, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->nxp, h->u[b], s));
+    }
+    h->state_pending = true;
+    return MMOD_OK;
+}
+
+MMOD_API mmod_status mmod_get_state(mmod_handle *h, float *u_prev, float *u_cur, mmod_stream stream) {
+    if (!h) return MMOD_ERR_ARG;
+    if (mmod_status st = check_latched(h)) return st;
+    if (!h->ran) return fail(h, MMOD_ERR_STATE, "no forward run yet");
+    DeviceGuard guard(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nt = h->cfg.nt;
+    // after nt steps u^{nt} is in buffer (nt+1)&1 and u^{nt-1} in nt&1
+    float *dst[2] = {u_prev, u_cur};
+    const float *bufs[2] = {h->u[nt & 1], h->u[(nt + 1) & 1]};
+    for (int b = 0; b < 2; ++b) {
+        if (!dst[b]) continue;
+        if (is_device_ptr(dst[b])) {
+            CK(h, launch_unpack(bufs[b], h->cfg.nx, h->cfg.ny, h->cfg.nz, h->nxp, dst[b], s));
+        } else {
+            if (!h->st_vol) CK(h, cudaMalloc(&h->st_vol, sizeof(float) * (size_t)h->npts));
+            CK(h, launch_unpack(bufs[b], h->cfg.nx, h->cfg.ny, h->cfg.nz, h->nxp, h->st_vol, s));
+            CK(h, cudaMemcpyAsync(dst[b], h->st_vol, sizeof(float) * (size_t)h->npts, cudaMemcpyDeviceToHost, s));
+            CK(h, cudaStreamSynchronize(s));
+        }
+    }
+    return MMOD_OK;
+}
+
+MMOD_API mmod_status mmod_forward(mmod_handle *h, const float *wavelet, float *traces, float *final_u,
+                                  mmod_stream stream) {
+    if (!h) return MMOD_ERR_ARG;
+    if (mmod_status st = check_latched(h)) return st;
+    if (!h->model_set) return fail(h, MMOD_ERR_STATE, "mmod_set_model has not succeeded");
+    const auto &c = h->cfg;
+    if (c.nsrc > 0 && !wavelet) return fail(h, MMOD_ERR_ARG, "null wavelet with nsrc > 0");
+    if (c.nrec > 0 && c.nt > 0 && !traces) return fail(h, MMOD_ERR_ARG, "null traces with nrec > 0");
+    DeviceGuard guard(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    long long launches = 0;
+
+    const float *dwav = wavelet;
+    const size_t nwav = (size_t)c.nsrc * c.nt;
+    if (c.nsrc > 0 && nwav > 0 && !is_device_ptr(wavelet)) {
+        if (!h->st_wav) CK(h, cudaMalloc(&h->st_wav, sizeof(float) * nwav));
+        CK(h, cudaMemcpyAsync(h->st_wav, wavelet, sizeof(float) * nwav, cudaMemcpyHostToDevice, s));
+        dwav = h->st_wav;
+    }
+    float *dtr = traces;
+    const bool host_tr = c.nrec > 0 && c.nt > 0 && !is_device_ptr(traces);
+    const size_t ntr = (size_t)c.nrec * c.nt;
+    if (host_tr) {
+        if (!h->st_tr) CK(h, cudaMalloc(&h->st_tr, sizeof(float) * ntr));
+        dtr = h->st_tr;
+    }
+    if (!h->state_pending) {
+        CK(h, cudaMemsetAsync(h->u[0], 0, sizeof(float) * (size_t)h->vol, s));
+        CK(h, cudaMemsetAsync(h->u[1], 0, sizeof(float) * (size_t)h->vol, s));
+    }
+    h->state_pending = false;
+
+    if (c.nt > 0) {
+        const int kern = use_tma(h) ? MMOD_KERNEL_TMA : MMOD_KERNEL_SIMPLE;
+        if (!h->gexec || h->g_wav != dwav || h->g_tr != dtr || h->g_kernel != kern) {
+            if (h->gexec) {
+                cudaGraphExecDestroy(h->gexec);
+                h->gexec = nullptr;
+            }
+            cudaGraph_t graph = nullptr;
+            CK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+            long long n_l = 0;
+            mmod_status st = enqueue_steps(h, dwav, dtr, h->cap, &n_l);
+            cudaError_t e_end = cudaStreamEndCapture(h->cap, &graph);
+            if (st != MMOD_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return st;
+            }
+            if (e_end != cudaSuccess) return fail_cuda(h, e_end, "cudaStreamEndCapture");
+            cudaError_t e_inst = cudaGraphInstantiate(&h->gexec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e_inst != cudaSuccess) {
+                h->gexec = nullptr;
+                return fail_cuda(h, e_inst, "cudaGraphInstantiate");
+            }
+            h->g_wav = dwav;
+            h->g_tr = dtr;
+            h->g_kernel = kern;
+            h->g_launches = n_l;
+        }
+        CK(h, cudaGraphLaunch(h->gexec, s));
+        launches += h->g_launches;
+    }
+    h->ran = true;
+    if (final_u) {
+        const float *ufin = h->u[(c.nt + 1) & 1];
+        if (is_device_ptr(final_u)) {
+            CK(h, launch_unpack(ufin, c.nx, c.ny, c.nz, h->nxp, final_u, s));
+        } else {
+            if (!h->st_vol) CK(h, cudaMalloc(&h->st_vol, sizeof(float) * (size_t)h->npts));
+            CK(h, launch_unpack(ufin, c.nx, c.ny, c.nz, h->nxp, h->st_vol, s));
+            CK(h, cudaMemcpyAsync(final_u, h->st_vol, sizeof(float) * (size_t)h->npts, cudaMemcpyDeviceToHost, s));
+        }
+        ++launches;
+    }
+    if (host_tr) CK(h, cudaMemcpyAsync(traces, dtr, sizeof(float) * ntr, cudaMemcpyDeviceToHost, s));
+    if (host_tr || (final_u && !is_device_ptr(final_u))) CK(h, cudaStreamSynchronize(s));
+    h->last_launches = launches;
+    return check_latched(h);
+}
+
+MMOD_API float mmod_last_loop_ms(mmod_handle *h) {
+    if (!h || !h->ran || h->cfg.nt == 0) return -1.0f;
+    DeviceGuard guard(h->device);
+    float ms = -1.0f;
+    if (cudaEventSynchronize(h->ev_t1) != cudaSuccess || cudaEventElapsedTime(&ms, h->ev_t0, h->ev_t1) != cudaSuccess) {
+        cudaGetLastError();
+        return -1.0f;
+    }
+    return ms;
+}

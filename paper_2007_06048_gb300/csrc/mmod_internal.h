@@ -1,0 +1,62 @@
+// Internal declarations of the propagator library: the handle, the argument
+// block of the step kernels and the launchers.  Not part of the public ABI.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "mmod.h"
+#include "stencil.cuh"
+
+namespace mmod {
+
+// Everything a step kernel needs; passed by value (kernel parameter space).
+struct StepArgs {
+    int nx, ny, nz;            // grid
+    int nxp;                   // padded row length (floats), multiple of 32
+    long long plane;           // nxp * ny
+    int nbl;                   // damping width: inner region is [nbl, n - 1 - nbl]
+    int nt;                    // steps of the run (wavelet row length)
+    int n;                     // this step: computes u^{n+1}
+    Weights w;                 // c_m / h_a^2
+    const float *ucur;         // u^n       (padded layout)
+    float *uprev;              // u^{n-1} in, u^{n+1} out
+    const float *c;            // dt^2 v^2  (padded layout)
+    const float *ex, *ey, *ez; // dt * eta per axis
+    // point sources, sorted by depth k: sources of plane k are
+    // [src_kstart[k], src_kstart[k+1])
+    const int *src_kstart;
+    const int *src_i, *src_j, *src_row;   // position and wavelet row
+    const float *src_scale;               // c(x_s) / (hx hy hz)
+    const float *wavelet;                 // [nsrc][nt]
+    // receivers: the kernel of step n copies u^n (its ucur) into traces[n-1]
+    int nrec;
+    const long long *rec_off;             // padded offsets
+    float *traces;                        // [nt][nrec]
+};
+
+// Launchers (mmod_step_simple.cu, mmod_step_tma.cu, mmod_setup.cu).
+cudaError_t launch_step_simple(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_gather(const float *u, const long long *rec_off, int nrec, float *dst,
+                          cudaStream_t s);
+
+struct TmaPlan;   // tile shape / grid decomposition of the TMA kernel
+cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap *cur_map,
+                            const CUtensorMap *prev_map, const CUtensorMap *c_map,
+                            const TmaPlan &plan, cudaStream_t s);
+
+cudaError_t launch_model_scan(const float *vel, long long n, unsigned int *vmax_bits,
+                              unsigned long long *bad, cudaStream_t s);
+cudaError_t launch_model_fill(const float *vel, int nx, int ny, int nz, int nxp, double dt,
+                              float *c, cudaStream_t s);
+cudaError_t launch_source_scale(const float *vel, int nx, int ny, int nsrc, const int *src_i,
+                                const int *src_j, const int *src_k, double dt, double cell,
+                                float *scale, cudaStream_t s);
+cudaError_t launch_pack(const float *dense, int nx, int ny, int nz, int nxp, float *padded,
+                        cudaStream_t s);
+cudaError_t launch_unpack(const float *padded, int nx, int ny, int nz, int nxp, float *dense,
+                          cudaStream_t s);
+
+}  // namespace mmod

@@ -1,0 +1,67 @@
+// Plain step kernel: one thread per grid point, neighbours read straight from
+// global memory (L1/L2 cached), u = 0 outside the grid by explicit bounds
+// tests.  It performs exactly the FP32 operations of the TMA kernel in the
+// same order (stencil.cuh), so the two agree bit for bit; it is the
+// validation kernel (MMOD_KERNEL_SIMPLE), not the fast path.
+#include "mmod_internal.h"
+
+namespace mmod {
+namespace {
+
+__device__ __forceinline__ float ld0(const float *__restrict__ u, const StepArgs &a, int i, int j,
+                                     int k) {
+    const bool in = (unsigned)i < (unsigned)a.nx && (unsigned)j < (unsigned)a.ny &&
+                    (unsigned)k < (unsigned)a.nz;
+    return in ? __ldg(u + (long long)k * a.plane + (long long)j * a.nxp + i) : 0.0f;
+}
+
+__global__ void __launch_bounds__(128) step_simple_kernel(const StepArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= a.nx || j >= a.ny) return;
+    const long long o = (long long)k * a.plane + (long long)j * a.nxp + i;
+    const float p = __ldg(a.ucur + o);
+    const float two_p = __fadd_rn(p, p);
+    float lap = 0.0f;
+#pragma unroll
+    for (int m = 1; m <= kRadius; ++m) lap = pair_acc(lap, a.w.x[m - 1], ld0(a.ucur, a, i + m, j, k), ld0(a.ucur, a, i - m, j, k), two_p);
+#pragma unroll
+    for (int m = 1; m <= kRadius; ++m) lap = pair_acc(lap, a.w.y[m - 1], ld0(a.ucur, a, i, j + m, k), ld0(a.ucur, a, i, j - m, k), two_p);
+#pragma unroll
+    for (int m = 1; m <= kRadius; ++m) lap = pair_acc(lap, a.w.z[m - 1], ld0(a.ucur, a, i, j, k + m), ld0(a.ucur, a, i, j, k - m), two_p);
+    const float e = __fadd_rn(__fadd_rn(__ldg(a.ex + i), __ldg(a.ey + j)), __ldg(a.ez + k));
+    float num = num_damped(two_p, a.uprev[o], __ldg(a.c + o), lap, e);
+    for (int t = __ldg(a.src_kstart + k); t < __ldg(a.src_kstart + k + 1); ++t)
+        if (__ldg(a.src_i + t) == i && __ldg(a.src_j + t) == j)
+            num = add_source(num, __ldg(a.src_scale + t),
+                             __ldg(a.wavelet + (long long)__ldg(a.src_row + t) * a.nt + a.n));
+    a.uprev[o] = finish_damped(num, e);
+}
+
+__global__ void gather_kernel(const float *__restrict__ u, const long long *__restrict__ off, int nrec,
+                              float *__restrict__ dst) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrec; r += gridDim.x * blockDim.x)
+        dst[r] = u[off[r]];
+}
+
+}  // namespace
+
+cudaError_t launch_step_simple(const StepArgs &a, cudaStream_t s) {
+    if (a.nx <= 0 || a.ny <= 0 || a.nz <= 0) return cudaSuccess;
+    dim3 block(32, 4);
+    dim3 grid((a.nx + 31) / 32, (a.ny + 3) / 4, a.nz);
+    step_simple_kernel<<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const float *u, const long long *rec_off, int nrec, float *dst,
+                          cudaStream_t s) {
+    if (nrec <= 0) return cudaSuccess;
+    int blocks = (nrec + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    gather_kernel<<<blocks, 256, 0, s>>>(u, rec_off, nrec, dst);
+    return cudaGetLastError();
+}
+
+}  // namespace mmod

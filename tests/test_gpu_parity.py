@@ -1,0 +1,157 @@
+"""GPU (FP32, C ABI) against the FP64 oracle.
+
+Gates from the propagator's accuracy target: relative L2 error of the
+wavefield and of the traces <= 1e-5 after 100 steps and <= 1e-4 after 1000.
+Relative L2 = ||gpu - oracle||_2 / ||oracle||_2 over the whole array, in FP64.
+Where the 100-step traces hold only numerical precursors (the 64^3 case:
+the first arrival reaches the receivers after step 280), their error is
+reported relative to max|u| * sqrt(#samples) instead ("below floor").
+"""
+import numpy as np
+import pytest
+
+import paper_2007_06048_gb300 as M
+import workloads as W
+from _gpu_util import rel_l2, run_gpu, run_oracle, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def test_homogeneous_64_100_steps(orc):
+    p = W.small_homogeneous(100)
+    tr_o, _, u_o = run_oracle(orc, p)
+    tr_g, u_g, prop = run_gpu(p)
+    assert rel_l2(u_g, u_o) <= 1e-5
+    floor = np.abs(u_o).max() * np.sqrt(tr_o.size)
+    assert np.linalg.norm(tr_g - tr_o) / floor <= 1e-5
+    assert prop.launches >= p.nt
+
+
+def test_homogeneous_64_1000_steps(orc):
+    p = W.small_homogeneous(1000)
+    tr_o, _, u_o = run_oracle(orc, p)
+    tr_g, u_g, _ = run_gpu(p)
+    assert rel_l2(u_g, u_o) <= 1e-4
+    assert rel_l2(tr_g, tr_o) <= 1e-4
+
+
+def test_layered_240_100_steps(orc):
+    p = W.layered_240(100)
+    tr_o, _, u_o = run_oracle(orc, p)
+    tr_g, u_g, _ = run_gpu(p)
+    assert rel_l2(u_g, u_o) <= 1e-5
+    assert rel_l2(tr_g, tr_o) <= 1e-5
+
+
+def test_layered_240_1000_steps_full_size(orc):
+    """The benchmarked workload itself: 240^3, 1000 steps, 57 600 receivers."""
+    p = W.layered_240(1000)
+    tr_o, _, u_o = run_oracle(orc, p)
+    tr_g, u_g, _ = run_gpu(p)
+    assert rel_l2(u_g, u_o) <= 1e-4
+    assert rel_l2(tr_g, tr_o) <= 1e-4
+
+
+SHAPES = [((9, 9, 9), 0), ((13, 17, 35), 2), ((70, 33, 65), 5), ((5, 40, 3), 1), ((1, 1, 1), 0),
+          ((2, 67, 129), 0), ((40, 1, 30), 0), ((37, 45, 131), 9)]
+
+
+@pytest.mark.parametrize("shape,nbl", SHAPES, ids=[f"{s}-L{n}" for s, n in SHAPES])
+def test_ragged_and_degenerate_shapes(orc, shape, nbl):
+    nz, ny, nx = shape
+    p = W.tiny_problem(shape=shape, nt=40, nbl=nbl, nsrc=3, nrec=9, seed=nx * 7 + ny * 3 + nz)
+    corners = [[0, 0, 0], [nx - 1, ny - 1, nz - 1], [nx - 1, 0, nz - 1], [0, ny - 1, 0]]
+    p.src_ijk[0] = corners[1]
+    p.src_ijk[1] = p.src_ijk[2]          # two sources on one point add up
+    p.rec_ijk[:4] = corners
+    p.rec_ijk[4] = p.rec_ijk[5]          # duplicated receiver
+    p.rec_ijk[6] = p.src_ijk[0]
+    tr_o, _, u_o = run_oracle(orc, p)
+    tr_g, u_g, _ = run_gpu(p)
+    assert rel_l2(u_g, u_o) <= 1e-5
+    assert rel_l2(tr_g, tr_o) <= 1e-5
+    assert np.array_equal(tr_g[:, 4], tr_g[:, 5])
+
+
+def test_zero_steps_and_no_sources_or_receivers(orc):
+    torch = torch_cuda()
+    p = W.tiny_problem(shape=(12, 11, 10), nt=0, nbl=2, nsrc=0, nrec=0)
+    prop = M.Propagator.from_problem(p)
+    prop.set_model(torch.from_numpy(p.vel).cuda())
+    fin = torch.full(p.vel.shape, 7.0, device="cuda")
+    prop.forward(None, None, fin)
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(fin).item() == 0
+    q = W.tiny_problem(shape=(12, 11, 10), nt=20, nbl=2, nsrc=0, nrec=3)
+    tr, u, _ = run_gpu(q)
+    assert not np.any(tr) and not np.any(u)
+
+
+def test_host_buffers_match_device_buffers():
+    """The end-to-end path: host numpy arrays in and out through the same ABI."""
+    torch = torch_cuda()
+    p = W.tiny_problem(shape=(30, 28, 70), nt=60, nbl=4, nsrc=2, nrec=11, seed=3)
+    tr_d, u_d, _ = run_gpu(p)
+    prop = M.Propagator.from_problem(p)
+    prop.set_model(np.ascontiguousarray(p.vel))
+    tr_h = np.zeros((p.nt, len(p.rec_ijk)), np.float32)
+    u_h = np.zeros(p.vel.shape, np.float32)
+    prop.forward(np.ascontiguousarray(p.wavelet), tr_h, u_h)
+    assert np.array_equal(tr_h, tr_d)
+    assert np.array_equal(u_h, u_d)
+    pinned_tr = torch.zeros((p.nt, len(p.rec_ijk)), pin_memory=True)
+    prop.forward(torch.from_numpy(np.ascontiguousarray(p.wavelet)).pin_memory(), pinned_tr, None)
+    assert np.array_equal(pinned_tr.numpy(), tr_d)
+
+
+def test_standing_wave_fp32():
+    """The exact discrete standing wave of Eq. 5 (see the oracle pins), now in
+    FP32 on the GPU through set_state / get_state: relative error ~ FP32 eps."""
+    shape = (48, 44, 52)
+    h = (10.0, 12.0, 9.0)
+    v, dt = 2000.0, 0.9e-3
+    k = np.array([2 * np.pi / 97.0, 2 * np.pi / 61.0, 2 * np.pi / 143.0])
+    nz, ny, nx = shape
+    Z, Y, X = np.meshgrid(np.arange(nz) * h[2], np.arange(ny) * h[1], np.arange(nx) * h[0], indexing="ij")
+    phi = np.cos(k[0] * X + 0.3) * np.cos(k[1] * Y + 1.1) * np.cos(k[2] * Z - 0.4)
+    c = [8 / 5, -1 / 5, 8 / 315, -1 / 560]
+    K = sum(4 * c[m - 1] * np.sin(m * k[a] * h[a] / 2) ** 2 / h[a] ** 2 for a in range(3) for m in range(1, 5))
+    cwdt = 1 - dt * dt * v * v * K / 2
+    nt = 5
+    p = W.Problem("standing", np.full(shape, v, np.float32), h, dt, nt, 0, np.zeros((0, 3), np.int32),
+                  np.zeros((0, nt), np.float32), np.zeros((0, 3), np.int32))
+    _, u, _, (up, uc) = run_gpu(p, state=(cwdt * phi, phi), want_state=True)
+    m = 4 * nt
+    inner = (slice(m, -m),) * 3
+    expect = np.cos(nt * np.arccos(cwdt)) * phi
+    assert np.array_equal(u, uc)
+    assert np.max(np.abs(u[inner] - expect[inner])) < 2e-5
+
+
+def test_error_paths():
+    torch = torch_cuda()
+    p = W.tiny_problem(shape=(16, 16, 16), nt=10, nbl=2)
+    prop = M.Propagator.from_problem(p)
+    wav = torch.from_numpy(p.wavelet).cuda()
+    tr = torch.zeros((p.nt, len(p.rec_ijk)), device="cuda")
+    with pytest.raises(M.MmodError) as ei:
+        prop.forward(wav, tr)
+    assert ei.value.status == -6                      # no model yet
+    bad = p.vel.copy()
+    bad[3, 4, 5] = -1.0
+    with pytest.raises(M.MmodError) as ei:
+        prop.set_model(torch.from_numpy(bad).cuda())
+    assert ei.value.status == -1
+    bad[3, 4, 5] = np.nan
+    with pytest.raises(M.MmodError) as ei:
+        prop.set_model(torch.from_numpy(bad).cuda())
+    assert ei.value.status == -1
+    fast = (p.vel * 10).astype(np.float32)            # breaks the CFL bound
+    with pytest.raises(M.MmodError) as ei:
+        prop.set_model(torch.from_numpy(fast).cuda())
+    assert ei.value.status == -2
+    prop.set_model(torch.from_numpy(p.vel).cuda())
+    prop.forward(wav, tr)
+    with pytest.raises(M.MmodError):
+        prop.set_kernel(99)
+    torch.cuda.synchronize()
