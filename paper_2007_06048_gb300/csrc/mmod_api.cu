@@ -73,6 +73,8 @@ struct mmod_handle {
     float *st_vol = nullptr;            // dense [nz][ny][nx] staging (lazy)
     float *st_wav = nullptr;            // [nsrc][nt] staging (lazy)
     float *st_tr = nullptr;             // [nt][nrec] staging (lazy)
+    int *err_host = nullptr;            // mapped pinned word: a kernel gave up waiting
+    int *err_dev = nullptr;
 
     cudaStream_t cap = nullptr;         // private stream used only for graph capture
     cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;   // bracket the step loop
@@ -118,6 +120,10 @@ mmod_status fail_cuda(mmod_handle *h, cudaError_t e, const char *what) {
     } while (0)
 
 mmod_status check_latched(mmod_handle *h) {
+    if (h->err_host && *(volatile int *)h->err_host) {
+        h->err = "a step kernel gave up waiting for its copies (device-side timeout)";
+        return MMOD_ERR_TIMEOUT;
+    }
     if (h->latched != cudaSuccess) {
         h->err = std::string("earlier CUDA failure: ") + cudaGetErrorName(h->latched);
         return MMOD_ERR_CUDA;
@@ -169,6 +175,7 @@ void free_all(mmod_handle *h) {
     if (h->ev_t0) cudaEventDestroy(h->ev_t0);
     if (h->ev_t1) cudaEventDestroy(h->ev_t1);
     if (h->cap) cudaStreamDestroy(h->cap);
+    if (h->err_host) cudaFreeHost(h->err_host);
 }
 
 // Damping profile of one axis (the ABI's reading of the layers), FP64 -> FP32
@@ -199,6 +206,7 @@ StepArgs step_args(mmod_handle *h, const float *wavelet, float *traces, int n) {
     a.src_scale = h->src_scale; a.wavelet = wavelet;
     a.nrec = h->cfg.nrec; a.rec_off = h->rec_off;
     a.traces = (n >= 1 && traces) ? traces + (long long)(n - 1) * h->cfg.nrec : nullptr;
+    a.err = h->err_dev;
     return a;
 }
 
@@ -212,7 +220,7 @@ mmod_status enqueue_steps(mmod_handle *h, const float *wav, float *tr, cudaStrea
     const int nt = h->cfg.nt, nrec = h->cfg.nrec;
     long long count = 0;
     const bool tma = use_tma(h);
-    CK(h, cudaEventRecord(h->ev_t0, s));
+    CK(h, cudaEventRecordWithFlags(h->ev_t0, s, cudaEventRecordExternal));
     for (int n = 0; n < nt; ++n) {
         StepArgs a = step_args(h, wav, tr, n);
         if (tma) {
@@ -233,7 +241,7 @@ mmod_status enqueue_steps(mmod_handle *h, const float *wav, float *tr, cudaStrea
         CK(h, launch_gather(h->u[(nt - 1) & 1], h->rec_off, nrec, tr + (long long)(nt - 1) * nrec, s));
         ++count;
     }
-    CK(h, cudaEventRecord(h->ev_t1, s));
+    CK(h, cudaEventRecordWithFlags(h->ev_t1, s, cudaEventRecordExternal));
     *nlaunch = count;
     return MMOD_OK;
 }
@@ -351,6 +359,9 @@ MMOD_API mmod_status mmod_create(const mmod_config *cfg, int device, mmod_handle
     CKC(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
     CKC(cudaEventCreate(&h->ev_t0));
     CKC(cudaEventCreate(&h->ev_t1));
+    CKC(cudaHostAlloc(&h->err_host, sizeof(int), cudaHostAllocMapped));
+    *h->err_host = 0;
+    CKC(cudaHostGetDevicePointer(&h->err_dev, h->err_host, 0));
     h->tma_ok = make_tma_plan(h->cfg, h->nxp, h->u, h->c, h->cur_map, h->prev_map, &h->c_map, &h->plan);
 #undef CKC
     *out = h;

@@ -35,6 +35,7 @@ struct StepArgs {
     int nrec;
     const long long *rec_off;             // padded offsets
     float *traces;                        // [nt][nrec]
+    int *err;                             // device view of the mapped error word
 };
 
 // Launchers (mmod_step_simple.cu, mmod_step_tma.cu, mmod_setup.cu).

@@ -155,3 +155,25 @@ def test_error_paths():
     with pytest.raises(M.MmodError):
         prop.set_kernel(99)
     torch.cuda.synchronize()
+
+
+BITWISE = SHAPES + [((64, 64, 64), 8), ((240, 240, 240), 20), ((200, 130, 97), 12)]
+
+
+@pytest.mark.parametrize("shape,nbl", BITWISE, ids=[f"{s}-L{n}" for s, n in BITWISE])
+def test_tma_kernel_is_bitwise_the_plain_kernel(shape, nbl):
+    """The pipelined kernel performs the plain kernel's FP32 operations in the
+    same order: final wavefield and traces agree bit for bit."""
+    nz, ny, nx = shape
+    if shape == (240, 240, 240):
+        p = W.layered_240(1000)
+    else:
+        p = W.tiny_problem(shape=shape, nt=50, nbl=nbl, nsrc=3, nrec=17, seed=nx + ny + nz)
+        p.src_ijk[0] = [nx - 1, 0, nz // 2]
+    tr_s, u_s, _ = run_gpu(p, kernel=M.KERNEL_SIMPLE)
+    tr_t, u_t, prop = run_gpu(p, kernel=M.KERNEL_TMA)
+    assert np.array_equal(u_s, u_t)
+    assert np.array_equal(tr_s, tr_t)
+    # one step kernel per time step plus the final receiver gather and the unpack
+    assert prop.launches == p.nt + 2
+    assert prop.loop_ms() > 0
