@@ -204,13 +204,15 @@ def run_mmod(args):
     npts = p.npoints
     prop = M.Propagator.from_problem(p, device=local)
     if args.kernel != "auto":
-        prop.set_kernel({"simple": M.KERNEL_SIMPLE, "tma": M.KERNEL_TMA}[args.kernel])
+        prop.set_kernel({"simple": M.KERNEL_SIMPLE, "tma": M.KERNEL_TMA,
+                         "tma_rotate": M.KERNEL_TMA_ROTATE}[args.kernel])
     stream = torch.cuda.current_stream(dev)
     vel_d = torch.from_numpy(p.vel).to(dev)
     wav_d = torch.from_numpy(np.ascontiguousarray(p.wavelet)).to(dev)
     tr_d = torch.empty((p.nt, len(p.rec_ijk)), device=dev)
     prop.set_model(vel_d, stream)
-    kernel_tag = "tma" if (args.kernel in ("auto", "tma") and prop_uses_tma(prop)) else "simple"
+    kernel_tag = ("tma_rotate" if args.kernel == "tma_rotate" else
+                  "tma" if (args.kernel in ("auto", "tma") and prop_uses_tma(prop)) else "simple")
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -313,7 +315,7 @@ def main():
     ap.add_argument("--impl", choices=["mmod", "reference"], default="mmod")
     ap.add_argument("--workload", default="layered240")
     ap.add_argument("--nt", type=int, default=None, help="override the workload's step count")
-    ap.add_argument("--kernel", choices=["auto", "simple", "tma"], default="auto")
+    ap.add_argument("--kernel", choices=["auto", "simple", "tma", "tma_rotate"], default="auto")
     ap.add_argument("--ref-seconds", type=float, default=20.0,
                     help="CPU seconds per oracle sample (cpu_baseline / reference arm)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -119,10 +119,14 @@ mmod_status mmod_set_state(mmod_handle *h, const float *u_prev, const float *u_c
 /* Copy the last forward's final state u^{nt-1}, u^{nt} (either may be NULL). */
 mmod_status mmod_get_state(mmod_handle *h, float *u_prev, float *u_cur, mmod_stream stream);
 
-/* Kernel selection for validation: MMOD_KERNEL_AUTO (default) picks the
- * TMA-pipelined kernel; MMOD_KERNEL_SIMPLE runs the plain one-thread-per-
- * point kernel, which performs the identical FP32 operations per point. */
-enum { MMOD_KERNEL_AUTO = 0, MMOD_KERNEL_SIMPLE = 1, MMOD_KERNEL_TMA = 2 };
+/* Kernel selection: MMOD_KERNEL_AUTO (default) picks the TMA-pipelined
+ * kernel; MMOD_KERNEL_SIMPLE runs the plain one-thread-per-point kernel, which
+ * performs the identical FP32 operations per point (validation);
+ * MMOD_KERNEL_TMA / MMOD_KERNEL_TMA_ROTATE force the pipelined kernel with its
+ * z register queue shifted after every plane (compact code) or rotated by
+ * unrolling nine planes (no moves, larger code).  All variants produce the
+ * same bits.  Errors: ARG (unknown id), UNSUPPORTED (no TMA plan). */
+enum { MMOD_KERNEL_AUTO = 0, MMOD_KERNEL_SIMPLE = 1, MMOD_KERNEL_TMA = 2, MMOD_KERNEL_TMA_ROTATE = 3 };
 mmod_status mmod_set_kernel(mmod_handle *h, int kernel);
 
 /* Number of kernel launches the last mmod_forward enqueued (all of this
@@ -143,6 +147,13 @@ double mmod_cfl_dt(double cfl, double hmin, double vmax);
  * The string is owned by the handle and valid until its next call.  With
  * h == NULL: the calling thread's last mmod_create failure. */
 const char *mmod_last_error(const mmod_handle *h);
+
+/* Self-check of the damping reciprocal used by the step kernels (hardware
+ * approximate reciprocal plus one Newton-Raphson step) against CUDA's
+ * correctly rounded reciprocal, on n values of d in [1, 8), on the current
+ * device.  Writes the largest difference in units in the last place.
+ * Synchronous; returns MMOD_OK, ARG, OOM or CUDA. */
+int mmod_check_recip(int n, unsigned int *max_ulp_out);
 
 /* Library version string, e.g. "mmod-gb300 0.1 sm_103a". */
 const char *mmod_version(void);

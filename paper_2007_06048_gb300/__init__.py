@@ -25,12 +25,12 @@ __all__ = ["MmodError", "build", "load", "mmod_create", "mmod_destroy", "mmod_se
 
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_UNSTABLE", -3: "ERR_OOM", -4: "ERR_CUDA",
           -5: "ERR_TIMEOUT", -6: "ERR_STATE", -7: "ERR_UNSUPPORTED"}
-KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_TMA = 0, 1, 2
+KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_TMA, KERNEL_TMA_ROTATE = 0, 1, 2, 3
 
 # Every symbol include/mmod.h declares (checked against the header by the tests).
 EXPORTED = ["mmod_create", "mmod_destroy", "mmod_set_model", "mmod_forward", "mmod_set_state",
             "mmod_get_state", "mmod_set_kernel", "mmod_last_launch_count", "mmod_last_loop_ms",
-            "mmod_cfl_dt", "mmod_last_error", "mmod_version"]
+            "mmod_cfl_dt", "mmod_last_error", "mmod_version", "mmod_check_recip"]
 
 
 class MmodError(RuntimeError):
@@ -78,6 +78,7 @@ def load():
         "mmod_cfl_dt": ([D, D, D], D),
         "mmod_last_error": ([P], ctypes.c_char_p),
         "mmod_version": ([], ctypes.c_char_p),
+        "mmod_check_recip": ([I, ctypes.POINTER(ctypes.c_uint)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -169,6 +170,13 @@ def mmod_get_state(h, u_prev, u_cur, stream=None):
 
 def mmod_set_kernel(h, kernel: int):
     _check(h, load().mmod_set_kernel(h, int(kernel)))
+
+
+def mmod_check_recip(n: int = 1 << 22) -> int:
+    """Max ulp difference of the kernels' damping reciprocal vs __frcp_rn."""
+    out = ctypes.c_uint(0)
+    _check(None, load().mmod_check_recip(int(n), ctypes.byref(out)))
+    return int(out.value)
 
 
 def mmod_last_error(h) -> str:

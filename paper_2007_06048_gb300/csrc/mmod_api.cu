@@ -211,7 +211,7 @@ StepArgs step_args(mmod_handle *h, const float *wavelet, float *traces, int n) {
 }
 
 bool use_tma(const mmod_handle *h) {
-    return h->tma_ok && (h->kernel == MMOD_KERNEL_AUTO || h->kernel == MMOD_KERNEL_TMA);
+    return h->tma_ok && h->kernel != MMOD_KERNEL_SIMPLE;
 }
 
 // Enqueue the nt steps (and receiver gathers) on stream s.  Returns the
@@ -224,7 +224,8 @@ mmod_status enqueue_steps(mmod_handle *h, const float *wav, float *tr, cudaStrea
     for (int n = 0; n < nt; ++n) {
         StepArgs a = step_args(h, wav, tr, n);
         if (tma) {
-            CK(h, launch_step_tma(a, &h->cur_map[(n + 1) & 1], &h->prev_map[n & 1], &h->c_map, h->plan, s));
+            CK(h, launch_step_tma(a, &h->cur_map[(n + 1) & 1], &h->prev_map[n & 1], &h->c_map, h->plan,
+                                  h->kernel == MMOD_KERNEL_TMA_ROTATE, s));
             ++count;
         } else {
             a.traces = nullptr;   // the plain path gathers with a separate kernel
@@ -381,9 +382,10 @@ MMOD_API mmod_status mmod_destroy(mmod_handle *h) {
 
 MMOD_API mmod_status mmod_set_kernel(mmod_handle *h, int kernel) {
     if (!h) return MMOD_ERR_ARG;
-    if (kernel != MMOD_KERNEL_AUTO && kernel != MMOD_KERNEL_SIMPLE && kernel != MMOD_KERNEL_TMA)
+    if (kernel != MMOD_KERNEL_AUTO && kernel != MMOD_KERNEL_SIMPLE && kernel != MMOD_KERNEL_TMA &&
+        kernel != MMOD_KERNEL_TMA_ROTATE)
         return fail(h, MMOD_ERR_ARG, "unknown kernel id");
-    if (kernel == MMOD_KERNEL_TMA && !h->tma_ok)
+    if ((kernel == MMOD_KERNEL_TMA || kernel == MMOD_KERNEL_TMA_ROTATE) && !h->tma_ok)
         return fail(h, MMOD_ERR_UNSUPPORTED, "TMA kernel unavailable for this grid");
     h->kernel = kernel;
     return MMOD_OK;
@@ -512,7 +514,8 @@ MMOD_API mmod_status mmod_forward(mmod_handle *h, const float *wavelet, float *t
     h->state_pending = false;
 
     if (c.nt > 0) {
-        const int kern = use_tma(h) ? MMOD_KERNEL_TMA : MMOD_KERNEL_SIMPLE;
+        const int kern = use_tma(h) ? (h->kernel == MMOD_KERNEL_TMA_ROTATE ? MMOD_KERNEL_TMA_ROTATE : MMOD_KERNEL_TMA)
+                                    : MMOD_KERNEL_SIMPLE;
         if (!h->gexec || h->g_wav != dwav || h->g_tr != dtr || h->g_kernel != kern) {
             if (h->gexec) {
                 cudaGraphExecDestroy(h->gexec);

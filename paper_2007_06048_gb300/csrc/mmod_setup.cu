@@ -125,3 +125,34 @@ cudaError_t launch_unpack(const float *padded, int nx, int ny, int nz, int nxp, 
 }
 
 }  // namespace mmod
+
+namespace mmod {
+namespace {
+
+// Largest difference, in units in the last place, between the kernels'
+// damping reciprocal and CUDA's correctly rounded __frcp_rn over n values of
+// d spread evenly over [1, 8).
+__global__ void recip_check_kernel(int n, unsigned int *max_ulp) {
+    unsigned int worst = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float d = 1.0f + 7.0f * ((float)i / (float)n);
+        const int a = __float_as_int(recip_nr(d)), b = __float_as_int(__frcp_rn(d));
+        const unsigned int ulp = (unsigned int)(a > b ? a - b : b - a);
+        worst = ulp > worst ? ulp : worst;
+    }
+    atomicMax(max_ulp, worst);
+}
+
+}  // namespace
+}  // namespace mmod
+
+extern "C" __attribute__((visibility("default"))) int mmod_check_recip(int n, unsigned int *max_ulp_out) {
+    if (n <= 0 || !max_ulp_out) return MMOD_ERR_ARG;
+    unsigned int *d = nullptr;
+    if (cudaMalloc(&d, sizeof(unsigned int)) != cudaSuccess) return MMOD_ERR_OOM;
+    cudaMemset(d, 0, sizeof(unsigned int));
+    mmod::recip_check_kernel<<<152, 256>>>(n, d);
+    cudaError_t e = cudaMemcpy(max_ulp_out, d, sizeof(unsigned int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    return e == cudaSuccess ? MMOD_OK : MMOD_ERR_CUDA;
+}

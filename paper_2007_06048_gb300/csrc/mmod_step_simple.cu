@@ -31,12 +31,13 @@ __global__ void __launch_bounds__(128) step_simple_kernel(const StepArgs a) {
 #pragma unroll
     for (int m = 1; m <= kRadius; ++m) lap = pair_acc(lap, a.w.z[m - 1], ld0(a.ucur, a, i, j, k + m), ld0(a.ucur, a, i, j, k - m), two_p);
     const float e = __fadd_rn(__fadd_rn(__ldg(a.ex + i), __ldg(a.ey + j)), __ldg(a.ez + k));
-    float num = num_damped(two_p, a.uprev[o], __ldg(a.c + o), lap, e);
+    const float r = damp_factor(e);
+    float out = __fmul_rn(num_damped(two_p, a.uprev[o], __ldg(a.c + o), lap, e), r);
     for (int t = __ldg(a.src_kstart + k); t < __ldg(a.src_kstart + k + 1); ++t)
         if (__ldg(a.src_i + t) == i && __ldg(a.src_j + t) == j)
-            num = add_source(num, __ldg(a.src_scale + t),
-                             __ldg(a.wavelet + (long long)__ldg(a.src_row + t) * a.nt + a.n));
-    a.uprev[o] = finish_damped(num, e);
+            out = add_source(out, __ldg(a.src_scale + t),
+                             __ldg(a.wavelet + (long long)__ldg(a.src_row + t) * a.nt + a.n), r);
+    a.uprev[o] = out;
 }
 
 __global__ void gather_kernel(const float *__restrict__ u, const long long *__restrict__ off, int nrec,

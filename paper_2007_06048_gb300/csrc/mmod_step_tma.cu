@@ -20,9 +20,9 @@
 // unrolling the z loop 9 times (no register moves).  The arithmetic per point
 // is stencil.cuh's, in the same order as the plain kernel: bit-identical.
 //
-// Waits are bounded: a wait that gives up sets the mapped error word, the CTA
-// stops at the next block barrier, drains its outstanding copies (bounded) and
-// returns; the host reports MMOD_ERR_TIMEOUT.
+// Waits are bounded (100 ms of wall-clock time each): a wait that gives up sets
+// the mapped error word, the CTA stops at the next block barrier, drains its
+// outstanding copies (bounded) and returns; the host reports MMOD_ERR_TIMEOUT.
 #include <cstdint>
 
 #include "mmod_internal.h"
@@ -38,7 +38,7 @@ constexpr int HX = TX + 2 * kRadius;   // 72: halo tile width
 constexpr int NSU = 8;                 // u^n slots: 5 resident planes + prefetch
 constexpr int NSC = 4;                 // u^{n-1}, c slots
 constexpr int QN = 2 * kRadius + 1;    // z register queue depth
-constexpr long long kSpinLimit = 1LL << 22;   // try_wait rounds before giving up
+constexpr unsigned long long kWaitNs = 100000000ull;   // a wait gives up after 100 ms
 
 template <int TY>
 struct Shape {
@@ -75,13 +75,35 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait; on give-up records the failure and returns false.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *abort_flag, int *err) {
-    for (long long i = 0; i < kSpinLimit; ++i)
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for a phase for at most kWaitNs of wall-clock time (try_wait suspends
+// the thread in hardware between polls).  The slow path gives up at once if
+// another CTA already reported a failure.  On give-up it records the failure
+// and returns false.
+__device__ __noinline__ bool mbar_wait_slow(uint64_t *bar, uint32_t parity, int *abort_flag, int *err) {
+    const unsigned long long t0 = global_ns();
+    while (!(err && *(volatile int *)err) && global_ns() - t0 < kWaitNs)
         if (mbar_try_wait(bar, parity)) return true;
     *abort_flag = 1;
     if (err) atomicExch(err, 1);
     return false;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *abort_flag, int *err) {
+    if (mbar_try_wait(bar, parity)) return true;
+    return mbar_wait_slow(bar, parity, abort_flag, err);
+}
+
+// Bounded drain wait used after a give-up: no error reporting.
+__device__ __noinline__ void mbar_drain(uint64_t *bar, uint32_t parity) {
+    const unsigned long long t0 = global_ns();
+    while (global_ns() - t0 < kWaitNs)
+        if (mbar_try_wait(bar, parity)) return;
 }
 
 __device__ __forceinline__ void tma_load_3d(float *dst, const CUtensorMap *map, int x, int y, int z,
@@ -129,20 +151,51 @@ __device__ __forceinline__ void issue_c(const Ctx<TY> &c, const CUtensorMap *pma
 
 // Own points of plane seq (rows 4+4w+r, columns 4+2*lane) into queue slot Q.
 template <int TY, int Q>
-__device__ __forceinline__ void read_own(const Ctx<TY> &c, int seq, float (&q)[QN][RY][RX]) {
+__device__ __forceinline__ void read_own(const Ctx<TY> &c, int seq, float2 (&q)[QN][RY]) {
     const float *base = c.cur + (seq % NSU) * Shape<TY>::CUR + (kRadius + RY * c.warp) * HX + kRadius + 2 * c.lane;
 #pragma unroll
-    for (int r = 0; r < RY; ++r) {
-        const float2 v = *reinterpret_cast<const float2 *>(base + r * HX);
-        q[Q][r][0] = v.x;
-        q[Q][r][1] = v.y;
+    for (int r = 0; r < RY; ++r) q[Q][r] = *reinterpret_cast<const float2 *>(base + r * HX);
+}
+
+__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
+__device__ __forceinline__ float2 bcast(float v) { return make_float2(v, v); }
+
+// Packed pair_acc: per component exactly stencil.cuh's pair_acc.
+__device__ __forceinline__ float2 pair_acc2(float2 acc, float2 w, float2 a, float2 b, float2 neg_two_p) {
+    return __ffma2_rn(w, __fadd2_rn(__fadd2_rn(a, b), neg_two_p), acc);
+}
+
+// Sources of plane k that fall on this thread's points (rare: one plane per
+// source).  Each thread re-reads the value it has just stored, so program
+// order makes it visible; the term is scaled by the point's damping factor.
+__device__ __noinline__ void add_plane_sources(const StepArgs &a, int k, int s_lo, int s_hi, int x, int y0,
+                                               float2 exr, const float (&eyr)[RY], float ez) {
+    for (int s = s_lo; s < s_hi; ++s) {
+        const int si = __ldg(a.src_i + s), sj = __ldg(a.src_j + s);
+        const int r = sj - y0;
+        if ((si != x && si != x + 1) || r < 0 || r >= RY) continue;
+        const float ex = si == x ? exr.x : exr.y;
+        float ey = eyr[0];
+#pragma unroll
+        for (int i = 1; i < RY; ++i)
+            if (r == i) ey = eyr[i];
+        const float e = __fadd_rn(__fadd_rn(ex, ey), ez);
+        float *dst = a.uprev + (long long)k * a.plane + (long long)sj * a.nxp + si;
+        const float wv = __ldg(a.wavelet + (long long)__ldg(a.src_row + s) * a.nt + a.n);
+        *dst = add_source(*dst, __ldg(a.src_scale + s), wv, damp_factor(e));
     }
 }
 
-// One z step with compile-time queue rotation R: computes plane z0 + t.
+struct Wts {
+    float2 x2, x4, y[kRadius], z[kRadius];   // broadcast pairs of w_am
+    float x1, x3;
+};
+
+// One z step computing plane z0 + t.  R is the queue rotation (0 when the
+// queue is shifted after every step instead).
 template <int TY, int R>
-__device__ __forceinline__ void step(const StepArgs &a, const Ctx<TY> &c, int t, float (&q)[QN][RY][RX],
-                                     const float (&exr)[RX], const float (&eyr)[RY], bool xy_damped) {
+__device__ __forceinline__ void step(const StepArgs &a, const Ctx<TY> &c, int t, float2 (&q)[QN][RY],
+                                     const Wts &w, float2 exr, const float (&eyr)[RY], bool xy_damped) {
     using S = Shape<TY>;
     const int k = c.z0 + t;
     // 1. the leading plane k+4 (sequence t+8) enters the queue
@@ -155,81 +208,59 @@ __device__ __forceinline__ void step(const StepArgs &a, const Ctx<TY> &c, int t,
 
     // 2. y neighbour columns: rows 4w .. 4w+11 of the centre plane (sequence t+4)
     const float *ctr = c.cur + ((t + kRadius) % NSU) * S::CUR;
-    float yc[RY + 2 * kRadius][RX];
+    float2 yc[RY + 2 * kRadius];
 #pragma unroll
-    for (int rr = 0; rr < RY + 2 * kRadius; ++rr) {
-        const float2 v = *reinterpret_cast<const float2 *>(ctr + (RY * c.warp + rr) * HX + kRadius + 2 * c.lane);
-        yc[rr][0] = v.x;
-        yc[rr][1] = v.y;
-    }
+    for (int rr = 0; rr < RY + 2 * kRadius; ++rr)
+        yc[rr] = *reinterpret_cast<const float2 *>(ctr + (RY * c.warp + rr) * HX + kRadius + 2 * c.lane);
     const float *upp = c.up + (t % NSC) * S::PC + (RY * c.warp) * TX + 2 * c.lane;
     const float *ccp = c.cc + (t % NSC) * S::PC + (RY * c.warp) * TX + 2 * c.lane;
     const bool damped = xy_damped || k < a.nbl || k > a.nz - 1 - a.nbl;
-    const float ez = damped ? __ldg(a.ez + k) : 0.0f;
-    const int s_lo = __ldg(a.src_kstart + k), s_hi = __ldg(a.src_kstart + k + 1);
-    float out[RY][RX];
-#pragma unroll
-    for (int r = 0; r < RY; ++r) {
-        // x neighbours: columns 2*lane .. 2*lane+9 of row 4+4w+r
-        float xv[RX + 2 * kRadius];
-        const float *row = ctr + (kRadius + RY * c.warp + r) * HX + 2 * c.lane;
-#pragma unroll
-        for (int j = 0; j < (RX + 2 * kRadius) / 2; ++j) {
-            const float2 v = *reinterpret_cast<const float2 *>(row + 2 * j);
-            xv[2 * j] = v.x;
-            xv[2 * j + 1] = v.y;
-        }
-        const float2 pp2 = *reinterpret_cast<const float2 *>(upp + r * TX);
-        const float2 cc2 = *reinterpret_cast<const float2 *>(ccp + r * TX);
-        const float ppv[RX] = {pp2.x, pp2.y};
-        const float ccv[RX] = {cc2.x, cc2.y};
-#pragma unroll
-        for (int cx = 0; cx < RX; ++cx) {
-            const float p = q[(kRadius + R) % QN][r][cx];
-            const float two_p = __fadd_rn(p, p);
-            float lap = 0.0f;
-#pragma unroll
-            for (int m = 1; m <= kRadius; ++m)
-                lap = pair_acc(lap, a.w.x[m - 1], xv[kRadius + cx + m], xv[kRadius + cx - m], two_p);
-#pragma unroll
-            for (int m = 1; m <= kRadius; ++m)
-                lap = pair_acc(lap, a.w.y[m - 1], yc[kRadius + r + m][cx], yc[kRadius + r - m][cx], two_p);
-#pragma unroll
-            for (int m = 1; m <= kRadius; ++m)
-                lap = pair_acc(lap, a.w.z[m - 1], q[(kRadius + m + R) % QN][r][cx], q[(kRadius - m + R) % QN][r][cx],
-                               two_p);
-            float e = 0.0f;
-            float num;
-            if (damped) {
-                e = __fadd_rn(__fadd_rn(exr[cx], eyr[r]), ez);
-                num = num_damped(two_p, ppv[cx], ccv[cx], lap, e);
-            } else {
-                num = num_inner(two_p, ppv[cx], ccv[cx], lap);
-            }
-            for (int s = s_lo; s < s_hi; ++s) {
-                if (__ldg(a.src_i + s) == c.x0 + 2 * c.lane + cx && __ldg(a.src_j + s) == c.y0 + RY * c.warp + r)
-                    num = add_source(num, __ldg(a.src_scale + s),
-                                     __ldg(a.wavelet + (long long)__ldg(a.src_row + s) * a.nt + a.n));
-            }
-            out[r][cx] = damped ? finish_damped(num, e) : num;
-        }
-    }
-    // 3. store u^{n+1} over u^{n-1}
+    const float ez = __ldg(a.ez + k);   // e is exactly 0 on planes without damping
     const int x = c.x0 + 2 * c.lane;
 #pragma unroll
     for (int r = 0; r < RY; ++r) {
+        // x neighbours: columns 2*lane .. 2*lane+9 of row 4+4w+r, as 5 aligned pairs
+        float2 xa[(RX + 2 * kRadius) / 2];
+        const float *row = ctr + (kRadius + RY * c.warp + r) * HX + 2 * c.lane;
+#pragma unroll
+        for (int j = 0; j < (RX + 2 * kRadius) / 2; ++j) xa[j] = *reinterpret_cast<const float2 *>(row + 2 * j);
+        const float2 p = q[(kRadius + R) % QN][r];
+        const float2 two_p = __fadd2_rn(p, p);
+        const float2 ntp = neg2(two_p);
+        float2 lap = make_float2(0.0f, 0.0f);
+        // x, m = 1 (odd offsets do not form aligned pairs: scalar)
+        lap.x = pair_acc(lap.x, w.x1, xa[2].y, xa[1].y, two_p.x);
+        lap.y = pair_acc(lap.y, w.x1, xa[3].x, xa[2].x, two_p.y);
+        lap = pair_acc2(lap, w.x2, xa[3], xa[1], ntp);
+        lap.x = pair_acc(lap.x, w.x3, xa[3].y, xa[0].y, two_p.x);
+        lap.y = pair_acc(lap.y, w.x3, xa[4].x, xa[1].x, two_p.y);
+        lap = pair_acc2(lap, w.x4, xa[4], xa[0], ntp);
+#pragma unroll
+        for (int m = 1; m <= kRadius; ++m) lap = pair_acc2(lap, w.y[m - 1], yc[kRadius + r + m], yc[kRadius + r - m], ntp);
+#pragma unroll
+        for (int m = 1; m <= kRadius; ++m)
+            lap = pair_acc2(lap, w.z[m - 1], q[(kRadius + m + R) % QN][r], q[(kRadius - m + R) % QN][r], ntp);
+        const float2 pp = *reinterpret_cast<const float2 *>(upp + r * TX);
+        const float2 cc = *reinterpret_cast<const float2 *>(ccp + r * TX);
+        // e = (e_x + e_y) + e_z; zero on planes without damping
+        const float2 e = __fadd2_rn(__fadd2_rn(exr, bcast(eyr[r])), bcast(ez));
+        float2 num = __ffma2_rn(cc, lap, __ffma2_rn(e, pp, __fadd2_rn(two_p, neg2(pp))));
+        if (damped) num = __fmul2_rn(num, make_float2(damp_factor(e.x), damp_factor(e.y)));
+        // 3. store u^{n+1} over u^{n-1}
         const int y = c.y0 + RY * c.warp + r;
         if (y < a.ny && x < a.nx) {
             float *dst = a.uprev + (long long)k * a.plane + (long long)y * a.nxp + x;
             if (x + 1 < a.nx)
-                *reinterpret_cast<float2 *>(dst) = make_float2(out[r][0], out[r][1]);
+                *reinterpret_cast<float2 *>(dst) = num;
             else
-                dst[0] = out[r][0];
+                dst[0] = num.x;
         }
     }
+    const int s_lo = __ldg(a.src_kstart + k), s_hi = __ldg(a.src_kstart + k + 1);
+    if (s_lo < s_hi) add_plane_sources(a, k, s_lo, s_hi, x, c.y0 + RY * c.warp, exr, eyr, ez);
 }
 
-template <int TY>
+template <int TY, bool ROT>
 __global__ void __launch_bounds__(Shape<TY>::NT, 2)
     step_tma_kernel(const StepArgs a, const __grid_constant__ CUtensorMap cur_map,
                     const __grid_constant__ CUtensorMap prev_map, const __grid_constant__ CUtensorMap c_map,
@@ -277,12 +308,23 @@ __global__ void __launch_bounds__(Shape<TY>::NT, 2)
     }
     if (T <= 0) return;
 
-    float exr[RX], eyr[RY];
+    Wts w;
+    w.x1 = a.w.x[0];
+    w.x2 = bcast(a.w.x[1]);
+    w.x3 = a.w.x[2];
+    w.x4 = bcast(a.w.x[3]);
 #pragma unroll
-    for (int cx = 0; cx < RX; ++cx) {
-        const int x = c.x0 + 2 * c.lane + cx;
-        exr[cx] = x < a.nx ? __ldg(a.ex + x) : 0.0f;
+    for (int m = 0; m < kRadius; ++m) {
+        w.y[m] = bcast(a.w.y[m]);
+        w.z[m] = bcast(a.w.z[m]);
     }
+    float2 exr;
+    {
+        const int x = c.x0 + 2 * c.lane;
+        exr.x = x < a.nx ? __ldg(a.ex + x) : 0.0f;
+        exr.y = x + 1 < a.nx ? __ldg(a.ex + x + 1) : 0.0f;
+    }
+    float eyr[RY];
 #pragma unroll
     for (int r = 0; r < RY; ++r) {
         const int y = c.y0 + RY * c.warp + r;
@@ -291,17 +333,20 @@ __global__ void __launch_bounds__(Shape<TY>::NT, 2)
     const bool xy_damped = c.x0 < a.nbl || c.x0 + TX - 1 > a.nx - 1 - a.nbl || c.y0 < a.nbl ||
                            c.y0 + TY - 1 > a.ny - 1 - a.nbl;
 
-    float q[QN][RY][RX];
+    float2 q[QN][RY];
     // Issue order of u^n sequences is 0, 1, 2, ... with no gaps: the prologue
     // issues 0..NSU-1, the fill below 4 more, then one per finished step.
     int u_hi = min(NSU, nseq);
     int c_hi = min(NSC, T);
     // planes z0-4 .. z0+3 (sequences 0..7) fill queue slots 0..7
-#define MMOD_FILL(Q)                                                                \
-    if (mbar_wait(&c.full_u[(Q) % NSU], ((Q) / NSU) & 1, c.abort_flag, a.err))      \
-        read_own<TY, (Q)>(c, (Q), q);
-    MMOD_FILL(0) MMOD_FILL(1) MMOD_FILL(2) MMOD_FILL(3) MMOD_FILL(4) MMOD_FILL(5) MMOD_FILL(6) MMOD_FILL(7)
-#undef MMOD_FILL
+    bool filled = true;
+#pragma unroll 1
+    for (int seq = 0; seq < 2 * kRadius; ++seq)
+        filled = filled && mbar_wait(&c.full_u[seq % NSU], (seq / NSU) & 1, c.abort_flag, a.err);
+    if (filled) {
+        read_own<TY, 0>(c, 0, q); read_own<TY, 1>(c, 1, q); read_own<TY, 2>(c, 2, q); read_own<TY, 3>(c, 3, q);
+        read_own<TY, 4>(c, 4, q); read_own<TY, 5>(c, 5, q); read_own<TY, 6>(c, 6, q); read_own<TY, 7>(c, 7, q);
+    }
     __syncthreads();
     // sequences 0..3 are only needed in registers: their slots take NSU..NSU+3
     if (!*c.abort_flag) {
@@ -319,28 +364,39 @@ __global__ void __launch_bounds__(Shape<TY>::NT, 2)
     }                                                                                      \
     u_hi = min((t) + kRadius + NSU + 1, nseq);                                             \
     c_hi = min((t) + NSC + 1, T);
+        if constexpr (ROT) {
+            // queue rotated by unrolling 9 steps: no register moves, larger code
 #define MMOD_STEP(R)                                                   \
     if (t + (R) < T) {                                                 \
-        step<TY, (R)>(a, c, t + (R), q, exr, eyr, xy_damped);          \
+        step<TY, (R)>(a, c, t + (R), q, w, exr, eyr, xy_damped);       \
         MMOD_RELEASE(t + (R))                                          \
     }
-        for (int t = 0; t < T; t += QN) {
-            MMOD_STEP(0) MMOD_STEP(1) MMOD_STEP(2) MMOD_STEP(3) MMOD_STEP(4)
-            MMOD_STEP(5) MMOD_STEP(6) MMOD_STEP(7) MMOD_STEP(8)
-        }
+#pragma unroll 1
+            for (int t = 0; t < T; t += QN) {
+                MMOD_STEP(0) MMOD_STEP(1) MMOD_STEP(2) MMOD_STEP(3) MMOD_STEP(4)
+                MMOD_STEP(5) MMOD_STEP(6) MMOD_STEP(7) MMOD_STEP(8)
+            }
 #undef MMOD_STEP
+        } else {
+            // queue shifted by one plane after every step: compact code
+#pragma unroll 1
+            for (int t = 0; t < T; ++t) {
+                step<TY, 0>(a, c, t, q, w, exr, eyr, xy_damped);
+#pragma unroll
+                for (int i = 0; i < QN - 1; ++i)
+#pragma unroll
+                    for (int r = 0; r < RY; ++r) q[i][r] = q[i + 1][r];
+                MMOD_RELEASE(t)
+            }
+        }
 #undef MMOD_RELEASE
     }
     // After a give-up, wait (bounded) for the copies this CTA still has in
     // flight (the latest sequence of every slot) before its shared memory is
     // released.
     if (*c.abort_flag && tid == 0) {
-        for (int seq = max(0, u_hi - NSU); seq < u_hi; ++seq)
-            for (long long i = 0; i < kSpinLimit; ++i)
-                if (mbar_try_wait(&c.full_u[seq % NSU], (seq / NSU) & 1)) break;
-        for (int t = max(0, c_hi - NSC); t < c_hi; ++t)
-            for (long long i = 0; i < kSpinLimit; ++i)
-                if (mbar_try_wait(&c.full_c[t % NSC], (t / NSC) & 1)) break;
+        for (int seq = max(0, u_hi - NSU); seq < u_hi; ++seq) mbar_drain(&c.full_u[seq % NSU], (seq / NSU) & 1);
+        for (int t = max(0, c_hi - NSC); t < c_hi; ++t) mbar_drain(&c.full_c[t % NSC], (t / NSC) & 1);
     }
 }
 
@@ -389,10 +445,12 @@ bool make_tma_plan(const mmod_config &cfg, int nxp, float *const u[2], const flo
         if (!encode(&prev_map[b], u[b], cfg, nxp, TX, kTY)) return false;
     }
     if (!encode(c_map, c, cfg, nxp, TX, kTY)) return false;
-    auto kern = step_tma_kernel<kTY>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
+    auto kern = step_tma_kernel<kTY, false>;
+    for (auto k : {step_tma_kernel<kTY, false>, step_tma_kernel<kTY, true>}) {
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
     }
     int dev = 0, sms = 0, occ = 0;
     cudaGetDevice(&dev);
@@ -426,14 +484,18 @@ bool make_tma_plan(const mmod_config &cfg, int nxp, float *const u[2], const flo
     plan->zlen = (cfg.nz + best_c - 1) / best_c;
     plan->grid = (int)(tiles * best_c);
     plan->smem = S::SMEM;
+    plan->rotate = false;
     return true;
 }
 
 cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap *cur_map, const CUtensorMap *prev_map,
-                            const CUtensorMap *c_map, const TmaPlan &plan, cudaStream_t s) {
+                            const CUtensorMap *c_map, const TmaPlan &plan, bool rotate, cudaStream_t s) {
     using S = Shape<kTY>;
     const Geom g{plan.tiles_x, plan.tiles_y, plan.zchunks, plan.zlen};
-    step_tma_kernel<kTY><<<plan.grid, S::NT, plan.smem, s>>>(a, *cur_map, *prev_map, *c_map, g);
+    if (plan.rotate || rotate)
+        step_tma_kernel<kTY, true><<<plan.grid, S::NT, plan.smem, s>>>(a, *cur_map, *prev_map, *c_map, g);
+    else
+        step_tma_kernel<kTY, false><<<plan.grid, S::NT, plan.smem, s>>>(a, *cur_map, *prev_map, *c_map, g);
     return cudaGetLastError();
 }
 

@@ -8,10 +8,14 @@
 // loses about a decimal digit over 1000 steps.
 //
 // Eq. 5 and the damping update (e = dt * eta, e = 0 inside):
-//     num     = 2p - pp + e * pp + c * lap (+ s * w[n] at a source)
-//     u^{n+1} = num / (1 + e)
-// With e = 0 the multiply-add and the division by 1 are exact, so a kernel may
-// use the undamped form in the inner region and get identical bits.
+//     num     = 2p - pp + e * pp + c * lap
+//     r       = 1 / (1 + e): hardware approximate reciprocal refined by one
+//               Newton-Raphson step r <- r + r (1 - d r); exactly 1 where e = 0
+//     u^{n+1} = num * r  (+ (s * w[n]) * r at a source point)
+// With e = 0 the multiply-add and the multiplication by r = 1 are exact, so a
+// kernel may skip the damping arithmetic where e = 0 and get identical bits.
+// The source term is added last so that kernels can apply it in a rare
+// separate pass over the few source points.
 //
 // Explicit __fadd_rn / __fmaf_rn pin every rounding: the compiler cannot
 // contract or reorder them, so all kernels produce the same bits per point.
@@ -40,12 +44,19 @@ __device__ __forceinline__ float num_damped(float two_p, float pp, float c, floa
     return __fmaf_rn(c, lap, __fmaf_rn(e, pp, __fsub_rn(two_p, pp)));
 }
 
-__device__ __forceinline__ float add_source(float num, float scale, float w) {
-    return __fmaf_rn(scale, w, num);
+// 1 / d for d = 1 + e in [1, 8): rcp.approx (relative error below 2^-22) then
+// one Newton-Raphson step for the reciprocal, r1 = r0 + r0 (1 - d r0), which
+// squares the relative error.  For d = 1 both steps are exact (r = 1).
+__device__ __forceinline__ float recip_nr(float d) {
+    float r0;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(d));
+    return __fmaf_rn(r0, __fmaf_rn(-d, r0, 1.0f), r0);
 }
 
-__device__ __forceinline__ float finish_damped(float num, float e) {
-    return __fdiv_rn(num, __fadd_rn(1.0f, e));
+__device__ __forceinline__ float damp_factor(float e) { return recip_nr(__fadd_rn(1.0f, e)); }
+
+__device__ __forceinline__ float add_source(float out, float scale, float w, float r) {
+    return __fmaf_rn(__fmul_rn(scale, w), r, out);
 }
 
 }  // namespace mmod

@@ -12,6 +12,7 @@ struct TmaPlan {
     int zlen = 0;                   // planes per z-range (last one may be shorter)
     int grid = 0;                   // CTAs launched
     int smem = 0;                   // dynamic shared memory per CTA, bytes
+    bool rotate = false;            // z queue rotated by unrolling (true) or shifted
 };
 
 // Chooses the decomposition for this grid and encodes the tensor maps of both
