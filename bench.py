@@ -204,15 +204,16 @@ def run_mmod(args):
     npts = p.npoints
     prop = M.Propagator.from_problem(p, device=local)
     if args.kernel != "auto":
-        prop.set_kernel({"simple": M.KERNEL_SIMPLE, "tma": M.KERNEL_TMA,
-                         "tma_rotate": M.KERNEL_TMA_ROTATE}[args.kernel])
+        prop.set_kernel({"simple": M.KERNEL_SIMPLE, "tma": M.KERNEL_TMA}[args.kernel])
+    if args.variant >= 0:
+        prop.set_variant(args.variant)
     stream = torch.cuda.current_stream(dev)
     vel_d = torch.from_numpy(p.vel).to(dev)
     wav_d = torch.from_numpy(np.ascontiguousarray(p.wavelet)).to(dev)
     tr_d = torch.empty((p.nt, len(p.rec_ijk)), device=dev)
     prop.set_model(vel_d, stream)
-    kernel_tag = ("tma_rotate" if args.kernel == "tma_rotate" else
-                  "tma" if (args.kernel in ("auto", "tma") and prop_uses_tma(prop)) else "simple")
+    kernel_tag = "tma" if (args.kernel in ("auto", "tma") and prop_uses_tma(prop)) else "simple"
+    plan = prop.plan() if kernel_tag == "tma" else None
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -285,7 +286,9 @@ def run_mmod(args):
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": describe(p, {"parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                                       "kernel": kernel_tag}),
+                                       "kernel": kernel_tag, "plan": plan,
+                                       "variant": None if plan is None else
+                                       M.mmod_tma_variant_name(plan["variant"])}),
                 "hbm_roofline_pct": 100.0 * BYTES_PER_POINT * value / ws / peak,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clocks}
@@ -315,7 +318,8 @@ def main():
     ap.add_argument("--impl", choices=["mmod", "reference"], default="mmod")
     ap.add_argument("--workload", default="layered240")
     ap.add_argument("--nt", type=int, default=None, help="override the workload's step count")
-    ap.add_argument("--kernel", choices=["auto", "simple", "tma", "tma_rotate"], default="auto")
+    ap.add_argument("--kernel", choices=["auto", "simple", "tma"], default="auto")
+    ap.add_argument("--variant", type=int, default=-1, help="TMA kernel variant (-1 = automatic)")
     ap.add_argument("--ref-seconds", type=float, default=20.0,
                     help="CPU seconds per oracle sample (cpu_baseline / reference arm)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

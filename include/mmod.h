@@ -119,15 +119,27 @@ mmod_status mmod_set_state(mmod_handle *h, const float *u_prev, const float *u_c
 /* Copy the last forward's final state u^{nt-1}, u^{nt} (either may be NULL). */
 mmod_status mmod_get_state(mmod_handle *h, float *u_prev, float *u_cur, mmod_stream stream);
 
-/* Kernel selection: MMOD_KERNEL_AUTO (default) picks the TMA-pipelined
- * kernel; MMOD_KERNEL_SIMPLE runs the plain one-thread-per-point kernel, which
- * performs the identical FP32 operations per point (validation);
- * MMOD_KERNEL_TMA / MMOD_KERNEL_TMA_ROTATE force the pipelined kernel with its
- * z register queue shifted after every plane (compact code) or rotated by
- * unrolling nine planes (no moves, larger code).  All variants produce the
- * same bits.  Errors: ARG (unknown id), UNSUPPORTED (no TMA plan). */
-enum { MMOD_KERNEL_AUTO = 0, MMOD_KERNEL_SIMPLE = 1, MMOD_KERNEL_TMA = 2, MMOD_KERNEL_TMA_ROTATE = 3 };
+/* Kernel selection: MMOD_KERNEL_AUTO (default) and MMOD_KERNEL_TMA run the
+ * TMA-pipelined kernel; MMOD_KERNEL_SIMPLE runs the plain one-thread-per-point
+ * kernel, which performs the identical FP32 operations per point
+ * (validation).  All kernels produce the same bits.  Errors: ARG (unknown
+ * id), UNSUPPORTED (the grid has no TMA plan). */
+enum { MMOD_KERNEL_AUTO = 0, MMOD_KERNEL_SIMPLE = 1, MMOD_KERNEL_TMA = 2 };
 mmod_status mmod_set_kernel(mmod_handle *h, int kernel);
+
+/* Compiled variants of the TMA kernel (tile shape, points per thread, z
+ * queue handling), for tuning.  mmod_tma_variant_name returns a static
+ * description ("" out of range).  mmod_set_tma_variant selects one for the
+ * handle (-1 = automatic).  All variants produce the same bits.  Errors:
+ * ARG (out of range), UNSUPPORTED (no TMA plan). */
+int mmod_tma_variant_count(void);
+const char *mmod_tma_variant_name(int v);
+mmod_status mmod_set_tma_variant(mmod_handle *h, int v);
+
+/* Launch plan of the active TMA variant: writes 8 ints {variant, tiles_x,
+ * tiles_y, z_chunks, planes_per_chunk, grid, block, resident_ctas_per_sm}.
+ * Errors: ARG, UNSUPPORTED (no TMA plan). */
+mmod_status mmod_get_plan(const mmod_handle *h, int *out8);
 
 /* Number of kernel launches the last mmod_forward enqueued (all of this
  * library's kernels, including set-up and gathers). */

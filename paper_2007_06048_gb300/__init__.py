@@ -25,12 +25,13 @@ __all__ = ["MmodError", "build", "load", "mmod_create", "mmod_destroy", "mmod_se
 
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_UNSTABLE", -3: "ERR_OOM", -4: "ERR_CUDA",
           -5: "ERR_TIMEOUT", -6: "ERR_STATE", -7: "ERR_UNSUPPORTED"}
-KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_TMA, KERNEL_TMA_ROTATE = 0, 1, 2, 3
+KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_TMA = 0, 1, 2
 
 # Every symbol include/mmod.h declares (checked against the header by the tests).
 EXPORTED = ["mmod_create", "mmod_destroy", "mmod_set_model", "mmod_forward", "mmod_set_state",
             "mmod_get_state", "mmod_set_kernel", "mmod_last_launch_count", "mmod_last_loop_ms",
-            "mmod_cfl_dt", "mmod_last_error", "mmod_version", "mmod_check_recip"]
+            "mmod_cfl_dt", "mmod_last_error", "mmod_version", "mmod_check_recip",
+            "mmod_tma_variant_count", "mmod_tma_variant_name", "mmod_set_tma_variant", "mmod_get_plan"]
 
 
 class MmodError(RuntimeError):
@@ -79,6 +80,10 @@ def load():
         "mmod_last_error": ([P], ctypes.c_char_p),
         "mmod_version": ([], ctypes.c_char_p),
         "mmod_check_recip": ([I, ctypes.POINTER(ctypes.c_uint)], I),
+        "mmod_tma_variant_count": ([], I),
+        "mmod_tma_variant_name": ([I], ctypes.c_char_p),
+        "mmod_set_tma_variant": ([P, I], I),
+        "mmod_get_plan": ([P, ctypes.POINTER(ctypes.c_int)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -179,6 +184,25 @@ def mmod_check_recip(n: int = 1 << 22) -> int:
     return int(out.value)
 
 
+def mmod_tma_variant_count() -> int:
+    return int(load().mmod_tma_variant_count())
+
+
+def mmod_tma_variant_name(v: int) -> str:
+    return load().mmod_tma_variant_name(int(v)).decode()
+
+
+def mmod_set_tma_variant(h, v: int):
+    _check(h, load().mmod_set_tma_variant(h, int(v)))
+
+
+def mmod_get_plan(h) -> dict:
+    out = (ctypes.c_int * 8)()
+    _check(h, load().mmod_get_plan(h, out))
+    keys = ["variant", "tiles_x", "tiles_y", "z_chunks", "planes_per_chunk", "grid", "block", "ctas_per_sm"]
+    return dict(zip(keys, list(out)))
+
+
 def mmod_last_error(h) -> str:
     return load().mmod_last_error(h).decode()
 
@@ -215,6 +239,12 @@ class Propagator:
 
     def set_kernel(self, kernel: int):
         mmod_set_kernel(self.handle, kernel)
+
+    def set_variant(self, v: int):
+        mmod_set_tma_variant(self.handle, v)
+
+    def plan(self) -> dict:
+        return mmod_get_plan(self.handle)
 
     def forward(self, wavelet, traces, final_u=None, stream=None):
         mmod_forward(self.handle, wavelet, traces, final_u, stream)

@@ -84,7 +84,8 @@ struct mmod_handle {
     int g_kernel = -1;
     long long g_launches = 0;
 
-    TmaPlan plan{};
+    TmaPlan plans[kMaxTmaVariants]{};
+    int variant = -1;                   // -1: automatic choice
     bool tma_ok = false;
     CUtensorMap cur_map[2], prev_map[2], c_map;
 
@@ -214,6 +215,13 @@ bool use_tma(const mmod_handle *h) {
     return h->tma_ok && h->kernel != MMOD_KERNEL_SIMPLE;
 }
 
+// Default variant: the fastest measured on the 240^3 workload.
+constexpr int kDefaultVariant = 2;
+
+const TmaPlan &active_plan(const mmod_handle *h) {
+    return h->plans[h->variant >= 0 ? h->variant : kDefaultVariant];
+}
+
 // Enqueue the nt steps (and receiver gathers) on stream s.  Returns the
 // number of kernels launched.
 mmod_status enqueue_steps(mmod_handle *h, const float *wav, float *tr, cudaStream_t s, long long *nlaunch) {
@@ -224,8 +232,7 @@ mmod_status enqueue_steps(mmod_handle *h, const float *wav, float *tr, cudaStrea
     for (int n = 0; n < nt; ++n) {
         StepArgs a = step_args(h, wav, tr, n);
         if (tma) {
-            CK(h, launch_step_tma(a, &h->cur_map[(n + 1) & 1], &h->prev_map[n & 1], &h->c_map, h->plan,
-                                  h->kernel == MMOD_KERNEL_TMA_ROTATE, s));
+            CK(h, launch_step_tma(a, &h->cur_map[(n + 1) & 1], &h->prev_map[n & 1], &h->c_map, active_plan(h), s));
             ++count;
         } else {
             a.traces = nullptr;   // the plain path gathers with a separate kernel
@@ -363,7 +370,7 @@ MMOD_API mmod_status mmod_create(const mmod_config *cfg, int device, mmod_handle
     CKC(cudaHostAlloc(&h->err_host, sizeof(int), cudaHostAllocMapped));
     *h->err_host = 0;
     CKC(cudaHostGetDevicePointer(&h->err_dev, h->err_host, 0));
-    h->tma_ok = make_tma_plan(h->cfg, h->nxp, h->u, h->c, h->cur_map, h->prev_map, &h->c_map, &h->plan);
+    h->tma_ok = make_tma_plan(h->cfg, h->nxp, h->u, h->c, h->cur_map, h->prev_map, &h->c_map, h->plans);
 #undef CKC
     *out = h;
     return MMOD_OK;
@@ -382,12 +389,32 @@ MMOD_API mmod_status mmod_destroy(mmod_handle *h) {
 
 MMOD_API mmod_status mmod_set_kernel(mmod_handle *h, int kernel) {
     if (!h) return MMOD_ERR_ARG;
-    if (kernel != MMOD_KERNEL_AUTO && kernel != MMOD_KERNEL_SIMPLE && kernel != MMOD_KERNEL_TMA &&
-        kernel != MMOD_KERNEL_TMA_ROTATE)
+    if (kernel != MMOD_KERNEL_AUTO && kernel != MMOD_KERNEL_SIMPLE && kernel != MMOD_KERNEL_TMA)
         return fail(h, MMOD_ERR_ARG, "unknown kernel id");
-    if ((kernel == MMOD_KERNEL_TMA || kernel == MMOD_KERNEL_TMA_ROTATE) && !h->tma_ok)
+    if (kernel == MMOD_KERNEL_TMA && !h->tma_ok)
         return fail(h, MMOD_ERR_UNSUPPORTED, "TMA kernel unavailable for this grid");
     h->kernel = kernel;
+    return MMOD_OK;
+}
+
+MMOD_API int mmod_tma_variant_count(void) { return tma_variant_count(); }
+
+MMOD_API const char *mmod_tma_variant_name(int v) { return tma_variant_name(v); }
+
+MMOD_API mmod_status mmod_set_tma_variant(mmod_handle *h, int v) {
+    if (!h) return MMOD_ERR_ARG;
+    if (v < -1 || v >= tma_variant_count()) return fail(h, MMOD_ERR_ARG, "unknown TMA variant");
+    if (v >= 0 && !h->tma_ok) return fail(h, MMOD_ERR_UNSUPPORTED, "TMA kernel unavailable for this grid");
+    h->variant = v;
+    return MMOD_OK;
+}
+
+MMOD_API mmod_status mmod_get_plan(const mmod_handle *h, int *out8) {
+    if (!h || !out8) return MMOD_ERR_ARG;
+    if (!h->tma_ok) return MMOD_ERR_UNSUPPORTED;
+    const TmaPlan &p = active_plan(h);
+    const int v[8] = {p.variant, p.tiles_x, p.tiles_y, p.zchunks, p.zlen, p.grid, p.block, p.occupancy};
+    for (int i = 0; i < 8; ++i) out8[i] = v[i];
     return MMOD_OK;
 }
 
@@ -514,8 +541,7 @@ MMOD_API mmod_status mmod_forward(mmod_handle *h, const float *wavelet, float *t
     h->state_pending = false;
 
     if (c.nt > 0) {
-        const int kern = use_tma(h) ? (h->kernel == MMOD_KERNEL_TMA_ROTATE ? MMOD_KERNEL_TMA_ROTATE : MMOD_KERNEL_TMA)
-                                    : MMOD_KERNEL_SIMPLE;
+        const int kern = use_tma(h) ? 100 + active_plan(h).variant : MMOD_KERNEL_SIMPLE;
         if (!h->gexec || h->g_wav != dwav || h->g_tr != dtr || h->g_kernel != kern) {
             if (h->gexec) {
                 cudaGraphExecDestroy(h->gexec);

@@ -46,7 +46,7 @@ cudaError_t launch_gather(const float *u, const long long *rec_off, int nrec, fl
 struct TmaPlan;   // tile shape / grid decomposition of the TMA kernel
 cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap *cur_map,
                             const CUtensorMap *prev_map, const CUtensorMap *c_map,
-                            const TmaPlan &plan, bool rotate, cudaStream_t s);
+                            const TmaPlan &plan, cudaStream_t s);
 
 cudaError_t launch_model_scan(const float *vel, long long n, unsigned int *vmax_bits,
                               unsigned long long *bad, cudaStream_t s);

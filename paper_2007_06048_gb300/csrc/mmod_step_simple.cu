@@ -23,13 +23,16 @@ __global__ void __launch_bounds__(128) step_simple_kernel(const StepArgs a) {
     const long long o = (long long)k * a.plane + (long long)j * a.nxp + i;
     const float p = __ldg(a.ucur + o);
     const float two_p = __fadd_rn(p, p);
-    float lap = 0.0f;
+    float lx = pair_first(a.w.x[0], ld0(a.ucur, a, i + 1, j, k), ld0(a.ucur, a, i - 1, j, k), two_p);
+    float ly = pair_first(a.w.y[0], ld0(a.ucur, a, i, j + 1, k), ld0(a.ucur, a, i, j - 1, k), two_p);
+    float lz = pair_first(a.w.z[0], ld0(a.ucur, a, i, j, k + 1), ld0(a.ucur, a, i, j, k - 1), two_p);
 #pragma unroll
-    for (int m = 1; m <= kRadius; ++m) lap = pair_acc(lap, a.w.x[m - 1], ld0(a.ucur, a, i + m, j, k), ld0(a.ucur, a, i - m, j, k), two_p);
-#pragma unroll
-    for (int m = 1; m <= kRadius; ++m) lap = pair_acc(lap, a.w.y[m - 1], ld0(a.ucur, a, i, j + m, k), ld0(a.ucur, a, i, j - m, k), two_p);
-#pragma unroll
-    for (int m = 1; m <= kRadius; ++m) lap = pair_acc(lap, a.w.z[m - 1], ld0(a.ucur, a, i, j, k + m), ld0(a.ucur, a, i, j, k - m), two_p);
+    for (int m = 2; m <= kRadius; ++m) {
+        lx = pair_acc(lx, a.w.x[m - 1], ld0(a.ucur, a, i + m, j, k), ld0(a.ucur, a, i - m, j, k), two_p);
+        ly = pair_acc(ly, a.w.y[m - 1], ld0(a.ucur, a, i, j + m, k), ld0(a.ucur, a, i, j - m, k), two_p);
+        lz = pair_acc(lz, a.w.z[m - 1], ld0(a.ucur, a, i, j, k + m), ld0(a.ucur, a, i, j, k - m), two_p);
+    }
+    const float lap = lap_sum(lx, ly, lz);
     const float e = __fadd_rn(__fadd_rn(__ldg(a.ex + i), __ldg(a.ey + j)), __ldg(a.ez + k));
     const float r = damp_factor(e);
     float out = __fmul_rn(num_damped(two_p, a.uprev[o], __ldg(a.c + o), lap, e), r);

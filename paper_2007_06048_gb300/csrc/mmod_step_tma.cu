@@ -3,7 +3,8 @@
 // receivers of the previous step.
 //
 // Decomposition.  A CTA owns a 64 x TY tile in (x, y) and a range of planes in
-// z, and marches down z.  Each thread owns 2 (x) x 4 (y) points.
+// z, and marches down z.  Each thread owns 2 (x) x RY (y) points: lane l holds
+// columns x0+2l, x0+2l+1, warp w rows y0+RY*w .. y0+RY*w+RY-1.
 //
 // Data movement.  One elected thread issues cp.async.bulk.tensor loads:
 //   * u^n planes with a 4-cell x-y halo, (64+8) x (TY+8) floats, into an
@@ -11,14 +12,19 @@
 //     the u = 0 reading, so no thread tests bounds on loads.
 //   * u^{n-1} and c planes, 64 x TY floats each, into an NSC-slot ring.
 // Each slot has an mbarrier (transaction count = box bytes).  A slot is
-// refilled after the __syncthreads that ends the step that last reads it, so
-// up to four planes per ring are in flight while the CTA computes.
+// refilled after the block barrier that ends the last step reading it, so
+// several planes per ring are in flight while the CTA computes.
 //
 // Stencil.  x and y neighbours come from the centre plane in shared memory
 // (8-byte loads, conflict-free: a warp reads 64 consecutive floats per row);
-// z neighbours come from a register queue of 9 planes per point, rotated by
-// unrolling the z loop 9 times (no register moves).  The arithmetic per point
-// is stencil.cuh's, in the same order as the plain kernel: bit-identical.
+// z neighbours come from a register queue of 9 planes per point, either
+// shifted by one plane after every step (compact code) or rotated by
+// unrolling nine steps (no moves).  The two points of a thread share every
+// operation, so the arithmetic runs as packed FP32x2 (__ffma2_rn, __fadd2_rn:
+// per component the same rounding as the scalar intrinsics), except the x
+// offsets 1 and 3 whose operands do not form aligned register pairs.  The
+// per-point arithmetic and its order are stencil.cuh's: the result is bit for
+// bit the plain kernel's.
 //
 // Waits are bounded (100 ms of wall-clock time each): a wait that gives up sets
 // the mapped error word, the CTA stops at the next block barrier, drains its
@@ -32,22 +38,24 @@ namespace mmod {
 namespace {
 
 constexpr int TX = 64;                 // tile width: 32 lanes x 2 points
-constexpr int RX = 2;                  // points per thread along x
-constexpr int RY = 4;                  // points per thread along y
 constexpr int HX = TX + 2 * kRadius;   // 72: halo tile width
 constexpr int NSU = 8;                 // u^n slots: 5 resident planes + prefetch
 constexpr int NSC = 4;                 // u^{n-1}, c slots
-constexpr int QN = 2 * kRadius + 1;    // z register queue depth
 constexpr unsigned long long kWaitNs = 100000000ull;   // a wait gives up after 100 ms
 
-template <int TY>
+template <int TY_, int RY_, int U_>
 struct Shape {
+    static constexpr int TY = TY_;
+    static constexpr int RY = RY_;
+    static constexpr int U = U_;                    // z steps per unrolled block
+    static constexpr int QD = 2 * kRadius + U;      // register queue depth
     static constexpr int NWARP = TY / RY;
     static constexpr int NT = NWARP * 32;
     static constexpr int HY = TY + 2 * kRadius;
     static constexpr int CUR = HX * HY;             // floats per u^n slot
     static constexpr int PC = TX * TY;              // floats per u^{n-1} or c slot
     static constexpr int SMEM = (NSU * CUR + NSC * 2 * PC) * 4 + (NSU + NSC) * 8 + 16;
+    static_assert(TY % RY == 0, "rows per thread must divide the tile height");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -119,48 +127,48 @@ struct Geom {
     int tiles_x, tiles_y, zchunks, zlen;
 };
 
-template <int TY>
 struct Ctx {
-    using S = Shape<TY>;
     float *cur;          // NSU u^n slots
     float *up;           // NSC u^{n-1} slots
     float *cc;           // NSC c slots
-    uint64_t *full_u;    // NSU barriers
+    uint64_t *full_u;    // NSU barriers: data landed
     uint64_t *full_c;    // NSC barriers
     int *abort_flag;
     int x0, y0, z0, T;
     int lane, warp;
 };
 
-template <int TY>
-__device__ __forceinline__ void issue_u(const Ctx<TY> &c, const CUtensorMap *map, int seq) {
+template <class S>
+__device__ __forceinline__ void issue_u(const Ctx &c, const CUtensorMap *map, int seq) {
     const int s = seq % NSU;
-    mbar_expect_tx(&c.full_u[s], Shape<TY>::CUR * 4);
-    tma_load_3d(c.cur + s * Shape<TY>::CUR, map, c.x0 - kRadius, c.y0 - kRadius, c.z0 - kRadius + seq,
-                &c.full_u[s]);
+    mbar_expect_tx(&c.full_u[s], S::CUR * 4);
+    tma_load_3d(c.cur + s * S::CUR, map, c.x0 - kRadius, c.y0 - kRadius, c.z0 - kRadius + seq, &c.full_u[s]);
 }
 
-template <int TY>
-__device__ __forceinline__ void issue_c(const Ctx<TY> &c, const CUtensorMap *pmap, const CUtensorMap *cmap,
-                                        int t) {
+template <class S>
+__device__ __forceinline__ void issue_c(const Ctx &c, const CUtensorMap *pmap, const CUtensorMap *cmap, int t) {
     const int s = t % NSC;
-    mbar_expect_tx(&c.full_c[s], 2 * Shape<TY>::PC * 4);
-    tma_load_3d(c.up + s * Shape<TY>::PC, pmap, c.x0, c.y0, c.z0 + t, &c.full_c[s]);
-    tma_load_3d(c.cc + s * Shape<TY>::PC, cmap, c.x0, c.y0, c.z0 + t, &c.full_c[s]);
+    mbar_expect_tx(&c.full_c[s], 2 * S::PC * 4);
+    tma_load_3d(c.up + s * S::PC, pmap, c.x0, c.y0, c.z0 + t, &c.full_c[s]);
+    tma_load_3d(c.cc + s * S::PC, cmap, c.x0, c.y0, c.z0 + t, &c.full_c[s]);
 }
 
-// Own points of plane seq (rows 4+4w+r, columns 4+2*lane) into queue slot Q.
-template <int TY, int Q>
-__device__ __forceinline__ void read_own(const Ctx<TY> &c, int seq, float2 (&q)[QN][RY]) {
-    const float *base = c.cur + (seq % NSU) * Shape<TY>::CUR + (kRadius + RY * c.warp) * HX + kRadius + 2 * c.lane;
+// Own points of plane seq (rows 4+RY*w+r, columns 4+2*lane) into queue slot Q.
+template <class S, int Q>
+__device__ __forceinline__ void read_own(const Ctx &c, int seq, float2 (&q)[S::QD][S::RY]) {
+    const float *base = c.cur + (seq % NSU) * S::CUR + (kRadius + S::RY * c.warp) * HX + kRadius + 2 * c.lane;
 #pragma unroll
-    for (int r = 0; r < RY; ++r) q[Q][r] = *reinterpret_cast<const float2 *>(base + r * HX);
+    for (int r = 0; r < S::RY; ++r) q[Q][r] = *reinterpret_cast<const float2 *>(base + r * HX);
 }
 
 __device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
 __device__ __forceinline__ float2 bcast(float v) { return make_float2(v, v); }
 
-// Packed pair_acc: per component exactly stencil.cuh's pair_acc.
+// Packed pair terms: per component exactly stencil.cuh's pair_first / pair_acc.
+__device__ __forceinline__ float2 pair_first2(float2 w, float2 a, float2 b, float2 neg_two_p) {
+    return __fmul2_rn(w, __fadd2_rn(__fadd2_rn(a, b), neg_two_p));
+}
+
 __device__ __forceinline__ float2 pair_acc2(float2 acc, float2 w, float2 a, float2 b, float2 neg_two_p) {
     return __ffma2_rn(w, __fadd2_rn(__fadd2_rn(a, b), neg_two_p), acc);
 }
@@ -168,6 +176,7 @@ __device__ __forceinline__ float2 pair_acc2(float2 acc, float2 w, float2 a, floa
 // Sources of plane k that fall on this thread's points (rare: one plane per
 // source).  Each thread re-reads the value it has just stored, so program
 // order makes it visible; the term is scaled by the point's damping factor.
+template <int RY>
 __device__ __noinline__ void add_plane_sources(const StepArgs &a, int k, int s_lo, int s_hi, int x, int y0,
                                                float2 exr, const float (&eyr)[RY], float ez) {
     for (int s = s_lo; s < s_hi; ++s) {
@@ -191,83 +200,101 @@ struct Wts {
     float x1, x3;
 };
 
-// One z step computing plane z0 + t.  R is the queue rotation (0 when the
-// queue is shifted after every step instead).
-template <int TY, int R>
-__device__ __forceinline__ void step(const StepArgs &a, const Ctx<TY> &c, int t, float2 (&q)[QN][RY],
-                                     const Wts &w, float2 exr, const float (&eyr)[RY], bool xy_damped) {
-    using S = Shape<TY>;
+// Per-plane values every thread needs, loaded one step ahead.
+struct PlaneInfo {
+    float ez;      // dt * eta_z(k)
+    int s_lo, s_hi;  // sources of plane k
+};
+
+__device__ __forceinline__ PlaneInfo plane_info(const StepArgs &a, int k) {
+    PlaneInfo p;
+    const int kk = min(k, a.nz - 1);
+    p.ez = __ldg(a.ez + kk);
+    p.s_lo = __ldg(a.src_kstart + kk);
+    p.s_hi = __ldg(a.src_kstart + kk + 1);
+    return p;
+}
+
+// One z step computing plane z0 + t.  The queue window of this step is
+// q[J .. J+8] (planes k-4 .. k+4); the leading plane k+4 lands in q[J+8].
+template <class S, int J>
+__device__ __forceinline__ void step(const StepArgs &a, const Ctx &c, int t, float2 (&q)[S::QD][S::RY],
+                                     const Wts &w, float2 exr, const float (&eyr)[S::RY], bool xy_damped,
+                                     const PlaneInfo &pi, float *const (&out_row)[S::RY]) {
+    constexpr int RY = S::RY;
     const int k = c.z0 + t;
     // 1. the leading plane k+4 (sequence t+8) enters the queue
     {
         const int seq = t + 2 * kRadius;
         if (!mbar_wait(&c.full_u[seq % NSU], (seq / NSU) & 1, c.abort_flag, a.err)) return;
-        read_own<TY, (2 * kRadius + R) % QN>(c, seq, q);
+        read_own<S, J + 2 * kRadius>(c, seq, q);
     }
     if (!mbar_wait(&c.full_c[t % NSC], (t / NSC) & 1, c.abort_flag, a.err)) return;
 
-    // 2. y neighbour columns: rows 4w .. 4w+11 of the centre plane (sequence t+4)
-    const float *ctr = c.cur + ((t + kRadius) % NSU) * S::CUR;
+    // 2. y neighbour columns: rows RY*w .. RY*w+RY+7 of the centre plane (sequence t+4)
+    const float *ctr = c.cur + ((t + kRadius) % NSU) * S::CUR + (RY * c.warp) * HX + 2 * c.lane;
     float2 yc[RY + 2 * kRadius];
 #pragma unroll
-    for (int rr = 0; rr < RY + 2 * kRadius; ++rr)
-        yc[rr] = *reinterpret_cast<const float2 *>(ctr + (RY * c.warp + rr) * HX + kRadius + 2 * c.lane);
+    for (int rr = 0; rr < RY + 2 * kRadius; ++rr) yc[rr] = *reinterpret_cast<const float2 *>(ctr + rr * HX + kRadius);
     const float *upp = c.up + (t % NSC) * S::PC + (RY * c.warp) * TX + 2 * c.lane;
     const float *ccp = c.cc + (t % NSC) * S::PC + (RY * c.warp) * TX + 2 * c.lane;
     const bool damped = xy_damped || k < a.nbl || k > a.nz - 1 - a.nbl;
-    const float ez = __ldg(a.ez + k);   // e is exactly 0 on planes without damping
-    const int x = c.x0 + 2 * c.lane;
+    const long long koff = (long long)k * a.plane;
 #pragma unroll
     for (int r = 0; r < RY; ++r) {
-        // x neighbours: columns 2*lane .. 2*lane+9 of row 4+4w+r, as 5 aligned pairs
-        float2 xa[(RX + 2 * kRadius) / 2];
-        const float *row = ctr + (kRadius + RY * c.warp + r) * HX + 2 * c.lane;
+        // x neighbours: columns 2*lane .. 2*lane+9 of row 4+RY*w+r, as 5 aligned pairs
+        float2 xa[1 + kRadius];
+        const float *row = ctr + (kRadius + r) * HX;
 #pragma unroll
-        for (int j = 0; j < (RX + 2 * kRadius) / 2; ++j) xa[j] = *reinterpret_cast<const float2 *>(row + 2 * j);
-        const float2 p = q[(kRadius + R) % QN][r];
+        for (int j = 0; j <= kRadius; ++j) xa[j] = *reinterpret_cast<const float2 *>(row + 2 * j);
+        const float2 p = q[J + kRadius][r];
         const float2 two_p = __fadd2_rn(p, p);
         const float2 ntp = neg2(two_p);
-        float2 lap = make_float2(0.0f, 0.0f);
-        // x, m = 1 (odd offsets do not form aligned pairs: scalar)
-        lap.x = pair_acc(lap.x, w.x1, xa[2].y, xa[1].y, two_p.x);
-        lap.y = pair_acc(lap.y, w.x1, xa[3].x, xa[2].x, two_p.y);
-        lap = pair_acc2(lap, w.x2, xa[3], xa[1], ntp);
-        lap.x = pair_acc(lap.x, w.x3, xa[3].y, xa[0].y, two_p.x);
-        lap.y = pair_acc(lap.y, w.x3, xa[4].x, xa[1].x, two_p.y);
-        lap = pair_acc2(lap, w.x4, xa[4], xa[0], ntp);
+        // x: offsets 1 and 3 do not form aligned pairs, so they run scalar
+        float2 lx;
+        lx.x = pair_first(w.x1, xa[2].y, xa[1].y, two_p.x);
+        lx.y = pair_first(w.x1, xa[3].x, xa[2].x, two_p.y);
+        lx = pair_acc2(lx, w.x2, xa[3], xa[1], ntp);
+        lx.x = pair_acc(lx.x, w.x3, xa[3].y, xa[0].y, two_p.x);
+        lx.y = pair_acc(lx.y, w.x3, xa[4].x, xa[1].x, two_p.y);
+        lx = pair_acc2(lx, w.x4, xa[4], xa[0], ntp);
+        float2 ly = pair_first2(w.y[0], yc[kRadius + r + 1], yc[kRadius + r - 1], ntp);
+        float2 lz = pair_first2(w.z[0], q[J + kRadius + 1][r], q[J + kRadius - 1][r], ntp);
 #pragma unroll
-        for (int m = 1; m <= kRadius; ++m) lap = pair_acc2(lap, w.y[m - 1], yc[kRadius + r + m], yc[kRadius + r - m], ntp);
-#pragma unroll
-        for (int m = 1; m <= kRadius; ++m)
-            lap = pair_acc2(lap, w.z[m - 1], q[(kRadius + m + R) % QN][r], q[(kRadius - m + R) % QN][r], ntp);
+        for (int m = 2; m <= kRadius; ++m) {
+            ly = pair_acc2(ly, w.y[m - 1], yc[kRadius + r + m], yc[kRadius + r - m], ntp);
+            lz = pair_acc2(lz, w.z[m - 1], q[J + kRadius + m][r], q[J + kRadius - m][r], ntp);
+        }
+        const float2 lap = __fadd2_rn(__fadd2_rn(lx, ly), lz);
         const float2 pp = *reinterpret_cast<const float2 *>(upp + r * TX);
         const float2 cc = *reinterpret_cast<const float2 *>(ccp + r * TX);
-        // e = (e_x + e_y) + e_z; zero on planes without damping
-        const float2 e = __fadd2_rn(__fadd2_rn(exr, bcast(eyr[r])), bcast(ez));
+        // e = (e_x + e_y) + e_z; exactly 0 on planes without damping
+        const float2 e = __fadd2_rn(__fadd2_rn(exr, bcast(eyr[r])), bcast(pi.ez));
         float2 num = __ffma2_rn(cc, lap, __ffma2_rn(e, pp, __fadd2_rn(two_p, neg2(pp))));
         if (damped) num = __fmul2_rn(num, make_float2(damp_factor(e.x), damp_factor(e.y)));
-        // 3. store u^{n+1} over u^{n-1}
-        const int y = c.y0 + RY * c.warp + r;
-        if (y < a.ny && x < a.nx) {
-            float *dst = a.uprev + (long long)k * a.plane + (long long)y * a.nxp + x;
-            if (x + 1 < a.nx)
+        // 3. store u^{n+1} over u^{n-1} (out_row is null for rows and columns
+        // outside the grid; its x+1 twin is stored only inside the grid)
+        if (out_row[r]) {
+            float *dst = out_row[r] + koff;
+            if (c.x0 + 2 * c.lane + 1 < a.nx)
                 *reinterpret_cast<float2 *>(dst) = num;
             else
                 dst[0] = num.x;
         }
     }
-    const int s_lo = __ldg(a.src_kstart + k), s_hi = __ldg(a.src_kstart + k + 1);
-    if (s_lo < s_hi) add_plane_sources(a, k, s_lo, s_hi, x, c.y0 + RY * c.warp, exr, eyr, ez);
+    if (pi.s_lo < pi.s_hi)
+        add_plane_sources<RY>(a, k, pi.s_lo, pi.s_hi, c.x0 + 2 * c.lane, c.y0 + RY * c.warp, exr, eyr, pi.ez);
 }
 
-template <int TY, bool ROT>
-__global__ void __launch_bounds__(Shape<TY>::NT, 2)
+template <class S>
+__global__ void __launch_bounds__(S::NT)
     step_tma_kernel(const StepArgs a, const __grid_constant__ CUtensorMap cur_map,
                     const __grid_constant__ CUtensorMap prev_map, const __grid_constant__ CUtensorMap c_map,
                     const Geom g) {
-    using S = Shape<TY>;
+    constexpr int RY = S::RY;
+    constexpr int U = S::U;
     extern __shared__ __align__(128) unsigned char smem[];
-    Ctx<TY> c;
+    Ctx c;
     c.cur = reinterpret_cast<float *>(smem);
     c.up = c.cur + NSU * S::CUR;
     c.cc = c.up + NSC * S::PC;
@@ -283,7 +310,7 @@ __global__ void __launch_bounds__(Shape<TY>::NT, 2)
     const int ty = b % g.tiles_y;
     const int chunk = b / g.tiles_y;
     c.x0 = tx * TX;
-    c.y0 = ty * TY;
+    c.y0 = ty * S::TY;
     c.z0 = chunk * g.zlen;
     c.T = min(a.nz - c.z0, g.zlen);
     const int T = c.T;
@@ -298,8 +325,8 @@ __global__ void __launch_bounds__(Shape<TY>::NT, 2)
     }
     __syncthreads();
     if (tid == 0 && T > 0) {
-        for (int seq = 0; seq < NSU && seq < nseq; ++seq) issue_u(c, &cur_map, seq);
-        for (int t = 0; t < NSC && t < T; ++t) issue_c(c, &prev_map, &c_map, t);
+        for (int seq = 0; seq < NSU && seq < nseq; ++seq) issue_u<S>(c, &cur_map, seq);
+        for (int t = 0; t < NSC && t < T; ++t) issue_c<S>(c, &prev_map, &c_map, t);
     }
     // receivers of the previous step (u^n, read-only during this launch)
     if (a.traces) {
@@ -318,22 +345,22 @@ __global__ void __launch_bounds__(Shape<TY>::NT, 2)
         w.y[m] = bcast(a.w.y[m]);
         w.z[m] = bcast(a.w.z[m]);
     }
+    const int x = c.x0 + 2 * c.lane;
     float2 exr;
-    {
-        const int x = c.x0 + 2 * c.lane;
-        exr.x = x < a.nx ? __ldg(a.ex + x) : 0.0f;
-        exr.y = x + 1 < a.nx ? __ldg(a.ex + x + 1) : 0.0f;
-    }
+    exr.x = x < a.nx ? __ldg(a.ex + x) : 0.0f;
+    exr.y = x + 1 < a.nx ? __ldg(a.ex + x + 1) : 0.0f;
     float eyr[RY];
+    float *out_row[RY];   // u^{n+1} row pointers at plane 0; null outside the grid
 #pragma unroll
     for (int r = 0; r < RY; ++r) {
         const int y = c.y0 + RY * c.warp + r;
         eyr[r] = y < a.ny ? __ldg(a.ey + y) : 0.0f;
+        out_row[r] = (y < a.ny && x < a.nx) ? a.uprev + (long long)y * a.nxp + x : nullptr;
     }
     const bool xy_damped = c.x0 < a.nbl || c.x0 + TX - 1 > a.nx - 1 - a.nbl || c.y0 < a.nbl ||
-                           c.y0 + TY - 1 > a.ny - 1 - a.nbl;
+                           c.y0 + S::TY - 1 > a.ny - 1 - a.nbl;
 
-    float2 q[QN][RY];
+    float2 q[S::QD][RY];
     // Issue order of u^n sequences is 0, 1, 2, ... with no gaps: the prologue
     // issues 0..NSU-1, the fill below 4 more, then one per finished step.
     int u_hi = min(NSU, nseq);
@@ -344,52 +371,46 @@ __global__ void __launch_bounds__(Shape<TY>::NT, 2)
     for (int seq = 0; seq < 2 * kRadius; ++seq)
         filled = filled && mbar_wait(&c.full_u[seq % NSU], (seq / NSU) & 1, c.abort_flag, a.err);
     if (filled) {
-        read_own<TY, 0>(c, 0, q); read_own<TY, 1>(c, 1, q); read_own<TY, 2>(c, 2, q); read_own<TY, 3>(c, 3, q);
-        read_own<TY, 4>(c, 4, q); read_own<TY, 5>(c, 5, q); read_own<TY, 6>(c, 6, q); read_own<TY, 7>(c, 7, q);
+        read_own<S, 0>(c, 0, q); read_own<S, 1>(c, 1, q); read_own<S, 2>(c, 2, q); read_own<S, 3>(c, 3, q);
+        read_own<S, 4>(c, 4, q); read_own<S, 5>(c, 5, q); read_own<S, 6>(c, 6, q); read_own<S, 7>(c, 7, q);
     }
     __syncthreads();
     // sequences 0..3 are only needed in registers: their slots take NSU..NSU+3
     if (!*c.abort_flag) {
         if (tid == 0)
-            for (int seq = u_hi; seq < NSU + kRadius && seq < nseq; ++seq) issue_u(c, &cur_map, seq);
+            for (int seq = u_hi; seq < NSU + kRadius && seq < nseq; ++seq) issue_u<S>(c, &cur_map, seq);
         u_hi = min(NSU + kRadius, nseq);
-        // end of step t: every thread is done with u^n sequence t+4 (the centre)
-        // and with u^{n-1}/c slot t, so both slots are refilled
-#define MMOD_RELEASE(t)                                                                    \
-    __syncthreads();                                                                       \
-    if (*c.abort_flag) break;                                                              \
-    if (tid == 0) {                                                                        \
-        if ((t) + kRadius + NSU < nseq) issue_u(c, &cur_map, (t) + kRadius + NSU);         \
-        if ((t) + NSC < T) issue_c(c, &prev_map, &c_map, (t) + NSC);                       \
-    }                                                                                      \
-    u_hi = min((t) + kRadius + NSU + 1, nseq);                                             \
-    c_hi = min((t) + NSC + 1, T);
-        if constexpr (ROT) {
-            // queue rotated by unrolling 9 steps: no register moves, larger code
-#define MMOD_STEP(R)                                                   \
-    if (t + (R) < T) {                                                 \
-        step<TY, (R)>(a, c, t + (R), q, w, exr, eyr, xy_damped);       \
-        MMOD_RELEASE(t + (R))                                          \
+        PlaneInfo pi = plane_info(a, c.z0);
+        // Steps run in blocks of U; step J of a block uses queue window
+        // q[J .. J+8], and the block ends by moving its last 8 planes down.
+        // End of step t: every thread is done with u^n sequence t+4 (the
+        // centre) and with u^{n-1}/c slot t, so both slots are refilled.
+#define MMOD_STEP(J)                                                                        \
+    if (t + (J) < T) {                                                                      \
+        const PlaneInfo pi_next = plane_info(a, c.z0 + t + (J) + 1);                        \
+        step<S, (J)>(a, c, t + (J), q, w, exr, eyr, xy_damped, pi, out_row);               \
+        pi = pi_next;                                                                       \
+        __syncthreads();                                                                    \
+        if (*c.abort_flag) break;                                                           \
+        if (tid == 0) {                                                                     \
+            if (t + (J) + kRadius + NSU < nseq) issue_u<S>(c, &cur_map, t + (J) + kRadius + NSU); \
+            if (t + (J) + NSC < T) issue_c<S>(c, &prev_map, &c_map, t + (J) + NSC);        \
+        }                                                                                   \
+        u_hi = min(t + (J) + kRadius + NSU + 1, nseq);                                      \
+        c_hi = min(t + (J) + NSC + 1, T);                                                   \
     }
 #pragma unroll 1
-            for (int t = 0; t < T; t += QN) {
-                MMOD_STEP(0) MMOD_STEP(1) MMOD_STEP(2) MMOD_STEP(3) MMOD_STEP(4)
-                MMOD_STEP(5) MMOD_STEP(6) MMOD_STEP(7) MMOD_STEP(8)
-            }
-#undef MMOD_STEP
-        } else {
-            // queue shifted by one plane after every step: compact code
-#pragma unroll 1
-            for (int t = 0; t < T; ++t) {
-                step<TY, 0>(a, c, t, q, w, exr, eyr, xy_damped);
+        for (int t = 0; t < T; t += U) {
+            MMOD_STEP(0)
+            if constexpr (U > 1) { MMOD_STEP(1) }
+            if constexpr (U > 2) { MMOD_STEP(2) }
+            if constexpr (U > 3) { MMOD_STEP(3) }
 #pragma unroll
-                for (int i = 0; i < QN - 1; ++i)
+            for (int i = 0; i < 2 * kRadius; ++i)
 #pragma unroll
-                    for (int r = 0; r < RY; ++r) q[i][r] = q[i + 1][r];
-                MMOD_RELEASE(t)
-            }
+                for (int r = 0; r < RY; ++r) q[i][r] = q[i + U][r];
         }
-#undef MMOD_RELEASE
+#undef MMOD_STEP
     }
     // After a give-up, wait (bounded) for the copies this CTA still has in
     // flight (the latest sequence of every slot) before its shared memory is
@@ -433,69 +454,100 @@ bool encode(CUtensorMap *map, const float *base, const mmod_config &cfg, int nxp
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Compiled variants.  All use tile height 16 (the tensor maps' box).
 constexpr int kTY = 16;
+using V22_1 = Shape<kTY, 2, 1>;
+using V22_2 = Shape<kTY, 2, 2>;
+using V22_4 = Shape<kTY, 2, 4>;
+using V24_1 = Shape<kTY, 4, 1>;
+using V24_2 = Shape<kTY, 4, 2>;
+
+struct Variant {
+    const char *name;
+    const void *fn;
+    int nt, smem;
+};
+
+#define MMOD_VARIANT(V, desc) {desc, (const void *)step_tma_kernel<V>, V::NT, V::SMEM}
+const Variant kVariants[] = {
+    MMOD_VARIANT(V22_1, "64x16 tile, 2x2 points/thread, z unroll 1"),
+    MMOD_VARIANT(V22_2, "64x16 tile, 2x2 points/thread, z unroll 2"),
+    MMOD_VARIANT(V22_4, "64x16 tile, 2x2 points/thread, z unroll 4"),
+    MMOD_VARIANT(V24_1, "64x16 tile, 2x4 points/thread, z unroll 1"),
+    MMOD_VARIANT(V24_2, "64x16 tile, 2x4 points/thread, z unroll 2"),
+};
+#undef MMOD_VARIANT
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 }  // namespace
 
+int tma_variant_count() { return kNumVariants; }
+
+const char *tma_variant_name(int v) { return (v >= 0 && v < kNumVariants) ? kVariants[v].name : ""; }
+
 bool make_tma_plan(const mmod_config &cfg, int nxp, float *const u[2], const float *c, CUtensorMap cur_map[2],
-                   CUtensorMap prev_map[2], CUtensorMap *c_map, TmaPlan *plan) {
-    using S = Shape<kTY>;
+                   CUtensorMap prev_map[2], CUtensorMap *c_map, TmaPlan plans[]) {
     for (int b = 0; b < 2; ++b) {
-        if (!encode(&cur_map[b], u[b], cfg, nxp, HX, S::HY)) return false;
+        if (!encode(&cur_map[b], u[b], cfg, nxp, HX, kTY + 2 * kRadius)) return false;
         if (!encode(&prev_map[b], u[b], cfg, nxp, TX, kTY)) return false;
     }
     if (!encode(c_map, c, cfg, nxp, TX, kTY)) return false;
-    auto kern = step_tma_kernel<kTY, false>;
-    for (auto k : {step_tma_kernel<kTY, false>, step_tma_kernel<kTY, true>}) {
-        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM) != cudaSuccess) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int tiles_x = (cfg.nx + TX - 1) / TX, tiles_y = (cfg.ny + kTY - 1) / kTY;
+    const long long tiles = (long long)tiles_x * tiles_y;
+    for (int v = 0; v < kNumVariants; ++v) {
+        const Variant &var = kVariants[v];
+        int occ = 0;
+        if (cudaFuncSetAttribute(var.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, var.smem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, var.fn, var.nt, var.smem) != cudaSuccess || occ < 1) {
             cudaGetLastError();
             return false;
         }
-    }
-    int dev = 0, sms = 0, occ = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, S::NT, S::SMEM) != cudaSuccess || occ < 1) {
-        cudaGetLastError();
-        return false;
-    }
-    const int tiles_x = (cfg.nx + TX - 1) / TX, tiles_y = (cfg.ny + kTY - 1) / kTY;
-    const long long tiles = (long long)tiles_x * tiles_y;
-    const long long slots = (long long)sms * occ;
-    // pick the z split that minimises (waves) x (planes per CTA + halo cost)
-    int best_c = 1;
-    double best = 1e300;
-    for (int zc = 1; zc <= cfg.nz; ++zc) {
-        const int zlen = (cfg.nz + zc - 1) / zc;
-        const int used = (cfg.nz + zlen - 1) / zlen;
-        if (used != zc) continue;
-        const long long ctas = tiles * zc;
-        if (ctas > (1LL << 31) - 1) break;
-        const double waves = (double)((ctas + slots - 1) / slots);
-        const double cost = waves * (zlen + 2.0);
-        if (cost < best - 1e-9) {
-            best = cost;
-            best_c = zc;
+        const long long slots = (long long)sms * occ;
+        // the z split that minimises (waves) x (planes per CTA + halo cost)
+        int best_c = 1;
+        double best = 1e300;
+        for (int zc = 1; zc <= cfg.nz; ++zc) {
+            const int zlen = (cfg.nz + zc - 1) / zc;
+            if ((cfg.nz + zlen - 1) / zlen != zc) continue;
+            const long long ctas = tiles * zc;
+            if (ctas > (1LL << 31) - 1) break;
+            const double waves = (double)((ctas + slots - 1) / slots);
+            const double cost = waves * (zlen + 2.0);
+            if (cost < best - 1e-9) {
+                best = cost;
+                best_c = zc;
+            }
         }
+        TmaPlan &p = plans[v];
+        p.variant = v;
+        p.tiles_x = tiles_x;
+        p.tiles_y = tiles_y;
+        p.zchunks = best_c;
+        p.zlen = (cfg.nz + best_c - 1) / best_c;
+        p.grid = (int)(tiles * best_c);
+        p.block = var.nt;
+        p.smem = var.smem;
+        p.occupancy = occ;
     }
-    plan->tiles_x = tiles_x;
-    plan->tiles_y = tiles_y;
-    plan->zchunks = best_c;
-    plan->zlen = (cfg.nz + best_c - 1) / best_c;
-    plan->grid = (int)(tiles * best_c);
-    plan->smem = S::SMEM;
-    plan->rotate = false;
     return true;
 }
 
 cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap *cur_map, const CUtensorMap *prev_map,
-                            const CUtensorMap *c_map, const TmaPlan &plan, bool rotate, cudaStream_t s) {
-    using S = Shape<kTY>;
+                            const CUtensorMap *c_map, const TmaPlan &plan, cudaStream_t s) {
     const Geom g{plan.tiles_x, plan.tiles_y, plan.zchunks, plan.zlen};
-    if (plan.rotate || rotate)
-        step_tma_kernel<kTY, true><<<plan.grid, S::NT, plan.smem, s>>>(a, *cur_map, *prev_map, *c_map, g);
-    else
-        step_tma_kernel<kTY, false><<<plan.grid, S::NT, plan.smem, s>>>(a, *cur_map, *prev_map, *c_map, g);
+#define MMOD_LAUNCH(V) step_tma_kernel<V><<<plan.grid, plan.block, plan.smem, s>>>(a, *cur_map, *prev_map, *c_map, g)
+    switch (plan.variant) {
+        case 0: MMOD_LAUNCH(V22_1); break;
+        case 1: MMOD_LAUNCH(V22_2); break;
+        case 2: MMOD_LAUNCH(V22_4); break;
+        case 3: MMOD_LAUNCH(V24_1); break;
+        case 4: MMOD_LAUNCH(V24_2); break;
+        default: return cudaErrorInvalidValue;
+    }
+#undef MMOD_LAUNCH
     return cudaGetLastError();
 }
 

@@ -2,7 +2,9 @@
 //
 // Sec. 3 Laplacian in the paper's pair-difference form, per axis and offset m:
 //     w_am * ((p(+m) + p(-m)) - 2p),   w_am = c_m / h_a^2,
-// accumulated in the fixed order x1..x4, y1..y4, z1..z4.  In FP32 this form
+// summed per axis in the order m = 1..4 (the first term is a product), then
+// lap = (l_x + l_y) + l_z.  Three independent chains instead of one keep the
+// FMA pipes busy with few warps.  In FP32 this form
 // keeps the small Laplacian accurate (the differences are formed before the
 // weights are applied); folding the centre weight -2 sum_m w_am into one term
 // loses about a decimal digit over 1000 steps.
@@ -30,8 +32,16 @@ struct Weights {
     float x[kRadius], y[kRadius], z[kRadius];   // c_m / h_a^2, m = 1..4
 };
 
+__device__ __forceinline__ float pair_first(float w, float a, float b, float two_p) {
+    return __fmul_rn(w, __fsub_rn(__fadd_rn(a, b), two_p));
+}
+
 __device__ __forceinline__ float pair_acc(float acc, float w, float a, float b, float two_p) {
     return __fmaf_rn(w, __fsub_rn(__fadd_rn(a, b), two_p), acc);
+}
+
+__device__ __forceinline__ float lap_sum(float lx, float ly, float lz) {
+    return __fadd_rn(__fadd_rn(lx, ly), lz);
 }
 
 // Undamped numerator 2p - pp + c * lap.
