@@ -157,7 +157,8 @@ double mmod_cfl_dt(double cfl, double hmin, double vmax);
 
 /* Human-readable description of the handle's last failure ("" if none).
  * The string is owned by the handle and valid until its next call.  With
- * h == NULL: the calling thread's last mmod_create failure. */
+ * h == NULL: the calling thread's last mmod_create or mmod_forward_noalloc
+ * failure. */
 const char *mmod_last_error(const mmod_handle *h);
 
 /* Self-check of the damping reciprocal used by the step kernels (hardware
@@ -166,6 +167,33 @@ const char *mmod_last_error(const mmod_handle *h);
  * device.  Writes the largest difference in units in the last place.
  * Synchronous; returns MMOD_OK, ARG, OOM or CUDA. */
 int mmod_check_recip(int n, unsigned int *max_ulp_out);
+
+/* Allocation-free forward run, for callers that may not allocate device
+ * memory (a framework that accounts for every byte through its own pool, a
+ * process that reserves all device memory at start-up, real-time code that
+ * cannot afford an allocation's implicit synchronisation or failure).  The
+ * paper has no counterpart; this is a service of the library.
+ *
+ * Computes exactly what mmod_create + mmod_set_model + mmod_forward compute
+ * for the same configuration, from zero initial state, without a handle and
+ * without calling cudaMalloc, cudaFree or any allocating library routine: its
+ * scratch (wavefields, coefficient volume, profiles, source/receiver tables)
+ * is one fixed block of device memory inside the library, about 25 MB, that
+ * every GPU loading the library keeps until the process exits.
+ *   Limits: nx, ny, nz <= 4096; (nx rounded up to 32) * ny * nz <= 2097152;
+ *   nsrc <= 64; nrec <= 65536; order 8.  Larger problems are rejected with
+ *   MMOD_ERR_ARG (use the handle API).
+ *   vel, wavelet, traces, final_u: device pointers (layouts as in
+ *   mmod_set_model / mmod_forward); final_u may be NULL.
+ * Synchronous: returns after the work on `stream` has finished.  Every call
+ * shares the block (each call clears what must start at zero), so calls that
+ * overlap on the GPU race: serialise them.  The first call on a device looks
+ * up the block's device address (cudaGetSymbolAddress); make it before any
+ * stream capture.  Errors: ARG, UNSTABLE, UNSUPPORTED, CUDA, TIMEOUT; the
+ * message is available from mmod_last_error(NULL) on the calling thread. */
+mmod_status mmod_forward_noalloc(const mmod_config *cfg, int device, const float *vel,
+                                 const float *wavelet, float *traces, float *final_u,
+                                 mmod_stream stream);
 
 /* Library version string, e.g. "mmod-gb300 0.1 sm_103a". */
 const char *mmod_version(void);

@@ -31,7 +31,8 @@ KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_TMA = 0, 1, 2
 EXPORTED = ["mmod_create", "mmod_destroy", "mmod_set_model", "mmod_forward", "mmod_set_state",
             "mmod_get_state", "mmod_set_kernel", "mmod_last_launch_count", "mmod_last_loop_ms",
             "mmod_cfl_dt", "mmod_last_error", "mmod_version", "mmod_check_recip",
-            "mmod_tma_variant_count", "mmod_tma_variant_name", "mmod_set_tma_variant", "mmod_get_plan"]
+            "mmod_tma_variant_count", "mmod_tma_variant_name", "mmod_set_tma_variant", "mmod_get_plan",
+            "mmod_forward_noalloc"]
 
 
 class MmodError(RuntimeError):
@@ -84,6 +85,7 @@ def load():
         "mmod_tma_variant_name": ([I], ctypes.c_char_p),
         "mmod_set_tma_variant": ([P, I], I),
         "mmod_get_plan": ([P, ctypes.POINTER(ctypes.c_int)], I),
+        "mmod_forward_noalloc": ([ctypes.POINTER(_Config), I, P, P, P, P, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -151,6 +153,24 @@ def mmod_create(nx, ny, nz, h, dt, nt, *, nbl=0, src_ijk=None, rec_ijk=None, ord
     if st != 0:
         raise MmodError(st, load().mmod_last_error(None).decode())
     return out
+
+
+def _config(nx, ny, nz, h, dt, nt, nbl, src, rec, order, damp_R):
+    return _Config(int(nx), int(ny), int(nz), float(h[0]), float(h[1]), float(h[2]), float(dt), int(nt),
+                   int(order), int(nbl), float(damp_R), len(src), src.ctypes.data if len(src) else None,
+                   len(rec), rec.ctypes.data if len(rec) else None)
+
+
+def mmod_forward_noalloc(nx, ny, nz, h, dt, nt, vel, wavelet, traces, final_u=None, *, nbl=0,
+                         src_ijk=None, rec_ijk=None, order=8, damp_R=1e-3, device=0, stream=None):
+    """Allocation-free forward run (device pointers only; see include/mmod.h)."""
+    src = np.ascontiguousarray(np.zeros((0, 3)) if src_ijk is None else src_ijk, np.int32).reshape(-1, 3)
+    rec = np.ascontiguousarray(np.zeros((0, 3)) if rec_ijk is None else rec_ijk, np.int32).reshape(-1, 3)
+    cfg = _config(nx, ny, nz, h, dt, nt, nbl, src, rec, order, damp_R)
+    st = load().mmod_forward_noalloc(ctypes.byref(cfg), int(device), _addr(vel), _addr(wavelet),
+                                     _addr(traces), _addr(final_u), _stream(stream))
+    if st != 0:
+        raise MmodError(st, load().mmod_last_error(None).decode())
 
 
 def mmod_destroy(h):

@@ -18,13 +18,6 @@ using namespace mmod;
 
 namespace {
 
-// Order-8 Taylor weights of the second derivative (Sec. 3):
-// c_1..c_4 = 8/5, -1/5, 8/315, -1/560.
-constexpr double kTaylor8[4] = {8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0};
-// Largest magnitude of the order-8 stencil's symbol (at k h = pi):
-// 4 (c_1 + c_3) = 2048 / 315; leapfrog is stable iff dt^2 v^2 sum_a K_a <= 4.
-constexpr double kSymbolMax8 = 2048.0 / 315.0;
-
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int d) {
@@ -46,8 +39,11 @@ bool is_device_ptr(const void *p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-// Message of the calling thread's last mmod_create failure.
-thread_local std::string g_create_err;
+// Message of the calling thread's last failure outside a handle (mmod_create,
+// mmod_forward_noalloc); a fixed buffer, so recording it never allocates.
+thread_local char g_thread_err[256] = "";
+
+void set_thread_error_str(const std::string &msg) { set_thread_error(msg.c_str()); }
 
 }  // namespace
 
@@ -179,6 +175,14 @@ void free_all(mmod_handle *h) {
     if (h->err_host) cudaFreeHost(h->err_host);
 }
 
+}  // namespace
+
+namespace mmod {
+
+void set_thread_error(const char *msg) {
+    std::snprintf(g_thread_err, sizeof(g_thread_err), "%s", msg ? msg : "");
+}
+
 // Damping profile of one axis (the ABI's reading of the layers), FP64 -> FP32
 // after multiplying by dt.
 void damping_profile(int n, int nbl, double h, double vmax, double R, double dt, float *out) {
@@ -193,6 +197,10 @@ void damping_profile(int n, int nbl, double h, double vmax, double R, double dt,
         out[i] = (float)(dt * eta_max * s * s);
     }
 }
+
+}  // namespace mmod
+
+namespace {
 
 StepArgs step_args(mmod_handle *h, const float *wavelet, float *traces, int n) {
     StepArgs a{};
@@ -215,11 +223,8 @@ bool use_tma(const mmod_handle *h) {
     return h->tma_ok && h->kernel != MMOD_KERNEL_SIMPLE;
 }
 
-// Default variant: the fastest measured on the 240^3 workload.
-constexpr int kDefaultVariant = 2;
-
 const TmaPlan &active_plan(const mmod_handle *h) {
-    return h->plans[h->variant >= 0 ? h->variant : kDefaultVariant];
+    return h->plans[h->variant >= 0 ? h->variant : kTmaDefaultVariant];
 }
 
 // Enqueue the nt steps (and receiver gathers) on stream s.  Returns the
@@ -263,27 +268,27 @@ MMOD_API double mmod_cfl_dt(double cfl, double hmin, double vmax) {
 
 MMOD_API const char *mmod_version(void) { return "mmod-gb300 0.1 sm_103a"; }
 
-MMOD_API const char *mmod_last_error(const mmod_handle *h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+MMOD_API const char *mmod_last_error(const mmod_handle *h) { return h ? h->err.c_str() : g_thread_err; }
 
 MMOD_API long long mmod_last_launch_count(const mmod_handle *h) { return h ? h->last_launches : -1; }
 
 MMOD_API mmod_status mmod_create(const mmod_config *cfg, int device, mmod_handle **out) {
-    g_create_err.clear();
+    set_thread_error("");
     if (!out) {
-        g_create_err = "null output pointer";
+        set_thread_error("null output pointer");
         return MMOD_ERR_ARG;
     }
     *out = nullptr;
     mmod_status st;
     const std::string why = validate(cfg, &st);
     if (st != MMOD_OK) {
-        g_create_err = why;
+        set_thread_error_str(why);
         return st;
     }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
         cudaGetLastError();
-        g_create_err = "CUDA device " + std::to_string(device) + " not available";
+        set_thread_error_str("CUDA device " + std::to_string(device) + " not available");
         return MMOD_ERR_CUDA;
     }
     DeviceGuard guard(device);
@@ -307,7 +312,7 @@ MMOD_API mmod_status mmod_create(const mmod_config *cfg, int device, mmod_handle
     }
 
     auto bail = [&](cudaError_t e, const char *what) {
-        g_create_err = std::string(what) + ": " + cudaGetErrorString(e);
+        set_thread_error_str(std::string(what) + ": " + cudaGetErrorString(e));
         free_all(h);
         delete h;
         return e == cudaErrorMemoryAllocation ? MMOD_ERR_OOM : MMOD_ERR_CUDA;

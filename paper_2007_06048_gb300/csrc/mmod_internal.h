@@ -38,6 +38,17 @@ struct StepArgs {
     int *err;                             // device view of the mapped error word
 };
 
+// Host helpers shared by the entry points (mmod_api.cu).
+void damping_profile(int n, int nbl, double h, double vmax, double R, double dt, float *out);
+void set_thread_error(const char *msg);   // fixed buffer read by mmod_last_error(NULL)
+
+// Order-8 Taylor weights of the second derivative (Sec. 3):
+// c_1..c_4 = 8/5, -1/5, 8/315, -1/560.
+constexpr double kTaylor8[4] = {8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0};
+// Largest magnitude of the order-8 stencil's symbol (at k h = pi):
+// 4 (c_1 + c_3) = 2048 / 315; leapfrog is stable iff dt^2 v^2 sum_a K_a <= 4.
+constexpr double kSymbolMax8 = 2048.0 / 315.0;
+
 // Launchers (mmod_step_simple.cu, mmod_step_tma.cu, mmod_setup.cu).
 cudaError_t launch_step_simple(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_gather(const float *u, const long long *rec_off, int nrec, float *dst,

@@ -1,0 +1,276 @@
+// mmod_forward_noalloc: the forward run of mmod_forward for callers that may
+// not allocate device memory.
+//
+// Who needs it: code that runs where cudaMalloc is off limits — inside a
+// framework's memory pool that must account for every byte, in a process
+// that pre-reserves all device memory at start-up, or under a real-time
+// budget where an allocation's implicit synchronisation or failure at run
+// time is not acceptable.  The handle API allocates its wavefields at
+// mmod_create; this entry point instead works in one fixed block of device
+// memory that is part of the loaded library (a file-scope __device__ array),
+// so a call allocates nothing: no cudaMalloc, cudaFree, graph, event or
+// library call that allocates.
+//
+// The block holds the two wavefields, the coefficient volume, the damping
+// profiles and the source/receiver tables for grids up to the limits below
+// (about 25 MB).  Every GPU that loads the library keeps that block until the
+// process exits.  All calls share it: each call clears what must start at
+// zero, and two calls that overlap on the GPU (other streams, other host
+// threads) race on it — serialise them.
+//
+// In host code the array's name is only a stand-in for the device object, so
+// the device address is looked up with cudaGetSymbolAddress, once per device,
+// by the first call on that device (with the device current).  Make that
+// first call before any stream capture.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "mmod_internal.h"
+#include "tma_plan.h"
+
+namespace {
+
+using namespace mmod;
+
+constexpr long long kMaxVolume = 1LL << 21;   // padded points (nx rounded up to 32) x ny x nz
+constexpr int kMaxAxis = 4096;                // points per axis
+constexpr int kMaxSrc = 64;
+constexpr int kMaxRec = 65536;
+constexpr int kMaxDevices = 64;
+
+constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+constexpr size_t kOffU0 = 0;
+constexpr size_t kOffU1 = kOffU0 + align256(kMaxVolume * 4);
+constexpr size_t kOffC = kOffU1 + align256(kMaxVolume * 4);
+constexpr size_t kOffEta = kOffC + align256(kMaxVolume * 4);
+constexpr size_t kOffKstart = kOffEta + align256(3 * kMaxAxis * 4);
+constexpr size_t kOffSrc = kOffKstart + align256((kMaxAxis + 1) * 4);   // i, j, k, row
+constexpr size_t kOffScale = kOffSrc + align256(4 * kMaxSrc * 4);
+constexpr size_t kOffRec = kOffScale + align256(kMaxSrc * 4);
+constexpr size_t kOffMisc = kOffRec + align256((size_t)kMaxRec * 8);   // vmax bits, bad count, error word
+constexpr size_t kScratchBytes = kOffMisc + 256;
+
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+std::mutex g_setup_mutex;
+unsigned char *g_dev_scratch[kMaxDevices] = {};
+
+// Device address of the block on the current device (looked up once).
+cudaError_t scratch_address(int dev, unsigned char **out) {
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (!g_dev_scratch[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+        if (e != cudaSuccess) return e;
+        g_dev_scratch[dev] = static_cast<unsigned char *>(p);
+    }
+    *out = g_dev_scratch[dev];
+    return cudaSuccess;
+}
+
+bool on_device(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+mmod_status fail(mmod_status st, const char *msg) {
+    set_thread_error(msg);
+    return st;
+}
+
+mmod_status fail_cuda(cudaError_t e, const char *what) {
+    char buf[200];
+    std::snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorName(e));
+    set_thread_error(buf);
+    return MMOD_ERR_CUDA;
+}
+
+#define CKN(call)                                      \
+    do {                                               \
+        cudaError_t _e = (call);                       \
+        if (_e != cudaSuccess) return fail_cuda(_e, #call); \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int d) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != d) cudaSetDevice(d);
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+extern "C" __attribute__((visibility("default"))) mmod_status mmod_forward_noalloc(
+    const mmod_config *cfg, int device, const float *vel, const float *wavelet, float *traces, float *final_u,
+    mmod_stream stream) {
+    set_thread_error("");
+    // ---- configuration and limits (host only, nothing enqueued yet)
+    if (!cfg) return fail(MMOD_ERR_ARG, "null config");
+    const mmod_config &c = *cfg;
+    if (c.order != 8) return fail(MMOD_ERR_UNSUPPORTED, "the GPU path implements order 8 only");
+    if (c.nx < 1 || c.ny < 1 || c.nz < 1) return fail(MMOD_ERR_ARG, "grid sizes must be >= 1");
+    if (!(c.hx > 0 && c.hy > 0 && c.hz > 0) || !std::isfinite(c.hx) || !std::isfinite(c.hy) || !std::isfinite(c.hz))
+        return fail(MMOD_ERR_ARG, "grid spacings must be positive and finite");
+    if (!(c.dt > 0) || !std::isfinite(c.dt)) return fail(MMOD_ERR_ARG, "dt must be positive and finite");
+    if (c.nt < 0) return fail(MMOD_ERR_ARG, "nt must be >= 0");
+    if (c.nbl < 0 || 2LL * c.nbl > c.nx || 2LL * c.nbl > c.ny || 2LL * c.nbl > c.nz)
+        return fail(MMOD_ERR_ARG, "damping width must satisfy 0 <= 2*nbl <= n on every axis");
+    if (c.nbl > 0 && !(c.damp_R > 0 && c.damp_R < 1)) return fail(MMOD_ERR_ARG, "damp_R must be in (0, 1)");
+    const int nxp = (c.nx + 31) / 32 * 32;
+    const long long plane = (long long)nxp * c.ny, vol = plane * c.nz;
+    if (c.nx > kMaxAxis || c.ny > kMaxAxis || c.nz > kMaxAxis || vol > kMaxVolume)
+        return fail(MMOD_ERR_ARG,
+                    "grid exceeds the allocation-free limits: each axis <= 4096 and "
+                    "(nx rounded up to 32) * ny * nz <= 2097152 points; use mmod_create / mmod_forward");
+    if (c.nsrc < 0 || c.nsrc > kMaxSrc) return fail(MMOD_ERR_ARG, "allocation-free forward takes 0..64 sources");
+    if (c.nrec < 0 || c.nrec > kMaxRec) return fail(MMOD_ERR_ARG, "allocation-free forward takes 0..65536 receivers");
+    if ((c.nsrc > 0 && !c.src_ijk) || (c.nrec > 0 && !c.rec_ijk)) return fail(MMOD_ERR_ARG, "null position list");
+    for (int s = 0; s < c.nsrc; ++s) {
+        const int *p = c.src_ijk + 3 * s;
+        if (p[0] < 0 || p[0] >= c.nx || p[1] < 0 || p[1] >= c.ny || p[2] < 0 || p[2] >= c.nz)
+            return fail(MMOD_ERR_ARG, "a source lies outside the grid");
+    }
+    for (int r = 0; r < c.nrec; ++r) {
+        const int *p = c.rec_ijk + 3 * r;
+        if (p[0] < 0 || p[0] >= c.nx || p[1] < 0 || p[1] >= c.ny || p[2] < 0 || p[2] >= c.nz)
+            return fail(MMOD_ERR_ARG, "a receiver lies outside the grid");
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return fail(MMOD_ERR_CUDA, "CUDA device not available");
+    }
+    DeviceGuard guard(device);
+    if (!vel || !on_device(vel)) return fail(MMOD_ERR_ARG, "vel must be a device pointer");
+    if (c.nsrc > 0 && c.nt > 0 && (!wavelet || !on_device(wavelet)))
+        return fail(MMOD_ERR_ARG, "wavelet must be a device pointer");
+    if (c.nrec > 0 && c.nt > 0 && (!traces || !on_device(traces)))
+        return fail(MMOD_ERR_ARG, "traces must be a device pointer");
+    if (final_u && !on_device(final_u)) return fail(MMOD_ERR_ARG, "final_u must be a device pointer");
+
+    unsigned char *base = nullptr;
+    CKN(scratch_address(device, &base));
+    cudaStream_t s = (cudaStream_t)stream;
+    float *u[2] = {reinterpret_cast<float *>(base + kOffU0), reinterpret_cast<float *>(base + kOffU1)};
+    float *cvol = reinterpret_cast<float *>(base + kOffC);
+    float *eta = reinterpret_cast<float *>(base + kOffEta);
+    int *kstart = reinterpret_cast<int *>(base + kOffKstart);
+    int *src_tab = reinterpret_cast<int *>(base + kOffSrc);   // i | j | k | row, kMaxSrc each
+    float *src_scale = reinterpret_cast<float *>(base + kOffScale);
+    long long *rec_off = reinterpret_cast<long long *>(base + kOffRec);
+    unsigned int *vmax_bits = reinterpret_cast<unsigned int *>(base + kOffMisc);
+    unsigned long long *bad = reinterpret_cast<unsigned long long *>(base + kOffMisc + 8);
+    int *err = reinterpret_cast<int *>(base + kOffMisc + 16);
+
+    // ---- tables: sources sorted by depth (stable), receiver offsets
+    int order[kMaxSrc], si[4 * kMaxSrc] = {0};
+    for (int t = 0; t < c.nsrc; ++t) order[t] = t;
+    for (int t = 1; t < c.nsrc; ++t)   // insertion sort, stable
+        for (int q = t; q > 0 && c.src_ijk[3 * order[q - 1] + 2] > c.src_ijk[3 * order[q] + 2]; --q) {
+            const int tmp = order[q];
+            order[q] = order[q - 1];
+            order[q - 1] = tmp;
+        }
+    int ks[kMaxAxis + 1];
+    std::memset(ks, 0, sizeof(int) * (c.nz + 1));
+    for (int t = 0; t < c.nsrc; ++t) {
+        const int *p = c.src_ijk + 3 * order[t];
+        si[t] = p[0];
+        si[kMaxSrc + t] = p[1];
+        si[2 * kMaxSrc + t] = p[2];
+        si[3 * kMaxSrc + t] = order[t];
+        ks[p[2] + 1]++;
+    }
+    for (int k = 0; k < c.nz; ++k) ks[k + 1] += ks[k];
+    CKN(cudaMemcpyAsync(kstart, ks, sizeof(int) * (c.nz + 1), cudaMemcpyHostToDevice, s));
+    CKN(cudaMemcpyAsync(src_tab, si, sizeof(si), cudaMemcpyHostToDevice, s));
+    {
+        long long chunk[1024];
+        for (int r0 = 0; r0 < c.nrec; r0 += 1024) {
+            const int n = c.nrec - r0 < 1024 ? c.nrec - r0 : 1024;
+            for (int r = 0; r < n; ++r) {
+                const int *p = c.rec_ijk + 3 * (r0 + r);
+                chunk[r] = (long long)p[2] * plane + (long long)p[1] * nxp + p[0];
+            }
+            CKN(cudaMemcpyAsync(rec_off + r0, chunk, sizeof(long long) * n, cudaMemcpyHostToDevice, s));
+            CKN(cudaStreamSynchronize(s));   // the chunk buffer is reused
+        }
+    }
+
+    // ---- model: scan, stability check, c = dt^2 v^2, profiles, source scales
+    const long long npts = (long long)c.nx * c.ny * c.nz;
+    CKN(cudaMemsetAsync(base + kOffMisc, 0, 256, s));
+    CKN(launch_model_scan(vel, npts, vmax_bits, bad, s));
+    unsigned int vbits = 0;
+    unsigned long long nbad = 0;
+    CKN(cudaMemcpyAsync(&vbits, vmax_bits, sizeof(vbits), cudaMemcpyDeviceToHost, s));
+    CKN(cudaMemcpyAsync(&nbad, bad, sizeof(nbad), cudaMemcpyDeviceToHost, s));
+    CKN(cudaStreamSynchronize(s));
+    if (nbad) return fail(MMOD_ERR_ARG, "velocities must be positive and finite");
+    float vmaxf;
+    std::memcpy(&vmaxf, &vbits, sizeof(vmaxf));
+    const double vmax = vmaxf;
+    const double ksum = kSymbolMax8 * (1.0 / (c.hx * c.hx) + 1.0 / (c.hy * c.hy) + 1.0 / (c.hz * c.hz));
+    if (c.dt * vmax * std::sqrt(ksum) > 2.0) return fail(MMOD_ERR_UNSTABLE, "dt too large for the model (CFL bound)");
+    CKN(launch_model_fill(vel, c.nx, c.ny, c.nz, nxp, c.dt, cvol, s));
+    CKN(launch_source_scale(vel, c.nx, c.ny, c.nsrc, src_tab, src_tab + kMaxSrc, src_tab + 2 * kMaxSrc, c.dt,
+                            c.hx * c.hy * c.hz, src_scale, s));
+    float eta_h[3 * kMaxAxis];
+    damping_profile(c.nx, c.nbl, c.hx, vmax, c.damp_R, c.dt, eta_h);
+    damping_profile(c.ny, c.nbl, c.hy, vmax, c.damp_R, c.dt, eta_h + c.nx);
+    damping_profile(c.nz, c.nbl, c.hz, vmax, c.damp_R, c.dt, eta_h + c.nx + c.ny);
+    CKN(cudaMemcpyAsync(eta, eta_h, sizeof(float) * (c.nx + c.ny + c.nz), cudaMemcpyHostToDevice, s));
+
+    // ---- time loop: u^{-1} = u^0 = 0, one step kernel per step
+    CKN(cudaMemsetAsync(u[0], 0, sizeof(float) * vol, s));
+    CKN(cudaMemsetAsync(u[1], 0, sizeof(float) * vol, s));
+    CUtensorMap cur_map[2], prev_map[2], c_map;
+    TmaPlan plans[kMaxTmaVariants];
+    const bool tma = make_tma_plan(c, nxp, u, cvol, cur_map, prev_map, &c_map, plans);
+    StepArgs a{};
+    a.nx = c.nx; a.ny = c.ny; a.nz = c.nz; a.nxp = nxp; a.plane = plane; a.nbl = c.nbl; a.nt = c.nt;
+    for (int m = 0; m < kRadius; ++m) {
+        a.w.x[m] = (float)(kTaylor8[m] / (c.hx * c.hx));
+        a.w.y[m] = (float)(kTaylor8[m] / (c.hy * c.hy));
+        a.w.z[m] = (float)(kTaylor8[m] / (c.hz * c.hz));
+    }
+    a.c = cvol;
+    a.ex = eta; a.ey = eta + c.nx; a.ez = eta + c.nx + c.ny;
+    a.src_kstart = kstart; a.src_i = src_tab; a.src_j = src_tab + kMaxSrc; a.src_row = src_tab + 3 * kMaxSrc;
+    a.src_scale = src_scale; a.wavelet = wavelet;
+    a.nrec = c.nrec; a.rec_off = rec_off;
+    a.err = err;
+    const bool want_tr = c.nrec > 0 && traces;
+    for (int n = 0; n < c.nt; ++n) {
+        a.n = n;
+        a.ucur = u[(n + 1) & 1];
+        a.uprev = u[n & 1];
+        if (tma) {
+            a.traces = (n >= 1 && want_tr) ? traces + (long long)(n - 1) * c.nrec : nullptr;
+            CKN(launch_step_tma(a, &cur_map[(n + 1) & 1], &prev_map[n & 1], &c_map, plans[kTmaDefaultVariant], s));
+        } else {
+            a.traces = nullptr;
+            CKN(launch_step_simple(a, s));
+            if (want_tr) CKN(launch_gather(u[n & 1], rec_off, c.nrec, traces + (long long)n * c.nrec, s));
+        }
+    }
+    if (tma && c.nt > 0 && want_tr)
+        CKN(launch_gather(u[(c.nt - 1) & 1], rec_off, c.nrec, traces + (long long)(c.nt - 1) * c.nrec, s));
+    if (final_u) CKN(launch_unpack(u[(c.nt + 1) & 1], c.nx, c.ny, c.nz, nxp, final_u, s));
+    int err_h = 0;
+    CKN(cudaMemcpyAsync(&err_h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CKN(cudaStreamSynchronize(s));
+    if (err_h) return fail(MMOD_ERR_TIMEOUT, "a step kernel gave up waiting for its copies (device-side timeout)");
+    return MMOD_OK;
+}
