@@ -142,6 +142,21 @@ def oracle_sample(p, seconds_target=20.0, max_steps=None):
                       f"{dt:.1f} s"}, dt, steps
 
 
+def weak_throughput(world: int, npts: int, nt: int, steps: int, ms: float) -> float:
+    """Whole-job Gpoint-updates/s: every rank advanced its own replica."""
+    return world * npts * nt * steps / (ms * 1e-3) / 1e9
+
+
+def reduce_max(value: float, dist, device) -> float:
+    """Maximum of a per-rank scalar over all ranks (identity without a group)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -240,12 +255,8 @@ def run_mmod(args):
         barrier()
     launches = prop.launches * args.steps
     ms = e0.elapsed_time(e1)
-    ms_max = ms
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = ws * npts * p.nt * args.steps / (ms_max * 1e-3) / 1e9
+    ms_max = reduce_max(ms, dist, dev)
+    value = weak_throughput(ws, npts, p.nt, args.steps, ms_max)
 
     # roofline of the dominant kernel: the step kernel, one launch per time step
     peak, peak_kind = load_peaks()
@@ -272,12 +283,8 @@ def run_mmod(args):
         prop.set_model(vel_h, stream)
         prop.forward(wav_h, tr_h, None, stream)
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": ws * npts * p.nt * e2e_steps / e2e_s / 1e9, "unit": UNIT,
+    e2e_s = reduce_max(time.perf_counter() - t0, dist, dev)
+    e2e = {"value": weak_throughput(ws, npts, p.nt, e2e_steps, e2e_s * 1e3), "unit": UNIT,
            "h2d_bytes_per_step": int(vel_h.numel() * 4 + wav_h.numel() * 4),
            "d2h_bytes_per_step": int(tr_h.numel() * 4),
            "api": "mmod_set_model + mmod_forward with pinned host buffers, wall clock"}
