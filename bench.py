@@ -227,6 +227,8 @@ def run_mmod(args):
         prop.set_kernel({"simple": M.KERNEL_SIMPLE, "tma": M.KERNEL_TMA}[args.kernel])
     if args.variant >= 0:
         prop.set_variant(args.variant)
+    if args.pdl is not None:
+        prop.set_option(M.OPT_PDL, args.pdl)
     stream = torch.cuda.current_stream(dev)
     vel_d = torch.from_numpy(p.vel).to(dev)
     wav_d = torch.from_numpy(np.ascontiguousarray(p.wavelet)).to(dev)
@@ -332,6 +334,7 @@ def main():
     ap.add_argument("--nt", type=int, default=None, help="override the workload's step count")
     ap.add_argument("--kernel", choices=["auto", "simple", "tma"], default="auto")
     ap.add_argument("--variant", type=int, default=-1, help="TMA kernel variant (-1 = automatic)")
+    ap.add_argument("--pdl", type=int, choices=[0, 1], default=None, help="override MMOD_OPT_PDL")
     ap.add_argument("--ref-seconds", type=float, default=20.0,
                     help="CPU seconds per oracle sample (cpu_baseline / reference arm)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

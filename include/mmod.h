@@ -136,6 +136,15 @@ int mmod_tma_variant_count(void);
 const char *mmod_tma_variant_name(int v);
 mmod_status mmod_set_tma_variant(mmod_handle *h, int v);
 
+/* Tuning options of the TMA kernel, 0 = off, 1 = on (results are the same
+ * bits either way):
+ *   MMOD_OPT_PDL  launch each step as a programmatic dependent of the
+ *                 previous one, so its set-up overlaps the previous step's
+ *                 tail (default on).
+ * Errors: ARG (unknown option or value). */
+enum { MMOD_OPT_PDL = 2 };
+mmod_status mmod_set_option(mmod_handle *h, int option, int value);
+
 /* Launch plan of the active TMA variant: writes 8 ints {variant, tiles_x,
  * tiles_y, z_chunks, planes_per_chunk, grid, block, resident_ctas_per_sm}.
  * Errors: ARG, UNSUPPORTED (no TMA plan). */

@@ -26,13 +26,14 @@ __all__ = ["MmodError", "build", "load", "mmod_create", "mmod_destroy", "mmod_se
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_UNSTABLE", -3: "ERR_OOM", -4: "ERR_CUDA",
           -5: "ERR_TIMEOUT", -6: "ERR_STATE", -7: "ERR_UNSUPPORTED"}
 KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_TMA = 0, 1, 2
+OPT_PDL = 2
 
 # Every symbol include/mmod.h declares (checked against the header by the tests).
 EXPORTED = ["mmod_create", "mmod_destroy", "mmod_set_model", "mmod_forward", "mmod_set_state",
             "mmod_get_state", "mmod_set_kernel", "mmod_last_launch_count", "mmod_last_loop_ms",
             "mmod_cfl_dt", "mmod_last_error", "mmod_version", "mmod_check_recip",
             "mmod_tma_variant_count", "mmod_tma_variant_name", "mmod_set_tma_variant", "mmod_get_plan",
-            "mmod_forward_noalloc"]
+            "mmod_forward_noalloc", "mmod_set_option"]
 
 
 class MmodError(RuntimeError):
@@ -86,6 +87,7 @@ def load():
         "mmod_set_tma_variant": ([P, I], I),
         "mmod_get_plan": ([P, ctypes.POINTER(ctypes.c_int)], I),
         "mmod_forward_noalloc": ([ctypes.POINTER(_Config), I, P, P, P, P, P], I),
+        "mmod_set_option": ([P, I, I], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -216,6 +218,10 @@ def mmod_set_tma_variant(h, v: int):
     _check(h, load().mmod_set_tma_variant(h, int(v)))
 
 
+def mmod_set_option(h, option: int, value: int):
+    _check(h, load().mmod_set_option(h, int(option), int(value)))
+
+
 def mmod_get_plan(h) -> dict:
     out = (ctypes.c_int * 8)()
     _check(h, load().mmod_get_plan(h, out))
@@ -265,6 +271,9 @@ class Propagator:
 
     def plan(self) -> dict:
         return mmod_get_plan(self.handle)
+
+    def set_option(self, option: int, value: int):
+        mmod_set_option(self.handle, option, value)
 
     def forward(self, wavelet, traces, final_u=None, stream=None):
         mmod_forward(self.handle, wavelet, traces, final_u, stream)

@@ -39,6 +39,9 @@ bool is_device_ptr(const void *p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Defaults of the tuning options (see mmod_set_option).
+constexpr int kDefaultPdl = 1;   // measured +1% on 240^3
+
 // Message of the calling thread's last failure outside a handle (mmod_create,
 // mmod_forward_noalloc); a fixed buffer, so recording it never allocates.
 thread_local char g_thread_err[256] = "";
@@ -82,6 +85,8 @@ struct mmod_handle {
 
     TmaPlan plans[kMaxTmaVariants]{};
     int variant = -1;                   // -1: automatic choice
+    int pdl = kDefaultPdl;              // MMOD_OPT_PDL
+    int g_opts = -1;                    // options the cached graph was captured with
     bool tma_ok = false;
     CUtensorMap cur_map[2], prev_map[2], c_map;
 
@@ -216,6 +221,7 @@ StepArgs step_args(mmod_handle *h, const float *wavelet, float *traces, int n) {
     a.nrec = h->cfg.nrec; a.rec_off = h->rec_off;
     a.traces = (n >= 1 && traces) ? traces + (long long)(n - 1) * h->cfg.nrec : nullptr;
     a.err = h->err_dev;
+    a.pdl = h->pdl;
     return a;
 }
 
@@ -414,6 +420,15 @@ MMOD_API mmod_status mmod_set_tma_variant(mmod_handle *h, int v) {
     return MMOD_OK;
 }
 
+MMOD_API mmod_status mmod_set_option(mmod_handle *h, int option, int value) {
+    if (!h) return MMOD_ERR_ARG;
+    if (value != 0 && value != 1) return fail(h, MMOD_ERR_ARG, "option values are 0 or 1");
+    switch (option) {
+        case MMOD_OPT_PDL: h->pdl = value; return MMOD_OK;
+        default: return fail(h, MMOD_ERR_ARG, "unknown option");
+    }
+}
+
 MMOD_API mmod_status mmod_get_plan(const mmod_handle *h, int *out8) {
     if (!h || !out8) return MMOD_ERR_ARG;
     if (!h->tma_ok) return MMOD_ERR_UNSUPPORTED;
@@ -547,7 +562,8 @@ MMOD_API mmod_status mmod_forward(mmod_handle *h, const float *wavelet, float *t
 
     if (c.nt > 0) {
         const int kern = use_tma(h) ? 100 + active_plan(h).variant : MMOD_KERNEL_SIMPLE;
-        if (!h->gexec || h->g_wav != dwav || h->g_tr != dtr || h->g_kernel != kern) {
+        const int opts = h->pdl;
+        if (!h->gexec || h->g_wav != dwav || h->g_tr != dtr || h->g_kernel != kern || h->g_opts != opts) {
             if (h->gexec) {
                 cudaGraphExecDestroy(h->gexec);
                 h->gexec = nullptr;
@@ -571,6 +587,7 @@ MMOD_API mmod_status mmod_forward(mmod_handle *h, const float *wavelet, float *t
             h->g_wav = dwav;
             h->g_tr = dtr;
             h->g_kernel = kern;
+            h->g_opts = opts;
             h->g_launches = n_l;
         }
         CK(h, cudaGraphLaunch(h->gexec, s));

@@ -36,6 +36,7 @@ struct StepArgs {
     const long long *rec_off;             // padded offsets
     float *traces;                        // [nt][nrec]
     int *err;                             // device view of the mapped error word
+    int pdl;                              // 1: launched as a programmatic dependent of the previous step
 };
 
 // Host helpers shared by the entry points (mmod_api.cu).

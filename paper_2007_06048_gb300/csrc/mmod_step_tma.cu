@@ -8,9 +8,9 @@
 //
 // Data movement.  One elected thread issues cp.async.bulk.tensor loads:
 //   * u^n planes with a 4-cell x-y halo, (64+8) x (TY+8) floats, into an
-//     NSU-slot ring.  The tensor map's zero fill outside the grid is exactly
+//     S::NSU-slot ring.  The tensor map's zero fill outside the grid is exactly
 //     the u = 0 reading, so no thread tests bounds on loads.
-//   * u^{n-1} and c planes, 64 x TY floats each, into an NSC-slot ring.
+//   * u^{n-1} and c planes, 64 x TY floats each, into an S::NSC-slot ring.
 // Each slot has an mbarrier (transaction count = box bytes).  A slot is
 // refilled after the block barrier that ends the last step reading it, so
 // several planes per ring are in flight while the CTA computes.
@@ -39,15 +39,15 @@ namespace {
 
 constexpr int TX = 64;                 // tile width: 32 lanes x 2 points
 constexpr int HX = TX + 2 * kRadius;   // 72: halo tile width
-constexpr int NSU = 8;                 // u^n slots: 5 resident planes + prefetch
-constexpr int NSC = 4;                 // u^{n-1}, c slots
 constexpr unsigned long long kWaitNs = 100000000ull;   // a wait gives up after 100 ms
 
-template <int TY_, int RY_, int U_>
+template <int TY_, int RY_, int U_, int NSU_ = 8, int NSC_ = 4>
 struct Shape {
     static constexpr int TY = TY_;
     static constexpr int RY = RY_;
     static constexpr int U = U_;                    // z steps per unrolled block
+    static constexpr int NSU = NSU_;                // u^n slots: 5 resident planes + prefetch
+    static constexpr int NSC = NSC_;                // u^{n-1}, c slots
     static constexpr int QD = 2 * kRadius + U;      // register queue depth
     static constexpr int NWARP = TY / RY;
     static constexpr int NT = NWARP * 32;
@@ -56,6 +56,7 @@ struct Shape {
     static constexpr int PC = TX * TY;              // floats per u^{n-1} or c slot
     static constexpr int SMEM = (NSU * CUR + NSC * 2 * PC) * 4 + (NSU + NSC) * 8 + 16;
     static_assert(TY % RY == 0, "rows per thread must divide the tile height");
+    static_assert(NSU >= 6 && NSU <= 8 && NSC >= 2, "ring depth outside the fill / release schedule");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -128,11 +129,11 @@ struct Geom {
 };
 
 struct Ctx {
-    float *cur;          // NSU u^n slots
-    float *up;           // NSC u^{n-1} slots
-    float *cc;           // NSC c slots
-    uint64_t *full_u;    // NSU barriers: data landed
-    uint64_t *full_c;    // NSC barriers
+    float *cur;          // S::NSU u^n slots
+    float *up;           // S::NSC u^{n-1} slots
+    float *cc;           // S::NSC c slots
+    uint64_t *full_u;    // S::NSU barriers: data landed
+    uint64_t *full_c;    // S::NSC barriers
     int *abort_flag;
     int x0, y0, z0, T;
     int lane, warp;
@@ -140,14 +141,14 @@ struct Ctx {
 
 template <class S>
 __device__ __forceinline__ void issue_u(const Ctx &c, const CUtensorMap *map, int seq) {
-    const int s = seq % NSU;
+    const int s = seq % S::NSU;
     mbar_expect_tx(&c.full_u[s], S::CUR * 4);
     tma_load_3d(c.cur + s * S::CUR, map, c.x0 - kRadius, c.y0 - kRadius, c.z0 - kRadius + seq, &c.full_u[s]);
 }
 
 template <class S>
 __device__ __forceinline__ void issue_c(const Ctx &c, const CUtensorMap *pmap, const CUtensorMap *cmap, int t) {
-    const int s = t % NSC;
+    const int s = t % S::NSC;
     mbar_expect_tx(&c.full_c[s], 2 * S::PC * 4);
     tma_load_3d(c.up + s * S::PC, pmap, c.x0, c.y0, c.z0 + t, &c.full_c[s]);
     tma_load_3d(c.cc + s * S::PC, cmap, c.x0, c.y0, c.z0 + t, &c.full_c[s]);
@@ -156,7 +157,7 @@ __device__ __forceinline__ void issue_c(const Ctx &c, const CUtensorMap *pmap, c
 // Own points of plane seq (rows 4+RY*w+r, columns 4+2*lane) into queue slot Q.
 template <class S, int Q>
 __device__ __forceinline__ void read_own(const Ctx &c, int seq, float2 (&q)[S::QD][S::RY]) {
-    const float *base = c.cur + (seq % NSU) * S::CUR + (kRadius + S::RY * c.warp) * HX + kRadius + 2 * c.lane;
+    const float *base = c.cur + (seq % S::NSU) * S::CUR + (kRadius + S::RY * c.warp) * HX + kRadius + 2 * c.lane;
 #pragma unroll
     for (int r = 0; r < S::RY; ++r) q[Q][r] = *reinterpret_cast<const float2 *>(base + r * HX);
 }
@@ -226,18 +227,18 @@ __device__ __forceinline__ void step(const StepArgs &a, const Ctx &c, int t, flo
     // 1. the leading plane k+4 (sequence t+8) enters the queue
     {
         const int seq = t + 2 * kRadius;
-        if (!mbar_wait(&c.full_u[seq % NSU], (seq / NSU) & 1, c.abort_flag, a.err)) return;
+        if (!mbar_wait(&c.full_u[seq % S::NSU], (seq / S::NSU) & 1, c.abort_flag, a.err)) return;
         read_own<S, J + 2 * kRadius>(c, seq, q);
     }
-    if (!mbar_wait(&c.full_c[t % NSC], (t / NSC) & 1, c.abort_flag, a.err)) return;
+    if (!mbar_wait(&c.full_c[t % S::NSC], (t / S::NSC) & 1, c.abort_flag, a.err)) return;
 
     // 2. y neighbour columns: rows RY*w .. RY*w+RY+7 of the centre plane (sequence t+4)
-    const float *ctr = c.cur + ((t + kRadius) % NSU) * S::CUR + (RY * c.warp) * HX + 2 * c.lane;
+    const float *ctr = c.cur + ((t + kRadius) % S::NSU) * S::CUR + (RY * c.warp) * HX + 2 * c.lane;
     float2 yc[RY + 2 * kRadius];
 #pragma unroll
     for (int rr = 0; rr < RY + 2 * kRadius; ++rr) yc[rr] = *reinterpret_cast<const float2 *>(ctr + rr * HX + kRadius);
-    const float *upp = c.up + (t % NSC) * S::PC + (RY * c.warp) * TX + 2 * c.lane;
-    const float *ccp = c.cc + (t % NSC) * S::PC + (RY * c.warp) * TX + 2 * c.lane;
+    const float *upp = c.up + (t % S::NSC) * S::PC + (RY * c.warp) * TX + 2 * c.lane;
+    const float *ccp = c.cc + (t % S::NSC) * S::PC + (RY * c.warp) * TX + 2 * c.lane;
     const bool damped = xy_damped || k < a.nbl || k > a.nz - 1 - a.nbl;
     const long long koff = (long long)k * a.plane;
 #pragma unroll
@@ -296,11 +297,11 @@ __global__ void __launch_bounds__(S::NT)
     extern __shared__ __align__(128) unsigned char smem[];
     Ctx c;
     c.cur = reinterpret_cast<float *>(smem);
-    c.up = c.cur + NSU * S::CUR;
-    c.cc = c.up + NSC * S::PC;
-    c.full_u = reinterpret_cast<uint64_t *>(c.cc + NSC * S::PC);
-    c.full_c = c.full_u + NSU;
-    c.abort_flag = reinterpret_cast<int *>(c.full_c + NSC);
+    c.up = c.cur + S::NSU * S::CUR;
+    c.cc = c.up + S::NSC * S::PC;
+    c.full_u = reinterpret_cast<uint64_t *>(c.cc + S::NSC * S::PC);
+    c.full_c = c.full_u + S::NSU;
+    c.abort_flag = reinterpret_cast<int *>(c.full_c + S::NSC);
     const int tid = threadIdx.x;
     c.lane = tid & 31;
     c.warp = tid >> 5;
@@ -317,16 +318,24 @@ __global__ void __launch_bounds__(S::NT)
     const int nseq = T + 2 * kRadius;   // u^n planes z0-4 .. z0+T+3
 
     if (tid == 0) {
-        for (int s = 0; s < NSU; ++s) mbar_init(&c.full_u[s], 1);
-        for (int s = 0; s < NSC; ++s) mbar_init(&c.full_c[s], 1);
+        for (int s = 0; s < S::NSU; ++s) mbar_init(&c.full_u[s], 1);
+        for (int s = 0; s < S::NSC; ++s) mbar_init(&c.full_c[s], 1);
         *c.abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
+    if (a.pdl) {
+        // Under programmatic dependent launch this grid may start while the
+        // previous step still runs: everything above is independent of it;
+        // wait for its completion (and memory) before reading u^n or u^{n-1}
+        // or writing u^{n+1}, then let the next step's grid be scheduled.
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    }
     __syncthreads();
     if (tid == 0 && T > 0) {
-        for (int seq = 0; seq < NSU && seq < nseq; ++seq) issue_u<S>(c, &cur_map, seq);
-        for (int t = 0; t < NSC && t < T; ++t) issue_c<S>(c, &prev_map, &c_map, t);
+        for (int seq = 0; seq < S::NSU && seq < nseq; ++seq) issue_u<S>(c, &cur_map, seq);
+        for (int t = 0; t < S::NSC && t < T; ++t) issue_c<S>(c, &prev_map, &c_map, t);
     }
     // receivers of the previous step (u^n, read-only during this launch)
     if (a.traces) {
@@ -362,24 +371,38 @@ __global__ void __launch_bounds__(S::NT)
 
     float2 q[S::QD][RY];
     // Issue order of u^n sequences is 0, 1, 2, ... with no gaps: the prologue
-    // issues 0..NSU-1, the fill below 4 more, then one per finished step.
-    int u_hi = min(NSU, nseq);
-    int c_hi = min(NSC, T);
-    // planes z0-4 .. z0+3 (sequences 0..7) fill queue slots 0..7
+    // issues 0..S::NSU-1, the fill below 4 more, then one per finished step.
+    int u_hi = min(S::NSU, nseq);
+    int c_hi = min(S::NSC, T);
+    // planes z0-4 .. z0+3 (sequences 0..7) fill queue slots 0..7.  Phase A
+    // reads what the prologue issued (sequences 0..min(NSU,8)-1); the slots
+    // of sequences 0..3 (never a centre) then take NSU..NSU+3; phase B reads
+    // sequences NSU..7 when the ring is shallower than 8.
+    constexpr int NA = S::NSU < 2 * kRadius ? S::NSU : 2 * kRadius;
     bool filled = true;
 #pragma unroll 1
-    for (int seq = 0; seq < 2 * kRadius; ++seq)
-        filled = filled && mbar_wait(&c.full_u[seq % NSU], (seq / NSU) & 1, c.abort_flag, a.err);
+    for (int seq = 0; seq < NA; ++seq)
+        filled = filled && mbar_wait(&c.full_u[seq % S::NSU], (seq / S::NSU) & 1, c.abort_flag, a.err);
     if (filled) {
         read_own<S, 0>(c, 0, q); read_own<S, 1>(c, 1, q); read_own<S, 2>(c, 2, q); read_own<S, 3>(c, 3, q);
-        read_own<S, 4>(c, 4, q); read_own<S, 5>(c, 5, q); read_own<S, 6>(c, 6, q); read_own<S, 7>(c, 7, q);
+        read_own<S, 4>(c, 4, q); read_own<S, 5>(c, 5, q);
+        if constexpr (NA > 6) read_own<S, 6>(c, 6, q);
+        if constexpr (NA > 7) read_own<S, 7>(c, 7, q);
     }
     __syncthreads();
-    // sequences 0..3 are only needed in registers: their slots take NSU..NSU+3
     if (!*c.abort_flag) {
         if (tid == 0)
-            for (int seq = u_hi; seq < NSU + kRadius && seq < nseq; ++seq) issue_u<S>(c, &cur_map, seq);
-        u_hi = min(NSU + kRadius, nseq);
+            for (int seq = u_hi; seq < S::NSU + kRadius && seq < nseq; ++seq) issue_u<S>(c, &cur_map, seq);
+        u_hi = min(S::NSU + kRadius, nseq);
+        if constexpr (NA < 2 * kRadius) {
+#pragma unroll 1
+            for (int seq = NA; seq < 2 * kRadius; ++seq)
+                filled = filled && mbar_wait(&c.full_u[seq % S::NSU], (seq / S::NSU) & 1, c.abort_flag, a.err);
+            if (filled) {
+                if constexpr (NA <= 6) read_own<S, 6>(c, 6, q);
+                read_own<S, 7>(c, 7, q);
+            }
+        }
         PlaneInfo pi = plane_info(a, c.z0);
         // Steps run in blocks of U; step J of a block uses queue window
         // q[J .. J+8], and the block ends by moving its last 8 planes down.
@@ -393,11 +416,11 @@ __global__ void __launch_bounds__(S::NT)
         __syncthreads();                                                                    \
         if (*c.abort_flag) break;                                                           \
         if (tid == 0) {                                                                     \
-            if (t + (J) + kRadius + NSU < nseq) issue_u<S>(c, &cur_map, t + (J) + kRadius + NSU); \
-            if (t + (J) + NSC < T) issue_c<S>(c, &prev_map, &c_map, t + (J) + NSC);        \
+            if (t + (J) + kRadius + S::NSU < nseq) issue_u<S>(c, &cur_map, t + (J) + kRadius + S::NSU); \
+            if (t + (J) + S::NSC < T) issue_c<S>(c, &prev_map, &c_map, t + (J) + S::NSC);        \
         }                                                                                   \
-        u_hi = min(t + (J) + kRadius + NSU + 1, nseq);                                      \
-        c_hi = min(t + (J) + NSC + 1, T);                                                   \
+        u_hi = min(t + (J) + kRadius + S::NSU + 1, nseq);                                      \
+        c_hi = min(t + (J) + S::NSC + 1, T);                                                   \
     }
 #pragma unroll 1
         for (int t = 0; t < T; t += U) {
@@ -416,8 +439,8 @@ __global__ void __launch_bounds__(S::NT)
     // flight (the latest sequence of every slot) before its shared memory is
     // released.
     if (*c.abort_flag && tid == 0) {
-        for (int seq = max(0, u_hi - NSU); seq < u_hi; ++seq) mbar_drain(&c.full_u[seq % NSU], (seq / NSU) & 1);
-        for (int t = max(0, c_hi - NSC); t < c_hi; ++t) mbar_drain(&c.full_c[t % NSC], (t / NSC) & 1);
+        for (int seq = max(0, u_hi - S::NSU); seq < u_hi; ++seq) mbar_drain(&c.full_u[seq % S::NSU], (seq / S::NSU) & 1);
+        for (int t = max(0, c_hi - S::NSC); t < c_hi; ++t) mbar_drain(&c.full_c[t % S::NSC], (t / S::NSC) & 1);
     }
 }
 
@@ -461,6 +484,8 @@ using V22_2 = Shape<kTY, 2, 2>;
 using V22_4 = Shape<kTY, 2, 4>;
 using V24_1 = Shape<kTY, 4, 1>;
 using V24_2 = Shape<kTY, 4, 2>;
+using V24_2s = Shape<kTY, 4, 2, 6, 2>;
+using V22_4s = Shape<kTY, 2, 4, 6, 2>;
 
 struct Variant {
     const char *name;
@@ -475,6 +500,8 @@ const Variant kVariants[] = {
     MMOD_VARIANT(V22_4, "64x16 tile, 2x2 points/thread, z unroll 4"),
     MMOD_VARIANT(V24_1, "64x16 tile, 2x4 points/thread, z unroll 1"),
     MMOD_VARIANT(V24_2, "64x16 tile, 2x4 points/thread, z unroll 2"),
+    MMOD_VARIANT(V24_2s, "64x16 tile, 2x4 points/thread, z unroll 2, shallow rings"),
+    MMOD_VARIANT(V22_4s, "64x16 tile, 2x2 points/thread, z unroll 4, shallow rings"),
 };
 #undef MMOD_VARIANT
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
@@ -538,13 +565,25 @@ bool make_tma_plan(const mmod_config &cfg, int nxp, float *const u[2], const flo
 cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap *cur_map, const CUtensorMap *prev_map,
                             const CUtensorMap *c_map, const TmaPlan &plan, cudaStream_t s) {
     const Geom g{plan.tiles_x, plan.tiles_y, plan.zchunks, plan.zlen};
-#define MMOD_LAUNCH(V) step_tma_kernel<V><<<plan.grid, plan.block, plan.smem, s>>>(a, *cur_map, *prev_map, *c_map, g)
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(plan.grid);
+    lc.blockDim = dim3(plan.block);
+    lc.dynamicSmemBytes = plan.smem;
+    lc.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = attr;
+    lc.numAttrs = a.pdl ? 1 : 0;
+#define MMOD_LAUNCH(V) cudaLaunchKernelEx(&lc, step_tma_kernel<V>, a, *cur_map, *prev_map, *c_map, g)
     switch (plan.variant) {
         case 0: MMOD_LAUNCH(V22_1); break;
         case 1: MMOD_LAUNCH(V22_2); break;
         case 2: MMOD_LAUNCH(V22_4); break;
         case 3: MMOD_LAUNCH(V24_1); break;
         case 4: MMOD_LAUNCH(V24_2); break;
+        case 5: MMOD_LAUNCH(V24_2s); break;
+        case 6: MMOD_LAUNCH(V22_4s); break;
         default: return cudaErrorInvalidValue;
     }
 #undef MMOD_LAUNCH

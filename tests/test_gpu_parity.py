@@ -182,6 +182,10 @@ def test_tma_kernel_is_bitwise_the_plain_kernel(shape, nbl):
         tr_t, u_t, prop = run_gpu(p, kernel=M.KERNEL_TMA, variant=v)
         assert np.array_equal(u_s, u_t), M.mmod_tma_variant_name(v)
         assert np.array_equal(tr_s, tr_t), M.mmod_tma_variant_name(v)
+    for pdl in (0, 1):   # programmatic dependent launch off / on
+        tr_o, u_o, _ = run_gpu(p, kernel=M.KERNEL_TMA, pdl=pdl)
+        assert np.array_equal(u_s, u_o), pdl
+        assert np.array_equal(tr_s, tr_o), pdl
     # one step kernel per time step plus the final receiver gather and the unpack
     assert prop.launches == p.nt + 2
     assert prop.loop_ms() > 0
