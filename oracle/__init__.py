@@ -16,7 +16,8 @@ closed form and the moment identities; Laplacian exact on polynomials of degree
 <= 9; the exact discrete standing wave (dispersion relation); discrete energy
 conservation (damping off) and decay (damping on); the 3-D homogeneous Green's
 function; a dense-matrix stepper on tiny grids; linearity, reciprocity and axis
-permutation.
+permutation; for the adjoint the dot-product test <F w, r> = <w, F^T r> and a
+dense transpose, for the gradient central finite differences of the misfit.
 """
 from __future__ import annotations
 
@@ -67,8 +68,10 @@ class Oracle:
         lib.orc_forward.argtypes = [I, I, I, D, D, D, D, I, I, I, D, P,
                                     I, P, P, I, P, P, P, P, P, P, I]
         lib.orc_max_threads.argtypes = []
+        lib.orc_adjoint.argtypes = [I, I, I, D, D, D, D, I, I, I, D, P, I, P, I, P, P, P, I]
+        lib.orc_gradient.argtypes = [I, I, I, D, D, D, D, I, I, I, D, P, I, P, P, I, P, P, P, I]
         for f in (lib.orc_fd_coeffs, lib.orc_damping_profile, lib.orc_laplacian,
-                  lib.orc_forward, lib.orc_max_threads):
+                  lib.orc_forward, lib.orc_max_threads, lib.orc_adjoint, lib.orc_gradient):
             f.restype = ctypes.c_int
         self.lib = lib
         self.path = path
@@ -137,6 +140,42 @@ class Oracle:
         return traces
 
 
+    def adjoint(self, vel, h, dt, nt, *, order=8, nbl=0, refl=1e-3, src_ijk=None, rec_ijk=None,
+                resid=None, nthreads=0):
+        """Transpose of the forward map wavelet -> traces: resid [nt][nrec] ->
+        adjoint source [nsrc][nt] (FP64)."""
+        vel = np.ascontiguousarray(vel, dtype=np.float32)
+        nz, ny, nx = vel.shape
+        src = np.ascontiguousarray(src_ijk, np.int32).reshape(-1, 3)
+        rec = np.ascontiguousarray(rec_ijk, np.int32).reshape(-1, 3)
+        r = np.ascontiguousarray(resid, np.float64).reshape(nt, len(rec))
+        adj = np.zeros((len(src), nt), np.float64)
+        rc = self.lib.orc_adjoint(nx, ny, nz, h[0], h[1], h[2], dt, nt, order, nbl, refl, _ptr(vel),
+                                  len(src), _ptr(src), len(rec), _ptr(rec), _ptr(r), _ptr(adj), nthreads)
+        if rc != 0:
+            raise ValueError(f"orc_adjoint -> {rc}")
+        return adj
+
+    def gradient(self, vel, h, dt, nt, *, order=8, nbl=0, refl=1e-3, src_ijk=None, wavelet=None,
+                 rec_ijk=None, resid=None, nthreads=0):
+        """dJ/dv for J = 1/2 sum |traces - d_obs|^2 given resid = traces - d_obs
+        ([nt][nrec]); returns [nz][ny][nx] FP64.  Stores every forward state:
+        small grids only."""
+        vel = np.ascontiguousarray(vel, dtype=np.float32)
+        nz, ny, nx = vel.shape
+        src = np.ascontiguousarray(src_ijk, np.int32).reshape(-1, 3)
+        rec = np.ascontiguousarray(rec_ijk, np.int32).reshape(-1, 3)
+        wav = np.ascontiguousarray(wavelet, np.float32).reshape(len(src), nt)
+        r = np.ascontiguousarray(resid, np.float64).reshape(nt, len(rec))
+        g = np.zeros(vel.shape, np.float64)
+        rc = self.lib.orc_gradient(nx, ny, nz, h[0], h[1], h[2], dt, nt, order, nbl, refl, _ptr(vel),
+                                   len(src), _ptr(src), _ptr(wav), len(rec), _ptr(rec), _ptr(r), _ptr(g),
+                                   nthreads)
+        if rc != 0:
+            raise ValueError(f"orc_gradient -> {rc}")
+        return g
+
+
 def _default() -> Oracle:
     global _lib
     if _lib is None:
@@ -165,3 +204,15 @@ def forward(vel, h, dt, nt, **kw):
 
 
 forward.__doc__ = Oracle.forward.__doc__
+
+
+def adjoint(vel, h, dt, nt, **kw):
+    return _default().adjoint(vel, h, dt, nt, **kw)
+
+
+def gradient(vel, h, dt, nt, **kw):
+    return _default().gradient(vel, h, dt, nt, **kw)
+
+
+adjoint.__doc__ = Oracle.adjoint.__doc__
+gradient.__doc__ = Oracle.gradient.__doc__

@@ -301,3 +301,192 @@ int orc_max_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* Adjoint of the forward map w -> traces (transpose of Alg. 1 with the     */
+/* readings above).  Writing the forward step as                            */
+/*   D u^{n+1} = 2 u^n - E u^{n-1} + C (L u^n + s^n),  d^n = R u^{n+1},     */
+/* D = 1 + e, E = 1 - e, C = dt^2 v^2, s^n = S w^n / (hx hy hz), the        */
+/* transpose runs backward from mu^{nt+1} = mu^{nt+2} = 0:                  */
+/*   D mu^n = 2 mu^{n+1} - E mu^{n+2} + L (C mu^{n+1}) + R^T r^{n-1}        */
+/* for n = nt .. 1, and the adjoint source is                               */
+/*   a[s][n-1] = C(x_s) mu^n(x_s) / (hx hy hz).                             */
+/* L is symmetric (u = 0 outside), so L^T = L.                              */
+/* resid [nt][nrec] FP64 in; adj [nsrc][nt] FP64 out.                       */
+/* If grad_c != NULL it also needs u_hist = u^{-1} .. u^{nt} (nt+2 padded   */
+/* volumes, as produced by orc_forward_history) and accumulates the         */
+/* gradient of J = 1/2 sum |d - d_obs|^2 with respect to c:                 */
+/*   dJ/dc(x) = sum_{n=1..nt} mu^n(x) (L u^{n-1} + s^{n-1})(x).             */
+/* ------------------------------------------------------------------------ */
+static int adjoint_core(int nx, int ny, int nz, double hx, double hy, double hz,
+                        double dt, int nt, int order, int nbl, double refl,
+                        const float *vel, int nsrc, const int *src_ijk, const float *wavelet,
+                        int nrec, const int *rec_ijk, const double *resid, double *adj,
+                        double *const *u_hist, double *grad_c)
+{
+    double cx[ORC_MAX_R + 1], cy[ORC_MAX_R + 1], cz[ORC_MAX_R + 1];
+    if (axis_weights(order, hx, hy, hz, cx, cy, cz) != 0) return -1;
+    const grid_t g = make_grid(nx, ny, nz, order / 2);
+    const long N = (long)nx * ny * nz;
+    double vmax = 0.0;
+    for (long q = 0; q < N; ++q) if ((double)vel[q] > vmax) vmax = (double)vel[q];
+    double *ex = (double *)malloc(sizeof(double) * nx);
+    double *ey = (double *)malloc(sizeof(double) * ny);
+    double *ez = (double *)malloc(sizeof(double) * nz);
+    double *C = padded_zeros(&g), *m0 = padded_zeros(&g), *m1 = padded_zeros(&g), *m2 = padded_zeros(&g);
+    double *cm = padded_zeros(&g);
+    int rc = 0;
+    if (!ex || !ey || !ez || !C || !m0 || !m1 || !m2 || !cm) { rc = -3; goto done; }
+    if (orc_damping_profile(nx, nbl, hx, vmax, refl, ex) || orc_damping_profile(ny, nbl, hy, vmax, refl, ey) ||
+        orc_damping_profile(nz, nbl, hz, vmax, refl, ez)) { rc = -1; goto done; }
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const double v = (double)vel[((long)k * ny + j) * nx + i];
+                C[at(&g, i, j, k)] = dt * dt * v * v;
+            }
+    const double cell = hx * hy * hz;
+    /* m1 = mu^{n+1}, m2 = mu^{n+2}, m0 receives mu^n */
+    for (int n = nt; n >= 1; --n) {
+        #pragma omp parallel for collapse(2) schedule(static)
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    const long o = at(&g, i, j, k);
+                    cm[o] = C[o] * m1[o];
+                }
+        #pragma omp parallel for collapse(2) schedule(static)
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    const long o = at(&g, i, j, k);
+                    const double e = (ex[i] + ey[j] + ez[k]) * dt;
+                    m0[o] = (2.0 * m1[o] - (1.0 - e) * m2[o] + lap_at(&g, cm, o, cx, cy, cz)) / (1.0 + e);
+                }
+        for (int r = 0; r < nrec; ++r) {          /* R^T r^{n-1}, inside the division */
+            const int *p = rec_ijk + 3 * r;
+            const long o = at(&g, p[0], p[1], p[2]);
+            const double e = (ex[p[0]] + ey[p[1]] + ez[p[2]]) * dt;
+            m0[o] += resid[(long)(n - 1) * nrec + r] / (1.0 + e);
+        }
+        for (int s = 0; s < nsrc; ++s) {
+            const int *p = src_ijk + 3 * s;
+            const long o = at(&g, p[0], p[1], p[2]);
+            if (adj) adj[(long)s * nt + (n - 1)] = C[o] * m0[o] / cell;
+        }
+        if (grad_c) {
+            /* term of forward step n-1: mu^n (L u^{n-1} + s^{n-1}); u_hist[m+1] = u^m */
+            const double *u = u_hist[n];   /* u^{n-1} */
+            #pragma omp parallel for collapse(2) schedule(static)
+            for (int k = 0; k < nz; ++k)
+                for (int j = 0; j < ny; ++j)
+                    for (int i = 0; i < nx; ++i) {
+                        const long o = at(&g, i, j, k);
+                        grad_c[((long)k * ny + j) * nx + i] += m0[o] * lap_at(&g, u, o, cx, cy, cz);
+                    }
+            for (int s = 0; s < nsrc; ++s) {
+                const int *p = src_ijk + 3 * s;
+                const long o = at(&g, p[0], p[1], p[2]);
+                grad_c[((long)p[2] * ny + p[1]) * nx + p[0]] += m0[o] * (double)wavelet[(long)s * nt + (n - 1)] / cell;
+            }
+        }
+        double *t = m2; m2 = m1; m1 = m0; m0 = t;
+    }
+done:
+    free(ex); free(ey); free(ez); free(C); free(m0); free(m1); free(m2); free(cm);
+    return rc;
+}
+
+static int check_positions(int nx, int ny, int nz, int n, const int *ijk)
+{
+    for (int s = 0; s < n; ++s) {
+        const int *p = ijk + 3 * s;
+        if (p[0] < 0 || p[0] >= nx || p[1] < 0 || p[1] >= ny || p[2] < 0 || p[2] >= nz) return -1;
+    }
+    return 0;
+}
+
+int orc_adjoint(int nx, int ny, int nz, double hx, double hy, double hz,
+                double dt, int nt, int order, int nbl, double refl, const float *vel,
+                int nsrc, const int *src_ijk, int nrec, const int *rec_ijk,
+                const double *resid, double *adj, int nthreads)
+{
+    if (nx < 1 || ny < 1 || nz < 1 || nt < 0 || dt <= 0 || !vel || nsrc < 0 || nrec < 0) return -1;
+    if (2 * nbl > nx || 2 * nbl > ny || 2 * nbl > nz || nbl < 0) return -1;
+    if ((nsrc && (!src_ijk || !adj)) || (nrec && (!rec_ijk || !resid))) return -1;
+    if (check_positions(nx, ny, nz, nsrc, src_ijk) || check_positions(nx, ny, nz, nrec, rec_ijk)) return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    return adjoint_core(nx, ny, nz, hx, hy, hz, dt, nt, order, nbl, refl, vel, nsrc, src_ijk, NULL,
+                        nrec, rec_ijk, resid, adj, NULL, NULL);
+}
+
+/* Gradient of J = 1/2 sum_n |R u^{n+1} - d_obs^n|^2 with respect to the
+ * velocity, for the residual resid = R u^{n+1} - d_obs^n given by the caller:
+ *   dJ/dv(x) = 2 dt^2 v(x) dJ/dc(x)  (c = dt^2 v^2).
+ * Runs the forward storing every state u^{-1} .. u^{nt} (small grids only),
+ * then the adjoint recurrence of orc_adjoint.  grad_v [nz][ny][nx] FP64. */
+int orc_gradient(int nx, int ny, int nz, double hx, double hy, double hz,
+                 double dt, int nt, int order, int nbl, double refl, const float *vel,
+                 int nsrc, const int *src_ijk, const float *wavelet,
+                 int nrec, const int *rec_ijk, const double *resid, double *grad_v, int nthreads)
+{
+    if (nx < 1 || ny < 1 || nz < 1 || nt < 0 || dt <= 0 || !vel || !grad_v || nsrc < 0 || nrec < 0) return -1;
+    if (2 * nbl > nx || 2 * nbl > ny || 2 * nbl > nz || nbl < 0) return -1;
+    if ((nsrc && (!src_ijk || !wavelet)) || (nrec && (!rec_ijk || !resid))) return -1;
+    if (check_positions(nx, ny, nz, nsrc, src_ijk) || check_positions(nx, ny, nz, nrec, rec_ijk)) return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    const grid_t g = make_grid(nx, ny, nz, order / 2);
+    const long N = (long)nx * ny * nz;
+    int rc = 0;
+    double **hist = (double **)calloc((size_t)nt + 2, sizeof(double *));
+    double *dense = (double *)malloc(sizeof(double) * (size_t)N);
+    double *prev = (double *)calloc((size_t)N, sizeof(double));
+    double *gc = (double *)calloc((size_t)N, sizeof(double));
+    if (!hist || !dense || !prev || !gc) { rc = -3; goto done; }
+    for (int m = 0; m < nt + 2; ++m)
+        if (!(hist[m] = padded_zeros(&g))) { rc = -3; goto done; }
+    /* hist[m+1] = u^m, m = -1 .. nt: one forward step at a time from the last state */
+    for (int m = 0; m < nt; ++m) {
+        double *cur = dense;
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    const long q = ((long)k * ny + j) * nx + i;
+                    prev[q] = hist[m][at(&g, i, j, k)];
+                    cur[q] = hist[m + 1][at(&g, i, j, k)];
+                }
+        /* the step m of the full run: u^{m+1} from u^m, u^{m-1} with w[m] */
+        float *wm = NULL;
+        if (nsrc) {
+            wm = (float *)malloc(sizeof(float) * nsrc);
+            if (!wm) { rc = -3; goto done; }
+            for (int s = 0; s < nsrc; ++s) wm[s] = wavelet[(long)s * nt + m];
+        }
+        double *up = (double *)malloc(sizeof(double) * (size_t)N), *un = (double *)malloc(sizeof(double) * (size_t)N);
+        if (!up || !un) { free(up); free(un); free(wm); rc = -3; goto done; }
+        rc = orc_forward(nx, ny, nz, hx, hy, hz, dt, 1, order, nbl, refl, vel, nsrc, src_ijk, wm,
+                         0, NULL, NULL, prev, cur, up, un, nthreads);
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i)
+                    hist[m + 2][at(&g, i, j, k)] = un[((long)k * ny + j) * nx + i];
+        free(up); free(un); free(wm);
+        if (rc) goto done;
+    }
+    rc = adjoint_core(nx, ny, nz, hx, hy, hz, dt, nt, order, nbl, refl, vel, nsrc, src_ijk, wavelet,
+                      nrec, rec_ijk, resid, NULL, hist, gc);
+    if (rc) goto done;
+    for (long q = 0; q < N; ++q) grad_v[q] = 2.0 * dt * dt * (double)vel[q] * gc[q];
+done:
+    if (hist) for (int m = 0; m < nt + 2; ++m) free(hist[m]);
+    free(hist); free(dense); free(prev); free(gc);
+    return rc;
+}

@@ -6,6 +6,7 @@ import os
 import pytest
 
 import oracle
+import test_oracle_adjoint as AD
 import test_oracle_bruteforce as BF
 import test_oracle_dynamics as DY
 import test_oracle_stencil as ST
@@ -37,9 +38,20 @@ def _standing(orc):
     DY.test_standing_wave_is_exact(orc, 8)
 
 
+def _adjoint(orc):
+    AD.test_dot_product(orc)
+    AD.test_adjoint_is_the_explicit_transpose(orc)
+
+
+def _grad(orc):
+    for kind in ("point", "smooth", "source"):
+        AD.test_gradient_matches_finite_differences(orc, kind)
+
+
 MUTATIONS = [
     ("damping drops (1 - eta dt) on u^{n-1}", "(1.0 - e) * up[o]", "up[o]", [_energy, _dense]),
-    ("damping sign flipped", "/ (1.0 + e);", "/ (1.0 - e);", [_energy, _dense]),
+    ("damping sign flipped", "un[o] = (2.0 * ucur[o] - (1.0 - e) * up[o] + C[o] * L) / (1.0 + e);",
+     "un[o] = (2.0 * ucur[o] - (1.0 - e) * up[o] + C[o] * L) / (1.0 - e);", [_energy, _dense]),
     ("y axis uses the x weights", "ly += cy[m]", "ly += cx[m]", [_poly, _dense]),
     ("z neighbour uses the y stride", "u[o - m * g->sz]", "u[o - m * g->sy]", [_poly, _dense, _energy]),
     ("centre term dropped on x", "lx += cx[m] * (u[o + m] + u[o - m] - 2.0 * p)",
@@ -53,6 +65,16 @@ MUTATIONS = [
      [_dense]),
     ("leapfrog uses 2 u^{n-1}", "un[o] = 2.0 * ucur[o] - up[o] + C[o] * L;",
      "un[o] = 2.0 * ucur[o] - 2.0 * up[o] + C[o] * L;", [_standing, _dense]),
+    ("adjoint applies C after L (the forward's order)", "cm[o] = C[o] * m1[o];", "cm[o] = m1[o] * (1.0 + 0.0 * C[o]);",
+     [_adjoint]),
+    ("adjoint residual outside the damping division", "m0[o] += resid[(long)(n - 1) * nrec + r] / (1.0 + e);",
+     "m0[o] += resid[(long)(n - 1) * nrec + r];", [_adjoint]),
+    ("adjoint source misses the 1/h^3 cell factor", "if (adj) adj[(long)s * nt + (n - 1)] = C[o] * m0[o] / cell;",
+     "if (adj) adj[(long)s * nt + (n - 1)] = C[o] * m0[o];", [_adjoint]),
+    ("gradient drops its source term", "+= m0[o] * (double)wavelet[(long)s * nt + (n - 1)] / cell;",
+     "+= 0.0 * m0[o] * (double)wavelet[(long)s * nt + (n - 1)] / cell;", [_grad]),
+    ("gradient pairs mu^n with u^n", "const double *u = u_hist[n];   /* u^{n-1} */",
+     "const double *u = u_hist[n + 1];", [_grad]),
 ]
 
 
