@@ -111,6 +111,42 @@ mmod_status mmod_set_model(mmod_handle *h, const float *vel, mmod_stream stream)
 mmod_status mmod_forward(mmod_handle *h, const float *wavelet, float *traces,
                          float *final_u, mmod_stream stream);
 
+/* Adjoint of the forward map wavelet -> traces (for a fixed model): given
+ * resid [nt][nrec] (FP32, the data-space vector r), writes adj_src [nsrc][nt]
+ * = F^T r, i.e. <F w, r> = <w, F^T r> for every wavelet w.  It is the
+ * transpose of the scheme above, run backward in time (the paper's Eq. 5
+ * is linear in the source term; the transpose is this library's addition for
+ * inversion, which the paper names as the use of forward modelling).  Uses
+ * the handle's wavefield buffers (the forward state is overwritten).
+ * Errors: STATE (no model), ARG, CUDA, TIMEOUT. */
+mmod_status mmod_adjoint(mmod_handle *h, const float *resid, float *adj_src, mmod_stream stream);
+
+/* Checkpoint storage of mmod_gradient. */
+enum { MMOD_CKPT_FP32 = 0, MMOD_CKPT_BF16 = 1, MMOD_CKPT_FP16 = 2 };
+
+/* Gradient of J = 1/2 sum_n |traces^n - d_obs^n|^2 with respect to the
+ * velocity, for the current model, given wavelet [nsrc][nt] and the residual
+ * resid [nt][nrec] = traces - d_obs of that model.  Writes grad_v
+ * [nz][ny][nx] (FP32, dJ/dv in J-units per m/s):
+ *   dJ/dv = 2 dt^2 v sum_n psi^{n+1} (D u^{n+1} - 2 u^n + E u^{n-1}) / c^2,
+ * psi the adjoint wavefield (zero-lag imaging condition).  The forward
+ * states are recomputed from ckpt_count checkpoints (two-level scheme: the
+ * run is cut into ckpt_count segments; each segment is replayed once, so the
+ * cost is two forward runs and one adjoint run).  Checkpoints are stored as
+ * MMOD_CKPT_FP32 (exact replay) or BF16 / FP16 with one scale per z plane
+ * (stepping stays FP32).  Device memory: mmod_gradient_memory().  Errors:
+ * STATE, ARG, OOM, CUDA, TIMEOUT. */
+mmod_status mmod_gradient(mmod_handle *h, const float *wavelet, const float *resid, float *grad_v,
+                          int ckpt_count, int ckpt_dtype, mmod_stream stream);
+
+/* Bytes of device memory mmod_gradient allocates for this checkpoint layout
+ * (on top of the handle's own volumes); -1 for invalid arguments. */
+long long mmod_gradient_memory(const mmod_handle *h, int ckpt_count, int ckpt_dtype);
+
+/* FP64 sum of a[i] * b[i] over n FP32 device values (dot-product tests,
+ * gradient norms).  Synchronises `stream`.  Errors: ARG, OOM, CUDA. */
+mmod_status mmod_dot(const float *a, const float *b, long long n, double *out, mmod_stream stream);
+
 /* Test hook: the next mmod_forward starts from u^{-1} = u_prev, u^0 = u_cur
  * ([nz][ny][nx] FP32, either may be NULL for zeros) instead of zeros. */
 mmod_status mmod_set_state(mmod_handle *h, const float *u_prev, const float *u_cur,

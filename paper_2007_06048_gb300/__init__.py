@@ -33,7 +33,9 @@ EXPORTED = ["mmod_create", "mmod_destroy", "mmod_set_model", "mmod_forward", "mm
             "mmod_get_state", "mmod_set_kernel", "mmod_last_launch_count", "mmod_last_loop_ms",
             "mmod_cfl_dt", "mmod_last_error", "mmod_version", "mmod_check_recip",
             "mmod_tma_variant_count", "mmod_tma_variant_name", "mmod_set_tma_variant", "mmod_get_plan",
-            "mmod_forward_noalloc", "mmod_set_option"]
+            "mmod_forward_noalloc", "mmod_set_option", "mmod_adjoint", "mmod_gradient",
+            "mmod_gradient_memory", "mmod_dot"]
+CKPT_FP32, CKPT_BF16, CKPT_FP16 = 0, 1, 2
 
 
 class MmodError(RuntimeError):
@@ -88,6 +90,10 @@ def load():
         "mmod_get_plan": ([P, ctypes.POINTER(ctypes.c_int)], I),
         "mmod_forward_noalloc": ([ctypes.POINTER(_Config), I, P, P, P, P, P], I),
         "mmod_set_option": ([P, I, I], I),
+        "mmod_adjoint": ([P, P, P, P], I),
+        "mmod_gradient": ([P, P, P, P, I, I, P], I),
+        "mmod_gradient_memory": ([P, I, I], ctypes.c_longlong),
+        "mmod_dot": ([P, P, ctypes.c_longlong, ctypes.POINTER(ctypes.c_double), P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -218,6 +224,29 @@ def mmod_set_tma_variant(h, v: int):
     _check(h, load().mmod_set_tma_variant(h, int(v)))
 
 
+def mmod_adjoint(h, resid, adj_src, stream=None):
+    _check(h, load().mmod_adjoint(h, _addr(resid), _addr(adj_src), _stream(stream)))
+
+
+def mmod_gradient(h, wavelet, resid, grad_v, ckpt_count, ckpt_dtype=0, stream=None):
+    _check(h, load().mmod_gradient(h, _addr(wavelet), _addr(resid), _addr(grad_v), int(ckpt_count),
+                                   int(ckpt_dtype), _stream(stream)))
+
+
+def mmod_gradient_memory(h, ckpt_count, ckpt_dtype=0) -> int:
+    return int(load().mmod_gradient_memory(h, int(ckpt_count), int(ckpt_dtype)))
+
+
+def mmod_dot(a, b, n=None, stream=None) -> float:
+    """FP64 dot product of two FP32 device arrays (computed by the library)."""
+    out = ctypes.c_double(0.0)
+    n = a.numel() if n is None else n
+    st = load().mmod_dot(_addr(a), _addr(b), int(n), ctypes.byref(out), _stream(stream))
+    if st != 0:
+        raise MmodError(st, "mmod_dot failed")
+    return float(out.value)
+
+
 def mmod_set_option(h, option: int, value: int):
     _check(h, load().mmod_set_option(h, int(option), int(value)))
 
@@ -274,6 +303,15 @@ class Propagator:
 
     def set_option(self, option: int, value: int):
         mmod_set_option(self.handle, option, value)
+
+    def adjoint(self, resid, adj_src, stream=None):
+        mmod_adjoint(self.handle, resid, adj_src, stream)
+
+    def gradient(self, wavelet, resid, grad_v, ckpt_count, ckpt_dtype=0, stream=None):
+        mmod_gradient(self.handle, wavelet, resid, grad_v, ckpt_count, ckpt_dtype, stream)
+
+    def gradient_memory(self, ckpt_count, ckpt_dtype=0) -> int:
+        return mmod_gradient_memory(self.handle, ckpt_count, ckpt_dtype)
 
     def forward(self, wavelet, traces, final_u=None, stream=None):
         mmod_forward(self.handle, wavelet, traces, final_u, stream)

@@ -1,0 +1,348 @@
+// Adjoint propagator, velocity gradient with checkpointing, FP64 dot product.
+//
+// Adjoint.  With D = 1 + e, E = 1 - e, C = dt^2 v^2, the transpose of the
+// forward map wavelet -> traces runs backward as
+//     D mu^n = 2 mu^{n+1} - E mu^{n+2} + L(C mu^{n+1}) + R^T r^{n-1}.
+// Multiplying by C shows that psi = C mu obeys the forward recurrence
+//     D psi^n = 2 psi^{n+1} - E psi^{n+2} + C L psi^{n+1} + C R^T r^{n-1},
+// so the adjoint reuses the forward step kernels run backward in time: the
+// receivers become injection points (scale c, no cell volume), the residual
+// reversed in time is their wavelet, and the sources are gathered; the
+// adjoint source is a[s][n] = psi^{n+1}(x_s) / (hx hy hz).
+//
+// Gradient.  dJ/dc(x) = sum_n mu^{n+1}(x) (L u^n + s^n)(x); with
+// C (L u^n + s^n) = D u^{n+1} - 2 u^n + E u^{n-1} this is the zero-lag
+// imaging condition sum_n psi^{n+1} (D u^{n+1} - 2 u^n + E u^{n-1}) / c^2,
+// and dJ/dv = 2 dt^2 v dJ/dc.  The forward states are recovered by two-level
+// checkpointing: the first sweep stores (u^{a-1}, u^a) at the start of each
+// of S segments of K steps (FP32, or BF16 / FP16 with one scale per z plane);
+// the backward sweep replays each segment from its checkpoint into K+2
+// stored volumes and runs the segment's adjoint steps against them.  Memory:
+// 2 S checkpoints + K + 2 volumes; work: two forward sweeps and one adjoint.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "mmod_handle.h"
+
+#define MMOD_API extern "C" __attribute__((visibility("default")))
+
+using namespace mmod;
+
+namespace {
+
+// ---- checkpoint storage: one scale per z plane, 16-bit values ------------
+
+template <class T>
+__device__ __forceinline__ T to_store(float v);
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <>
+__device__ __forceinline__ __half to_store<__half>(float v) { return __float2half_rn(v); }
+__device__ __forceinline__ float from_store(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float from_store(__half v) { return __half2float(v); }
+
+// One CTA per plane: scale = max |u| over the plane, stored = u / scale.
+template <class T>
+__global__ void compress_kernel(const float *__restrict__ u, long long plane, T *__restrict__ out,
+                                float *__restrict__ scale) {
+    const long long base = (long long)blockIdx.x * plane;
+    float m = 0.0f;
+    for (long long q = threadIdx.x; q < plane; q += blockDim.x) m = fmaxf(m, fabsf(u[base + q]));
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    __shared__ float part[32];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0f;
+        for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+        if (threadIdx.x == 0) part[0] = m;
+    }
+    __syncthreads();
+    const float s = part[0];
+    if (threadIdx.x == 0) scale[blockIdx.x] = s;
+    const float inv = s > 0.0f ? 1.0f / s : 0.0f;
+    for (long long q = threadIdx.x; q < plane; q += blockDim.x) out[base + q] = to_store<T>(u[base + q] * inv);
+}
+
+template <class T>
+__global__ void decompress_kernel(const T *__restrict__ in, const float *__restrict__ scale, long long plane,
+                                  float *__restrict__ u) {
+    const long long base = (long long)blockIdx.x * plane;
+    const float s = scale[blockIdx.x];
+    for (long long q = threadIdx.x; q < plane; q += blockDim.x) u[base + q] = from_store(in[base + q]) * s;
+}
+
+size_t ckpt_elem_bytes(int dtype) { return dtype == MMOD_CKPT_FP32 ? 4 : 2; }
+
+// Save the volume u as checkpoint volume slot (FP32: copy; 16-bit: compress).
+cudaError_t save_volume(mmod_handle *h, const float *u, int slot, cudaStream_t s) {
+    auto &gw = h->gw;
+    const size_t eb = ckpt_elem_bytes(gw.dtype);
+    char *dst = static_cast<char *>(gw.ckpt) + (size_t)slot * h->vol * eb;
+    if (gw.dtype == MMOD_CKPT_FP32)
+        return cudaMemcpyAsync(dst, u, sizeof(float) * (size_t)h->vol, cudaMemcpyDeviceToDevice, s);
+    float *sc = gw.ckpt_scale + (size_t)slot * h->cfg.nz;
+    if (gw.dtype == MMOD_CKPT_BF16)
+        compress_kernel<__nv_bfloat16><<<h->cfg.nz, 256, 0, s>>>(u, h->plane, reinterpret_cast<__nv_bfloat16 *>(dst), sc);
+    else
+        compress_kernel<__half><<<h->cfg.nz, 256, 0, s>>>(u, h->plane, reinterpret_cast<__half *>(dst), sc);
+    return cudaGetLastError();
+}
+
+cudaError_t restore_volume(mmod_handle *h, int slot, float *u, cudaStream_t s) {
+    auto &gw = h->gw;
+    const size_t eb = ckpt_elem_bytes(gw.dtype);
+    const char *src = static_cast<const char *>(gw.ckpt) + (size_t)slot * h->vol * eb;
+    if (gw.dtype == MMOD_CKPT_FP32)
+        return cudaMemcpyAsync(u, src, sizeof(float) * (size_t)h->vol, cudaMemcpyDeviceToDevice, s);
+    const float *sc = gw.ckpt_scale + (size_t)slot * h->cfg.nz;
+    if (gw.dtype == MMOD_CKPT_BF16)
+        decompress_kernel<__nv_bfloat16><<<h->cfg.nz, 256, 0, s>>>(reinterpret_cast<const __nv_bfloat16 *>(src), sc,
+                                                                    h->plane, u);
+    else
+        decompress_kernel<__half><<<h->cfg.nz, 256, 0, s>>>(reinterpret_cast<const __half *>(src), sc, h->plane, u);
+    return cudaGetLastError();
+}
+
+// Allocate (or keep) the gradient work space for S segments of K steps.
+mmod_status ensure_grad_work(mmod_handle *h, int nseg, int seglen, int dtype) {
+    auto &gw = h->gw;
+    if (gw.nseg == nseg && gw.seglen == seglen && gw.dtype == dtype) return MMOD_OK;
+    free_grad_work(h);
+    const size_t vb = sizeof(float) * (size_t)h->vol;
+    gw.seg.assign(seglen + 2, nullptr);
+    gw.seg_cur.resize(seglen + 2);
+    gw.seg_prev.resize(seglen + 2);
+    for (int i = 0; i < seglen + 2; ++i) {
+        MMOD_CK(h, cudaMalloc(&gw.seg[i], vb));
+        MMOD_CK(h, cudaMemset(gw.seg[i], 0, vb));
+        if (h->tma_ok && !encode_maps(h->cfg, h->nxp, gw.seg[i], &gw.seg_cur[i], &gw.seg_prev[i]))
+            return fail(h, MMOD_ERR_CUDA, "tensor map encoding failed for a segment buffer");
+    }
+    for (int b = 0; b < 2; ++b) {
+        MMOD_CK(h, cudaMalloc(&gw.psi[b], vb));
+        if (h->tma_ok && !encode_maps(h->cfg, h->nxp, gw.psi[b], &gw.psi_cur[b], &gw.psi_prev[b]))
+            return fail(h, MMOD_ERR_CUDA, "tensor map encoding failed for an adjoint buffer");
+    }
+    MMOD_CK(h, cudaMalloc(&gw.gradc, vb));
+    gw.ckpt_bytes = (size_t)nseg * 2 * (size_t)h->vol * ckpt_elem_bytes(dtype);
+    MMOD_CK(h, cudaMalloc(&gw.ckpt, gw.ckpt_bytes));
+    if (dtype != MMOD_CKPT_FP32) MMOD_CK(h, cudaMalloc(&gw.ckpt_scale, sizeof(float) * (size_t)nseg * 2 * h->cfg.nz));
+    gw.nseg = nseg;
+    gw.seglen = seglen;
+    gw.dtype = dtype;
+    return MMOD_OK;
+}
+
+// Device copy of an input array: device pointers pass through, host arrays go
+// through the staging buffer *stage (allocated on first use, n floats).
+mmod_status device_input(mmod_handle *h, const float *p, size_t n, float **stage, const float **out,
+                         cudaStream_t s) {
+    if (is_device_ptr(p)) {
+        *out = p;
+        return MMOD_OK;
+    }
+    if (!*stage) MMOD_CK(h, cudaMalloc(stage, sizeof(float) * std::max<size_t>(n, 1)));
+    if (n) MMOD_CK(h, cudaMemcpyAsync(*stage, p, sizeof(float) * n, cudaMemcpyHostToDevice, s));
+    *out = *stage;
+    return MMOD_OK;
+}
+
+}  // namespace
+
+namespace mmod {
+
+void free_grad_work(mmod_handle *h) {
+    auto &gw = h->gw;
+    for (float *p : gw.seg)
+        if (p) cudaFree(p);
+    gw.seg.clear();
+    gw.seg_cur.clear();
+    gw.seg_prev.clear();
+    for (float *&p : gw.psi) {
+        if (p) cudaFree(p);
+        p = nullptr;
+    }
+    if (gw.gradc) cudaFree(gw.gradc);
+    if (gw.ckpt) cudaFree(gw.ckpt);
+    if (gw.ckpt_scale) cudaFree(gw.ckpt_scale);
+    gw.gradc = nullptr;
+    gw.ckpt = nullptr;
+    gw.ckpt_scale = nullptr;
+    gw.nseg = gw.seglen = 0;
+    gw.dtype = -1;
+    gw.ckpt_bytes = 0;
+}
+
+}  // namespace mmod
+
+MMOD_API mmod_status mmod_adjoint(mmod_handle *h, const float *resid, float *adj_src, mmod_stream stream) {
+    if (!h) return MMOD_ERR_ARG;
+    if (mmod_status st = check_latched(h)) return st;
+    if (!h->model_set) return fail(h, MMOD_ERR_STATE, "mmod_set_model has not succeeded");
+    const auto &c = h->cfg;
+    if (c.nrec > 0 && c.nt > 0 && !resid) return fail(h, MMOD_ERR_ARG, "null residual with nrec > 0");
+    if (c.nsrc > 0 && c.nt > 0 && !adj_src) return fail(h, MMOD_ERR_ARG, "null adjoint source with nsrc > 0");
+    DeviceGuard guard(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nres = (size_t)c.nt * c.nrec, nadj = (size_t)c.nt * c.nsrc;
+    long long launches = 0;
+    const float *dres = nullptr;
+    if (mmod_status st = device_input(h, resid, nres, &h->st_tr, &dres, s)) return st;
+    if (!h->st_adjw) MMOD_CK(h, cudaMalloc(&h->st_adjw, sizeof(float) * std::max<size_t>(nres, 1)));
+    if (!h->st_adjg) MMOD_CK(h, cudaMalloc(&h->st_adjg, sizeof(float) * std::max<size_t>(nadj, 1)));
+    if (nres) MMOD_CK(h, launch_reverse_transpose(dres, c.nt, c.nrec, h->st_adjw, s));
+    MMOD_CK(h, cudaMemsetAsync(h->u[0], 0, sizeof(float) * (size_t)h->vol, s));
+    MMOD_CK(h, cudaMemsetAsync(h->u[1], 0, sizeof(float) * (size_t)h->vol, s));
+    h->state_pending = false;
+    if (c.nt > 0)
+        if (mmod_status st = run_loop_graph(h, h->g_adj, h->adj, h->st_adjw, c.nsrc > 0 ? h->st_adjg : nullptr, s,
+                                            &launches))
+            return st;
+    h->ran = false;   // the wavefield buffers now hold the adjoint state
+    if (nadj) {
+        const bool dev_out = is_device_ptr(adj_src);
+        float *dst = adj_src;
+        if (!dev_out) {
+            if (!h->st_adjo) MMOD_CK(h, cudaMalloc(&h->st_adjo, sizeof(float) * nadj));
+            dst = h->st_adjo;
+        }
+        MMOD_CK(h, launch_unreverse_transpose(h->st_adjg, c.nt, c.nsrc, 1.0 / (c.hx * c.hy * c.hz), dst, s));
+        ++launches;
+        if (!dev_out) {
+            MMOD_CK(h, cudaMemcpyAsync(adj_src, dst, sizeof(float) * nadj, cudaMemcpyDeviceToHost, s));
+            MMOD_CK(h, cudaStreamSynchronize(s));
+        }
+    }
+    h->last_launches = launches + (nres ? 1 : 0);
+    return check_latched(h);
+}
+
+MMOD_API mmod_status mmod_gradient(mmod_handle *h, const float *wavelet, const float *resid, float *grad_v,
+                                   int ckpt_count, int ckpt_dtype, mmod_stream stream) {
+    if (!h) return MMOD_ERR_ARG;
+    if (mmod_status st = check_latched(h)) return st;
+    if (!h->model_set) return fail(h, MMOD_ERR_STATE, "mmod_set_model has not succeeded");
+    const auto &c = h->cfg;
+    if (!grad_v) return fail(h, MMOD_ERR_ARG, "null gradient output");
+    if (ckpt_count < 1) return fail(h, MMOD_ERR_ARG, "ckpt_count must be >= 1");
+    if (ckpt_dtype != MMOD_CKPT_FP32 && ckpt_dtype != MMOD_CKPT_BF16 && ckpt_dtype != MMOD_CKPT_FP16)
+        return fail(h, MMOD_ERR_ARG, "unknown checkpoint type");
+    if (c.nsrc > 0 && c.nt > 0 && !wavelet) return fail(h, MMOD_ERR_ARG, "null wavelet with nsrc > 0");
+    if (c.nrec > 0 && c.nt > 0 && !resid) return fail(h, MMOD_ERR_ARG, "null residual with nrec > 0");
+    DeviceGuard guard(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nt = c.nt;
+    const int seglen = std::max(1, (nt + ckpt_count - 1) / ckpt_count);
+    const int nseg = nt > 0 ? (nt + seglen - 1) / seglen : 0;
+    if (mmod_status st = ensure_grad_work(h, std::max(nseg, 1), seglen, ckpt_dtype)) return st;
+    auto &gw = h->gw;
+    const bool tma = use_tma(h);
+    long long launches = 0;
+    const size_t vb = sizeof(float) * (size_t)h->vol;
+
+    const float *dwav = nullptr, *dres = nullptr;
+    if (mmod_status st = device_input(h, wavelet, (size_t)c.nsrc * nt, &h->st_wav, &dwav, s)) return st;
+    if (mmod_status st = device_input(h, resid, (size_t)c.nrec * nt, &h->st_tr, &dres, s)) return st;
+    const size_t nres = (size_t)nt * c.nrec;
+    if (!h->st_adjw) MMOD_CK(h, cudaMalloc(&h->st_adjw, sizeof(float) * std::max<size_t>(nres, 1)));
+    if (nres) MMOD_CK(h, launch_reverse_transpose(dres, nt, c.nrec, h->st_adjw, s));
+
+    // ---- sweep 1: forward with a checkpoint at the start of every segment
+    MMOD_CK(h, cudaMemsetAsync(h->u[0], 0, vb, s));
+    MMOD_CK(h, cudaMemsetAsync(h->u[1], 0, vb, s));
+    h->state_pending = false;
+    StepArgs fa = base_args(h, h->fwd, dwav);
+    fa.nrec = 0;   // no receivers in the gradient's forward sweeps
+    for (int sg = 0; sg < nseg; ++sg) {
+        const int a0 = sg * seglen, b0 = std::min(nt, a0 + seglen);
+        // at step a0: u^{a0-1} in u[a0 & 1], u^{a0} in u[(a0 + 1) & 1]
+        MMOD_CK(h, save_volume(h, h->u[a0 & 1], 2 * sg, s));
+        MMOD_CK(h, save_volume(h, h->u[(a0 + 1) & 1], 2 * sg + 1, s));
+        for (int n = a0; n < b0; ++n) {
+            fa.n = n;
+            fa.ucur = h->u[(n + 1) & 1];
+            fa.uprev = h->u[n & 1];
+            fa.uout = h->u[n & 1];
+            MMOD_CK(h, enqueue_step(h, fa, &h->cur_map[(n + 1) & 1], &h->prev_map[n & 1], tma, nullptr, s, &launches));
+        }
+    }
+
+    // ---- backward: replay each segment, then its adjoint steps + imaging
+    MMOD_CK(h, cudaMemsetAsync(gw.psi[0], 0, vb, s));
+    MMOD_CK(h, cudaMemsetAsync(gw.psi[1], 0, vb, s));
+    MMOD_CK(h, cudaMemsetAsync(gw.gradc, 0, vb, s));
+    StepArgs aa = base_args(h, h->adj, h->st_adjw);
+    aa.nrec = 0;
+    for (int sg = nseg - 1; sg >= 0; --sg) {
+        const int a0 = sg * seglen, b0 = std::min(nt, a0 + seglen);
+        MMOD_CK(h, restore_volume(h, 2 * sg, gw.seg[0], s));
+        MMOD_CK(h, restore_volume(h, 2 * sg + 1, gw.seg[1], s));
+        for (int n = a0; n < b0; ++n) {   // seg[j] holds u^{a0-1+j}
+            const int j = n - a0;
+            fa.n = n;
+            fa.ucur = gw.seg[j + 1];
+            fa.uprev = gw.seg[j];
+            fa.uout = gw.seg[j + 2];
+            MMOD_CK(h, enqueue_step(h, fa, tma ? &gw.seg_cur[j + 1] : nullptr, tma ? &gw.seg_prev[j] : nullptr, tma,
+                                    nullptr, s, &launches));
+        }
+        for (int n = b0 - 1; n >= a0; --n) {
+            const int m = nt - 1 - n;   // adjoint step m produces psi^{n+1}
+            const int j = n - a0;
+            aa.n = m;
+            aa.ucur = gw.psi[(m + 1) & 1];
+            aa.uprev = gw.psi[m & 1];
+            aa.uout = gw.psi[m & 1];
+            MMOD_CK(h, enqueue_step(h, aa, tma ? &gw.psi_cur[(m + 1) & 1] : nullptr,
+                                    tma ? &gw.psi_prev[m & 1] : nullptr, tma, nullptr, s, &launches));
+            MMOD_CK(h, launch_imaging(gw.psi[m & 1], gw.seg[j + 2], gw.seg[j + 1], gw.seg[j], h->c, aa.ex, aa.ey,
+                                      aa.ez, c.nx, c.ny, c.nz, h->nxp, gw.gradc, s));
+            ++launches;
+        }
+    }
+    h->ran = false;
+    // ---- dJ/dv = 2 dt^2 v dJ/dc
+    const size_t npts = (size_t)h->npts;
+    const bool dev_out = is_device_ptr(grad_v);
+    float *dst = grad_v;
+    if (!dev_out) {
+        if (!h->st_vol) MMOD_CK(h, cudaMalloc(&h->st_vol, sizeof(float) * npts));
+        dst = h->st_vol;
+    }
+    MMOD_CK(h, launch_grad_to_velocity(gw.gradc, h->vel_copy, c.nx, c.ny, c.nz, h->nxp, c.dt, dst, s));
+    ++launches;
+    if (!dev_out) {
+        MMOD_CK(h, cudaMemcpyAsync(grad_v, dst, sizeof(float) * npts, cudaMemcpyDeviceToHost, s));
+        MMOD_CK(h, cudaStreamSynchronize(s));
+    }
+    h->last_launches = launches;
+    return check_latched(h);
+}
+
+MMOD_API long long mmod_gradient_memory(const mmod_handle *h, int ckpt_count, int ckpt_dtype) {
+    if (!h || ckpt_count < 1) return -1;
+    const int nt = h->cfg.nt;
+    const int seglen = std::max(1, (nt + ckpt_count - 1) / ckpt_count);
+    const int nseg = nt > 0 ? (nt + seglen - 1) / seglen : 1;
+    const long long vb = 4LL * h->vol;
+    const long long eb = ckpt_dtype == MMOD_CKPT_FP32 ? 4 : 2;
+    return (long long)(seglen + 2 + 3) * vb + (long long)nseg * 2 * h->vol * eb +
+           (ckpt_dtype == MMOD_CKPT_FP32 ? 0 : 4LL * nseg * 2 * h->cfg.nz);
+}
+
+MMOD_API mmod_status mmod_dot(const float *a, const float *b, long long n, double *out, mmod_stream stream) {
+    if (!a || !b || !out || n < 0) return MMOD_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    double *d = nullptr;
+    if (cudaMallocAsync(&d, sizeof(double), s) != cudaSuccess) return MMOD_ERR_OOM;
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(double), s);
+    if (e == cudaSuccess) e = launch_dot(a, b, n, d, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, sizeof(double), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(d, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? MMOD_OK : MMOD_ERR_CUDA;
+}

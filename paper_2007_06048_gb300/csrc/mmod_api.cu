@@ -1,5 +1,7 @@
-// C ABI of the propagator (include/mmod.h): validation, the handle, staging of
-// host buffers, the CUDA-graph-captured time loop (Alg. 1) and error latching.
+// C ABI of the propagator (include/mmod.h): validation, the handle, the
+// source/receiver geometry, staging of host buffers, the CUDA-graph-captured
+// time loop (Alg. 1) and error latching.  The adjoint and gradient entry
+// points are in mmod_adjoint.cu.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -9,35 +11,13 @@
 #include <string>
 #include <vector>
 
-#include "mmod_internal.h"
-#include "tma_plan.h"
+#include "mmod_handle.h"
 
 #define MMOD_API extern "C" __attribute__((visibility("default")))
 
 using namespace mmod;
 
 namespace {
-
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int d) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != d) cudaSetDevice(d);
-    }
-    ~DeviceGuard() {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
-
-bool is_device_ptr(const void *p) {
-    if (!p) return false;
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
 
 // Defaults of the tuning options (see mmod_set_option).
 constexpr int kDefaultPdl = 1;   // measured +1% on 240^3
@@ -47,91 +27,6 @@ constexpr int kDefaultPdl = 1;   // measured +1% on 240^3
 thread_local char g_thread_err[256] = "";
 
 void set_thread_error_str(const std::string &msg) { set_thread_error(msg.c_str()); }
-
-}  // namespace
-
-struct mmod_handle {
-    mmod_config cfg{};
-    std::vector<int> src, rec;     // owned copies of the position lists
-    int device = 0;
-    int nxp = 0;
-    long long plane = 0, vol = 0;  // padded plane / volume, in floats
-    long long npts = 0;            // nx * ny * nz
-    Weights w{};
-
-    float *u[2] = {nullptr, nullptr};   // wavefields (padded)
-    float *c = nullptr;                 // dt^2 v^2 (padded)
-    float *eta = nullptr;               // dt * eta_x | dt * eta_y | dt * eta_z
-    int *src_kstart = nullptr, *src_i = nullptr, *src_j = nullptr, *src_k = nullptr,
-        *src_row = nullptr;
-    float *src_scale = nullptr;
-    long long *rec_off = nullptr;
-    unsigned int *vmax_bits = nullptr;
-    unsigned long long *bad = nullptr;
-
-    float *st_vol = nullptr;            // dense [nz][ny][nx] staging (lazy)
-    float *st_wav = nullptr;            // [nsrc][nt] staging (lazy)
-    float *st_tr = nullptr;             // [nt][nrec] staging (lazy)
-    int *err_host = nullptr;            // mapped pinned word: a kernel gave up waiting
-    int *err_dev = nullptr;
-
-    cudaStream_t cap = nullptr;         // private stream used only for graph capture
-    cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;   // bracket the step loop
-    cudaGraphExec_t gexec = nullptr;
-    const float *g_wav = nullptr;
-    float *g_tr = nullptr;
-    int g_kernel = -1;
-    long long g_launches = 0;
-
-    TmaPlan plans[kMaxTmaVariants]{};
-    int variant = -1;                   // -1: automatic choice
-    int pdl = kDefaultPdl;              // MMOD_OPT_PDL
-    int g_opts = -1;                    // options the cached graph was captured with
-    bool tma_ok = false;
-    CUtensorMap cur_map[2], prev_map[2], c_map;
-
-    bool model_set = false;
-    double vmax = 0.0;
-    bool state_pending = false;
-    bool ran = false;
-    int kernel = MMOD_KERNEL_AUTO;
-    long long last_launches = 0;
-    cudaError_t latched = cudaSuccess;
-    std::string err;
-};
-
-namespace {
-
-mmod_status fail(mmod_handle *h, mmod_status st, const std::string &msg) {
-    if (h) h->err = msg;
-    return st;
-}
-
-mmod_status fail_cuda(mmod_handle *h, cudaError_t e, const char *what) {
-    if (h) {
-        if (h->latched == cudaSuccess) h->latched = e;
-        h->err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
-    }
-    return e == cudaErrorMemoryAllocation ? MMOD_ERR_OOM : MMOD_ERR_CUDA;
-}
-
-#define CK(h, call)                                   \
-    do {                                              \
-        cudaError_t _e = (call);                      \
-        if (_e != cudaSuccess) return fail_cuda((h), _e, #call); \
-    } while (0)
-
-mmod_status check_latched(mmod_handle *h) {
-    if (h->err_host && *(volatile int *)h->err_host) {
-        h->err = "a step kernel gave up waiting for its copies (device-side timeout)";
-        return MMOD_ERR_TIMEOUT;
-    }
-    if (h->latched != cudaSuccess) {
-        h->err = std::string("earlier CUDA failure: ") + cudaGetErrorName(h->latched);
-        return MMOD_ERR_CUDA;
-    }
-    return MMOD_OK;
-}
 
 bool in_grid(const mmod_config &c, const int *p) {
     return p[0] >= 0 && p[0] < c.nx && p[1] >= 0 && p[1] < c.ny && p[2] >= 0 && p[2] < c.nz;
@@ -165,19 +60,106 @@ std::string validate(const mmod_config *c, mmod_status *st) {
     return "";
 }
 
+void free_inj(DevInj &t) {
+    for (int *p : {t.tile_start, t.pt_i, t.pt_j, t.pt_k, t.pt_first, t.src_row, t.src_i, t.src_j, t.src_k})
+        if (p) cudaFree(p);
+    if (t.pt_off) cudaFree(t.pt_off);
+    if (t.src_scale) cudaFree(t.src_scale);
+    t = DevInj();
+}
+
+void free_graph(GraphSlot &g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g = GraphSlot();
+}
+
 void free_all(mmod_handle *h) {
-    if (h->gexec) cudaGraphExecDestroy(h->gexec);
-    for (float *p : {h->u[0], h->u[1], h->c, h->eta, h->src_scale, h->st_vol, h->st_wav, h->st_tr})
+    free_graph(h->g_fwd);
+    free_graph(h->g_adj);
+    free_grad_work(h);
+    for (float *p : {h->u[0], h->u[1], h->c, h->eta, h->vel_copy, h->st_vol, h->st_wav, h->st_tr, h->st_adjw,
+                     h->st_adjg, h->st_adjo})
         if (p) cudaFree(p);
-    for (int *p : {h->src_kstart, h->src_i, h->src_j, h->src_k, h->src_row})
-        if (p) cudaFree(p);
-    if (h->rec_off) cudaFree(h->rec_off);
+    free_inj(h->fwd.inj);
+    free_inj(h->adj.inj);
+    if (h->fwd.gather_off) cudaFree(h->fwd.gather_off);
+    if (h->adj.gather_off) cudaFree(h->adj.gather_off);
     if (h->vmax_bits) cudaFree(h->vmax_bits);
     if (h->bad) cudaFree(h->bad);
     if (h->ev_t0) cudaEventDestroy(h->ev_t0);
     if (h->ev_t1) cudaEventDestroy(h->ev_t1);
     if (h->cap) cudaStreamDestroy(h->cap);
     if (h->err_host) cudaFreeHost(h->err_host);
+}
+
+template <class T>
+cudaError_t upload(T **dst, const std::vector<T> &v) {
+    const size_t n = std::max<size_t>(v.size(), 1);
+    cudaError_t e = cudaMalloc(dst, sizeof(T) * n);
+    if (e != cudaSuccess) return e;
+    if (v.empty()) return cudaMemset(*dst, 0, sizeof(T));
+    return cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+}
+
+// Injection table of the positions pos[n][3]: sources grouped by grid point
+// (stable order), points sorted by (plane, tile, j, i) and bucketed per
+// (plane, 64 x 16 tile).  src_row = index of the position in pos.
+cudaError_t build_inj(const mmod_config &c, long long plane, int nxp, const int *pos, int n, DevInj *t) {
+    t->tiles_x = (c.nx + kInjTileX - 1) / kInjTileX;
+    t->tiles_y = (c.ny + kInjTileY - 1) / kInjTileY;
+    const long long tiles = (long long)t->tiles_x * t->tiles_y;
+    auto bucket = [&](int s) {
+        const int *p = pos + 3 * s;
+        return ((long long)p[2] * t->tiles_y + p[1] / kInjTileY) * t->tiles_x + p[0] / kInjTileX;
+    };
+    std::vector<int> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        const long long ba = bucket(a), bb = bucket(b);
+        if (ba != bb) return ba < bb;
+        const int *pa = pos + 3 * a, *pb = pos + 3 * b;
+        if (pa[1] != pb[1]) return pa[1] < pb[1];
+        return pa[0] < pb[0];
+    });
+    std::vector<int> pt_i, pt_j, pt_k, pt_first, src_row(n), si(n), sj(n), sk(n);
+    std::vector<long long> pt_off;
+    std::vector<int> tile_start((size_t)(c.nz * tiles + 1), 0);
+    for (int q = 0; q < n; ++q) {
+        const int s = order[q];
+        const int *p = pos + 3 * s;
+        src_row[q] = s;
+        si[q] = p[0];
+        sj[q] = p[1];
+        sk[q] = p[2];
+        const bool same = q > 0 && std::memcmp(pos + 3 * order[q - 1], p, 3 * sizeof(int)) == 0;
+        if (!same) {
+            pt_i.push_back(p[0]);
+            pt_j.push_back(p[1]);
+            pt_k.push_back(p[2]);
+            pt_off.push_back((long long)p[2] * plane + (long long)p[1] * nxp + p[0]);
+            pt_first.push_back(q);
+            tile_start[(size_t)bucket(s) + 1]++;
+        }
+    }
+    pt_first.push_back(n);
+    for (size_t b = 1; b < tile_start.size(); ++b) tile_start[b] += tile_start[b - 1];
+    t->npts = (int)pt_i.size();
+    t->nsrc = n;
+    cudaError_t e;
+    if ((e = upload(&t->tile_start, tile_start)) || (e = upload(&t->pt_i, pt_i)) || (e = upload(&t->pt_j, pt_j)) ||
+        (e = upload(&t->pt_k, pt_k)) || (e = upload(&t->pt_off, pt_off)) || (e = upload(&t->pt_first, pt_first)) ||
+        (e = upload(&t->src_row, src_row)) || (e = upload(&t->src_i, si)) || (e = upload(&t->src_j, sj)) ||
+        (e = upload(&t->src_k, sk)))
+        return e;
+    e = cudaMalloc(&t->src_scale, sizeof(float) * std::max(n, 1));
+    if (e != cudaSuccess) return e;
+    return cudaMemset(t->src_scale, 0, sizeof(float) * std::max(n, 1));
+}
+
+cudaError_t build_gather(long long plane, int nxp, const int *pos, int n, long long **off) {
+    std::vector<long long> o(n);
+    for (int r = 0; r < n; ++r) o[r] = (long long)pos[3 * r + 2] * plane + (long long)pos[3 * r + 1] * nxp + pos[3 * r];
+    return upload(off, o);
 }
 
 }  // namespace
@@ -203,76 +185,162 @@ void damping_profile(int n, int nbl, double h, double vmax, double R, double dt,
     }
 }
 
-}  // namespace mmod
-
-namespace {
-
-StepArgs step_args(mmod_handle *h, const float *wavelet, float *traces, int n) {
-    StepArgs a{};
-    a.nx = h->cfg.nx; a.ny = h->cfg.ny; a.nz = h->cfg.nz;
-    a.nxp = h->nxp; a.plane = h->plane; a.nbl = h->cfg.nbl; a.nt = h->cfg.nt; a.n = n;
-    a.w = h->w;
-    a.ucur = h->u[(n + 1) & 1];
-    a.uprev = h->u[n & 1];
-    a.c = h->c;
-    a.ex = h->eta; a.ey = h->eta + h->cfg.nx; a.ez = h->eta + h->cfg.nx + h->cfg.ny;
-    a.src_kstart = h->src_kstart; a.src_i = h->src_i; a.src_j = h->src_j; a.src_row = h->src_row;
-    a.src_scale = h->src_scale; a.wavelet = wavelet;
-    a.nrec = h->cfg.nrec; a.rec_off = h->rec_off;
-    a.traces = (n >= 1 && traces) ? traces + (long long)(n - 1) * h->cfg.nrec : nullptr;
-    a.err = h->err_dev;
-    a.pdl = h->pdl;
-    return a;
+mmod_status fail(mmod_handle *h, mmod_status st, const std::string &msg) {
+    if (h) h->err = msg;
+    return st;
 }
 
-bool use_tma(const mmod_handle *h) {
-    return h->tma_ok && h->kernel != MMOD_KERNEL_SIMPLE;
+mmod_status fail_cuda(mmod_handle *h, cudaError_t e, const char *what) {
+    if (h) {
+        if (h->latched == cudaSuccess) h->latched = e;
+        h->err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    }
+    return e == cudaErrorMemoryAllocation ? MMOD_ERR_OOM : MMOD_ERR_CUDA;
 }
+
+mmod_status check_latched(mmod_handle *h) {
+    if (h->err_host && *(volatile int *)h->err_host) {
+        h->err = "a step kernel gave up waiting for its copies (device-side timeout)";
+        return MMOD_ERR_TIMEOUT;
+    }
+    if (h->latched != cudaSuccess) {
+        h->err = std::string("earlier CUDA failure: ") + cudaGetErrorName(h->latched);
+        return MMOD_ERR_CUDA;
+    }
+    return MMOD_OK;
+}
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+bool use_tma(const mmod_handle *h) { return h->tma_ok && h->kernel != MMOD_KERNEL_SIMPLE; }
 
 const TmaPlan &active_plan(const mmod_handle *h) {
     return h->plans[h->variant >= 0 ? h->variant : kTmaDefaultVariant];
 }
 
-// Enqueue the nt steps (and receiver gathers) on stream s.  Returns the
-// number of kernels launched.
-mmod_status enqueue_steps(mmod_handle *h, const float *wav, float *tr, cudaStream_t s, long long *nlaunch) {
-    const int nt = h->cfg.nt, nrec = h->cfg.nrec;
-    long long count = 0;
+// Step arguments shared by every step of a run (n, buffers and gathers are
+// filled per step).
+StepArgs base_args(mmod_handle *h, const Geometry &geo, const float *wavelet) {
+    StepArgs a{};
+    a.nx = h->cfg.nx; a.ny = h->cfg.ny; a.nz = h->cfg.nz;
+    a.nxp = h->nxp; a.plane = h->plane; a.nbl = h->cfg.nbl; a.nt = h->cfg.nt;
+    a.w = h->w;
+    a.c = h->c;
+    a.ex = h->eta; a.ey = h->eta + h->cfg.nx; a.ez = h->eta + h->cfg.nx + h->cfg.ny;
+    a.inj = geo.inj.view();
+    a.wavelet = wavelet;
+    a.nrec = geo.ngather; a.rec_off = geo.gather_off;
+    a.traces = nullptr;
+    a.err = h->err_dev;
+    a.pdl = h->pdl;
+    return a;
+}
+
+// Enqueue one step of a run on stream s.  Plain path: step kernel, then the
+// injection kernel, then (if plain_gather_dst) the receivers of u^{n+1}.
+// TMA path: one kernel (injection inside; receivers of u^n go to a.traces).
+cudaError_t enqueue_step(mmod_handle *h, const StepArgs &a, const CUtensorMap *cur, const CUtensorMap *prev,
+                         bool tma, float *plain_gather_dst, cudaStream_t s, long long *count) {
+    cudaError_t e;
+    if (tma) {
+        e = launch_step_tma(a, cur, prev, &h->c_map, active_plan(h), s);
+        ++*count;
+        return e;
+    }
+    StepArgs b = a;
+    b.traces = nullptr;
+    if ((e = launch_step_simple(b, s)) != cudaSuccess) return e;
+    ++*count;
+    if (a.inj.npts > 0) {
+        if ((e = launch_inject(b, s)) != cudaSuccess) return e;
+        ++*count;
+    }
+    if (plain_gather_dst && a.nrec > 0) {
+        if ((e = launch_gather(a.uout, a.rec_off, a.nrec, plain_gather_dst, s)) != cudaSuccess) return e;
+        ++*count;
+    }
+    return cudaSuccess;
+}
+
+// The time loop of a run from the state in u[0] (u^{-1}) and u[1] (u^0): nt
+// steps with the geometry geo, traces [nt][ngather] (nullable), bracketed by
+// the loop events.  Returns the number of kernels launched in *count.
+static mmod_status enqueue_loop(mmod_handle *h, const Geometry &geo, const float *wav, float *tr, cudaStream_t s,
+                                long long *count) {
+    const int nt = h->cfg.nt, ng = geo.ngather;
     const bool tma = use_tma(h);
-    CK(h, cudaEventRecordWithFlags(h->ev_t0, s, cudaEventRecordExternal));
+    *count = 0;
+    MMOD_CK(h, cudaEventRecordWithFlags(h->ev_t0, s, cudaEventRecordExternal));
+    StepArgs a = base_args(h, geo, wav);
     for (int n = 0; n < nt; ++n) {
-        StepArgs a = step_args(h, wav, tr, n);
-        if (tma) {
-            CK(h, launch_step_tma(a, &h->cur_map[(n + 1) & 1], &h->prev_map[n & 1], &h->c_map, active_plan(h), s));
-            ++count;
-        } else {
-            a.traces = nullptr;   // the plain path gathers with a separate kernel
-            CK(h, launch_step_simple(a, s));
-            ++count;
-            if (nrec > 0 && tr) {
-                CK(h, launch_gather(h->u[n & 1], h->rec_off, nrec, tr + (long long)n * nrec, s));
-                ++count;
-            }
-        }
+        a.n = n;
+        a.ucur = h->u[(n + 1) & 1];
+        a.uprev = h->u[n & 1];
+        a.uout = h->u[n & 1];
+        a.traces = (n >= 1 && tr && ng > 0) ? tr + (long long)(n - 1) * ng : nullptr;
+        MMOD_CK(h, enqueue_step(h, a, &h->cur_map[(n + 1) & 1], &h->prev_map[n & 1], tma,
+                                (tr && ng > 0) ? tr + (long long)n * ng : nullptr, s, count));
     }
-    if (tma && nt > 0 && nrec > 0 && tr) {
+    if (tma && nt > 0 && ng > 0 && tr) {
         // u^{nt} sits in u[(nt - 1) & 1]; the last step kernel had no successor
-        CK(h, launch_gather(h->u[(nt - 1) & 1], h->rec_off, nrec, tr + (long long)(nt - 1) * nrec, s));
-        ++count;
+        MMOD_CK(h, launch_gather(h->u[(nt - 1) & 1], geo.gather_off, ng, tr + (long long)(nt - 1) * ng, s));
+        ++*count;
     }
-    CK(h, cudaEventRecordWithFlags(h->ev_t1, s, cudaEventRecordExternal));
-    *nlaunch = count;
+    MMOD_CK(h, cudaEventRecordWithFlags(h->ev_t1, s, cudaEventRecordExternal));
     return MMOD_OK;
 }
 
-}  // namespace
+// Launch the cached graph of a loop, capturing it first when its inputs
+// changed.
+mmod_status run_loop_graph(mmod_handle *h, GraphSlot &g, const Geometry &geo, const float *wav, float *tr,
+                           cudaStream_t s, long long *launches) {
+    const int kern = use_tma(h) ? 100 + active_plan(h).variant : MMOD_KERNEL_SIMPLE;
+    const int opts = h->pdl;
+    const void *key[4] = {wav, tr, &geo, nullptr};
+    if (!g.exec || std::memcmp(g.key, key, sizeof(key)) != 0 || g.kernel != kern || g.opts != opts) {
+        free_graph(g);
+        cudaGraph_t graph = nullptr;
+        MMOD_CK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+        long long n_l = 0;
+        mmod_status st = enqueue_loop(h, geo, wav, tr, h->cap, &n_l);
+        cudaError_t e_end = cudaStreamEndCapture(h->cap, &graph);
+        if (st != MMOD_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e_end != cudaSuccess) return fail_cuda(h, e_end, "cudaStreamEndCapture");
+        cudaError_t e_inst = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e_inst != cudaSuccess) {
+            g.exec = nullptr;
+            return fail_cuda(h, e_inst, "cudaGraphInstantiate");
+        }
+        std::memcpy(g.key, key, sizeof(key));
+        g.kernel = kern;
+        g.opts = opts;
+        g.launches = n_l;
+    }
+    MMOD_CK(h, cudaGraphLaunch(g.exec, s));
+    *launches += g.launches;
+    return MMOD_OK;
+}
+
+}  // namespace mmod
 
 MMOD_API double mmod_cfl_dt(double cfl, double hmin, double vmax) {
     if (!(cfl > 0) || !(hmin > 0) || !(vmax > 0)) return -1.0;
     return cfl * hmin / vmax;
 }
 
-MMOD_API const char *mmod_version(void) { return "mmod-gb300 0.1 sm_103a"; }
+MMOD_API const char *mmod_version(void) { return "mmod-gb300 0.2 sm_103a"; }
 
 MMOD_API const char *mmod_last_error(const mmod_handle *h) { return h ? h->err.c_str() : g_thread_err; }
 
@@ -302,6 +370,7 @@ MMOD_API mmod_status mmod_create(const mmod_config *cfg, int device, mmod_handle
     if (!h) return MMOD_ERR_OOM;
     h->cfg = *cfg;
     h->device = device;
+    h->pdl = kDefaultPdl;
     h->src.assign(cfg->src_ijk, cfg->src_ijk + 3 * (size_t)cfg->nsrc);
     h->rec.assign(cfg->rec_ijk, cfg->rec_ijk + 3 * (size_t)cfg->nrec);
     h->cfg.src_ijk = h->src.data();
@@ -340,41 +409,15 @@ MMOD_API mmod_status mmod_create(const mmod_config *cfg, int device, mmod_handle
     CKC(cudaMemset(h->eta, 0, sizeof(float) * (size_t)(nx + ny + nz)));
     CKC(cudaMalloc(&h->vmax_bits, sizeof(unsigned int)));
     CKC(cudaMalloc(&h->bad, sizeof(unsigned long long)));
-
-    // Sources sorted by depth (stable: sources at one point keep their order).
-    const int nsrc = cfg->nsrc;
-    std::vector<int> order(nsrc);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return h->src[3 * a + 2] < h->src[3 * b + 2]; });
-    std::vector<int> kstart(nz + 1, 0), si(nsrc), sj(nsrc), sk(nsrc), srow(nsrc);
-    for (int t = 0; t < nsrc; ++t) {
-        const int s = order[t];
-        si[t] = h->src[3 * s]; sj[t] = h->src[3 * s + 1]; sk[t] = h->src[3 * s + 2]; srow[t] = s;
-        kstart[sk[t] + 1]++;
-    }
-    for (int k = 0; k < nz; ++k) kstart[k + 1] += kstart[k];
-    CKC(cudaMalloc(&h->src_kstart, sizeof(int) * (nz + 1)));
-    CKC(cudaMemcpy(h->src_kstart, kstart.data(), sizeof(int) * (nz + 1), cudaMemcpyHostToDevice));
-    const size_t sb = sizeof(int) * (size_t)std::max(nsrc, 1);
-    CKC(cudaMalloc(&h->src_i, sb));
-    CKC(cudaMalloc(&h->src_j, sb));
-    CKC(cudaMalloc(&h->src_k, sb));
-    CKC(cudaMalloc(&h->src_row, sb));
-    CKC(cudaMalloc(&h->src_scale, sizeof(float) * (size_t)std::max(nsrc, 1)));
-    if (nsrc) {
-        CKC(cudaMemcpy(h->src_i, si.data(), sizeof(int) * nsrc, cudaMemcpyHostToDevice));
-        CKC(cudaMemcpy(h->src_j, sj.data(), sizeof(int) * nsrc, cudaMemcpyHostToDevice));
-        CKC(cudaMemcpy(h->src_k, sk.data(), sizeof(int) * nsrc, cudaMemcpyHostToDevice));
-        CKC(cudaMemcpy(h->src_row, srow.data(), sizeof(int) * nsrc, cudaMemcpyHostToDevice));
-        CKC(cudaMemset(h->src_scale, 0, sizeof(float) * nsrc));
-    }
-    const int nrec = cfg->nrec;
-    std::vector<long long> roff(std::max(nrec, 1), 0);
-    for (int r = 0; r < nrec; ++r)
-        roff[r] = (long long)h->rec[3 * r + 2] * h->plane + (long long)h->rec[3 * r + 1] * h->nxp + h->rec[3 * r];
-    CKC(cudaMalloc(&h->rec_off, sizeof(long long) * roff.size()));
-    CKC(cudaMemcpy(h->rec_off, roff.data(), sizeof(long long) * roff.size(), cudaMemcpyHostToDevice));
-
+    // forward: sources injected, receivers gathered; adjoint: the reverse
+    CKC(build_inj(h->cfg, h->plane, h->nxp, h->src.data(), cfg->nsrc, &h->fwd.inj));
+    CKC(build_gather(h->plane, h->nxp, h->rec.data(), cfg->nrec, &h->fwd.gather_off));
+    h->fwd.ngather = cfg->nrec;
+    h->fwd.cell = cfg->hx * cfg->hy * cfg->hz;
+    CKC(build_inj(h->cfg, h->plane, h->nxp, h->rec.data(), cfg->nrec, &h->adj.inj));
+    CKC(build_gather(h->plane, h->nxp, h->src.data(), cfg->nsrc, &h->adj.gather_off));
+    h->adj.ngather = cfg->nsrc;
+    h->adj.cell = 1.0;
     CKC(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
     CKC(cudaEventCreate(&h->ev_t0));
     CKC(cudaEventCreate(&h->ev_t1));
@@ -447,18 +490,18 @@ MMOD_API mmod_status mmod_set_model(mmod_handle *h, const float *vel, mmod_strea
     const auto &c = h->cfg;
     const float *dvel = vel;
     if (!is_device_ptr(vel)) {
-        if (!h->st_vol) CK(h, cudaMalloc(&h->st_vol, sizeof(float) * (size_t)h->npts));
-        CK(h, cudaMemcpyAsync(h->st_vol, vel, sizeof(float) * (size_t)h->npts, cudaMemcpyHostToDevice, s));
+        if (!h->st_vol) MMOD_CK(h, cudaMalloc(&h->st_vol, sizeof(float) * (size_t)h->npts));
+        MMOD_CK(h, cudaMemcpyAsync(h->st_vol, vel, sizeof(float) * (size_t)h->npts, cudaMemcpyHostToDevice, s));
         dvel = h->st_vol;
     }
-    CK(h, cudaMemsetAsync(h->vmax_bits, 0, sizeof(unsigned int), s));
-    CK(h, cudaMemsetAsync(h->bad, 0, sizeof(unsigned long long), s));
-    CK(h, launch_model_scan(dvel, h->npts, h->vmax_bits, h->bad, s));
+    MMOD_CK(h, cudaMemsetAsync(h->vmax_bits, 0, sizeof(unsigned int), s));
+    MMOD_CK(h, cudaMemsetAsync(h->bad, 0, sizeof(unsigned long long), s));
+    MMOD_CK(h, launch_model_scan(dvel, h->npts, h->vmax_bits, h->bad, s));
     unsigned int vbits = 0;
     unsigned long long nbad = 0;
-    CK(h, cudaMemcpyAsync(&vbits, h->vmax_bits, sizeof(vbits), cudaMemcpyDeviceToHost, s));
-    CK(h, cudaMemcpyAsync(&nbad, h->bad, sizeof(nbad), cudaMemcpyDeviceToHost, s));
-    CK(h, cudaStreamSynchronize(s));
+    MMOD_CK(h, cudaMemcpyAsync(&vbits, h->vmax_bits, sizeof(vbits), cudaMemcpyDeviceToHost, s));
+    MMOD_CK(h, cudaMemcpyAsync(&nbad, h->bad, sizeof(nbad), cudaMemcpyDeviceToHost, s));
+    MMOD_CK(h, cudaStreamSynchronize(s));
     if (nbad) return fail(h, MMOD_ERR_ARG, std::to_string(nbad) + " velocities are not positive and finite");
     float vmaxf;
     std::memcpy(&vmaxf, &vbits, sizeof(vmaxf));
@@ -469,15 +512,18 @@ MMOD_API mmod_status mmod_set_model(mmod_handle *h, const float *vel, mmod_strea
         return fail(h, MMOD_ERR_UNSTABLE, "dt too large: dt*vmax*sqrt(sum 6.5016/h^2) = " +
                                               std::to_string(c.dt * vmax * std::sqrt(ksum)) + " > 2");
     }
-    CK(h, launch_model_fill(dvel, c.nx, c.ny, c.nz, h->nxp, c.dt, h->c, s));
-    CK(h, launch_source_scale(dvel, c.nx, c.ny, c.nsrc, h->src_i, h->src_j, h->src_k, c.dt,
-                              c.hx * c.hy * c.hz, h->src_scale, s));
+    MMOD_CK(h, launch_model_fill(dvel, c.nx, c.ny, c.nz, h->nxp, c.dt, h->c, s));
+    for (Geometry *g : {&h->fwd, &h->adj})
+        MMOD_CK(h, launch_source_scale(dvel, c.nx, c.ny, g->inj.nsrc, g->inj.src_i, g->inj.src_j, g->inj.src_k,
+                                       c.dt, g->cell, g->inj.src_scale, s));
+    if (!h->vel_copy) MMOD_CK(h, cudaMalloc(&h->vel_copy, sizeof(float) * (size_t)h->npts));
+    MMOD_CK(h, cudaMemcpyAsync(h->vel_copy, dvel, sizeof(float) * (size_t)h->npts, cudaMemcpyDeviceToDevice, s));
     std::vector<float> eta(c.nx + c.ny + c.nz);
     damping_profile(c.nx, c.nbl, c.hx, vmax, c.damp_R, c.dt, eta.data());
     damping_profile(c.ny, c.nbl, c.hy, vmax, c.damp_R, c.dt, eta.data() + c.nx);
     damping_profile(c.nz, c.nbl, c.hz, vmax, c.damp_R, c.dt, eta.data() + c.nx + c.ny);
-    CK(h, cudaMemcpyAsync(h->eta, eta.data(), sizeof(float) * eta.size(), cudaMemcpyHostToDevice, s));
-    CK(h, cudaStreamSynchronize(s));   // eta lives on the host stack
+    MMOD_CK(h, cudaMemcpyAsync(h->eta, eta.data(), sizeof(float) * eta.size(), cudaMemcpyHostToDevice, s));
+    MMOD_CK(h, cudaStreamSynchronize(s));   // eta lives on the host stack
     h->vmax = vmax;
     h->model_set = true;
     return MMOD_OK;
@@ -493,12 +539,12 @@ MMOD_API mmod_status mmod_set_state(mmod_handle *h, const float *u_prev, const f
     for (int b = 0; b < 2; ++b) {
         const float *d = src[b];
         if (d && !is_device_ptr(d)) {
-            if (!h->st_vol) CK(h, cudaMalloc(&h->st_vol, sizeof(float) * (size_t)h->npts));
-            CK(h, cudaMemcpyAsync(h->st_vol, d, sizeof(float) * (size_t)h->npts, cudaMemcpyHostToDevice, s));
+            if (!h->st_vol) MMOD_CK(h, cudaMalloc(&h->st_vol, sizeof(float) * (size_t)h->npts));
+            MMOD_CK(h, cudaMemcpyAsync(h->st_vol, d, sizeof(float) * (size_t)h->npts, cudaMemcpyHostToDevice, s));
             d = h->st_vol;
         }
         // buffer 0 holds u^{n-1}, buffer 1 holds u^n at step 0
-        CK(h, launch_pack(d, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->nxp, h->u[b], s));
+        MMOD_CK(h, launch_pack(d, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->nxp, h->u[b], s));
     }
     h->state_pending = true;
     return MMOD_OK;
@@ -517,12 +563,12 @@ MMOD_API mmod_status mmod_get_state(mmod_handle *h, float *u_prev, float *u_cur,
     for (int b = 0; b < 2; ++b) {
         if (!dst[b]) continue;
         if (is_device_ptr(dst[b])) {
-            CK(h, launch_unpack(bufs[b], h->cfg.nx, h->cfg.ny, h->cfg.nz, h->nxp, dst[b], s));
+            MMOD_CK(h, launch_unpack(bufs[b], h->cfg.nx, h->cfg.ny, h->cfg.nz, h->nxp, dst[b], s));
         } else {
-            if (!h->st_vol) CK(h, cudaMalloc(&h->st_vol, sizeof(float) * (size_t)h->npts));
-            CK(h, launch_unpack(bufs[b], h->cfg.nx, h->cfg.ny, h->cfg.nz, h->nxp, h->st_vol, s));
-            CK(h, cudaMemcpyAsync(dst[b], h->st_vol, sizeof(float) * (size_t)h->npts, cudaMemcpyDeviceToHost, s));
-            CK(h, cudaStreamSynchronize(s));
+            if (!h->st_vol) MMOD_CK(h, cudaMalloc(&h->st_vol, sizeof(float) * (size_t)h->npts));
+            MMOD_CK(h, launch_unpack(bufs[b], h->cfg.nx, h->cfg.ny, h->cfg.nz, h->nxp, h->st_vol, s));
+            MMOD_CK(h, cudaMemcpyAsync(dst[b], h->st_vol, sizeof(float) * (size_t)h->npts, cudaMemcpyDeviceToHost, s));
+            MMOD_CK(h, cudaStreamSynchronize(s));
         }
     }
     return MMOD_OK;
@@ -534,7 +580,7 @@ MMOD_API mmod_status mmod_forward(mmod_handle *h, const float *wavelet, float *t
     if (mmod_status st = check_latched(h)) return st;
     if (!h->model_set) return fail(h, MMOD_ERR_STATE, "mmod_set_model has not succeeded");
     const auto &c = h->cfg;
-    if (c.nsrc > 0 && !wavelet) return fail(h, MMOD_ERR_ARG, "null wavelet with nsrc > 0");
+    if (c.nsrc > 0 && c.nt > 0 && !wavelet) return fail(h, MMOD_ERR_ARG, "null wavelet with nsrc > 0");
     if (c.nrec > 0 && c.nt > 0 && !traces) return fail(h, MMOD_ERR_ARG, "null traces with nrec > 0");
     DeviceGuard guard(h->device);
     cudaStream_t s = (cudaStream_t)stream;
@@ -543,70 +589,39 @@ MMOD_API mmod_status mmod_forward(mmod_handle *h, const float *wavelet, float *t
     const float *dwav = wavelet;
     const size_t nwav = (size_t)c.nsrc * c.nt;
     if (c.nsrc > 0 && nwav > 0 && !is_device_ptr(wavelet)) {
-        if (!h->st_wav) CK(h, cudaMalloc(&h->st_wav, sizeof(float) * nwav));
-        CK(h, cudaMemcpyAsync(h->st_wav, wavelet, sizeof(float) * nwav, cudaMemcpyHostToDevice, s));
+        if (!h->st_wav) MMOD_CK(h, cudaMalloc(&h->st_wav, sizeof(float) * nwav));
+        MMOD_CK(h, cudaMemcpyAsync(h->st_wav, wavelet, sizeof(float) * nwav, cudaMemcpyHostToDevice, s));
         dwav = h->st_wav;
     }
     float *dtr = traces;
     const bool host_tr = c.nrec > 0 && c.nt > 0 && !is_device_ptr(traces);
     const size_t ntr = (size_t)c.nrec * c.nt;
     if (host_tr) {
-        if (!h->st_tr) CK(h, cudaMalloc(&h->st_tr, sizeof(float) * ntr));
+        if (!h->st_tr) MMOD_CK(h, cudaMalloc(&h->st_tr, sizeof(float) * ntr));
         dtr = h->st_tr;
     }
     if (!h->state_pending) {
-        CK(h, cudaMemsetAsync(h->u[0], 0, sizeof(float) * (size_t)h->vol, s));
-        CK(h, cudaMemsetAsync(h->u[1], 0, sizeof(float) * (size_t)h->vol, s));
+        MMOD_CK(h, cudaMemsetAsync(h->u[0], 0, sizeof(float) * (size_t)h->vol, s));
+        MMOD_CK(h, cudaMemsetAsync(h->u[1], 0, sizeof(float) * (size_t)h->vol, s));
     }
     h->state_pending = false;
-
-    if (c.nt > 0) {
-        const int kern = use_tma(h) ? 100 + active_plan(h).variant : MMOD_KERNEL_SIMPLE;
-        const int opts = h->pdl;
-        if (!h->gexec || h->g_wav != dwav || h->g_tr != dtr || h->g_kernel != kern || h->g_opts != opts) {
-            if (h->gexec) {
-                cudaGraphExecDestroy(h->gexec);
-                h->gexec = nullptr;
-            }
-            cudaGraph_t graph = nullptr;
-            CK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-            long long n_l = 0;
-            mmod_status st = enqueue_steps(h, dwav, dtr, h->cap, &n_l);
-            cudaError_t e_end = cudaStreamEndCapture(h->cap, &graph);
-            if (st != MMOD_OK) {
-                if (graph) cudaGraphDestroy(graph);
-                return st;
-            }
-            if (e_end != cudaSuccess) return fail_cuda(h, e_end, "cudaStreamEndCapture");
-            cudaError_t e_inst = cudaGraphInstantiate(&h->gexec, graph, 0);
-            cudaGraphDestroy(graph);
-            if (e_inst != cudaSuccess) {
-                h->gexec = nullptr;
-                return fail_cuda(h, e_inst, "cudaGraphInstantiate");
-            }
-            h->g_wav = dwav;
-            h->g_tr = dtr;
-            h->g_kernel = kern;
-            h->g_opts = opts;
-            h->g_launches = n_l;
-        }
-        CK(h, cudaGraphLaunch(h->gexec, s));
-        launches += h->g_launches;
-    }
+    if (c.nt > 0)
+        if (mmod_status st = run_loop_graph(h, h->g_fwd, h->fwd, dwav, c.nrec > 0 ? dtr : nullptr, s, &launches))
+            return st;
     h->ran = true;
     if (final_u) {
         const float *ufin = h->u[(c.nt + 1) & 1];
         if (is_device_ptr(final_u)) {
-            CK(h, launch_unpack(ufin, c.nx, c.ny, c.nz, h->nxp, final_u, s));
+            MMOD_CK(h, launch_unpack(ufin, c.nx, c.ny, c.nz, h->nxp, final_u, s));
         } else {
-            if (!h->st_vol) CK(h, cudaMalloc(&h->st_vol, sizeof(float) * (size_t)h->npts));
-            CK(h, launch_unpack(ufin, c.nx, c.ny, c.nz, h->nxp, h->st_vol, s));
-            CK(h, cudaMemcpyAsync(final_u, h->st_vol, sizeof(float) * (size_t)h->npts, cudaMemcpyDeviceToHost, s));
+            if (!h->st_vol) MMOD_CK(h, cudaMalloc(&h->st_vol, sizeof(float) * (size_t)h->npts));
+            MMOD_CK(h, launch_unpack(ufin, c.nx, c.ny, c.nz, h->nxp, h->st_vol, s));
+            MMOD_CK(h, cudaMemcpyAsync(final_u, h->st_vol, sizeof(float) * (size_t)h->npts, cudaMemcpyDeviceToHost, s));
         }
         ++launches;
     }
-    if (host_tr) CK(h, cudaMemcpyAsync(traces, dtr, sizeof(float) * ntr, cudaMemcpyDeviceToHost, s));
-    if (host_tr || (final_u && !is_device_ptr(final_u))) CK(h, cudaStreamSynchronize(s));
+    if (host_tr) MMOD_CK(h, cudaMemcpyAsync(traces, dtr, sizeof(float) * ntr, cudaMemcpyDeviceToHost, s));
+    if (host_tr || (final_u && !is_device_ptr(final_u))) MMOD_CK(h, cudaStreamSynchronize(s));
     h->last_launches = launches;
     return check_latched(h);
 }

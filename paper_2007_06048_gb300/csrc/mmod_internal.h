@@ -12,6 +12,22 @@
 
 namespace mmod {
 
+// Point sources grouped by grid point and bucketed per (plane, x-y tile) of
+// the TMA kernel (64 x 16 tiles): the points of plane k in tile (tx, ty) are
+// [tile_start[b], tile_start[b+1]), b = (k * tiles_y + ty) * tiles_x + tx.
+// Point p carries the sources [pt_first[p], pt_first[p+1]) in a fixed order.
+constexpr int kInjTileX = 64, kInjTileY = 16;
+
+struct InjTable {
+    const int *tile_start;      // [nz * tiles_y * tiles_x + 1]
+    const int *pt_i, *pt_j, *pt_k;
+    const long long *pt_off;    // padded offset of the point
+    const int *pt_first;        // [npts + 1]
+    const int *src_row;         // wavelet row of each source (point order)
+    const float *src_scale;     // injection scale of each source
+    int tiles_x, tiles_y, npts;
+};
+
 // Everything a step kernel needs; passed by value (kernel parameter space).
 struct StepArgs {
     int nx, ny, nz;            // grid
@@ -22,15 +38,12 @@ struct StepArgs {
     int n;                     // this step: computes u^{n+1}
     Weights w;                 // c_m / h_a^2
     const float *ucur;         // u^n       (padded layout)
-    float *uprev;              // u^{n-1} in, u^{n+1} out
+    const float *uprev;        // u^{n-1}
+    float *uout;               // u^{n+1}   (may be uprev: in-place rotation)
     const float *c;            // dt^2 v^2  (padded layout)
     const float *ex, *ey, *ez; // dt * eta per axis
-    // point sources, sorted by depth k: sources of plane k are
-    // [src_kstart[k], src_kstart[k+1])
-    const int *src_kstart;
-    const int *src_i, *src_j, *src_row;   // position and wavelet row
-    const float *src_scale;               // c(x_s) / (hx hy hz)
-    const float *wavelet;                 // [nsrc][nt]
+    InjTable inj;              // sources of this run
+    const float *wavelet;      // [rows][nt]
     // receivers: the kernel of step n copies u^n (its ucur) into traces[n-1]
     int nrec;
     const long long *rec_off;             // padded offsets
@@ -38,6 +51,19 @@ struct StepArgs {
     int *err;                             // device view of the mapped error word
     int pdl;                              // 1: launched as a programmatic dependent of the previous step
 };
+
+// Adds the sources of injection point p to u^{n+1} (already stored): the
+// point's damping factor r scales each term, sources in table order.
+__device__ __forceinline__ void inject_point(const StepArgs &a, int p) {
+    const int i = __ldg(a.inj.pt_i + p), j = __ldg(a.inj.pt_j + p), k = __ldg(a.inj.pt_k + p);
+    const float r = damp_factor(__fadd_rn(__fadd_rn(__ldg(a.ex + i), __ldg(a.ey + j)), __ldg(a.ez + k)));
+    float *dst = a.uout + __ldg(a.inj.pt_off + p);
+    float v = *dst;
+    for (int s = __ldg(a.inj.pt_first + p); s < __ldg(a.inj.pt_first + p + 1); ++s)
+        v = add_source(v, __ldg(a.inj.src_scale + s),
+                       __ldg(a.wavelet + (long long)__ldg(a.inj.src_row + s) * a.nt + a.n), r);
+    *dst = v;
+}
 
 // Host helpers shared by the entry points (mmod_api.cu).
 void damping_profile(int n, int nbl, double h, double vmax, double R, double dt, float *out);
@@ -52,6 +78,7 @@ constexpr double kSymbolMax8 = 2048.0 / 315.0;
 
 // Launchers (mmod_step_simple.cu, mmod_step_tma.cu, mmod_setup.cu).
 cudaError_t launch_step_simple(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_inject(const StepArgs &a, cudaStream_t s);   // all points, after a plain step
 cudaError_t launch_gather(const float *u, const long long *rec_off, int nrec, float *dst,
                           cudaStream_t s);
 
@@ -67,6 +94,18 @@ cudaError_t launch_model_fill(const float *vel, int nx, int ny, int nz, int nxp,
 cudaError_t launch_source_scale(const float *vel, int nx, int ny, int nsrc, const int *src_i,
                                 const int *src_j, const int *src_k, double dt, double cell,
                                 float *scale, cudaStream_t s);
+// Adjoint helpers: resid [nt][nrec] -> out [nrec][nt] reversed in time;
+// g [nt][nsrc] -> adj [nsrc][nt], adj[s][n] = g[nt-1-n][s] * scale.
+cudaError_t launch_reverse_transpose(const float *in, int nt, int ncol, float *out, cudaStream_t s);
+cudaError_t launch_unreverse_transpose(const float *g, int nt, int ncol, double scale, float *out,
+                                       cudaStream_t s);
+// Gradient helpers (mmod_setup.cu).
+cudaError_t launch_imaging(const float *psi, const float *u_next, const float *u_cur, const float *u_prev,
+                           const float *c, const float *ex, const float *ey, const float *ez, int nx, int ny,
+                           int nz, int nxp, float *grad_c, cudaStream_t s);
+cudaError_t launch_grad_to_velocity(const float *grad_c, const float *vel, int nx, int ny, int nz, int nxp,
+                                    double dt, float *grad_v, cudaStream_t s);
+cudaError_t launch_dot(const float *a, const float *b, long long n, double *out, cudaStream_t s);
 cudaError_t launch_pack(const float *dense, int nx, int ny, int nz, int nxp, float *padded,
                         cudaStream_t s);
 cudaError_t launch_unpack(const float *padded, int nx, int ny, int nz, int nxp, float *dense,

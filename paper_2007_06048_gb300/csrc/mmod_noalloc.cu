@@ -25,6 +25,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
 
 #include "mmod_internal.h"
@@ -44,10 +45,15 @@ constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t kOffU0 = 0;
 constexpr size_t kOffU1 = kOffU0 + align256(kMaxVolume * 4);
 constexpr size_t kOffC = kOffU1 + align256(kMaxVolume * 4);
+// Injection buckets (planes x 64x16 tiles) never exceed 32768 within the
+// limits above: the worst case is ny = 1, nz * nx / 64 <= 2^21 / 64.
+constexpr int kMaxBuckets = 32768;
 constexpr size_t kOffEta = kOffC + align256(kMaxVolume * 4);
-constexpr size_t kOffKstart = kOffEta + align256(3 * kMaxAxis * 4);
-constexpr size_t kOffSrc = kOffKstart + align256((kMaxAxis + 1) * 4);   // i, j, k, row
-constexpr size_t kOffScale = kOffSrc + align256(4 * kMaxSrc * 4);
+constexpr size_t kOffTiles = kOffEta + align256(3 * kMaxAxis * 4);
+constexpr size_t kOffTab = kOffTiles + align256((kMaxBuckets + 1) * 4);   // point and source tables
+constexpr size_t kTabInts = 8 * kMaxSrc + 1;   // pt_i, pt_j, pt_k, pt_first(+1), src_row, src_i, src_j, src_k
+constexpr size_t kOffPtOff = kOffTab + align256(kTabInts * 4);
+constexpr size_t kOffScale = kOffPtOff + align256(kMaxSrc * 8);
 constexpr size_t kOffRec = kOffScale + align256(kMaxSrc * 4);
 constexpr size_t kOffMisc = kOffRec + align256((size_t)kMaxRec * 8);   // vmax bits, bad count, error word
 constexpr size_t kScratchBytes = kOffMisc + 256;
@@ -165,36 +171,80 @@ extern "C" __attribute__((visibility("default"))) mmod_status mmod_forward_noall
     float *u[2] = {reinterpret_cast<float *>(base + kOffU0), reinterpret_cast<float *>(base + kOffU1)};
     float *cvol = reinterpret_cast<float *>(base + kOffC);
     float *eta = reinterpret_cast<float *>(base + kOffEta);
-    int *kstart = reinterpret_cast<int *>(base + kOffKstart);
-    int *src_tab = reinterpret_cast<int *>(base + kOffSrc);   // i | j | k | row, kMaxSrc each
+    int *tiles_d = reinterpret_cast<int *>(base + kOffTiles);
+    int *tab_d = reinterpret_cast<int *>(base + kOffTab);
+    long long *pt_off_d = reinterpret_cast<long long *>(base + kOffPtOff);
     float *src_scale = reinterpret_cast<float *>(base + kOffScale);
     long long *rec_off = reinterpret_cast<long long *>(base + kOffRec);
     unsigned int *vmax_bits = reinterpret_cast<unsigned int *>(base + kOffMisc);
     unsigned long long *bad = reinterpret_cast<unsigned long long *>(base + kOffMisc + 8);
     int *err = reinterpret_cast<int *>(base + kOffMisc + 16);
 
-    // ---- tables: sources sorted by depth (stable), receiver offsets
-    int order[kMaxSrc], si[4 * kMaxSrc] = {0};
+    // ---- injection table (sources grouped by point, bucketed per plane and
+    // 64 x 16 tile, as the handle API builds it) and receiver offsets
+    const int tiles_x = (c.nx + kInjTileX - 1) / kInjTileX, tiles_y = (c.ny + kInjTileY - 1) / kInjTileY;
+    const long long nbuckets = (long long)c.nz * tiles_x * tiles_y;
+    if (nbuckets > kMaxBuckets) return fail(MMOD_ERR_ARG, "grid exceeds the allocation-free limits (tile buckets)");
+    auto bucket = [&](int s) {
+        const int *p = c.src_ijk + 3 * s;
+        return ((long long)p[2] * tiles_y + p[1] / kInjTileY) * tiles_x + p[0] / kInjTileX;
+    };
+    auto before = [&](int a, int b) {   // strict order: bucket, j, i, then input order
+        const long long ba = bucket(a), bb = bucket(b);
+        if (ba != bb) return ba < bb;
+        const int *pa = c.src_ijk + 3 * a, *pb = c.src_ijk + 3 * b;
+        if (pa[1] != pb[1]) return pa[1] < pb[1];
+        if (pa[0] != pb[0]) return pa[0] < pb[0];
+        return a < b;
+    };
+    int order[kMaxSrc];
     for (int t = 0; t < c.nsrc; ++t) order[t] = t;
-    for (int t = 1; t < c.nsrc; ++t)   // insertion sort, stable
-        for (int q = t; q > 0 && c.src_ijk[3 * order[q - 1] + 2] > c.src_ijk[3 * order[q] + 2]; --q) {
+    for (int t = 1; t < c.nsrc; ++t)   // insertion sort (at most 64 entries)
+        for (int q = t; q > 0 && before(order[q], order[q - 1]); --q) {
             const int tmp = order[q];
             order[q] = order[q - 1];
             order[q - 1] = tmp;
         }
-    int ks[kMaxAxis + 1];
-    std::memset(ks, 0, sizeof(int) * (c.nz + 1));
-    for (int t = 0; t < c.nsrc; ++t) {
-        const int *p = c.src_ijk + 3 * order[t];
-        si[t] = p[0];
-        si[kMaxSrc + t] = p[1];
-        si[2 * kMaxSrc + t] = p[2];
-        si[3 * kMaxSrc + t] = order[t];
-        ks[p[2] + 1]++;
+    int tab[kTabInts] = {0};
+    int *pt_i = tab, *pt_j = tab + kMaxSrc, *pt_k = tab + 2 * kMaxSrc, *pt_first = tab + 3 * kMaxSrc;
+    int *src_row = tab + 4 * kMaxSrc + 1, *src_i = src_row + kMaxSrc, *src_j = src_i + kMaxSrc, *src_k = src_j + kMaxSrc;
+    long long pt_off[kMaxSrc] = {0}, pt_bucket[kMaxSrc] = {0};
+    int npt = 0;
+    for (int q = 0; q < c.nsrc; ++q) {
+        const int sidx = order[q];
+        const int *p = c.src_ijk + 3 * sidx;
+        src_row[q] = sidx;
+        src_i[q] = p[0];
+        src_j[q] = p[1];
+        src_k[q] = p[2];
+        const bool same = q > 0 && std::memcmp(c.src_ijk + 3 * order[q - 1], p, 3 * sizeof(int)) == 0;
+        if (!same) {
+            pt_i[npt] = p[0];
+            pt_j[npt] = p[1];
+            pt_k[npt] = p[2];
+            pt_off[npt] = (long long)p[2] * plane + (long long)p[1] * nxp + p[0];
+            pt_bucket[npt] = bucket(sidx);
+            pt_first[npt] = q;
+            ++npt;
+        }
     }
-    for (int k = 0; k < c.nz; ++k) ks[k + 1] += ks[k];
-    CKN(cudaMemcpyAsync(kstart, ks, sizeof(int) * (c.nz + 1), cudaMemcpyHostToDevice, s));
-    CKN(cudaMemcpyAsync(src_tab, si, sizeof(si), cudaMemcpyHostToDevice, s));
+    pt_first[npt] = c.nsrc;
+    CKN(cudaMemcpyAsync(tab_d, tab, sizeof(tab), cudaMemcpyHostToDevice, s));
+    CKN(cudaMemcpyAsync(pt_off_d, pt_off, sizeof(pt_off), cudaMemcpyHostToDevice, s));
+    CKN(cudaStreamSynchronize(s));   // the host tables above live on the stack
+    {
+        int chunk[1024];   // tile_start[b] = points in buckets < b
+        int ptr = 0;
+        for (long long b0 = 0; b0 <= nbuckets; b0 += 1024) {
+            const int n = (int)std::min<long long>(1024, nbuckets + 1 - b0);
+            for (int q = 0; q < n; ++q) {
+                while (ptr < npt && pt_bucket[ptr] < b0 + q) ++ptr;
+                chunk[q] = ptr;
+            }
+            CKN(cudaMemcpyAsync(tiles_d + b0, chunk, sizeof(int) * n, cudaMemcpyHostToDevice, s));
+            CKN(cudaStreamSynchronize(s));   // the chunk buffer is reused
+        }
+    }
     {
         long long chunk[1024];
         for (int r0 = 0; r0 < c.nrec; r0 += 1024) {
@@ -224,8 +274,11 @@ extern "C" __attribute__((visibility("default"))) mmod_status mmod_forward_noall
     const double ksum = kSymbolMax8 * (1.0 / (c.hx * c.hx) + 1.0 / (c.hy * c.hy) + 1.0 / (c.hz * c.hz));
     if (c.dt * vmax * std::sqrt(ksum) > 2.0) return fail(MMOD_ERR_UNSTABLE, "dt too large for the model (CFL bound)");
     CKN(launch_model_fill(vel, c.nx, c.ny, c.nz, nxp, c.dt, cvol, s));
-    CKN(launch_source_scale(vel, c.nx, c.ny, c.nsrc, src_tab, src_tab + kMaxSrc, src_tab + 2 * kMaxSrc, c.dt,
-                            c.hx * c.hy * c.hz, src_scale, s));
+    {
+        int *tab_src_i = tab_d + 4 * kMaxSrc + 1 + kMaxSrc;
+        CKN(launch_source_scale(vel, c.nx, c.ny, c.nsrc, tab_src_i, tab_src_i + kMaxSrc, tab_src_i + 2 * kMaxSrc,
+                                c.dt, c.hx * c.hy * c.hz, src_scale, s));
+    }
     float eta_h[3 * kMaxAxis];
     damping_profile(c.nx, c.nbl, c.hx, vmax, c.damp_R, c.dt, eta_h);
     damping_profile(c.ny, c.nbl, c.hy, vmax, c.damp_R, c.dt, eta_h + c.nx);
@@ -247,8 +300,13 @@ extern "C" __attribute__((visibility("default"))) mmod_status mmod_forward_noall
     }
     a.c = cvol;
     a.ex = eta; a.ey = eta + c.nx; a.ez = eta + c.nx + c.ny;
-    a.src_kstart = kstart; a.src_i = src_tab; a.src_j = src_tab + kMaxSrc; a.src_row = src_tab + 3 * kMaxSrc;
-    a.src_scale = src_scale; a.wavelet = wavelet;
+    a.inj.tile_start = tiles_d;
+    a.inj.pt_i = tab_d; a.inj.pt_j = tab_d + kMaxSrc; a.inj.pt_k = tab_d + 2 * kMaxSrc;
+    a.inj.pt_first = tab_d + 3 * kMaxSrc; a.inj.src_row = tab_d + 4 * kMaxSrc + 1;
+    a.inj.pt_off = pt_off_d; a.inj.src_scale = src_scale;
+    a.inj.tiles_x = tiles_x; a.inj.tiles_y = tiles_y; a.inj.npts = npt;
+    a.wavelet = wavelet;
+    a.pdl = 0;
     a.nrec = c.nrec; a.rec_off = rec_off;
     a.err = err;
     const bool want_tr = c.nrec > 0 && traces;
@@ -256,12 +314,14 @@ extern "C" __attribute__((visibility("default"))) mmod_status mmod_forward_noall
         a.n = n;
         a.ucur = u[(n + 1) & 1];
         a.uprev = u[n & 1];
+        a.uout = u[n & 1];
         if (tma) {
             a.traces = (n >= 1 && want_tr) ? traces + (long long)(n - 1) * c.nrec : nullptr;
             CKN(launch_step_tma(a, &cur_map[(n + 1) & 1], &prev_map[n & 1], &c_map, plans[kTmaDefaultVariant], s));
         } else {
             a.traces = nullptr;
             CKN(launch_step_simple(a, s));
+            if (npt > 0) CKN(launch_inject(a, s));
             if (want_tr) CKN(launch_gather(u[n & 1], rec_off, c.nrec, traces + (long long)n * c.nrec, s));
         }
     }

@@ -156,3 +156,127 @@ extern "C" __attribute__((visibility("default"))) int mmod_check_recip(int n, un
     cudaFree(d);
     return e == cudaSuccess ? MMOD_OK : MMOD_ERR_CUDA;
 }
+
+// ---------------------------------------------------------------------------
+// Adjoint and gradient helpers.
+// ---------------------------------------------------------------------------
+namespace mmod {
+namespace {
+
+// out[c][m] = in[nt-1-m][c]: the residual, reversed in time, as one row per
+// injection point (the wavelet layout of the adjoint run).
+__global__ void reverse_transpose_kernel(const float *__restrict__ in, int nt, int ncol, float *__restrict__ out) {
+    const long long total = (long long)nt * ncol;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int col = (int)(q / nt), m = (int)(q % nt);
+        out[q] = in[(long long)(nt - 1 - m) * ncol + col];
+    }
+}
+
+// adj[s][n] = g[nt-1-n][s] * scale.
+__global__ void unreverse_transpose_kernel(const float *__restrict__ g, int nt, int ncol, double scale,
+                                           float *__restrict__ adj) {
+    const long long total = (long long)nt * ncol;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int col = (int)(q / nt), n = (int)(q % nt);
+        adj[q] = (float)((double)g[(long long)(nt - 1 - n) * ncol + col] * scale);
+    }
+}
+
+// Zero-lag imaging condition of forward step n:
+//   grad_c += psi^{n+1} (D u^{n+1} - 2 u^n + E u^{n-1}) / c^2,
+// psi = c mu the adjoint wavefield, D = 1 + e, E = 1 - e.  Padding columns
+// are left untouched.
+__global__ void imaging_kernel(const float *__restrict__ psi, const float *__restrict__ un,
+                               const float *__restrict__ uc, const float *__restrict__ up,
+                               const float *__restrict__ c, const float *__restrict__ ex,
+                               const float *__restrict__ ey, const float *__restrict__ ez, int nx, int ny, int nz,
+                               int nxp, float *__restrict__ grad) {
+    const long long total = (long long)nxp * ny * nz;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(q % nxp);
+        if (i >= nx) continue;
+        const long long row = q / nxp;
+        const int j = (int)(row % ny), k = (int)(row / ny);
+        const float e = __fadd_rn(__fadd_rn(ex[i], ey[j]), ez[k]);
+        const float d2 = __fmaf_rn(__fadd_rn(1.0f, e), un[q],
+                                   __fmaf_rn(-2.0f, uc[q], __fmul_rn(__fsub_rn(1.0f, e), up[q])));
+        const float cc = c[q];
+        grad[q] = __fmaf_rn(psi[q], d2 / (cc * cc), grad[q]);
+    }
+}
+
+// grad_v = 2 dt^2 v grad_c (c = dt^2 v^2), dense output.
+__global__ void grad_to_velocity_kernel(const float *__restrict__ gc, const float *__restrict__ vel, int nx,
+                                        int ny, int nz, int nxp, double dt, float *__restrict__ gv) {
+    const long long total = (long long)nx * ny * nz;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(q % nx);
+        const long long row = q / nx;
+        gv[q] = (float)(2.0 * dt * dt * (double)vel[q] * (double)gc[row * nxp + i]);
+    }
+}
+
+// FP64 sum of a[i] * b[i] (block partials, then one atomic per block).
+__global__ void dot_kernel(const float *__restrict__ a, const float *__restrict__ b, long long n, double *out) {
+    double acc = 0.0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+        acc += (double)a[q] * (double)b[q];
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    __shared__ double part[32];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        acc = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (threadIdx.x == 0) atomicAdd(out, acc);
+    }
+}
+
+inline int grid2(long long n) {
+    long long b = (n + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    return b < 1 ? 1 : (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_reverse_transpose(const float *in, int nt, int ncol, float *out, cudaStream_t s) {
+    if ((long long)nt * ncol == 0) return cudaSuccess;
+    reverse_transpose_kernel<<<grid2((long long)nt * ncol), 256, 0, s>>>(in, nt, ncol, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unreverse_transpose(const float *g, int nt, int ncol, double scale, float *out,
+                                       cudaStream_t s) {
+    if ((long long)nt * ncol == 0) return cudaSuccess;
+    unreverse_transpose_kernel<<<grid2((long long)nt * ncol), 256, 0, s>>>(g, nt, ncol, scale, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_imaging(const float *psi, const float *u_next, const float *u_cur, const float *u_prev,
+                           const float *c, const float *ex, const float *ey, const float *ez, int nx, int ny,
+                           int nz, int nxp, float *grad_c, cudaStream_t s) {
+    imaging_kernel<<<grid2((long long)nxp * ny * nz), 256, 0, s>>>(psi, u_next, u_cur, u_prev, c, ex, ey, ez, nx,
+                                                                   ny, nz, nxp, grad_c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_to_velocity(const float *grad_c, const float *vel, int nx, int ny, int nz, int nxp,
+                                    double dt, float *grad_v, cudaStream_t s) {
+    grad_to_velocity_kernel<<<grid2((long long)nx * ny * nz), 256, 0, s>>>(grad_c, vel, nx, ny, nz, nxp, dt,
+                                                                           grad_v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dot(const float *a, const float *b, long long n, double *out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    dot_kernel<<<grid2(n), 256, 0, s>>>(a, b, n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace mmod

@@ -1,7 +1,8 @@
 // Plain step kernel: one thread per grid point, neighbours read straight from
 // global memory (L1/L2 cached), u = 0 outside the grid by explicit bounds
-// tests.  It performs exactly the FP32 operations of the TMA kernel in the
-// same order (stencil.cuh), so the two agree bit for bit; it is the
+// tests, then a separate injection kernel adds the sources.  It performs
+// exactly the FP32 operations of the TMA kernel in the same order
+// (stencil.cuh, inject_point), so the two agree bit for bit; it is the
 // validation kernel (MMOD_KERNEL_SIMPLE), not the fast path.
 #include "mmod_internal.h"
 
@@ -34,13 +35,13 @@ __global__ void __launch_bounds__(128) step_simple_kernel(const StepArgs a) {
     }
     const float lap = lap_sum(lx, ly, lz);
     const float e = __fadd_rn(__fadd_rn(__ldg(a.ex + i), __ldg(a.ey + j)), __ldg(a.ez + k));
-    const float r = damp_factor(e);
-    float out = __fmul_rn(num_damped(two_p, a.uprev[o], __ldg(a.c + o), lap, e), r);
-    for (int t = __ldg(a.src_kstart + k); t < __ldg(a.src_kstart + k + 1); ++t)
-        if (__ldg(a.src_i + t) == i && __ldg(a.src_j + t) == j)
-            out = add_source(out, __ldg(a.src_scale + t),
-                             __ldg(a.wavelet + (long long)__ldg(a.src_row + t) * a.nt + a.n), r);
-    a.uprev[o] = out;
+    a.uout[o] = __fmul_rn(num_damped(two_p, a.uprev[o], __ldg(a.c + o), lap, e), damp_factor(e));
+}
+
+// Sources, after the step: one thread per injection point (stencil order).
+__global__ void inject_kernel(const StepArgs a) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < a.inj.npts; p += gridDim.x * blockDim.x)
+        inject_point(a, p);
 }
 
 __global__ void gather_kernel(const float *__restrict__ u, const long long *__restrict__ off, int nrec,
@@ -56,6 +57,14 @@ cudaError_t launch_step_simple(const StepArgs &a, cudaStream_t s) {
     dim3 block(32, 4);
     dim3 grid((a.nx + 31) / 32, (a.ny + 3) / 4, a.nz);
     step_simple_kernel<<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inject(const StepArgs &a, cudaStream_t s) {
+    if (a.inj.npts <= 0) return cudaSuccess;
+    int blocks = (a.inj.npts + 127) / 128;
+    if (blocks > 1024) blocks = 1024;
+    inject_kernel<<<blocks, 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -174,28 +174,6 @@ __device__ __forceinline__ float2 pair_acc2(float2 acc, float2 w, float2 a, floa
     return __ffma2_rn(w, __fadd2_rn(__fadd2_rn(a, b), neg_two_p), acc);
 }
 
-// Sources of plane k that fall on this thread's points (rare: one plane per
-// source).  Each thread re-reads the value it has just stored, so program
-// order makes it visible; the term is scaled by the point's damping factor.
-template <int RY>
-__device__ __noinline__ void add_plane_sources(const StepArgs &a, int k, int s_lo, int s_hi, int x, int y0,
-                                               float2 exr, const float (&eyr)[RY], float ez) {
-    for (int s = s_lo; s < s_hi; ++s) {
-        const int si = __ldg(a.src_i + s), sj = __ldg(a.src_j + s);
-        const int r = sj - y0;
-        if ((si != x && si != x + 1) || r < 0 || r >= RY) continue;
-        const float ex = si == x ? exr.x : exr.y;
-        float ey = eyr[0];
-#pragma unroll
-        for (int i = 1; i < RY; ++i)
-            if (r == i) ey = eyr[i];
-        const float e = __fadd_rn(__fadd_rn(ex, ey), ez);
-        float *dst = a.uprev + (long long)k * a.plane + (long long)sj * a.nxp + si;
-        const float wv = __ldg(a.wavelet + (long long)__ldg(a.src_row + s) * a.nt + a.n);
-        *dst = add_source(*dst, __ldg(a.src_scale + s), wv, damp_factor(e));
-    }
-}
-
 struct Wts {
     float2 x2, x4, y[kRadius], z[kRadius];   // broadcast pairs of w_am
     float x1, x3;
@@ -203,16 +181,12 @@ struct Wts {
 
 // Per-plane values every thread needs, loaded one step ahead.
 struct PlaneInfo {
-    float ez;      // dt * eta_z(k)
-    int s_lo, s_hi;  // sources of plane k
+    float ez;        // dt * eta_z(k)
 };
 
 __device__ __forceinline__ PlaneInfo plane_info(const StepArgs &a, int k) {
     PlaneInfo p;
-    const int kk = min(k, a.nz - 1);
-    p.ez = __ldg(a.ez + kk);
-    p.s_lo = __ldg(a.src_kstart + kk);
-    p.s_hi = __ldg(a.src_kstart + kk + 1);
+    p.ez = __ldg(a.ez + min(k, a.nz - 1));
     return p;
 }
 
@@ -240,7 +214,7 @@ __device__ __forceinline__ void step(const StepArgs &a, const Ctx &c, int t, flo
     const float *upp = c.up + (t % S::NSC) * S::PC + (RY * c.warp) * TX + 2 * c.lane;
     const float *ccp = c.cc + (t % S::NSC) * S::PC + (RY * c.warp) * TX + 2 * c.lane;
     const bool damped = xy_damped || k < a.nbl || k > a.nz - 1 - a.nbl;
-    const long long koff = (long long)k * a.plane;
+    const long long koff = (long long)k * a.plane;   // out_row already points into uout
 #pragma unroll
     for (int r = 0; r < RY; ++r) {
         // x neighbours: columns 2*lane .. 2*lane+9 of row 4+RY*w+r, as 5 aligned pairs
@@ -283,8 +257,6 @@ __device__ __forceinline__ void step(const StepArgs &a, const Ctx &c, int t, flo
                 dst[0] = num.x;
         }
     }
-    if (pi.s_lo < pi.s_hi)
-        add_plane_sources<RY>(a, k, pi.s_lo, pi.s_hi, c.x0 + 2 * c.lane, c.y0 + RY * c.warp, exr, eyr, pi.ez);
 }
 
 template <class S>
@@ -364,7 +336,7 @@ __global__ void __launch_bounds__(S::NT)
     for (int r = 0; r < RY; ++r) {
         const int y = c.y0 + RY * c.warp + r;
         eyr[r] = y < a.ny ? __ldg(a.ey + y) : 0.0f;
-        out_row[r] = (y < a.ny && x < a.nx) ? a.uprev + (long long)y * a.nxp + x : nullptr;
+        out_row[r] = (y < a.ny && x < a.nx) ? a.uout + (long long)y * a.nxp + x : nullptr;
     }
     const bool xy_damped = c.x0 < a.nbl || c.x0 + TX - 1 > a.nx - 1 - a.nbl || c.y0 < a.nbl ||
                            c.y0 + S::TY - 1 > a.ny - 1 - a.nbl;
@@ -435,6 +407,20 @@ __global__ void __launch_bounds__(S::NT)
         }
 #undef MMOD_STEP
     }
+    // Sources of this CTA's tile and planes: nothing in this launch reads the
+    // u^{n+1} it writes, so they are added once the whole z range is stored
+    // (the block barrier makes every thread's stores visible).  One warp per
+    // plane, one lane per injection point.
+    __syncthreads();
+    if (!*c.abort_flag) {
+        const int tile = (c.y0 / kInjTileY) * a.inj.tiles_x + c.x0 / kInjTileX;
+        const int per_plane = a.inj.tiles_y * a.inj.tiles_x;
+        for (int k = c.z0 + c.warp; k < c.z0 + T; k += S::NWARP) {
+            const int lo = __ldg(a.inj.tile_start + k * per_plane + tile);
+            const int hi = __ldg(a.inj.tile_start + k * per_plane + tile + 1);
+            for (int p = lo + c.lane; p < hi; p += 32) inject_point(a, p);
+        }
+    }
     // After a give-up, wait (bounded) for the copies this CTA still has in
     // flight (the latest sequence of every slot) before its shared memory is
     // released.
@@ -479,6 +465,7 @@ bool encode(CUtensorMap *map, const float *base, const mmod_config &cfg, int nxp
 
 // Compiled variants.  All use tile height 16 (the tensor maps' box).
 constexpr int kTY = 16;
+static_assert(kTY == kInjTileY && TX == kInjTileX, "injection buckets must match the kernel's tiles");
 using V22_1 = Shape<kTY, 2, 1>;
 using V22_2 = Shape<kTY, 2, 2>;
 using V22_4 = Shape<kTY, 2, 4>;
@@ -511,6 +498,10 @@ constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 int tma_variant_count() { return kNumVariants; }
 
 const char *tma_variant_name(int v) { return (v >= 0 && v < kNumVariants) ? kVariants[v].name : ""; }
+
+bool encode_maps(const mmod_config &cfg, int nxp, const float *buf, CUtensorMap *cur, CUtensorMap *prev) {
+    return encode(cur, buf, cfg, nxp, HX, kTY + 2 * kRadius) && encode(prev, buf, cfg, nxp, TX, kTY);
+}
 
 bool make_tma_plan(const mmod_config &cfg, int nxp, float *const u[2], const float *c, CUtensorMap cur_map[2],
                    CUtensorMap prev_map[2], CUtensorMap *c_map, TmaPlan plans[]) {

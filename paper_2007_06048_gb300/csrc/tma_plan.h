@@ -28,6 +28,10 @@ const char *tma_variant_name(int v);
 // Encodes the tensor maps of both wavefield buffers and of the coefficient
 // volume and fills one plan per compiled variant.  Returns false when the TMA
 // kernel cannot serve the grid (the caller then uses the plain kernel).
+// Tensor maps of one padded volume buffer as the kernel's u^n (halo box) and
+// u^{n-1} (tile box) operand.
+bool encode_maps(const mmod_config &cfg, int nxp, const float *buf, CUtensorMap *cur, CUtensorMap *prev);
+
 bool make_tma_plan(const mmod_config &cfg, int nxp, float *const u[2], const float *c, CUtensorMap cur_map[2],
                    CUtensorMap prev_map[2], CUtensorMap *c_map, TmaPlan plans[]);
 

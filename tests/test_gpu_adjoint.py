@@ -1,0 +1,156 @@
+"""GPU adjoint and velocity gradient against the FP64 oracle.
+
+Tolerances (relative L2 over the whole array, FP64 norms):
+  adjoint source (transpose of the forward map), <= 100 steps: 1e-5, as the
+  forward parity gate (the adjoint runs the same FP32 step kernels);
+  gradient, FP32 checkpoints: 1e-4 — the imaging condition subtracts nearly
+  equal FP32 wavefields (D u^{n+1} - 2 u^n + E u^{n-1}), which costs about
+  two decimal digits against the oracle's L u^n + s^n; the measured error
+  is reported by test_gradient_checkpoint_precision;
+  16-bit checkpoints: the replayed forward starts from rounded states, so the
+  gradient moves by ~ the storage precision (BF16 8 bits, FP16 11 bits of
+  mantissa after per-plane scaling): gates 2e-2 (BF16) and 3e-3 (FP16).
+Dot-product test: <F w, r> = <w, F^T r> with FP32 operators and FP64 sums
+(mmod_dot) to 1e-6 relative.
+"""
+import numpy as np
+import pytest
+
+import paper_2007_06048_gb300 as M
+import workloads as W
+from _gpu_util import rel_l2, run_gpu, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _problem(shape=(24, 26, 70), nt=90, nbl=4, nsrc=2, nrec=40, seed=13):
+    p = W.tiny_problem(shape=shape, nt=nt, nbl=nbl, nsrc=nsrc, nrec=nrec, seed=seed)
+    nz, ny, nx = shape
+    p.rec_ijk[1] = p.rec_ijk[0]                      # duplicated receiver
+    p.rec_ijk[2:22] = [[i, ny // 2, 1] for i in range(3, 23)]   # a dense line in one plane
+    return p
+
+
+def _gpu_adjoint(p, resid, kernel=M.KERNEL_AUTO):
+    torch = torch_cuda()
+    prop = M.Propagator.from_problem(p)
+    if kernel != M.KERNEL_AUTO:
+        prop.set_kernel(kernel)
+    prop.set_model(torch.from_numpy(p.vel).cuda())
+    r = torch.from_numpy(np.ascontiguousarray(resid, np.float32)).cuda()
+    adj = torch.zeros((len(p.src_ijk), p.nt), device="cuda")
+    prop.adjoint(r, adj)
+    torch.cuda.synchronize()
+    return adj.cpu().numpy(), prop
+
+
+def test_adjoint_matches_oracle(orc):
+    p = _problem()
+    rng = np.random.default_rng(3)
+    resid = rng.standard_normal((p.nt, len(p.rec_ijk))).astype(np.float32)
+    a_gpu, _ = _gpu_adjoint(p, resid)
+    a_orc = orc.adjoint(p.vel, p.h, p.dt, p.nt, nbl=p.nbl, src_ijk=p.src_ijk, rec_ijk=p.rec_ijk, resid=resid)
+    assert rel_l2(a_gpu, a_orc) <= 1e-5
+
+
+def test_adjoint_plain_and_tma_kernels_agree_bitwise():
+    p = _problem(shape=(33, 40, 131), nt=40, nrec=60, seed=5)
+    resid = np.random.default_rng(1).standard_normal((p.nt, len(p.rec_ijk))).astype(np.float32)
+    a_t, _ = _gpu_adjoint(p, resid, M.KERNEL_TMA)
+    a_s, _ = _gpu_adjoint(p, resid, M.KERNEL_SIMPLE)
+    assert np.array_equal(a_t, a_s)
+
+
+def test_dot_product_fp64_sums():
+    """<F w, r> = <w, F^T r> with the FP32 GPU operators, sums in FP64 on the GPU."""
+    torch = torch_cuda()
+    p = _problem(shape=(40, 44, 64), nt=120, nrec=50, seed=21)
+    rng = np.random.default_rng(4)
+    w = torch.from_numpy(rng.standard_normal((len(p.src_ijk), p.nt)).astype(np.float32)).cuda()
+    r = torch.from_numpy(rng.standard_normal((p.nt, len(p.rec_ijk))).astype(np.float32)).cuda()
+    prop = M.Propagator.from_problem(p)
+    prop.set_model(torch.from_numpy(p.vel).cuda())
+    Fw = torch.zeros((p.nt, len(p.rec_ijk)), device="cuda")
+    prop.forward(w, Fw)
+    FTr = torch.zeros((len(p.src_ijk), p.nt), device="cuda")
+    prop.adjoint(r, FTr)
+    lhs = M.mmod_dot(Fw, r)
+    rhs = M.mmod_dot(w, FTr)
+    assert abs(lhs - rhs) <= 1e-6 * abs(lhs), (lhs, rhs)
+
+
+def test_many_sources_with_duplicates_forward(orc):
+    p = W.tiny_problem(shape=(20, 50, 70), nt=30, nbl=3, nsrc=300, nrec=7, seed=9)
+    p.src_ijk[5] = p.src_ijk[4]
+    p.src_ijk[6] = p.src_ijk[4]
+    tr_o, _, u_o = orc.forward(p.vel, p.h, p.dt, p.nt, nbl=p.nbl, src_ijk=p.src_ijk, wavelet=p.wavelet,
+                               rec_ijk=p.rec_ijk, want_state=True)
+    tr_g, u_g, _ = run_gpu(p)
+    assert rel_l2(u_g, u_o) <= 1e-5
+    tr_s, u_s, _ = run_gpu(p, kernel=M.KERNEL_SIMPLE)
+    assert np.array_equal(u_s, u_g) and np.array_equal(tr_s, tr_g)
+
+
+def _gradient_case(nt=80):
+    p = W.tiny_problem(shape=(26, 28, 30), nt=nt, nbl=5, nsrc=1, nrec=30, seed=31)
+    p.vel = np.round(p.vel).astype(np.float32)
+    p.src_ijk[0] = [15, 14, 3]
+    p.rec_ijk[:] = [[3 + (r % 6) * 4, 4 + (r // 6) * 4, 1] for r in range(30)]
+    p.wavelet = W.ricker(30.0, p.dt, nt)[None, :]
+    return p
+
+
+def _gpu_gradient(p, resid, ckpt, dtype):
+    torch = torch_cuda()
+    prop = M.Propagator.from_problem(p)
+    prop.set_model(torch.from_numpy(p.vel).cuda())
+    g = torch.zeros(p.vel.shape, device="cuda")
+    prop.gradient(torch.from_numpy(p.wavelet).cuda(), torch.from_numpy(resid.astype(np.float32)).cuda(), g,
+                  ckpt, dtype)
+    torch.cuda.synchronize()
+    return g.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def grad_ref(orc):
+    p = _gradient_case()
+    vel_true = (p.vel * 1.04).astype(np.float32)
+    d_obs = orc.forward(vel_true, p.h, p.dt, p.nt, nbl=p.nbl, src_ijk=p.src_ijk, wavelet=p.wavelet, rec_ijk=p.rec_ijk)
+    tr = orc.forward(p.vel, p.h, p.dt, p.nt, nbl=p.nbl, src_ijk=p.src_ijk, wavelet=p.wavelet, rec_ijk=p.rec_ijk)
+    resid = tr - d_obs
+    g = orc.gradient(p.vel, p.h, p.dt, p.nt, nbl=p.nbl, src_ijk=p.src_ijk, wavelet=p.wavelet, rec_ijk=p.rec_ijk,
+                     resid=resid)
+    return p, resid, g
+
+
+def test_gradient_fp32_checkpoints_matches_oracle(grad_ref):
+    p, resid, g_o = grad_ref
+    g = _gpu_gradient(p, resid, 8, M.CKPT_FP32)
+    assert np.abs(g_o).max() > 0
+    assert rel_l2(g, g_o) <= 1e-4
+
+
+def test_gradient_fp32_is_independent_of_the_checkpoint_count(grad_ref):
+    p, resid, _ = grad_ref
+    ref = _gpu_gradient(p, resid, 1, M.CKPT_FP32)
+    for ck in (3, 8, p.nt):
+        assert np.array_equal(_gpu_gradient(p, resid, ck, M.CKPT_FP32), ref), ck
+
+
+@pytest.mark.parametrize("dtype,gate", [(M.CKPT_BF16, 2e-2), (M.CKPT_FP16, 3e-3)])
+def test_gradient_checkpoint_precision(grad_ref, dtype, gate):
+    p, resid, g_o = grad_ref
+    g = _gpu_gradient(p, resid, 8, dtype)
+    err = rel_l2(g, g_o)
+    print(f"checkpoint dtype {dtype}: gradient rel L2 vs FP64 oracle {err:.3e}")
+    assert err <= gate
+
+
+def test_gradient_memory_accounting():
+    torch = torch_cuda()
+    p = _gradient_case(nt=100)
+    prop = M.Propagator.from_problem(p)
+    m32 = prop.gradient_memory(10, M.CKPT_FP32)
+    m16 = prop.gradient_memory(10, M.CKPT_BF16)
+    assert 0 < m16 < m32
+    torch.cuda.synchronize()
