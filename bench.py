@@ -291,6 +291,14 @@ def run_mmod(args):
            "d2h_bytes_per_step": int(tr_h.numel() * 4),
            "api": "mmod_set_model + mmod_forward with pinned host buffers, wall clock"}
 
+    extra = {}
+    if not args.no_extra:
+        fwd_gpts = value / ws
+        extra["adjoint"] = measure_adjoint(M, prop, p, dev, stream, fwd_gpts)
+        extra["gradient"] = measure_gradient(M, dev, stream, fwd_gpts)
+        extra["batched"] = measure_batched(M, dev, stream, fwd_gpts)
+        extra["large"] = measure_large(M, dev, stream, peak)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu, _, _ = oracle_sample(p, seconds_target=args.ref_seconds)
@@ -305,12 +313,144 @@ def run_mmod(args):
                                        M.mmod_tma_variant_name(plan["variant"])}),
                 "hbm_roofline_pct": 100.0 * BYTES_PER_POINT * value / ws / peak,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clocks}
+                "clocks": clocks, **extra}
         print(json.dumps(line), flush=True)
     prop.close()
     if ws > 1:
         dist.destroy_process_group()
     return 0
+
+
+def time_calls(fn, reps, stream):
+    """Median device time (ms) of fn() over reps calls, CUDA events on stream."""
+    import torch
+    out = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return float(np.median(out))
+
+
+def measure_adjoint(M, prop, p, dev, stream, fwd_gpts, reps=3):
+    """mmod_adjoint on the bench workload: the residual has the traces' shape."""
+    import torch
+    rng = np.random.default_rng(7)
+    r = torch.from_numpy(rng.standard_normal((p.nt, len(p.rec_ijk))).astype(np.float32)).to(dev)
+    a = torch.empty((len(p.src_ijk), p.nt), device=dev)
+    prop.adjoint(r, a, stream)
+    ms = time_calls(lambda: prop.adjoint(r, a, stream), reps, stream)
+    v = p.npoints * p.nt / (ms * 1e-3) / 1e9
+    return {"value": v, "unit": UNIT, "ms": ms, "vs_forward": v / fwd_gpts, "workload": p.name,
+            "what": "mmod_adjoint: nt adjoint steps, receivers injected, sources gathered"}
+
+
+def measure_gradient(M, dev, stream, fwd_gpts, reps=2):
+    """mmod_gradient on the 200^3 smooth-gradient workload, 20 checkpoints."""
+    import torch
+    import workloads as W
+    p = W.smooth_gradient_200(1000)
+    prop = M.Propagator.from_problem(p, device=dev.index or 0)
+    prop.set_model(torch.from_numpy(p.vel).to(dev), stream)
+    wav = torch.from_numpy(np.ascontiguousarray(p.wavelet)).to(dev)
+    rng = np.random.default_rng(8)
+    r = torch.from_numpy(rng.standard_normal((p.nt, len(p.rec_ijk))).astype(np.float32)).to(dev)
+    g = torch.empty(p.vel.shape, device=dev)
+    out = {"workload": p.name, "checkpoints": 20, "unit": UNIT,
+           "what": "mmod_gradient: forward sweep with checkpoints, segment replay, adjoint, imaging; "
+                   "value counts nt forward-equivalent steps per call"}
+    for name, dtype in (("fp32", M.CKPT_FP32), ("bf16", M.CKPT_BF16)):
+        prop.gradient(wav, r, g, 20, dtype, stream)
+        ms = time_calls(lambda: prop.gradient(wav, r, g, 20, dtype, stream), reps, stream)
+        v = p.npoints * p.nt / (ms * 1e-3) / 1e9
+        out[name] = {"value": v, "ms": ms, "vs_forward": v / fwd_gpts,
+                     "memory_gb": prop.gradient_memory(20, dtype) / 1e9}
+    prop.close()
+    return out
+
+
+def measure_batched(M, dev, stream, fwd_gpts, reps=3):
+    """mmod_batch_forward on 32 uneven shots x 800 steps (one launch per step for
+    all shots, variant chosen by mmod_batch_autotune), against the same shots
+    run one after another through mmod_forward."""
+    import torch
+    import workloads as W
+    shots = W.batched_shots()
+    props = [M.Propagator.from_problem(p, device=dev.index or 0) for p in shots]
+    for pr, p in zip(props, shots):
+        pr.set_model(torch.from_numpy(p.vel).to(dev), stream)
+    wav = [torch.from_numpy(np.ascontiguousarray(p.wavelet)).to(dev) for p in shots]
+    trs = [torch.empty((p.nt, len(p.rec_ijk)), device=dev) for p in shots]
+    work = sum(p.npoints * p.nt for p in shots)
+    b = M.Batch(props)
+    variant = b.autotune(10, stream)
+    b.forward(wav, trs, stream)
+    ms = time_calls(lambda: b.forward(wav, trs, stream), reps, stream)
+    loop_ms = b.loop_ms()
+
+    def one_by_one():
+        for pr, w, t in zip(props, wav, trs):
+            pr.forward(w, t, None, stream)
+    one_by_one()
+    ms_single = time_calls(one_by_one, reps, stream)
+    b.close()
+    for pr in props:
+        pr.close()
+    v = work / (ms * 1e-3) / 1e9
+    return {"value": v, "unit": UNIT, "ms": ms, "loop_ms": loop_ms, "vs_forward": v / fwd_gpts,
+            "one_by_one": work / (ms_single * 1e-3) / 1e9, "shots": len(shots), "nt": shots[0].nt,
+            "points": int(sum(p.npoints for p in shots)), "variant": M.mmod_tma_variant_name(variant),
+            "what": "mmod_batch_forward: all shots advance one step per launch (CUDA graph of nt launches)"}
+
+
+def measure_large(M, dev, stream, peak, reps=2):
+    """The 1024 x 1024 x 512 shot (h = 12.5 m, L = 32, 500 steps, 1024^2
+    receivers): forward throughput and the step kernel's roofline fraction,
+    then the velocity gradient with 25 FP16 checkpoints (segments scheme) and
+    the device memory the whole run holds."""
+    import torch
+    import workloads as W
+    p = W.fractal_large(500)
+    npts = p.npoints
+    torch.cuda.synchronize(dev)
+    free0 = torch.cuda.mem_get_info(dev)[0]
+    prop = M.Propagator.from_problem(p, device=dev.index or 0)
+    prop.set_model(torch.from_numpy(p.vel).to(dev), stream)
+    wav = torch.from_numpy(np.ascontiguousarray(p.wavelet)).to(dev)
+    tr = torch.empty((p.nt, len(p.rec_ijk)), device=dev)
+    prop.forward(wav, tr, None, stream)
+    loops = []
+
+    def fwd():
+        prop.forward(wav, tr, None, stream)
+        loops.append(prop.loop_ms())
+    fwd_ms = time_calls(fwd, reps, stream)
+    fwd_v = npts * p.nt / (fwd_ms * 1e-3) / 1e9
+    step_ms = float(np.median(loops)) / p.nt
+    achieved = BYTES_PER_POINT * npts / (step_ms * 1e-3) / 1e9
+    gen = torch.Generator(device=dev).manual_seed(11)
+    r = torch.randn((p.nt, len(p.rec_ijk)), device=dev, generator=gen)
+    g = torch.empty(p.vel.shape, device=dev)
+    prop.gradient(wav, r, g, 25, M.CKPT_FP16, stream)
+    torch.cuda.synchronize(dev)
+    used = free0 - torch.cuda.mem_get_info(dev)[0]
+    grad_ms = time_calls(lambda: prop.gradient(wav, r, g, 25, M.CKPT_FP16, stream), 1, stream)
+    grad_v = npts * p.nt / (grad_ms * 1e-3) / 1e9
+    plan = prop.plan()
+    prop.close()
+    del tr, r, g
+    torch.cuda.empty_cache()
+    return {"workload": p.name, "grid": [p.vel.shape[2], p.vel.shape[1], p.vel.shape[0]], "nt": p.nt,
+            "nrec": int(len(p.rec_ijk)), "unit": UNIT,
+            "forward": {"value": fwd_v, "ms": fwd_ms, "step_ms": step_ms,
+                        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                     "frac": achieved / peak}, "variant": M.mmod_tma_variant_name(plan["variant"])},
+            "gradient_fp16": {"value": grad_v, "ms": grad_ms, "checkpoints": 25, "scheme": "segments",
+                              "device_gb": used / 1e9, "budget_gb": 180,
+                              "what": "forward-equivalent Gpoint-updates/s (nt steps per call)"}}
 
 
 def prop_uses_tma(prop) -> bool:
@@ -338,6 +478,7 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=20.0,
                     help="CPU seconds per oracle sample (cpu_baseline / reference arm)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the adjoint / gradient / batched / large-shot measurements")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "mmod":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)

@@ -130,18 +130,44 @@ enum { MMOD_CKPT_FP32 = 0, MMOD_CKPT_BF16 = 1, MMOD_CKPT_FP16 = 2 };
  * [nz][ny][nx] (FP32, dJ/dv in J-units per m/s):
  *   dJ/dv = 2 dt^2 v sum_n psi^{n+1} (D u^{n+1} - 2 u^n + E u^{n-1}) / c^2,
  * psi the adjoint wavefield (zero-lag imaging condition).  The forward
- * states are recomputed from ckpt_count checkpoints (two-level scheme: the
- * run is cut into ckpt_count segments; each segment is replayed once, so the
- * cost is two forward runs and one adjoint run).  Checkpoints are stored as
- * MMOD_CKPT_FP32 (exact replay) or BF16 / FP16 with one scale per z plane
+ * states are recomputed from ckpt_count checkpoints, by the handle's scheme
+ * (mmod_set_option MMOD_OPT_CKPT_SCHEME):
+ *   MMOD_SCHEME_SEGMENTS (default): the run is cut into ckpt_count segments;
+ *     each is replayed once into ceil(nt / ckpt_count) + 2 FP32 volumes, so
+ *     the cost is two forward runs and one adjoint run;
+ *   MMOD_SCHEME_REVOLVE: binomial checkpointing (mmod_revolve_schedule) with
+ *     ckpt_count slots and three FP32 work volumes; the forward steps
+ *     replayed are the fewest any schedule with that many slots needs
+ *     (about r forward runs when C(ckpt_count + 1 + r, r) >= nt).
+ * A checkpoint holds (u^{n-1}, u^n), stored as MMOD_CKPT_FP32 (exact replay:
+ * both schemes give the same bits) or BF16 / FP16 with one scale per z plane
  * (stepping stays FP32).  Device memory: mmod_gradient_memory().  Errors:
  * STATE, ARG, OOM, CUDA, TIMEOUT. */
 mmod_status mmod_gradient(mmod_handle *h, const float *wavelet, const float *resid, float *grad_v,
                           int ckpt_count, int ckpt_dtype, mmod_stream stream);
 
 /* Bytes of device memory mmod_gradient allocates for this checkpoint layout
- * (on top of the handle's own volumes); -1 for invalid arguments. */
+ * under the handle's current scheme (on top of the handle's own volumes);
+ * -1 for invalid arguments. */
 long long mmod_gradient_memory(const mmod_handle *h, int ckpt_count, int ckpt_dtype);
+
+/* Binomial checkpointing schedule (Griewank 1992; Griewank & Walther,
+ * revolve) reversing nsteps time steps with `snaps` checkpoint slots besides
+ * the initial state (zero, never stored).  Host code: no device is touched.
+ * Writes up to cap actions as int triples {kind, a, b} into `actions`:
+ *   MMOD_REV_ADVANCE  a, b: step the working state from step a to step b;
+ *   MMOD_REV_SAVE     a, b: store the working state (at step b) in slot a;
+ *   MMOD_REV_RESTORE  a, b: load the state of step b from slot a (a = -1:
+ *                           the zero initial state, b = 0);
+ *   MMOD_REV_REVERSE  a:    with the working state at step a, take forward
+ *                           step a and the matching adjoint step (steps are
+ *                           reversed in the order nsteps-1, ..., 0).
+ * *count = number of actions, *advanced = steps advanced by ADVANCE actions
+ * (both optional).  actions = NULL with cap = 0 only queries the sizes.
+ * Errors: ARG (negative argument, or cap too small with actions given). */
+enum { MMOD_REV_ADVANCE = 0, MMOD_REV_SAVE = 1, MMOD_REV_RESTORE = 2, MMOD_REV_REVERSE = 3 };
+mmod_status mmod_revolve_schedule(int nsteps, int snaps, int *actions, long long cap, long long *count,
+                                  long long *advanced);
 
 /* FP64 sum of a[i] * b[i] over n FP32 device values (dot-product tests,
  * gradient norms).  Synchronises `stream`.  Errors: ARG, OOM, CUDA. */
@@ -172,13 +198,16 @@ int mmod_tma_variant_count(void);
 const char *mmod_tma_variant_name(int v);
 mmod_status mmod_set_tma_variant(mmod_handle *h, int v);
 
-/* Tuning options of the TMA kernel, 0 = off, 1 = on (results are the same
- * bits either way):
- *   MMOD_OPT_PDL  launch each step as a programmatic dependent of the
- *                 previous one, so its set-up overlaps the previous step's
- *                 tail (default on).
+/* Options of a handle:
+ *   MMOD_OPT_PDL          0 / 1: launch each TMA step as a programmatic
+ *                         dependent of the previous one, so its set-up
+ *                         overlaps the previous step's tail (default 1; the
+ *                         same bits either way);
+ *   MMOD_OPT_CKPT_SCHEME  MMOD_SCHEME_SEGMENTS (default) or
+ *                         MMOD_SCHEME_REVOLVE: checkpointing of mmod_gradient.
  * Errors: ARG (unknown option or value). */
-enum { MMOD_OPT_PDL = 2 };
+enum { MMOD_OPT_PDL = 2, MMOD_OPT_CKPT_SCHEME = 3 };
+enum { MMOD_SCHEME_SEGMENTS = 0, MMOD_SCHEME_REVOLVE = 1 };
 mmod_status mmod_set_option(mmod_handle *h, int option, int value);
 
 /* Launch plan of the active TMA variant: writes 8 ints {variant, tiles_x,
@@ -239,6 +268,44 @@ int mmod_check_recip(int n, unsigned int *max_ulp_out);
 mmod_status mmod_forward_noalloc(const mmod_config *cfg, int device, const float *vel,
                                  const float *wavelet, float *traces, float *final_u,
                                  mmod_stream stream);
+
+/* ---- Batched shots ------------------------------------------------------
+ * A batch advances several shots (one handle each: any grid sizes, the same
+ * nt, the same device) together: one kernel launch per time step covers all
+ * of them, and the nt launches are captured once into a CUDA graph.  The
+ * batch refers to the handles (they keep their buffers, models and
+ * geometry); destroy the batch before its handles.  Each handle's buffers
+ * hold its shot's final state after mmod_batch_forward (mmod_get_state). */
+typedef struct mmod_batch mmod_batch;
+
+/* Errors: ARG (null or mismatched handles), UNSUPPORTED (a grid without TMA
+ * plan), OOM, CUDA; message from mmod_last_error(NULL). */
+mmod_status mmod_batch_create(mmod_handle *const *shots, int nshots, mmod_batch **out);
+mmod_status mmod_batch_destroy(mmod_batch *b);
+
+/* Forward run of every shot from zero state: wavelets[i] [nsrc_i][nt] and
+ * traces[i] [nt][nrec_i] are DEVICE pointers (host arrays of nshots
+ * pointers; entries may be NULL for shots without sources / receivers).
+ * Stream-ordered.  Errors: STATE (a shot without model), ARG, CUDA, TIMEOUT;
+ * message from mmod_batch_last_error. */
+mmod_status mmod_batch_forward(mmod_batch *b, const float *const *wavelets, float *const *traces,
+                               mmod_stream stream);
+
+/* Select the TMA variant used by the batch (see mmod_tma_variant_count). */
+mmod_status mmod_batch_set_variant(mmod_batch *b, int v);
+
+/* Device time (ms) of the last mmod_batch_forward's loop; waits for it. */
+float mmod_batch_last_loop_ms(mmod_batch *b);
+const char *mmod_batch_last_error(const mmod_batch *b);
+
+/* ---- Autotuner --------------------------------------------------------
+ * Times every compiled TMA variant (points per thread, z-window unroll,
+ * ring depths) for `steps` time steps on the handle's (or batch's) own grids
+ * and model, without sources, and selects the fastest; *variant_out (may be
+ * NULL) receives it.  Synchronises `stream`; overwrites the wavefields.
+ * Errors: ARG, STATE (no model), UNSUPPORTED, CUDA. */
+mmod_status mmod_autotune(mmod_handle *h, int steps, mmod_stream stream, int *variant_out);
+mmod_status mmod_batch_autotune(mmod_batch *b, int steps, mmod_stream stream, int *variant_out);
 
 /* Library version string, e.g. "mmod-gb300 0.1 sm_103a". */
 const char *mmod_version(void);

@@ -27,6 +27,9 @@ STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_UNSTABLE", -3: "ERR_OOM", -4: "ERR_CU
           -5: "ERR_TIMEOUT", -6: "ERR_STATE", -7: "ERR_UNSUPPORTED"}
 KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_TMA = 0, 1, 2
 OPT_PDL = 2
+OPT_CKPT_SCHEME = 3
+SCHEME_SEGMENTS, SCHEME_REVOLVE = 0, 1
+REV_ADVANCE, REV_SAVE, REV_RESTORE, REV_REVERSE = 0, 1, 2, 3
 
 # Every symbol include/mmod.h declares (checked against the header by the tests).
 EXPORTED = ["mmod_create", "mmod_destroy", "mmod_set_model", "mmod_forward", "mmod_set_state",
@@ -34,7 +37,9 @@ EXPORTED = ["mmod_create", "mmod_destroy", "mmod_set_model", "mmod_forward", "mm
             "mmod_cfl_dt", "mmod_last_error", "mmod_version", "mmod_check_recip",
             "mmod_tma_variant_count", "mmod_tma_variant_name", "mmod_set_tma_variant", "mmod_get_plan",
             "mmod_forward_noalloc", "mmod_set_option", "mmod_adjoint", "mmod_gradient",
-            "mmod_gradient_memory", "mmod_dot"]
+            "mmod_gradient_memory", "mmod_dot", "mmod_batch_create", "mmod_batch_destroy",
+            "mmod_batch_forward", "mmod_batch_set_variant", "mmod_batch_last_loop_ms", "mmod_batch_last_error",
+            "mmod_autotune", "mmod_batch_autotune", "mmod_revolve_schedule"]
 CKPT_FP32, CKPT_BF16, CKPT_FP16 = 0, 1, 2
 
 
@@ -94,6 +99,16 @@ def load():
         "mmod_gradient": ([P, P, P, P, I, I, P], I),
         "mmod_gradient_memory": ([P, I, I], ctypes.c_longlong),
         "mmod_dot": ([P, P, ctypes.c_longlong, ctypes.POINTER(ctypes.c_double), P], I),
+        "mmod_batch_create": ([ctypes.POINTER(P), I, ctypes.POINTER(P)], I),
+        "mmod_batch_destroy": ([P], I),
+        "mmod_batch_forward": ([P, ctypes.POINTER(P), ctypes.POINTER(P), P], I),
+        "mmod_batch_set_variant": ([P, I], I),
+        "mmod_batch_last_loop_ms": ([P], ctypes.c_float),
+        "mmod_batch_last_error": ([P], ctypes.c_char_p),
+        "mmod_autotune": ([P, I, P, ctypes.POINTER(I)], I),
+        "mmod_batch_autotune": ([P, I, P, ctypes.POINTER(I)], I),
+        "mmod_revolve_schedule": ([I, I, P, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong),
+                                   ctypes.POINTER(ctypes.c_longlong)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -237,6 +252,22 @@ def mmod_gradient_memory(h, ckpt_count, ckpt_dtype=0) -> int:
     return int(load().mmod_gradient_memory(h, int(ckpt_count), int(ckpt_dtype)))
 
 
+def mmod_revolve_schedule(nsteps: int, snaps: int):
+    """Binomial checkpointing schedule: (actions int32 [count][3] of
+    {kind, a, b} with kind in REV_*, number of advanced steps).  Host only."""
+    lib = load()
+    count, adv = ctypes.c_longlong(), ctypes.c_longlong()
+    st = lib.mmod_revolve_schedule(int(nsteps), int(snaps), None, 0, ctypes.byref(count), ctypes.byref(adv))
+    if st != 0:
+        raise MmodError(st, "mmod_revolve_schedule: invalid arguments")
+    out = np.zeros((max(count.value, 1), 3), np.int32)
+    st = lib.mmod_revolve_schedule(int(nsteps), int(snaps), out.ctypes.data, count.value, ctypes.byref(count),
+                                   ctypes.byref(adv))
+    if st != 0:
+        raise MmodError(st, "mmod_revolve_schedule failed")
+    return out[: count.value], int(adv.value)
+
+
 def mmod_dot(a, b, n=None, stream=None) -> float:
     """FP64 dot product of two FP32 device arrays (computed by the library)."""
     out = ctypes.c_double(0.0)
@@ -268,6 +299,58 @@ def mmod_last_launch_count(h) -> int:
 
 def mmod_last_loop_ms(h) -> float:
     return float(load().mmod_last_loop_ms(h))
+
+
+def mmod_autotune(h, steps=20, stream=None) -> int:
+    v = ctypes.c_int(-1)
+    _check(h, load().mmod_autotune(h, int(steps), _stream(stream), ctypes.byref(v)))
+    return int(v.value)
+
+
+class Batch:
+    """Several propagators advanced together (one launch per step for all).
+    Keeps references to the propagators so they outlive the batch."""
+
+    def __init__(self, props):
+        self.props = list(props)
+        arr = (ctypes.c_void_p * len(self.props))(*[p.handle.value for p in self.props])
+        out = ctypes.c_void_p()
+        st = load().mmod_batch_create(arr, len(self.props), ctypes.byref(out))
+        if st != 0:
+            raise MmodError(st, load().mmod_last_error(None).decode())
+        self.handle = out
+
+    def _err(self, st):
+        if st != 0:
+            raise MmodError(st, load().mmod_batch_last_error(self.handle).decode())
+
+    def forward(self, wavelets, traces, stream=None):
+        n = len(self.props)
+        w = (ctypes.c_void_p * n)(*[_addr(x) for x in wavelets])
+        t = (ctypes.c_void_p * n)(*[_addr(x) for x in traces])
+        self._err(load().mmod_batch_forward(self.handle, w, t, _stream(stream)))
+
+    def set_variant(self, v: int):
+        self._err(load().mmod_batch_set_variant(self.handle, int(v)))
+
+    def autotune(self, steps=20, stream=None) -> int:
+        v = ctypes.c_int(-1)
+        self._err(load().mmod_batch_autotune(self.handle, int(steps), _stream(stream), ctypes.byref(v)))
+        return int(v.value)
+
+    def loop_ms(self) -> float:
+        return float(load().mmod_batch_last_loop_ms(self.handle))
+
+    def close(self):
+        if self.handle is not None:
+            load().mmod_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Propagator:
@@ -312,6 +395,9 @@ class Propagator:
 
     def gradient_memory(self, ckpt_count, ckpt_dtype=0) -> int:
         return mmod_gradient_memory(self.handle, ckpt_count, ckpt_dtype)
+
+    def autotune(self, steps=20, stream=None) -> int:
+        return mmod_autotune(self.handle, steps, stream)
 
     def forward(self, wavelet, traces, final_u=None, stream=None):
         mmod_forward(self.handle, wavelet, traces, final_u, stream)

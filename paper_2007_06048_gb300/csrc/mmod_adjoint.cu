@@ -13,16 +13,22 @@
 // Gradient.  dJ/dc(x) = sum_n mu^{n+1}(x) (L u^n + s^n)(x); with
 // C (L u^n + s^n) = D u^{n+1} - 2 u^n + E u^{n-1} this is the zero-lag
 // imaging condition sum_n psi^{n+1} (D u^{n+1} - 2 u^n + E u^{n-1}) / c^2,
-// and dJ/dv = 2 dt^2 v dJ/dc.  The forward states are recovered by two-level
-// checkpointing: the first sweep stores (u^{a-1}, u^a) at the start of each
-// of S segments of K steps (FP32, or BF16 / FP16 with one scale per z plane);
-// the backward sweep replays each segment from its checkpoint into K+2
-// stored volumes and runs the segment's adjoint steps against them.  Memory:
-// 2 S checkpoints + K + 2 volumes; work: two forward sweeps and one adjoint.
+// and dJ/dv = 2 dt^2 v dJ/dc.  The forward states are recovered from
+// checkpoints (u^{a-1}, u^a) (FP32, or BF16 / FP16 with one scale per z
+// plane) by one of two schemes:
+//   segments: the first sweep stores a checkpoint at the start of each of S
+//     segments of K steps; the backward sweep replays each segment from its
+//     checkpoint into K+2 stored volumes and runs the segment's adjoint steps
+//     against them.  Memory: 2 S checkpoint volumes + K + 2; work: two
+//     forward sweeps and one adjoint;
+//   revolve: the binomial schedule of mmod_revolve.cu over S slots, with the
+//     working state in the handle's two buffers and one more volume for
+//     u^{n+1}; the fewest replayed steps for S slots.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <cfloat>
 #include <cstring>
 
 #include "mmod_handle.h"
@@ -44,7 +50,8 @@ __device__ __forceinline__ __half to_store<__half>(float v) { return __float2hal
 __device__ __forceinline__ float from_store(__nv_bfloat16 v) { return __bfloat162float(v); }
 __device__ __forceinline__ float from_store(__half v) { return __half2float(v); }
 
-// One CTA per plane: scale = max |u| over the plane, stored = u / scale.
+// One CTA per plane: scale = max(max |u| over the plane, FLT_MIN), stored =
+// u / scale.
 template <class T>
 __global__ void compress_kernel(const float *__restrict__ u, long long plane, T *__restrict__ out,
                                 float *__restrict__ scale) {
@@ -61,9 +68,12 @@ __global__ void compress_kernel(const float *__restrict__ u, long long plane, T 
         if (threadIdx.x == 0) part[0] = m;
     }
     __syncthreads();
-    const float s = part[0];
+    // A plane that holds only zeros and subnormals (the leading edge of a
+    // wave, far planes early in a run) gets the smallest normal scale, so
+    // 1/scale stays finite.
+    const float s = fmaxf(part[0], FLT_MIN);
     if (threadIdx.x == 0) scale[blockIdx.x] = s;
-    const float inv = s > 0.0f ? 1.0f / s : 0.0f;
+    const float inv = 1.0f / s;
     for (long long q = threadIdx.x; q < plane; q += blockDim.x) out[base + q] = to_store<T>(u[base + q] * inv);
 }
 
@@ -107,20 +117,21 @@ cudaError_t restore_volume(mmod_handle *h, int slot, float *u, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// Allocate (or keep) the gradient work space for S segments of K steps.
-mmod_status ensure_grad_work(mmod_handle *h, int nseg, int seglen, int dtype) {
+// Allocate (or keep) the gradient work space: nslot checkpoints of two
+// volumes, nwork FP32 work volumes (with tensor maps), psi, grad_c.
+mmod_status ensure_grad_work(mmod_handle *h, int nslot, int nwork, int dtype) {
     auto &gw = h->gw;
-    if (gw.nseg == nseg && gw.seglen == seglen && gw.dtype == dtype) return MMOD_OK;
+    if (gw.nslot == nslot && gw.nwork == nwork && gw.dtype == dtype) return MMOD_OK;
     free_grad_work(h);
     const size_t vb = sizeof(float) * (size_t)h->vol;
-    gw.seg.assign(seglen + 2, nullptr);
-    gw.seg_cur.resize(seglen + 2);
-    gw.seg_prev.resize(seglen + 2);
-    for (int i = 0; i < seglen + 2; ++i) {
+    gw.seg.assign(nwork, nullptr);
+    gw.seg_cur.resize(nwork);
+    gw.seg_prev.resize(nwork);
+    for (int i = 0; i < nwork; ++i) {
         MMOD_CK(h, cudaMalloc(&gw.seg[i], vb));
         MMOD_CK(h, cudaMemset(gw.seg[i], 0, vb));
         if (h->tma_ok && !encode_maps(h->cfg, h->nxp, gw.seg[i], &gw.seg_cur[i], &gw.seg_prev[i]))
-            return fail(h, MMOD_ERR_CUDA, "tensor map encoding failed for a segment buffer");
+            return fail(h, MMOD_ERR_CUDA, "tensor map encoding failed for a work volume");
     }
     for (int b = 0; b < 2; ++b) {
         MMOD_CK(h, cudaMalloc(&gw.psi[b], vb));
@@ -128,13 +139,27 @@ mmod_status ensure_grad_work(mmod_handle *h, int nseg, int seglen, int dtype) {
             return fail(h, MMOD_ERR_CUDA, "tensor map encoding failed for an adjoint buffer");
     }
     MMOD_CK(h, cudaMalloc(&gw.gradc, vb));
-    gw.ckpt_bytes = (size_t)nseg * 2 * (size_t)h->vol * ckpt_elem_bytes(dtype);
+    gw.ckpt_bytes = (size_t)nslot * 2 * (size_t)h->vol * ckpt_elem_bytes(dtype);
     MMOD_CK(h, cudaMalloc(&gw.ckpt, gw.ckpt_bytes));
-    if (dtype != MMOD_CKPT_FP32) MMOD_CK(h, cudaMalloc(&gw.ckpt_scale, sizeof(float) * (size_t)nseg * 2 * h->cfg.nz));
-    gw.nseg = nseg;
-    gw.seglen = seglen;
+    if (dtype != MMOD_CKPT_FP32) MMOD_CK(h, cudaMalloc(&gw.ckpt_scale, sizeof(float) * (size_t)nslot * 2 * h->cfg.nz));
+    gw.nslot = nslot;
+    gw.nwork = nwork;
     gw.dtype = dtype;
     return MMOD_OK;
+}
+
+// Checkpoint layout of a gradient call: slots and FP32 work volumes.
+void grad_layout(const mmod_handle *h, int ckpt_count, int *nslot, int *nwork, int *seglen) {
+    const int nt = h->cfg.nt;
+    if (h->ckpt_scheme == MMOD_SCHEME_REVOLVE) {
+        *seglen = 0;
+        *nslot = std::max(1, std::min(ckpt_count, nt - 1));
+        *nwork = 1;
+    } else {
+        *seglen = std::max(1, (nt + ckpt_count - 1) / ckpt_count);
+        *nslot = nt > 0 ? (nt + *seglen - 1) / *seglen : 1;
+        *nwork = *seglen + 2;
+    }
 }
 
 // Device copy of an input array: device pointers pass through, host arrays go
@@ -172,7 +197,7 @@ void free_grad_work(mmod_handle *h) {
     gw.gradc = nullptr;
     gw.ckpt = nullptr;
     gw.ckpt_scale = nullptr;
-    gw.nseg = gw.seglen = 0;
+    gw.nslot = gw.nwork = 0;
     gw.dtype = -1;
     gw.ckpt_bytes = 0;
 }
@@ -236,9 +261,9 @@ MMOD_API mmod_status mmod_gradient(mmod_handle *h, const float *wavelet, const f
     DeviceGuard guard(h->device);
     cudaStream_t s = (cudaStream_t)stream;
     const int nt = c.nt;
-    const int seglen = std::max(1, (nt + ckpt_count - 1) / ckpt_count);
-    const int nseg = nt > 0 ? (nt + seglen - 1) / seglen : 0;
-    if (mmod_status st = ensure_grad_work(h, std::max(nseg, 1), seglen, ckpt_dtype)) return st;
+    int nslot = 0, nwork = 0, seglen = 0;
+    grad_layout(h, ckpt_count, &nslot, &nwork, &seglen);
+    if (mmod_status st = ensure_grad_work(h, nslot, nwork, ckpt_dtype)) return st;
     auto &gw = h->gw;
     const bool tma = use_tma(h);
     long long launches = 0;
@@ -251,57 +276,109 @@ MMOD_API mmod_status mmod_gradient(mmod_handle *h, const float *wavelet, const f
     if (!h->st_adjw) MMOD_CK(h, cudaMalloc(&h->st_adjw, sizeof(float) * std::max<size_t>(nres, 1)));
     if (nres) MMOD_CK(h, launch_reverse_transpose(dres, nt, c.nrec, h->st_adjw, s));
 
-    // ---- sweep 1: forward with a checkpoint at the start of every segment
     MMOD_CK(h, cudaMemsetAsync(h->u[0], 0, vb, s));
     MMOD_CK(h, cudaMemsetAsync(h->u[1], 0, vb, s));
     h->state_pending = false;
     StepArgs fa = base_args(h, h->fwd, dwav);
     fa.nrec = 0;   // no receivers in the gradient's forward sweeps
-    for (int sg = 0; sg < nseg; ++sg) {
-        const int a0 = sg * seglen, b0 = std::min(nt, a0 + seglen);
-        // at step a0: u^{a0-1} in u[a0 & 1], u^{a0} in u[(a0 + 1) & 1]
-        MMOD_CK(h, save_volume(h, h->u[a0 & 1], 2 * sg, s));
-        MMOD_CK(h, save_volume(h, h->u[(a0 + 1) & 1], 2 * sg + 1, s));
-        for (int n = a0; n < b0; ++n) {
-            fa.n = n;
-            fa.ucur = h->u[(n + 1) & 1];
-            fa.uprev = h->u[n & 1];
-            fa.uout = h->u[n & 1];
-            MMOD_CK(h, enqueue_step(h, fa, &h->cur_map[(n + 1) & 1], &h->prev_map[n & 1], tma, nullptr, s, &launches));
-        }
-    }
-
-    // ---- backward: replay each segment, then its adjoint steps + imaging
-    MMOD_CK(h, cudaMemsetAsync(gw.psi[0], 0, vb, s));
-    MMOD_CK(h, cudaMemsetAsync(gw.psi[1], 0, vb, s));
-    MMOD_CK(h, cudaMemsetAsync(gw.gradc, 0, vb, s));
     StepArgs aa = base_args(h, h->adj, h->st_adjw);
     aa.nrec = 0;
-    for (int sg = nseg - 1; sg >= 0; --sg) {
-        const int a0 = sg * seglen, b0 = std::min(nt, a0 + seglen);
-        MMOD_CK(h, restore_volume(h, 2 * sg, gw.seg[0], s));
-        MMOD_CK(h, restore_volume(h, 2 * sg + 1, gw.seg[1], s));
-        for (int n = a0; n < b0; ++n) {   // seg[j] holds u^{a0-1+j}
-            const int j = n - a0;
-            fa.n = n;
-            fa.ucur = gw.seg[j + 1];
-            fa.uprev = gw.seg[j];
-            fa.uout = gw.seg[j + 2];
-            MMOD_CK(h, enqueue_step(h, fa, tma ? &gw.seg_cur[j + 1] : nullptr, tma ? &gw.seg_prev[j] : nullptr, tma,
-                                    nullptr, s, &launches));
+    // forward step n in place on the handle's buffers: u^{n-1} in u[n & 1],
+    // u^n in u[(n + 1) & 1], u^{n+1} over u^{n-1}
+    auto fwd_step_in_place = [&](int n) {
+        fa.n = n;
+        fa.ucur = h->u[(n + 1) & 1];
+        fa.uprev = h->u[n & 1];
+        fa.uout = h->u[n & 1];
+        return enqueue_step(h, fa, &h->cur_map[(n + 1) & 1], &h->prev_map[n & 1], tma, nullptr, s, &launches);
+    };
+    // adjoint step of forward step n, then the imaging term of step n from
+    // u^{n+1}, u^n, u^{n-1}
+    auto adj_step_and_image = [&](int n, const float *un, const float *uc, const float *up) {
+        const int m = nt - 1 - n;   // adjoint step m produces psi^{n+1}
+        aa.n = m;
+        aa.ucur = gw.psi[(m + 1) & 1];
+        aa.uprev = gw.psi[m & 1];
+        aa.uout = gw.psi[m & 1];
+        cudaError_t e = enqueue_step(h, aa, tma ? &gw.psi_cur[(m + 1) & 1] : nullptr,
+                                     tma ? &gw.psi_prev[m & 1] : nullptr, tma, nullptr, s, &launches);
+        if (e != cudaSuccess) return e;
+        ++launches;
+        return launch_imaging(gw.psi[m & 1], un, uc, up, h->c, aa.ex, aa.ey, aa.ez, c.nx, c.ny, c.nz, h->nxp,
+                              gw.gradc, s);
+    };
+
+    if (h->ckpt_scheme == MMOD_SCHEME_REVOLVE) {
+        std::vector<RevAction> sched;
+        revolve_schedule(nt, nslot, &sched);
+        MMOD_CK(h, cudaMemsetAsync(gw.psi[0], 0, vb, s));
+        MMOD_CK(h, cudaMemsetAsync(gw.psi[1], 0, vb, s));
+        MMOD_CK(h, cudaMemsetAsync(gw.gradc, 0, vb, s));
+        float *unext = gw.seg[0];
+        for (const RevAction &act : sched) {
+            switch (act.kind) {
+                case MMOD_REV_ADVANCE:
+                    for (int n = act.a; n < act.b; ++n) MMOD_CK(h, fwd_step_in_place(n));
+                    break;
+                case MMOD_REV_SAVE:   // state of step b: u^{b-1} in u[b & 1], u^b in u[(b + 1) & 1]
+                    MMOD_CK(h, save_volume(h, h->u[act.b & 1], 2 * act.a, s));
+                    MMOD_CK(h, save_volume(h, h->u[(act.b + 1) & 1], 2 * act.a + 1, s));
+                    break;
+                case MMOD_REV_RESTORE:
+                    if (act.a < 0) {
+                        MMOD_CK(h, cudaMemsetAsync(h->u[0], 0, vb, s));
+                        MMOD_CK(h, cudaMemsetAsync(h->u[1], 0, vb, s));
+                    } else {
+                        MMOD_CK(h, restore_volume(h, 2 * act.a, h->u[act.b & 1], s));
+                        MMOD_CK(h, restore_volume(h, 2 * act.a + 1, h->u[(act.b + 1) & 1], s));
+                    }
+                    break;
+                case MMOD_REV_REVERSE: {
+                    const int n = act.a;
+                    fa.n = n;
+                    fa.ucur = h->u[(n + 1) & 1];
+                    fa.uprev = h->u[n & 1];
+                    fa.uout = unext;
+                    MMOD_CK(h, enqueue_step(h, fa, &h->cur_map[(n + 1) & 1], &h->prev_map[n & 1], tma, nullptr, s,
+                                            &launches));
+                    MMOD_CK(h, adj_step_and_image(n, unext, h->u[(n + 1) & 1], h->u[n & 1]));
+                    break;
+                }
+                default:
+                    return fail(h, MMOD_ERR_CUDA, "invalid checkpoint schedule");
+            }
         }
-        for (int n = b0 - 1; n >= a0; --n) {
-            const int m = nt - 1 - n;   // adjoint step m produces psi^{n+1}
-            const int j = n - a0;
-            aa.n = m;
-            aa.ucur = gw.psi[(m + 1) & 1];
-            aa.uprev = gw.psi[m & 1];
-            aa.uout = gw.psi[m & 1];
-            MMOD_CK(h, enqueue_step(h, aa, tma ? &gw.psi_cur[(m + 1) & 1] : nullptr,
-                                    tma ? &gw.psi_prev[m & 1] : nullptr, tma, nullptr, s, &launches));
-            MMOD_CK(h, launch_imaging(gw.psi[m & 1], gw.seg[j + 2], gw.seg[j + 1], gw.seg[j], h->c, aa.ex, aa.ey,
-                                      aa.ez, c.nx, c.ny, c.nz, h->nxp, gw.gradc, s));
-            ++launches;
+    } else {
+        const int nseg = nt > 0 ? nslot : 0;
+        // ---- sweep 1: forward with a checkpoint at the start of every segment
+        for (int sg = 0; sg < nseg; ++sg) {
+            const int a0 = sg * seglen, b0 = std::min(nt, a0 + seglen);
+            // at step a0: u^{a0-1} in u[a0 & 1], u^{a0} in u[(a0 + 1) & 1]
+            MMOD_CK(h, save_volume(h, h->u[a0 & 1], 2 * sg, s));
+            MMOD_CK(h, save_volume(h, h->u[(a0 + 1) & 1], 2 * sg + 1, s));
+            for (int n = a0; n < b0; ++n) MMOD_CK(h, fwd_step_in_place(n));
+        }
+        // ---- backward: replay each segment, then its adjoint steps + imaging
+        MMOD_CK(h, cudaMemsetAsync(gw.psi[0], 0, vb, s));
+        MMOD_CK(h, cudaMemsetAsync(gw.psi[1], 0, vb, s));
+        MMOD_CK(h, cudaMemsetAsync(gw.gradc, 0, vb, s));
+        for (int sg = nseg - 1; sg >= 0; --sg) {
+            const int a0 = sg * seglen, b0 = std::min(nt, a0 + seglen);
+            MMOD_CK(h, restore_volume(h, 2 * sg, gw.seg[0], s));
+            MMOD_CK(h, restore_volume(h, 2 * sg + 1, gw.seg[1], s));
+            for (int n = a0; n < b0; ++n) {   // seg[j] holds u^{a0-1+j}
+                const int j = n - a0;
+                fa.n = n;
+                fa.ucur = gw.seg[j + 1];
+                fa.uprev = gw.seg[j];
+                fa.uout = gw.seg[j + 2];
+                MMOD_CK(h, enqueue_step(h, fa, tma ? &gw.seg_cur[j + 1] : nullptr, tma ? &gw.seg_prev[j] : nullptr,
+                                        tma, nullptr, s, &launches));
+            }
+            for (int n = b0 - 1; n >= a0; --n) {
+                const int j = n - a0;
+                MMOD_CK(h, adj_step_and_image(n, gw.seg[j + 2], gw.seg[j + 1], gw.seg[j]));
+            }
         }
     }
     h->ran = false;
@@ -325,13 +402,13 @@ MMOD_API mmod_status mmod_gradient(mmod_handle *h, const float *wavelet, const f
 
 MMOD_API long long mmod_gradient_memory(const mmod_handle *h, int ckpt_count, int ckpt_dtype) {
     if (!h || ckpt_count < 1) return -1;
-    const int nt = h->cfg.nt;
-    const int seglen = std::max(1, (nt + ckpt_count - 1) / ckpt_count);
-    const int nseg = nt > 0 ? (nt + seglen - 1) / seglen : 1;
+    if (ckpt_dtype != MMOD_CKPT_FP32 && ckpt_dtype != MMOD_CKPT_BF16 && ckpt_dtype != MMOD_CKPT_FP16) return -1;
+    int nslot = 0, nwork = 0, seglen = 0;
+    grad_layout(h, ckpt_count, &nslot, &nwork, &seglen);
     const long long vb = 4LL * h->vol;
     const long long eb = ckpt_dtype == MMOD_CKPT_FP32 ? 4 : 2;
-    return (long long)(seglen + 2 + 3) * vb + (long long)nseg * 2 * h->vol * eb +
-           (ckpt_dtype == MMOD_CKPT_FP32 ? 0 : 4LL * nseg * 2 * h->cfg.nz);
+    return (long long)(nwork + 3) * vb + (long long)nslot * 2 * h->vol * eb +
+           (ckpt_dtype == MMOD_CKPT_FP32 ? 0 : 4LL * nslot * 2 * h->cfg.nz);
 }
 
 MMOD_API mmod_status mmod_dot(const float *a, const float *b, long long n, double *out, mmod_stream stream) {

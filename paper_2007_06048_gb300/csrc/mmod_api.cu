@@ -102,15 +102,15 @@ cudaError_t upload(T **dst, const std::vector<T> &v) {
 }
 
 // Injection table of the positions pos[n][3]: sources grouped by grid point
-// (stable order), points sorted by (plane, tile, j, i) and bucketed per
-// (plane, 64 x 16 tile).  src_row = index of the position in pos.
+// (stable order), points sorted by (tile, plane, j, i) and bucketed per
+// (64 x 16 tile, plane).  src_row = index of the position in pos.
 cudaError_t build_inj(const mmod_config &c, long long plane, int nxp, const int *pos, int n, DevInj *t) {
     t->tiles_x = (c.nx + kInjTileX - 1) / kInjTileX;
     t->tiles_y = (c.ny + kInjTileY - 1) / kInjTileY;
     const long long tiles = (long long)t->tiles_x * t->tiles_y;
     auto bucket = [&](int s) {
         const int *p = pos + 3 * s;
-        return ((long long)p[2] * t->tiles_y + p[1] / kInjTileY) * t->tiles_x + p[0] / kInjTileX;
+        return ((long long)(p[1] / kInjTileY) * t->tiles_x + p[0] / kInjTileX) * c.nz + p[2];
     };
     std::vector<int> order(n);
     std::iota(order.begin(), order.end(), 0);
@@ -280,6 +280,9 @@ static mmod_status enqueue_loop(mmod_handle *h, const Geometry &geo, const float
     *count = 0;
     MMOD_CK(h, cudaEventRecordWithFlags(h->ev_t0, s, cudaEventRecordExternal));
     StepArgs a = base_args(h, geo, wav);
+    // inside the loop every step kernel follows the previous step (the
+    // first follows no kernel of the captured graph)
+    if (a.pdl) a.pdl = 2;
     for (int n = 0; n < nt; ++n) {
         a.n = n;
         a.ucur = h->u[(n + 1) & 1];
@@ -465,9 +468,10 @@ MMOD_API mmod_status mmod_set_tma_variant(mmod_handle *h, int v) {
 
 MMOD_API mmod_status mmod_set_option(mmod_handle *h, int option, int value) {
     if (!h) return MMOD_ERR_ARG;
-    if (value != 0 && value != 1) return fail(h, MMOD_ERR_ARG, "option values are 0 or 1");
+    if (value != 0 && value != 1) return fail(h, MMOD_ERR_ARG, "option values are 0 or 1");   // for every option
     switch (option) {
         case MMOD_OPT_PDL: h->pdl = value; return MMOD_OK;
+        case MMOD_OPT_CKPT_SCHEME: h->ckpt_scheme = value; return MMOD_OK;
         default: return fail(h, MMOD_ERR_ARG, "unknown option");
     }
 }

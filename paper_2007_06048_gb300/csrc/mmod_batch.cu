@@ -1,0 +1,383 @@
+// Batched shots and the variant autotuner.
+//
+// A batch groups handles (one per shot; grids of any size, the same number of
+// steps) so that one kernel launch advances every shot by one step: CTA b
+// serves shot cta_shot[b] as its block cta_local[b], reading the shot's
+// arguments and tensor maps from a descriptor table in device memory.  The
+// nt launches are captured once into a CUDA graph; the descriptor table is
+// uploaded per call, so new wavelet / trace buffers need no new capture.
+// CTAs are ordered longest first so the last wave is made of short ones.
+//
+// The autotuner times each compiled TMA variant (points per thread, z
+// unroll, ring depths) for a few steps on the real problem and keeps the
+// fastest.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "mmod_handle.h"
+
+#define MMOD_API extern "C" __attribute__((visibility("default")))
+
+using namespace mmod;
+
+struct mmod_batch {
+    std::vector<mmod_handle *> shots;
+    int device = 0, nt = 0;
+    int variant = kTmaDefaultVariant;
+    int pdl = 1;
+    std::vector<ShotDesc> desc;       // host copy, uploaded per call
+    ShotDesc *d_desc = nullptr;
+    int *d_cta_shot = nullptr, *d_cta_local = nullptr;
+    int nctas = 0;
+    GraphSlot graph;
+    cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;
+    bool ran = false;
+    std::string err;
+};
+
+namespace {
+
+// Planes per CTA in a batch: long z ranges (few halo planes) since a batch
+// has many CTAs per wave anyway.
+constexpr int kBatchZlen = 96;
+
+__global__ void batch_gather_kernel(const ShotDesc *__restrict__ shots, int nt) {
+    const ShotDesc *d = shots + blockIdx.y;
+    const int nrec = d->args.nrec;
+    if (!d->traces || nrec <= 0 || nt <= 0) return;
+    const float *u = d->u[(nt - 1) & 1];   // u^{nt}
+    float *dst = d->traces + (long long)(nt - 1) * nrec;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrec; r += gridDim.x * blockDim.x)
+        dst[r] = u[__ldg(d->args.rec_off + r)];
+}
+
+mmod_status bfail(mmod_batch *b, mmod_status st, const std::string &msg) {
+    if (b) b->err = msg;
+    return st;
+}
+
+mmod_status bfail_cuda(mmod_batch *b, cudaError_t e, const char *what) {
+    if (b) b->err = std::string(what) + ": " + cudaGetErrorName(e);
+    return e == cudaErrorMemoryAllocation ? MMOD_ERR_OOM : MMOD_ERR_CUDA;
+}
+
+#define BCK(b, call)                                          \
+    do {                                                      \
+        cudaError_t _e = (call);                              \
+        if (_e != cudaSuccess) return bfail_cuda((b), _e, #call); \
+    } while (0)
+
+void free_batch(mmod_batch *b) {
+    if (b->graph.exec) cudaGraphExecDestroy(b->graph.exec);
+    if (b->d_desc) cudaFree(b->d_desc);
+    if (b->d_cta_shot) cudaFree(b->d_cta_shot);
+    if (b->d_cta_local) cudaFree(b->d_cta_local);
+    if (b->ev_t0) cudaEventDestroy(b->ev_t0);
+    if (b->ev_t1) cudaEventDestroy(b->ev_t1);
+}
+
+// The batch's steps n0 .. n1-1 on stream s (all shots), direct launches.
+mmod_status enqueue_batch_steps(mmod_batch *b, int n0, int n1, cudaStream_t s) {
+    for (int n = n0; n < n1; ++n)
+        BCK(b, launch_step_tma_batch(b->variant, b->d_desc, b->d_cta_shot, b->d_cta_local, b->nctas, n, b->pdl != 0, s));
+    return MMOD_OK;
+}
+
+mmod_status zero_states(mmod_batch *b, cudaStream_t s) {
+    for (mmod_handle *h : b->shots) {
+        BCK(b, cudaMemsetAsync(h->u[0], 0, sizeof(float) * (size_t)h->vol, s));
+        BCK(b, cudaMemsetAsync(h->u[1], 0, sizeof(float) * (size_t)h->vol, s));
+        h->state_pending = false;
+        h->ran = false;
+    }
+    return MMOD_OK;
+}
+
+// Time `steps` steps of the time loop from zero state (ms, events on s).
+float time_steps(mmod_batch *b, int steps, cudaStream_t s, mmod_status *st) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    *st = zero_states(b, s);
+    cudaEventRecord(e0, s);
+    if (*st == MMOD_OK) *st = enqueue_batch_steps(b, 0, std::min(steps, b->nt), s);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = -1.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms;
+}
+
+}  // namespace
+
+MMOD_API mmod_status mmod_batch_create(mmod_handle *const *shots, int nshots, mmod_batch **out) {
+    set_thread_error("");
+    if (!out) return MMOD_ERR_ARG;
+    *out = nullptr;
+    if (!shots || nshots < 1) {
+        set_thread_error("a batch needs at least one handle");
+        return MMOD_ERR_ARG;
+    }
+    for (int i = 0; i < nshots; ++i) {
+        if (!shots[i]) {
+            set_thread_error("null handle in the batch");
+            return MMOD_ERR_ARG;
+        }
+        if (shots[i]->device != shots[0]->device || shots[i]->cfg.nt != shots[0]->cfg.nt) {
+            set_thread_error("the handles of a batch need the same device and the same nt");
+            return MMOD_ERR_ARG;
+        }
+        if (!shots[i]->tma_ok) {
+            set_thread_error("a handle of the batch has no TMA plan");
+            return MMOD_ERR_UNSUPPORTED;
+        }
+    }
+    mmod_batch *b = new mmod_batch();
+    b->shots.assign(shots, shots + nshots);
+    b->device = shots[0]->device;
+    b->nt = shots[0]->cfg.nt;
+    DeviceGuard guard(b->device);
+    b->desc.resize(nshots);
+    std::vector<int> cta_shot, cta_local, cta_len;
+    for (int i = 0; i < nshots; ++i) {
+        mmod_handle *h = shots[i];
+        ShotDesc &d = b->desc[i];
+        std::memset(&d, 0, sizeof(d));
+        for (int k = 0; k < 2; ++k) {
+            d.cur[k] = h->cur_map[k];
+            d.prev[k] = h->prev_map[k];
+            d.u[k] = h->u[k];
+        }
+        d.cmap = h->c_map;
+        d.args = base_args(h, h->fwd, nullptr);
+        const TmaPlan &p = h->plans[0];
+        const int zchunks = (h->cfg.nz + kBatchZlen - 1) / kBatchZlen;
+        const int zlen = (h->cfg.nz + zchunks - 1) / zchunks;
+        d.geom = Geom{p.tiles_x, p.tiles_y, (h->cfg.nz + zlen - 1) / zlen, zlen};
+        d.nblocks = d.geom.tiles_x * d.geom.tiles_y * d.geom.zchunks;
+        for (int lb = 0; lb < d.nblocks; ++lb) {
+            const int chunk = lb / (d.geom.tiles_x * d.geom.tiles_y);
+            cta_shot.push_back(i);
+            cta_local.push_back(lb);
+            cta_len.push_back(std::min(zlen, h->cfg.nz - chunk * zlen));
+        }
+    }
+    // longest z ranges first: the last wave holds the short ones
+    std::vector<int> order(cta_shot.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cta_len[a] > cta_len[c]; });
+    std::vector<int> cs(order.size()), cl(order.size());
+    for (size_t q = 0; q < order.size(); ++q) {
+        cs[q] = cta_shot[order[q]];
+        cl[q] = cta_local[order[q]];
+    }
+    b->nctas = (int)cs.size();
+    auto bail = [&](cudaError_t e, const char *what) {
+        set_thread_error((std::string(what) + ": " + cudaGetErrorName(e)).c_str());
+        free_batch(b);
+        delete b;
+        return e == cudaErrorMemoryAllocation ? MMOD_ERR_OOM : MMOD_ERR_CUDA;
+    };
+#define CKB(call)                                  \
+    do {                                           \
+        cudaError_t _e = (call);                   \
+        if (_e != cudaSuccess) return bail(_e, #call); \
+    } while (0)
+    CKB(cudaMalloc(&b->d_desc, sizeof(ShotDesc) * nshots));
+    CKB(cudaMalloc(&b->d_cta_shot, sizeof(int) * cs.size()));
+    CKB(cudaMalloc(&b->d_cta_local, sizeof(int) * cl.size()));
+    CKB(cudaMemcpy(b->d_cta_shot, cs.data(), sizeof(int) * cs.size(), cudaMemcpyHostToDevice));
+    CKB(cudaMemcpy(b->d_cta_local, cl.data(), sizeof(int) * cl.size(), cudaMemcpyHostToDevice));
+    CKB(cudaEventCreate(&b->ev_t0));
+    CKB(cudaEventCreate(&b->ev_t1));
+#undef CKB
+    *out = b;
+    return MMOD_OK;
+}
+
+MMOD_API mmod_status mmod_batch_destroy(mmod_batch *b) {
+    if (!b) return MMOD_OK;
+    {
+        DeviceGuard guard(b->device);
+        cudaDeviceSynchronize();
+        free_batch(b);
+    }
+    delete b;
+    return MMOD_OK;
+}
+
+MMOD_API const char *mmod_batch_last_error(const mmod_batch *b) { return b ? b->err.c_str() : ""; }
+
+MMOD_API mmod_status mmod_batch_set_variant(mmod_batch *b, int v) {
+    if (!b) return MMOD_ERR_ARG;
+    int block, smem;
+    if (v < 0 || !tma_variant_shape(v, &block, &smem)) return bfail(b, MMOD_ERR_ARG, "unknown TMA variant");
+    b->variant = v;
+    return MMOD_OK;
+}
+
+MMOD_API mmod_status mmod_batch_forward(mmod_batch *b, const float *const *wavelets, float *const *traces,
+                                        mmod_stream stream) {
+    if (!b) return MMOD_ERR_ARG;
+    DeviceGuard guard(b->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int ns = (int)b->shots.size();
+    for (int i = 0; i < ns; ++i) {
+        mmod_handle *h = b->shots[i];
+        if (mmod_status st = check_latched(h)) return bfail(b, st, "shot " + std::to_string(i) + ": " + h->err);
+        if (!h->model_set) return bfail(b, MMOD_ERR_STATE, "shot " + std::to_string(i) + " has no model");
+        const float *w = wavelets ? wavelets[i] : nullptr;
+        float *t = traces ? traces[i] : nullptr;
+        if (h->cfg.nsrc > 0 && b->nt > 0 && (!w || !is_device_ptr(w)))
+            return bfail(b, MMOD_ERR_ARG, "shot " + std::to_string(i) + ": wavelet must be a device pointer");
+        if (h->cfg.nrec > 0 && b->nt > 0 && (!t || !is_device_ptr(t)))
+            return bfail(b, MMOD_ERR_ARG, "shot " + std::to_string(i) + ": traces must be a device pointer");
+        b->desc[i].args.wavelet = w;
+        b->desc[i].args.pdl = b->pdl ? 2 : 0;   // the captured steps follow one another
+        b->desc[i].args.err = h->err_dev;
+        b->desc[i].traces = t;
+    }
+    BCK(b, cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(ShotDesc) * ns, cudaMemcpyHostToDevice, s));
+    if (mmod_status st = zero_states(b, s)) return st;
+    if (b->nt > 0) {
+        GraphSlot &g = b->graph;
+        if (!g.exec || g.kernel != b->variant || g.opts != b->pdl) {
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+            g = GraphSlot();
+            mmod_handle *h0 = b->shots[0];
+            cudaGraph_t graph = nullptr;
+            BCK(b, cudaStreamBeginCapture(h0->cap, cudaStreamCaptureModeThreadLocal));
+            mmod_status st = MMOD_OK;
+            if (cudaEventRecordWithFlags(b->ev_t0, h0->cap, cudaEventRecordExternal) != cudaSuccess)
+                st = MMOD_ERR_CUDA;
+            if (st == MMOD_OK) st = enqueue_batch_steps(b, 0, b->nt, h0->cap);
+            if (st == MMOD_OK) {
+                batch_gather_kernel<<<dim3(64, ns), 256, 0, h0->cap>>>(b->d_desc, b->nt);
+                if (cudaGetLastError() != cudaSuccess) st = MMOD_ERR_CUDA;
+            }
+            if (st == MMOD_OK && cudaEventRecordWithFlags(b->ev_t1, h0->cap, cudaEventRecordExternal) != cudaSuccess)
+                st = MMOD_ERR_CUDA;
+            cudaError_t e_end = cudaStreamEndCapture(h0->cap, &graph);
+            if (st != MMOD_OK || e_end != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                return bfail(b, st != MMOD_OK ? st : MMOD_ERR_CUDA, "capturing the batch loop failed");
+            }
+            cudaError_t e_inst = cudaGraphInstantiate(&g.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e_inst != cudaSuccess) {
+                g.exec = nullptr;
+                return bfail_cuda(b, e_inst, "cudaGraphInstantiate");
+            }
+            g.kernel = b->variant;
+            g.opts = b->pdl;
+            g.launches = b->nt + 1;
+        }
+        BCK(b, cudaGraphLaunch(g.exec, s));
+    }
+    b->ran = b->nt > 0;
+    for (mmod_handle *h : b->shots) {
+        if (mmod_status st = check_latched(h)) return bfail(b, st, h->err);
+        h->ran = true;   // each handle's buffers hold its shot's final state
+    }
+    return MMOD_OK;
+}
+
+MMOD_API float mmod_batch_last_loop_ms(mmod_batch *b) {
+    if (!b || !b->ran) return -1.0f;
+    DeviceGuard guard(b->device);
+    float ms = -1.0f;
+    if (cudaEventSynchronize(b->ev_t1) != cudaSuccess || cudaEventElapsedTime(&ms, b->ev_t0, b->ev_t1) != cudaSuccess) {
+        cudaGetLastError();
+        return -1.0f;
+    }
+    return ms;
+}
+
+MMOD_API mmod_status mmod_batch_autotune(mmod_batch *b, int steps, mmod_stream stream, int *variant_out) {
+    if (!b || steps < 1) return MMOD_ERR_ARG;
+    DeviceGuard guard(b->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int ns = (int)b->shots.size();
+    for (int i = 0; i < ns; ++i) {
+        if (!b->shots[i]->model_set) return bfail(b, MMOD_ERR_STATE, "shot " + std::to_string(i) + " has no model");
+        b->desc[i].args.wavelet = nullptr;   // no sources while tuning
+        b->desc[i].args.inj.npts = 0;
+        b->desc[i].traces = nullptr;
+        b->desc[i].args.err = b->shots[i]->err_dev;
+        b->desc[i].args.pdl = b->pdl;
+    }
+    BCK(b, cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(ShotDesc) * ns, cudaMemcpyHostToDevice, s));
+    const int keep = b->variant;
+    int best = keep;
+    float best_ms = 1e30f;
+    for (int v = 0; v < tma_variant_count(); ++v) {
+        b->variant = v;
+        mmod_status st;
+        time_steps(b, std::min(2, steps), s, &st);   // warm-up
+        const float ms = time_steps(b, steps, s, &st);
+        if (st != MMOD_OK) {
+            b->variant = keep;
+            return st;
+        }
+        if (ms > 0 && ms < best_ms) {
+            best_ms = ms;
+            best = v;
+        }
+    }
+    for (int i = 0; i < ns; ++i) b->desc[i].args.inj.npts = b->shots[i]->fwd.inj.npts;
+    b->variant = best;
+    if (variant_out) *variant_out = best;
+    return MMOD_OK;
+}
+
+MMOD_API mmod_status mmod_autotune(mmod_handle *h, int steps, mmod_stream stream, int *variant_out) {
+    if (!h || steps < 1) return MMOD_ERR_ARG;
+    if (mmod_status st = check_latched(h)) return st;
+    if (!h->model_set) return fail(h, MMOD_ERR_STATE, "mmod_set_model has not succeeded");
+    if (!h->tma_ok) return fail(h, MMOD_ERR_UNSUPPORTED, "TMA kernel unavailable for this grid");
+    DeviceGuard guard(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int best = kTmaDefaultVariant;
+    float best_ms = 1e30f;
+    const int nsteps = std::min(steps, std::max(h->cfg.nt, 1));
+    cudaEvent_t e0, e1;
+    MMOD_CK(h, cudaEventCreate(&e0));
+    MMOD_CK(h, cudaEventCreate(&e1));
+    StepArgs a = base_args(h, h->fwd, nullptr);
+    a.inj.npts = 0;   // no sources while tuning
+    a.nrec = 0;
+    for (int v = 0; v < tma_variant_count(); ++v) {
+        h->variant = v;
+        float ms = 0.0f;
+        for (int rep = 0; rep < 2; ++rep) {   // the first repetition warms up
+            MMOD_CK(h, cudaMemsetAsync(h->u[0], 0, sizeof(float) * (size_t)h->vol, s));
+            MMOD_CK(h, cudaMemsetAsync(h->u[1], 0, sizeof(float) * (size_t)h->vol, s));
+            MMOD_CK(h, cudaEventRecord(e0, s));
+            long long count = 0;
+            for (int n = 0; n < nsteps; ++n) {
+                a.n = n;
+                a.ucur = h->u[(n + 1) & 1];
+                a.uprev = h->u[n & 1];
+                a.uout = h->u[n & 1];
+                MMOD_CK(h, enqueue_step(h, a, &h->cur_map[(n + 1) & 1], &h->prev_map[n & 1], true, nullptr, s, &count));
+            }
+            MMOD_CK(h, cudaEventRecord(e1, s));
+            MMOD_CK(h, cudaEventSynchronize(e1));
+            MMOD_CK(h, cudaEventElapsedTime(&ms, e0, e1));
+        }
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->variant = best;
+    h->ran = false;
+    if (variant_out) *variant_out = best;
+    return check_latched(h);
+}

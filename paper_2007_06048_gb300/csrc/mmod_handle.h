@@ -79,19 +79,20 @@ struct mmod_handle {
     mmod::TmaPlan plans[mmod::kMaxTmaVariants]{};
     int variant = -1;                   // -1: automatic choice
     int pdl = 1;                        // MMOD_OPT_PDL
+    int ckpt_scheme = MMOD_SCHEME_SEGMENTS;   // MMOD_OPT_CKPT_SCHEME
     bool tma_ok = false;
     CUtensorMap cur_map[2], prev_map[2], c_map;
 
     // gradient work space (lazy, sized for the last checkpoint layout)
     struct GradWork {
-        int nseg = 0, seglen = 0, dtype = -1;
-        std::vector<float *> seg;           // seglen + 2 padded volumes
+        int nslot = 0, nwork = 0, dtype = -1;
+        std::vector<float *> seg;           // nwork padded FP32 work volumes
         std::vector<CUtensorMap> seg_cur, seg_prev;
         float *psi[2] = {nullptr, nullptr};
         CUtensorMap psi_cur[2], psi_prev[2];
         float *gradc = nullptr;             // padded FP32 accumulator
-        void *ckpt = nullptr;               // nseg * 2 volumes (FP32 or 16-bit)
-        float *ckpt_scale = nullptr;        // nseg * 2 * nz per-plane scales (16-bit storage)
+        void *ckpt = nullptr;               // nslot * 2 volumes (FP32 or 16-bit)
+        float *ckpt_scale = nullptr;        // nslot * 2 * nz per-plane scales (16-bit storage)
         size_t ckpt_bytes = 0;
     } gw;
 
@@ -106,6 +107,13 @@ struct mmod_handle {
 };
 
 namespace mmod {
+
+// Binomial checkpointing (mmod_revolve.cu): one action of a reversal
+// schedule, kind = MMOD_REV_*; returns the number of advanced steps.
+struct RevAction {
+    int kind, a, b;
+};
+long long revolve_schedule(int nsteps, int snaps, std::vector<RevAction> *out);
 
 // Shared by the entry points (mmod_api.cu).
 mmod_status fail(mmod_handle *h, mmod_status st, const std::string &msg);

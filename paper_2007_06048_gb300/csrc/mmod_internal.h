@@ -12,14 +12,15 @@
 
 namespace mmod {
 
-// Point sources grouped by grid point and bucketed per (plane, x-y tile) of
+// Point sources grouped by grid point and bucketed per (x-y tile, plane) of
 // the TMA kernel (64 x 16 tiles): the points of plane k in tile (tx, ty) are
-// [tile_start[b], tile_start[b+1]), b = (k * tiles_y + ty) * tiles_x + tx.
+// [tile_start[b], tile_start[b+1]), b = (ty * tiles_x + tx) * nz + k, so the
+// points of one tile over a z range [k0, k1) are one contiguous run.
 // Point p carries the sources [pt_first[p], pt_first[p+1]) in a fixed order.
 constexpr int kInjTileX = 64, kInjTileY = 16;
 
 struct InjTable {
-    const int *tile_start;      // [nz * tiles_y * tiles_x + 1]
+    const int *tile_start;      // [tiles_y * tiles_x * nz + 1]
     const int *pt_i, *pt_j, *pt_k;
     const long long *pt_off;    // padded offset of the point
     const int *pt_first;        // [npts + 1]
@@ -49,7 +50,9 @@ struct StepArgs {
     const long long *rec_off;             // padded offsets
     float *traces;                        // [nt][nrec]
     int *err;                             // device view of the mapped error word
-    int pdl;                              // 1: launched as a programmatic dependent of the previous step
+    int pdl;                              // 0: plain launch; 1: programmatic dependent launch;
+                                          // 2: the same, and the previous kernel in the stream
+                                          //    is the previous step of this run
 };
 
 // Adds the sources of injection point p to u^{n+1} (already stored): the
@@ -83,9 +86,32 @@ cudaError_t launch_gather(const float *u, const long long *rec_off, int nrec, fl
                           cudaStream_t s);
 
 struct TmaPlan;   // tile shape / grid decomposition of the TMA kernel
+
+// x-y tiles and z ranges of one grid (one shot) for the TMA kernel.
+struct Geom {
+    int tiles_x, tiles_y, zchunks, zlen;
+};
+
+// One shot of a batch as the batch kernel reads it from global memory: its
+// tensor maps (both wavefield buffers as u^n and u^{n-1} operands, and c),
+// its step arguments (n, buffer roles and traces are set per step by the
+// kernel), buffers, traces and decomposition.
+struct ShotDesc {
+    CUtensorMap cur[2], prev[2], cmap;
+    StepArgs args;
+    float *u[2];
+    float *traces;   // [nt][nrec] or null
+    Geom geom;
+    int nblocks;     // CTAs of this shot per step
+};
 cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap *cur_map,
                             const CUtensorMap *prev_map, const CUtensorMap *c_map,
                             const TmaPlan &plan, cudaStream_t s);
+
+// All shots of a batch, one step (variant = compiled TMA variant index).
+cudaError_t launch_step_tma_batch(int variant, const ShotDesc *shots, const int *cta_shot, const int *cta_local,
+                                  int nctas, int n, bool pdl, cudaStream_t s);
+bool tma_variant_shape(int v, int *block, int *smem);
 
 cudaError_t launch_model_scan(const float *vel, long long n, unsigned int *vmax_bits,
                               unsigned long long *bad, cudaStream_t s);

@@ -180,14 +180,14 @@ extern "C" __attribute__((visibility("default"))) mmod_status mmod_forward_noall
     unsigned long long *bad = reinterpret_cast<unsigned long long *>(base + kOffMisc + 8);
     int *err = reinterpret_cast<int *>(base + kOffMisc + 16);
 
-    // ---- injection table (sources grouped by point, bucketed per plane and
+    // ---- injection table (sources grouped by point, bucketed per tile and
     // 64 x 16 tile, as the handle API builds it) and receiver offsets
     const int tiles_x = (c.nx + kInjTileX - 1) / kInjTileX, tiles_y = (c.ny + kInjTileY - 1) / kInjTileY;
     const long long nbuckets = (long long)c.nz * tiles_x * tiles_y;
     if (nbuckets > kMaxBuckets) return fail(MMOD_ERR_ARG, "grid exceeds the allocation-free limits (tile buckets)");
     auto bucket = [&](int s) {
         const int *p = c.src_ijk + 3 * s;
-        return ((long long)p[2] * tiles_y + p[1] / kInjTileY) * tiles_x + p[0] / kInjTileX;
+        return ((long long)(p[1] / kInjTileY) * tiles_x + p[0] / kInjTileX) * c.nz + p[2];
     };
     auto before = [&](int a, int b) {   // strict order: bucket, j, i, then input order
         const long long ba = bucket(a), bb = bucket(b);

@@ -1,6 +1,8 @@
 // Set-up kernels (run once per model or per call, outside the time loop):
 // model scan (maximum velocity, invalid-value count), c = dt^2 v^2 into the
 // padded layout, source scales, and dense <-> padded copies.
+#include <algorithm>
+
 #include "mmod_internal.h"
 
 namespace mmod {
@@ -194,18 +196,22 @@ __global__ void imaging_kernel(const float *__restrict__ psi, const float *__res
                                const float *__restrict__ c, const float *__restrict__ ex,
                                const float *__restrict__ ey, const float *__restrict__ ez, int nx, int ny, int nz,
                                int nxp, float *__restrict__ grad) {
-    const long long total = (long long)nxp * ny * nz;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
-         q += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(q % nxp);
-        if (i >= nx) continue;
-        const long long row = q / nxp;
-        const int j = (int)(row % ny), k = (int)(row / ny);
-        const float e = __fadd_rn(__fadd_rn(ex[i], ey[j]), ez[k]);
-        const float d2 = __fmaf_rn(__fadd_rn(1.0f, e), un[q],
-                                   __fmaf_rn(-2.0f, uc[q], __fmul_rn(__fsub_rn(1.0f, e), up[q])));
-        const float cc = c[q];
-        grad[q] = __fmaf_rn(psi[q], d2 / (cc * cc), grad[q]);
+    // one warp per grid row (j, k), lanes along x
+    const int lane = threadIdx.x & 31;
+    const int warps = (int)(blockDim.x >> 5);
+    const int rows = ny * nz;
+    for (int row = blockIdx.x * warps + (int)(threadIdx.x >> 5); row < rows; row += gridDim.x * warps) {
+        const int j = row % ny, k = row / ny;
+        const float eyj = ey[j], ezk = ez[k];
+        const long long base = (long long)row * nxp;
+        for (int i = lane; i < nx; i += 32) {
+            const long long q = base + i;
+            const float e = __fadd_rn(__fadd_rn(ex[i], eyj), ezk);
+            const float d2 = __fmaf_rn(__fadd_rn(1.0f, e), un[q],
+                                       __fmaf_rn(-2.0f, uc[q], __fmul_rn(__fsub_rn(1.0f, e), up[q])));
+            const float cc = c[q];
+            grad[q] = __fmaf_rn(psi[q], __fdiv_rn(d2, __fmul_rn(cc, cc)), grad[q]);
+        }
     }
 }
 
@@ -261,8 +267,9 @@ cudaError_t launch_unreverse_transpose(const float *g, int nt, int ncol, double 
 cudaError_t launch_imaging(const float *psi, const float *u_next, const float *u_cur, const float *u_prev,
                            const float *c, const float *ex, const float *ey, const float *ez, int nx, int ny,
                            int nz, int nxp, float *grad_c, cudaStream_t s) {
-    imaging_kernel<<<grid2((long long)nxp * ny * nz), 256, 0, s>>>(psi, u_next, u_cur, u_prev, c, ex, ey, ez, nx,
-                                                                   ny, nz, nxp, grad_c);
+    const int rows = ny * nz;
+    imaging_kernel<<<(int)std::min<long long>((rows + 7) / 8, 152LL * 16), 256, 0, s>>>(
+        psi, u_next, u_cur, u_prev, c, ex, ey, ez, nx, ny, nz, nxp, grad_c);
     return cudaGetLastError();
 }
 

@@ -124,10 +124,6 @@ __device__ __forceinline__ void tma_load_3d(float *dst, const CUtensorMap *map, 
         : "memory");
 }
 
-struct Geom {
-    int tiles_x, tiles_y, zchunks, zlen;
-};
-
 struct Ctx {
     float *cur;          // S::NSU u^n slots
     float *up;           // S::NSC u^{n-1} slots
@@ -259,11 +255,14 @@ __device__ __forceinline__ void step(const StepArgs &a, const Ctx &c, int t, flo
     }
 }
 
+// The work of one CTA: block `bid` of the `nbid` blocks of one grid (one
+// shot).  The single-shot kernel passes its parameters; the batch kernel a
+// shot's arguments staged in shared memory and that shot's tensor maps in
+// global memory.
 template <class S>
-__global__ void __launch_bounds__(S::NT)
-    step_tma_kernel(const StepArgs a, const __grid_constant__ CUtensorMap cur_map,
-                    const __grid_constant__ CUtensorMap prev_map, const __grid_constant__ CUtensorMap c_map,
-                    const Geom g) {
+__device__ __forceinline__ void step_tma_body(const StepArgs &a, const CUtensorMap *cur_map,
+                                              const CUtensorMap *prev_map, const CUtensorMap *c_map, const Geom &g,
+                                              int bid, int nbid) {
     constexpr int RY = S::RY;
     constexpr int U = S::U;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -277,7 +276,7 @@ __global__ void __launch_bounds__(S::NT)
     const int tid = threadIdx.x;
     c.lane = tid & 31;
     c.warp = tid >> 5;
-    int b = blockIdx.x;
+    int b = bid;
     const int tx = b % g.tiles_x;
     b /= g.tiles_x;
     const int ty = b % g.tiles_y;
@@ -296,22 +295,30 @@ __global__ void __launch_bounds__(S::NT)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
+    // pdl == 2: the previous kernel in the stream is the previous step of
+    // this run.  It only reads u^{n-1} (as its u^n), and the step that wrote
+    // u^{n-1} had completed before the previous step let this grid start, so
+    // the first planes of c and u^{n-1} are requested before the wait.
+    const bool early = a.pdl == 2;
+    if (early && tid == 0 && T > 0)
+        for (int t = 0; t < S::NSC && t < T; ++t) issue_c<S>(c, prev_map, c_map, t);
     if (a.pdl) {
         // Under programmatic dependent launch this grid may start while the
-        // previous step still runs: everything above is independent of it;
-        // wait for its completion (and memory) before reading u^n or u^{n-1}
-        // or writing u^{n+1}, then let the next step's grid be scheduled.
+        // previous kernel still runs: wait for its completion (and memory)
+        // before reading u^n or writing u^{n+1} over u^{n-1}, which the
+        // previous step reads; then let the next step's grid be scheduled.
         asm volatile("griddepcontrol.wait;" ::: "memory");
         asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     }
     __syncthreads();
     if (tid == 0 && T > 0) {
-        for (int seq = 0; seq < S::NSU && seq < nseq; ++seq) issue_u<S>(c, &cur_map, seq);
-        for (int t = 0; t < S::NSC && t < T; ++t) issue_c<S>(c, &prev_map, &c_map, t);
+        for (int seq = 0; seq < S::NSU && seq < nseq; ++seq) issue_u<S>(c, cur_map, seq);
+        if (!early)
+            for (int t = 0; t < S::NSC && t < T; ++t) issue_c<S>(c, prev_map, c_map, t);
     }
     // receivers of the previous step (u^n, read-only during this launch)
     if (a.traces) {
-        for (int r = blockIdx.x * S::NT + tid; r < a.nrec; r += gridDim.x * S::NT)
+        for (int r = bid * S::NT + tid; r < a.nrec; r += nbid * S::NT)
             a.traces[r] = a.ucur[__ldg(a.rec_off + r)];
     }
     if (T <= 0) return;
@@ -364,7 +371,7 @@ __global__ void __launch_bounds__(S::NT)
     __syncthreads();
     if (!*c.abort_flag) {
         if (tid == 0)
-            for (int seq = u_hi; seq < S::NSU + kRadius && seq < nseq; ++seq) issue_u<S>(c, &cur_map, seq);
+            for (int seq = u_hi; seq < S::NSU + kRadius && seq < nseq; ++seq) issue_u<S>(c, cur_map, seq);
         u_hi = min(S::NSU + kRadius, nseq);
         if constexpr (NA < 2 * kRadius) {
 #pragma unroll 1
@@ -388,8 +395,8 @@ __global__ void __launch_bounds__(S::NT)
         __syncthreads();                                                                    \
         if (*c.abort_flag) break;                                                           \
         if (tid == 0) {                                                                     \
-            if (t + (J) + kRadius + S::NSU < nseq) issue_u<S>(c, &cur_map, t + (J) + kRadius + S::NSU); \
-            if (t + (J) + S::NSC < T) issue_c<S>(c, &prev_map, &c_map, t + (J) + S::NSC);        \
+            if (t + (J) + kRadius + S::NSU < nseq) issue_u<S>(c, cur_map, t + (J) + kRadius + S::NSU); \
+            if (t + (J) + S::NSC < T) issue_c<S>(c, prev_map, c_map, t + (J) + S::NSC);        \
         }                                                                                   \
         u_hi = min(t + (J) + kRadius + S::NSU + 1, nseq);                                      \
         c_hi = min(t + (J) + S::NSC + 1, T);                                                   \
@@ -409,17 +416,14 @@ __global__ void __launch_bounds__(S::NT)
     }
     // Sources of this CTA's tile and planes: nothing in this launch reads the
     // u^{n+1} it writes, so they are added once the whole z range is stored
-    // (the block barrier makes every thread's stores visible).  One warp per
-    // plane, one lane per injection point.
+    // (the block barrier makes every thread's stores visible).  The points of
+    // one tile over planes [z0, z0 + T) are one run of the table; one thread
+    // per injection point.
     __syncthreads();
-    if (!*c.abort_flag) {
-        const int tile = (c.y0 / kInjTileY) * a.inj.tiles_x + c.x0 / kInjTileX;
-        const int per_plane = a.inj.tiles_y * a.inj.tiles_x;
-        for (int k = c.z0 + c.warp; k < c.z0 + T; k += S::NWARP) {
-            const int lo = __ldg(a.inj.tile_start + k * per_plane + tile);
-            const int hi = __ldg(a.inj.tile_start + k * per_plane + tile + 1);
-            for (int p = lo + c.lane; p < hi; p += 32) inject_point(a, p);
-        }
+    if (!*c.abort_flag && a.inj.npts > 0) {
+        const long long b = ((long long)(c.y0 / kInjTileY) * a.inj.tiles_x + c.x0 / kInjTileX) * a.nz + c.z0;
+        const int lo = __ldg(a.inj.tile_start + b), hi = __ldg(a.inj.tile_start + b + T);
+        for (int p = lo + tid; p < hi; p += S::NT) inject_point(a, p);
     }
     // After a give-up, wait (bounded) for the copies this CTA still has in
     // flight (the latest sequence of every slot) before its shared memory is
@@ -428,6 +432,55 @@ __global__ void __launch_bounds__(S::NT)
         for (int seq = max(0, u_hi - S::NSU); seq < u_hi; ++seq) mbar_drain(&c.full_u[seq % S::NSU], (seq / S::NSU) & 1);
         for (int t = max(0, c_hi - S::NSC); t < c_hi; ++t) mbar_drain(&c.full_c[t % S::NSC], (t / S::NSC) & 1);
     }
+}
+
+template <class S>
+__global__ void __launch_bounds__(S::NT)
+    step_tma_kernel(const StepArgs a, const __grid_constant__ CUtensorMap cur_map,
+                    const __grid_constant__ CUtensorMap prev_map, const __grid_constant__ CUtensorMap c_map,
+                    const Geom g) {
+    step_tma_body<S>(a, &cur_map, &prev_map, &c_map, g, blockIdx.x, gridDim.x);
+}
+
+// Batch: every shot of the batch advances one step in one launch.  CTA b
+// serves shot cta_shot[b] as its block cta_local[b]; the shot's arguments
+// are copied to shared memory, its buffer roles follow the step parity.
+// The shot's StepArgs live in dynamic shared memory just past the body's
+// rings and barriers, so the kernel declares no static shared memory and the
+// rings keep the dynamic window's 128-byte alignment.
+template <class S>
+__host__ __device__ constexpr int batch_args_offset() {
+    return (S::SMEM + 15) / 16 * 16;
+}
+template <class S>
+__host__ __device__ constexpr int batch_smem() {
+    return batch_args_offset<S>() + (int)sizeof(StepArgs);
+}
+
+template <class S>
+__global__ void __launch_bounds__(S::NT)
+    step_tma_batch_kernel(const ShotDesc *__restrict__ shots, const int *__restrict__ cta_shot,
+                          const int *__restrict__ cta_local, int n) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    StepArgs &sa = *reinterpret_cast<StepArgs *>(smem + batch_args_offset<S>());
+    const int shot = __ldg(cta_shot + blockIdx.x);
+    const ShotDesc *d = shots + shot;
+    {
+        const int *src = reinterpret_cast<const int *>(&d->args);
+        int *dst = reinterpret_cast<int *>(&sa);
+        for (int i = threadIdx.x; i < (int)(sizeof(StepArgs) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        sa.n = n;
+        sa.ucur = d->u[(n + 1) & 1];
+        sa.uprev = d->u[n & 1];
+        sa.uout = d->u[n & 1];
+        sa.traces = (n >= 1 && d->traces && sa.nrec > 0) ? d->traces + (long long)(n - 1) * sa.nrec : nullptr;
+    }
+    __syncthreads();
+    step_tma_body<S>(sa, &d->cur[(n + 1) & 1], &d->prev[n & 1], &d->cmap, d->geom, __ldg(cta_local + blockIdx.x),
+                     d->nblocks);
 }
 
 using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -477,10 +530,13 @@ using V22_4s = Shape<kTY, 2, 4, 6, 2>;
 struct Variant {
     const char *name;
     const void *fn;
-    int nt, smem;
+    const void *batch_fn;
+    int nt, smem, batch_smem;
 };
 
-#define MMOD_VARIANT(V, desc) {desc, (const void *)step_tma_kernel<V>, V::NT, V::SMEM}
+#define MMOD_VARIANT(V, desc) \
+    {desc, (const void *)step_tma_kernel<V>, (const void *)step_tma_batch_kernel<V>, V::NT, V::SMEM, \
+     batch_smem<V>()}
 const Variant kVariants[] = {
     MMOD_VARIANT(V22_1, "64x16 tile, 2x2 points/thread, z unroll 1"),
     MMOD_VARIANT(V22_2, "64x16 tile, 2x2 points/thread, z unroll 2"),
@@ -519,6 +575,7 @@ bool make_tma_plan(const mmod_config &cfg, int nxp, float *const u[2], const flo
         const Variant &var = kVariants[v];
         int occ = 0;
         if (cudaFuncSetAttribute(var.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, var.smem) != cudaSuccess ||
+            cudaFuncSetAttribute(var.batch_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, var.batch_smem) != cudaSuccess ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, var.fn, var.nt, var.smem) != cudaSuccess || occ < 1) {
             cudaGetLastError();
             return false;
@@ -578,6 +635,43 @@ cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap *cur_map, const
         default: return cudaErrorInvalidValue;
     }
 #undef MMOD_LAUNCH
+    return cudaGetLastError();
+}
+
+bool tma_variant_shape(int v, int *block, int *smem) {
+    if (v < 0 || v >= kNumVariants) return false;
+    *block = kVariants[v].nt;
+    *smem = kVariants[v].smem;
+    return true;
+}
+
+cudaError_t launch_step_tma_batch(int variant, const ShotDesc *shots, const int *cta_shot, const int *cta_local,
+                                  int nctas, int n, bool pdl, cudaStream_t s) {
+    if (variant < 0 || variant >= kNumVariants) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(nctas);
+    lc.blockDim = dim3(kVariants[variant].nt);
+    lc.dynamicSmemBytes = kVariants[variant].batch_smem;
+    lc.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = attr;
+    lc.numAttrs = pdl ? 1 : 0;
+    cudaError_t e;
+#define MMOD_LAUNCH_B(V) e = cudaLaunchKernelEx(&lc, step_tma_batch_kernel<V>, shots, cta_shot, cta_local, n)
+    switch (variant) {
+        case 0: MMOD_LAUNCH_B(V22_1); break;
+        case 1: MMOD_LAUNCH_B(V22_2); break;
+        case 2: MMOD_LAUNCH_B(V22_4); break;
+        case 3: MMOD_LAUNCH_B(V24_1); break;
+        case 4: MMOD_LAUNCH_B(V24_2); break;
+        case 5: MMOD_LAUNCH_B(V24_2s); break;
+        case 6: MMOD_LAUNCH_B(V22_4s); break;
+        default: return cudaErrorInvalidValue;
+    }
+#undef MMOD_LAUNCH_B
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

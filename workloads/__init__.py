@@ -64,13 +64,14 @@ def cfl_dt(cfl: float, h, vmax: float) -> float:
     return float(cfl) * float(min(h)) / float(vmax)
 
 
-def _smooth_noise(shape, sigma: float, seed: int, amp: float) -> np.ndarray:
-    """White N(0,1) noise, Gaussian-smoothed (sigma in cells), scaled to max |.| = amp."""
+def _smooth_noise(shape, sigma: float, seed: int, amp: float, dtype=np.float64) -> np.ndarray:
+    """White N(0,1) noise, Gaussian-smoothed (sigma in cells), scaled to max |.| = amp.
+    dtype sets the precision of the smoothing (FP32 for the large batched set)."""
     from scipy.ndimage import gaussian_filter
     rng = np.random.default_rng(seed)
-    n = rng.standard_normal(shape)
+    n = rng.standard_normal(shape).astype(dtype)
     s = gaussian_filter(n, sigma=sigma, mode="wrap")
-    return s * (amp / np.max(np.abs(s)))
+    return (s * (amp / np.max(np.abs(s)))).astype(np.float64)
 
 
 def surface_grid(nx: int, ny: int, k: int = 0, start: int = 0, stride: int = 1,
@@ -144,30 +145,37 @@ def smooth_gradient_200(nt: int = 1000, n: int = 200, anomaly: bool = False) -> 
 
 def batched_shots(nshots: int = 32, nt: int = 800, seed: int = 4) -> list:
     """Shots with uneven grids: nx, ny in U{128..320}, nz in U{128..256} (step 16),
-    L = 20, per-shot 3-5 flat layers (seed 4+s) times a +-5% smoothed field,
-    Ricker f ~ U[8, 20] Hz at (nx/2, ny/2, 4), receivers at k = 0 with stride 4."""
+    L = 20, per-shot 3-5 flat layers (seed 4+s) times a +-5% smoothed field
+    (smoothing in FP32), Ricker f ~ U[8, 20] Hz at (nx/2, ny/2, 4), receivers
+    at k = 0 with stride 4.  Sizes are drawn in order from seed; each shot's
+    model only from its own seeds, so the shots are built in parallel."""
+    from concurrent.futures import ThreadPoolExecutor
     rng = np.random.default_rng(seed)
-    shots = []
+    dims = []
     for s in range(nshots):
         nx = int(rng.choice(np.arange(128, 321, 16)))
         ny = int(rng.choice(np.arange(128, 321, 16)))
         nz = int(rng.choice(np.arange(128, 257, 16)))
-        f = float(rng.uniform(8.0, 20.0))
+        dims.append((nx, ny, nz, float(rng.uniform(8.0, 20.0))))
+
+    def build(s):
+        nx, ny, nz, f = dims[s]
         r2 = np.random.default_rng(seed + s)
         nl = int(r2.integers(3, 6))
         depths = np.sort(r2.choice(np.arange(30, nz - 30), size=nl - 1, replace=False))
         lv = np.sort(r2.uniform(1500.0, 4500.0, size=nl))
         vz = lv[np.searchsorted(depths, np.arange(nz), side="right")]
-        vel = np.broadcast_to(vz[:, None, None], (nz, ny, nx)).astype(np.float64)
-        vel = vel * (1.0 + _smooth_noise((nz, ny, nx), 4.0, 1000 + seed + s, 0.05))
-        vel32 = vel.astype(np.float32)
+        pert = _smooth_noise((nz, ny, nx), 4.0, 1000 + seed + s, 0.05, dtype=np.float32)
+        vel32 = (vz[:, None, None] * (1.0 + pert)).astype(np.float32)
         h = (10.0, 10.0, 10.0)
         dt = cfl_dt(0.4, h, float(vel32.max()))
         src = np.array([[nx // 2, ny // 2, 4]], np.int32)
-        shots.append(Problem(f"shot{s}-{nx}x{ny}x{nz}", vel32, h, dt, nt, 20, src,
-                             ricker(f, dt, nt)[None, :], surface_grid(nx, ny, 0, stride=4),
-                             meta={"fpeak": f}))
-    return shots
+        return Problem(f"shot{s}-{nx}x{ny}x{nz}", vel32, h, dt, nt, 20, src,
+                       ricker(f, dt, nt)[None, :], surface_grid(nx, ny, 0, stride=4),
+                       meta={"fpeak": f})
+
+    with ThreadPoolExecutor(max_workers=8) as ex:
+        return list(ex.map(build, range(nshots)))
 
 
 def fractal_large(nt: int = 500, shape=(512, 1024, 1024), seed: int = 5, beta: float = 3.0) -> Problem:
@@ -175,19 +183,21 @@ def fractal_large(nt: int = 500, shape=(512, 1024, 1024), seed: int = 5, beta: f
     with amplitude spectrum |k|^(-beta/2) (FP64 FFT, seed 5) mapped linearly to
     [1500, 5000] m/s.  dt from CFL 0.4.  Ricker 10 Hz at (nx/2, ny/2, 4);
     receivers on every (i, j) of plane k = 0."""
+    import scipy.fft as sfft
     nz, ny, nx = shape
     rng = np.random.default_rng(seed)
-    noise = rng.standard_normal(shape)
-    spec = np.fft.rfftn(noise)
+    spec = sfft.rfftn(rng.standard_normal(shape), workers=-1)
     kz = np.fft.fftfreq(nz)[:, None, None]
     ky = np.fft.fftfreq(ny)[None, :, None]
     kx = np.fft.rfftfreq(nx)[None, None, :]
-    kk = np.sqrt(kz * kz + ky * ky + kx * kx)
-    kk[0, 0, 0] = np.inf
-    spec *= kk ** (-beta / 2.0)
-    f = np.fft.irfftn(spec, s=shape)
-    f = (f - f.min()) / (f.max() - f.min())
-    vel32 = (1500.0 + 3500.0 * f).astype(np.float32)
+    kk2 = kz * kz + ky * ky + kx * kx
+    kk2[0, 0, 0] = np.inf
+    spec *= kk2 ** (-beta / 4.0)          # |k|^(-beta/2)
+    del kk2
+    f = sfft.irfftn(spec, s=shape, workers=-1)
+    del spec
+    lo, hi = f.min(), f.max()
+    vel32 = (1500.0 + 3500.0 * ((f - lo) / (hi - lo))).astype(np.float32)
     h = (12.5, 12.5, 12.5)
     dt = cfl_dt(0.4, h, 5000.0)
     src = np.array([[nx // 2, ny // 2, 4]], np.int32)
