@@ -204,11 +204,37 @@ mmod_status mmod_set_tma_variant(mmod_handle *h, int v);
  *                         overlaps the previous step's tail (default 1; the
  *                         same bits either way);
  *   MMOD_OPT_CKPT_SCHEME  MMOD_SCHEME_SEGMENTS (default) or
- *                         MMOD_SCHEME_REVOLVE: checkpointing of mmod_gradient.
+ *                         MMOD_SCHEME_REVOLVE: checkpointing of mmod_gradient;
+ *   MMOD_OPT_PERSISTENT   0 / 1: run the time loop of mmod_forward and
+ *                         mmod_adjoint as one cooperative launch in which each
+ *                         work unit (64 x 16 tile x z range) starts a step as
+ *                         soon as its neighbours finished the previous one
+ *                         (default 0: slower than one launch per step on the
+ *                         measured grids; the same bits either way; variants
+ *                         without a persistent form ignore it);
+ *   MMOD_OPT_ZLEN         >= 0: planes per z range of a CTA (0 = the plan's
+ *                         choice, which fills one wave of resident CTAs); the
+ *                         same bits for any value;
+ *   MMOD_OPT_PERSISTENT_CTAS  >= 0: at most this many CTAs for the persistent
+ *                         run (0 = as many as fit at once; a small value makes
+ *                         each CTA serve many units, for tests);
+ *   MMOD_OPT_TEST_STALL   1: test hook of the failure path.  The next
+ *                         persistent run waits for neighbour counters that
+ *                         nothing sets; every wait gives up after 100 ms, the
+ *                         kernel returns and the call reports MMOD_ERR_TIMEOUT
+ *                         (the handle stays in that state; the device and
+ *                         other handles stay usable).
  * Errors: ARG (unknown option or value). */
-enum { MMOD_OPT_PDL = 2, MMOD_OPT_CKPT_SCHEME = 3 };
+enum { MMOD_OPT_PDL = 2, MMOD_OPT_CKPT_SCHEME = 3, MMOD_OPT_PERSISTENT = 4, MMOD_OPT_PERSISTENT_CTAS = 5,
+       MMOD_OPT_TEST_STALL = 6, MMOD_OPT_ZLEN = 7 };
 enum { MMOD_SCHEME_SEGMENTS = 0, MMOD_SCHEME_REVOLVE = 1 };
 mmod_status mmod_set_option(mmod_handle *h, int option, int value);
+
+/* CTAs of the persistent kernel the next mmod_forward / mmod_adjoint of this
+ * handle will launch; 0 when it runs one launch per step (plain kernel, a
+ * variant without a persistent form, z ranges thinner than the stencil
+ * radius, or MMOD_OPT_PERSISTENT off); -1 for a null handle. */
+int mmod_persistent_grid(const mmod_handle *h);
 
 /* Launch plan of the active TMA variant: writes 8 ints {variant, tiles_x,
  * tiles_y, z_chunks, planes_per_chunk, grid, block, resident_ctas_per_sm}.

@@ -28,6 +28,10 @@ STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_UNSTABLE", -3: "ERR_OOM", -4: "ERR_CU
 KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_TMA = 0, 1, 2
 OPT_PDL = 2
 OPT_CKPT_SCHEME = 3
+OPT_PERSISTENT = 4
+OPT_PERSISTENT_CTAS = 5
+OPT_TEST_STALL = 6
+OPT_ZLEN = 7
 SCHEME_SEGMENTS, SCHEME_REVOLVE = 0, 1
 REV_ADVANCE, REV_SAVE, REV_RESTORE, REV_REVERSE = 0, 1, 2, 3
 
@@ -39,7 +43,7 @@ EXPORTED = ["mmod_create", "mmod_destroy", "mmod_set_model", "mmod_forward", "mm
             "mmod_forward_noalloc", "mmod_set_option", "mmod_adjoint", "mmod_gradient",
             "mmod_gradient_memory", "mmod_dot", "mmod_batch_create", "mmod_batch_destroy",
             "mmod_batch_forward", "mmod_batch_set_variant", "mmod_batch_last_loop_ms", "mmod_batch_last_error",
-            "mmod_autotune", "mmod_batch_autotune", "mmod_revolve_schedule"]
+            "mmod_autotune", "mmod_batch_autotune", "mmod_revolve_schedule", "mmod_persistent_grid"]
 CKPT_FP32, CKPT_BF16, CKPT_FP16 = 0, 1, 2
 
 
@@ -109,6 +113,7 @@ def load():
         "mmod_batch_autotune": ([P, I, P, ctypes.POINTER(I)], I),
         "mmod_revolve_schedule": ([I, I, P, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong),
                                    ctypes.POINTER(ctypes.c_longlong)], I),
+        "mmod_persistent_grid": ([P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -383,6 +388,10 @@ class Propagator:
 
     def plan(self) -> dict:
         return mmod_get_plan(self.handle)
+
+    def persistent_grid(self) -> int:
+        """CTAs of the persistent kernel the next run launches (0: one launch per step)."""
+        return int(load().mmod_persistent_grid(self.handle))
 
     def set_option(self, option: int, value: int):
         mmod_set_option(self.handle, option, value)

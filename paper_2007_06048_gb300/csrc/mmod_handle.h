@@ -34,6 +34,9 @@ struct Geometry {
     long long *gather_off = nullptr;
     int ngather = 0;
     double cell = 1.0;   // divisor of the injection scale
+    // gathers bucketed per (64 x 16 tile, plane) for the persistent kernel
+    int *g_start = nullptr, *g_idx = nullptr;
+    long long *g_off = nullptr;
 };
 
 // A cached CUDA graph of one time loop.
@@ -79,6 +82,13 @@ struct mmod_handle {
     mmod::TmaPlan plans[mmod::kMaxTmaVariants]{};
     int variant = -1;                   // -1: automatic choice
     int pdl = 1;                        // MMOD_OPT_PDL
+    int persistent = 1;                 // MMOD_OPT_PERSISTENT
+    int persistent_ctas = 0;            // MMOD_OPT_PERSISTENT_CTAS (0: as many as fit)
+    int test_stall = 0;                 // MMOD_OPT_TEST_STALL (one run)
+    int zlen_override = 0;              // MMOD_OPT_ZLEN (0: the plan's z ranges)
+    mutable mmod::TmaPlan plan_tmp;     // active_plan() with the override applied
+    int *counters = nullptr;            // per work unit of the persistent kernel
+    long long ncounters = 0;
     int ckpt_scheme = MMOD_SCHEME_SEGMENTS;   // MMOD_OPT_CKPT_SCHEME
     bool tma_ok = false;
     CUtensorMap cur_map[2], prev_map[2], c_map;
@@ -121,6 +131,7 @@ mmod_status fail_cuda(mmod_handle *h, cudaError_t e, const char *what);
 mmod_status check_latched(mmod_handle *h);
 bool is_device_ptr(const void *p);
 bool use_tma(const mmod_handle *h);
+int persistent_grid_of(const mmod_handle *h);
 const TmaPlan &active_plan(const mmod_handle *h);
 StepArgs base_args(mmod_handle *h, const Geometry &geo, const float *wavelet);
 // Enqueues one step (plain path: step, injection, optional gather of

@@ -57,16 +57,19 @@ struct StepArgs {
 
 // Adds the sources of injection point p to u^{n+1} (already stored): the
 // point's damping factor r scales each term, sources in table order.
-__device__ __forceinline__ void inject_point(const StepArgs &a, int p) {
+// uout / n: the step's u^{n+1} buffer and step index.
+__device__ __forceinline__ void inject_point_at(const StepArgs &a, float *uout, int n, int p) {
     const int i = __ldg(a.inj.pt_i + p), j = __ldg(a.inj.pt_j + p), k = __ldg(a.inj.pt_k + p);
     const float r = damp_factor(__fadd_rn(__fadd_rn(__ldg(a.ex + i), __ldg(a.ey + j)), __ldg(a.ez + k)));
-    float *dst = a.uout + __ldg(a.inj.pt_off + p);
+    float *dst = uout + __ldg(a.inj.pt_off + p);
     float v = *dst;
     for (int s = __ldg(a.inj.pt_first + p); s < __ldg(a.inj.pt_first + p + 1); ++s)
         v = add_source(v, __ldg(a.inj.src_scale + s),
-                       __ldg(a.wavelet + (long long)__ldg(a.inj.src_row + s) * a.nt + a.n), r);
+                       __ldg(a.wavelet + (long long)__ldg(a.inj.src_row + s) * a.nt + n), r);
     *dst = v;
 }
+
+__device__ __forceinline__ void inject_point(const StepArgs &a, int p) { inject_point_at(a, a.uout, a.n, p); }
 
 // Host helpers shared by the entry points (mmod_api.cu).
 void damping_profile(int n, int nbl, double h, double vmax, double R, double dt, float *out);
@@ -107,6 +110,34 @@ struct ShotDesc {
 cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap *cur_map,
                             const CUtensorMap *prev_map, const CUtensorMap *c_map,
                             const TmaPlan &plan, cudaStream_t s);
+
+// Persistent run: one cooperative launch advances steps n0 .. n1-1.  Each CTA
+// owns the work units (tile x z range) unit = blockIdx.x + k * gridDim.x;
+// a unit starts step n once its 26 neighbours have completed step n-1
+// (counters[v] >= n: they wrote the u^n it reads and finished reading the
+// u^{n-1} it overwrites), so no launch boundary separates the steps.  The
+// receivers of a unit (bucketed like the injection table: entries
+// [rec_start[b], rec_start[b+1]), b = tile * nz + k) are recorded by the
+// unit right after its sources.
+struct TmaMaps {
+    CUtensorMap cur[2], prev[2], c;   // u^n / u^{n-1} operand maps of both buffers, c
+};
+struct PersistArgs {
+    int n0, n1, units;
+    int *counters;                    // per unit: steps completed, zeroed before the run
+    const int *rec_start, *rec_idx;   // receivers bucketed per (tile, plane); original index
+    const long long *rec_off;         // padded offset of each bucketed receiver
+    float *traces;                    // [nt][nrec] or null
+    int nrec;
+    float *u[2];
+};
+// Work units of the persistent kernel: the plan's tiles and z ranges of at
+// least kRadius planes.  Grid: CTAs that fit at once, capped by max_ctas > 0;
+// 0 when the variant has no persistent instantiation.
+Geom persistent_geom(const TmaPlan &plan, int nz);
+int persistent_grid(const TmaPlan &plan, int nz, int max_ctas);
+cudaError_t launch_step_tma_persistent(const StepArgs &a, const TmaMaps &maps, const TmaPlan &plan,
+                                       const PersistArgs &pa, int grid, cudaStream_t s);
 
 // All shots of a batch, one step (variant = compiled TMA variant index).
 cudaError_t launch_step_tma_batch(int variant, const ShotDesc *shots, const int *cta_shot, const int *cta_local,

@@ -29,6 +29,7 @@
 // Waits are bounded (100 ms of wall-clock time each): a wait that gives up sets
 // the mapped error word, the CTA stops at the next block barrier, drains its
 // outstanding copies (bounded) and returns; the host reports MMOD_ERR_TIMEOUT.
+#include <algorithm>
 #include <cstdint>
 
 #include "mmod_internal.h"
@@ -41,8 +42,9 @@ constexpr int TX = 64;                 // tile width: 32 lanes x 2 points
 constexpr int HX = TX + 2 * kRadius;   // 72: halo tile width
 constexpr unsigned long long kWaitNs = 100000000ull;   // a wait gives up after 100 ms
 
-template <int TY_, int RY_, int U_, int NSU_ = 8, int NSC_ = 4>
+template <int TY_, int RY_, int U_, int NSU_ = 8, int NSC_ = 4, int MINB_ = 1>
 struct Shape {
+    static constexpr int MINB = MINB_;              // resident CTAs per SM the registers are capped for
     static constexpr int TY = TY_;
     static constexpr int RY = RY_;
     static constexpr int U = U_;                    // z steps per unrolled block
@@ -65,6 +67,26 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Orders this thread's view of global memory (generic proxy) before its
+// later bulk-tensor copies (async proxy).
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+__device__ __forceinline__ int ld_acquire_gpu(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_gpu(int *p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
@@ -255,14 +277,84 @@ __device__ __forceinline__ void step(const StepArgs &a, const Ctx &c, int t, flo
     }
 }
 
+// Per-step values of a launch, kept apart from StepArgs so the persistent
+// kernel can take StepArgs from its (constant) parameters: the step, the
+// u^{n+1} buffer, and for one-launch-per-step runs the previous step's
+// receivers (traces[n-1] = u^n, gathered from ucur; null: none).
+struct StepVar {
+    int n;
+    float *uout;
+    const float *ucur;
+    float *traces;
+};
+
+// What a CTA waits for before it reads u^n and overwrites u^{n-1}.
+//
+// One launch per step: the previous step's grid, through programmatic
+// dependent launch (pdl 1 or 2) or the launch order (pdl 0).  With pdl == 2
+// the previous kernel is the previous step, which only reads u^{n-1}, so the
+// c and u^{n-1} planes are requested before the wait.
+struct PdlDep {
+    int pdl;
+    static constexpr bool kProxyFence = false;
+    __device__ bool early() const { return pdl == 2; }
+    __device__ bool reinit() const { return false; }
+    __device__ void wait(int, int *, int *) const {
+        if (pdl) {
+            asm volatile("griddepcontrol.wait;" ::: "memory");
+            asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+        }
+    }
+};
+
+// Persistent run: the 26 neighbouring units (x-y tiles and z ranges, with
+// diagonals: the u^n halo box touches all of them) must have completed step
+// n-1.  One thread polls each neighbour's counter (acquire, bounded by
+// kWaitNs; a give-up sets the abort flag and the error word).  The unit's
+// own u^{n-1} and c are its own earlier writes or constant, so they are
+// requested before the wait.  Barriers of an earlier unit are invalidated
+// and set up again.
+struct NeighborDep {
+    const int *counters;
+    int unit, n;
+    Geom g;
+    bool first;
+    static constexpr bool kProxyFence = true;
+    __device__ bool early() const { return true; }
+    __device__ bool reinit() const { return !first; }
+    __device__ void wait(int tid, int *abort_flag, int *err) const;
+};
+
+__device__ __noinline__ void NeighborDep::wait(int tid, int *abort_flag, int *err) const {
+    if (tid >= 27 || tid == 13) return;   // 13: the unit itself
+    int b = unit;
+    const int tx = b % g.tiles_x;
+    b /= g.tiles_x;
+    const int ty = b % g.tiles_y;
+    const int ch = b / g.tiles_y;
+    const int vx = tx + tid % 3 - 1, vy = ty + (tid / 3) % 3 - 1, vz = ch + tid / 9 - 1;
+    if (vx < 0 || vx >= g.tiles_x || vy < 0 || vy >= g.tiles_y || vz < 0 || vz >= g.zchunks) return;
+    const int *cnt = counters + (vz * g.tiles_y + vy) * g.tiles_x + vx;
+    if (ld_acquire_gpu(cnt) >= n) return;
+    const unsigned long long t0 = global_ns();
+    while (ld_acquire_gpu(cnt) < n) {
+        if (*(volatile int *)err || global_ns() - t0 >= kWaitNs) {
+            *(volatile int *)abort_flag = 1;
+            atomicExch(err, 1);
+            return;
+        }
+        __nanosleep(64);
+    }
+}
+
 // The work of one CTA: block `bid` of the `nbid` blocks of one grid (one
 // shot).  The single-shot kernel passes its parameters; the batch kernel a
 // shot's arguments staged in shared memory and that shot's tensor maps in
 // global memory.
-template <class S>
-__device__ __forceinline__ void step_tma_body(const StepArgs &a, const CUtensorMap *cur_map,
+template <class S, class Dep>
+__device__ __forceinline__ void step_tma_body(const StepArgs &a, const StepVar &v, const CUtensorMap *cur_map,
                                               const CUtensorMap *prev_map, const CUtensorMap *c_map, const Geom &g,
-                                              int bid, int nbid) {
+                                              int bid, int nbid, const Dep &dep) {
     constexpr int RY = S::RY;
     constexpr int U = S::U;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -289,37 +381,37 @@ __device__ __forceinline__ void step_tma_body(const StepArgs &a, const CUtensorM
     const int nseq = T + 2 * kRadius;   // u^n planes z0-4 .. z0+T+3
 
     if (tid == 0) {
+        if (dep.reinit()) {   // the previous unit consumed every copy it issued
+            for (int s = 0; s < S::NSU; ++s) mbar_inval(&c.full_u[s]);
+            for (int s = 0; s < S::NSC; ++s) mbar_inval(&c.full_c[s]);
+        }
         for (int s = 0; s < S::NSU; ++s) mbar_init(&c.full_u[s], 1);
         for (int s = 0; s < S::NSC; ++s) mbar_init(&c.full_c[s], 1);
         *c.abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    // pdl == 2: the previous kernel in the stream is the previous step of
-    // this run.  It only reads u^{n-1} (as its u^n), and the step that wrote
-    // u^{n-1} had completed before the previous step let this grid start, so
-    // the first planes of c and u^{n-1} are requested before the wait.
-    const bool early = a.pdl == 2;
-    if (early && tid == 0 && T > 0)
+    if constexpr (Dep::kProxyFence) __syncthreads();   // the flag is 0 before any waiter may set it
+    // c and u^{n-1} first where the dependency allows it (see PdlDep and
+    // NeighborDep), then wait, then u^n.
+    const bool early = dep.early();
+    if (early && tid == 0 && T > 0) {
+        if constexpr (Dep::kProxyFence) fence_proxy_async_global();
         for (int t = 0; t < S::NSC && t < T; ++t) issue_c<S>(c, prev_map, c_map, t);
-    if (a.pdl) {
-        // Under programmatic dependent launch this grid may start while the
-        // previous kernel still runs: wait for its completion (and memory)
-        // before reading u^n or writing u^{n+1} over u^{n-1}, which the
-        // previous step reads; then let the next step's grid be scheduled.
-        asm volatile("griddepcontrol.wait;" ::: "memory");
-        asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     }
+    dep.wait(tid, c.abort_flag, a.err);
     __syncthreads();
-    if (tid == 0 && T > 0) {
+    const bool dep_ok = !*c.abort_flag;
+    if (tid == 0 && T > 0 && dep_ok) {
+        if constexpr (Dep::kProxyFence) fence_proxy_async_global();
         for (int seq = 0; seq < S::NSU && seq < nseq; ++seq) issue_u<S>(c, cur_map, seq);
         if (!early)
             for (int t = 0; t < S::NSC && t < T; ++t) issue_c<S>(c, prev_map, c_map, t);
     }
     // receivers of the previous step (u^n, read-only during this launch)
-    if (a.traces) {
+    if (v.traces) {
         for (int r = bid * S::NT + tid; r < a.nrec; r += nbid * S::NT)
-            a.traces[r] = a.ucur[__ldg(a.rec_off + r)];
+            v.traces[r] = v.ucur[__ldg(a.rec_off + r)];
     }
     if (T <= 0) return;
 
@@ -343,7 +435,7 @@ __device__ __forceinline__ void step_tma_body(const StepArgs &a, const CUtensorM
     for (int r = 0; r < RY; ++r) {
         const int y = c.y0 + RY * c.warp + r;
         eyr[r] = y < a.ny ? __ldg(a.ey + y) : 0.0f;
-        out_row[r] = (y < a.ny && x < a.nx) ? a.uout + (long long)y * a.nxp + x : nullptr;
+        out_row[r] = (y < a.ny && x < a.nx) ? v.uout + (long long)y * a.nxp + x : nullptr;
     }
     const bool xy_damped = c.x0 < a.nbl || c.x0 + TX - 1 > a.nx - 1 - a.nbl || c.y0 < a.nbl ||
                            c.y0 + S::TY - 1 > a.ny - 1 - a.nbl;
@@ -351,8 +443,8 @@ __device__ __forceinline__ void step_tma_body(const StepArgs &a, const CUtensorM
     float2 q[S::QD][RY];
     // Issue order of u^n sequences is 0, 1, 2, ... with no gaps: the prologue
     // issues 0..S::NSU-1, the fill below 4 more, then one per finished step.
-    int u_hi = min(S::NSU, nseq);
-    int c_hi = min(S::NSC, T);
+    int u_hi = dep_ok ? min(S::NSU, nseq) : 0;
+    int c_hi = (dep_ok || early) ? min(S::NSC, T) : 0;
     // planes z0-4 .. z0+3 (sequences 0..7) fill queue slots 0..7.  Phase A
     // reads what the prologue issued (sequences 0..min(NSU,8)-1); the slots
     // of sequences 0..3 (never a centre) then take NSU..NSU+3; phase B reads
@@ -423,7 +515,7 @@ __device__ __forceinline__ void step_tma_body(const StepArgs &a, const CUtensorM
     if (!*c.abort_flag && a.inj.npts > 0) {
         const long long b = ((long long)(c.y0 / kInjTileY) * a.inj.tiles_x + c.x0 / kInjTileX) * a.nz + c.z0;
         const int lo = __ldg(a.inj.tile_start + b), hi = __ldg(a.inj.tile_start + b + T);
-        for (int p = lo + tid; p < hi; p += S::NT) inject_point(a, p);
+        for (int p = lo + tid; p < hi; p += S::NT) inject_point_at(a, v.uout, v.n, p);
     }
     // After a give-up, wait (bounded) for the copies this CTA still has in
     // flight (the latest sequence of every slot) before its shared memory is
@@ -435,11 +527,12 @@ __device__ __forceinline__ void step_tma_body(const StepArgs &a, const CUtensorM
 }
 
 template <class S>
-__global__ void __launch_bounds__(S::NT)
+__global__ void __launch_bounds__(S::NT, S::MINB)
     step_tma_kernel(const StepArgs a, const __grid_constant__ CUtensorMap cur_map,
                     const __grid_constant__ CUtensorMap prev_map, const __grid_constant__ CUtensorMap c_map,
                     const Geom g) {
-    step_tma_body<S>(a, &cur_map, &prev_map, &c_map, g, blockIdx.x, gridDim.x);
+    step_tma_body<S>(a, StepVar{a.n, a.uout, a.ucur, a.traces}, &cur_map, &prev_map, &c_map, g, blockIdx.x,
+                     gridDim.x, PdlDep{a.pdl});
 }
 
 // Batch: every shot of the batch advances one step in one launch.  CTA b
@@ -458,7 +551,7 @@ __host__ __device__ constexpr int batch_smem() {
 }
 
 template <class S>
-__global__ void __launch_bounds__(S::NT)
+__global__ void __launch_bounds__(S::NT, S::MINB)
     step_tma_batch_kernel(const ShotDesc *__restrict__ shots, const int *__restrict__ cta_shot,
                           const int *__restrict__ cta_local, int n) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -479,8 +572,52 @@ __global__ void __launch_bounds__(S::NT)
         sa.traces = (n >= 1 && d->traces && sa.nrec > 0) ? d->traces + (long long)(n - 1) * sa.nrec : nullptr;
     }
     __syncthreads();
-    step_tma_body<S>(sa, &d->cur[(n + 1) & 1], &d->prev[n & 1], &d->cmap, d->geom, __ldg(cta_local + blockIdx.x),
-                     d->nblocks);
+    step_tma_body<S>(sa, StepVar{sa.n, sa.uout, sa.ucur, sa.traces}, &d->cur[(n + 1) & 1], &d->prev[n & 1],
+                     &d->cmap, d->geom, __ldg(cta_local + blockIdx.x), d->nblocks, PdlDep{sa.pdl});
+}
+
+// Persistent run (PersistArgs): steps n0 .. n1-1 in one cooperative launch.
+// StepArgs stay in the kernel's constant parameters (a.pdl is ignored); the
+// step and the buffer roles go in a StepVar; each unit signals its counter
+// once its u^{n+1} (sources and receivers included) is complete.
+template <class S>
+__global__ void __launch_bounds__(S::NT, S::MINB)
+    step_tma_persistent_kernel(const StepArgs a, const __grid_constant__ TmaMaps maps, const Geom g,
+                               const PersistArgs pa) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int *abort_flag = reinterpret_cast<const int *>(smem + (S::NSU * S::CUR + S::NSC * 2 * S::PC) * 4 +
+                                                          (S::NSU + S::NSC) * 8);
+    bool first = true;
+    for (int n = pa.n0; n < pa.n1; ++n) {
+        float *uout = pa.u[n & 1];
+        for (int unit = blockIdx.x; unit < pa.units; unit += gridDim.x) {
+            step_tma_body<S>(a, StepVar{n, uout, nullptr, nullptr}, &maps.cur[(n + 1) & 1], &maps.prev[n & 1],
+                             &maps.c, g, unit, pa.units, NeighborDep{pa.counters, unit, n, g, first});
+            first = false;
+            __syncthreads();
+            if (*abort_flag) return;   // the body drained its copies; waiters give up on the error word
+            // receivers of this unit: u^{n+1} after its sources
+            if (pa.traces && pa.nrec > 0) {
+                int b = unit;
+                const int tx = b % g.tiles_x;
+                b /= g.tiles_x;
+                const int ty = b % g.tiles_y;
+                const int z0 = (b / g.tiles_y) * g.zlen;
+                const int T = min(a.nz - z0, g.zlen);
+                const long long q = ((long long)ty * g.tiles_x + tx) * a.nz + z0;
+                const int lo = __ldg(pa.rec_start + q), hi = __ldg(pa.rec_start + q + T);
+                float *row = pa.traces + (long long)n * pa.nrec;
+                for (int p = lo + threadIdx.x; p < hi; p += blockDim.x)
+                    row[__ldg(pa.rec_idx + p)] = uout[__ldg(pa.rec_off + p)];
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                fence_proxy_async_global();
+                __threadfence();
+                st_release_gpu(pa.counters + unit, n + 1);
+            }
+        }
+    }
 }
 
 using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -526,25 +663,32 @@ using V24_1 = Shape<kTY, 4, 1>;
 using V24_2 = Shape<kTY, 4, 2>;
 using V24_2s = Shape<kTY, 4, 2, 6, 2>;
 using V22_4s = Shape<kTY, 2, 4, 6, 2>;
+using V22_4s3 = Shape<kTY, 2, 4, 6, 2, 3>;
+using V22_2s3 = Shape<kTY, 2, 2, 6, 2, 3>;
 
 struct Variant {
     const char *name;
     const void *fn;
     const void *batch_fn;
+    const void *persist_fn;   // null: no persistent form compiled
     int nt, smem, batch_smem;
 };
 
-#define MMOD_VARIANT(V, desc) \
-    {desc, (const void *)step_tma_kernel<V>, (const void *)step_tma_batch_kernel<V>, V::NT, V::SMEM, \
+#define MMOD_VARIANT(V, desc, P) \
+    {desc, (const void *)step_tma_kernel<V>, (const void *)step_tma_batch_kernel<V>, P, V::NT, V::SMEM, \
      batch_smem<V>()}
 const Variant kVariants[] = {
-    MMOD_VARIANT(V22_1, "64x16 tile, 2x2 points/thread, z unroll 1"),
-    MMOD_VARIANT(V22_2, "64x16 tile, 2x2 points/thread, z unroll 2"),
-    MMOD_VARIANT(V22_4, "64x16 tile, 2x2 points/thread, z unroll 4"),
-    MMOD_VARIANT(V24_1, "64x16 tile, 2x4 points/thread, z unroll 1"),
-    MMOD_VARIANT(V24_2, "64x16 tile, 2x4 points/thread, z unroll 2"),
-    MMOD_VARIANT(V24_2s, "64x16 tile, 2x4 points/thread, z unroll 2, shallow rings"),
-    MMOD_VARIANT(V22_4s, "64x16 tile, 2x2 points/thread, z unroll 4, shallow rings"),
+    MMOD_VARIANT(V22_1, "64x16 tile, 2x2 points/thread, z unroll 1", nullptr),
+    MMOD_VARIANT(V22_2, "64x16 tile, 2x2 points/thread, z unroll 2", nullptr),
+    MMOD_VARIANT(V22_4, "64x16 tile, 2x2 points/thread, z unroll 4",
+                 (const void *)step_tma_persistent_kernel<V22_4>),
+    MMOD_VARIANT(V24_1, "64x16 tile, 2x4 points/thread, z unroll 1", nullptr),
+    MMOD_VARIANT(V24_2, "64x16 tile, 2x4 points/thread, z unroll 2", nullptr),
+    MMOD_VARIANT(V24_2s, "64x16 tile, 2x4 points/thread, z unroll 2, shallow rings",
+                 (const void *)step_tma_persistent_kernel<V24_2s>),
+    MMOD_VARIANT(V22_4s, "64x16 tile, 2x2 points/thread, z unroll 4, shallow rings", nullptr),
+    MMOD_VARIANT(V22_4s3, "64x16 tile, 2x2 points/thread, z unroll 4, shallow rings, 3 CTAs/SM", nullptr),
+    MMOD_VARIANT(V22_2s3, "64x16 tile, 2x2 points/thread, z unroll 2, shallow rings, 3 CTAs/SM", nullptr),
 };
 #undef MMOD_VARIANT
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
@@ -576,6 +720,9 @@ bool make_tma_plan(const mmod_config &cfg, int nxp, float *const u[2], const flo
         int occ = 0;
         if (cudaFuncSetAttribute(var.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, var.smem) != cudaSuccess ||
             cudaFuncSetAttribute(var.batch_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, var.batch_smem) != cudaSuccess ||
+            (var.persist_fn &&
+             cudaFuncSetAttribute(var.persist_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, var.smem) !=
+                 cudaSuccess) ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, var.fn, var.nt, var.smem) != cudaSuccess || occ < 1) {
             cudaGetLastError();
             return false;
@@ -632,9 +779,61 @@ cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap *cur_map, const
         case 4: MMOD_LAUNCH(V24_2); break;
         case 5: MMOD_LAUNCH(V24_2s); break;
         case 6: MMOD_LAUNCH(V22_4s); break;
+        case 7: MMOD_LAUNCH(V22_4s3); break;
+        case 8: MMOD_LAUNCH(V22_2s3); break;
         default: return cudaErrorInvalidValue;
     }
 #undef MMOD_LAUNCH
+    return cudaGetLastError();
+}
+
+Geom persistent_geom(const TmaPlan &plan, int nz) {
+    // z ranges at least as thick as the stencil radius: a unit's halo then
+    // reaches only the adjacent range
+    const int zlen = std::max(plan.zlen, kRadius);
+    return Geom{plan.tiles_x, plan.tiles_y, (nz + zlen - 1) / zlen, zlen};
+}
+
+int persistent_grid(const TmaPlan &plan, int nz, int max_ctas) {
+    if (plan.variant < 0 || plan.variant >= kNumVariants || nz < 1) return 0;
+    const Variant &var = kVariants[plan.variant];
+    if (!var.persist_fn) return 0;
+    const Geom g = persistent_geom(plan, nz);
+    int dev = 0, sms = 0, occ = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, var.persist_fn, var.nt, var.smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    long long grid = std::min<long long>((long long)sms * occ, (long long)g.tiles_x * g.tiles_y * g.zchunks);
+    if (max_ctas > 0) grid = std::min<long long>(grid, max_ctas);
+    return (int)std::max<long long>(grid, 0);
+}
+
+cudaError_t launch_step_tma_persistent(const StepArgs &a, const TmaMaps &maps, const TmaPlan &plan,
+                                       const PersistArgs &pa, int grid, cudaStream_t s) {
+    if (plan.variant < 0 || plan.variant >= kNumVariants || !kVariants[plan.variant].persist_fn || grid < 1)
+        return cudaErrorInvalidValue;
+    const Geom g = persistent_geom(plan, a.nz);
+    if (pa.units != g.tiles_x * g.tiles_y * g.zchunks) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(grid);
+    lc.blockDim = dim3(kVariants[plan.variant].nt);
+    lc.dynamicSmemBytes = kVariants[plan.variant].smem;
+    lc.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;   // all CTAs resident: units wait on one another
+    attr[0].val.cooperative = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    cudaError_t e;
+    switch (plan.variant) {
+        case 2: e = cudaLaunchKernelEx(&lc, step_tma_persistent_kernel<V22_4>, a, maps, g, pa); break;
+        case 5: e = cudaLaunchKernelEx(&lc, step_tma_persistent_kernel<V24_2s>, a, maps, g, pa); break;
+        default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -668,6 +867,8 @@ cudaError_t launch_step_tma_batch(int variant, const ShotDesc *shots, const int 
         case 4: MMOD_LAUNCH_B(V24_2); break;
         case 5: MMOD_LAUNCH_B(V24_2s); break;
         case 6: MMOD_LAUNCH_B(V22_4s); break;
+        case 7: MMOD_LAUNCH_B(V22_4s3); break;
+        case 8: MMOD_LAUNCH_B(V22_2s3); break;
         default: return cudaErrorInvalidValue;
     }
 #undef MMOD_LAUNCH_B

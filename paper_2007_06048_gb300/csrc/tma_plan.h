@@ -6,7 +6,7 @@
 
 namespace mmod {
 
-constexpr int kMaxTmaVariants = 8;
+constexpr int kMaxTmaVariants = 12;
 // Variant used unless a handle selects another: the fastest measured on the
 // 240^3 workload (64x16 tile, 2x2 points per thread, z unroll 4).
 constexpr int kTmaDefaultVariant = 2;
