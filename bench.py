@@ -386,6 +386,11 @@ def measure_batched(M, dev, stream, fwd_gpts, reps=3):
     trs = [torch.empty((p.nt, len(p.rec_ijk)), device=dev) for p in shots]
     work = sum(p.npoints * p.nt for p in shots)
     b = M.Batch(props)
+    b.set_mode(M.BATCH_FUSED)                 # the fused launch, for the record
+    fused_variant = b.autotune(10, stream)
+    b.forward(wav, trs, stream)
+    ms_fused = time_calls(lambda: b.forward(wav, trs, stream), reps, stream)
+    b.set_mode(M.BATCH_STREAMS)               # the default mode
     variant = b.autotune(10, stream)
     b.forward(wav, trs, stream)
     ms = time_calls(lambda: b.forward(wav, trs, stream), reps, stream)
@@ -401,9 +406,13 @@ def measure_batched(M, dev, stream, fwd_gpts, reps=3):
         pr.close()
     v = work / (ms * 1e-3) / 1e9
     return {"value": v, "unit": UNIT, "ms": ms, "loop_ms": loop_ms, "vs_forward": v / fwd_gpts,
-            "one_by_one": work / (ms_single * 1e-3) / 1e9, "shots": len(shots), "nt": shots[0].nt,
+            "hbm_frac": BYTES_PER_POINT * v / load_peaks()[0],
+            "one_by_one": work / (ms_single * 1e-3) / 1e9, "fused": work / (ms_fused * 1e-3) / 1e9,
+            "fused_variant": M.mmod_tma_variant_name(fused_variant),
+            "shots": len(shots), "nt": shots[0].nt,
             "points": int(sum(p.npoints for p in shots)), "variant": M.mmod_tma_variant_name(variant),
-            "what": "mmod_batch_forward: all shots advance one step per launch (CUDA graph of nt launches)"}
+            "what": "mmod_batch_forward, streams mode: the shots' graphs overlap on four streams; "
+                    "fused: one launch per step for all shots"}
 
 
 def measure_large(M, dev, stream, peak, reps=2):

@@ -195,6 +195,11 @@ mmod_status mmod_set_kernel(mmod_handle *h, int kernel);
  * handle (-1 = automatic).  All variants produce the same bits.  Errors:
  * ARG (out of range), UNSUPPORTED (no TMA plan). */
 int mmod_tma_variant_count(void);
+/* Resources of variant v on the current device, 14 ints: threads per CTA,
+ * dynamic shared bytes, then {registers per thread, local bytes per thread,
+ * static shared bytes, resident CTAs per SM} for its one-step, batch and
+ * persistent kernels (-1 where not compiled).  Errors: ARG (out of range). */
+mmod_status mmod_tma_variant_info(int v, int *out14);
 const char *mmod_tma_variant_name(int v);
 mmod_status mmod_set_tma_variant(mmod_handle *h, int v);
 
@@ -297,11 +302,17 @@ mmod_status mmod_forward_noalloc(const mmod_config *cfg, int device, const float
 
 /* ---- Batched shots ------------------------------------------------------
  * A batch advances several shots (one handle each: any grid sizes, the same
- * nt, the same device) together: one kernel launch per time step covers all
- * of them, and the nt launches are captured once into a CUDA graph.  The
- * batch refers to the handles (they keep their buffers, models and
- * geometry); destroy the batch before its handles.  Each handle's buffers
- * hold its shot's final state after mmod_batch_forward (mmod_get_state). */
+ * nt, the same device) together, in one of two modes (mmod_batch_set_mode):
+ *   MMOD_BATCH_STREAMS (default): each shot's own time loop (the handle's
+ *     graph of one-step kernels) on one of four internal streams forked
+ *     from and joined back to the caller's stream, so the shots' kernels
+ *     overlap;
+ *   MMOD_BATCH_FUSED: one kernel launch per time step covers all shots, the
+ *     nt launches captured once into a CUDA graph.
+ * Both give every shot the bits it gets alone.  The batch refers to the
+ * handles (they keep their buffers, models and geometry); destroy the batch
+ * before its handles.  Each handle's buffers hold its shot's final state
+ * after mmod_batch_forward (mmod_get_state). */
 typedef struct mmod_batch mmod_batch;
 
 /* Errors: ARG (null or mismatched handles), UNSUPPORTED (a grid without TMA
@@ -317,8 +328,13 @@ mmod_status mmod_batch_destroy(mmod_batch *b);
 mmod_status mmod_batch_forward(mmod_batch *b, const float *const *wavelets, float *const *traces,
                                mmod_stream stream);
 
-/* Select the TMA variant used by the batch (see mmod_tma_variant_count). */
+/* Select the TMA variant used by the batch (see mmod_tma_variant_count); in
+ * streams mode it is set on every handle of the batch. */
 mmod_status mmod_batch_set_variant(mmod_batch *b, int v);
+
+/* MMOD_BATCH_STREAMS or MMOD_BATCH_FUSED.  Errors: ARG. */
+enum { MMOD_BATCH_STREAMS = 0, MMOD_BATCH_FUSED = 1 };
+mmod_status mmod_batch_set_mode(mmod_batch *b, int mode);
 
 /* Device time (ms) of the last mmod_batch_forward's loop; waits for it. */
 float mmod_batch_last_loop_ms(mmod_batch *b);

@@ -32,6 +32,7 @@ OPT_PERSISTENT = 4
 OPT_PERSISTENT_CTAS = 5
 OPT_TEST_STALL = 6
 OPT_ZLEN = 7
+BATCH_STREAMS, BATCH_FUSED = 0, 1
 SCHEME_SEGMENTS, SCHEME_REVOLVE = 0, 1
 REV_ADVANCE, REV_SAVE, REV_RESTORE, REV_REVERSE = 0, 1, 2, 3
 
@@ -43,7 +44,8 @@ EXPORTED = ["mmod_create", "mmod_destroy", "mmod_set_model", "mmod_forward", "mm
             "mmod_forward_noalloc", "mmod_set_option", "mmod_adjoint", "mmod_gradient",
             "mmod_gradient_memory", "mmod_dot", "mmod_batch_create", "mmod_batch_destroy",
             "mmod_batch_forward", "mmod_batch_set_variant", "mmod_batch_last_loop_ms", "mmod_batch_last_error",
-            "mmod_autotune", "mmod_batch_autotune", "mmod_revolve_schedule", "mmod_persistent_grid"]
+            "mmod_autotune", "mmod_batch_autotune", "mmod_revolve_schedule", "mmod_persistent_grid",
+            "mmod_tma_variant_info", "mmod_batch_set_mode"]
 CKPT_FP32, CKPT_BF16, CKPT_FP16 = 0, 1, 2
 
 
@@ -114,6 +116,8 @@ def load():
         "mmod_revolve_schedule": ([I, I, P, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong),
                                    ctypes.POINTER(ctypes.c_longlong)], I),
         "mmod_persistent_grid": ([P], I),
+        "mmod_tma_variant_info": ([I, ctypes.POINTER(I)], I),
+        "mmod_batch_set_mode": ([P, I], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -273,6 +277,17 @@ def mmod_revolve_schedule(nsteps: int, snaps: int):
     return out[: count.value], int(adv.value)
 
 
+def mmod_tma_variant_info(v: int) -> dict:
+    """Threads, shared memory, registers, local bytes and residency of variant v's kernels."""
+    out = (ctypes.c_int * 14)()
+    st = load().mmod_tma_variant_info(int(v), out)
+    if st != 0:
+        raise MmodError(st, "mmod_tma_variant_info: variant out of range")
+    keys = ("registers", "local_bytes", "static_smem", "ctas_per_sm")
+    return {"threads": out[0], "dynamic_smem": out[1],
+            **{k: dict(zip(keys, out[2 + 4 * i: 6 + 4 * i])) for i, k in enumerate(("step", "batch", "persistent"))}}
+
+
 def mmod_dot(a, b, n=None, stream=None) -> float:
     """FP64 dot product of two FP32 device arrays (computed by the library)."""
     out = ctypes.c_double(0.0)
@@ -337,6 +352,10 @@ class Batch:
 
     def set_variant(self, v: int):
         self._err(load().mmod_batch_set_variant(self.handle, int(v)))
+
+    def set_mode(self, mode: int):
+        """BATCH_STREAMS (default) or BATCH_FUSED."""
+        self._err(load().mmod_batch_set_mode(self.handle, int(mode)))
 
     def autotune(self, steps=20, stream=None) -> int:
         v = ctypes.c_int(-1)

@@ -584,6 +584,11 @@ MMOD_API mmod_status mmod_set_option(mmod_handle *h, int option, int value) {
     }
 }
 
+MMOD_API mmod_status mmod_tma_variant_info(int v, int *out14) {
+    if (!out14) return MMOD_ERR_ARG;
+    return tma_variant_info(v, out14) ? MMOD_OK : MMOD_ERR_ARG;
+}
+
 MMOD_API int mmod_persistent_grid(const mmod_handle *h) {
     if (!h) return -1;
     DeviceGuard guard(h->device);

@@ -1,12 +1,17 @@
 // Batched shots and the variant autotuner.
 //
 // A batch groups handles (one per shot; grids of any size, the same number of
-// steps) so that one kernel launch advances every shot by one step: CTA b
-// serves shot cta_shot[b] as its block cta_local[b], reading the shot's
-// arguments and tensor maps from a descriptor table in device memory.  The
-// nt launches are captured once into a CUDA graph; the descriptor table is
-// uploaded per call, so new wavelet / trace buffers need no new capture.
-// CTAs are ordered longest first so the last wave is made of short ones.
+// steps) and runs them in one of two ways:
+//   streams (default): each shot's own time loop (its cached graph of
+//     one-step kernels) on one of kSubStreams internal streams, forked from
+//     and joined back to the caller's stream, so the shots' waves overlap and
+//     hide one another's tails;
+//   fused: one kernel launch per step advances every shot: CTA b serves shot
+//     cta_shot[b] as its block cta_local[b], reading the shot's arguments and
+//     tensor maps from a descriptor table in device memory.  The nt launches
+//     are captured once into a CUDA graph; the descriptor table is uploaded
+//     per call, so new wavelet / trace buffers need no new capture.  CTAs are
+//     ordered longest first so the last wave is made of short ones.
 //
 // The autotuner times each compiled TMA variant (points per thread, z
 // unroll, ring depths) for a few steps on the real problem and keeps the
@@ -22,11 +27,17 @@
 
 using namespace mmod;
 
+constexpr int kSubStreams = 4;
+
 struct mmod_batch {
     std::vector<mmod_handle *> shots;
     int device = 0, nt = 0;
+    int mode = MMOD_BATCH_STREAMS;
     int variant = kTmaDefaultVariant;
+    bool variant_set = false;
     int pdl = 1;
+    cudaStream_t sub[kSubStreams] = {};
+    cudaEvent_t fork = nullptr, join[kSubStreams] = {};
     std::vector<ShotDesc> desc;       // host copy, uploaded per call
     ShotDesc *d_desc = nullptr;
     int *d_cta_shot = nullptr, *d_cta_local = nullptr;
@@ -70,6 +81,11 @@ mmod_status bfail_cuda(mmod_batch *b, cudaError_t e, const char *what) {
     } while (0)
 
 void free_batch(mmod_batch *b) {
+    for (int k = 0; k < kSubStreams; ++k) {
+        if (b->sub[k]) cudaStreamDestroy(b->sub[k]);
+        if (b->join[k]) cudaEventDestroy(b->join[k]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
     if (b->graph.exec) cudaGraphExecDestroy(b->graph.exec);
     if (b->d_desc) cudaFree(b->d_desc);
     if (b->d_cta_shot) cudaFree(b->d_cta_shot);
@@ -112,7 +128,48 @@ float time_steps(mmod_batch *b, int steps, cudaStream_t s, mmod_status *st) {
     return ms;
 }
 
+// Fork the internal streams from s (after everything already on s).
+mmod_status fork_streams(mmod_batch *b, cudaStream_t s) {
+    BCK(b, cudaEventRecord(b->fork, s));
+    for (int k = 0; k < kSubStreams; ++k) BCK(b, cudaStreamWaitEvent(b->sub[k], b->fork, 0));
+    return MMOD_OK;
+}
+
+// Join the internal streams back into s.
+mmod_status join_streams(mmod_batch *b, cudaStream_t s) {
+    for (int k = 0; k < kSubStreams; ++k) {
+        BCK(b, cudaEventRecord(b->join[k], b->sub[k]));
+        BCK(b, cudaStreamWaitEvent(s, b->join[k], 0));
+    }
+    return MMOD_OK;
+}
+
 }  // namespace
+
+namespace mmod {
+
+// `steps` steps of h's time loop from zero state without sources or
+// receivers, direct launches on s (autotuning).
+mmod_status enqueue_tune_steps(mmod_handle *h, int steps, cudaStream_t s) {
+    MMOD_CK(h, cudaMemsetAsync(h->u[0], 0, sizeof(float) * (size_t)h->vol, s));
+    MMOD_CK(h, cudaMemsetAsync(h->u[1], 0, sizeof(float) * (size_t)h->vol, s));
+    StepArgs a = base_args(h, h->fwd, nullptr);
+    a.inj.npts = 0;   // no sources while tuning
+    a.nrec = 0;
+    long long count = 0;
+    for (int n = 0; n < std::min(steps, h->cfg.nt); ++n) {
+        a.n = n;
+        a.ucur = h->u[(n + 1) & 1];
+        a.uprev = h->u[n & 1];
+        a.uout = h->u[n & 1];
+        MMOD_CK(h, enqueue_step(h, a, &h->cur_map[(n + 1) & 1], &h->prev_map[n & 1], true, nullptr, s, &count));
+    }
+    h->state_pending = false;
+    h->ran = false;
+    return MMOD_OK;
+}
+
+}  // namespace mmod
 
 MMOD_API mmod_status mmod_batch_create(mmod_handle *const *shots, int nshots, mmod_batch **out) {
     set_thread_error("");
@@ -194,6 +251,11 @@ MMOD_API mmod_status mmod_batch_create(mmod_handle *const *shots, int nshots, mm
     CKB(cudaMemcpy(b->d_cta_local, cl.data(), sizeof(int) * cl.size(), cudaMemcpyHostToDevice));
     CKB(cudaEventCreate(&b->ev_t0));
     CKB(cudaEventCreate(&b->ev_t1));
+    CKB(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+    for (int k = 0; k < kSubStreams; ++k) {
+        CKB(cudaStreamCreateWithFlags(&b->sub[k], cudaStreamNonBlocking));
+        CKB(cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming));
+    }
 #undef CKB
     *out = b;
     return MMOD_OK;
@@ -217,6 +279,15 @@ MMOD_API mmod_status mmod_batch_set_variant(mmod_batch *b, int v) {
     int block, smem;
     if (v < 0 || !tma_variant_shape(v, &block, &smem)) return bfail(b, MMOD_ERR_ARG, "unknown TMA variant");
     b->variant = v;
+    b->variant_set = true;
+    for (mmod_handle *h : b->shots) h->variant = v;   // streams mode runs each handle's own plan
+    return MMOD_OK;
+}
+
+MMOD_API mmod_status mmod_batch_set_mode(mmod_batch *b, int mode) {
+    if (!b) return MMOD_ERR_ARG;
+    if (mode != MMOD_BATCH_STREAMS && mode != MMOD_BATCH_FUSED) return bfail(b, MMOD_ERR_ARG, "unknown batch mode");
+    b->mode = mode;
     return MMOD_OK;
 }
 
@@ -226,6 +297,31 @@ MMOD_API mmod_status mmod_batch_forward(mmod_batch *b, const float *const *wavel
     DeviceGuard guard(b->device);
     cudaStream_t s = (cudaStream_t)stream;
     const int ns = (int)b->shots.size();
+    if (b->mode == MMOD_BATCH_STREAMS) {
+        for (int i = 0; i < ns; ++i) {
+            mmod_handle *h = b->shots[i];
+            const float *w = wavelets ? wavelets[i] : nullptr;
+            float *t = traces ? traces[i] : nullptr;
+            if (h->cfg.nsrc > 0 && b->nt > 0 && (!w || !is_device_ptr(w)))
+                return bfail(b, MMOD_ERR_ARG, "shot " + std::to_string(i) + ": wavelet must be a device pointer");
+            if (h->cfg.nrec > 0 && b->nt > 0 && (!t || !is_device_ptr(t)))
+                return bfail(b, MMOD_ERR_ARG, "shot " + std::to_string(i) + ": traces must be a device pointer");
+        }
+        BCK(b, cudaEventRecord(b->ev_t0, s));
+        if (mmod_status st = fork_streams(b, s)) return st;
+        for (int i = 0; i < ns; ++i) {
+            mmod_handle *h = b->shots[i];
+            if (mmod_status st = mmod_forward(h, wavelets ? wavelets[i] : nullptr, traces ? traces[i] : nullptr,
+                                              nullptr, (mmod_stream)b->sub[i % kSubStreams])) {
+                join_streams(b, s);
+                return bfail(b, st, "shot " + std::to_string(i) + ": " + h->err);
+            }
+        }
+        if (mmod_status st = join_streams(b, s)) return st;
+        BCK(b, cudaEventRecord(b->ev_t1, s));
+        b->ran = b->nt > 0;
+        return MMOD_OK;
+    }
     for (int i = 0; i < ns; ++i) {
         mmod_handle *h = b->shots[i];
         if (mmod_status st = check_latched(h)) return bfail(b, st, "shot " + std::to_string(i) + ": " + h->err);
@@ -302,6 +398,42 @@ MMOD_API mmod_status mmod_batch_autotune(mmod_batch *b, int steps, mmod_stream s
     DeviceGuard guard(b->device);
     cudaStream_t s = (cudaStream_t)stream;
     const int ns = (int)b->shots.size();
+    if (b->mode == MMOD_BATCH_STREAMS) {
+        for (int i = 0; i < ns; ++i)
+            if (!b->shots[i]->model_set) return bfail(b, MMOD_ERR_STATE, "shot " + std::to_string(i) + " has no model");
+        cudaEvent_t e0, e1;
+        BCK(b, cudaEventCreate(&e0));
+        BCK(b, cudaEventCreate(&e1));
+        int best = kTmaDefaultVariant;
+        float best_ms = 1e30f;
+        mmod_status st = MMOD_OK;
+        for (int v = 0; v < tma_variant_count() && st == MMOD_OK; ++v) {
+            for (mmod_handle *h : b->shots) h->variant = v;
+            float ms = -1.0f;
+            for (int rep = 0; rep < 2 && st == MMOD_OK; ++rep) {   // the first repetition warms up
+                if (cudaEventRecord(e0, s) != cudaSuccess) st = MMOD_ERR_CUDA;
+                if (st == MMOD_OK) st = fork_streams(b, s);
+                for (int i = 0; i < ns && st == MMOD_OK; ++i)
+                    st = enqueue_tune_steps(b->shots[i], steps, b->sub[i % kSubStreams]);
+                if (st == MMOD_OK) st = join_streams(b, s);
+                if (st == MMOD_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                                      cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                    st = MMOD_ERR_CUDA;
+            }
+            if (st == MMOD_OK && ms > 0 && ms < best_ms) {
+                best_ms = ms;
+                best = v;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        for (mmod_handle *h : b->shots) h->variant = best;
+        if (st != MMOD_OK) return bfail(b, st, "autotuning the batch failed");
+        b->variant = best;
+        b->variant_set = true;
+        if (variant_out) *variant_out = best;
+        return MMOD_OK;
+    }
     for (int i = 0; i < ns; ++i) {
         if (!b->shots[i]->model_set) return bfail(b, MMOD_ERR_STATE, "shot " + std::to_string(i) + " has no model");
         b->desc[i].args.wavelet = nullptr;   // no sources while tuning
@@ -343,28 +475,15 @@ MMOD_API mmod_status mmod_autotune(mmod_handle *h, int steps, mmod_stream stream
     cudaStream_t s = (cudaStream_t)stream;
     int best = kTmaDefaultVariant;
     float best_ms = 1e30f;
-    const int nsteps = std::min(steps, std::max(h->cfg.nt, 1));
     cudaEvent_t e0, e1;
     MMOD_CK(h, cudaEventCreate(&e0));
     MMOD_CK(h, cudaEventCreate(&e1));
-    StepArgs a = base_args(h, h->fwd, nullptr);
-    a.inj.npts = 0;   // no sources while tuning
-    a.nrec = 0;
     for (int v = 0; v < tma_variant_count(); ++v) {
         h->variant = v;
         float ms = 0.0f;
         for (int rep = 0; rep < 2; ++rep) {   // the first repetition warms up
-            MMOD_CK(h, cudaMemsetAsync(h->u[0], 0, sizeof(float) * (size_t)h->vol, s));
-            MMOD_CK(h, cudaMemsetAsync(h->u[1], 0, sizeof(float) * (size_t)h->vol, s));
             MMOD_CK(h, cudaEventRecord(e0, s));
-            long long count = 0;
-            for (int n = 0; n < nsteps; ++n) {
-                a.n = n;
-                a.ucur = h->u[(n + 1) & 1];
-                a.uprev = h->u[n & 1];
-                a.uout = h->u[n & 1];
-                MMOD_CK(h, enqueue_step(h, a, &h->cur_map[(n + 1) & 1], &h->prev_map[n & 1], true, nullptr, s, &count));
-            }
+            if (mmod_status st = enqueue_tune_steps(h, steps, s)) return st;
             MMOD_CK(h, cudaEventRecord(e1, s));
             MMOD_CK(h, cudaEventSynchronize(e1));
             MMOD_CK(h, cudaEventElapsedTime(&ms, e0, e1));
@@ -377,7 +496,6 @@ MMOD_API mmod_status mmod_autotune(mmod_handle *h, int steps, mmod_stream stream
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     h->variant = best;
-    h->ran = false;
     if (variant_out) *variant_out = best;
     return check_latched(h);
 }

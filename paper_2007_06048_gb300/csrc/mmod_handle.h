@@ -132,6 +132,7 @@ mmod_status check_latched(mmod_handle *h);
 bool is_device_ptr(const void *p);
 bool use_tma(const mmod_handle *h);
 int persistent_grid_of(const mmod_handle *h);
+mmod_status enqueue_tune_steps(mmod_handle *h, int steps, cudaStream_t s);   // mmod_batch.cu
 const TmaPlan &active_plan(const mmod_handle *h);
 StepArgs base_args(mmod_handle *h, const Geometry &geo, const float *wavelet);
 // Enqueues one step (plain path: step, injection, optional gather of

@@ -143,6 +143,10 @@ cudaError_t launch_step_tma_persistent(const StepArgs &a, const TmaMaps &maps, c
 cudaError_t launch_step_tma_batch(int variant, const ShotDesc *shots, const int *cta_shot, const int *cta_local,
                                   int nctas, int n, bool pdl, cudaStream_t s);
 bool tma_variant_shape(int v, int *block, int *smem);
+// 14 ints: threads, dynamic shared bytes, then {registers, local bytes,
+// static shared bytes, resident CTAs per SM} of the step, batch and
+// persistent kernels (-1 where a kernel is not compiled).
+bool tma_variant_info(int v, int *out);
 
 cudaError_t launch_model_scan(const float *vel, long long n, unsigned int *vmax_bits,
                               unsigned long long *bad, cudaStream_t s);

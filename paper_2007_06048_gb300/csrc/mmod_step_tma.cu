@@ -45,6 +45,8 @@ constexpr unsigned long long kWaitNs = 100000000ull;   // a wait gives up after 
 template <int TY_, int RY_, int U_, int NSU_ = 8, int NSC_ = 4, int MINB_ = 1>
 struct Shape {
     static constexpr int MINB = MINB_;              // resident CTAs per SM the registers are capped for
+    // the batch and persistent kernels always keep two CTAs per SM resident
+    static constexpr int MINB2 = MINB_ > 2 ? MINB_ : 2;
     static constexpr int TY = TY_;
     static constexpr int RY = RY_;
     static constexpr int U = U_;                    // z steps per unrolled block
@@ -551,7 +553,7 @@ __host__ __device__ constexpr int batch_smem() {
 }
 
 template <class S>
-__global__ void __launch_bounds__(S::NT, S::MINB)
+__global__ void __launch_bounds__(S::NT, S::MINB2)
     step_tma_batch_kernel(const ShotDesc *__restrict__ shots, const int *__restrict__ cta_shot,
                           const int *__restrict__ cta_local, int n) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -581,7 +583,7 @@ __global__ void __launch_bounds__(S::NT, S::MINB)
 // step and the buffer roles go in a StepVar; each unit signals its counter
 // once its u^{n+1} (sources and receivers included) is complete.
 template <class S>
-__global__ void __launch_bounds__(S::NT, S::MINB)
+__global__ void __launch_bounds__(S::NT, S::MINB2)
     step_tma_persistent_kernel(const StepArgs a, const __grid_constant__ TmaMaps maps, const Geom g,
                                const PersistArgs pa) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -835,6 +837,33 @@ cudaError_t launch_step_tma_persistent(const StepArgs &a, const TmaMaps &maps, c
     }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
+}
+
+bool tma_variant_info(int v, int *out) {
+    if (v < 0 || v >= kNumVariants) return false;
+    const Variant &var = kVariants[v];
+    const void *fns[3] = {var.fn, var.batch_fn, var.persist_fn};
+    const int dyn[3] = {var.smem, var.batch_smem, var.smem};
+    out[0] = var.nt;
+    out[1] = var.smem;
+    for (int k = 0; k < 3; ++k) {
+        int *o = out + 2 + 4 * k;
+        o[0] = o[1] = o[2] = o[3] = -1;
+        if (!fns[k]) continue;
+        cudaFuncAttributes fa;
+        int occ = 0;
+        if (cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, dyn[k]) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, fns[k]) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fns[k], var.nt, dyn[k]) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        o[0] = fa.numRegs;
+        o[1] = (int)fa.localSizeBytes;
+        o[2] = (int)fa.sharedSizeBytes;
+        o[3] = occ;
+    }
+    return true;
 }
 
 bool tma_variant_shape(int v, int *block, int *smem) {

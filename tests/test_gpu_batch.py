@@ -1,9 +1,9 @@
 """Batched shots and the autotuner on the GPU.
 
-A batch advances shots of uneven grid sizes, time steps and damping widths in
-one launch per step; every shot must come out bit for bit as when it runs
-alone through mmod_forward (same per-point arithmetic, only the CTA
-decomposition differs).  The autotuner must pick a valid variant and leave
+A batch advances shots of uneven grid sizes and damping widths together, on
+overlapping streams or in one fused launch per step; every shot must come
+out bit for bit as when it runs alone through mmod_forward (same per-point
+arithmetic, only the CTA decomposition differs).  The autotuner must pick a valid variant and leave
 results unchanged.
 """
 import numpy as np
@@ -22,12 +22,13 @@ def _shots(nt=60):
     return [W.tiny_problem(shape=s, nt=nt, nbl=L, nsrc=2, nrec=15, seed=i + 40) for i, (s, L) in enumerate(SHAPES)]
 
 
-def _run_batch(shots, autotune=False):
+def _run_batch(shots, autotune=False, mode=M.BATCH_STREAMS):
     torch = torch_cuda()
     props = [M.Propagator.from_problem(p) for p in shots]
     for pr, p in zip(props, shots):
         pr.set_model(torch.from_numpy(p.vel).cuda())
     b = M.Batch(props)
+    b.set_mode(mode)
     v = b.autotune(steps=5) if autotune else None
     wav = [torch.from_numpy(p.wavelet).cuda() for p in shots]
     tr = [torch.zeros((p.nt, len(p.rec_ijk)), device="cuda") for p in shots]
@@ -44,18 +45,20 @@ def _run_batch(shots, autotune=False):
     return [t.cpu().numpy() for t in tr], finals, v
 
 
-def test_batch_matches_single_shots_bitwise():
+@pytest.mark.parametrize("mode", [M.BATCH_STREAMS, M.BATCH_FUSED])
+def test_batch_matches_single_shots_bitwise(mode):
     shots = _shots()
-    tr_b, u_b, _ = _run_batch(shots)
+    tr_b, u_b, _ = _run_batch(shots, mode=mode)
     for i, p in enumerate(shots):
         tr_s, u_s, _ = run_gpu(p)
         assert np.array_equal(tr_b[i], tr_s), i
         assert np.array_equal(u_b[i], u_s), i
 
 
-def test_batch_autotune_keeps_results():
+@pytest.mark.parametrize("mode", [M.BATCH_STREAMS, M.BATCH_FUSED])
+def test_batch_autotune_keeps_results(mode):
     shots = _shots(nt=30)
-    tr_b, u_b, v = _run_batch(shots, autotune=True)
+    tr_b, u_b, v = _run_batch(shots, autotune=True, mode=mode)
     assert 0 <= v < M.mmod_tma_variant_count()
     for i, p in enumerate(shots):
         tr_s, u_s, _ = run_gpu(p, kernel=M.KERNEL_SIMPLE)
@@ -87,3 +90,12 @@ def test_batch_rejects_mismatched_steps():
     with pytest.raises(M.MmodError) as ei:
         M.Batch([a, b])
     assert ei.value.status == -1
+
+
+def test_batch_mode_rejects_unknown():
+    torch_cuda()
+    a = M.Propagator.from_problem(W.tiny_problem(shape=(20, 20, 40), nt=10))
+    b = M.Batch([a])
+    with pytest.raises(M.MmodError):
+        b.set_mode(7)
+    b.close()
