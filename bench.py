@@ -349,7 +349,8 @@ def measure_adjoint(M, prop, p, dev, stream, fwd_gpts, reps=3):
 
 
 def measure_gradient(M, dev, stream, fwd_gpts, reps=2):
-    """mmod_gradient on the 200^3 smooth-gradient workload, 20 checkpoints."""
+    """mmod_gradient on the 200^3 smooth-gradient workload: 20 FP32 or BF16
+    checkpoints, and FP32 with every state kept (no replay)."""
     import torch
     import workloads as W
     p = W.smooth_gradient_200(1000)
@@ -359,15 +360,16 @@ def measure_gradient(M, dev, stream, fwd_gpts, reps=2):
     rng = np.random.default_rng(8)
     r = torch.from_numpy(rng.standard_normal((p.nt, len(p.rec_ijk))).astype(np.float32)).to(dev)
     g = torch.empty(p.vel.shape, device=dev)
-    out = {"workload": p.name, "checkpoints": 20, "unit": UNIT,
+    out = {"workload": p.name, "unit": UNIT,
            "what": "mmod_gradient: forward sweep with checkpoints, segment replay, adjoint, imaging; "
                    "value counts nt forward-equivalent steps per call"}
-    for name, dtype in (("fp32", M.CKPT_FP32), ("bf16", M.CKPT_BF16)):
-        prop.gradient(wav, r, g, 20, dtype, stream)
-        ms = time_calls(lambda: prop.gradient(wav, r, g, 20, dtype, stream), reps, stream)
+    for name, dtype, ck in (("fp32", M.CKPT_FP32, 20), ("bf16", M.CKPT_BF16, 20),
+                            ("fp32_every_state", M.CKPT_FP32, p.nt)):
+        prop.gradient(wav, r, g, ck, dtype, stream)
+        ms = time_calls(lambda: prop.gradient(wav, r, g, ck, dtype, stream), reps, stream)
         v = p.npoints * p.nt / (ms * 1e-3) / 1e9
-        out[name] = {"value": v, "ms": ms, "vs_forward": v / fwd_gpts,
-                     "memory_gb": prop.gradient_memory(20, dtype) / 1e9}
+        out[name] = {"value": v, "ms": ms, "vs_forward": v / fwd_gpts, "checkpoints": ck,
+                     "memory_gb": prop.gradient_memory(ck, dtype) / 1e9}
     prop.close()
     return out
 

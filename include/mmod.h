@@ -134,7 +134,9 @@ enum { MMOD_CKPT_FP32 = 0, MMOD_CKPT_BF16 = 1, MMOD_CKPT_FP16 = 2 };
  * (mmod_set_option MMOD_OPT_CKPT_SCHEME):
  *   MMOD_SCHEME_SEGMENTS (default): the run is cut into ckpt_count segments;
  *     each is replayed once into ceil(nt / ckpt_count) + 2 FP32 volumes, so
- *     the cost is two forward runs and one adjoint run;
+ *     the cost is two forward runs and one adjoint run; with FP32 storage and
+ *     ckpt_count >= nt every state is kept instead (nt + 2 volumes, one
+ *     forward run and one adjoint run);
  *   MMOD_SCHEME_REVOLVE: binomial checkpointing (mmod_revolve_schedule) with
  *     ckpt_count slots and three FP32 work volumes; the forward steps
  *     replayed are the fewest any schedule with that many slots needs

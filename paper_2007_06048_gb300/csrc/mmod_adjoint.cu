@@ -23,7 +23,9 @@
 //     forward sweeps and one adjoint;
 //   revolve: the binomial schedule of mmod_revolve.cu over S slots, with the
 //     working state in the handle's two buffers and one more volume for
-//     u^{n+1}; the fewest replayed steps for S slots.
+//     u^{n+1}; the fewest replayed steps for S slots;
+//   segments with S >= nt and FP32 storage keeps every state (nt + 2
+//     volumes, written out of place by the first sweep): no replay.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -140,8 +142,9 @@ mmod_status ensure_grad_work(mmod_handle *h, int nslot, int nwork, int dtype) {
     }
     MMOD_CK(h, cudaMalloc(&gw.gradc, vb));
     gw.ckpt_bytes = (size_t)nslot * 2 * (size_t)h->vol * ckpt_elem_bytes(dtype);
-    MMOD_CK(h, cudaMalloc(&gw.ckpt, gw.ckpt_bytes));
-    if (dtype != MMOD_CKPT_FP32) MMOD_CK(h, cudaMalloc(&gw.ckpt_scale, sizeof(float) * (size_t)nslot * 2 * h->cfg.nz));
+    if (nslot > 0) MMOD_CK(h, cudaMalloc(&gw.ckpt, gw.ckpt_bytes));
+    if (nslot > 0 && dtype != MMOD_CKPT_FP32)
+        MMOD_CK(h, cudaMalloc(&gw.ckpt_scale, sizeof(float) * (size_t)nslot * 2 * h->cfg.nz));
     gw.nslot = nslot;
     gw.nwork = nwork;
     gw.dtype = dtype;
@@ -149,8 +152,16 @@ mmod_status ensure_grad_work(mmod_handle *h, int nslot, int nwork, int dtype) {
 }
 
 // Checkpoint layout of a gradient call: slots and FP32 work volumes.
-void grad_layout(const mmod_handle *h, int ckpt_count, int *nslot, int *nwork, int *seglen) {
+// seglen = 0 with nslot = 0: every forward state is kept (FP32 checkpoints,
+// ckpt_count >= nt), so nothing is replayed.
+void grad_layout(const mmod_handle *h, int ckpt_count, int dtype, int *nslot, int *nwork, int *seglen) {
     const int nt = h->cfg.nt;
+    if (h->ckpt_scheme == MMOD_SCHEME_SEGMENTS && dtype == MMOD_CKPT_FP32 && ckpt_count >= nt && nt > 0) {
+        *seglen = 0;
+        *nslot = 0;
+        *nwork = nt + 2;
+        return;
+    }
     if (h->ckpt_scheme == MMOD_SCHEME_REVOLVE) {
         *seglen = 0;
         *nslot = std::max(1, std::min(ckpt_count, nt - 1));
@@ -262,7 +273,7 @@ MMOD_API mmod_status mmod_gradient(mmod_handle *h, const float *wavelet, const f
     cudaStream_t s = (cudaStream_t)stream;
     const int nt = c.nt;
     int nslot = 0, nwork = 0, seglen = 0;
-    grad_layout(h, ckpt_count, &nslot, &nwork, &seglen);
+    grad_layout(h, ckpt_count, ckpt_dtype, &nslot, &nwork, &seglen);
     if (mmod_status st = ensure_grad_work(h, nslot, nwork, ckpt_dtype)) return st;
     auto &gw = h->gw;
     const bool tma = use_tma(h);
@@ -308,7 +319,23 @@ MMOD_API mmod_status mmod_gradient(mmod_handle *h, const float *wavelet, const f
                               gw.gradc, s);
     };
 
-    if (h->ckpt_scheme == MMOD_SCHEME_REVOLVE) {
+    if (seglen == 0 && nslot == 0) {
+        // every state kept: seg[m] = u^{m-1}, the sweep writes out of place
+        MMOD_CK(h, cudaMemsetAsync(gw.seg[0], 0, vb, s));
+        MMOD_CK(h, cudaMemsetAsync(gw.seg[1], 0, vb, s));
+        for (int n = 0; n < nt; ++n) {
+            fa.n = n;
+            fa.ucur = gw.seg[n + 1];
+            fa.uprev = gw.seg[n];
+            fa.uout = gw.seg[n + 2];
+            MMOD_CK(h, enqueue_step(h, fa, tma ? &gw.seg_cur[n + 1] : nullptr, tma ? &gw.seg_prev[n] : nullptr, tma,
+                                    nullptr, s, &launches));
+        }
+        MMOD_CK(h, cudaMemsetAsync(gw.psi[0], 0, vb, s));
+        MMOD_CK(h, cudaMemsetAsync(gw.psi[1], 0, vb, s));
+        MMOD_CK(h, cudaMemsetAsync(gw.gradc, 0, vb, s));
+        for (int n = nt - 1; n >= 0; --n) MMOD_CK(h, adj_step_and_image(n, gw.seg[n + 2], gw.seg[n + 1], gw.seg[n]));
+    } else if (h->ckpt_scheme == MMOD_SCHEME_REVOLVE) {
         std::vector<RevAction> sched;
         revolve_schedule(nt, nslot, &sched);
         MMOD_CK(h, cudaMemsetAsync(gw.psi[0], 0, vb, s));
@@ -404,7 +431,7 @@ MMOD_API long long mmod_gradient_memory(const mmod_handle *h, int ckpt_count, in
     if (!h || ckpt_count < 1) return -1;
     if (ckpt_dtype != MMOD_CKPT_FP32 && ckpt_dtype != MMOD_CKPT_BF16 && ckpt_dtype != MMOD_CKPT_FP16) return -1;
     int nslot = 0, nwork = 0, seglen = 0;
-    grad_layout(h, ckpt_count, &nslot, &nwork, &seglen);
+    grad_layout(h, ckpt_count, ckpt_dtype, &nslot, &nwork, &seglen);
     const long long vb = 4LL * h->vol;
     const long long eb = ckpt_dtype == MMOD_CKPT_FP32 ? 4 : 2;
     return (long long)(nwork + 3) * vb + (long long)nslot * 2 * h->vol * eb +

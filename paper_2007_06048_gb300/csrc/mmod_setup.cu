@@ -191,26 +191,46 @@ __global__ void unreverse_transpose_kernel(const float *__restrict__ g, int nt, 
 //   grad_c += psi^{n+1} (D u^{n+1} - 2 u^n + E u^{n-1}) / c^2,
 // psi = c mu the adjoint wavefield, D = 1 + e, E = 1 - e.  Padding columns
 // are left untouched.
-__global__ void imaging_kernel(const float *__restrict__ psi, const float *__restrict__ un,
-                               const float *__restrict__ uc, const float *__restrict__ up,
-                               const float *__restrict__ c, const float *__restrict__ ex,
+__device__ __forceinline__ float imaging_term(float psi, float un, float uc, float up, float cc, float e,
+                                              float g) {
+    const float d2 = __fmaf_rn(__fadd_rn(1.0f, e), un, __fmaf_rn(-2.0f, uc, __fmul_rn(__fsub_rn(1.0f, e), up)));
+    return __fmaf_rn(psi, __fdiv_rn(d2, __fmul_rn(cc, cc)), g);
+}
+
+// Four consecutive x of one row per thread (16-byte loads; rows are padded to
+// 32 floats, so a group never straddles rows); columns past nx are loaded
+// (in bounds of the padded row) but not stored.
+__global__ void imaging_kernel(const float4 *__restrict__ psi, const float4 *__restrict__ un,
+                               const float4 *__restrict__ uc, const float4 *__restrict__ up,
+                               const float4 *__restrict__ c, const float *__restrict__ ex,
                                const float *__restrict__ ey, const float *__restrict__ ez, int nx, int ny, int nz,
-                               int nxp, float *__restrict__ grad) {
-    // one warp per grid row (j, k), lanes along x
-    const int lane = threadIdx.x & 31;
-    const int warps = (int)(blockDim.x >> 5);
-    const int rows = ny * nz;
-    for (int row = blockIdx.x * warps + (int)(threadIdx.x >> 5); row < rows; row += gridDim.x * warps) {
+                               int nxp, float4 *__restrict__ grad) {
+    const int per_row = nxp >> 2;
+    const long long total = (long long)per_row * ny * nz;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int row = total <= 0xffffffffLL ? (int)((unsigned)q / (unsigned)per_row) : (int)(q / per_row);
+        const int i0 = (int)(q - (long long)row * per_row) * 4;
+        if (i0 >= nx) continue;
         const int j = row % ny, k = row / ny;
-        const float eyj = ey[j], ezk = ez[k];
-        const long long base = (long long)row * nxp;
-        for (int i = lane; i < nx; i += 32) {
-            const long long q = base + i;
-            const float e = __fadd_rn(__fadd_rn(ex[i], eyj), ezk);
-            const float d2 = __fmaf_rn(__fadd_rn(1.0f, e), un[q],
-                                       __fmaf_rn(-2.0f, uc[q], __fmul_rn(__fsub_rn(1.0f, e), up[q])));
-            const float cc = c[q];
-            grad[q] = __fmaf_rn(psi[q], __fdiv_rn(d2, __fmul_rn(cc, cc)), grad[q]);
+        const float eyj = __ldg(ey + j), ezk = __ldg(ez + k);
+        const float4 ps = psi[q], a = un[q], b = uc[q], d = up[q], cc = c[q];
+        float4 g = grad[q];
+        float e[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) e[t] = __fadd_rn(__fadd_rn(__ldg(ex + min(i0 + t, nx - 1)), eyj), ezk);
+        float4 r;
+        r.x = imaging_term(ps.x, a.x, b.x, d.x, cc.x, e[0], g.x);
+        r.y = imaging_term(ps.y, a.y, b.y, d.y, cc.y, e[1], g.y);
+        r.z = imaging_term(ps.z, a.z, b.z, d.z, cc.z, e[2], g.z);
+        r.w = imaging_term(ps.w, a.w, b.w, d.w, cc.w, e[3], g.w);
+        if (i0 + 3 < nx) {
+            grad[q] = r;
+        } else {   // the row's last group: keep the padding untouched
+            float *gp = reinterpret_cast<float *>(grad + q);
+            gp[0] = r.x;
+            if (i0 + 1 < nx) gp[1] = r.y;
+            if (i0 + 2 < nx) gp[2] = r.z;
         }
     }
 }
@@ -267,9 +287,11 @@ cudaError_t launch_unreverse_transpose(const float *g, int nt, int ncol, double 
 cudaError_t launch_imaging(const float *psi, const float *u_next, const float *u_cur, const float *u_prev,
                            const float *c, const float *ex, const float *ey, const float *ez, int nx, int ny,
                            int nz, int nxp, float *grad_c, cudaStream_t s) {
-    const int rows = ny * nz;
-    imaging_kernel<<<(int)std::min<long long>((rows + 7) / 8, 152LL * 16), 256, 0, s>>>(
-        psi, u_next, u_cur, u_prev, c, ex, ey, ez, nx, ny, nz, nxp, grad_c);
+    const long long groups = (long long)(nxp / 4) * ny * nz;
+    imaging_kernel<<<(int)std::min<long long>((groups + 255) / 256, 152LL * 8), 256, 0, s>>>(
+        reinterpret_cast<const float4 *>(psi), reinterpret_cast<const float4 *>(u_next),
+        reinterpret_cast<const float4 *>(u_cur), reinterpret_cast<const float4 *>(u_prev),
+        reinterpret_cast<const float4 *>(c), ex, ey, ez, nx, ny, nz, nxp, reinterpret_cast<float4 *>(grad_c));
     return cudaGetLastError();
 }
 
