@@ -64,12 +64,12 @@ class Oracle:
         I, D = ctypes.c_int, ctypes.c_double
         lib.orc_fd_coeffs.argtypes = [I, P]
         lib.orc_damping_profile.argtypes = [I, I, D, D, D, P]
-        lib.orc_laplacian.argtypes = [I, I, I, D, D, D, I, P, P]
+        lib.orc_laplacian.argtypes = [I, I, I, D, D, D, I, P, P, I]
         lib.orc_forward.argtypes = [I, I, I, D, D, D, D, I, I, I, D, P,
-                                    I, P, P, I, P, P, P, P, P, P, I]
+                                    I, P, P, I, P, P, P, P, P, P, I, I]
         lib.orc_max_threads.argtypes = []
-        lib.orc_adjoint.argtypes = [I, I, I, D, D, D, D, I, I, I, D, P, I, P, I, P, P, P, I]
-        lib.orc_gradient.argtypes = [I, I, I, D, D, D, D, I, I, I, D, P, I, P, P, I, P, P, P, I]
+        lib.orc_adjoint.argtypes = [I, I, I, D, D, D, D, I, I, I, D, P, I, P, I, P, P, P, I, I]
+        lib.orc_gradient.argtypes = [I, I, I, D, D, D, D, I, I, I, D, P, I, P, P, I, P, P, P, I, I]
         for f in (lib.orc_fd_coeffs, lib.orc_damping_profile, lib.orc_laplacian,
                   lib.orc_forward, lib.orc_max_threads, lib.orc_adjoint, lib.orc_gradient):
             f.restype = ctypes.c_int
@@ -95,21 +95,23 @@ class Oracle:
             raise ValueError(f"orc_damping_profile -> {rc}")
         return out
 
-    def laplacian(self, u: np.ndarray, h, order: int = 8) -> np.ndarray:
-        """Sec. 3 Laplacian of u [nz][ny][nx] with u = 0 outside the grid."""
+    def laplacian(self, u: np.ndarray, h, order: int = 8, free_surface: bool = False) -> np.ndarray:
+        """Sec. 3 Laplacian of u [nz][ny][nx] with u = 0 outside the grid (with
+        free_surface, the odd image of reading R15 above k = 0)."""
         u = np.ascontiguousarray(u, dtype=np.float64)
         nz, ny, nx = u.shape
         hx, hy, hz = h
         out = np.empty_like(u)
-        rc = self.lib.orc_laplacian(nx, ny, nz, hx, hy, hz, order, _ptr(u), _ptr(out))
+        rc = self.lib.orc_laplacian(nx, ny, nz, hx, hy, hz, order, _ptr(u), _ptr(out), int(free_surface))
         if rc != 0:
             raise ValueError(f"orc_laplacian -> {rc}")
         return out
 
     def forward(self, vel: np.ndarray, h, dt: float, nt: int, *, order: int = 8, nbl: int = 0,
                 refl: float = 1e-3, src_ijk=None, wavelet=None, rec_ijk=None,
-                u_prev0=None, u_cur0=None, want_state: bool = False, nthreads: int = 0):
-        """Alg. 1 / Alg. 2 forward run in FP64.
+                u_prev0=None, u_cur0=None, want_state: bool = False, nthreads: int = 0,
+                free_surface: bool = False):
+        """Alg. 1 / Alg. 2 forward run in FP64 (free_surface: reading R15).
 
         vel: [nz][ny][nx] float32 m/s.  src_ijk: [nsrc][3] (i, j, k).  wavelet:
         [nsrc][nt] float32.  rec_ijk: [nrec][3].  Returns traces [nt][nrec]
@@ -132,7 +134,7 @@ class Oracle:
         rc = self.lib.orc_forward(nx, ny, nz, hx, hy, hz, dt, nt, order, nbl, refl, _ptr(vel),
                                   nsrc, _ptr(src) if nsrc else None, _ptr(wav),
                                   nrec, _ptr(rec) if nrec else None, _ptr(traces) if nrec else None,
-                                  _ptr(up0), _ptr(uc0), _ptr(upo), _ptr(uco), nthreads)
+                                  _ptr(up0), _ptr(uc0), _ptr(upo), _ptr(uco), nthreads, int(free_surface))
         if rc != 0:
             raise ValueError(f"orc_forward -> {rc}")
         if want_state:
@@ -141,7 +143,7 @@ class Oracle:
 
 
     def adjoint(self, vel, h, dt, nt, *, order=8, nbl=0, refl=1e-3, src_ijk=None, rec_ijk=None,
-                resid=None, nthreads=0):
+                resid=None, nthreads=0, free_surface=False):
         """Transpose of the forward map wavelet -> traces: resid [nt][nrec] ->
         adjoint source [nsrc][nt] (FP64)."""
         vel = np.ascontiguousarray(vel, dtype=np.float32)
@@ -151,13 +153,14 @@ class Oracle:
         r = np.ascontiguousarray(resid, np.float64).reshape(nt, len(rec))
         adj = np.zeros((len(src), nt), np.float64)
         rc = self.lib.orc_adjoint(nx, ny, nz, h[0], h[1], h[2], dt, nt, order, nbl, refl, _ptr(vel),
-                                  len(src), _ptr(src), len(rec), _ptr(rec), _ptr(r), _ptr(adj), nthreads)
+                                  len(src), _ptr(src), len(rec), _ptr(rec), _ptr(r), _ptr(adj), nthreads,
+                                  int(free_surface))
         if rc != 0:
             raise ValueError(f"orc_adjoint -> {rc}")
         return adj
 
     def gradient(self, vel, h, dt, nt, *, order=8, nbl=0, refl=1e-3, src_ijk=None, wavelet=None,
-                 rec_ijk=None, resid=None, nthreads=0):
+                 rec_ijk=None, resid=None, nthreads=0, free_surface=False):
         """dJ/dv for J = 1/2 sum |traces - d_obs|^2 given resid = traces - d_obs
         ([nt][nrec]); returns [nz][ny][nx] FP64.  Stores every forward state:
         small grids only."""
@@ -170,7 +173,7 @@ class Oracle:
         g = np.zeros(vel.shape, np.float64)
         rc = self.lib.orc_gradient(nx, ny, nz, h[0], h[1], h[2], dt, nt, order, nbl, refl, _ptr(vel),
                                    len(src), _ptr(src), _ptr(wav), len(rec), _ptr(rec), _ptr(r), _ptr(g),
-                                   nthreads)
+                                   nthreads, int(free_surface))
         if rc != 0:
             raise ValueError(f"orc_gradient -> {rc}")
         return g
@@ -195,8 +198,8 @@ def damping_profile(n: int, nbl: int, h: float, vmax: float, refl: float = 1e-3)
     return _default().damping_profile(n, nbl, h, vmax, refl)
 
 
-def laplacian(u: np.ndarray, h, order: int = 8) -> np.ndarray:
-    return _default().laplacian(u, h, order)
+def laplacian(u: np.ndarray, h, order: int = 8, free_surface: bool = False) -> np.ndarray:
+    return _default().laplacian(u, h, order, free_surface)
 
 
 def forward(vel, h, dt, nt, **kw):

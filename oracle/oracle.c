@@ -31,6 +31,11 @@
  *       add of Alg. 1 is  c(x_s) w[n] / (hx hy hz (1 + eta(x_s) dt)),  i.e.
  *       the source sits inside the damped update's numerator.
  *   R7  receivers record u^{n+1} at grid points after the add of step n.
+ *   R15 free surface (the paper's option at the surface, Sec. 3): p = 0 on
+ *       the plane k = 0, imposed as the odd image  u(i, j, -m) = -u(i, j, m)
+ *       for the stencil and u(i, j, 0) = 0 after every step (sources added
+ *       there vanish, receivers there read 0); the top damping layer is
+ *       removed (eta_z = 0 for k < L), the other five faces keep theirs.
  *
  * Index convention: i along x (fastest), j along y, k along z (depth, k = 0 at
  * the surface); user arrays are [nz][ny][nx].
@@ -130,6 +135,23 @@ static double *padded_zeros(const grid_t *g)
     return (double *)calloc((size_t)(g->px * g->py * g->pz), sizeof(double));
 }
 
+/* Reading R15: fill the R planes above the surface with the odd image of
+ * the planes below it (every padded x-y position, so edges stay zero).    */
+static void mirror_top(const grid_t *g, double *u)
+{
+    for (int m = 1; m <= g->R && m < g->nz; ++m)
+        for (int j = -g->R; j < g->ny + g->R; ++j)
+            for (int i = -g->R; i < g->nx + g->R; ++i)
+                u[at(g, i, j, -m)] = -u[at(g, i, j, m)];
+}
+
+/* Reading R15: p = 0 on the surface plane k = 0. */
+static void zero_top(const grid_t *g, double *u)
+{
+    for (int j = 0; j < g->ny; ++j)
+        for (int i = 0; i < g->nx; ++i) u[at(g, i, j, 0)] = 0.0;
+}
+
 /* Sec. 3 Laplacian at one point: per axis  sum_m c_am [p(+m) + p(-m) - 2p]. */
 static inline double lap_at(const grid_t *g, const double *u, long o,
                             const double *cx, const double *cy, const double *cz)
@@ -159,7 +181,7 @@ static int axis_weights(int order, double hx, double hy, double hz,
 
 /* Sec. 3 Laplacian of a whole field u [nz][ny][nx] into out, u = 0 outside. */
 int orc_laplacian(int nx, int ny, int nz, double hx, double hy, double hz, int order,
-                  const double *u, double *out)
+                  const double *u, double *out, int free_surface)
 {
     if (nx < 1 || ny < 1 || nz < 1 || !u || !out) return -1;
     double cx[ORC_MAX_R + 1], cy[ORC_MAX_R + 1], cz[ORC_MAX_R + 1];
@@ -171,6 +193,7 @@ int orc_laplacian(int nx, int ny, int nz, double hx, double hy, double hz, int o
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i)
                 pu[at(&g, i, j, k)] = u[((long)k * ny + j) * nx + i];
+    if (free_surface) mirror_top(&g, pu);
     #pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
@@ -197,10 +220,11 @@ int orc_forward(int nx, int ny, int nz, double hx, double hy, double hz,
                 int nsrc, const int *src_ijk, const float *wavelet,
                 int nrec, const int *rec_ijk, double *traces,
                 const double *u_prev0, const double *u_cur0,
-                double *u_prev_out, double *u_cur_out, int nthreads)
+                double *u_prev_out, double *u_cur_out, int nthreads, int free_surface)
 {
     if (nx < 1 || ny < 1 || nz < 1 || nt < 0 || dt <= 0 || !vel) return -1;
     if (hx <= 0 || hy <= 0 || hz <= 0) return -1;
+    if (free_surface && nz <= order / 2) return -1;
     if (2 * nbl > nx || 2 * nbl > ny || 2 * nbl > nz || nbl < 0) return -1;
     if (nsrc < 0 || nrec < 0 || (nsrc > 0 && (!src_ijk || !wavelet))) return -1;
     if (nrec > 0 && (!rec_ijk || !traces)) return -1;
@@ -233,6 +257,8 @@ int orc_forward(int nx, int ny, int nz, double hx, double hy, double hz,
     if (!ex || !ey || !ez || !C || !ua || !ub || !uc) { rc = -3; goto done; }
     if (orc_damping_profile(nx, nbl, hx, vmax, refl, ex) || orc_damping_profile(ny, nbl, hy, vmax, refl, ey) ||
         orc_damping_profile(nz, nbl, hz, vmax, refl, ez)) { rc = -1; goto done; }
+    if (free_surface)   /* reading R15: no absorbing layer under the free surface */
+        for (int k = 0; k < nbl && k < nz - 1 - nbl; ++k) ez[k] = 0.0;
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
@@ -242,6 +268,7 @@ int orc_forward(int nx, int ny, int nz, double hx, double hy, double hz,
                 if (u_prev0) ua[at(&g, i, j, k)] = u_prev0[q];
                 if (u_cur0) ub[at(&g, i, j, k)] = u_cur0[q];
             }
+    if (free_surface) { zero_top(&g, ua); zero_top(&g, ub); }
 
     /* Alg. 2 region bounds: inner = [x3,x4] x [y3,y4] x [z3,z4]. */
     const int x3 = nbl, x4 = nx - 1 - nbl, y3 = nbl, y4 = ny - 1 - nbl, z3 = nbl, z4 = nz - 1 - nbl;
@@ -249,6 +276,7 @@ int orc_forward(int nx, int ny, int nz, double hx, double hy, double hz,
     double *up = ua, *ucur = ub, *un = uc;   /* u^{n-1}, u^n, u^{n+1} */
 
     for (int n = 0; n < nt; ++n) {          /* Alg. 1 time loop */
+        if (free_surface) mirror_top(&g, ucur);
         #pragma omp parallel for collapse(2) schedule(static)
         for (int k = 0; k < nz; ++k)
             for (int j = 0; j < ny; ++j)
@@ -272,6 +300,7 @@ int orc_forward(int nx, int ny, int nz, double hx, double hy, double hz,
             const double e = (ex[p[0]] + ey[p[1]] + ez[p[2]]) * dt;
             un[o] += C[o] * (double)wavelet[(long)s * nt + n] / (cell * (1.0 + e));
         }
+        if (free_surface) zero_top(&g, un);
         /* Reading R7: receivers sample u^{n+1}. */
         for (int r = 0; r < nrec; ++r) {
             const int *p = rec_ijk + 3 * r;
@@ -322,7 +351,7 @@ static int adjoint_core(int nx, int ny, int nz, double hx, double hy, double hz,
                         double dt, int nt, int order, int nbl, double refl,
                         const float *vel, int nsrc, const int *src_ijk, const float *wavelet,
                         int nrec, const int *rec_ijk, const double *resid, double *adj,
-                        double *const *u_hist, double *grad_c)
+                        double *const *u_hist, double *grad_c, int free_surface)
 {
     double cx[ORC_MAX_R + 1], cy[ORC_MAX_R + 1], cz[ORC_MAX_R + 1];
     if (axis_weights(order, hx, hy, hz, cx, cy, cz) != 0) return -1;
@@ -339,6 +368,8 @@ static int adjoint_core(int nx, int ny, int nz, double hx, double hy, double hz,
     if (!ex || !ey || !ez || !C || !m0 || !m1 || !m2 || !cm) { rc = -3; goto done; }
     if (orc_damping_profile(nx, nbl, hx, vmax, refl, ex) || orc_damping_profile(ny, nbl, hy, vmax, refl, ey) ||
         orc_damping_profile(nz, nbl, hz, vmax, refl, ez)) { rc = -1; goto done; }
+    if (free_surface)
+        for (int k = 0; k < nbl && k < nz - 1 - nbl; ++k) ez[k] = 0.0;
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
@@ -355,6 +386,7 @@ static int adjoint_core(int nx, int ny, int nz, double hx, double hy, double hz,
                     const long o = at(&g, i, j, k);
                     cm[o] = C[o] * m1[o];
                 }
+        if (free_surface) mirror_top(&g, cm);   /* the restricted L is symmetric: L^T = L */
         #pragma omp parallel for collapse(2) schedule(static)
         for (int k = 0; k < nz; ++k)
             for (int j = 0; j < ny; ++j)
@@ -369,6 +401,7 @@ static int adjoint_core(int nx, int ny, int nz, double hx, double hy, double hz,
             const double e = (ex[p[0]] + ey[p[1]] + ez[p[2]]) * dt;
             m0[o] += resid[(long)(n - 1) * nrec + r] / (1.0 + e);
         }
+        if (free_surface) zero_top(&g, m0);     /* the transpose of the surface projection */
         for (int s = 0; s < nsrc; ++s) {
             const int *p = src_ijk + 3 * s;
             const long o = at(&g, p[0], p[1], p[2]);
@@ -377,6 +410,7 @@ static int adjoint_core(int nx, int ny, int nz, double hx, double hy, double hz,
         if (grad_c) {
             /* term of forward step n-1: mu^n (L u^{n-1} + s^{n-1}); u_hist[m+1] = u^m */
             const double *u = u_hist[n];   /* u^{n-1} */
+            if (free_surface) mirror_top(&g, u_hist[n]);
             #pragma omp parallel for collapse(2) schedule(static)
             for (int k = 0; k < nz; ++k)
                 for (int j = 0; j < ny; ++j)
@@ -409,9 +443,10 @@ static int check_positions(int nx, int ny, int nz, int n, const int *ijk)
 int orc_adjoint(int nx, int ny, int nz, double hx, double hy, double hz,
                 double dt, int nt, int order, int nbl, double refl, const float *vel,
                 int nsrc, const int *src_ijk, int nrec, const int *rec_ijk,
-                const double *resid, double *adj, int nthreads)
+                const double *resid, double *adj, int nthreads, int free_surface)
 {
     if (nx < 1 || ny < 1 || nz < 1 || nt < 0 || dt <= 0 || !vel || nsrc < 0 || nrec < 0) return -1;
+    if (free_surface && nz <= order / 2) return -1;
     if (2 * nbl > nx || 2 * nbl > ny || 2 * nbl > nz || nbl < 0) return -1;
     if ((nsrc && (!src_ijk || !adj)) || (nrec && (!rec_ijk || !resid))) return -1;
     if (check_positions(nx, ny, nz, nsrc, src_ijk) || check_positions(nx, ny, nz, nrec, rec_ijk)) return -1;
@@ -421,7 +456,7 @@ int orc_adjoint(int nx, int ny, int nz, double hx, double hy, double hz,
     (void)nthreads;
 #endif
     return adjoint_core(nx, ny, nz, hx, hy, hz, dt, nt, order, nbl, refl, vel, nsrc, src_ijk, NULL,
-                        nrec, rec_ijk, resid, adj, NULL, NULL);
+                        nrec, rec_ijk, resid, adj, NULL, NULL, free_surface);
 }
 
 /* Gradient of J = 1/2 sum_n |R u^{n+1} - d_obs^n|^2 with respect to the
@@ -432,8 +467,10 @@ int orc_adjoint(int nx, int ny, int nz, double hx, double hy, double hz,
 int orc_gradient(int nx, int ny, int nz, double hx, double hy, double hz,
                  double dt, int nt, int order, int nbl, double refl, const float *vel,
                  int nsrc, const int *src_ijk, const float *wavelet,
-                 int nrec, const int *rec_ijk, const double *resid, double *grad_v, int nthreads)
+                 int nrec, const int *rec_ijk, const double *resid, double *grad_v, int nthreads,
+                 int free_surface)
 {
+    if (free_surface && nz <= order / 2) return -1;
     if (nx < 1 || ny < 1 || nz < 1 || nt < 0 || dt <= 0 || !vel || !grad_v || nsrc < 0 || nrec < 0) return -1;
     if (2 * nbl > nx || 2 * nbl > ny || 2 * nbl > nz || nbl < 0) return -1;
     if ((nsrc && (!src_ijk || !wavelet)) || (nrec && (!rec_ijk || !resid))) return -1;
@@ -473,7 +510,7 @@ int orc_gradient(int nx, int ny, int nz, double hx, double hy, double hz,
         double *up = (double *)malloc(sizeof(double) * (size_t)N), *un = (double *)malloc(sizeof(double) * (size_t)N);
         if (!up || !un) { free(up); free(un); free(wm); rc = -3; goto done; }
         rc = orc_forward(nx, ny, nz, hx, hy, hz, dt, 1, order, nbl, refl, vel, nsrc, src_ijk, wm,
-                         0, NULL, NULL, prev, cur, up, un, nthreads);
+                         0, NULL, NULL, prev, cur, up, un, nthreads, free_surface);
         for (int k = 0; k < nz; ++k)
             for (int j = 0; j < ny; ++j)
                 for (int i = 0; i < nx; ++i)
@@ -482,7 +519,7 @@ int orc_gradient(int nx, int ny, int nz, double hx, double hy, double hz,
         if (rc) goto done;
     }
     rc = adjoint_core(nx, ny, nz, hx, hy, hz, dt, nt, order, nbl, refl, vel, nsrc, src_ijk, wavelet,
-                      nrec, rec_ijk, resid, NULL, hist, gc);
+                      nrec, rec_ijk, resid, NULL, hist, gc, free_surface);
     if (rc) goto done;
     for (long q = 0; q < N; ++q) grad_v[q] = 2.0 * dt * dt * (double)vel[q] * gc[q];
 done:

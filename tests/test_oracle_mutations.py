@@ -9,6 +9,7 @@ import oracle
 import test_oracle_adjoint as AD
 import test_oracle_bruteforce as BF
 import test_oracle_dynamics as DY
+import test_oracle_free_surface as FS
 import test_oracle_stencil as ST
 
 
@@ -43,6 +44,12 @@ def _adjoint(orc):
     AD.test_adjoint_is_the_explicit_transpose(orc)
 
 
+def _fs(orc):
+    FS.test_odd_image_laplacian_is_exact_at_the_surface(orc)
+    FS.test_dense_stepper_with_free_surface(orc, (11, 10, 12), 2)
+    FS.test_adjoint_dot_product_with_free_surface(orc)
+
+
 def _grad(orc):
     for kind in ("point", "smooth", "source"):
         AD.test_gradient_matches_finite_differences(orc, kind)
@@ -75,6 +82,11 @@ MUTATIONS = [
      "+= 0.0 * m0[o] * (double)wavelet[(long)s * nt + (n - 1)] / cell;", [_grad]),
     ("gradient pairs mu^n with u^n", "const double *u = u_hist[n];   /* u^{n-1} */",
      "const double *u = u_hist[n + 1];", [_grad]),
+    ("free surface uses the even image", "u[at(g, i, j, -m)] = -u[at(g, i, j, m)];",
+     "u[at(g, i, j, -m)] = u[at(g, i, j, m)];", [_fs]),
+    ("free surface keeps the top damping layer", "for (int k = 0; k < nbl && k < nz - 1 - nbl; ++k) ez[k] = 0.0;\n    for (int k = 0; k < nz; ++k)\n        for (int j = 0; j < ny; ++j)\n            for (int i = 0; i < nx; ++i) {\n                const long q",
+     "for (int k = 0; k < 0; ++k) ez[k] = 0.0;\n    for (int k = 0; k < nz; ++k)\n        for (int j = 0; j < ny; ++j)\n            for (int i = 0; i < nx; ++i) {\n                const long q", [_fs]),
+    ("adjoint misses the surface projection", "if (free_surface) zero_top(&g, m0);", "", [_fs]),
 ]
 
 
