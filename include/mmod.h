@@ -78,6 +78,11 @@ typedef struct {
     const int *src_ijk;      /* host [nsrc][3] (i, j, k); copied by mmod_create */
     int nrec;                /* number of receivers, >= 0 */
     const int *rec_ijk;      /* host [nrec][3] (i, j, k); copied by mmod_create */
+    int free_surface;        /* 1: free surface at k = 0 (the paper's surface option,
+                                Sec. 3): p = 0 on that plane through the odd image
+                                u(-m) = -u(m), no damping layer under it, sources on
+                                the plane do nothing and receivers there read 0;
+                                needs nz >= 5.  0: damping layers on all six faces. */
 } mmod_config;
 
 /* Create a handle on CUDA device `device`: validates the configuration,
@@ -176,7 +181,8 @@ mmod_status mmod_revolve_schedule(int nsteps, int snaps, int *actions, long long
 mmod_status mmod_dot(const float *a, const float *b, long long n, double *out, mmod_stream stream);
 
 /* Test hook: the next mmod_forward starts from u^{-1} = u_prev, u^0 = u_cur
- * ([nz][ny][nx] FP32, either may be NULL for zeros) instead of zeros. */
+ * ([nz][ny][nx] FP32, either may be NULL for zeros) instead of zeros (with a
+ * free surface, the plane k = 0 of both is set to 0). */
 mmod_status mmod_set_state(mmod_handle *h, const float *u_prev, const float *u_cur,
                            mmod_stream stream);
 

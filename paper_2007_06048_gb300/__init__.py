@@ -61,7 +61,8 @@ class _Config(ctypes.Structure):
                 ("dt", ctypes.c_double), ("nt", ctypes.c_int), ("order", ctypes.c_int),
                 ("nbl", ctypes.c_int), ("damp_R", ctypes.c_double),
                 ("nsrc", ctypes.c_int), ("src_ijk", ctypes.c_void_p),
-                ("nrec", ctypes.c_int), ("rec_ijk", ctypes.c_void_p)]
+                ("nrec", ctypes.c_int), ("rec_ijk", ctypes.c_void_p),
+                ("free_surface", ctypes.c_int)]
 
 
 _lib = None
@@ -173,13 +174,11 @@ def mmod_version() -> str:
 
 
 def mmod_create(nx, ny, nz, h, dt, nt, *, nbl=0, src_ijk=None, rec_ijk=None, order=8,
-                damp_R=1e-3, device=0):
+                damp_R=1e-3, device=0, free_surface=False):
     """Create a handle (ctypes void pointer).  src_ijk / rec_ijk: [n][3] int."""
     src = np.ascontiguousarray(np.zeros((0, 3)) if src_ijk is None else src_ijk, np.int32).reshape(-1, 3)
     rec = np.ascontiguousarray(np.zeros((0, 3)) if rec_ijk is None else rec_ijk, np.int32).reshape(-1, 3)
-    cfg = _Config(int(nx), int(ny), int(nz), float(h[0]), float(h[1]), float(h[2]), float(dt), int(nt),
-                  int(order), int(nbl), float(damp_R), len(src), src.ctypes.data if len(src) else None,
-                  len(rec), rec.ctypes.data if len(rec) else None)
+    cfg = _config(nx, ny, nz, h, dt, nt, nbl, src, rec, order, damp_R, free_surface)
     out = ctypes.c_void_p()
     st = load().mmod_create(ctypes.byref(cfg), int(device), ctypes.byref(out))
     if st != 0:
@@ -187,18 +186,19 @@ def mmod_create(nx, ny, nz, h, dt, nt, *, nbl=0, src_ijk=None, rec_ijk=None, ord
     return out
 
 
-def _config(nx, ny, nz, h, dt, nt, nbl, src, rec, order, damp_R):
+def _config(nx, ny, nz, h, dt, nt, nbl, src, rec, order, damp_R, free_surface=False):
     return _Config(int(nx), int(ny), int(nz), float(h[0]), float(h[1]), float(h[2]), float(dt), int(nt),
                    int(order), int(nbl), float(damp_R), len(src), src.ctypes.data if len(src) else None,
-                   len(rec), rec.ctypes.data if len(rec) else None)
+                   len(rec), rec.ctypes.data if len(rec) else None, int(bool(free_surface)))
 
 
 def mmod_forward_noalloc(nx, ny, nz, h, dt, nt, vel, wavelet, traces, final_u=None, *, nbl=0,
-                         src_ijk=None, rec_ijk=None, order=8, damp_R=1e-3, device=0, stream=None):
+                         src_ijk=None, rec_ijk=None, order=8, damp_R=1e-3, device=0, stream=None,
+                         free_surface=False):
     """Allocation-free forward run (device pointers only; see include/mmod.h)."""
     src = np.ascontiguousarray(np.zeros((0, 3)) if src_ijk is None else src_ijk, np.int32).reshape(-1, 3)
     rec = np.ascontiguousarray(np.zeros((0, 3)) if rec_ijk is None else rec_ijk, np.int32).reshape(-1, 3)
-    cfg = _config(nx, ny, nz, h, dt, nt, nbl, src, rec, order, damp_R)
+    cfg = _config(nx, ny, nz, h, dt, nt, nbl, src, rec, order, damp_R, free_surface)
     st = load().mmod_forward_noalloc(ctypes.byref(cfg), int(device), _addr(vel), _addr(wavelet),
                                      _addr(traces), _addr(final_u), _stream(stream))
     if st != 0:
@@ -381,20 +381,21 @@ class Propagator:
     """Owning wrapper around one handle for a given problem geometry."""
 
     def __init__(self, shape, h, dt, nt, *, nbl=0, src_ijk=None, rec_ijk=None, damp_R=1e-3,
-                 device=0, order=8):
+                 device=0, order=8, free_surface=False):
         nz, ny, nx = shape
         self.shape = tuple(shape)
         self.nt = int(nt)
         self.nsrc = 0 if src_ijk is None else len(np.asarray(src_ijk).reshape(-1, 3))
         self.nrec = 0 if rec_ijk is None else len(np.asarray(rec_ijk).reshape(-1, 3))
         self.device = device
+        self.free_surface = bool(free_surface)
         self.handle = mmod_create(nx, ny, nz, h, dt, nt, nbl=nbl, src_ijk=src_ijk, rec_ijk=rec_ijk,
-                                  order=order, damp_R=damp_R, device=device)
+                                  order=order, damp_R=damp_R, device=device, free_surface=free_surface)
 
     @classmethod
     def from_problem(cls, p, device=0):
         return cls(p.vel.shape, p.h, p.dt, p.nt, nbl=p.nbl, src_ijk=p.src_ijk, rec_ijk=p.rec_ijk,
-                   damp_R=p.refl, device=device, order=p.order)
+                   damp_R=p.refl, device=device, order=p.order, free_surface=p.free_surface)
 
     def set_model(self, vel, stream=None):
         mmod_set_model(self.handle, vel, stream)

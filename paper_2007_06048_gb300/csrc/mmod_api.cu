@@ -53,6 +53,8 @@ std::string validate(const mmod_config *c, mmod_status *st) {
         if (!in_grid(*c, c->src_ijk + 3 * s)) return "source " + std::to_string(s) + " outside the grid";
     for (int r = 0; r < c->nrec; ++r)
         if (!in_grid(*c, c->rec_ijk + 3 * r)) return "receiver " + std::to_string(r) + " outside the grid";
+    if (c->free_surface != 0 && c->free_surface != 1) return "free_surface must be 0 or 1";
+    if (c->free_surface && c->nz < kRadius + 1) return "a free surface needs nz >= 5";
     if (c->order != 8) {
         *st = MMOD_ERR_UNSUPPORTED;
         return "the GPU path implements order 8 only";
@@ -118,8 +120,10 @@ cudaError_t build_inj(const mmod_config &c, long long plane, int nxp, const int 
         const int *p = pos + 3 * s;
         return ((long long)(p[1] / kInjTileY) * t->tiles_x + p[0] / kInjTileX) * c.nz + p[2];
     };
-    std::vector<int> order(n);
-    std::iota(order.begin(), order.end(), 0);
+    // with a free surface, positions on the plane k = 0 inject nothing
+    std::vector<int> order;
+    for (int q = 0; q < n; ++q)
+        if (!(c.free_surface && pos[3 * q + 2] == 0)) order.push_back(q);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
         const long long ba = bucket(a), bb = bucket(b);
         if (ba != bb) return ba < bb;
@@ -127,10 +131,11 @@ cudaError_t build_inj(const mmod_config &c, long long plane, int nxp, const int 
         if (pa[1] != pb[1]) return pa[1] < pb[1];
         return pa[0] < pb[0];
     });
-    std::vector<int> pt_i, pt_j, pt_k, pt_first, src_row(n), si(n), sj(n), sk(n);
+    const int m = (int)order.size();
+    std::vector<int> pt_i, pt_j, pt_k, pt_first, src_row(m), si(m), sj(m), sk(m);
     std::vector<long long> pt_off;
     std::vector<int> tile_start((size_t)(c.nz * tiles + 1), 0);
-    for (int q = 0; q < n; ++q) {
+    for (int q = 0; q < m; ++q) {
         const int s = order[q];
         const int *p = pos + 3 * s;
         src_row[q] = s;
@@ -147,19 +152,19 @@ cudaError_t build_inj(const mmod_config &c, long long plane, int nxp, const int 
             tile_start[(size_t)bucket(s) + 1]++;
         }
     }
-    pt_first.push_back(n);
+    pt_first.push_back(m);
     for (size_t b = 1; b < tile_start.size(); ++b) tile_start[b] += tile_start[b - 1];
     t->npts = (int)pt_i.size();
-    t->nsrc = n;
+    t->nsrc = m;
     cudaError_t e;
     if ((e = upload(&t->tile_start, tile_start)) || (e = upload(&t->pt_i, pt_i)) || (e = upload(&t->pt_j, pt_j)) ||
         (e = upload(&t->pt_k, pt_k)) || (e = upload(&t->pt_off, pt_off)) || (e = upload(&t->pt_first, pt_first)) ||
         (e = upload(&t->src_row, src_row)) || (e = upload(&t->src_i, si)) || (e = upload(&t->src_j, sj)) ||
         (e = upload(&t->src_k, sk)))
         return e;
-    e = cudaMalloc(&t->src_scale, sizeof(float) * std::max(n, 1));
+    e = cudaMalloc(&t->src_scale, sizeof(float) * std::max(m, 1));
     if (e != cudaSuccess) return e;
-    return cudaMemset(t->src_scale, 0, sizeof(float) * std::max(n, 1));
+    return cudaMemset(t->src_scale, 0, sizeof(float) * std::max(m, 1));
 }
 
 // Gather positions pos[n][3] bucketed per (64 x 16 tile, plane), tile-major
@@ -217,6 +222,10 @@ void damping_profile(int n, int nbl, double h, double vmax, double R, double dt,
         const double s = (double)d / nbl;
         out[i] = (float)(dt * eta_max * s * s);
     }
+}
+
+void clear_surface_layer(int nz, int nbl, float *ez) {
+    for (int k = 0; k < nbl && k < nz - 1 - nbl; ++k) ez[k] = 0.0f;
 }
 
 mmod_status fail(mmod_handle *h, mmod_status st, const std::string &msg) {
@@ -291,6 +300,7 @@ StepArgs base_args(mmod_handle *h, const Geometry &geo, const float *wavelet) {
     a.nrec = geo.ngather; a.rec_off = geo.gather_off;
     a.traces = nullptr;
     a.err = h->err_dev;
+    a.fs = h->cfg.free_surface;
     a.pdl = h->pdl;
     return a;
 }
@@ -645,6 +655,7 @@ MMOD_API mmod_status mmod_set_model(mmod_handle *h, const float *vel, mmod_strea
     damping_profile(c.nx, c.nbl, c.hx, vmax, c.damp_R, c.dt, eta.data());
     damping_profile(c.ny, c.nbl, c.hy, vmax, c.damp_R, c.dt, eta.data() + c.nx);
     damping_profile(c.nz, c.nbl, c.hz, vmax, c.damp_R, c.dt, eta.data() + c.nx + c.ny);
+    if (c.free_surface) clear_surface_layer(c.nz, c.nbl, eta.data() + c.nx + c.ny);
     MMOD_CK(h, cudaMemcpyAsync(h->eta, eta.data(), sizeof(float) * eta.size(), cudaMemcpyHostToDevice, s));
     MMOD_CK(h, cudaStreamSynchronize(s));   // eta lives on the host stack
     h->vmax = vmax;
@@ -668,6 +679,8 @@ MMOD_API mmod_status mmod_set_state(mmod_handle *h, const float *u_prev, const f
         }
         // buffer 0 holds u^{n-1}, buffer 1 holds u^n at step 0
         MMOD_CK(h, launch_pack(d, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->nxp, h->u[b], s));
+        // a free surface holds p = 0 on its plane from the start
+        if (h->cfg.free_surface) MMOD_CK(h, cudaMemsetAsync(h->u[b], 0, sizeof(float) * (size_t)h->plane, s));
     }
     h->state_pending = true;
     return MMOD_OK;

@@ -50,6 +50,7 @@ struct StepArgs {
     const long long *rec_off;             // padded offsets
     float *traces;                        // [nt][nrec]
     int *err;                             // device view of the mapped error word
+    int fs;                               // free surface at k = 0 (odd image, p = 0 on the plane)
     int pdl;                              // 0: plain launch; 1: programmatic dependent launch;
                                           // 2: the same, and the previous kernel in the stream
                                           //    is the previous step of this run
@@ -73,6 +74,8 @@ __device__ __forceinline__ void inject_point(const StepArgs &a, int p) { inject_
 
 // Host helpers shared by the entry points (mmod_api.cu).
 void damping_profile(int n, int nbl, double h, double vmax, double R, double dt, float *out);
+// With a free surface the z axis has no layer under the surface plane.
+void clear_surface_layer(int nz, int nbl, float *ez);
 void set_thread_error(const char *msg);   // fixed buffer read by mmod_last_error(NULL)
 
 // Order-8 Taylor weights of the second derivative (Sec. 3):

@@ -133,6 +133,8 @@ extern "C" __attribute__((visibility("default"))) mmod_status mmod_forward_noall
     if (c.nbl < 0 || 2LL * c.nbl > c.nx || 2LL * c.nbl > c.ny || 2LL * c.nbl > c.nz)
         return fail(MMOD_ERR_ARG, "damping width must satisfy 0 <= 2*nbl <= n on every axis");
     if (c.nbl > 0 && !(c.damp_R > 0 && c.damp_R < 1)) return fail(MMOD_ERR_ARG, "damp_R must be in (0, 1)");
+    if (c.free_surface != 0 && c.free_surface != 1) return fail(MMOD_ERR_ARG, "free_surface must be 0 or 1");
+    if (c.free_surface && c.nz < kRadius + 1) return fail(MMOD_ERR_ARG, "a free surface needs nz >= 5");
     const int nxp = (c.nx + 31) / 32 * 32;
     const long long plane = (long long)nxp * c.ny, vol = plane * c.nz;
     if (c.nx > kMaxAxis || c.ny > kMaxAxis || c.nz > kMaxAxis || vol > kMaxVolume)
@@ -198,8 +200,10 @@ extern "C" __attribute__((visibility("default"))) mmod_status mmod_forward_noall
         return a < b;
     };
     int order[kMaxSrc];
-    for (int t = 0; t < c.nsrc; ++t) order[t] = t;
-    for (int t = 1; t < c.nsrc; ++t)   // insertion sort (at most 64 entries)
+    int nkeep = 0;   // with a free surface, sources on the plane k = 0 inject nothing
+    for (int t = 0; t < c.nsrc; ++t)
+        if (!(c.free_surface && c.src_ijk[3 * t + 2] == 0)) order[nkeep++] = t;
+    for (int t = 1; t < nkeep; ++t)   // insertion sort (at most 64 entries)
         for (int q = t; q > 0 && before(order[q], order[q - 1]); --q) {
             const int tmp = order[q];
             order[q] = order[q - 1];
@@ -210,7 +214,7 @@ extern "C" __attribute__((visibility("default"))) mmod_status mmod_forward_noall
     int *src_row = tab + 4 * kMaxSrc + 1, *src_i = src_row + kMaxSrc, *src_j = src_i + kMaxSrc, *src_k = src_j + kMaxSrc;
     long long pt_off[kMaxSrc] = {0}, pt_bucket[kMaxSrc] = {0};
     int npt = 0;
-    for (int q = 0; q < c.nsrc; ++q) {
+    for (int q = 0; q < nkeep; ++q) {
         const int sidx = order[q];
         const int *p = c.src_ijk + 3 * sidx;
         src_row[q] = sidx;
@@ -228,7 +232,7 @@ extern "C" __attribute__((visibility("default"))) mmod_status mmod_forward_noall
             ++npt;
         }
     }
-    pt_first[npt] = c.nsrc;
+    pt_first[npt] = nkeep;
     CKN(cudaMemcpyAsync(tab_d, tab, sizeof(tab), cudaMemcpyHostToDevice, s));
     CKN(cudaMemcpyAsync(pt_off_d, pt_off, sizeof(pt_off), cudaMemcpyHostToDevice, s));
     CKN(cudaStreamSynchronize(s));   // the host tables above live on the stack
@@ -276,13 +280,14 @@ extern "C" __attribute__((visibility("default"))) mmod_status mmod_forward_noall
     CKN(launch_model_fill(vel, c.nx, c.ny, c.nz, nxp, c.dt, cvol, s));
     {
         int *tab_src_i = tab_d + 4 * kMaxSrc + 1 + kMaxSrc;
-        CKN(launch_source_scale(vel, c.nx, c.ny, c.nsrc, tab_src_i, tab_src_i + kMaxSrc, tab_src_i + 2 * kMaxSrc,
+        CKN(launch_source_scale(vel, c.nx, c.ny, nkeep, tab_src_i, tab_src_i + kMaxSrc, tab_src_i + 2 * kMaxSrc,
                                 c.dt, c.hx * c.hy * c.hz, src_scale, s));
     }
     float eta_h[3 * kMaxAxis];
     damping_profile(c.nx, c.nbl, c.hx, vmax, c.damp_R, c.dt, eta_h);
     damping_profile(c.ny, c.nbl, c.hy, vmax, c.damp_R, c.dt, eta_h + c.nx);
     damping_profile(c.nz, c.nbl, c.hz, vmax, c.damp_R, c.dt, eta_h + c.nx + c.ny);
+    if (c.free_surface) clear_surface_layer(c.nz, c.nbl, eta_h + c.nx + c.ny);
     CKN(cudaMemcpyAsync(eta, eta_h, sizeof(float) * (c.nx + c.ny + c.nz), cudaMemcpyHostToDevice, s));
 
     // ---- time loop: u^{-1} = u^0 = 0, one step kernel per step
@@ -306,6 +311,7 @@ extern "C" __attribute__((visibility("default"))) mmod_status mmod_forward_noall
     a.inj.pt_off = pt_off_d; a.inj.src_scale = src_scale;
     a.inj.tiles_x = tiles_x; a.inj.tiles_y = tiles_y; a.inj.npts = npt;
     a.wavelet = wavelet;
+    a.fs = c.free_surface;
     a.pdl = 0;
     a.nrec = c.nrec; a.rec_off = rec_off;
     a.err = err;

@@ -9,11 +9,16 @@
 namespace mmod {
 namespace {
 
+// u = 0 outside the grid, except above a free surface: the odd image
+// u(i, j, -m) = -u(i, j, m).
 __device__ __forceinline__ float ld0(const float *__restrict__ u, const StepArgs &a, int i, int j,
                                      int k) {
+    const bool image = a.fs && k < 0;
+    if (image) k = -k;
     const bool in = (unsigned)i < (unsigned)a.nx && (unsigned)j < (unsigned)a.ny &&
                     (unsigned)k < (unsigned)a.nz;
-    return in ? __ldg(u + (long long)k * a.plane + (long long)j * a.nxp + i) : 0.0f;
+    const float v = in ? __ldg(u + (long long)k * a.plane + (long long)j * a.nxp + i) : 0.0f;
+    return image ? -v : v;
 }
 
 __global__ void __launch_bounds__(128) step_simple_kernel(const StepArgs a) {
@@ -35,7 +40,8 @@ __global__ void __launch_bounds__(128) step_simple_kernel(const StepArgs a) {
     }
     const float lap = lap_sum(lx, ly, lz);
     const float e = __fadd_rn(__fadd_rn(__ldg(a.ex + i), __ldg(a.ey + j)), __ldg(a.ez + k));
-    a.uout[o] = __fmul_rn(num_damped(two_p, a.uprev[o], __ldg(a.c + o), lap, e), damp_factor(e));
+    const float out = __fmul_rn(num_damped(two_p, a.uprev[o], __ldg(a.c + o), lap, e), damp_factor(e));
+    a.uout[o] = (a.fs && k == 0) ? 0.0f : out;   // p = 0 on a free surface
 }
 
 // Sources, after the step: one thread per injection point (stencil order).

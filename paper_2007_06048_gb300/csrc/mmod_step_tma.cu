@@ -157,13 +157,16 @@ struct Ctx {
     int *abort_flag;
     int x0, y0, z0, T;
     int lane, warp;
+    bool mirror;         // free surface and z0 < 4: the halo planes above k = 0 are odd images
 };
 
 template <class S>
 __device__ __forceinline__ void issue_u(const Ctx &c, const CUtensorMap *map, int seq) {
     const int s = seq % S::NSU;
+    int z = c.z0 - kRadius + seq;
+    if (c.mirror && z < 0) z = -z;   // plane -m is the image of plane m (negated when read)
     mbar_expect_tx(&c.full_u[s], S::CUR * 4);
-    tma_load_3d(c.cur + s * S::CUR, map, c.x0 - kRadius, c.y0 - kRadius, c.z0 - kRadius + seq, &c.full_u[s]);
+    tma_load_3d(c.cur + s * S::CUR, map, c.x0 - kRadius, c.y0 - kRadius, z, &c.full_u[s]);
 }
 
 template <class S>
@@ -267,6 +270,7 @@ __device__ __forceinline__ void step(const StepArgs &a, const Ctx &c, int t, flo
         const float2 e = __fadd2_rn(__fadd2_rn(exr, bcast(eyr[r])), bcast(pi.ez));
         float2 num = __ffma2_rn(cc, lap, __ffma2_rn(e, pp, __fadd2_rn(two_p, neg2(pp))));
         if (damped) num = __fmul2_rn(num, make_float2(damp_factor(e.x), damp_factor(e.y)));
+        if (a.fs && k == 0) num = make_float2(0.0f, 0.0f);   // p = 0 on a free surface
         // 3. store u^{n+1} over u^{n-1} (out_row is null for rows and columns
         // outside the grid; its x+1 twin is stored only inside the grid)
         if (out_row[r]) {
@@ -379,6 +383,7 @@ __device__ __forceinline__ void step_tma_body(const StepArgs &a, const StepVar &
     c.y0 = ty * S::TY;
     c.z0 = chunk * g.zlen;
     c.T = min(a.nz - c.z0, g.zlen);
+    c.mirror = a.fs && c.z0 < kRadius;
     const int T = c.T;
     const int nseq = T + 2 * kRadius;   // u^n planes z0-4 .. z0+T+3
 
@@ -475,6 +480,14 @@ __device__ __forceinline__ void step_tma_body(const StepArgs &a, const StepVar &
                 if constexpr (NA <= 6) read_own<S, 6>(c, 6, q);
                 read_own<S, 7>(c, 7, q);
             }
+        }
+        if (c.mirror && filled) {   // queue planes above k = 0 (z0-4+i < 0) hold the images: negate
+#pragma unroll
+            for (int i = 0; i < kRadius; ++i)
+                if (i < kRadius - c.z0) {
+#pragma unroll
+                    for (int r = 0; r < RY; ++r) q[i][r] = neg2(q[i][r]);
+                }
         }
         PlaneInfo pi = plane_info(a, c.z0);
         // Steps run in blocks of U; step J of a block uses queue window

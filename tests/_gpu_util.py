@@ -41,7 +41,8 @@ def run_gpu(p, kernel=M.KERNEL_AUTO, want_final=True, state=None, want_state=Fal
 
 def run_oracle(orc, p, **kw):
     return orc.forward(p.vel, p.h, p.dt, p.nt, order=p.order, nbl=p.nbl, refl=p.refl,
-                       src_ijk=p.src_ijk, wavelet=p.wavelet, rec_ijk=p.rec_ijk, want_state=True, **kw)
+                       src_ijk=p.src_ijk, wavelet=p.wavelet, rec_ijk=p.rec_ijk, want_state=True,
+                       free_surface=p.free_surface, **kw)
 
 
 def rel_l2(got, ref):

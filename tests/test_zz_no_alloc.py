@@ -30,14 +30,20 @@ def _noalloc(p, torch):
     nz, ny, nx = p.vel.shape
     torch.cuda.synchronize()
     M.mmod_forward_noalloc(nx, ny, nz, p.h, p.dt, p.nt, vel, wav, tr, fin, nbl=p.nbl,
-                           src_ijk=p.src_ijk, rec_ijk=p.rec_ijk, damp_R=p.refl)
+                           src_ijk=p.src_ijk, rec_ijk=p.rec_ijk, damp_R=p.refl, free_surface=p.free_surface)
     return tr.cpu().numpy(), fin.cpu().numpy()
 
 
-@pytest.mark.parametrize("shape,nt,nbl", [((30, 28, 70), 60, 4), ((100, 96, 128), 120, 12)])
-def test_matches_handle_api_on_two_calls(shape, nt, nbl):
+@pytest.mark.parametrize("shape,nt,nbl,fs", [((30, 28, 70), 60, 4, False), ((100, 96, 128), 120, 12, False),
+                                             ((30, 28, 70), 60, 4, True)])
+def test_matches_handle_api_on_two_calls(shape, nt, nbl, fs):
     torch = torch_cuda()
     p = W.tiny_problem(shape=shape, nt=nt, nbl=nbl, nsrc=3, nrec=23, seed=sum(shape))
+    if fs:   # free surface, with a source and a receiver on its plane
+        p.free_surface = True
+        p.src_ijk[0] = [5, 6, 0]
+        p.src_ijk[1:] = [[20, 10, 3], [40, 20, 12]]
+        p.rec_ijk[0] = [7, 8, 0]
     tr_ref, u_ref, _ = run_gpu(p)
     assert np.abs(u_ref).max() > 0
     for _ in range(2):   # the second call reuses the block the first one left behind

@@ -35,6 +35,7 @@ class Problem:
     order: int = 8
     refl: float = 1e-3
     meta: dict = field(default_factory=dict)
+    free_surface: bool = False      # p = 0 on the plane k = 0 (odd image), no top layer
 
     @property
     def shape(self):
