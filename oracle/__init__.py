@@ -64,14 +64,16 @@ class Oracle:
         I, D = ctypes.c_int, ctypes.c_double
         lib.orc_fd_coeffs.argtypes = [I, P]
         lib.orc_damping_profile.argtypes = [I, I, D, D, D, P]
-        lib.orc_laplacian.argtypes = [I, I, I, D, D, D, I, P, P, I]
+        lib.orc_laplacian.argtypes = [I, I, I, D, D, D, I, P, P, I, P]
         lib.orc_forward.argtypes = [I, I, I, D, D, D, D, I, I, I, D, P,
-                                    I, P, P, I, P, P, P, P, P, P, I, I]
+                                    I, P, P, I, P, P, P, P, P, P, I, I, P]
+        lib.orc_optimized_coeffs.argtypes = [I, D, I, P]
         lib.orc_max_threads.argtypes = []
         lib.orc_adjoint.argtypes = [I, I, I, D, D, D, D, I, I, I, D, P, I, P, I, P, P, P, I, I]
         lib.orc_gradient.argtypes = [I, I, I, D, D, D, D, I, I, I, D, P, I, P, P, I, P, P, P, I, I]
         for f in (lib.orc_fd_coeffs, lib.orc_damping_profile, lib.orc_laplacian,
-                  lib.orc_forward, lib.orc_max_threads, lib.orc_adjoint, lib.orc_gradient):
+                  lib.orc_forward, lib.orc_max_threads, lib.orc_adjoint, lib.orc_gradient,
+                  lib.orc_optimized_coeffs):
             f.restype = ctypes.c_int
         self.lib = lib
         self.path = path
@@ -87,6 +89,15 @@ class Oracle:
             raise ValueError(f"orc_fd_coeffs(order={order}) -> {rc}")
         return out
 
+    def optimized_coeffs(self, order: int, kmax: float, nq: int = 4000) -> np.ndarray:
+        """[c0, c1..cR] of reading R16: least-squares weights over kh in [0, kmax]
+        with sum m^2 c_m = 1 (unit spacing)."""
+        out = np.zeros(order // 2 + 1, dtype=np.float64)
+        rc = self.lib.orc_optimized_coeffs(order, float(kmax), int(nq), _ptr(out))
+        if rc != 0:
+            raise ValueError(f"orc_optimized_coeffs -> {rc}")
+        return out
+
     def damping_profile(self, n: int, nbl: int, h: float, vmax: float, refl: float = 1e-3) -> np.ndarray:
         """eta_a(i), i = 0..n-1, of the damping layers (reading R3)."""
         out = np.zeros(n, dtype=np.float64)
@@ -95,14 +106,16 @@ class Oracle:
             raise ValueError(f"orc_damping_profile -> {rc}")
         return out
 
-    def laplacian(self, u: np.ndarray, h, order: int = 8, free_surface: bool = False) -> np.ndarray:
+    def laplacian(self, u: np.ndarray, h, order: int = 8, free_surface: bool = False, coef=None) -> np.ndarray:
         """Sec. 3 Laplacian of u [nz][ny][nx] with u = 0 outside the grid (with
         free_surface, the odd image of reading R15 above k = 0)."""
         u = np.ascontiguousarray(u, dtype=np.float64)
         nz, ny, nx = u.shape
         hx, hy, hz = h
         out = np.empty_like(u)
-        rc = self.lib.orc_laplacian(nx, ny, nz, hx, hy, hz, order, _ptr(u), _ptr(out), int(free_surface))
+        cf = None if coef is None else np.ascontiguousarray(coef, np.float64)
+        rc = self.lib.orc_laplacian(nx, ny, nz, hx, hy, hz, order, _ptr(u), _ptr(out), int(free_surface),
+                                    _ptr(cf))
         if rc != 0:
             raise ValueError(f"orc_laplacian -> {rc}")
         return out
@@ -110,8 +123,9 @@ class Oracle:
     def forward(self, vel: np.ndarray, h, dt: float, nt: int, *, order: int = 8, nbl: int = 0,
                 refl: float = 1e-3, src_ijk=None, wavelet=None, rec_ijk=None,
                 u_prev0=None, u_cur0=None, want_state: bool = False, nthreads: int = 0,
-                free_surface: bool = False):
-        """Alg. 1 / Alg. 2 forward run in FP64 (free_surface: reading R15).
+                free_surface: bool = False, coef=None):
+        """Alg. 1 / Alg. 2 forward run in FP64 (free_surface: reading R15; coef:
+        c_1..c_R of the Laplacian instead of the Taylor weights, reading R16).
 
         vel: [nz][ny][nx] float32 m/s.  src_ijk: [nsrc][3] (i, j, k).  wavelet:
         [nsrc][nt] float32.  rec_ijk: [nrec][3].  Returns traces [nt][nrec]
@@ -134,7 +148,8 @@ class Oracle:
         rc = self.lib.orc_forward(nx, ny, nz, hx, hy, hz, dt, nt, order, nbl, refl, _ptr(vel),
                                   nsrc, _ptr(src) if nsrc else None, _ptr(wav),
                                   nrec, _ptr(rec) if nrec else None, _ptr(traces) if nrec else None,
-                                  _ptr(up0), _ptr(uc0), _ptr(upo), _ptr(uco), nthreads, int(free_surface))
+                                  _ptr(up0), _ptr(uc0), _ptr(upo), _ptr(uco), nthreads, int(free_surface),
+                                  _ptr(None if coef is None else np.ascontiguousarray(coef, np.float64)))
         if rc != 0:
             raise ValueError(f"orc_forward -> {rc}")
         if want_state:
@@ -198,8 +213,12 @@ def damping_profile(n: int, nbl: int, h: float, vmax: float, refl: float = 1e-3)
     return _default().damping_profile(n, nbl, h, vmax, refl)
 
 
-def laplacian(u: np.ndarray, h, order: int = 8, free_surface: bool = False) -> np.ndarray:
-    return _default().laplacian(u, h, order, free_surface)
+def optimized_coeffs(order: int, kmax: float, nq: int = 4000) -> np.ndarray:
+    return _default().optimized_coeffs(order, kmax, nq)
+
+
+def laplacian(u: np.ndarray, h, order: int = 8, free_surface: bool = False, coef=None) -> np.ndarray:
+    return _default().laplacian(u, h, order, free_surface, coef)
 
 
 def forward(vel, h, dt, nt, **kw):

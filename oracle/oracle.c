@@ -31,6 +31,13 @@
  *       add of Alg. 1 is  c(x_s) w[n] / (hx hy hz (1 + eta(x_s) dt)),  i.e.
  *       the source sits inside the damped update's numerator.
  *   R7  receivers record u^{n+1} at grid points after the add of step n.
+ *   R16 optimised stencils (Sec. 3: weights that "reduce the dispersion
+ *       error at the expense of formal order", none given): c_1..c_R minimise
+ *       the squared relative error of the 1-D second-derivative symbol,
+ *          int_0^kmax ( sum_m 2 c_m (1 - cos m k) / k^2 - 1 )^2 dk,
+ *       over the band kh in [0, kmax], subject to sum_m m^2 c_m = 1 (exact
+ *       for quadratics, second order); orc_optimized_coeffs.  Any weight set
+ *       can drive the Laplacian and the stepper (coef argument).
  *   R15 free surface (the paper's option at the surface, Sec. 3): p = 0 on
  *       the plane k = 0, imposed as the odd image  u(i, j, -m) = -u(i, j, m)
  *       for the stencil and u(i, j, 0) = 0 after every step (sources added
@@ -83,6 +90,56 @@ int orc_fd_coeffs(int order, double *c)
     }
     double sum = 0.0;
     for (int m = 1; m <= R; ++m) { c[m] = A[m - 1][R] / A[m - 1][m - 1]; sum += c[m]; }
+    c[0] = -2.0 * sum;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Reading R16: least-squares weights over the band [0, kmax] (radians per  */
+/* cell) with the consistency constraint sum_m m^2 c_m = 1.  The integral   */
+/* is a composite trapezoid rule on nq intervals; a_m(k) = 2(1 - cos mk)/k^2 */
+/* (a_m(0) = m^2).  Stationarity of the Lagrangian gives the symmetric      */
+/* system  [G g; g^T 0] [c; lambda] = [b; 1],  G_mn = int a_m a_n,          */
+/* b_m = int a_m, g_m = m^2, solved by Gaussian elimination with pivots.    */
+/* Output as orc_fd_coeffs: c[0] = -2 sum c_m, c[m] = c_m.                  */
+/* ------------------------------------------------------------------------ */
+int orc_optimized_coeffs(int order, double kmax, int nq, double *c)
+{
+    if (order < 2 || order % 2 != 0 || order / 2 > ORC_MAX_R || !c) return -1;
+    if (!(kmax > 0.0 && kmax <= 3.14159265358979323846) || nq < 2) return -1;
+    const int R = order / 2, n = R + 1;
+    double A[ORC_MAX_R + 1][ORC_MAX_R + 2];
+    for (int r = 0; r < n; ++r)
+        for (int q = 0; q <= n; ++q) A[r][q] = 0.0;
+    for (int q = 0; q <= nq; ++q) {
+        const double k = kmax * q / nq;
+        const double w = (q == 0 || q == nq) ? 0.5 * kmax / nq : kmax / nq;
+        double a[ORC_MAX_R + 1];
+        for (int m = 1; m <= R; ++m)
+            a[m] = (q == 0) ? (double)m * m : 2.0 * (1.0 - cos(m * k)) / (k * k);
+        for (int i = 1; i <= R; ++i) {
+            for (int j = 1; j <= R; ++j) A[i - 1][j - 1] += w * a[i] * a[j];
+            A[i - 1][n] += w * a[i];
+        }
+    }
+    for (int m = 1; m <= R; ++m) { A[m - 1][R] = (double)m * m; A[R][m - 1] = (double)m * m; }
+    A[R][R] = 0.0;
+    A[R][n] = 1.0;
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < n; ++r)
+            if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
+        if (A[piv][col] == 0.0) return -2;
+        if (piv != col)
+            for (int q = 0; q <= n; ++q) { double t = A[col][q]; A[col][q] = A[piv][q]; A[piv][q] = t; }
+        for (int r = 0; r < n; ++r) {
+            if (r == col) continue;
+            const double f = A[r][col] / A[col][col];
+            for (int q = col; q <= n; ++q) A[r][q] -= f * A[col][q];
+        }
+    }
+    double sum = 0.0;
+    for (int m = 1; m <= R; ++m) { c[m] = A[m - 1][n] / A[m - 1][m - 1]; sum += c[m]; }
     c[0] = -2.0 * sum;
     return 0;
 }
@@ -166,11 +223,17 @@ static inline double lap_at(const grid_t *g, const double *u, long o,
     return lx + ly + lz;
 }
 
-static int axis_weights(int order, double hx, double hy, double hz,
+/* coef: NULL for the Taylor weights of the order, else c_1..c_R (unit spacing). */
+static int axis_weights(int order, const double *coef, double hx, double hy, double hz,
                         double *cx, double *cy, double *cz)
 {
     double c[ORC_MAX_R + 1];
     if (orc_fd_coeffs(order, c) != 0) return -1;
+    if (coef) {
+        double sum = 0.0;
+        for (int m = 1; m <= order / 2; ++m) { c[m] = coef[m - 1]; sum += c[m]; }
+        c[0] = -2.0 * sum;
+    }
     for (int m = 0; m <= order / 2; ++m) {
         cx[m] = c[m] / (hx * hx);
         cy[m] = c[m] / (hy * hy);
@@ -181,11 +244,11 @@ static int axis_weights(int order, double hx, double hy, double hz,
 
 /* Sec. 3 Laplacian of a whole field u [nz][ny][nx] into out, u = 0 outside. */
 int orc_laplacian(int nx, int ny, int nz, double hx, double hy, double hz, int order,
-                  const double *u, double *out, int free_surface)
+                  const double *u, double *out, int free_surface, const double *coef)
 {
     if (nx < 1 || ny < 1 || nz < 1 || !u || !out) return -1;
     double cx[ORC_MAX_R + 1], cy[ORC_MAX_R + 1], cz[ORC_MAX_R + 1];
-    if (axis_weights(order, hx, hy, hz, cx, cy, cz) != 0) return -1;
+    if (axis_weights(order, coef, hx, hy, hz, cx, cy, cz) != 0) return -1;
     const grid_t g = make_grid(nx, ny, nz, order / 2);
     double *pu = padded_zeros(&g);
     if (!pu) return -3;
@@ -220,7 +283,8 @@ int orc_forward(int nx, int ny, int nz, double hx, double hy, double hz,
                 int nsrc, const int *src_ijk, const float *wavelet,
                 int nrec, const int *rec_ijk, double *traces,
                 const double *u_prev0, const double *u_cur0,
-                double *u_prev_out, double *u_cur_out, int nthreads, int free_surface)
+                double *u_prev_out, double *u_cur_out, int nthreads, int free_surface,
+                const double *coef)
 {
     if (nx < 1 || ny < 1 || nz < 1 || nt < 0 || dt <= 0 || !vel) return -1;
     if (hx <= 0 || hy <= 0 || hz <= 0) return -1;
@@ -242,7 +306,7 @@ int orc_forward(int nx, int ny, int nz, double hx, double hy, double hz,
     (void)nthreads;
 #endif
     double cx[ORC_MAX_R + 1], cy[ORC_MAX_R + 1], cz[ORC_MAX_R + 1];
-    if (axis_weights(order, hx, hy, hz, cx, cy, cz) != 0) return -1;
+    if (axis_weights(order, coef, hx, hy, hz, cx, cy, cz) != 0) return -1;
     const grid_t g = make_grid(nx, ny, nz, order / 2);
     const long N = (long)nx * ny * nz;
 
@@ -354,7 +418,7 @@ static int adjoint_core(int nx, int ny, int nz, double hx, double hy, double hz,
                         double *const *u_hist, double *grad_c, int free_surface)
 {
     double cx[ORC_MAX_R + 1], cy[ORC_MAX_R + 1], cz[ORC_MAX_R + 1];
-    if (axis_weights(order, hx, hy, hz, cx, cy, cz) != 0) return -1;
+    if (axis_weights(order, NULL, hx, hy, hz, cx, cy, cz) != 0) return -1;
     const grid_t g = make_grid(nx, ny, nz, order / 2);
     const long N = (long)nx * ny * nz;
     double vmax = 0.0;
@@ -510,7 +574,7 @@ int orc_gradient(int nx, int ny, int nz, double hx, double hy, double hz,
         double *up = (double *)malloc(sizeof(double) * (size_t)N), *un = (double *)malloc(sizeof(double) * (size_t)N);
         if (!up || !un) { free(up); free(un); free(wm); rc = -3; goto done; }
         rc = orc_forward(nx, ny, nz, hx, hy, hz, dt, 1, order, nbl, refl, vel, nsrc, src_ijk, wm,
-                         0, NULL, NULL, prev, cur, up, un, nthreads, free_surface);
+                         0, NULL, NULL, prev, cur, up, un, nthreads, free_surface, NULL);
         for (int k = 0; k < nz; ++k)
             for (int j = 0; j < ny; ++j)
                 for (int i = 0; i < nx; ++i)
