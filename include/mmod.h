@@ -176,6 +176,25 @@ enum { MMOD_REV_ADVANCE = 0, MMOD_REV_SAVE = 1, MMOD_REV_RESTORE = 2, MMOD_REV_R
 mmod_status mmod_revolve_schedule(int nsteps, int snaps, int *actions, long long cap, long long *count,
                                   long long *advanced);
 
+/* ---- Stencil weights ----------------------------------------------------
+ * The Laplacian's weights c_1..c_4 (unit spacing; the kernels use
+ * c_m / h_a^2 on axis a).  Default: the order-8 Taylor weights 8/5, -1/5,
+ * 8/315, -1/560 (Sec. 3).  Sec. 3 also allows weights that reduce the
+ * dispersion error at the expense of formal order; the library computes them
+ * as the minimiser of  int_0^kmax (sum_m 2 c_m (1 - cos m k) / k^2 - 1)^2 dk
+ * (relative error of the 1-D symbol over the band kh in [0, kmax], radians
+ * per cell, 0 < kmax <= pi) subject to sum_m m^2 c_m = 1.
+ *
+ * mmod_optimized_coefficients: writes c_1..c_4 into c4 (host).  Errors: ARG.
+ * mmod_set_fd_coefficients: the handle uses c4 (host, 4 doubles; NULL = the
+ *   Taylor weights) from its next run on; c4 must satisfy sum m^2 c_m = 1
+ *   to 1e-6.  The stability bound follows the weights (max over k of
+ *   sum 2 c_m (1 - cos m k), 2048/315 for Taylor); a loaded model that
+ *   violates it is dropped (UNSTABLE).  The allocation-free entry point uses
+ *   the Taylor weights.  Errors: ARG, UNSTABLE. */
+mmod_status mmod_optimized_coefficients(double kmax, double *c4);
+mmod_status mmod_set_fd_coefficients(mmod_handle *h, const double *c4);
+
 /* FP64 sum of a[i] * b[i] over n FP32 device values (dot-product tests,
  * gradient norms).  Synchronises `stream`.  Errors: ARG, OOM, CUDA. */
 mmod_status mmod_dot(const float *a, const float *b, long long n, double *out, mmod_stream stream);

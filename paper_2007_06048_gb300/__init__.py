@@ -45,7 +45,8 @@ EXPORTED = ["mmod_create", "mmod_destroy", "mmod_set_model", "mmod_forward", "mm
             "mmod_gradient_memory", "mmod_dot", "mmod_batch_create", "mmod_batch_destroy",
             "mmod_batch_forward", "mmod_batch_set_variant", "mmod_batch_last_loop_ms", "mmod_batch_last_error",
             "mmod_autotune", "mmod_batch_autotune", "mmod_revolve_schedule", "mmod_persistent_grid",
-            "mmod_tma_variant_info", "mmod_batch_set_mode"]
+            "mmod_tma_variant_info", "mmod_batch_set_mode", "mmod_optimized_coefficients",
+            "mmod_set_fd_coefficients"]
 CKPT_FP32, CKPT_BF16, CKPT_FP16 = 0, 1, 2
 
 
@@ -119,6 +120,8 @@ def load():
         "mmod_persistent_grid": ([P], I),
         "mmod_tma_variant_info": ([I, ctypes.POINTER(I)], I),
         "mmod_batch_set_mode": ([P, I], I),
+        "mmod_optimized_coefficients": ([D, P], I),
+        "mmod_set_fd_coefficients": ([P, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -288,6 +291,15 @@ def mmod_tma_variant_info(v: int) -> dict:
             **{k: dict(zip(keys, out[2 + 4 * i: 6 + 4 * i])) for i, k in enumerate(("step", "batch", "persistent"))}}
 
 
+def mmod_optimized_coefficients(kmax: float) -> np.ndarray:
+    """c_1..c_4 minimising the relative symbol error over kh in [0, kmax]."""
+    out = np.zeros(4, np.float64)
+    st = load().mmod_optimized_coefficients(float(kmax), out.ctypes.data)
+    if st != 0:
+        raise MmodError(st, "mmod_optimized_coefficients: kmax must be in (0, pi]")
+    return out
+
+
 def mmod_dot(a, b, n=None, stream=None) -> float:
     """FP64 dot product of two FP32 device arrays (computed by the library)."""
     out = ctypes.c_double(0.0)
@@ -408,6 +420,13 @@ class Propagator:
 
     def plan(self) -> dict:
         return mmod_get_plan(self.handle)
+
+    def set_fd_coefficients(self, c4=None):
+        """Laplacian weights c_1..c_4 (None: the Taylor weights)."""
+        arr = None if c4 is None else np.ascontiguousarray(c4, np.float64).reshape(4)
+        st = load().mmod_set_fd_coefficients(self.handle, None if arr is None else arr.ctypes.data)
+        if st != 0:
+            raise MmodError(st, load().mmod_last_error(self.handle).decode())
 
     def persistent_grid(self) -> int:
         """CTAs of the persistent kernel the next run launches (0: one launch per step)."""

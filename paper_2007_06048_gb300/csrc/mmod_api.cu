@@ -265,6 +265,11 @@ bool is_device_ptr(const void *p) {
 
 bool use_tma(const mmod_handle *h) { return h->tma_ok && h->kernel != MMOD_KERNEL_SIMPLE; }
 
+void drop_graphs(mmod_handle *h) {
+    free_graph(h->g_fwd);
+    free_graph(h->g_adj);
+}
+
 // CTAs of the persistent kernel for the next run (0: one launch per step).
 int persistent_grid_of(const mmod_handle *h) {
     if (!use_tma(h) || !h->persistent || !h->counters) return 0;
@@ -481,11 +486,7 @@ MMOD_API mmod_status mmod_create(const mmod_config *cfg, int device, mmod_handle
     h->plane = (long long)h->nxp * ny;
     h->vol = h->plane * nz;
     h->npts = (long long)nx * ny * nz;
-    for (int m = 0; m < kRadius; ++m) {
-        h->w.x[m] = (float)(kTaylor8[m] / (cfg->hx * cfg->hx));
-        h->w.y[m] = (float)(kTaylor8[m] / (cfg->hy * cfg->hy));
-        h->w.z[m] = (float)(kTaylor8[m] / (cfg->hz * cfg->hz));
-    }
+    set_weights(h, kTaylor8);
 
     auto bail = [&](cudaError_t e, const char *what) {
         set_thread_error_str(std::string(what) + ": " + cudaGetErrorString(e));
@@ -639,10 +640,10 @@ MMOD_API mmod_status mmod_set_model(mmod_handle *h, const float *vel, mmod_strea
     float vmaxf;
     std::memcpy(&vmaxf, &vbits, sizeof(vmaxf));
     const double vmax = vmaxf;
-    const double ksum = kSymbolMax8 * (1.0 / (c.hx * c.hx) + 1.0 / (c.hy * c.hy) + 1.0 / (c.hz * c.hz));
+    const double ksum = h->symbol_max * (1.0 / (c.hx * c.hx) + 1.0 / (c.hy * c.hy) + 1.0 / (c.hz * c.hz));
     if (c.dt * vmax * std::sqrt(ksum) > 2.0) {
         h->model_set = false;
-        return fail(h, MMOD_ERR_UNSTABLE, "dt too large: dt*vmax*sqrt(sum 6.5016/h^2) = " +
+        return fail(h, MMOD_ERR_UNSTABLE, "dt too large: dt*vmax*sqrt(sum S_max/h^2) = " +
                                               std::to_string(c.dt * vmax * std::sqrt(ksum)) + " > 2");
     }
     MMOD_CK(h, launch_model_fill(dvel, c.nx, c.ny, c.nz, h->nxp, c.dt, h->c, s));

@@ -333,6 +333,7 @@ MMOD_API mmod_status mmod_batch_forward(mmod_batch *b, const float *const *wavel
         if (h->cfg.nrec > 0 && b->nt > 0 && (!t || !is_device_ptr(t)))
             return bfail(b, MMOD_ERR_ARG, "shot " + std::to_string(i) + ": traces must be a device pointer");
         b->desc[i].args.wavelet = w;
+        b->desc[i].args.w = h->w;                // the handle's current stencil weights
         b->desc[i].args.pdl = b->pdl ? 2 : 0;   // the captured steps follow one another
         b->desc[i].args.err = h->err_dev;
         b->desc[i].traces = t;

@@ -57,6 +57,8 @@ struct mmod_handle {
     long long plane = 0, vol = 0;  // padded plane / volume, in floats
     long long npts = 0;            // nx * ny * nz
     mmod::Weights w{};
+    double coef[mmod::kRadius] = {};    // c_1..c_4 of the Laplacian (unit spacing)
+    double symbol_max = 0.0;            // max over k of sum 2 c_m (1 - cos m k): stability bound
 
     float *u[2] = {nullptr, nullptr};   // wavefields (padded)
     float *c = nullptr;                 // dt^2 v^2 (padded)
@@ -133,6 +135,11 @@ bool is_device_ptr(const void *p);
 bool use_tma(const mmod_handle *h);
 int persistent_grid_of(const mmod_handle *h);
 mmod_status enqueue_tune_steps(mmod_handle *h, int steps, cudaStream_t s);   // mmod_batch.cu
+// Stencil weights (mmod_coeffs.cu).
+bool optimized_weights(double kmax, double c[kRadius]);
+double symbol_max(const double c[kRadius]);
+void set_weights(mmod_handle *h, const double c[kRadius]);
+void drop_graphs(mmod_handle *h);   // mmod_api.cu: captured loops must be re-captured
 const TmaPlan &active_plan(const mmod_handle *h);
 StepArgs base_args(mmod_handle *h, const Geometry &geo, const float *wavelet);
 // Enqueues one step (plain path: step, injection, optional gather of
