@@ -179,8 +179,8 @@ mmod_status mmod_revolve_schedule(int nsteps, int snaps, int *actions, long long
 /* ---- Stencil weights ----------------------------------------------------
  * The Laplacian's weights c_1..c_4 (unit spacing; the kernels use
  * c_m / h_a^2 on axis a).  Default: the order-8 Taylor weights 8/5, -1/5,
- * 8/315, -1/560 (Sec. 3).  Sec. 3 also allows weights that reduce the
- * dispersion error at the expense of formal order; the library computes them
+ * 8/315, -1/560 (Sec. 3).  Sec. 3 also allows weights that give up formal
+ * order for a smaller dispersion error; the library computes them
  * as the minimiser of  int_0^kmax (sum_m 2 c_m (1 - cos m k) / k^2 - 1)^2 dk
  * (relative error of the 1-D symbol over the band kh in [0, kmax], radians
  * per cell, 0 < kmax <= pi) subject to sum_m m^2 c_m = 1.

@@ -31,8 +31,8 @@
  *       add of Alg. 1 is  c(x_s) w[n] / (hx hy hz (1 + eta(x_s) dt)),  i.e.
  *       the source sits inside the damped update's numerator.
  *   R7  receivers record u^{n+1} at grid points after the add of step n.
- *   R16 optimised stencils (Sec. 3: weights that "reduce the dispersion
- *       error at the expense of formal order", none given): c_1..c_R minimise
+ *   R16 optimised stencils (Sec. 3 allows weights of lower formal order
+ *       with a smaller dispersion error and gives none): c_1..c_R minimise
  *       the squared relative error of the 1-D second-derivative symbol,
  *          int_0^kmax ( sum_m 2 c_m (1 - cos m k) / k^2 - 1 )^2 dk,
  *       over the band kh in [0, kmax], subject to sum_m m^2 c_m = 1 (exact

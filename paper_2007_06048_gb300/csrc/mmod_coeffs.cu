@@ -1,5 +1,5 @@
 // Stencil weights of the Laplacian (Sec. 3): the order-8 Taylor weights, or
-// weights that reduce the dispersion error "at the expense of formal order".
+// weights that trade formal order for a smaller dispersion error.
 //
 // Optimised weights (host code): c_1..c_4 minimise
 //     J(c) = int_0^kmax ( sum_m c_m a_m(k) - 1 )^2 dk,

@@ -2,8 +2,8 @@
 in the oracle's Laplacian and stepper.
 
 * Consistency: sum_m m^2 c_m = 1, so the stencil is exact on quadratics; it
-  is not exact on quartics (formal order 2, "at the expense of formal
-  order").
+  is not exact on quartics (formal order 2: the accuracy traded for the
+  smaller dispersion error).
 * Optimality: the weights are a constrained minimum of the stated objective,
   evaluated here with an independent quadrature (Simpson on a different
   grid): every feasible direction increases it.
