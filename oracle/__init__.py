@@ -68,12 +68,13 @@ class Oracle:
         lib.orc_forward.argtypes = [I, I, I, D, D, D, D, I, I, I, D, P,
                                     I, P, P, I, P, P, P, P, P, P, I, I, P]
         lib.orc_optimized_coeffs.argtypes = [I, D, I, P]
+        lib.orc_forward_cpml.argtypes = [I, I, I, D, D, D, D, I, I, D, D, P, I, P, P, I, P, P, P, I, I]
         lib.orc_max_threads.argtypes = []
         lib.orc_adjoint.argtypes = [I, I, I, D, D, D, D, I, I, I, D, P, I, P, I, P, P, P, I, I]
         lib.orc_gradient.argtypes = [I, I, I, D, D, D, D, I, I, I, D, P, I, P, P, I, P, P, P, I, I]
         for f in (lib.orc_fd_coeffs, lib.orc_damping_profile, lib.orc_laplacian,
                   lib.orc_forward, lib.orc_max_threads, lib.orc_adjoint, lib.orc_gradient,
-                  lib.orc_optimized_coeffs):
+                  lib.orc_optimized_coeffs, lib.orc_forward_cpml):
             f.restype = ctypes.c_int
         self.lib = lib
         self.path = path
@@ -157,6 +158,28 @@ class Oracle:
         return traces
 
 
+    def forward_cpml(self, vel, h, dt, nt, *, nbl=0, refl=1e-3, f0=0.0, src_ijk=None, wavelet=None,
+                     rec_ijk=None, want_state=False, nthreads=0, free_surface=False):
+        """Reading R17: forward run with CPML layers (order 8).  Returns traces
+        [nt][nrec] and, with want_state, also u^{nt}."""
+        vel = np.ascontiguousarray(vel, dtype=np.float32)
+        nz, ny, nx = vel.shape
+        src = (np.zeros((0, 3), np.int32) if src_ijk is None
+               else np.ascontiguousarray(src_ijk, np.int32).reshape(-1, 3))
+        rec = (np.zeros((0, 3), np.int32) if rec_ijk is None
+               else np.ascontiguousarray(rec_ijk, np.int32).reshape(-1, 3))
+        nsrc, nrec = src.shape[0], rec.shape[0]
+        wav = np.ascontiguousarray(wavelet, np.float32).reshape(nsrc, nt) if nsrc else None
+        traces = np.zeros((nt, nrec), np.float64)
+        uco = np.empty(vel.shape, np.float64) if want_state else None
+        rc = self.lib.orc_forward_cpml(nx, ny, nz, h[0], h[1], h[2], dt, nt, nbl, refl, f0, _ptr(vel),
+                                       nsrc, _ptr(src) if nsrc else None, _ptr(wav),
+                                       nrec, _ptr(rec) if nrec else None, _ptr(traces) if nrec else None,
+                                       _ptr(uco), nthreads, int(free_surface))
+        if rc != 0:
+            raise ValueError(f"orc_forward_cpml -> {rc}")
+        return (traces, uco) if want_state else traces
+
     def adjoint(self, vel, h, dt, nt, *, order=8, nbl=0, refl=1e-3, src_ijk=None, rec_ijk=None,
                 resid=None, nthreads=0, free_surface=False):
         """Transpose of the forward map wavelet -> traces: resid [nt][nrec] ->
@@ -211,6 +234,10 @@ def fd_coeffs(order: int) -> np.ndarray:
 
 def damping_profile(n: int, nbl: int, h: float, vmax: float, refl: float = 1e-3) -> np.ndarray:
     return _default().damping_profile(n, nbl, h, vmax, refl)
+
+
+def forward_cpml(vel, h, dt, nt, **kw):
+    return _default().forward_cpml(vel, h, dt, nt, **kw)
 
 
 def optimized_coeffs(order: int, kmax: float, nq: int = 4000) -> np.ndarray:

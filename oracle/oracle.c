@@ -38,6 +38,22 @@
  *       over the band kh in [0, kmax], subject to sum_m m^2 c_m = 1 (exact
  *       for quadratics, second order); orc_optimized_coeffs.  Any weight set
  *       can drive the Laplacian and the stepper (coef argument).
+ *   R17 CPML (Sec. 3 names a convolutional PML, with no formula): the
+ *       second-order equation with complex-frequency-shifted stretching
+ *       s_a = 1 + d_a / (alpha_a + i w) on each axis,
+ *          u_tt = v^2 sum_a [ D2_a u + D1_a psi_a + zeta_a ] + v^2 f,
+ *          psi_a  = chi_a * D1_a u,   zeta_a = chi_a * (D2_a u + D1_a psi_a),
+ *          chi_a(t) = -d_a exp(-(d_a + alpha_a) t),
+ *       with the recursive convolutions  m^n = b m^{n-1} + g q^n,
+ *       b = exp(-(d + alpha) dt),  g = d (b - 1) / (d + alpha),  D2_a the
+ *       order-8 second difference, D1_a the order-8 centred first difference
+ *       (weights 4/5, -1/5, 4/105, -1/280), psi = 0 outside the grid.  Per
+ *       step: psi^n from u^n, then zeta^n and u^{n+1} = 2u^n - u^{n-1} +
+ *       C (sum_a (D2_a u^n + D1_a psi_a^n + zeta_a^n) + s^n).  Profiles on L
+ *       cells per face: d_a = d0_a (x/L)^2, alpha_a = pi f0 (1 - x/L), x the
+ *       depth into the layer (x = L at the outer cell, 0 from cell L
+ *       inward), d0_a = 3 v_max ln(1/R) / (2 L h_a).  With a free surface the
+ *       top layer is absent (reading R15).  orc_forward_cpml.
  *   R15 free surface (the paper's option at the surface, Sec. 3): p = 0 on
  *       the plane k = 0, imposed as the odd image  u(i, j, -m) = -u(i, j, m)
  *       for the stencil and u(i, j, 0) = 0 after every step (sources added
@@ -382,6 +398,148 @@ int orc_forward(int nx, int ny, int nz, double hx, double hy, double hz,
             }
 done:
     free(ex); free(ey); free(ez); free(C); free(ua); free(ub); free(uc);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Reading R17: CPML forward run.  Memory variables are full padded volumes */
+/* (zero where the profiles vanish).  Arguments as orc_forward; f0 sets the */
+/* frequency shift alpha_max = pi f0 (0: none).                             */
+/* ------------------------------------------------------------------------ */
+static const double orc_d1[5] = {0.0, 4.0 / 5.0, -1.0 / 5.0, 4.0 / 105.0, -1.0 / 280.0};
+static int check_positions(int nx, int ny, int nz, int n, const int *ijk);
+
+/* CPML coefficients b, g of one axis (n cells, L per face; the top face of z
+ * is dropped when top_free). */
+static void cpml_profile(int n, int L, double h, double vmax, double refl, double f0, double dt, int top_free,
+                         double *b, double *g)
+{
+    const double d0 = L > 0 ? 3.0 * vmax * log(1.0 / refl) / (2.0 * L * h) : 0.0;
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < n; ++i) {
+        int x = 0;
+        if (!top_free && L - i > x) x = L - i;
+        if (i - (n - 1 - L) > x) x = i - (n - 1 - L);
+        if (L == 0 || x == 0) { b[i] = 1.0; g[i] = 0.0; continue; }
+        const double s = (double)x / L;
+        const double d = d0 * s * s, alpha = pi * f0 * (1.0 - s);
+        b[i] = exp(-(d + alpha) * dt);
+        g[i] = d * (b[i] - 1.0) / (d + alpha);
+    }
+}
+
+int orc_forward_cpml(int nx, int ny, int nz, double hx, double hy, double hz,
+                     double dt, int nt, int nbl, double refl, double f0,
+                     const float *vel,
+                     int nsrc, const int *src_ijk, const float *wavelet,
+                     int nrec, const int *rec_ijk, double *traces,
+                     double *u_cur_out, int nthreads, int free_surface)
+{
+    const int order = 8, R = 4;
+    if (nx < 1 || ny < 1 || nz < 1 || nt < 0 || dt <= 0 || !vel || f0 < 0) return -1;
+    if (hx <= 0 || hy <= 0 || hz <= 0) return -1;
+    if (2 * nbl > nx || 2 * nbl > ny || 2 * nbl > nz || nbl < 0) return -1;
+    if (nbl > 0 && !(refl > 0.0 && refl < 1.0)) return -1;
+    if (free_surface && nz <= R) return -1;
+    if (nsrc < 0 || nrec < 0 || (nsrc > 0 && (!src_ijk || !wavelet)) || (nrec > 0 && (!rec_ijk || !traces)))
+        return -1;
+    if (check_positions(nx, ny, nz, nsrc, src_ijk) || check_positions(nx, ny, nz, nrec, rec_ijk)) return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    double cx[ORC_MAX_R + 1], cy[ORC_MAX_R + 1], cz[ORC_MAX_R + 1];
+    if (axis_weights(order, NULL, hx, hy, hz, cx, cy, cz) != 0) return -1;
+    const grid_t g = make_grid(nx, ny, nz, R);
+    const long N = (long)nx * ny * nz;
+    double vmax = 0.0;
+    for (long q = 0; q < N; ++q) if ((double)vel[q] > vmax) vmax = (double)vel[q];
+    double *bx = malloc(sizeof(double) * nx), *gx = malloc(sizeof(double) * nx);
+    double *by = malloc(sizeof(double) * ny), *gy = malloc(sizeof(double) * ny);
+    double *bz = malloc(sizeof(double) * nz), *gz = malloc(sizeof(double) * nz);
+    double *C = padded_zeros(&g), *ua = padded_zeros(&g), *ub = padded_zeros(&g), *uc = padded_zeros(&g);
+    double *psi[3], *zeta[3];
+    int rc = 0;
+    for (int a = 0; a < 3; ++a) { psi[a] = padded_zeros(&g); zeta[a] = padded_zeros(&g); }
+    if (!bx || !gx || !by || !gy || !bz || !gz || !C || !ua || !ub || !uc) { rc = -3; goto done; }
+    for (int a = 0; a < 3; ++a) if (!psi[a] || !zeta[a]) { rc = -3; goto done; }
+    cpml_profile(nx, nbl, hx, vmax, refl, f0, dt, 0, bx, gx);
+    cpml_profile(ny, nbl, hy, vmax, refl, f0, dt, 0, by, gy);
+    cpml_profile(nz, nbl, hz, vmax, refl, f0, dt, free_surface, bz, gz);
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const double v = (double)vel[((long)k * ny + j) * nx + i];
+                C[at(&g, i, j, k)] = dt * dt * v * v;
+            }
+    const double cell = hx * hy * hz;
+    const long stride[3] = {1, g.sy, g.sz};
+    const double hh[3] = {hx, hy, hz};
+    const double *cw[3] = {cx, cy, cz};
+    double *up = ua, *ucur = ub, *un = uc;
+    for (int n = 0; n < nt; ++n) {
+        if (free_surface) mirror_top(&g, ucur);
+        /* pass 1: psi_a^n = b psi_a^{n-1} + g D1_a u^n wherever the profile is on */
+        #pragma omp parallel for collapse(2) schedule(static)
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    const long o = at(&g, i, j, k);
+                    const int idx[3] = {i, j, k};
+                    const double *B[3] = {bx, by, bz}, *G[3] = {gx, gy, gz};
+                    for (int a = 0; a < 3; ++a) {
+                        const double gg = G[a][idx[a]];
+                        if (gg == 0.0) continue;
+                        double d1 = 0.0;
+                        for (int m = 1; m <= R; ++m) d1 += orc_d1[m] * (ucur[o + m * stride[a]] - ucur[o - m * stride[a]]);
+                        psi[a][o] = B[a][idx[a]] * psi[a][o] + gg * d1 / hh[a];
+                    }
+                }
+        /* pass 2: zeta_a^n and u^{n+1} */
+        #pragma omp parallel for collapse(2) schedule(static)
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    const long o = at(&g, i, j, k);
+                    const int idx[3] = {i, j, k};
+                    const double *B[3] = {bx, by, bz}, *G[3] = {gx, gy, gz};
+                    double total = 0.0;
+                    for (int a = 0; a < 3; ++a) {
+                        double d2 = 0.0;
+                        for (int m = 1; m <= R; ++m)
+                            d2 += cw[a][m] * (ucur[o + m * stride[a]] + ucur[o - m * stride[a]] - 2.0 * ucur[o]);
+                        const double gg = G[a][idx[a]];
+                        if (gg == 0.0) { total += d2; continue; }
+                        double dpsi = 0.0;
+                        for (int m = 1; m <= R; ++m)
+                            dpsi += orc_d1[m] * (psi[a][o + m * stride[a]] - psi[a][o - m * stride[a]]);
+                        dpsi /= hh[a];
+                        zeta[a][o] = B[a][idx[a]] * zeta[a][o] + gg * (d2 + dpsi);
+                        total += d2 + dpsi + zeta[a][o];
+                    }
+                    un[o] = 2.0 * ucur[o] - up[o] + C[o] * total;
+                }
+        for (int s = 0; s < nsrc; ++s) {
+            const int *p = src_ijk + 3 * s;
+            const long o = at(&g, p[0], p[1], p[2]);
+            un[o] += C[o] * (double)wavelet[(long)s * nt + n] / cell;
+        }
+        if (free_surface) zero_top(&g, un);
+        for (int r = 0; r < nrec; ++r) {
+            const int *p = rec_ijk + 3 * r;
+            traces[n * (long)nrec + r] = un[at(&g, p[0], p[1], p[2])];   /* reading R7 */
+        }
+        double *t = up; up = ucur; ucur = un; un = t;
+    }
+    if (u_cur_out)
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) u_cur_out[((long)k * ny + j) * nx + i] = ucur[at(&g, i, j, k)];
+done:
+    free(bx); free(gx); free(by); free(gy); free(bz); free(gz);
+    free(C); free(ua); free(ub); free(uc);
+    for (int a = 0; a < 3; ++a) { free(psi[a]); free(zeta[a]); }
     return rc;
 }
 

@@ -8,6 +8,7 @@ import pytest
 import oracle
 import test_oracle_adjoint as AD
 import test_oracle_bruteforce as BF
+import test_oracle_cpml as CP
 import test_oracle_dynamics as DY
 import test_oracle_free_surface as FS
 import test_oracle_stencil as ST
@@ -50,6 +51,10 @@ def _fs(orc):
     FS.test_adjoint_dot_product_with_free_surface(orc)
 
 
+def _cpml(orc):
+    CP.test_dense_stepper_agrees(orc, (12, 10, 11), 3, False)
+
+
 def _grad(orc):
     for kind in ("point", "smooth", "source"):
         AD.test_gradient_matches_finite_differences(orc, kind)
@@ -65,7 +70,8 @@ MUTATIONS = [
      "lx += cx[m] * (u[o + m] + u[o - m] - p)", [_poly, _standing]),
     ("Taylor right-hand side wrong", "(p == 1) ? 1.0 : 0.0", "(p == 1) ? 2.0 : 0.0", [_coeffs, _poly]),
     ("source outside the (1 + eta dt) division", "(cell * (1.0 + e))", "cell", [_dense, _reciprocity]),
-    ("source sign flipped", "un[o] += C[o]", "un[o] -= C[o]", [_dense]),
+    ("source sign flipped", "un[o] += C[o] * (double)wavelet[(long)s * nt + n] / (cell * (1.0 + e));",
+     "un[o] -= C[o] * (double)wavelet[(long)s * nt + n] / (cell * (1.0 + e));", [_dense]),
     ("receivers record u^n instead of u^{n+1}", "traces[(long)n * nrec + r] = un[", "traces[(long)n * nrec + r] = ucur[",
      [_dense]),
     ("damping profile shifted by one cell", "if (nbl - i > d) d = nbl - i;", "if (nbl - i - 1 > d) d = nbl - i - 1;",
@@ -87,6 +93,9 @@ MUTATIONS = [
     ("free surface keeps the top damping layer", "for (int k = 0; k < nbl && k < nz - 1 - nbl; ++k) ez[k] = 0.0;\n    for (int k = 0; k < nz; ++k)\n        for (int j = 0; j < ny; ++j)\n            for (int i = 0; i < nx; ++i) {\n                const long q",
      "for (int k = 0; k < 0; ++k) ez[k] = 0.0;\n    for (int k = 0; k < nz; ++k)\n        for (int j = 0; j < ny; ++j)\n            for (int i = 0; i < nx; ++i) {\n                const long q", [_fs]),
     ("adjoint misses the surface projection", "if (free_surface) zero_top(&g, m0);", "", [_fs]),
+    ("CPML memory forgets its decay", "psi[a][o] = B[a][idx[a]] * psi[a][o] + gg * d1 / hh[a];",
+     "psi[a][o] = psi[a][o] + gg * d1 / hh[a];", [_cpml]),
+    ("CPML drops the second memory variable", "total += d2 + dpsi + zeta[a][o];", "total += d2 + dpsi;", [_cpml]),
 ]
 
 
