@@ -299,6 +299,7 @@ def run_mmod(args):
         extra["batched"] = measure_batched(M, dev, stream, fwd_gpts)
         extra["large"] = measure_large(M, dev, stream, peak)
         extra["free_surface"] = measure_free_surface(M, dev, stream, fwd_gpts)
+        extra["cpml"] = measure_cpml(M, dev, stream, fwd_gpts)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -437,6 +438,25 @@ def measure_free_surface(M, dev, stream, fwd_gpts, reps=3):
     return {"value": v, "unit": UNIT, "ms": ms, "vs_forward": v / fwd_gpts, "workload": p.name + " + free surface"}
 
 
+def measure_cpml(M, dev, stream, fwd_gpts, reps=3):
+    """The bench workload with CPML layers (20 cells, 10 Hz shift) instead of
+    damping layers: the memory variables' cost."""
+    import torch
+    import workloads as W
+    p = W.layered_240(1000)
+    p.cpml, p.cpml_f0 = True, 10.0
+    prop = M.Propagator.from_problem(p, device=dev.index or 0)
+    prop.set_model(torch.from_numpy(p.vel).to(dev), stream)
+    wav = torch.from_numpy(np.ascontiguousarray(p.wavelet)).to(dev)
+    tr = torch.empty((p.nt, len(p.rec_ijk)), device=dev)
+    prop.forward(wav, tr, None, stream)
+    ms = time_calls(lambda: prop.forward(wav, tr, None, stream), reps, stream)
+    prop.close()
+    v = p.npoints * p.nt / (ms * 1e-3) / 1e9
+    return {"value": v, "unit": UNIT, "ms": ms, "vs_forward": v / fwd_gpts, "workload": p.name + " + CPML (L=20)",
+            "what": "step kernel + psi and layer-correction kernels per step"}
+
+
 def measure_large(M, dev, stream, peak, reps=2):
     """The 1024 x 1024 x 512 shot (h = 12.5 m, L = 32, 500 steps, 1024^2
     receivers): forward throughput and the step kernel's roofline fraction,
@@ -509,7 +529,7 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=20.0,
                     help="CPU seconds per oracle sample (cpu_baseline / reference arm)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the adjoint / gradient / batched / large-shot / free-surface measurements")
+    ap.add_argument("--no-extra", action="store_true", help="skip the adjoint / gradient / batched / large-shot / free-surface / CPML measurements")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "mmod":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)

@@ -83,7 +83,19 @@ typedef struct {
                                 u(-m) = -u(m), no damping layer under it, sources on
                                 the plane do nothing and receivers there read 0;
                                 needs nz >= 5.  0: damping layers on all six faces. */
+    int boundary;            /* MMOD_BOUNDARY_DAMPING (0): the layers damp (u_tt + 2 eta u_t);
+                                MMOD_BOUNDARY_CPML (1): the nbl-cell layers are a
+                                convolutional PML (the paper's boundary, Sec. 3) with
+                                memory variables psi_a, zeta_a per axis, profiles
+                                d = d0 (x/L)^2, d0 = 3 vmax ln(1/damp_R) / (2 L h),
+                                alpha = pi cpml_f0 (1 - x/L); forward runs only
+                                (adjoint, gradient, fused batches, persistent runs and
+                                the allocation-free path answer UNSUPPORTED). */
+    double cpml_f0;          /* CPML frequency shift, Hz (>= 0; the source's peak
+                                frequency is typical) */
 } mmod_config;
+
+enum { MMOD_BOUNDARY_DAMPING = 0, MMOD_BOUNDARY_CPML = 1 };
 
 /* Create a handle on CUDA device `device`: validates the configuration,
  * copies the source/receiver lists and allocates the wavefields and

@@ -32,6 +32,7 @@ OPT_PERSISTENT = 4
 OPT_PERSISTENT_CTAS = 5
 OPT_TEST_STALL = 6
 OPT_ZLEN = 7
+BOUNDARY_DAMPING, BOUNDARY_CPML = 0, 1
 BATCH_STREAMS, BATCH_FUSED = 0, 1
 SCHEME_SEGMENTS, SCHEME_REVOLVE = 0, 1
 REV_ADVANCE, REV_SAVE, REV_RESTORE, REV_REVERSE = 0, 1, 2, 3
@@ -63,7 +64,7 @@ class _Config(ctypes.Structure):
                 ("nbl", ctypes.c_int), ("damp_R", ctypes.c_double),
                 ("nsrc", ctypes.c_int), ("src_ijk", ctypes.c_void_p),
                 ("nrec", ctypes.c_int), ("rec_ijk", ctypes.c_void_p),
-                ("free_surface", ctypes.c_int)]
+                ("free_surface", ctypes.c_int), ("boundary", ctypes.c_int), ("cpml_f0", ctypes.c_double)]
 
 
 _lib = None
@@ -177,11 +178,11 @@ def mmod_version() -> str:
 
 
 def mmod_create(nx, ny, nz, h, dt, nt, *, nbl=0, src_ijk=None, rec_ijk=None, order=8,
-                damp_R=1e-3, device=0, free_surface=False):
+                damp_R=1e-3, device=0, free_surface=False, cpml=False, cpml_f0=0.0):
     """Create a handle (ctypes void pointer).  src_ijk / rec_ijk: [n][3] int."""
     src = np.ascontiguousarray(np.zeros((0, 3)) if src_ijk is None else src_ijk, np.int32).reshape(-1, 3)
     rec = np.ascontiguousarray(np.zeros((0, 3)) if rec_ijk is None else rec_ijk, np.int32).reshape(-1, 3)
-    cfg = _config(nx, ny, nz, h, dt, nt, nbl, src, rec, order, damp_R, free_surface)
+    cfg = _config(nx, ny, nz, h, dt, nt, nbl, src, rec, order, damp_R, free_surface, cpml, cpml_f0)
     out = ctypes.c_void_p()
     st = load().mmod_create(ctypes.byref(cfg), int(device), ctypes.byref(out))
     if st != 0:
@@ -189,10 +190,11 @@ def mmod_create(nx, ny, nz, h, dt, nt, *, nbl=0, src_ijk=None, rec_ijk=None, ord
     return out
 
 
-def _config(nx, ny, nz, h, dt, nt, nbl, src, rec, order, damp_R, free_surface=False):
+def _config(nx, ny, nz, h, dt, nt, nbl, src, rec, order, damp_R, free_surface=False, cpml=False, cpml_f0=0.0):
     return _Config(int(nx), int(ny), int(nz), float(h[0]), float(h[1]), float(h[2]), float(dt), int(nt),
                    int(order), int(nbl), float(damp_R), len(src), src.ctypes.data if len(src) else None,
-                   len(rec), rec.ctypes.data if len(rec) else None, int(bool(free_surface)))
+                   len(rec), rec.ctypes.data if len(rec) else None, int(bool(free_surface)),
+                   BOUNDARY_CPML if cpml else BOUNDARY_DAMPING, float(cpml_f0))
 
 
 def mmod_forward_noalloc(nx, ny, nz, h, dt, nt, vel, wavelet, traces, final_u=None, *, nbl=0,
@@ -393,7 +395,7 @@ class Propagator:
     """Owning wrapper around one handle for a given problem geometry."""
 
     def __init__(self, shape, h, dt, nt, *, nbl=0, src_ijk=None, rec_ijk=None, damp_R=1e-3,
-                 device=0, order=8, free_surface=False):
+                 device=0, order=8, free_surface=False, cpml=False, cpml_f0=0.0):
         nz, ny, nx = shape
         self.shape = tuple(shape)
         self.nt = int(nt)
@@ -402,12 +404,14 @@ class Propagator:
         self.device = device
         self.free_surface = bool(free_surface)
         self.handle = mmod_create(nx, ny, nz, h, dt, nt, nbl=nbl, src_ijk=src_ijk, rec_ijk=rec_ijk,
-                                  order=order, damp_R=damp_R, device=device, free_surface=free_surface)
+                                  order=order, damp_R=damp_R, device=device, free_surface=free_surface,
+                                  cpml=cpml, cpml_f0=cpml_f0)
 
     @classmethod
     def from_problem(cls, p, device=0):
         return cls(p.vel.shape, p.h, p.dt, p.nt, nbl=p.nbl, src_ijk=p.src_ijk, rec_ijk=p.rec_ijk,
-                   damp_R=p.refl, device=device, order=p.order, free_surface=p.free_surface)
+                   damp_R=p.refl, device=device, order=p.order, free_surface=p.free_surface,
+                   cpml=p.cpml, cpml_f0=p.cpml_f0)
 
     def set_model(self, vel, stream=None):
         mmod_set_model(self.handle, vel, stream)

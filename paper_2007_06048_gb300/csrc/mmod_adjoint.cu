@@ -218,6 +218,7 @@ void free_grad_work(mmod_handle *h) {
 MMOD_API mmod_status mmod_adjoint(mmod_handle *h, const float *resid, float *adj_src, mmod_stream stream) {
     if (!h) return MMOD_ERR_ARG;
     if (mmod_status st = check_latched(h)) return st;
+    if (is_cpml(h)) return fail(h, MMOD_ERR_UNSUPPORTED, "the adjoint is built for the damping layers only");
     if (!h->model_set) return fail(h, MMOD_ERR_STATE, "mmod_set_model has not succeeded");
     const auto &c = h->cfg;
     if (c.nrec > 0 && c.nt > 0 && !resid) return fail(h, MMOD_ERR_ARG, "null residual with nrec > 0");
@@ -261,6 +262,7 @@ MMOD_API mmod_status mmod_gradient(mmod_handle *h, const float *wavelet, const f
                                    int ckpt_count, int ckpt_dtype, mmod_stream stream) {
     if (!h) return MMOD_ERR_ARG;
     if (mmod_status st = check_latched(h)) return st;
+    if (is_cpml(h)) return fail(h, MMOD_ERR_UNSUPPORTED, "the gradient is built for the damping layers only");
     if (!h->model_set) return fail(h, MMOD_ERR_STATE, "mmod_set_model has not succeeded");
     const auto &c = h->cfg;
     if (!grad_v) return fail(h, MMOD_ERR_ARG, "null gradient output");

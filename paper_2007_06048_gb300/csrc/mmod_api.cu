@@ -54,6 +54,9 @@ std::string validate(const mmod_config *c, mmod_status *st) {
     for (int r = 0; r < c->nrec; ++r)
         if (!in_grid(*c, c->rec_ijk + 3 * r)) return "receiver " + std::to_string(r) + " outside the grid";
     if (c->free_surface != 0 && c->free_surface != 1) return "free_surface must be 0 or 1";
+    if (c->boundary != MMOD_BOUNDARY_DAMPING && c->boundary != MMOD_BOUNDARY_CPML) return "unknown boundary";
+    if (c->boundary == MMOD_BOUNDARY_CPML && !(c->cpml_f0 >= 0.0 && std::isfinite(c->cpml_f0)))
+        return "cpml_f0 must be finite and >= 0";
     if (c->free_surface && c->nz < kRadius + 1) return "a free surface needs nz >= 5";
     if (c->order != 8) {
         *st = MMOD_ERR_UNSUPPORTED;
@@ -92,6 +95,8 @@ void free_all(mmod_handle *h) {
         if (g->g_off) cudaFree(g->g_off);
     }
     if (h->counters) cudaFree(h->counters);
+    if (h->cpml_mem) cudaFree(h->cpml_mem);
+    if (h->cpml_bg) cudaFree(h->cpml_bg);
     if (h->vmax_bits) cudaFree(h->vmax_bits);
     if (h->bad) cudaFree(h->bad);
     if (h->ev_t0) cudaEventDestroy(h->ev_t0);
@@ -224,6 +229,47 @@ void damping_profile(int n, int nbl, double h, double vmax, double R, double dt,
     }
 }
 
+// CPML coefficients of one axis: b = exp(-(d + alpha) dt), g = d (b - 1) /
+// (d + alpha) with d = d0 (x/L)^2, alpha = pi f0 (1 - x/L), x the depth into
+// the layer (L at the outer cell, 0 from cell L inward); b = 1, g = 0
+// elsewhere.  top_free drops the layer at index 0 (free surface).
+void cpml_profile(int n, int L, double h, double vmax, double R, double f0, double dt, bool top_free, float *b,
+                  float *g) {
+    const double d0 = L > 0 ? 3.0 * vmax * std::log(1.0 / R) / (2.0 * L * h) : 0.0;
+    for (int i = 0; i < n; ++i) {
+        const int x = std::max({top_free ? 0 : L - i, i - (n - 1 - L), 0});
+        if (L == 0 || x == 0) {
+            b[i] = 1.0f;
+            g[i] = 0.0f;
+            continue;
+        }
+        const double sx = (double)x / L, d = d0 * sx * sx, alpha = M_PI * f0 * (1.0 - sx);
+        const double bb = std::exp(-(d + alpha) * dt);
+        b[i] = (float)bb;
+        g[i] = (float)(d * (bb - 1.0) / (d + alpha));
+    }
+}
+
+CpmlArgs cpml_args(const mmod_handle *h) {
+    const auto &c = h->cfg;
+    CpmlArgs p{};
+    p.nx = c.nx; p.ny = c.ny; p.nz = c.nz; p.nxp = h->nxp; p.plane = h->plane; p.fs = c.free_surface;
+    const size_t n3 = (size_t)(c.nx + c.ny + c.nz);
+    const int off[3] = {0, c.nx, c.nx + c.ny};
+    for (int a = 0; a < 3; ++a) {
+        p.psi[a] = h->cpml_mem + (size_t)a * h->vol;
+        p.zeta[a] = h->cpml_mem + (size_t)(3 + a) * h->vol;
+        p.b[a] = h->cpml_bg + off[a];
+        p.g[a] = h->cpml_bg + n3 + off[a];
+    }
+    p.inv_h[0] = (float)(1.0 / c.hx); p.inv_h[1] = (float)(1.0 / c.hy); p.inv_h[2] = (float)(1.0 / c.hz);
+    for (int m = 0; m < kRadius; ++m) {
+        p.w[0][m] = h->w.x[m]; p.w[1][m] = h->w.y[m]; p.w[2][m] = h->w.z[m];
+    }
+    p.c = h->c;
+    return p;
+}
+
 void clear_surface_layer(int nz, int nbl, float *ez) {
     for (int k = 0; k < nbl && k < nz - 1 - nbl; ++k) ez[k] = 0.0f;
 }
@@ -272,7 +318,7 @@ void drop_graphs(mmod_handle *h) {
 
 // CTAs of the persistent kernel for the next run (0: one launch per step).
 int persistent_grid_of(const mmod_handle *h) {
-    if (!use_tma(h) || !h->persistent || !h->counters) return 0;
+    if (!use_tma(h) || !h->persistent || !h->counters || is_cpml(h)) return 0;
     const TmaPlan &plan = active_plan(h);
     const Geom g = persistent_geom(plan, h->cfg.nz);
     if ((long long)g.tiles_x * g.tiles_y * g.zchunks > h->ncounters) return 0;
@@ -346,6 +392,33 @@ static mmod_status enqueue_loop(mmod_handle *h, const Geometry &geo, const float
     *count = 0;
     MMOD_CK(h, cudaEventRecordWithFlags(h->ev_t0, s, cudaEventRecordExternal));
     StepArgs a = base_args(h, geo, wav);
+    if (is_cpml(h)) {
+        // CPML: psi from u^n, the undamped step (sources included), the layer
+        // correction of u^{n+1}, then (plain kernel) the receivers of u^{n+1}
+        const CpmlArgs cp = cpml_args(h);
+        a.pdl = 0;
+        for (int n = 0; n < nt; ++n) {
+            a.n = n;
+            a.ucur = h->u[(n + 1) & 1];
+            a.uprev = h->u[n & 1];
+            a.uout = h->u[n & 1];
+            a.traces = (n >= 1 && tr && ng > 0) ? tr + (long long)(n - 1) * ng : nullptr;
+            MMOD_CK(h, launch_cpml_psi(cp, a.ucur, s));
+            MMOD_CK(h, enqueue_step(h, a, &h->cur_map[(n + 1) & 1], &h->prev_map[n & 1], tma, nullptr, s, count));
+            MMOD_CK(h, launch_cpml_correct(cp, a.ucur, a.uout, s));
+            *count += 2;
+            if (!tma && tr && ng > 0) {
+                MMOD_CK(h, launch_gather(a.uout, geo.gather_off, ng, tr + (long long)n * ng, s));
+                ++*count;
+            }
+        }
+        if (tma && nt > 0 && ng > 0 && tr) {
+            MMOD_CK(h, launch_gather(h->u[(nt - 1) & 1], geo.gather_off, ng, tr + (long long)(nt - 1) * ng, s));
+            ++*count;
+        }
+        MMOD_CK(h, cudaEventRecordWithFlags(h->ev_t1, s, cudaEventRecordExternal));
+        return MMOD_OK;
+    }
     // inside the loop every step kernel follows the previous step (the
     // first follows no kernel of the captured graph)
     if (a.pdl) a.pdl = 2;
@@ -509,6 +582,12 @@ MMOD_API mmod_status mmod_create(const mmod_config *cfg, int device, mmod_handle
     CKC(cudaMemset(h->u[1], 0, vbytes));
     CKC(cudaMemset(h->c, 0, vbytes));
     CKC(cudaMemset(h->eta, 0, sizeof(float) * (size_t)(nx + ny + nz)));
+    if (is_cpml(h)) {
+        CKC(cudaMalloc(&h->cpml_mem, 6 * vbytes));
+        CKC(cudaMemset(h->cpml_mem, 0, 6 * vbytes));
+        CKC(cudaMalloc(&h->cpml_bg, sizeof(float) * 2 * (size_t)(nx + ny + nz)));
+        CKC(cudaMemset(h->cpml_bg, 0, sizeof(float) * 2 * (size_t)(nx + ny + nz)));
+    }
     CKC(cudaMalloc(&h->vmax_bits, sizeof(unsigned int)));
     CKC(cudaMalloc(&h->bad, sizeof(unsigned long long)));
     // forward: sources injected, receivers gathered; adjoint: the reverse
@@ -657,6 +736,20 @@ MMOD_API mmod_status mmod_set_model(mmod_handle *h, const float *vel, mmod_strea
     damping_profile(c.ny, c.nbl, c.hy, vmax, c.damp_R, c.dt, eta.data() + c.nx);
     damping_profile(c.nz, c.nbl, c.hz, vmax, c.damp_R, c.dt, eta.data() + c.nx + c.ny);
     if (c.free_surface) clear_surface_layer(c.nz, c.nbl, eta.data() + c.nx + c.ny);
+    std::vector<float> bg;
+    if (is_cpml(h)) {   // the layers are a CPML: no damping term, per-cell b, g per axis
+        std::fill(eta.begin(), eta.end(), 0.0f);
+        bg.assign(2 * (size_t)(c.nx + c.ny + c.nz), 0.0f);
+        const int n3[3] = {c.nx, c.ny, c.nz};
+        const double h3[3] = {c.hx, c.hy, c.hz};
+        size_t off = 0;
+        for (int a = 0; a < 3; ++a) {
+            cpml_profile(n3[a], c.nbl, h3[a], vmax, c.damp_R, c.cpml_f0, c.dt, a == 2 && c.free_surface,
+                         bg.data() + off, bg.data() + (size_t)(c.nx + c.ny + c.nz) + off);
+            off += n3[a];
+        }
+        MMOD_CK(h, cudaMemcpyAsync(h->cpml_bg, bg.data(), sizeof(float) * bg.size(), cudaMemcpyHostToDevice, s));
+    }
     MMOD_CK(h, cudaMemcpyAsync(h->eta, eta.data(), sizeof(float) * eta.size(), cudaMemcpyHostToDevice, s));
     MMOD_CK(h, cudaStreamSynchronize(s));   // eta lives on the host stack
     h->vmax = vmax;
@@ -741,6 +834,7 @@ MMOD_API mmod_status mmod_forward(mmod_handle *h, const float *wavelet, float *t
         MMOD_CK(h, cudaMemsetAsync(h->u[0], 0, sizeof(float) * (size_t)h->vol, s));
         MMOD_CK(h, cudaMemsetAsync(h->u[1], 0, sizeof(float) * (size_t)h->vol, s));
     }
+    if (is_cpml(h)) MMOD_CK(h, cudaMemsetAsync(h->cpml_mem, 0, 6 * sizeof(float) * (size_t)h->vol, s));
     h->state_pending = false;
     if (c.nt > 0)
         if (mmod_status st = run_loop_graph(h, h->g_fwd, h->fwd, dwav, c.nrec > 0 ? dtr : nullptr, s, &launches))

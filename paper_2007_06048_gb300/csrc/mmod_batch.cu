@@ -338,6 +338,9 @@ MMOD_API mmod_status mmod_batch_forward(mmod_batch *b, const float *const *wavel
         b->desc[i].args.err = h->err_dev;
         b->desc[i].traces = t;
     }
+    for (int i = 0; i < ns; ++i)
+        if (is_cpml(b->shots[i]))
+            return bfail(b, MMOD_ERR_UNSUPPORTED, "the fused batch kernel has no CPML; use MMOD_BATCH_STREAMS");
     BCK(b, cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(ShotDesc) * ns, cudaMemcpyHostToDevice, s));
     if (mmod_status st = zero_states(b, s)) return st;
     if (b->nt > 0) {

@@ -88,6 +88,8 @@ struct mmod_handle {
     int persistent_ctas = 0;            // MMOD_OPT_PERSISTENT_CTAS (0: as many as fit)
     int test_stall = 0;                 // MMOD_OPT_TEST_STALL (one run)
     int zlen_override = 0;              // MMOD_OPT_ZLEN (0: the plan's z ranges)
+    float *cpml_mem = nullptr;          // CPML: psi_x, psi_y, psi_z, zeta_x, zeta_y, zeta_z volumes
+    float *cpml_bg = nullptr;           // CPML: b_x | b_y | b_z | g_x | g_y | g_z per cell
     mutable mmod::TmaPlan plan_tmp;     // active_plan() with the override applied
     int *counters = nullptr;            // per work unit of the persistent kernel
     long long ncounters = 0;
@@ -140,6 +142,8 @@ bool optimized_weights(double kmax, double c[kRadius]);
 double symbol_max(const double c[kRadius]);
 void set_weights(mmod_handle *h, const double c[kRadius]);
 void drop_graphs(mmod_handle *h);   // mmod_api.cu: captured loops must be re-captured
+inline bool is_cpml(const mmod_handle *h) { return h->cfg.boundary == MMOD_BOUNDARY_CPML; }
+CpmlArgs cpml_args(const mmod_handle *h);
 const TmaPlan &active_plan(const mmod_handle *h);
 StepArgs base_args(mmod_handle *h, const Geometry &geo, const float *wavelet);
 // Enqueues one step (plain path: step, injection, optional gather of

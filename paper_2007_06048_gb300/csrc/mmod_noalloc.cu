@@ -134,6 +134,8 @@ extern "C" __attribute__((visibility("default"))) mmod_status mmod_forward_noall
         return fail(MMOD_ERR_ARG, "damping width must satisfy 0 <= 2*nbl <= n on every axis");
     if (c.nbl > 0 && !(c.damp_R > 0 && c.damp_R < 1)) return fail(MMOD_ERR_ARG, "damp_R must be in (0, 1)");
     if (c.free_surface != 0 && c.free_surface != 1) return fail(MMOD_ERR_ARG, "free_surface must be 0 or 1");
+    if (c.boundary != MMOD_BOUNDARY_DAMPING)
+        return fail(MMOD_ERR_UNSUPPORTED, "the allocation-free forward has damping layers only");
     if (c.free_surface && c.nz < kRadius + 1) return fail(MMOD_ERR_ARG, "a free surface needs nz >= 5");
     const int nxp = (c.nx + 31) / 32 * 32;
     const long long plane = (long long)nxp * c.ny, vol = plane * c.nz;

@@ -40,6 +40,11 @@ def run_gpu(p, kernel=M.KERNEL_AUTO, want_final=True, state=None, want_state=Fal
 
 
 def run_oracle(orc, p, **kw):
+    if p.cpml:   # returns (traces, None, u^{nt}) like the damped forward
+        tr, u = orc.forward_cpml(p.vel, p.h, p.dt, p.nt, nbl=p.nbl, refl=p.refl, f0=p.cpml_f0,
+                                 src_ijk=p.src_ijk, wavelet=p.wavelet, rec_ijk=p.rec_ijk, want_state=True,
+                                 free_surface=p.free_surface)
+        return tr, None, u
     return orc.forward(p.vel, p.h, p.dt, p.nt, order=p.order, nbl=p.nbl, refl=p.refl,
                        src_ijk=p.src_ijk, wavelet=p.wavelet, rec_ijk=p.rec_ijk, want_state=True,
                        free_surface=p.free_surface, **kw)

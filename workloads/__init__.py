@@ -36,6 +36,8 @@ class Problem:
     refl: float = 1e-3
     meta: dict = field(default_factory=dict)
     free_surface: bool = False      # p = 0 on the plane k = 0 (odd image), no top layer
+    cpml: bool = False              # the nbl-cell layers are a CPML instead of damping layers
+    cpml_f0: float = 0.0            # CPML frequency shift (Hz)
 
     @property
     def shape(self):
