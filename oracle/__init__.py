@@ -16,7 +16,10 @@ closed form and the moment identities; Laplacian exact on polynomials of degree
 <= 9; the exact discrete standing wave (dispersion relation); discrete energy
 conservation (damping off) and decay (damping on); the 3-D homogeneous Green's
 function; a dense-matrix stepper on tiny grids; linearity, reciprocity and axis
-permutation; for the adjoint the dot-product test <F w, r> = <w, F^T r> and a
+permutation; for the variable-density staggered system (reading R18) the
+staggered weights' closed form, exact staggered differences of polynomials,
+the exact discrete standing wave, discrete energy identities, a dense stepper,
+the Green's function and the reflection of a density contrast; for the adjoint the dot-product test <F w, r> = <w, F^T r> and a
 dense transpose, for the gradient central finite differences of the misfit.
 """
 from __future__ import annotations
@@ -69,12 +72,15 @@ class Oracle:
                                     I, P, P, I, P, P, P, P, P, P, I, I, P]
         lib.orc_optimized_coeffs.argtypes = [I, D, I, P]
         lib.orc_forward_cpml.argtypes = [I, I, I, D, D, D, D, I, I, D, D, P, I, P, P, I, P, P, P, I, I]
+        lib.orc_staggered_coeffs.argtypes = [I, P]
+        lib.orc_forward_vd.argtypes = [I, I, I, D, D, D, D, I, I, D, I, D, P, P, I, P, P, I, P, P, P, P, I]
         lib.orc_max_threads.argtypes = []
         lib.orc_adjoint.argtypes = [I, I, I, D, D, D, D, I, I, I, D, P, I, P, I, P, P, P, I, I]
         lib.orc_gradient.argtypes = [I, I, I, D, D, D, D, I, I, I, D, P, I, P, P, I, P, P, P, I, I]
         for f in (lib.orc_fd_coeffs, lib.orc_damping_profile, lib.orc_laplacian,
                   lib.orc_forward, lib.orc_max_threads, lib.orc_adjoint, lib.orc_gradient,
-                  lib.orc_optimized_coeffs, lib.orc_forward_cpml):
+                  lib.orc_optimized_coeffs, lib.orc_forward_cpml, lib.orc_staggered_coeffs,
+                  lib.orc_forward_vd):
             f.restype = ctypes.c_int
         self.lib = lib
         self.path = path
@@ -180,6 +186,45 @@ class Oracle:
             raise ValueError(f"orc_forward_cpml -> {rc}")
         return (traces, uco) if want_state else traces
 
+    def staggered_coeffs(self, order: int) -> np.ndarray:
+        """[0, a_1..a_R]: staggered first-derivative weights (reading R18, unit spacing)."""
+        out = np.zeros(order // 2 + 1, dtype=np.float64)
+        rc = self.lib.orc_staggered_coeffs(order, _ptr(out))
+        if rc != 0:
+            raise ValueError(f"orc_staggered_coeffs(order={order}) -> {rc}")
+        return out
+
+    def forward_vd(self, vel, rho, h, dt, nt, *, nbl=0, refl=1e-3, cpml=False, f0=0.0, src_ijk=None,
+                   wavelet=None, rec_ijk=None, state0=None, want_state=False, nthreads=0):
+        """Reading R18: variable-density first-order system on the staggered
+        grid (order 8), damping layers or (cpml) CPML layers.
+
+        vel, rho: [nz][ny][nx] float32.  state0: optional [4][nz][ny][nx]
+        (p^0, vx, vy, vz at -1/2).  Returns traces [nt][nrec] (p^{n+1} at the
+        receivers) and, with want_state, the final [4][nz][ny][nx] state
+        (p^{nt}, velocities at nt - 1/2).
+        """
+        vel = np.ascontiguousarray(vel, dtype=np.float32)
+        rho = np.ascontiguousarray(rho, dtype=np.float32)
+        assert rho.shape == vel.shape
+        nz, ny, nx = vel.shape
+        src = (np.zeros((0, 3), np.int32) if src_ijk is None
+               else np.ascontiguousarray(src_ijk, np.int32).reshape(-1, 3))
+        rec = (np.zeros((0, 3), np.int32) if rec_ijk is None
+               else np.ascontiguousarray(rec_ijk, np.int32).reshape(-1, 3))
+        nsrc, nrec = src.shape[0], rec.shape[0]
+        wav = np.ascontiguousarray(wavelet, np.float32).reshape(nsrc, nt) if nsrc else None
+        traces = np.zeros((nt, nrec), np.float64)
+        s0 = None if state0 is None else np.ascontiguousarray(state0, np.float64).reshape(4, nz, ny, nx)
+        so = np.empty((4, nz, ny, nx), np.float64) if want_state else None
+        rc = self.lib.orc_forward_vd(nx, ny, nz, h[0], h[1], h[2], dt, nt, nbl, refl, int(bool(cpml)), f0,
+                                     _ptr(vel), _ptr(rho), nsrc, _ptr(src) if nsrc else None, _ptr(wav),
+                                     nrec, _ptr(rec) if nrec else None, _ptr(traces) if nrec else None,
+                                     _ptr(s0), _ptr(so), nthreads)
+        if rc != 0:
+            raise ValueError(f"orc_forward_vd -> {rc}")
+        return (traces, so) if want_state else traces
+
     def adjoint(self, vel, h, dt, nt, *, order=8, nbl=0, refl=1e-3, src_ijk=None, rec_ijk=None,
                 resid=None, nthreads=0, free_surface=False):
         """Transpose of the forward map wavelet -> traces: resid [nt][nrec] ->
@@ -238,6 +283,17 @@ def damping_profile(n: int, nbl: int, h: float, vmax: float, refl: float = 1e-3)
 
 def forward_cpml(vel, h, dt, nt, **kw):
     return _default().forward_cpml(vel, h, dt, nt, **kw)
+
+
+def staggered_coeffs(order: int) -> np.ndarray:
+    return _default().staggered_coeffs(order)
+
+
+def forward_vd(vel, rho, h, dt, nt, **kw):
+    return _default().forward_vd(vel, rho, h, dt, nt, **kw)
+
+
+forward_vd.__doc__ = Oracle.forward_vd.__doc__
 
 
 def optimized_coeffs(order: int, kmax: float, nq: int = 4000) -> np.ndarray:

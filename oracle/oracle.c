@@ -60,6 +60,12 @@
  *       there vanish, receivers there read 0); the top damping layer is
  *       removed (eta_z = 0 for k < L), the other five faces keep theirs.
  *
+ *   R18 the variable-density first-order system of Sec. 3 (the paper's
+ *       "acoustic_iso" on a staggered Yee grid): p at the grid points, the
+ *       particle-velocity components half a cell along their axes, leapfrog
+ *       with the velocities at half steps, order-8 staggered weights, damping
+ *       or CPML layers; stated in full before orc_forward_vd.
+ *
  * Index convention: i along x (fastest), j along y, k along z (depth, k = 0 at
  * the surface); user arrays are [nz][ny][nx].
  */
@@ -747,5 +753,266 @@ int orc_gradient(int nx, int ny, int nz, double hx, double hy, double hz,
 done:
     if (hist) for (int m = 0; m < nt + 2; ++m) free(hist[m]);
     free(hist); free(dense); free(prev); free(gc);
+    return rc;
+}
+
+/* ======================================================================== */
+/* Reading R18: the first-order variable-density system of Sec. 3 on a      */
+/* staggered (Yee) grid.                                                    */
+/*                                                                          */
+/*   (1/(rho v^2)) p_t - div vel = f,     rho vel_t - grad p = 0            */
+/*                                                                          */
+/* i.e.  p_t = K (div vel + f),  vel_t = b grad p,  K = rho v^2, b = 1/rho. */
+/* p, K, rho live at the grid points (i, j, k); the component along axis a  */
+/* lives half a cell further along a (vx[k][j][i] at x = (i + 1/2) hx).     */
+/* Leapfrog in time: vel at half steps n - 1/2, p at whole steps n.         */
+/*   D+_a p (i + 1/2) = sum_m a_m [p(i + m) - p(i - m + 1)] / h_a           */
+/*   D-_a q (i)       = sum_m a_m [q(i + m - 1) - q(i - m)] / h_a           */
+/* with the staggered weights a_m below and p = vel = 0 outside the grid    */
+/* (reading R2), so that D-_a = -(D+_a)^T.  Buoyancy at a half point is the */
+/* mean of b at its two grid points (b at the grid point itself past the    */
+/* last one).  The source f = delta(x - x_s) w(t): sample w[n] drives the   */
+/* step from p^n to p^{n+1}; receivers record p^{n+1} (reading R7).         */
+/*                                                                          */
+/* Boundary layers (the grid includes them, reading R4):                    */
+/*   damping: p and each component relax at eta = eta_x + eta_y + eta_z    */
+/*     taken at their own (possibly half-cell) positions, centred in time:  */
+/*       vel_a^{n+1/2} = [(1 - e/2) vel_a^{n-1/2} + dt b_a D+_a p^n]/(1+e/2) */
+/*       p^{n+1} = [(1 - e/2) p^n + dt K (sum_a D-_a vel_a^{n+1/2} + s^n)]  */
+/*                 / (1 + e/2),     e = dt eta,  s^n = w[n] / (hx hy hz)    */
+/*     with the profile of reading R3 at the continuous depth x into the    */
+/*     layer (x <= L): eta = eta_max (x/L)^2.                               */
+/*   CPML: each derivative gains a memory variable on its axis's layers,    */
+/*       psi_a^n = B psi_a^{n-1} + G D+_a p^n      (at vel_a's points)      */
+/*       vel_a^{n+1/2} = vel_a^{n-1/2} + dt b_a (D+_a p^n + psi_a^n)        */
+/*       phi_a^{n+1/2} = B phi_a^{n-1/2} + G D-_a vel_a^{n+1/2} (at p's)    */
+/*       p^{n+1} = p^n + dt K (sum_a (D-_a vel_a + phi_a) + s^n)            */
+/*     B = exp(-(d + alpha) dt), G = d (B - 1)/(d + alpha), with d, alpha   */
+/*     of reading R17 at the continuous depth x into the layer.             */
+/* ======================================================================== */
+
+/* Staggered first-derivative weights of order 2R:
+ *   sum_m a_m [f(x + (m - 1/2) h) - f(x - (m - 1/2) h)] = h f'(x) + O(h^{2R+1})
+ * exactly when  sum_m 2 (m - 1/2) a_m = 1  and  sum_m (m - 1/2)^{2q+1} a_m = 0,
+ * q = 1..R-1 (Taylor expansion of the odd part).  Output a[0] = 0, a[m]. */
+int orc_staggered_coeffs(int order, double *a)
+{
+    if (order < 2 || order % 2 != 0 || order / 2 > ORC_MAX_R || !a) return -1;
+    const int R = order / 2;
+    double A[ORC_MAX_R][ORC_MAX_R + 1];
+    for (int q = 0; q < R; ++q) {
+        for (int m = 1; m <= R; ++m) A[q][m - 1] = pow(m - 0.5, 2.0 * q + 1.0);
+        A[q][R] = (q == 0) ? 0.5 : 0.0;
+    }
+    for (int col = 0; col < R; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < R; ++r)
+            if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
+        if (A[piv][col] == 0.0) return -2;
+        if (piv != col)
+            for (int q = 0; q <= R; ++q) { double t = A[col][q]; A[col][q] = A[piv][q]; A[piv][q] = t; }
+        for (int r = 0; r < R; ++r) {
+            if (r == col) continue;
+            const double f = A[r][col] / A[col][col];
+            for (int q = col; q <= R; ++q) A[r][q] -= f * A[col][q];
+        }
+    }
+    a[0] = 0.0;
+    for (int m = 1; m <= R; ++m) a[m] = A[m - 1][R] / A[m - 1][m - 1];
+    return 0;
+}
+
+/* Depth into the layers (cells) of the continuous position x on an axis of
+ * n points with L-cell layers, capped at L. */
+static double layer_depth(double x, int n, int L)
+{
+    double d = 0.0;
+    if (L - x > d) d = L - x;
+    if (x - (n - 1 - L) > d) d = x - (n - 1 - L);
+    return d > L ? (double)L : d;
+}
+
+/* Profiles of one axis at the grid points (half = 0) or the half points
+ * i + 1/2 (half = 1): damping eta, or the CPML pair B, G. */
+static void vd_profile(int n, int L, double h, double vmax, double refl, double f0, double dt, int half,
+                       double *eta, double *B, double *G)
+{
+    const double d0 = L > 0 ? 3.0 * vmax * log(1.0 / refl) / (2.0 * L * h) : 0.0;
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < n; ++i) {
+        const double x = L > 0 ? layer_depth(i + 0.5 * half, n, L) : 0.0;
+        const double s = L > 0 ? x / L : 0.0;
+        const double d = d0 * s * s;
+        eta[i] = d;
+        if (x == 0.0) { B[i] = 1.0; G[i] = 0.0; continue; }
+        const double alpha = pi * f0 * (1.0 - s);
+        B[i] = exp(-(d + alpha) * dt);
+        G[i] = d * (B[i] - 1.0) / (d + alpha);
+    }
+}
+
+/* Forward run of reading R18 (order 8).
+ * vel, rho   [nz][ny][nx] FP32 (m/s, kg/m^3)
+ * cpml       0: damping layers, 1: CPML with frequency shift alpha_max = pi f0
+ * state0     optional [4][nz][ny][nx] initial p^0, vx, vy, vz at -1/2 (NULL = 0)
+ * state_out  optional final p^{nt}, vx, vy, vz at nt - 1/2
+ * traces     [nt][nrec] FP64: p^{n+1} at the receivers. */
+int orc_forward_vd(int nx, int ny, int nz, double hx, double hy, double hz,
+                   double dt, int nt, int nbl, double refl, int cpml, double f0,
+                   const float *vel, const float *rho,
+                   int nsrc, const int *src_ijk, const float *wavelet,
+                   int nrec, const int *rec_ijk, double *traces,
+                   const double *state0, double *state_out, int nthreads)
+{
+    const int R = 4;
+    if (nx < 1 || ny < 1 || nz < 1 || nt < 0 || dt <= 0 || !vel || !rho || f0 < 0) return -1;
+    if (hx <= 0 || hy <= 0 || hz <= 0 || (cpml != 0 && cpml != 1)) return -1;
+    if (2 * nbl > nx || 2 * nbl > ny || 2 * nbl > nz || nbl < 0) return -1;
+    if (nbl > 0 && !(refl > 0.0 && refl < 1.0)) return -1;
+    if (nsrc < 0 || nrec < 0 || (nsrc > 0 && (!src_ijk || !wavelet)) || (nrec > 0 && (!rec_ijk || !traces)))
+        return -1;
+    if (check_positions(nx, ny, nz, nsrc, src_ijk) || check_positions(nx, ny, nz, nrec, rec_ijk)) return -1;
+    const long N = (long)nx * ny * nz;
+    for (long q = 0; q < N; ++q) if (!(rho[q] > 0.0f) || !(vel[q] > 0.0f)) return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    double aw[ORC_MAX_R + 1];
+    if (orc_staggered_coeffs(2 * R, aw) != 0) return -1;
+    const grid_t g = make_grid(nx, ny, nz, R);
+    const int n3[3] = {nx, ny, nz};
+    const double hh[3] = {hx, hy, hz};
+    const long stride[3] = {1, g.sy, g.sz};
+    double vmax = 0.0;
+    for (long q = 0; q < N; ++q) if ((double)vel[q] > vmax) vmax = (double)vel[q];
+
+    int rc = 0;
+    double *prof[3][2][3];   /* [axis][half][eta, B, G] */
+    for (int a = 0; a < 3; ++a)
+        for (int s = 0; s < 2; ++s)
+            for (int t = 0; t < 3; ++t) prof[a][s][t] = (double *)malloc(sizeof(double) * n3[a]);
+    double *K = padded_zeros(&g), *Bc = padded_zeros(&g), *p = padded_zeros(&g);
+    double *v[3], *bh[3], *psi[3], *phi[3];
+    for (int a = 0; a < 3; ++a) {
+        v[a] = padded_zeros(&g); bh[a] = padded_zeros(&g);
+        psi[a] = cpml ? padded_zeros(&g) : NULL; phi[a] = cpml ? padded_zeros(&g) : NULL;
+    }
+    for (int a = 0; a < 3; ++a) {
+        for (int s = 0; s < 2; ++s)
+            for (int t = 0; t < 3; ++t) if (!prof[a][s][t]) rc = -3;
+        if (!v[a] || !bh[a] || (cpml && (!psi[a] || !phi[a]))) rc = -3;
+    }
+    if (!K || !Bc || !p) rc = -3;
+    if (rc) goto done;
+    for (int a = 0; a < 3; ++a)
+        for (int s = 0; s < 2; ++s)
+            vd_profile(n3[a], nbl, hh[a], vmax, refl, f0, dt, s, prof[a][s][0], prof[a][s][1], prof[a][s][2]);
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const long q = ((long)k * ny + j) * nx + i, o = at(&g, i, j, k);
+                const double vv = (double)vel[q], rr = (double)rho[q];
+                K[o] = rr * vv * vv;
+                Bc[o] = 1.0 / rr;
+                if (state0) {
+                    p[o] = state0[q];
+                    for (int a = 0; a < 3; ++a) v[a][o] = state0[(a + 1) * N + q];
+                }
+            }
+    /* buoyancy at the half points: mean of the two neighbours, or the point's own past the last one */
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const long o = at(&g, i, j, k);
+                const int idx[3] = {i, j, k};
+                for (int a = 0; a < 3; ++a)
+                    bh[a][o] = idx[a] + 1 < n3[a] ? 0.5 * (Bc[o] + Bc[o + stride[a]]) : Bc[o];
+            }
+    const double cell = hx * hy * hz;
+    for (int n = 0; n < nt; ++n) {
+        /* particle velocities at n + 1/2 from p^n */
+        #pragma omp parallel for collapse(2) schedule(static)
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    const long o = at(&g, i, j, k);
+                    const int idx[3] = {i, j, k};
+                    for (int a = 0; a < 3; ++a) {
+                        double dp = 0.0;
+                        for (int m = 1; m <= R; ++m)
+                            dp += aw[m] * (p[o + m * stride[a]] - p[o - (m - 1) * stride[a]]);
+                        dp /= hh[a];
+                        if (cpml) {
+                            const double Gc = prof[a][1][2][idx[a]];
+                            if (Gc != 0.0) {
+                                psi[a][o] = prof[a][1][1][idx[a]] * psi[a][o] + Gc * dp;
+                                dp += psi[a][o];
+                            }
+                            v[a][o] += dt * bh[a][o] * dp;
+                        } else {
+                            double eta = 0.0;
+                            for (int c = 0; c < 3; ++c) eta += prof[c][c == a][0][idx[c]];
+                            const double e = dt * eta;
+                            v[a][o] = ((1.0 - 0.5 * e) * v[a][o] + dt * bh[a][o] * dp) / (1.0 + 0.5 * e);
+                        }
+                    }
+                }
+        /* pressure at n + 1 from the velocities at n + 1/2 */
+        #pragma omp parallel for collapse(2) schedule(static)
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    const long o = at(&g, i, j, k);
+                    const int idx[3] = {i, j, k};
+                    double div = 0.0;
+                    for (int a = 0; a < 3; ++a) {
+                        double dv = 0.0;
+                        for (int m = 1; m <= R; ++m)
+                            dv += aw[m] * (v[a][o + (m - 1) * stride[a]] - v[a][o - m * stride[a]]);
+                        dv /= hh[a];
+                        if (cpml) {
+                            const double Gc = prof[a][0][2][idx[a]];
+                            if (Gc != 0.0) {
+                                phi[a][o] = prof[a][0][1][idx[a]] * phi[a][o] + Gc * dv;
+                                dv += phi[a][o];
+                            }
+                        }
+                        div += dv;
+                    }
+                    if (cpml) {
+                        p[o] += dt * K[o] * div;
+                    } else {
+                        const double e = dt * (prof[0][0][0][i] + prof[1][0][0][j] + prof[2][0][0][k]);
+                        p[o] = ((1.0 - 0.5 * e) * p[o] + dt * K[o] * div) / (1.0 + 0.5 * e);
+                    }
+                }
+        for (int s = 0; s < nsrc; ++s) {
+            const int *q = src_ijk + 3 * s;
+            const long o = at(&g, q[0], q[1], q[2]);
+            const double e = cpml ? 0.0 : dt * (prof[0][0][0][q[0]] + prof[1][0][0][q[1]] + prof[2][0][0][q[2]]);
+            p[o] += dt * K[o] * (double)wavelet[(long)s * nt + n] / (cell * (1.0 + 0.5 * e));
+        }
+        for (int r = 0; r < nrec; ++r) {
+            const int *q = rec_ijk + 3 * r;
+            traces[n * (long)nrec + r] = p[at(&g, q[0], q[1], q[2])];
+        }
+    }
+    if (state_out)
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    const long q = ((long)k * ny + j) * nx + i, o = at(&g, i, j, k);
+                    state_out[q] = p[o];
+                    for (int a = 0; a < 3; ++a) state_out[(a + 1) * N + q] = v[a][o];
+                }
+done:
+    for (int a = 0; a < 3; ++a) {
+        for (int s = 0; s < 2; ++s)
+            for (int t = 0; t < 3; ++t) free(prof[a][s][t]);
+        free(v[a]); free(bh[a]); free(psi[a]); free(phi[a]);
+    }
+    free(K); free(Bc); free(p);
     return rc;
 }

@@ -12,6 +12,7 @@ import test_oracle_cpml as CP
 import test_oracle_dynamics as DY
 import test_oracle_free_surface as FS
 import test_oracle_stencil as ST
+import test_oracle_vd as VD
 
 
 def _dense(orc):
@@ -55,6 +56,29 @@ def _cpml(orc):
     CP.test_dense_stepper_agrees(orc, (12, 10, 11), 3, False)
 
 
+def _vd_dense(orc):
+    for cpml in (False, True):
+        VD.test_dense_stepper_agrees(orc, (11, 10, 12), 2, cpml)
+
+
+def _vd_poly(orc):
+    VD.test_dplus_exact_on_polynomials(orc)
+    VD.test_dminus_exact_on_polynomials(orc)
+
+
+def _vd_coeffs(orc):
+    VD.test_staggered_coeffs_closed_form(orc, 8)
+
+
+def _vd_energy(orc):
+    VD.test_energy_conserved_without_layers(orc)
+    VD.test_energy_change_with_damping_is_exact(orc)
+
+
+def _vd_standing(orc):
+    VD.test_standing_wave_is_exact(orc)
+
+
 def _grad(orc):
     for kind in ("point", "smooth", "source"):
         AD.test_gradient_matches_finite_differences(orc, kind)
@@ -96,6 +120,18 @@ MUTATIONS = [
     ("CPML memory forgets its decay", "psi[a][o] = B[a][idx[a]] * psi[a][o] + gg * d1 / hh[a];",
      "psi[a][o] = psi[a][o] + gg * d1 / hh[a];", [_cpml]),
     ("CPML drops the second memory variable", "total += d2 + dpsi + zeta[a][o];", "total += d2 + dpsi;", [_cpml]),
+    ("staggered D- offsets swapped", "dv += aw[m] * (v[a][o + (m - 1) * stride[a]] - v[a][o - m * stride[a]]);",
+     "dv += aw[m] * (v[a][o + m * stride[a]] - v[a][o - (m - 1) * stride[a]]);", [_vd_poly, _vd_energy]),
+    ("staggered weights: wrong consistency right-hand side", "A[q][R] = (q == 0) ? 0.5 : 0.0;",
+     "A[q][R] = (q == 0) ? 1.0 : 0.0;", [_vd_coeffs, _vd_poly]),
+    ("half-point buoyancy not averaged", "? 0.5 * (Bc[o] + Bc[o + stride[a]]) : Bc[o];", "? Bc[o] : Bc[o];",
+     [_vd_dense]),
+    ("K = rho v instead of rho v^2", "K[o] = rr * vv * vv;", "K[o] = rr * vv;", [_vd_standing, _vd_dense]),
+    ("velocity damping at grid-point positions", "eta += prof[c][c == a][0][idx[c]];", "eta += prof[c][0][0][idx[c]];",
+     [_vd_dense, _vd_energy]),
+    ("VD source outside the (1 + e/2) division", "(double)wavelet[(long)s * nt + n] / (cell * (1.0 + 0.5 * e));",
+     "(double)wavelet[(long)s * nt + n] / cell;", [_vd_dense]),
+    ("VD CPML drops the pressure-gradient memory", "dp += psi[a][o];", "dp += 0.0 * psi[a][o];", [_vd_dense]),
 ]
 
 

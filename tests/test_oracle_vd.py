@@ -1,0 +1,577 @@
+"""Pins of the oracle's variable-density stepper (reading R18: the first-order
+system of Sec. 3 on a staggered Yee grid).
+
+* Staggered weights: the textbook closed form in exact rationals for orders
+  2..8 and the odd-moment identities.
+* Staggered differences, driven through single steps of the stepper: exact
+  derivatives of every polynomial of degree <= 8 at the half points (D+) and
+  at the grid points (D-), and the known x^9 truncation error.
+* Exact discrete standing wave (constant K, b): p^n = cos(n w dt) phi with
+  sin(w dt / 2) = (dt / 2) v |S|, S_a = (2 / h_a) sum_m a_m sin((2m - 1) k_a h_a / 2).
+* Discrete energy p^T K^-1 p + v^{n+1/2 T} B^-1 v^{n-1/2} conserved without
+  layers, and with damping layers changed each step by an exact identity.
+* A dense-matrix stepper written here (Kronecker difference matrices,
+  damping and CPML layers) agrees to FP64 rounding on tiny grids.
+* Physics: the homogeneous Green's function rho w'(t - r/v) / (4 pi r), and a
+  flat density contrast at constant velocity, whose reflected and
+  transmitted fields are exactly R and 1 + R times the incident one at every
+  angle, R = (rho2 - rho1) / (rho2 + rho1).
+"""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+A8 = [Fraction(1225, 1024), Fraction(-245, 3072), Fraction(49, 5120), Fraction(-5, 7168)]
+CLOSED = {2: [Fraction(1)], 4: [Fraction(9, 8), Fraction(-1, 24)],
+          6: [Fraction(75, 64), Fraction(-25, 384), Fraction(3, 640)], 8: A8}
+
+
+@pytest.mark.parametrize("order", [2, 4, 6, 8])
+def test_staggered_coeffs_closed_form(orc, order):
+    a = orc.staggered_coeffs(order)
+    assert a[0] == 0.0
+    ref = CLOSED[order]
+    for m, c in enumerate(ref, start=1):
+        assert a[m] == pytest.approx(float(c), rel=1e-14, abs=1e-16)
+    # consistency and vanishing odd moments, in exact arithmetic on the closed form
+    R = order // 2
+    half = [Fraction(2 * m - 1, 2) for m in range(1, R + 1)]
+    assert sum(2 * h * c for h, c in zip(half, ref)) == 1
+    for q in range(1, R):
+        assert sum(h ** (2 * q + 1) * c for h, c in zip(half, ref)) == 0
+
+
+def _axes(shape, h):
+    nz, ny, nx = shape
+    return (np.arange(nx) * h[0], np.arange(ny) * h[1], np.arange(nz) * h[2])
+
+
+def _ones(shape):
+    return np.ones(shape, np.float32)
+
+
+def _poly(coef, xs, half_axis=None, h=None):
+    """sum of coef[(px,py,pz)] x^px y^py z^pz on the grid, shifted by h/2 along half_axis."""
+    x, y, z = [c + (0.5 * h[a] if a == half_axis else 0.0) for a, c in enumerate(xs)]
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    out = np.zeros(Z.shape)
+    for (px, py, pz), c in coef.items():
+        out += c * X ** px * Y ** py * Z ** pz
+    return out
+
+
+def _dpoly(coef, axis):
+    out = {}
+    for p, c in coef.items():
+        if p[axis] == 0:
+            continue
+        q = list(p)
+        q[axis] -= 1
+        out[tuple(q)] = out.get(tuple(q), 0.0) + c * p[axis]
+    return out
+
+
+POLY = {(8, 0, 0): 1e-8, (0, 5, 3): 2e-9, (2, 2, 4): -3e-10, (1, 1, 1): 0.5, (0, 0, 7): 1e-9,
+        (3, 4, 0): 1e-9, (0, 0, 0): 2.0}
+
+
+def test_dplus_exact_on_polynomials(orc):
+    """One step from p^0 = poly, vel = 0, rho = 1, no layers: vel^{1/2}_a = dt D+_a p^0."""
+    shape, h, dt = (20, 19, 21), (0.5, 0.6, 0.45), 1e-3
+    xs = [c - c.mean() for c in _axes(shape, h)]
+    p0 = _poly(POLY, xs)
+    st = np.zeros((4,) + shape)
+    st[0] = p0
+    _, out = orc.forward_vd(_ones(shape), _ones(shape), h, dt, 1, state0=st, want_state=True)
+    inner = (slice(4, -4),) * 3
+    for a in range(3):
+        got = out[1 + a] / dt
+        ref = _poly(_dpoly(POLY, a), xs, half_axis=a, h=h)
+        assert np.max(np.abs(got - ref)[inner]) < 1e-9 * np.max(np.abs(ref[inner])), a
+
+
+def test_dminus_exact_on_polynomials(orc):
+    """One step from p^0 = 0, vel_a^{-1/2} = poly at the half points, rho = 1,
+    K = 1: p^1 = dt D-_a vel_a."""
+    shape, h, dt = (20, 19, 21), (0.5, 0.6, 0.45), 1e-3
+    xs = [c - c.mean() for c in _axes(shape, h)]
+    inner = (slice(4, -4),) * 3
+    for a in range(3):
+        st = np.zeros((4,) + shape)
+        st[1 + a] = _poly(POLY, xs, half_axis=a, h=h)
+        _, out = orc.forward_vd(_ones(shape), _ones(shape), h, dt, 1, state0=st, want_state=True)
+        assert np.array_equal(out[1 + a], st[1 + a])          # D+ of p = 0 adds nothing
+        got = out[0] / dt
+        ref = _poly(_dpoly(POLY, a), xs)
+        assert np.max(np.abs(got - ref)[inner]) < 1e-9 * np.max(np.abs(ref[inner])), a
+
+
+def test_truncation_error_on_x9(orc):
+    """D+ x^9 at the half point x = 0 equals 2 h^8 sum_m a_m (m - 1/2)^9, where
+    the exact derivative is 0 (order 8, not more)."""
+    shape, h, dt = (12, 12, 21), (0.7, 1.0, 1.0), 1e-3
+    i0 = 9                                            # half point i0 + 1/2 sits at x = 0
+    x = (np.arange(shape[2]) - i0 - 0.5) * h[0]
+    st = np.zeros((4,) + shape)
+    st[0] = np.broadcast_to(x ** 9, shape)
+    _, out = orc.forward_vd(_ones(shape), _ones(shape), h, dt, 1, state0=st, want_state=True)
+    got = out[1][6, 6, i0] / dt
+    const = float(2 * sum(c * Fraction(2 * m - 1, 2) ** 9 for m, c in enumerate(A8, start=1)))
+    assert const != 0.0
+    assert got == pytest.approx(const * h[0] ** 8, rel=1e-9)
+
+
+def _S(k, h):
+    return sum(2.0 / h * float(a) * np.sin((2 * m - 1) * k * h / 2) for m, a in enumerate(A8, start=1))
+
+
+def test_standing_wave_is_exact(orc):
+    shape = (72, 70, 74)
+    h = (10.0, 12.0, 9.0)
+    v, rho = 2200.0, 1800.0
+    dt = 0.9e-3
+    K, b = rho * v * v, 1.0 / rho
+    k = np.array([2 * np.pi / 97.0, 2 * np.pi / 61.0, 2 * np.pi / 143.0])
+    s = (0.3, 1.1, -0.4)
+    S = np.array([_S(k[a], h[a]) for a in range(3)])
+    wdt = 2 * np.arcsin(0.5 * dt * v * np.linalg.norm(S))
+    xs = _axes(shape, h)
+
+    def field(half_axis):
+        f = []
+        for a in range(3):
+            c = xs[a] + (0.5 * h[a] if a == half_axis else 0.0)
+            f.append(np.sin(k[a] * c + s[a]) if a == half_axis else np.cos(k[a] * c + s[a]))
+        return f[2][:, None, None] * f[1][None, :, None] * f[0][None, None, :]
+
+    phi = field(None)
+    psi = [field(a) for a in range(3)]
+    V0 = 0.5 * dt * b * S
+    st = np.zeros((4,) + shape)
+    st[0] = phi
+    for a in range(3):
+        st[1 + a] = V0[a] * psi[a]
+    nsteps = 4
+    _, out = orc.forward_vd(np.full(shape, v, np.float32), np.full(shape, rho, np.float32), h, dt, nsteps,
+                            state0=st, want_state=True)
+    # scalar recurrence of the amplitudes
+    P, V = 1.0, V0.copy()
+    for n in range(nsteps):
+        V = V - dt * b * S * P
+        P = P + dt * K * float(np.dot(S, V))
+    assert P == pytest.approx(np.cos(nsteps * wdt), rel=1e-12)
+    m = 7 * nsteps + 1
+    inner = (slice(m, -m),) * 3
+    assert np.max(np.abs(out[0] - P * phi)[inner]) < 1e-12
+    for a in range(3):
+        assert np.max(np.abs(out[1 + a] - V[a] * psi[a])[inner]) < 1e-12 * abs(V0[a]) / 1e-3 + 1e-18
+    assert np.max(np.abs(out[0] - P * phi)) > 1e-6        # the zero boundary does act outside
+    w_cont = v * np.linalg.norm(k)
+    assert abs(wdt / dt - w_cont) / w_cont < 3e-3
+
+
+def _bh(rho):
+    """Buoyancy at the half points along each axis (mean of the two neighbours)."""
+    b = 1.0 / rho.astype(np.float64)
+    out = []
+    for ax in (2, 1, 0):                       # x, y, z are the last, middle, first array axes
+        bb = b.copy()
+        sl_lo = [slice(None)] * 3
+        sl_hi = [slice(None)] * 3
+        sl_lo[ax] = slice(0, -1)
+        sl_hi[ax] = slice(1, None)
+        bb[tuple(sl_lo)] = 0.5 * (b[tuple(sl_lo)] + b[tuple(sl_hi)])
+        out.append(bb)
+    return out
+
+
+def _energy(p, v_new, v_old, K, bh):
+    return np.sum(p * p / K) + sum(np.sum(v_new[a] * v_old[a] / bh[a]) for a in range(3))
+
+
+def _rand_model(rng, shape):
+    vel = rng.uniform(1500.0, 3500.0, shape).astype(np.float32)
+    rho = rng.uniform(1000.0, 2600.0, shape).astype(np.float32)
+    return vel, rho
+
+
+def test_energy_conserved_without_layers(orc):
+    rng = np.random.default_rng(21)
+    shape = (18, 20, 22)
+    h = (10.0, 9.0, 11.0)
+    vel, rho = _rand_model(rng, shape)
+    dt = W.cfl_dt(0.3, h, 3500.0)
+    K = rho.astype(np.float64) * vel.astype(np.float64) ** 2
+    bh = _bh(rho)
+    st = rng.standard_normal((4,) + shape)
+    st[0] *= 1e6
+    e_ref = None
+    for nt in (0, 37, 400):
+        _, s_n = orc.forward_vd(vel, rho, h, dt, nt, state0=st, want_state=True)
+        _, s_n1 = orc.forward_vd(vel, rho, h, dt, 1, state0=s_n, want_state=True)
+        e = _energy(s_n[0], s_n1[1:], s_n[1:], K, bh)
+        assert e > 0
+        if e_ref is None:
+            e_ref = e
+        assert e == pytest.approx(e_ref, rel=1e-11), nt
+
+
+def _layer_depth(x, n, L):
+    return min(max(L - x, x - (n - 1 - L), 0.0), float(L))
+
+
+def _eta(n, L, h, vmax, refl=1e-3, half=False):
+    d0 = 3 * vmax * np.log(1 / refl) / (2 * L * h) if L else 0.0
+    return np.array([d0 * (_layer_depth(i + 0.5 * half, n, L) / L) ** 2 if L else 0.0 for i in range(n)])
+
+
+def _eta3(shape, L, h, vmax, half_axis=None):
+    nz, ny, nx = shape
+    ex = _eta(nx, L, h[0], vmax, half=half_axis == 0)
+    ey = _eta(ny, L, h[1], vmax, half=half_axis == 1)
+    ez = _eta(nz, L, h[2], vmax, half=half_axis == 2)
+    return ez[:, None, None] + ey[None, :, None] + ex[None, None, :]
+
+
+def test_energy_change_with_damping_is_exact(orc):
+    """E^{n+1} - E^n = -sum e_p (p^{n+1} + p^n)^2 / (2K)
+                       - sum_a sum e_a v_a^{n+1/2} (v_a^{n+3/2} + 2 v_a^{n+1/2} + v_a^{n-1/2}) / (2 b_a)."""
+    rng = np.random.default_rng(22)
+    shape = (16, 17, 18)
+    h = (10.0, 10.0, 12.0)
+    nbl = 4
+    vel, rho = _rand_model(rng, shape)
+    dt = W.cfl_dt(0.3, h, 3500.0)
+    vmax = float(vel.max())
+    K = rho.astype(np.float64) * vel.astype(np.float64) ** 2
+    bh = _bh(rho)
+    e_p = dt * _eta3(shape, nbl, h, vmax)
+    e_v = [dt * _eta3(shape, nbl, h, vmax, half_axis=a) for a in range(3)]
+    assert e_p.max() > 0 and np.count_nonzero(e_p == 0) > 0
+    s0 = rng.standard_normal((4,) + shape)
+    s0[0] *= 1e6
+    states = [s0]
+    for _ in range(8):
+        _, s = orc.forward_vd(vel, rho, h, dt, 1, nbl=nbl, state0=states[-1], want_state=True)
+        states.append(s)
+    for n in range(len(states) - 2):
+        a, b, c = states[n], states[n + 1], states[n + 2]
+        e_n = _energy(a[0], b[1:], a[1:], K, bh)
+        e_n1 = _energy(b[0], c[1:], b[1:], K, bh)
+        dec = -np.sum(e_p * (b[0] + a[0]) ** 2 / (2 * K))
+        dec -= sum(np.sum(e_v[q] * b[1 + q] * (c[1 + q] + 2 * b[1 + q] + a[1 + q]) / (2 * bh[q])) for q in range(3))
+        assert e_n1 - e_n == pytest.approx(dec, rel=1e-8, abs=1e-12 * abs(e_n))
+
+
+# ---------------------------------------------------------------------------
+# dense stepper
+# ---------------------------------------------------------------------------
+
+def _dplus1(n, h):
+    D = np.zeros((n, n))
+    for i in range(n):
+        for m, a in enumerate(A8, start=1):
+            if i + m < n:
+                D[i, i + m] += float(a) / h
+            if 0 <= i - m + 1 < n:
+                D[i, i - m + 1] -= float(a) / h
+    return D
+
+
+def _dminus1(n, h):
+    D = np.zeros((n, n))
+    for i in range(n):
+        for m, a in enumerate(A8, start=1):
+            if 0 <= i + m - 1 < n:
+                D[i, i + m - 1] += float(a) / h
+            if i - m >= 0:
+                D[i, i - m] -= float(a) / h
+    return D
+
+
+def _kron_axis(D1, shape, axis):
+    nz, ny, nx = shape
+    Ix, Iy, Iz = np.eye(nx), np.eye(ny), np.eye(nz)
+    if axis == 0:
+        return np.kron(Iz, np.kron(Iy, D1))
+    if axis == 1:
+        return np.kron(Iz, np.kron(D1, Ix))
+    return np.kron(D1, np.kron(Iy, Ix))
+
+
+def _cpml_bg(n, L, h, vmax, refl, f0, dt, half):
+    B, G = np.ones(n), np.zeros(n)
+    if L == 0:
+        return B, G
+    d0 = 3 * vmax * np.log(1 / refl) / (2 * L * h)
+    for i in range(n):
+        x = _layer_depth(i + 0.5 * half, n, L)
+        if x == 0:
+            continue
+        s = x / L
+        d, al = d0 * s * s, np.pi * f0 * (1 - s)
+        B[i] = np.exp(-(d + al) * dt)
+        G[i] = d * (B[i] - 1) / (d + al)
+    return B, G
+
+
+def _bg3(shape, L, h, vmax, refl, f0, dt, axis, half):
+    n = shape[2 - axis]
+    B, G = _cpml_bg(n, L, h[axis], vmax, refl, f0, dt, half)
+    sh = [1, 1, 1]
+    sh[2 - axis] = n
+    return np.broadcast_to(B.reshape(sh), shape).ravel(), np.broadcast_to(G.reshape(sh), shape).ravel()
+
+
+def dense_vd(vel, rho, h, dt, nt, nbl, src, wav, rec, cpml=False, f0=0.0, refl=1e-3):
+    shape = vel.shape
+    N = vel.size
+    v64, r64 = vel.astype(np.float64).ravel(), rho.astype(np.float64).ravel()
+    K = r64 * v64 * v64
+    bh = [b.ravel() for b in _bh(rho)]
+    Dp = [_kron_axis(_dplus1(shape[2 - a], h[a]), shape, a) for a in range(3)]
+    Dm = [_kron_axis(_dminus1(shape[2 - a], h[a]), shape, a) for a in range(3)]
+    vmax = float(vel.max())
+    e_p = (dt * _eta3(shape, nbl, h, vmax)).ravel()
+    e_v = [(dt * _eta3(shape, nbl, h, vmax, half_axis=a)).ravel() for a in range(3)]
+    Bh = [_bg3(shape, nbl, h, vmax, refl, f0, dt, a, 1) for a in range(3)]
+    Bg = [_bg3(shape, nbl, h, vmax, refl, f0, dt, a, 0) for a in range(3)]
+    p = np.zeros(N)
+    v = [np.zeros(N) for _ in range(3)]
+    psi = [np.zeros(N) for _ in range(3)]
+    phi = [np.zeros(N) for _ in range(3)]
+    lin = lambda q: (q[2] * shape[1] + q[1]) * shape[2] + q[0]
+    cell = h[0] * h[1] * h[2]
+    tr = np.zeros((nt, len(rec)))
+    for n in range(nt):
+        for a in range(3):
+            dp = Dp[a] @ p
+            if cpml:
+                psi[a] = Bh[a][0] * psi[a] + Bh[a][1] * dp
+                v[a] = v[a] + dt * bh[a] * (dp + psi[a])
+            else:
+                v[a] = ((1 - 0.5 * e_v[a]) * v[a] + dt * bh[a] * dp) / (1 + 0.5 * e_v[a])
+        div = np.zeros(N)
+        for a in range(3):
+            dv = Dm[a] @ v[a]
+            if cpml:
+                phi[a] = Bg[a][0] * phi[a] + Bg[a][1] * dv
+                dv = dv + phi[a]
+            div += dv
+        if cpml:
+            p = p + dt * K * div
+        else:
+            p = ((1 - 0.5 * e_p) * p + dt * K * div) / (1 + 0.5 * e_p)
+        for s, q in enumerate(src):
+            o = lin(q)
+            e = 0.0 if cpml else e_p[o]
+            p[o] += dt * K[o] * float(wav[s, n]) / (cell * (1 + 0.5 * e))
+        for r, q in enumerate(rec):
+            tr[n, r] = p[lin(q)]
+    return tr, p.reshape(shape), [x.reshape(shape) for x in v]
+
+
+def _tiny_vd(shape, nt, nbl, seed, h=(10.0, 11.0, 12.0)):
+    rng = np.random.default_rng(seed)
+    nz, ny, nx = shape
+    vel, rho = _rand_model(rng, shape)
+    dt = W.cfl_dt(0.3, h, 3500.0)
+    src = np.array([[0, 0, 0], [nx - 1, ny // 2, nz - 1], [nx // 2, ny - 1, 1]], np.int32)
+    rec = np.array([[nx - 1, ny - 1, nz - 1], [1, 2, 3], [nx // 2, ny // 2, nz // 2], [0, ny - 1, 0]], np.int32)
+    wav = np.stack([W.ricker(f, dt, nt) for f in (25.0, 30.0, 40.0)])
+    return vel, rho, h, dt, src, wav, rec
+
+
+@pytest.mark.parametrize("cpml", [False, True])
+@pytest.mark.parametrize("shape,nbl", [((11, 10, 12), 2), ((9, 12, 10), 3), ((10, 9, 9), 0)])
+def test_dense_stepper_agrees(orc, shape, nbl, cpml):
+    nt = 40
+    vel, rho, h, dt, src, wav, rec = _tiny_vd(shape, nt, nbl, seed=sum(shape) + nbl)
+    tr_o, st_o = orc.forward_vd(vel, rho, h, dt, nt, nbl=nbl, cpml=cpml, f0=12.0, src_ijk=src, wavelet=wav,
+                                rec_ijk=rec, want_state=True)
+    tr_d, p_d, v_d = dense_vd(vel, rho, h, dt, nt, nbl, src, wav, rec, cpml=cpml, f0=12.0)
+    scale = np.max(np.abs(tr_d))
+    assert scale > 0
+    assert np.max(np.abs(tr_o - tr_d)) < 1e-12 * scale
+    assert np.max(np.abs(st_o[0] - p_d)) < 1e-12 * np.max(np.abs(p_d))
+    for a in range(3):
+        assert np.max(np.abs(st_o[1 + a] - v_d[a])) < 1e-12 * np.max(np.abs(v_d[a]))
+
+
+def test_constant_density_value_does_not_change_velocity_field_shape(orc):
+    """With constant density, p scales with rho and the particle velocities do
+    not depend on it (p_tt = v^2 lap p + rho v^2 f_t)."""
+    vel, rho, h, dt, src, wav, rec = _tiny_vd((10, 11, 12), 30, 2, seed=5)
+    one = np.full(vel.shape, 1000.0, np.float32)
+    two = np.full(vel.shape, 2500.0, np.float32)
+    t1, s1 = orc.forward_vd(vel, one, h, dt, 30, nbl=2, src_ijk=src, wavelet=wav, rec_ijk=rec, want_state=True)
+    t2, s2 = orc.forward_vd(vel, two, h, dt, 30, nbl=2, src_ijk=src, wavelet=wav, rec_ijk=rec, want_state=True)
+    np.testing.assert_allclose(t2, 2.5 * t1, rtol=1e-11, atol=1e-14 * np.max(np.abs(t2)))
+    np.testing.assert_allclose(s2[1:], s1[1:], rtol=1e-11, atol=1e-14 * np.max(np.abs(s1[1:])))
+
+
+# ---------------------------------------------------------------------------
+# physics
+# ---------------------------------------------------------------------------
+
+def _ricker_dt(tau, f):
+    """d/dtau of (1 - 2 a tau^2) exp(-a tau^2), a = (pi f)^2."""
+    a = (np.pi * f) ** 2
+    return -2 * a * tau * (3 - 2 * a * tau * tau) * np.exp(-a * tau * tau)
+
+
+def _wall_time(pos, src, n, h, v):
+    """Earliest arrival of a reflection off the zero cells beyond each face."""
+    t = np.inf
+    for ax in range(3):
+        for wall in (-1, n):
+            img = np.array(src, float)
+            img[ax] = 2 * wall - src[ax]
+            t = min(t, h * np.linalg.norm(img - pos) / v)
+    return t
+
+
+def _green_case(orc, rho1, rho2=None, k_if=None, n=100, h=10.0, v=1500.0, f=10.0, tmax=0.5, dt=1e-3,
+                offs=()):
+    nt = int(round(tmax / dt))
+    vel = np.full((n, n, n), v, np.float32)
+    rho = np.full((n, n, n), rho1, np.float32)
+    if rho2 is not None:
+        rho[k_if:] = rho2
+    s0 = n // 2
+    src = np.array([[s0, s0, s0]], np.int32)
+    rec = np.array([[s0 + a, s0 + b, s0 + c] for a, b, c in offs], np.int32)
+    w = W.ricker(f, dt, nt)
+    tr = orc.forward_vd(vel, rho, (h, h, h), dt, nt, src_ijk=src, wavelet=w[None, :], rec_ijk=rec)
+    return tr, nt
+
+
+def _exact_direct(t, r, v, f, dt, rho):
+    # sample w[n] drives the step centred at (n + 1/2) dt: source time function w(t - dt/2)
+    return rho * _ricker_dt(t - 0.5 * dt - r / v - 1.5 / f, f) / (4 * np.pi * r)
+
+
+@pytest.mark.slow
+def test_green_function(orc):
+    n, h, v, f, dt, rho = 100, 10.0, 1500.0, 10.0, 1e-3, 1800.0
+    offs = [(15, 0, 0), (0, -20, 0), (0, 0, 22), (12, 12, 12), (-14, 0, 14)]
+    tr, nt = _green_case(orc, rho, offs=offs, n=n, h=h, v=v, f=f, dt=dt)
+    t = (np.arange(nt) + 1) * dt
+    s0 = n // 2
+    for i, (a, b, c) in enumerate(offs):
+        pos = np.array([s0 + a, s0 + b, s0 + c], float)
+        r = h * np.sqrt(a * a + b * b + c * c)
+        keep = t < _wall_time(pos, [s0] * 3, n, h, v) - 3 * dt
+        exact = _exact_direct(t, r, v, f, dt, rho)
+        err = np.linalg.norm((tr[:, i] - exact)[keep]) / np.linalg.norm(exact[keep])
+        assert err < 0.02, (offs[i], err)
+
+
+@pytest.mark.slow
+def test_density_contrast_reflection_and_transmission(orc):
+    """Constant v, rho1 above the plane between k_if - 1 and k_if, rho2 below.
+    Reflected = with - without the contrast, against R times the image
+    source's field; transmitted against (1 + R) times the direct field.  The
+    sharp discrete contrast costs about 5 % in waveform at 6 points per
+    wavelength (the homogeneous case is under 2 %); the amplitudes R and 1 + R
+    hold to 2.5 %, and the reflection fits an interface at the mid-plane
+    z = (k_if - 1/2) h clearly better than one a quarter cell off."""
+    n, h, v, f, dt = 100, 10.0, 1500.0, 10.0, 1e-3
+    rho1, rho2 = 1000.0, 2500.0
+    R = (rho2 - rho1) / (rho2 + rho1)
+    s0 = n // 2
+    k_if = s0 + 12
+    above = [(15, 0, 0), (0, -20, 0), (0, 0, -10), (10, 10, -6)]
+    below = [(0, 0, 20), (12, 0, 22), (0, -10, 25)]
+    offs = above + below
+    tr_b, nt = _green_case(orc, rho1, rho2, k_if, offs=offs, n=n, h=h, v=v, f=f, dt=dt)
+    tr_a, _ = _green_case(orc, rho1, offs=offs, n=n, h=h, v=v, f=f, dt=dt)
+    t = (np.arange(nt) + 1) * dt
+    src = np.array([s0, s0, s0], float) * h
+
+    def errors(shift):
+        img = src.copy()
+        img[2] = 2 * (k_if - 0.5 + shift) * h - src[2]
+        out = []
+        for i, (a, b, c) in enumerate(offs):
+            pos = np.array([s0 + a, s0 + b, s0 + c], float)
+            keep = t < _wall_time(pos, [s0] * 3, n, h, v) - 3 * dt
+            assert np.count_nonzero(keep) > 0.5 * nt
+            x = pos * h
+            if (a, b, c) in above:
+                got = tr_b[:, i] - tr_a[:, i]
+                exact = R * _exact_direct(t, np.linalg.norm(x - img), v, f, dt, rho1)
+            else:
+                got = tr_b[:, i]
+                exact = (1 + R) * _exact_direct(t, np.linalg.norm(x - src), v, f, dt, rho1)
+            err = np.linalg.norm((got - exact)[keep]) / np.linalg.norm(exact[keep])
+            amp = np.dot(got[keep], exact[keep]) / np.dot(exact[keep], exact[keep])
+            out.append((err, amp))
+        return out
+
+    mid = errors(0.0)
+    for o, (err, amp) in zip(offs, mid):
+        assert err < 0.08, (o, err)
+        assert amp == pytest.approx(1.0, abs=0.025), (o, amp)
+    for shift in (-0.25, 0.25):
+        off = errors(shift)
+        for o, (e_mid, _), (e_off, _) in zip(offs, mid, off):
+            if o in above:
+                assert e_off > 2.5 * e_mid, (o, shift, e_mid, e_off)
+
+
+@pytest.mark.slow
+def test_layers_absorb(orc):
+    """Against a run on a grid so large that nothing returns in the window,
+    10-cell CPML layers leave under 0.2 % at receivers outside the layers and
+    damping layers of the same width leave far more (the first-order
+    system's damping is matched at normal incidence only).  Measured: CPML
+    2e-4, damping 3-7 %."""
+    v, h, f, rho = 2000.0, 10.0, 15.0, 1700.0
+    dt = W.cfl_dt(0.35, (h, h, h), v)
+    nt, L, n, big = 300, 10, 60, 150
+    recs = [(18, 0, 0), (15, 15, 0), (0, 0, 17), (-16, 8, -8)]
+
+    def run(nn, nbl, cpml):
+        vel = np.full((nn, nn, nn), v, np.float32)
+        rr = np.full((nn, nn, nn), rho, np.float32)
+        c = nn // 2
+        src = np.array([[c, c, c]], np.int32)
+        rec = np.array([[c + a, c + b, c + e] for a, b, e in recs], np.int32)
+        w = W.ricker(f, dt, nt)[None, :]
+        return orc.forward_vd(vel, rr, (h, h, h), dt, nt, nbl=nbl, cpml=cpml, f0=f, src_ijk=src, wavelet=w,
+                              rec_ijk=rec)
+
+    ref = run(big, 0, False)
+    err = {}
+    for kind in (True, False):
+        tr = run(n, L, kind)
+        err[kind] = max(np.linalg.norm(tr[:, r] - ref[:, r]) / np.linalg.norm(ref[:, r]) for r in range(len(recs)))
+    assert err[True] < 2e-3, err
+    assert err[False] > 20 * err[True], err
+    assert err[False] < 0.2, err
+
+
+@pytest.mark.parametrize("cpml", [False, True])
+def test_long_run_decays(orc, cpml):
+    """A rough random model (strong scattering in v and rho) keeps losing
+    energy through the layers for 3000 steps after the source stops."""
+    rng = np.random.default_rng(3)
+    shape = (30, 32, 34)
+    vel, rho = _rand_model(rng, shape)
+    h = (10.0, 11.0, 12.0)
+    dt = W.cfl_dt(0.3, h, 3500.0)
+    nt = 3000
+    w = W.ricker(25.0, dt, nt)
+    w[200:] = 0.0
+    src = np.array([[17, 16, 15]], np.int32)
+    rec = np.array([[5, 5, 5], [17, 16, 20], [28, 3, 25]], np.int32)
+    tr = orc.forward_vd(vel, rho, h, dt, nt, nbl=8, cpml=cpml, f0=25.0, src_ijk=src, wavelet=w[None, :],
+                        rec_ijk=rec)
+    window = [np.abs(tr[a:a + 300]).max() for a in range(0, nt, 300)]
+    assert window[0] > 0
+    assert window[-1] < 1e-2 * window[0]
+    assert window[-1] < window[5] < window[2]
