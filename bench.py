@@ -292,14 +292,16 @@ def run_mmod(args):
            "api": "mmod_set_model + mmod_forward with pinned host buffers, wall clock"}
 
     extra = {}
-    if not args.no_extra:
-        fwd_gpts = value / ws
-        extra["adjoint"] = measure_adjoint(M, prop, p, dev, stream, fwd_gpts)
-        extra["gradient"] = measure_gradient(M, dev, stream, fwd_gpts)
-        extra["batched"] = measure_batched(M, dev, stream, fwd_gpts)
-        extra["large"] = measure_large(M, dev, stream, peak)
-        extra["free_surface"] = measure_free_surface(M, dev, stream, fwd_gpts)
-        extra["cpml"] = measure_cpml(M, dev, stream, fwd_gpts)
+    fwd_gpts = value / ws
+    measures = {"adjoint": lambda: measure_adjoint(M, prop, p, dev, stream, fwd_gpts),
+                "gradient": lambda: measure_gradient(M, dev, stream, fwd_gpts),
+                "batched": lambda: measure_batched(M, dev, stream, fwd_gpts),
+                "large": lambda: measure_large(M, dev, stream, peak),
+                "free_surface": lambda: measure_free_surface(M, dev, stream, fwd_gpts),
+                "cpml": lambda: measure_cpml(M, dev, stream, fwd_gpts),
+                "variable_density": lambda: measure_vd(M, dev, stream, fwd_gpts, peak, args.nt or 1000)}
+    for name in extras_of(args):
+        extra[name] = measures[name]()
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -457,6 +459,54 @@ def measure_cpml(M, dev, stream, fwd_gpts, reps=3):
             "what": "step kernel + psi and layer-correction kernels per step"}
 
 
+VD_BYTES_PER_POINT = 56   # velocity kernel 32 B + pressure kernel 24 B (FP32)
+
+
+def measure_vd(M, dev, stream, fwd_gpts, peak, nt, reps=3):
+    """The variable-density staggered system (velocity and pressure kernels
+    per step) on the 240^3 layered model with Gardner densities."""
+    import torch
+    import workloads as W
+    p = W.layered_240_vd(nt)
+    prop = M.StaggeredPropagator.from_problem(p, device=dev.index or 0)
+    prop.set_model(torch.from_numpy(p.vel).to(dev), torch.from_numpy(p.rho).to(dev), stream)
+    wav = torch.from_numpy(np.ascontiguousarray(p.wavelet)).to(dev)
+    tr = torch.empty((p.nt, len(p.rec_ijk)), device=dev)
+    prop.forward(wav, tr, None, stream)
+    loops = []
+
+    def fwd():
+        prop.forward(wav, tr, None, stream)
+        loops.append(prop.loop_ms())
+    ms = time_calls(fwd, reps, stream)
+    step_ms = float(np.median(loops)) / p.nt
+    plan = prop.plan()
+    launches = prop.launches
+    prop.close()
+    v = p.npoints * p.nt / (ms * 1e-3) / 1e9
+    achieved = VD_BYTES_PER_POINT * p.npoints / (step_ms * 1e-3) / 1e9
+    return {"value": v, "unit": UNIT, "ms": ms, "step_ms": step_ms, "vs_forward": v / fwd_gpts,
+            "workload": p.name, "plan": plan, "launches_per_run": launches,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "bytes_per_point": VD_BYTES_PER_POINT,
+                         "what": "per step: velocity kernel reads p, vx, vy, vz, dt/rho and writes vx, vy, vz "
+                                 "(32 B); pressure kernel reads vx, vy, vz, p, dt K and writes p (24 B)"},
+            "what": "mmod_vd_forward: TMA velocity + pressure kernels and the source add per step"}
+
+
+def extras_of(args):
+    names = ["adjoint", "gradient", "batched", "large", "free_surface", "cpml", "variable_density"]
+    if args.no_extra or args.extra == "none":
+        return []
+    if args.extra == "all":
+        return names
+    want = [x.strip() for x in args.extra.split(",") if x.strip()]
+    bad = [x for x in want if x not in names]
+    if bad:
+        raise SystemExit(f"unknown --extra {bad}; choose from {names}")
+    return want
+
+
 def measure_large(M, dev, stream, peak, reps=2):
     """The 1024 x 1024 x 512 shot (h = 12.5 m, L = 32, 500 steps, 1024^2
     receivers): forward throughput and the step kernel's roofline fraction,
@@ -529,7 +579,10 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=20.0,
                     help="CPU seconds per oracle sample (cpu_baseline / reference arm)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the adjoint / gradient / batched / large-shot / free-surface / CPML measurements")
+    ap.add_argument("--no-extra", action="store_true", help="skip every extra measurement (same as --extra none)")
+    ap.add_argument("--extra", default="all",
+                    help="extra measurements after the main line: all, none, or a comma list of adjoint, gradient, "
+                         "batched, large, free_surface, cpml, variable_density")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "mmod":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)

@@ -388,6 +388,61 @@ const char *mmod_batch_last_error(const mmod_batch *b);
 mmod_status mmod_autotune(mmod_handle *h, int steps, mmod_stream stream, int *variant_out);
 mmod_status mmod_batch_autotune(mmod_batch *b, int steps, mmod_stream stream, int *variant_out);
 
+/* ---- Variable-density propagator (staggered Yee grid) ------------------
+ * The paper's first-order acoustic system with variable density (Sec. 3,
+ * the "acoustic_iso" kernel):
+ *     (1 / (rho v^2)) p_t - div vel = f,      rho vel_t - grad p = 0,
+ * on a staggered grid: p, rho, v at the grid points (i, j, k); the particle
+ * velocity along axis a half a cell further along a (vx at (i + 1/2, j, k)).
+ * Leapfrog with the velocities at half steps; per step n:
+ *   vel_a^{n+1/2} = [(1 - e/2) vel_a^{n-1/2} + dt b_a D+_a p^n] / (1 + e/2)
+ *   p^{n+1}       = [(1 - e/2) p^n + dt K (sum_a D-_a vel_a^{n+1/2} + s^n)] / (1 + e/2)
+ * K = rho v^2, b_a the mean of 1/rho over the half point's two grid points
+ * (1/rho of the point itself past the last one), D+_a / D-_a the order-8
+ * staggered differences  sum_m a_m (q(i+m) - q(i-m+1)) / h  and
+ * sum_m a_m (q(i+m-1) - q(i-m)) / h,  a_m = 1225/1024, -245/3072, 49/5120,
+ * -5/7168, with p = vel = 0 outside the grid; e = dt eta, eta the damping
+ * profile of mmod.h summed over the axes at each field's own (possibly half)
+ * position; s^n = w[n] / (hx hy hz) at a source point; traces[n][r] = p^{n+1}
+ * at receiver r.  With cfg->boundary = MMOD_BOUNDARY_CPML the layers are a
+ * CPML instead: each derivative gains a memory variable m = B m + G D on its
+ * axis's layers (B = exp(-(d + alpha) dt), G = d (B - 1) / (d + alpha), the
+ * profiles of the CPML above at the continuous depth into the layer), and
+ * e = 0.  Order 8 only; no free surface (UNSUPPORTED).  All pointers are
+ * DEVICE pointers (ARG otherwise).  Streams, errors and latching as above.
+ *
+ * mmod_vd_create: as mmod_create; allocates p, vx, vy, vz, dt K, dt / rho
+ *   (6 padded volumes; 12 with CPML).  Message: mmod_vd_last_error(NULL).
+ * mmod_vd_set_model: vel and rho [nz][ny][nx] FP32 (m/s, kg/m^3, finite and
+ *   > 0); synchronises `stream`.  UNSTABLE when
+ *   dt veff (2 S) sqrt(sum_a 1/h_a^2) > 2, S = sum_m |a_m| (the symbol's
+ *   largest magnitude), veff^2 = max over points of rho v^2 / min(rho over
+ *   the point and its six neighbours).
+ * mmod_vd_set_state: the next forward starts from state [4][nz][ny][nx] =
+ *   p^0, vx, vy, vz at -1/2 (NULL: zeros) instead of zeros.
+ * mmod_vd_forward: nt steps; wavelet [nsrc][nt], traces [nt][nrec],
+ *   final_state [4][nz][ny][nx] (p^{nt}, velocities at nt - 1/2; may be NULL).
+ * mmod_vd_set_kernel: MMOD_KERNEL_AUTO / MMOD_KERNEL_TMA (the TMA-pipelined
+ *   velocity and pressure kernels) or MMOD_KERNEL_SIMPLE (one thread per
+ *   point, the same FP32 operations: the same bits).
+ * mmod_vd_uses_tma: 1 when the next run uses the TMA kernels (-1: NULL).
+ * mmod_vd_get_plan: 6 ints {tiles_x, tiles_y, z_chunks, planes_per_chunk,
+ *   CTAs per kernel, threads per CTA}; UNSUPPORTED when no TMA plan.
+ * mmod_vd_last_loop_ms / mmod_vd_last_launch_count: as for mmod_forward. */
+typedef struct mmod_vd mmod_vd;
+mmod_status mmod_vd_create(const mmod_config *cfg, int device, mmod_vd **out);
+mmod_status mmod_vd_destroy(mmod_vd *h);
+mmod_status mmod_vd_set_model(mmod_vd *h, const float *vel, const float *rho, mmod_stream stream);
+mmod_status mmod_vd_set_state(mmod_vd *h, const float *state, mmod_stream stream);
+mmod_status mmod_vd_forward(mmod_vd *h, const float *wavelet, float *traces, float *final_state,
+                            mmod_stream stream);
+mmod_status mmod_vd_set_kernel(mmod_vd *h, int kernel);
+int mmod_vd_uses_tma(const mmod_vd *h);
+mmod_status mmod_vd_get_plan(const mmod_vd *h, int *out6);
+float mmod_vd_last_loop_ms(mmod_vd *h);
+long long mmod_vd_last_launch_count(const mmod_vd *h);
+const char *mmod_vd_last_error(const mmod_vd *h);
+
 /* Library version string, e.g. "mmod-gb300 0.1 sm_103a". */
 const char *mmod_version(void);
 

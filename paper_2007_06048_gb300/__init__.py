@@ -47,7 +47,9 @@ EXPORTED = ["mmod_create", "mmod_destroy", "mmod_set_model", "mmod_forward", "mm
             "mmod_batch_forward", "mmod_batch_set_variant", "mmod_batch_last_loop_ms", "mmod_batch_last_error",
             "mmod_autotune", "mmod_batch_autotune", "mmod_revolve_schedule", "mmod_persistent_grid",
             "mmod_tma_variant_info", "mmod_batch_set_mode", "mmod_optimized_coefficients",
-            "mmod_set_fd_coefficients"]
+            "mmod_set_fd_coefficients", "mmod_vd_create", "mmod_vd_destroy", "mmod_vd_set_model",
+            "mmod_vd_set_state", "mmod_vd_forward", "mmod_vd_set_kernel", "mmod_vd_uses_tma",
+            "mmod_vd_last_loop_ms", "mmod_vd_last_launch_count", "mmod_vd_last_error", "mmod_vd_get_plan"]
 CKPT_FP32, CKPT_BF16, CKPT_FP16 = 0, 1, 2
 
 
@@ -123,6 +125,17 @@ def load():
         "mmod_batch_set_mode": ([P, I], I),
         "mmod_optimized_coefficients": ([D, P], I),
         "mmod_set_fd_coefficients": ([P, P], I),
+        "mmod_vd_create": ([ctypes.POINTER(_Config), I, ctypes.POINTER(P)], I),
+        "mmod_vd_destroy": ([P], I),
+        "mmod_vd_set_model": ([P, P, P, P], I),
+        "mmod_vd_set_state": ([P, P, P], I),
+        "mmod_vd_forward": ([P, P, P, P, P], I),
+        "mmod_vd_set_kernel": ([P, I], I),
+        "mmod_vd_uses_tma": ([P], I),
+        "mmod_vd_last_loop_ms": ([P], ctypes.c_float),
+        "mmod_vd_last_launch_count": ([P], ctypes.c_longlong),
+        "mmod_vd_last_error": ([P], ctypes.c_char_p),
+        "mmod_vd_get_plan": ([P, ctypes.POINTER(I)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -470,6 +483,85 @@ class Propagator:
     def close(self):
         if self.handle is not None:
             mmod_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class StaggeredPropagator:
+    """Owning wrapper around one variable-density (staggered-grid) handle:
+    mmod_vd_create / mmod_vd_set_model / mmod_vd_forward.  Device tensors only."""
+
+    def __init__(self, shape, h, dt, nt, *, nbl=0, src_ijk=None, rec_ijk=None, damp_R=1e-3,
+                 device=0, cpml=False, cpml_f0=0.0):
+        nz, ny, nx = shape
+        self.shape = tuple(shape)
+        self.nt = int(nt)
+        src = np.zeros((0, 3), np.int32) if src_ijk is None else np.ascontiguousarray(src_ijk, np.int32).reshape(-1, 3)
+        rec = np.zeros((0, 3), np.int32) if rec_ijk is None else np.ascontiguousarray(rec_ijk, np.int32).reshape(-1, 3)
+        self.nsrc, self.nrec = len(src), len(rec)
+        self.device = device
+        cfg = _config(nx, ny, nz, h, dt, nt, nbl, src, rec, 8, damp_R, False, cpml, cpml_f0)
+        out = ctypes.c_void_p()
+        st = load().mmod_vd_create(ctypes.byref(cfg), device, ctypes.byref(out))
+        if st != 0:
+            raise MmodError(st, load().mmod_vd_last_error(None).decode())
+        self.handle = out.value
+
+    @classmethod
+    def from_problem(cls, p, device=0):
+        return cls(p.vel.shape, p.h, p.dt, p.nt, nbl=p.nbl, src_ijk=p.src_ijk, rec_ijk=p.rec_ijk,
+                   damp_R=p.refl, device=device, cpml=p.cpml, cpml_f0=p.cpml_f0)
+
+    def _check(self, st):
+        if st != 0:
+            raise MmodError(st, load().mmod_vd_last_error(self.handle).decode())
+
+    def set_model(self, vel, rho, stream=None):
+        self._check(load().mmod_vd_set_model(self.handle, _addr(vel), _addr(rho), _stream(stream)))
+
+    def set_state(self, state, stream=None):
+        """state [4][nz][ny][nx] device FP32: p^0, vx, vy, vz at -1/2 (None: zeros)."""
+        self._check(load().mmod_vd_set_state(self.handle, _addr(state), _stream(stream)))
+
+    def forward(self, wavelet, traces, final_state=None, stream=None):
+        self._check(load().mmod_vd_forward(self.handle, _addr(wavelet), _addr(traces), _addr(final_state),
+                                           _stream(stream)))
+
+    def set_kernel(self, kernel: int):
+        self._check(load().mmod_vd_set_kernel(self.handle, kernel))
+
+    @property
+    def uses_tma(self) -> bool:
+        return load().mmod_vd_uses_tma(self.handle) == 1
+
+    def plan(self) -> dict:
+        out = (ctypes.c_int * 6)()
+        st = load().mmod_vd_get_plan(self.handle, out)
+        if st not in (0, -7):
+            self._check(st)
+        return dict(zip(["tiles_x", "tiles_y", "z_chunks", "planes_per_chunk", "grid", "block"], list(out)))
+
+    @property
+    def launches(self) -> int:
+        return int(load().mmod_vd_last_launch_count(self.handle))
+
+    def loop_ms(self) -> float:
+        return float(load().mmod_vd_last_loop_ms(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            load().mmod_vd_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -95,6 +95,11 @@ cudaError_t launch_gather(const float *u, const long long *rec_off, int nrec, fl
 
 struct TmaPlan;   // tile shape / grid decomposition of the TMA kernel
 
+// Tensor map of a padded FP32 volume [nz][ny][nxp] with logical extent
+// nx x ny x nz and a bx x by x 1 box (zero fill outside the extent).  False
+// when the driver's encoder is unavailable or rejects the map.
+bool encode_box(CUtensorMap *map, const float *base, int nx, int ny, int nz, int nxp, int bx, int by);
+
 // x-y tiles and z ranges of one grid (one shot) for the TMA kernel.
 struct Geom {
     int tiles_x, tiles_y, zchunks, zlen;

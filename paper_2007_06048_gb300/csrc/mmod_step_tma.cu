@@ -34,13 +34,13 @@
 
 #include "mmod_internal.h"
 #include "tma_plan.h"
+#include "tma_ptx.cuh"
 
 namespace mmod {
 namespace {
 
 constexpr int TX = 64;                 // tile width: 32 lanes x 2 points
 constexpr int HX = TX + 2 * kRadius;   // 72: halo tile width
-constexpr unsigned long long kWaitNs = 100000000ull;   // a wait gives up after 100 ms
 
 template <int TY_, int RY_, int U_, int NSU_ = 8, int NSC_ = 4, int MINB_ = 1>
 struct Shape {
@@ -62,91 +62,6 @@ struct Shape {
     static_assert(TY % RY == 0, "rows per thread must divide the tile height");
     static_assert(NSU >= 6 && NSU <= 8 && NSC >= 2, "ring depth outside the fill / release schedule");
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
-    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// Orders this thread's view of global memory (generic proxy) before its
-// later bulk-tensor copies (async proxy).
-__device__ __forceinline__ void fence_proxy_async_global() {
-    asm volatile("fence.proxy.async.global;" ::: "memory");
-}
-
-__device__ __forceinline__ int ld_acquire_gpu(const int *p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release_gpu(int *p, int v) {
-    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Wait for a phase for at most kWaitNs of wall-clock time (try_wait suspends
-// the thread in hardware between polls).  The slow path gives up at once if
-// another CTA already reported a failure.  On give-up it records the failure
-// and returns false.
-__device__ __noinline__ bool mbar_wait_slow(uint64_t *bar, uint32_t parity, int *abort_flag, int *err) {
-    const unsigned long long t0 = global_ns();
-    while (!(err && *(volatile int *)err) && global_ns() - t0 < kWaitNs)
-        if (mbar_try_wait(bar, parity)) return true;
-    *abort_flag = 1;
-    if (err) atomicExch(err, 1);
-    return false;
-}
-
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *abort_flag, int *err) {
-    if (mbar_try_wait(bar, parity)) return true;
-    return mbar_wait_slow(bar, parity, abort_flag, err);
-}
-
-// Bounded drain wait used after a give-up: no error reporting.
-__device__ __noinline__ void mbar_drain(uint64_t *bar, uint32_t parity) {
-    const unsigned long long t0 = global_ns();
-    while (global_ns() - t0 < kWaitNs)
-        if (mbar_try_wait(bar, parity)) return;
-}
-
-__device__ __forceinline__ void tma_load_3d(float *dst, const CUtensorMap *map, int x, int y, int z,
-                                            uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-        : "memory");
-}
 
 struct Ctx {
     float *cur;          // S::NSU u^n slots
@@ -713,6 +628,14 @@ constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 int tma_variant_count() { return kNumVariants; }
 
 const char *tma_variant_name(int v) { return (v >= 0 && v < kNumVariants) ? kVariants[v].name : ""; }
+
+bool encode_box(CUtensorMap *map, const float *base, int nx, int ny, int nz, int nxp, int bx, int by) {
+    mmod_config c{};
+    c.nx = nx;
+    c.ny = ny;
+    c.nz = nz;
+    return encode(map, base, c, nxp, bx, by);
+}
 
 bool encode_maps(const mmod_config &cfg, int nxp, const float *buf, CUtensorMap *cur, CUtensorMap *prev) {
     return encode(cur, buf, cfg, nxp, HX, kTY + 2 * kRadius) && encode(prev, buf, cfg, nxp, TX, kTY);

@@ -1,0 +1,197 @@
+"""Variable-density staggered propagator on the GPU (FP32, C ABI) against the
+FP64 oracle (reading R18), with the same gates as the constant-density path:
+relative L2 of pressure, velocities and traces <= 1e-5 after up to 100 steps
+and <= 1e-4 after 1000.  The TMA kernels and the plain kernels must agree bit
+for bit."""
+import numpy as np
+import pytest
+
+import paper_2007_06048_gb300 as M
+import workloads as W
+from _gpu_util import rel_l2, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def run_vd(p, kernel=M.KERNEL_AUTO, state=None):
+    torch = torch_cuda()
+    prop = M.StaggeredPropagator.from_problem(p)
+    if kernel != M.KERNEL_AUTO:
+        prop.set_kernel(kernel)
+    prop.set_model(torch.from_numpy(np.ascontiguousarray(p.vel)).cuda(),
+                   torch.from_numpy(np.ascontiguousarray(p.rho)).cuda())
+    nsrc, nrec = len(p.src_ijk), len(p.rec_ijk)
+    wav = torch.from_numpy(np.ascontiguousarray(p.wavelet, np.float32)).cuda() if nsrc else None
+    tr = torch.zeros((p.nt, nrec), device="cuda") if nrec else None
+    fin = torch.zeros((4,) + p.vel.shape, device="cuda")
+    if state is not None:
+        prop.set_state(torch.from_numpy(np.ascontiguousarray(state, np.float32)).cuda())
+    prop.forward(wav, tr, fin)
+    torch.cuda.synchronize()
+    return (np.zeros((p.nt, 0)) if tr is None else tr.cpu().numpy()), fin.cpu().numpy(), prop
+
+
+def run_oracle_vd(orc, p, state0=None):
+    return orc.forward_vd(p.vel, p.rho, p.h, p.dt, p.nt, nbl=p.nbl, refl=p.refl, cpml=p.cpml, f0=p.cpml_f0,
+                          src_ijk=p.src_ijk, wavelet=p.wavelet, rec_ijk=p.rec_ijk, state0=state0,
+                          want_state=True)
+
+
+def check(tr_g, st_g, tr_o, st_o, tol):
+    for f in range(4):
+        if np.linalg.norm(st_o[f]) > 0:
+            assert rel_l2(st_g[f], st_o[f]) <= tol, ("field", f, rel_l2(st_g[f], st_o[f]))
+    if tr_o.size and np.linalg.norm(tr_o) > 0:
+        assert rel_l2(tr_g, tr_o) <= tol, ("traces", rel_l2(tr_g, tr_o))
+
+
+SHAPES = [((9, 9, 9), 0), ((13, 17, 35), 2), ((70, 33, 65), 5), ((5, 40, 3), 1), ((1, 1, 1), 0),
+          ((2, 67, 129), 0), ((40, 1, 30), 0), ((37, 45, 131), 9)]
+
+
+@pytest.mark.parametrize("cpml", [False, True], ids=["damping", "cpml"])
+@pytest.mark.parametrize("shape,nbl", SHAPES, ids=[f"{s}-L{n}" for s, n in SHAPES])
+def test_ragged_and_degenerate_shapes(orc, shape, nbl, cpml):
+    nz, ny, nx = shape
+    p = W.tiny_problem_vd(shape=shape, nt=60, nbl=nbl, nsrc=3, nrec=9, seed=nx * 7 + ny * 3 + nz)
+    p.cpml, p.cpml_f0 = cpml, 25.0
+    corners = [[0, 0, 0], [nx - 1, ny - 1, nz - 1], [nx - 1, 0, nz - 1], [0, ny - 1, 0]]
+    p.src_ijk[0] = corners[1]
+    p.src_ijk[1] = p.src_ijk[2]          # two sources on one point add up
+    p.rec_ijk[:4] = corners
+    p.rec_ijk[4] = p.rec_ijk[5]          # duplicated receiver
+    p.rec_ijk[6] = p.src_ijk[0]
+    tr_o, st_o = run_oracle_vd(orc, p)
+    tr_g, st_g, prop = run_vd(p)
+    check(tr_g, st_g, tr_o, st_o, 1e-5)
+    assert np.array_equal(tr_g[:, 4], tr_g[:, 5])
+    tr_s, st_s, _ = run_vd(p, kernel=M.KERNEL_SIMPLE)
+    assert np.array_equal(tr_s, tr_g) and np.array_equal(st_s, st_g)
+    assert prop.uses_tma
+
+
+def test_layered_240_100_steps(orc):
+    p = W.layered_240_vd(100)
+    tr_o, st_o = run_oracle_vd(orc, p)
+    tr_g, st_g, prop = run_vd(p)
+    check(tr_g, st_g, tr_o, st_o, 1e-5)
+    assert prop.launches >= 3 * p.nt
+
+
+def test_layered_240_1000_steps_full_size(orc):
+    """The benchmarked variable-density workload itself: 240^3, 1000 steps,
+    57 600 receivers, damping layers."""
+    p = W.layered_240_vd(1000)
+    tr_o, st_o = run_oracle_vd(orc, p)
+    tr_g, st_g, _ = run_vd(p)
+    check(tr_g, st_g, tr_o, st_o, 1e-4)
+
+
+def test_cpml_128_300_steps(orc):
+    p = W.tiny_problem_vd(shape=(128, 120, 136), nt=300, nbl=12, nsrc=2, nrec=40, seed=4)
+    p.cpml, p.cpml_f0 = True, 20.0
+    tr_o, st_o = run_oracle_vd(orc, p)
+    tr_g, st_g, _ = run_vd(p)
+    check(tr_g, st_g, tr_o, st_o, 1e-5)
+
+
+@pytest.mark.parametrize("shape,nbl,cpml", [((64, 64, 64), 8, False), ((97, 130, 200), 12, True),
+                                            ((240, 240, 240), 20, False)])
+def test_tma_kernels_are_bitwise_the_plain_kernels(shape, nbl, cpml):
+    if shape == (240, 240, 240):
+        p = W.layered_240_vd(200)
+    else:
+        p = W.tiny_problem_vd(shape=shape, nt=80, nbl=nbl, nsrc=2, nrec=30, seed=9)
+    p.cpml, p.cpml_f0 = cpml, 15.0
+    tr_t, st_t, prop = run_vd(p)
+    assert prop.uses_tma
+    tr_s, st_s, prop_s = run_vd(p, kernel=M.KERNEL_SIMPLE)
+    assert not prop_s.uses_tma
+    assert np.array_equal(tr_t, tr_s)
+    assert np.array_equal(st_t, st_s)
+
+
+def test_standing_wave_fp32():
+    """The exact discrete standing wave (constant K, b) in FP32 on the GPU:
+    p^n = P_n phi at points the zero boundary has not reached."""
+    shape, h, v, rho, dt = (72, 70, 74), (10.0, 12.0, 9.0), 2200.0, 1800.0, 0.9e-3
+    K, b = rho * v * v, 1.0 / rho
+    k = np.array([2 * np.pi / 97.0, 2 * np.pi / 61.0, 2 * np.pi / 143.0])
+    s = (0.3, 1.1, -0.4)
+    a8 = [1225 / 1024, -245 / 3072, 49 / 5120, -5 / 7168]
+    S = np.array([sum(2.0 / h[ax] * a8[m - 1] * np.sin((2 * m - 1) * k[ax] * h[ax] / 2) for m in range(1, 5))
+                  for ax in range(3)])
+    nz, ny, nx = shape
+    xs = (np.arange(nx) * h[0], np.arange(ny) * h[1], np.arange(nz) * h[2])
+
+    def field(half):
+        f = [np.sin(k[a] * (xs[a] + 0.5 * h[a]) + s[a]) if a == half else np.cos(k[a] * xs[a] + s[a]) for a in range(3)]
+        return f[2][:, None, None] * f[1][None, :, None] * f[0][None, None, :]
+
+    V0 = 0.5 * dt * b * S
+    st = np.stack([field(None)] + [V0[a] * field(a) for a in range(3)])
+    nsteps = 4
+    p = W.Problem("standing", np.full(shape, v, np.float32), h, dt, nsteps, 0, np.zeros((0, 3), np.int32),
+                  np.zeros((0, nsteps), np.float32), np.zeros((0, 3), np.int32), rho=np.full(shape, rho, np.float32))
+    _, out, _ = run_vd(p, state=st)
+    P, V = 1.0, V0.copy()
+    for _ in range(nsteps):
+        V = V - dt * b * S * P
+        P = P + dt * K * float(np.dot(S, V))
+    m = 7 * nsteps + 1
+    inner = (slice(m, -m),) * 3
+    assert rel_l2(out[0][inner], (P * st[0])[inner]) < 2e-6
+    for a in range(3):
+        assert rel_l2(out[1 + a][inner], (V[a] / V0[a] * st[1 + a])[inner]) < 2e-6
+
+
+def test_zero_steps_and_no_sources_or_receivers(orc):
+    p = W.tiny_problem_vd(shape=(20, 21, 22), nt=0, nbl=2, nsrc=1, nrec=2)
+    tr, st, _ = run_vd(p)
+    assert tr.shape == (0, 2) and not st.any()
+    q = W.tiny_problem_vd(shape=(20, 21, 22), nt=30, nbl=2, nsrc=0, nrec=0)
+    rng = np.random.default_rng(3)
+    st0 = rng.standard_normal((4,) + q.vel.shape).astype(np.float32)
+    st0[0] *= 1e6
+    _, st_g, _ = run_vd(q, state=st0)
+    _, st_o = orc.forward_vd(q.vel, q.rho, q.h, q.dt, q.nt, nbl=q.nbl, state0=st0, want_state=True)
+    check(np.zeros(0), st_g, np.zeros(0), st_o, 1e-5)
+
+
+def test_error_paths():
+    torch = torch_cuda()
+    p = W.tiny_problem_vd(shape=(20, 21, 22), nt=10, nbl=2)
+    base = dict(nbl=p.nbl, src_ijk=p.src_ijk, rec_ijk=p.rec_ijk)
+    with pytest.raises(M.MmodError) as e:
+        M.StaggeredPropagator(p.vel.shape, p.h, p.dt, p.nt, nbl=30)
+    assert e.value.status == -1
+    cfg = M._config(22, 21, 20, p.h, p.dt, p.nt, 2, p.src_ijk, p.rec_ijk, 6, 1e-3)
+    import ctypes
+    out = ctypes.c_void_p()
+    assert M.load().mmod_vd_create(ctypes.byref(cfg), 0, ctypes.byref(out)) == -7     # order 6
+    cfg = M._config(22, 21, 20, p.h, p.dt, p.nt, 2, p.src_ijk, p.rec_ijk, 8, 1e-3, free_surface=True)
+    assert M.load().mmod_vd_create(ctypes.byref(cfg), 0, ctypes.byref(out)) == -7     # free surface
+    prop = M.StaggeredPropagator(p.vel.shape, p.h, p.dt, p.nt, **base)
+    wav = torch.zeros((2, p.nt), device="cuda")
+    tr = torch.zeros((p.nt, len(p.rec_ijk)), device="cuda")
+    with pytest.raises(M.MmodError) as e:
+        prop.forward(wav, tr)
+    assert e.value.status == -6                                   # no model yet
+    vel = torch.from_numpy(p.vel).cuda()
+    rho = torch.from_numpy(p.rho).cuda()
+    with pytest.raises(M.MmodError) as e:
+        prop.set_model(torch.from_numpy(p.vel), rho)               # host pointer
+    assert e.value.status == -1
+    bad = rho.clone()
+    bad[3, 4, 5] = -1.0
+    with pytest.raises(M.MmodError) as e:
+        prop.set_model(vel, bad)
+    assert e.value.status == -1
+    fast = M.StaggeredPropagator(p.vel.shape, p.h, p.dt * 4, p.nt, **base)
+    with pytest.raises(M.MmodError) as e:
+        fast.set_model(vel, rho)
+    assert e.value.status == -2
+    prop.set_model(vel, rho)
+    prop.forward(wav, tr)
+    torch.cuda.synchronize()
+    assert prop.loop_ms() > 0

@@ -17,7 +17,8 @@ from dataclasses import dataclass, field
 import numpy as np
 
 __all__ = ["Problem", "ricker", "cfl_dt", "small_homogeneous", "layered_240",
-           "smooth_gradient_200", "batched_shots", "fractal_large", "tiny_problem"]
+           "smooth_gradient_200", "batched_shots", "fractal_large", "tiny_problem",
+           "gardner_density", "layered_240_vd", "tiny_problem_vd"]
 
 
 @dataclass
@@ -38,6 +39,7 @@ class Problem:
     free_surface: bool = False      # p = 0 on the plane k = 0 (odd image), no top layer
     cpml: bool = False              # the nbl-cell layers are a CPML instead of damping layers
     cpml_f0: float = 0.0            # CPML frequency shift (Hz)
+    rho: np.ndarray | None = None   # [nz][ny][nx] float32 kg/m^3: variable-density (staggered) system
 
     @property
     def shape(self):
@@ -221,3 +223,33 @@ def tiny_problem(shape=(11, 10, 12), nt: int = 30, nbl: int = 2, seed: int = 7,
     w = np.stack([ricker(f, dt, nt) for f in rng.uniform(20.0, 40.0, nsrc)]) if nsrc else np.zeros((0, nt), np.float32)
     return Problem(f"tiny-{nx}x{ny}x{nz}", vel, tuple(h), dt, nt, nbl, src.astype(np.int32),
                    w.astype(np.float32), rec.astype(np.int32))
+
+
+def gardner_density(vel: np.ndarray, seed: int, amp: float = 0.03, sigma: float = 4.0) -> np.ndarray:
+    """Density from velocity by Gardner's empirical rule rho = 310 v^0.25
+    (kg/m^3, v in m/s; 1930 kg/m^3 at 1500 m/s, 2540 at 4500), times
+    (1 + delta), delta a seeded white field Gaussian-smoothed (sigma cells)
+    scaled to max |delta| = amp, so density is not a function of velocity.
+    FP64, rounded once to FP32."""
+    v = vel.astype(np.float64)
+    rho = 310.0 * v ** 0.25 * (1.0 + _smooth_noise(vel.shape, sigma, seed, amp))
+    return rho.astype(np.float32)
+
+
+def layered_240_vd(nt: int = 1000, n: int = 240) -> Problem:
+    """The layered 240^3 workload with density: Gardner's rule on its velocity
+    times a seed-6 smoothed +-3 % field; dt from CFL 0.4 on the model maximum."""
+    p = layered_240(nt, n)
+    p.rho = gardner_density(p.vel, 6)
+    p.name = f"layered-vd-{n}^3"
+    return p
+
+
+def tiny_problem_vd(shape=(11, 10, 12), nt: int = 30, nbl: int = 2, seed: int = 7,
+                    h=(10.0, 11.0, 12.0), nsrc: int = 2, nrec: int = 5) -> Problem:
+    """tiny_problem with a density drawn per cell from U[1000, 2600] (seed + 1000)."""
+    p = tiny_problem(shape, nt, nbl, seed, h, nsrc, nrec)
+    rng = np.random.default_rng(seed + 1000)
+    p.rho = rng.uniform(1000.0, 2600.0, size=shape).astype(np.float32)
+    p.name = p.name.replace("tiny", "tiny-vd")
+    return p
