@@ -121,22 +121,6 @@ cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap *cur_map,
                             const CUtensorMap *prev_map, const CUtensorMap *c_map,
                             const TmaPlan &plan, cudaStream_t s);
 
-// CPML layers (mmod_cpml.cu): memory variables psi_a, zeta_a (padded
-// volumes), per-cell coefficients b_a, g_a of each axis (g = 0 outside the
-// layers), the step kernels' weights and 1 / h_a.
-struct CpmlArgs {
-    int nx, ny, nz, nxp;
-    long long plane;
-    int fs;
-    float *psi[3], *zeta[3];
-    const float *b[3], *g[3];
-    float inv_h[3];
-    float w[3][kRadius];
-    const float *c;
-};
-cudaError_t launch_cpml_psi(const CpmlArgs &p, const float *u, cudaStream_t s);
-cudaError_t launch_cpml_correct(const CpmlArgs &p, const float *u, float *uout, cudaStream_t s);
-
 // Persistent run: one cooperative launch advances steps n0 .. n1-1.  Each CTA
 // owns the work units (tile x z range) unit = blockIdx.x + k * gridDim.x;
 // a unit starts step n once its 26 neighbours have completed step n-1
