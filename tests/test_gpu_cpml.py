@@ -55,6 +55,23 @@ def test_cpml_kernels_and_variants_bitwise():
         assert np.array_equal(u_t, u_s) and np.array_equal(tr_t, tr_s), v
 
 
+@pytest.mark.parametrize("fs", [False, True])
+def test_cpml_interior_tiles_bitwise(orc, fs):
+    """A grid with step-kernel tiles both inside and across the layers
+    (70 x 80 x 200, 8-cell layers), with and without the free surface: the
+    TMA step kernel equals the plain one bit for bit under CPML, and both
+    match the oracle."""
+    p = _cpml(W.tiny_problem(shape=(70, 80, 200), nt=60, nbl=8, nsrc=3, nrec=20, seed=12), fs=fs)
+    p.src_ijk[0] = [100, 40, 3]          # in the top layer (or under the surface)
+    p.src_ijk[1] = [3, 40, 35]           # in an x layer
+    tr_s, u_s, _ = run_gpu(p, kernel=M.KERNEL_SIMPLE)
+    tr_t, u_t, _ = run_gpu(p, kernel=M.KERNEL_TMA)
+    assert np.array_equal(u_t, u_s) and np.array_equal(tr_t, tr_s)
+    tr_o, _, u_o = run_oracle(orc, p)
+    assert rel_l2(u_t, u_o) <= 1e-5
+    assert trace_err(tr_t, tr_o, u_o) <= 1e-5
+
+
 def test_cpml_absorbs_on_the_gpu():
     """Against a GPU run on a grid large enough that nothing returns in the
     window: the CPML of 10 cells leaves < 2 %, the damping layer much more."""
