@@ -426,6 +426,10 @@ mmod_status mmod_batch_autotune(mmod_batch *b, int steps, mmod_stream stream, in
  *   velocity and pressure kernels) or MMOD_KERNEL_SIMPLE (one thread per
  *   point, the same FP32 operations: the same bits).
  * mmod_vd_uses_tma: 1 when the next run uses the TMA kernels (-1: NULL).
+ * mmod_vd_set_option: MMOD_OPT_PDL 0 / 1 (default 0): launch the TMA
+ *   kernels as programmatic dependents, so that each requests the data its
+ *   predecessor does not write (own velocities and buoyancy; p and dt K)
+ *   while the predecessor finishes; the same bits either way.  ARG otherwise.
  * mmod_vd_get_plan: 6 ints {tiles_x, tiles_y, z_chunks, planes_per_chunk,
  *   CTAs per kernel, threads per CTA}; UNSUPPORTED when no TMA plan.
  * mmod_vd_last_loop_ms / mmod_vd_last_launch_count: as for mmod_forward. */
@@ -438,6 +442,7 @@ mmod_status mmod_vd_forward(mmod_vd *h, const float *wavelet, float *traces, flo
                             mmod_stream stream);
 mmod_status mmod_vd_set_kernel(mmod_vd *h, int kernel);
 int mmod_vd_uses_tma(const mmod_vd *h);
+mmod_status mmod_vd_set_option(mmod_vd *h, int option, int value);
 mmod_status mmod_vd_get_plan(const mmod_vd *h, int *out6);
 float mmod_vd_last_loop_ms(mmod_vd *h);
 long long mmod_vd_last_launch_count(const mmod_vd *h);

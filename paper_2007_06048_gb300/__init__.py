@@ -48,7 +48,7 @@ EXPORTED = ["mmod_create", "mmod_destroy", "mmod_set_model", "mmod_forward", "mm
             "mmod_autotune", "mmod_batch_autotune", "mmod_revolve_schedule", "mmod_persistent_grid",
             "mmod_tma_variant_info", "mmod_batch_set_mode", "mmod_optimized_coefficients",
             "mmod_set_fd_coefficients", "mmod_vd_create", "mmod_vd_destroy", "mmod_vd_set_model",
-            "mmod_vd_set_state", "mmod_vd_forward", "mmod_vd_set_kernel", "mmod_vd_uses_tma",
+            "mmod_vd_set_state", "mmod_vd_forward", "mmod_vd_set_kernel", "mmod_vd_uses_tma", "mmod_vd_set_option",
             "mmod_vd_last_loop_ms", "mmod_vd_last_launch_count", "mmod_vd_last_error", "mmod_vd_get_plan"]
 CKPT_FP32, CKPT_BF16, CKPT_FP16 = 0, 1, 2
 
@@ -132,6 +132,7 @@ def load():
         "mmod_vd_forward": ([P, P, P, P, P], I),
         "mmod_vd_set_kernel": ([P, I], I),
         "mmod_vd_uses_tma": ([P], I),
+        "mmod_vd_set_option": ([P, I, I], I),
         "mmod_vd_last_loop_ms": ([P], ctypes.c_float),
         "mmod_vd_last_launch_count": ([P], ctypes.c_longlong),
         "mmod_vd_last_error": ([P], ctypes.c_char_p),
@@ -540,6 +541,9 @@ class StaggeredPropagator:
 
     def set_kernel(self, kernel: int):
         self._check(load().mmod_vd_set_kernel(self.handle, kernel))
+
+    def set_option(self, option: int, value: int):
+        self._check(load().mmod_vd_set_option(self.handle, option, value))
 
     @property
     def uses_tma(self) -> bool:

@@ -13,11 +13,13 @@ from _gpu_util import rel_l2, torch_cuda
 pytestmark = pytest.mark.gpu
 
 
-def run_vd(p, kernel=M.KERNEL_AUTO, state=None):
+def run_vd(p, kernel=M.KERNEL_AUTO, state=None, pdl=None):
     torch = torch_cuda()
     prop = M.StaggeredPropagator.from_problem(p)
     if kernel != M.KERNEL_AUTO:
         prop.set_kernel(kernel)
+    if pdl is not None:
+        prop.set_option(M.OPT_PDL, pdl)
     prop.set_model(torch.from_numpy(np.ascontiguousarray(p.vel)).cuda(),
                    torch.from_numpy(np.ascontiguousarray(p.rho)).cuda())
     nsrc, nrec = len(p.src_ijk), len(p.rec_ijk)
@@ -109,6 +111,8 @@ def test_tma_kernels_are_bitwise_the_plain_kernels(shape, nbl, cpml):
     assert not prop_s.uses_tma
     assert np.array_equal(tr_t, tr_s)
     assert np.array_equal(st_t, st_s)
+    tr_n, st_n, _ = run_vd(p, pdl=1)           # with programmatic dependent launch
+    assert np.array_equal(tr_n, tr_s) and np.array_equal(st_n, st_s)
 
 
 def test_standing_wave_fp32():

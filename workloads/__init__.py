@@ -18,7 +18,7 @@ import numpy as np
 
 __all__ = ["Problem", "ricker", "cfl_dt", "small_homogeneous", "layered_240",
            "smooth_gradient_200", "batched_shots", "fractal_large", "tiny_problem",
-           "gardner_density", "layered_240_vd", "tiny_problem_vd"]
+           "gardner_density", "layered_240_vd", "tiny_problem_vd", "layered_vd_plain"]
 
 
 @dataclass
@@ -253,3 +253,24 @@ def tiny_problem_vd(shape=(11, 10, 12), nt: int = 30, nbl: int = 2, seed: int = 
     p.rho = rng.uniform(1000.0, 2600.0, size=shape).astype(np.float32)
     p.name = p.name.replace("tiny", "tiny-vd")
     return p
+
+
+def layered_vd_plain(nt: int = 100, n: int = 512) -> Problem:
+    """n^3, h = 10 m, L = 20: the four flat layers of layered_240 (interfaces
+    drawn by seed 1 in [L+10, n-L-10]) without the smoothed perturbations,
+    density by Gardner's rule without perturbation (cheap to build at large
+    n).  dt from CFL 0.4; Ricker 10 Hz at (n/2, n/2, 4); receivers on every
+    (i, j) of plane k = 0 with stride 4."""
+    L = 20
+    rng = np.random.default_rng(1)
+    depths = np.sort(rng.choice(np.arange(L + 10, n - L - 10 + 1), size=3, replace=False))
+    layer_v = np.array([1500.0, 2200.0, 3000.0, 4500.0])
+    vz = layer_v[np.searchsorted(depths, np.arange(n), side="right")]
+    vel32 = np.ascontiguousarray(np.broadcast_to(vz[:, None, None].astype(np.float32), (n, n, n)))
+    rz = (310.0 * vz ** 0.25).astype(np.float32)
+    rho32 = np.ascontiguousarray(np.broadcast_to(rz[:, None, None], (n, n, n)))
+    h = (10.0, 10.0, 10.0)
+    dt = cfl_dt(0.4, h, 4500.0)
+    src = np.array([[n // 2, n // 2, 4]], np.int32)
+    return Problem(f"layered-vd-plain-{n}^3", vel32, h, dt, nt, L, src, ricker(10.0, dt, nt)[None, :],
+                   surface_grid(n, n, 0, stride=4), rho=rho32, meta={"cfl": 0.4, "interfaces": depths.tolist()})
