@@ -115,16 +115,41 @@ class ClockSampler:
                 "samples": len(rows), "power_w_max": max(r[2] for r in rows), "reasons": reasons}
 
 
-def oracle_sample(p, seconds_target=20.0, max_steps=None):
-    """Time the FP64 oracle on the host cores on the first steps of the workload."""
+PAPER_CONTEXT = {"value": 240 ** 3 * 300 / 30.47 / 1e9, "unit": UNIT,
+                 "what": "the paper's sequential example run (acoustic_iso_cd, 240^3, 20 m, 300 steps, "
+                         "Time Kernel 30.47 s, one thread, hardware not stated, FP32; Sec. 5.3): context, "
+                         "a different configuration, not a baseline"}
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+_ALL_THREADS = None
+
+
+def oracle_sample(p, seconds_target=20.0, max_steps=None, nthreads=0):
+    """Time the FP64 oracle on the host cores on the first steps of the workload
+    (nthreads 0: every core)."""
     import oracle
+    global _ALL_THREADS
     oracle.build()
-    threads = oracle.max_threads()
+    if _ALL_THREADS is None:   # before any single-thread run changes the OpenMP default
+        _ALL_THREADS = oracle.max_threads()
+    threads = nthreads or _ALL_THREADS
     npts = p.npoints
     def run(n):
         t0 = time.perf_counter()
         oracle.forward(p.vel, p.h, p.dt, n, nbl=p.nbl, src_ijk=p.src_ijk, wavelet=p.wavelet[:, :n],
-                       rec_ijk=p.rec_ijk)
+                       rec_ijk=p.rec_ijk, nthreads=threads)
         return time.perf_counter() - t0
 
     # per-step time from the difference of two short runs (set-up cancels)
@@ -135,9 +160,10 @@ def oracle_sample(p, seconds_target=20.0, max_steps=None):
         steps = min(steps, max_steps)
     t0 = time.perf_counter()
     oracle.forward(p.vel, p.h, p.dt, steps, nbl=p.nbl, src_ijk=p.src_ijk, wavelet=p.wavelet[:, :steps],
-                   rec_ijk=p.rec_ijk)
+                   rec_ijk=p.rec_ijk, nthreads=threads)
     dt = time.perf_counter() - t0
     return {"value": npts * steps / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "cpu": cpu_model(),
             "sample": f"{p.name}: first {steps} of {p.nt} steps, FP64, OpenMP {threads} threads, "
                       f"{dt:.1f} s"}, dt, steps
 
@@ -306,6 +332,9 @@ def run_mmod(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu, _, _ = oracle_sample(p, seconds_target=args.ref_seconds)
+        one, _, _ = oracle_sample(p, seconds_target=min(args.ref_seconds, 8.0), nthreads=1)
+        cpu["single_thread"] = {"value": one["value"], "sample": one["sample"]}
+        cpu["paper_context"] = PAPER_CONTEXT
     clocks = clk.summary()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
