@@ -73,7 +73,7 @@ class Oracle:
         lib.orc_optimized_coeffs.argtypes = [I, D, I, P]
         lib.orc_forward_cpml.argtypes = [I, I, I, D, D, D, D, I, I, D, D, P, I, P, P, I, P, P, P, I, I]
         lib.orc_staggered_coeffs.argtypes = [I, P]
-        lib.orc_forward_vd.argtypes = [I, I, I, D, D, D, D, I, I, D, I, D, P, P, I, P, P, I, P, P, P, P, I]
+        lib.orc_forward_vd.argtypes = [I, I, I, D, D, D, D, I, I, D, I, D, P, P, I, P, P, I, P, P, P, P, I, I]
         lib.orc_max_threads.argtypes = []
         lib.orc_adjoint.argtypes = [I, I, I, D, D, D, D, I, I, I, D, P, I, P, I, P, P, P, I, I]
         lib.orc_gradient.argtypes = [I, I, I, D, D, D, D, I, I, I, D, P, I, P, P, I, P, P, P, I, I]
@@ -195,9 +195,10 @@ class Oracle:
         return out
 
     def forward_vd(self, vel, rho, h, dt, nt, *, nbl=0, refl=1e-3, cpml=False, f0=0.0, src_ijk=None,
-                   wavelet=None, rec_ijk=None, state0=None, want_state=False, nthreads=0):
+                   wavelet=None, rec_ijk=None, state0=None, want_state=False, nthreads=0, free_surface=False):
         """Reading R18: variable-density first-order system on the staggered
-        grid (order 8), damping layers or (cpml) CPML layers.
+        grid (order 8), damping layers or (cpml) CPML layers, optionally a
+        free surface at k = 0.
 
         vel, rho: [nz][ny][nx] float32.  state0: optional [4][nz][ny][nx]
         (p^0, vx, vy, vz at -1/2).  Returns traces [nt][nrec] (p^{n+1} at the
@@ -220,7 +221,7 @@ class Oracle:
         rc = self.lib.orc_forward_vd(nx, ny, nz, h[0], h[1], h[2], dt, nt, nbl, refl, int(bool(cpml)), f0,
                                      _ptr(vel), _ptr(rho), nsrc, _ptr(src) if nsrc else None, _ptr(wav),
                                      nrec, _ptr(rec) if nrec else None, _ptr(traces) if nrec else None,
-                                     _ptr(s0), _ptr(so), nthreads)
+                                     _ptr(s0), _ptr(so), nthreads, int(bool(free_surface)))
         if rc != 0:
             raise ValueError(f"orc_forward_vd -> {rc}")
         return (traces, so) if want_state else traces

@@ -64,7 +64,8 @@
  *       "acoustic_iso" on a staggered Yee grid): p at the grid points, the
  *       particle-velocity components half a cell along their axes, leapfrog
  *       with the velocities at half steps, order-8 staggered weights, damping
- *       or CPML layers; stated in full before orc_forward_vd.
+ *       or CPML layers, optionally the free surface (p odd and v_z even
+ *       about k = 0); stated in full before orc_forward_vd.
  *
  * Index convention: i along x (fastest), j along y, k along z (depth, k = 0 at
  * the surface); user arrays are [nz][ny][nx].
@@ -824,10 +825,10 @@ int orc_staggered_coeffs(int order, double *a)
 
 /* Depth into the layers (cells) of the continuous position x on an axis of
  * n points with L-cell layers, capped at L. */
-static double layer_depth(double x, int n, int L)
+static double layer_depth(double x, int n, int L, int top_free)
 {
     double d = 0.0;
-    if (L - x > d) d = L - x;
+    if (!top_free && L - x > d) d = L - x;
     if (x - (n - 1 - L) > d) d = x - (n - 1 - L);
     return d > L ? (double)L : d;
 }
@@ -835,12 +836,12 @@ static double layer_depth(double x, int n, int L)
 /* Profiles of one axis at the grid points (half = 0) or the half points
  * i + 1/2 (half = 1): damping eta, or the CPML pair B, G. */
 static void vd_profile(int n, int L, double h, double vmax, double refl, double f0, double dt, int half,
-                       double *eta, double *B, double *G)
+                       int top_free, double *eta, double *B, double *G)
 {
     const double d0 = L > 0 ? 3.0 * vmax * log(1.0 / refl) / (2.0 * L * h) : 0.0;
     const double pi = 3.14159265358979323846;
     for (int i = 0; i < n; ++i) {
-        const double x = L > 0 ? layer_depth(i + 0.5 * half, n, L) : 0.0;
+        const double x = L > 0 ? layer_depth(i + 0.5 * half, n, L, top_free) : 0.0;
         const double s = L > 0 ? x / L : 0.0;
         const double d = d0 * s * s;
         eta[i] = d;
@@ -851,20 +852,46 @@ static void vd_profile(int n, int L, double h, double vmax, double refl, double 
     }
 }
 
+/* Free surface of the staggered system (reading R18 with the surface option
+ * of Sec. 3, as reading R15): p = 0 on the plane k = 0.  Above it p and the
+ * horizontal velocities are odd images, p(-m) = -p(m); v_z, which sits at
+ * the half points k + 1/2, is an even image, v_z(-m) = v_z(m - 1) (index -m
+ * is the position -m + 1/2, the mirror of m - 1/2).  Only p is read across
+ * the surface by the velocity update and only v_z by the pressure update. */
+static void vd_mirror_p(const grid_t *g, double *p)
+{
+    for (int m = 1; m <= g->R && m < g->nz; ++m)
+        for (int j = -g->R; j < g->ny + g->R; ++j)
+            for (int i = -g->R; i < g->nx + g->R; ++i)
+                p[at(g, i, j, -m)] = -p[at(g, i, j, m)];
+}
+
+static void vd_mirror_vz(const grid_t *g, double *vz)
+{
+    for (int m = 1; m <= g->R && m - 1 < g->nz; ++m)
+        for (int j = -g->R; j < g->ny + g->R; ++j)
+            for (int i = -g->R; i < g->nx + g->R; ++i)
+                vz[at(g, i, j, -m)] = vz[at(g, i, j, m - 1)];
+}
+
 /* Forward run of reading R18 (order 8).
  * vel, rho   [nz][ny][nx] FP32 (m/s, kg/m^3)
  * cpml       0: damping layers, 1: CPML with frequency shift alpha_max = pi f0
  * state0     optional [4][nz][ny][nx] initial p^0, vx, vy, vz at -1/2 (NULL = 0)
  * state_out  optional final p^{nt}, vx, vy, vz at nt - 1/2
- * traces     [nt][nrec] FP64: p^{n+1} at the receivers. */
+ * traces     [nt][nrec] FP64: p^{n+1} at the receivers.
+ * free_surface  1: p = 0 on k = 0 (images above it), no top layer; the
+ *            plane k = 0 of p is set to 0 after every step (sources there
+ *            vanish, receivers read 0) and in the initial state. */
 int orc_forward_vd(int nx, int ny, int nz, double hx, double hy, double hz,
                    double dt, int nt, int nbl, double refl, int cpml, double f0,
                    const float *vel, const float *rho,
                    int nsrc, const int *src_ijk, const float *wavelet,
                    int nrec, const int *rec_ijk, double *traces,
-                   const double *state0, double *state_out, int nthreads)
+                   const double *state0, double *state_out, int nthreads, int free_surface)
 {
     const int R = 4;
+    if (free_surface && nz <= R) return -1;
     if (nx < 1 || ny < 1 || nz < 1 || nt < 0 || dt <= 0 || !vel || !rho || f0 < 0) return -1;
     if (hx <= 0 || hy <= 0 || hz <= 0 || (cpml != 0 && cpml != 1)) return -1;
     if (2 * nbl > nx || 2 * nbl > ny || 2 * nbl > nz || nbl < 0) return -1;
@@ -908,7 +935,8 @@ int orc_forward_vd(int nx, int ny, int nz, double hx, double hy, double hz,
     if (rc) goto done;
     for (int a = 0; a < 3; ++a)
         for (int s = 0; s < 2; ++s)
-            vd_profile(n3[a], nbl, hh[a], vmax, refl, f0, dt, s, prof[a][s][0], prof[a][s][1], prof[a][s][2]);
+            vd_profile(n3[a], nbl, hh[a], vmax, refl, f0, dt, s, a == 2 && free_surface, prof[a][s][0],
+                       prof[a][s][1], prof[a][s][2]);
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
@@ -931,7 +959,9 @@ int orc_forward_vd(int nx, int ny, int nz, double hx, double hy, double hz,
                     bh[a][o] = idx[a] + 1 < n3[a] ? 0.5 * (Bc[o] + Bc[o + stride[a]]) : Bc[o];
             }
     const double cell = hx * hy * hz;
+    if (free_surface) zero_top(&g, p);
     for (int n = 0; n < nt; ++n) {
+        if (free_surface) vd_mirror_p(&g, p);
         /* particle velocities at n + 1/2 from p^n */
         #pragma omp parallel for collapse(2) schedule(static)
         for (int k = 0; k < nz; ++k)
@@ -959,6 +989,7 @@ int orc_forward_vd(int nx, int ny, int nz, double hx, double hy, double hz,
                         }
                     }
                 }
+        if (free_surface) vd_mirror_vz(&g, v[2]);
         /* pressure at n + 1 from the velocities at n + 1/2 */
         #pragma omp parallel for collapse(2) schedule(static)
         for (int k = 0; k < nz; ++k)
@@ -994,6 +1025,7 @@ int orc_forward_vd(int nx, int ny, int nz, double hx, double hy, double hz,
             const double e = cpml ? 0.0 : dt * (prof[0][0][0][q[0]] + prof[1][0][0][q[1]] + prof[2][0][0][q[2]]);
             p[o] += dt * K[o] * (double)wavelet[(long)s * nt + n] / (cell * (1.0 + 0.5 * e));
         }
+        if (free_surface) zero_top(&g, p);
         for (int r = 0; r < nrec; ++r) {
             const int *q = rec_ijk + 3 * r;
             traces[n * (long)nrec + r] = p[at(&g, q[0], q[1], q[2])];

@@ -79,6 +79,12 @@ def _vd_standing(orc):
     VD.test_standing_wave_is_exact(orc)
 
 
+def _vd_fs(orc):
+    VD.test_standing_wave_with_free_surface_is_exact(orc)
+    VD.test_energy_conserved_with_free_surface(orc)
+    VD.test_dense_stepper_with_free_surface(orc, (11, 10, 12), 2, False)
+
+
 def _grad(orc):
     for kind in ("point", "smooth", "source"):
         AD.test_gradient_matches_finite_differences(orc, kind)
@@ -132,6 +138,12 @@ MUTATIONS = [
     ("VD source outside the (1 + e/2) division", "(double)wavelet[(long)s * nt + n] / (cell * (1.0 + 0.5 * e));",
      "(double)wavelet[(long)s * nt + n] / cell;", [_vd_dense]),
     ("VD CPML drops the pressure-gradient memory", "dp += psi[a][o];", "dp += 0.0 * psi[a][o];", [_vd_dense]),
+    ("VD surface: v_z mirrored odd", "vz[at(g, i, j, -m)] = vz[at(g, i, j, m - 1)];",
+     "vz[at(g, i, j, -m)] = -vz[at(g, i, j, m - 1)];", [_vd_fs]),
+    ("VD surface: v_z mirrored without the half-cell shift", "vz[at(g, i, j, -m)] = vz[at(g, i, j, m - 1)];",
+     "vz[at(g, i, j, -m)] = vz[at(g, i, j, m)];", [_vd_fs]),
+    ("VD surface: p mirrored even", "p[at(g, i, j, -m)] = -p[at(g, i, j, m)];",
+     "p[at(g, i, j, -m)] = p[at(g, i, j, m)];", [_vd_fs]),
 ]
 
 

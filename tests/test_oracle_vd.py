@@ -219,20 +219,20 @@ def test_energy_conserved_without_layers(orc):
         assert e == pytest.approx(e_ref, rel=1e-11), nt
 
 
-def _layer_depth(x, n, L):
-    return min(max(L - x, x - (n - 1 - L), 0.0), float(L))
+def _layer_depth(x, n, L, top_free=False):
+    return min(max(0.0 if top_free else L - x, x - (n - 1 - L), 0.0), float(L))
 
 
-def _eta(n, L, h, vmax, refl=1e-3, half=False):
+def _eta(n, L, h, vmax, refl=1e-3, half=False, top_free=False):
     d0 = 3 * vmax * np.log(1 / refl) / (2 * L * h) if L else 0.0
-    return np.array([d0 * (_layer_depth(i + 0.5 * half, n, L) / L) ** 2 if L else 0.0 for i in range(n)])
+    return np.array([d0 * (_layer_depth(i + 0.5 * half, n, L, top_free) / L) ** 2 if L else 0.0 for i in range(n)])
 
 
-def _eta3(shape, L, h, vmax, half_axis=None):
+def _eta3(shape, L, h, vmax, half_axis=None, fs=False):
     nz, ny, nx = shape
     ex = _eta(nx, L, h[0], vmax, half=half_axis == 0)
     ey = _eta(ny, L, h[1], vmax, half=half_axis == 1)
-    ez = _eta(nz, L, h[2], vmax, half=half_axis == 2)
+    ez = _eta(nz, L, h[2], vmax, half=half_axis == 2, top_free=fs)
     return ez[:, None, None] + ey[None, :, None] + ex[None, None, :]
 
 
@@ -302,13 +302,13 @@ def _kron_axis(D1, shape, axis):
     return np.kron(D1, np.kron(Iy, Ix))
 
 
-def _cpml_bg(n, L, h, vmax, refl, f0, dt, half):
+def _cpml_bg(n, L, h, vmax, refl, f0, dt, half, top_free=False):
     B, G = np.ones(n), np.zeros(n)
     if L == 0:
         return B, G
     d0 = 3 * vmax * np.log(1 / refl) / (2 * L * h)
     for i in range(n):
-        x = _layer_depth(i + 0.5 * half, n, L)
+        x = _layer_depth(i + 0.5 * half, n, L, top_free)
         if x == 0:
             continue
         s = x / L
@@ -318,15 +318,42 @@ def _cpml_bg(n, L, h, vmax, refl, f0, dt, half):
     return B, G
 
 
-def _bg3(shape, L, h, vmax, refl, f0, dt, axis, half):
+def _bg3(shape, L, h, vmax, refl, f0, dt, axis, half, fs=False):
     n = shape[2 - axis]
-    B, G = _cpml_bg(n, L, h[axis], vmax, refl, f0, dt, half)
+    B, G = _cpml_bg(n, L, h[axis], vmax, refl, f0, dt, half, top_free=fs and axis == 2)
     sh = [1, 1, 1]
     sh[2 - axis] = n
     return np.broadcast_to(B.reshape(sh), shape).ravel(), np.broadcast_to(G.reshape(sh), shape).ravel()
 
 
-def dense_vd(vel, rho, h, dt, nt, nbl, src, wav, rec, cpml=False, f0=0.0, refl=1e-3):
+def _dplus1_fs(n, h):
+    """D+ along z with the odd image of p above k = 0 (p(-q) = -p(q), p(0) = 0)."""
+    D = np.zeros((n, n))
+    for i in range(n):
+        for m, a in enumerate(A8, start=1):
+            for q, sgn in ((i + m, 1.0), (i - m + 1, -1.0)):
+                if q >= n or q == 0:
+                    continue
+                if q > 0:
+                    D[i, q] += sgn * float(a) / h
+                else:
+                    D[i, -q] -= sgn * float(a) / h
+    return D
+
+
+def _dminus1_fs(n, h):
+    """D- along z with the even image of v_z above k = 0 (v_z(-q) = v_z(q - 1))."""
+    D = np.zeros((n, n))
+    for i in range(n):
+        for m, a in enumerate(A8, start=1):
+            for q, sgn in ((i + m - 1, 1.0), (i - m, -1.0)):
+                if q >= n:
+                    continue
+                D[i, q if q >= 0 else -q - 1] += sgn * float(a) / h
+    return D
+
+
+def dense_vd(vel, rho, h, dt, nt, nbl, src, wav, rec, cpml=False, f0=0.0, refl=1e-3, fs=False):
     shape = vel.shape
     N = vel.size
     v64, r64 = vel.astype(np.float64).ravel(), rho.astype(np.float64).ravel()
@@ -334,11 +361,17 @@ def dense_vd(vel, rho, h, dt, nt, nbl, src, wav, rec, cpml=False, f0=0.0, refl=1
     bh = [b.ravel() for b in _bh(rho)]
     Dp = [_kron_axis(_dplus1(shape[2 - a], h[a]), shape, a) for a in range(3)]
     Dm = [_kron_axis(_dminus1(shape[2 - a], h[a]), shape, a) for a in range(3)]
+    if fs:
+        Dp[2] = _kron_axis(_dplus1_fs(shape[0], h[2]), shape, 2)
+        Dm[2] = _kron_axis(_dminus1_fs(shape[0], h[2]), shape, 2)
+    top = np.zeros(shape, bool)
+    top[0] = fs
+    top = top.ravel()
     vmax = float(vel.max())
-    e_p = (dt * _eta3(shape, nbl, h, vmax)).ravel()
-    e_v = [(dt * _eta3(shape, nbl, h, vmax, half_axis=a)).ravel() for a in range(3)]
-    Bh = [_bg3(shape, nbl, h, vmax, refl, f0, dt, a, 1) for a in range(3)]
-    Bg = [_bg3(shape, nbl, h, vmax, refl, f0, dt, a, 0) for a in range(3)]
+    e_p = (dt * _eta3(shape, nbl, h, vmax, fs=fs)).ravel()
+    e_v = [(dt * _eta3(shape, nbl, h, vmax, half_axis=a, fs=fs)).ravel() for a in range(3)]
+    Bh = [_bg3(shape, nbl, h, vmax, refl, f0, dt, a, 1, fs) for a in range(3)]
+    Bg = [_bg3(shape, nbl, h, vmax, refl, f0, dt, a, 0, fs) for a in range(3)]
     p = np.zeros(N)
     v = [np.zeros(N) for _ in range(3)]
     psi = [np.zeros(N) for _ in range(3)]
@@ -369,6 +402,7 @@ def dense_vd(vel, rho, h, dt, nt, nbl, src, wav, rec, cpml=False, f0=0.0, refl=1
             o = lin(q)
             e = 0.0 if cpml else e_p[o]
             p[o] += dt * K[o] * float(wav[s, n]) / (cell * (1 + 0.5 * e))
+        p[top] = 0.0
         for r, q in enumerate(rec):
             tr[n, r] = p[lin(q)]
     return tr, p.reshape(shape), [x.reshape(shape) for x in v]
@@ -575,3 +609,124 @@ def test_long_run_decays(orc, cpml):
     assert window[0] > 0
     assert window[-1] < 1e-2 * window[0]
     assert window[-1] < window[5] < window[2]
+
+
+# ---------------------------------------------------------------------------
+# free surface (p = 0 on k = 0: p odd, v_z even about the surface)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("cpml", [False, True])
+@pytest.mark.parametrize("shape,nbl", [((11, 10, 12), 2), ((10, 12, 9), 3), ((9, 9, 10), 0)])
+def test_dense_stepper_with_free_surface(orc, shape, nbl, cpml):
+    nt = 40
+    vel, rho, h, dt, src, wav, rec = _tiny_vd(shape, nt, nbl, seed=sum(shape) + 7 * nbl)
+    src[0] = [1, 1, 0]                    # on the surface: vanishes
+    src[2] = [shape[2] // 2, 2, 1]        # just below it
+    rec[3] = [0, shape[1] - 1, 0]         # on the surface: reads 0
+    tr_o, st_o = orc.forward_vd(vel, rho, h, dt, nt, nbl=nbl, cpml=cpml, f0=12.0, src_ijk=src, wavelet=wav,
+                                rec_ijk=rec, want_state=True, free_surface=True)
+    tr_d, p_d, v_d = dense_vd(vel, rho, h, dt, nt, nbl, src, wav, rec, cpml=cpml, f0=12.0, fs=True)
+    assert np.max(np.abs(tr_o - tr_d)) < 1e-12 * np.max(np.abs(tr_d))
+    assert np.max(np.abs(st_o[0] - p_d)) < 1e-12 * np.max(np.abs(p_d))
+    for a in range(3):
+        assert np.max(np.abs(st_o[1 + a] - v_d[a])) < 1e-12 * np.max(np.abs(v_d[a]))
+    assert not tr_o[:, 3].any() and not st_o[0][0].any()
+
+
+def test_standing_wave_with_free_surface_is_exact(orc):
+    """p = P_n cos(kx x) cos(ky y) sin(kz z) vanishes on z = 0 and has the
+    images' parity, so the discrete standing wave is exact up to the surface."""
+    shape = (60, 70, 74)
+    h = (10.0, 12.0, 9.0)
+    v, rho = 2200.0, 1800.0
+    dt = 0.9e-3
+    K, b = rho * v * v, 1.0 / rho
+    k = np.array([2 * np.pi / 97.0, 2 * np.pi / 61.0, 2 * np.pi / 143.0])
+    sx, sy = 0.3, 1.1
+    S = np.array([_S(k[a], h[a]) for a in range(3)])
+    nz, ny, nx = shape
+    x, y, z = np.arange(nx) * h[0], np.arange(ny) * h[1], np.arange(nz) * h[2]
+
+    def prod(fz, fy, fx):
+        return fz[:, None, None] * fy[None, :, None] * fx[None, None, :]
+
+    cx, cy = np.cos(k[0] * x + sx), np.cos(k[1] * y + sy)
+    phi = prod(np.sin(k[2] * z), cy, cx)
+    psi_x = prod(np.sin(k[2] * z), cy, np.sin(k[0] * (x + 0.5 * h[0]) + sx))
+    psi_y = prod(np.sin(k[2] * z), np.sin(k[1] * (y + 0.5 * h[1]) + sy), cx)
+    psi_z = prod(np.cos(k[2] * (z + 0.5 * h[2])), cy, cx)
+    # D+ of cos -> -S sin, of sin -> +S cos; D- of sin -> +S cos, of cos -> -S sin
+    sgn = np.array([1.0, 1.0, -1.0])
+    V0 = 0.5 * dt * b * S * sgn
+    st = np.stack([phi, V0[0] * psi_x, V0[1] * psi_y, V0[2] * psi_z])
+    nsteps = 4
+    _, out = orc.forward_vd(np.full(shape, v, np.float32), np.full(shape, rho, np.float32), h, dt, nsteps,
+                            state0=st, want_state=True, free_surface=True)
+    P, V = 1.0, V0.copy()
+    for _ in range(nsteps):
+        V = V - dt * b * S * sgn * P
+        P = P + dt * K * float(np.dot(S * sgn, V))
+    wdt = 2 * np.arcsin(0.5 * dt * v * np.linalg.norm(S))
+    assert P == pytest.approx(np.cos(nsteps * wdt), rel=1e-12)
+    m = 7 * nsteps + 1
+    near = (slice(0, nz - m), slice(m, -m), slice(m, -m))     # up to and including the surface
+    assert np.max(np.abs(out[0] - P * phi)[near]) < 1e-12
+    fields = [psi_x, psi_y, psi_z]
+    for a in range(3):
+        assert np.max(np.abs(out[1 + a] - V[a] * fields[a])[near]) < 1e-12 * abs(V0[a]) / 1e-3 + 1e-18
+    # the odd image matters: without the surface the same start is not exact there
+    _, plain = orc.forward_vd(np.full(shape, v, np.float32), np.full(shape, rho, np.float32), h, dt, nsteps,
+                              state0=st, want_state=True)
+    assert np.max(np.abs(plain[0] - P * phi)[near]) > 1e-6
+
+
+def test_energy_conserved_with_free_surface(orc):
+    rng = np.random.default_rng(23)
+    shape = (18, 20, 22)
+    h = (10.0, 9.0, 11.0)
+    vel, rho = _rand_model(rng, shape)
+    dt = W.cfl_dt(0.3, h, 3500.0)
+    K = rho.astype(np.float64) * vel.astype(np.float64) ** 2
+    bh = _bh(rho)
+    st = rng.standard_normal((4,) + shape)
+    st[0] *= 1e6
+    st[0][0] = 0.0
+    e_ref = None
+    for nt in (0, 37, 400):
+        _, s_n = orc.forward_vd(vel, rho, h, dt, nt, state0=st, want_state=True, free_surface=True)
+        _, s_n1 = orc.forward_vd(vel, rho, h, dt, 1, state0=s_n, want_state=True, free_surface=True)
+        e = _energy(s_n[0], s_n1[1:], s_n[1:], K, bh)
+        if e_ref is None:
+            e_ref = e
+        assert e == pytest.approx(e_ref, rel=1e-11), nt
+
+
+@pytest.mark.slow
+def test_green_function_with_free_surface(orc):
+    """Homogeneous medium with the surface: the direct field minus the field
+    of the image source mirrored across z = 0."""
+    n, h, v, f, dt, rho = 100, 10.0, 1500.0, 10.0, 1e-3, 1800.0
+    nt = 500
+    s0, zs = n // 2, 12
+    src = np.array([[s0, s0, zs]], np.int32)
+    offs = [(15, 0, -8), (0, -20, -10), (12, 12, 6), (-14, 0, -11)]
+    rec = np.array([[s0 + a, s0 + b, zs + c] for a, b, c in offs], np.int32)
+    w = W.ricker(f, dt, nt)
+    tr = orc.forward_vd(np.full((n, n, n), v, np.float32), np.full((n, n, n), rho, np.float32), (h, h, h), dt, nt,
+                        src_ijk=src, wavelet=w[None, :], rec_ijk=rec, free_surface=True)
+    t = (np.arange(nt) + 1) * dt
+    for i, (a, b, c) in enumerate(offs):
+        pos = np.array([s0 + a, s0 + b, zs + c], float)
+        r = h * np.linalg.norm([a, b, c])
+        ri = h * np.linalg.norm([a, b, zs + c + zs])
+        # reflections off the zero cells beyond the other five faces
+        t_wall = np.inf
+        for ax in range(3):
+            for wall in ((-1, n) if ax < 2 else (n,)):
+                img = np.array([s0, s0, zs], float)
+                img[ax] = 2 * wall - img[ax]
+                t_wall = min(t_wall, h * np.linalg.norm(img - pos) / v)
+        keep = t < t_wall - 3 * dt
+        exact = _exact_direct(t, r, v, f, dt, rho) - _exact_direct(t, ri, v, f, dt, rho)
+        err = np.linalg.norm((tr[:, i] - exact)[keep]) / np.linalg.norm(exact[keep])
+        assert err < 0.03, (offs[i], err)
