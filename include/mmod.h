@@ -408,8 +408,13 @@ mmod_status mmod_batch_autotune(mmod_batch *b, int steps, mmod_stream stream, in
  * CPML instead: each derivative gains a memory variable m = B m + G D on its
  * axis's layers (B = exp(-(d + alpha) dt), G = d (B - 1) / (d + alpha), the
  * profiles of the CPML above at the continuous depth into the layer), and
- * e = 0.  Order 8 only; no free surface (UNSUPPORTED).  All pointers are
- * DEVICE pointers (ARG otherwise).  Streams, errors and latching as above.
+ * e = 0.  cfg->free_surface = 1: p = 0 on the plane k = 0 (the paper's
+ * surface option), imposed through images above it, the odd image
+ * p(-m) = -p(m) and for v_z, which sits at the half points, the even image
+ * v_z(-m) = v_z(m - 1); no top layer; sources on the plane do nothing and
+ * receivers there read 0; needs nz >= 5 (ARG otherwise).  Order 8 only
+ * (UNSUPPORTED otherwise).  All pointers are DEVICE pointers (ARG
+ * otherwise).  Streams, errors and latching as above.
  *
  * mmod_vd_create: as mmod_create; allocates p, vx, vy, vz, dt K, dt / rho
  *   (6 padded volumes; 12 with CPML).  Message: mmod_vd_last_error(NULL).
@@ -419,7 +424,8 @@ mmod_status mmod_batch_autotune(mmod_batch *b, int steps, mmod_stream stream, in
  *   largest magnitude), veff^2 = max over points of rho v^2 / min(rho over
  *   the point and its six neighbours).
  * mmod_vd_set_state: the next forward starts from state [4][nz][ny][nx] =
- *   p^0, vx, vy, vz at -1/2 (NULL: zeros) instead of zeros.
+ *   p^0, vx, vy, vz at -1/2 (NULL: zeros) instead of zeros (with a free
+ *   surface the plane k = 0 of p is set to 0).
  * mmod_vd_forward: nt steps; wavelet [nsrc][nt], traces [nt][nrec],
  *   final_state [4][nz][ny][nx] (p^{nt}, velocities at nt - 1/2; may be NULL).
  * mmod_vd_set_kernel: MMOD_KERNEL_AUTO / MMOD_KERNEL_TMA (the TMA-pipelined

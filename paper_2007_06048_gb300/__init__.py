@@ -504,7 +504,7 @@ class StaggeredPropagator:
     mmod_vd_create / mmod_vd_set_model / mmod_vd_forward.  Device tensors only."""
 
     def __init__(self, shape, h, dt, nt, *, nbl=0, src_ijk=None, rec_ijk=None, damp_R=1e-3,
-                 device=0, cpml=False, cpml_f0=0.0):
+                 device=0, cpml=False, cpml_f0=0.0, free_surface=False):
         nz, ny, nx = shape
         self.shape = tuple(shape)
         self.nt = int(nt)
@@ -512,7 +512,7 @@ class StaggeredPropagator:
         rec = np.zeros((0, 3), np.int32) if rec_ijk is None else np.ascontiguousarray(rec_ijk, np.int32).reshape(-1, 3)
         self.nsrc, self.nrec = len(src), len(rec)
         self.device = device
-        cfg = _config(nx, ny, nz, h, dt, nt, nbl, src, rec, 8, damp_R, False, cpml, cpml_f0)
+        cfg = _config(nx, ny, nz, h, dt, nt, nbl, src, rec, 8, damp_R, free_surface, cpml, cpml_f0)
         out = ctypes.c_void_p()
         st = load().mmod_vd_create(ctypes.byref(cfg), device, ctypes.byref(out))
         if st != 0:
@@ -522,7 +522,7 @@ class StaggeredPropagator:
     @classmethod
     def from_problem(cls, p, device=0):
         return cls(p.vel.shape, p.h, p.dt, p.nt, nbl=p.nbl, src_ijk=p.src_ijk, rec_ijk=p.rec_ijk,
-                   damp_R=p.refl, device=device, cpml=p.cpml, cpml_f0=p.cpml_f0)
+                   damp_R=p.refl, device=device, cpml=p.cpml, cpml_f0=p.cpml_f0, free_surface=p.free_surface)
 
     def _check(self, st):
         if st != 0:

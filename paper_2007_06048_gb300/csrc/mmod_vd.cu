@@ -17,7 +17,9 @@
 // profile, centred: x <- [(1 - eps) x + dt (...)] / (1 + eps), eps = dt eta / 2
 // at each field's own position) or CPML (one memory variable per derivative
 // in its axis's layers, recursive convolution m = B m + G D).  Receivers
-// record p^{n+1} after the injection of step n.
+// record p^{n+1} after the injection of step n.  Free surface (option): p = 0
+// on the plane k = 0; above it p is the odd image p(-m) = -p(m) and v_z (at
+// the half points) the even image v_z(-m) = v_z(m - 1); no top layer.
 //
 // Kernels.  Both step kernels give a CTA a 64 x 16 x-y tile and a range of
 // planes; one elected thread streams planes into shared-memory rings with
@@ -58,6 +60,7 @@ struct VdArgs {
     long long plane;
     int nbl;
     int cpml;
+    int fs;                    // free surface at k = 0
     float w[3][kRadius];       // a_m / h_a
     float *p;                  // pressure (padded)
     float *v[3];               // velocities (padded)
@@ -138,6 +141,18 @@ __device__ __forceinline__ float at_or0(const float *f, const VdArgs &a, int i, 
     return in ? f[(long long)k * a.plane + (long long)j * a.nxp + i] : 0.0f;
 }
 
+// p above a free surface: the odd image; v_z: the even image shifted by the
+// half cell, v_z(-m) = v_z(m - 1).
+__device__ __forceinline__ float p_at(const VdArgs &a, int i, int j, int k) {
+    if (a.fs && k < 0) return -at_or0(a.p, a, i, j, -k);
+    return at_or0(a.p, a, i, j, k);
+}
+
+__device__ __forceinline__ float vz_at(const VdArgs &a, int i, int j, int k) {
+    if (a.fs && k < 0) return at_or0(a.v[2], a, i, j, -k - 1);
+    return at_or0(a.v[2], a, i, j, k);
+}
+
 __global__ void vd_velocity_simple(VdArgs a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z;
@@ -155,8 +170,8 @@ __global__ void vd_velocity_simple(VdArgs a) {
         const int di = ax == 0, dj = ax == 1, dk = ax == 2;
         float h[kRadius], l[kRadius];
         for (int m = 1; m <= kRadius; ++m) {
-            h[m - 1] = at_or0(a.p, a, i + m * di, j + m * dj, k + m * dk);
-            l[m - 1] = at_or0(a.p, a, i - (m - 1) * di, j - (m - 1) * dj, k - (m - 1) * dk);
+            h[m - 1] = p_at(a, i + m * di, j + m * dj, k + m * dk);
+            l[m - 1] = p_at(a, i - (m - 1) * di, j - (m - 1) * dj, k - (m - 1) * dk);
         }
         float d = stag_diff(a.w[ax], h[0], l[0], h[1], l[1], h[2], l[2], h[3], l[3]);
         const bool nxt = idx[ax] + 1 < n3[ax];
@@ -188,8 +203,13 @@ __global__ void vd_pressure_simple(VdArgs a) {
         const int di = ax == 0, dj = ax == 1, dk = ax == 2;
         float h[kRadius], l[kRadius];
         for (int m = 1; m <= kRadius; ++m) {
-            h[m - 1] = at_or0(a.v[ax], a, i + (m - 1) * di, j + (m - 1) * dj, k + (m - 1) * dk);
-            l[m - 1] = at_or0(a.v[ax], a, i - m * di, j - m * dj, k - m * dk);
+            if (ax == 2) {
+                h[m - 1] = vz_at(a, i, j, k + (m - 1));
+                l[m - 1] = vz_at(a, i, j, k - m);
+            } else {
+                h[m - 1] = at_or0(a.v[ax], a, i + (m - 1) * di, j + (m - 1) * dj, k);
+                l[m - 1] = at_or0(a.v[ax], a, i - m * di, j - m * dj, k);
+            }
         }
         dv[ax] = stag_diff(a.w[ax], h[0], l[0], h[1], l[1], h[2], l[2], h[3], l[3]);
         if (a.cpml) {
@@ -198,7 +218,9 @@ __global__ void vd_pressure_simple(VdArgs a) {
         }
     }
     const float div = __fadd_rn(__fadd_rn(dv[0], dv[1]), dv[2]);
-    if (a.cpml) {
+    if (a.fs && k == 0) {
+        a.p[o] = 0.0f;   // p = 0 on the free surface
+    } else if (a.cpml) {
         a.p[o] = undamped(a.p[o], a.kd[o], div);
     } else {
         const float eps = __fadd_rn(__fadd_rn(a.eg[0][i], a.eg[1][j]), a.eg[2][k]);
@@ -433,9 +455,10 @@ __global__ void __launch_bounds__(NT, 2)
 
     auto issue_p = [&](int seq) {
         const int s = seq % VNSP;
+        int z = z0 - (kRadius - 1) + seq;
+        if (a.fs && z < 0) z = -z;   // plane -m holds the odd image of plane m (negated in the queue)
         mbar_expect_tx(&c.bar_p[s], V_SLOT_P * 4);
-        tma_load_3d(c.ring_p + s * V_SLOT_P, &maps.p_halo, x0 - kRadius, y0 - kRadius, z0 - (kRadius - 1) + seq,
-                    &c.bar_p[s]);
+        tma_load_3d(c.ring_p + s * V_SLOT_P, &maps.p_halo, x0 - kRadius, y0 - kRadius, z, &c.bar_p[s]);
         hi_p = seq + 1;
     };
     auto issue_o = [&](int seq) {
@@ -500,6 +523,14 @@ __global__ void __launch_bounds__(NT, 2)
             for (int i = 0; i < 2 * kRadius - 1; ++i)
                 if (i == s) v_read_q(c, s, q[i]);
         }
+    }
+    if (a.fs && ok) {   // queue planes above k = 0 (z0-3+i < 0) hold the images: negate
+#pragma unroll
+        for (int i = 0; i < kRadius - 1; ++i)
+            if (z0 - (kRadius - 1) + i < 0) {
+#pragma unroll
+                for (int r = 0; r < RY; ++r) q[i][r] = make_float2(-q[i][r].x, -q[i][r].y);
+            }
     }
     __syncthreads();
     // the slots of planes z0-3 .. z0-1 (never a centre) are refilled now
@@ -598,7 +629,9 @@ __device__ __forceinline__ bool p_plane(const VdArgs &a, const PCtx &c, int t, f
         const float2 po = *reinterpret_cast<const float2 *>(tp + yl * TX + c.xl);
         const float2 ko = *reinterpret_cast<const float2 *>(tk + yl * TX + c.xl);
         float2 pn;
-        if (!a.cpml && (c.lay_xy[r] || zl))
+        if (a.fs && k == 0)
+            pn = make_float2(0.0f, 0.0f);   // p = 0 on the free surface
+        else if (!a.cpml && (c.lay_xy[r] || zl))
             pn = relax2(po, ko, div, __fadd2_rn(__fadd2_rn(c.egx, bc2(c.egy[r])), bc2(egz)));
         else
             pn = undamped2(po, ko, div);
@@ -646,8 +679,10 @@ __global__ void __launch_bounds__(NT, 2)
     };
     auto issue_z = [&](int seq) {
         const int s = seq % PNSZ;
+        int z = z0 - kRadius + seq;
+        if (a.fs && z < 0) z = -z - 1;   // v_z(-m) = v_z(m - 1): the even image across the surface
         mbar_expect_tx(&c.bar_z[s], OWN * 4);
-        tma_load_3d(c.ring_z + s * OWN, &maps.own[2], x0, y0, z0 - kRadius + seq, &c.bar_z[s]);
+        tma_load_3d(c.ring_z + s * OWN, &maps.own[2], x0, y0, z, &c.bar_z[s]);
         hi_z = seq + 1;
     };
 
@@ -856,22 +891,23 @@ mmod_status vd_latched(mmod_vd *h) {
     return MMOD_OK;
 }
 
-// Depth of the continuous position x into the layers of an axis (capped at L).
-double layer_depth(double x, int n, int L) {
+// Depth of the continuous position x into the layers of an axis (capped at
+// L); top_free drops the layer at index 0 (free surface).
+double layer_depth(double x, int n, int L, bool top_free) {
     double d = 0.0;
-    if (L - x > d) d = L - x;
+    if (!top_free && L - x > d) d = L - x;
     if (x - (n - 1 - L) > d) d = x - (n - 1 - L);
     return d > L ? (double)L : d;
 }
 
 // Profiles of one axis at grid (half = 0) or half points: eps = dt eta / 2,
 // and the CPML pair B, G (reading shared with the oracle).
-void axis_profiles(int n, int L, double h, double vmax, double R, double f0, double dt, int half, double *eps,
-                   float *B, float *G) {
+void axis_profiles(int n, int L, double h, double vmax, double R, double f0, double dt, int half, bool top_free,
+                   double *eps, float *B, float *G) {
     const double d0 = L > 0 ? 3.0 * vmax * std::log(1.0 / R) / (2.0 * L * h) : 0.0;
     const double pi = 3.14159265358979323846;
     for (int i = 0; i < n; ++i) {
-        const double x = L > 0 ? layer_depth(i + 0.5 * half, n, L) : 0.0;
+        const double x = L > 0 ? layer_depth(i + 0.5 * half, n, L, top_free) : 0.0;
         const double s = L > 0 ? x / L : 0.0;
         const double d = d0 * s * s;
         eps[i] = 0.5 * dt * d;
@@ -893,6 +929,7 @@ VdArgs vd_args(mmod_vd *h) {
     a.nx = c.nx; a.ny = c.ny; a.nz = c.nz; a.nxp = h->nxp; a.plane = h->plane;
     a.nbl = c.nbl;
     a.cpml = c.boundary == MMOD_BOUNDARY_CPML;
+    a.fs = c.free_surface ? 1 : 0;
     std::memcpy(a.w, h->w, sizeof(a.w));
     a.p = h->p;
     for (int ax = 0; ax < 3; ++ax) {
@@ -1049,7 +1086,8 @@ std::string vd_validate(const mmod_config *c, mmod_status *st) {
         return "cpml_f0 must be finite and >= 0";
     *st = MMOD_ERR_UNSUPPORTED;
     if (c->order != 8) return "the staggered propagator supports order 8 only";
-    if (c->free_surface) return "the staggered propagator has no free-surface option";
+    *st = MMOD_ERR_ARG;
+    if (c->free_surface && c->nz <= kRadius) return "a free surface needs nz >= 5";
     *st = MMOD_OK;
     return "";
 }
@@ -1248,9 +1286,10 @@ MMOD_API mmod_status mmod_vd_set_model(mmod_vd *h, const float *vel, const float
     size_t off = 0;
     for (int ax = 0; ax < 3; ++ax) {
         std::vector<double> eg(n3[ax]), eh(n3[ax]);
-        axis_profiles(n3[ax], c.nbl, hh[ax], h->vmax, c.damp_R, c.cpml_f0, c.dt, 0, eg.data(),
+        const bool top_free = ax == 2 && c.free_surface;
+        axis_profiles(n3[ax], c.nbl, hh[ax], h->vmax, c.damp_R, c.cpml_f0, c.dt, 0, top_free, eg.data(),
                       &prof[2 * nsum + off], &prof[3 * nsum + off]);
-        axis_profiles(n3[ax], c.nbl, hh[ax], h->vmax, c.damp_R, c.cpml_f0, c.dt, 1, eh.data(),
+        axis_profiles(n3[ax], c.nbl, hh[ax], h->vmax, c.damp_R, c.cpml_f0, c.dt, 1, top_free, eh.data(),
                       &prof[4 * nsum + off], &prof[5 * nsum + off]);
         for (int i = 0; i < n3[ax]; ++i) {
             prof[off + i] = (float)eg[i];
@@ -1269,6 +1308,9 @@ MMOD_API mmod_status mmod_vd_set_model(mmod_vd *h, const float *vel, const float
         vd_source_scale<<<(c.nsrc + 127) / 128, 128, 0, s>>>(vel, rho, c.nx, c.ny, c.nsrc, h->src_ijk_d, h->src_eps,
                                                              c.dt, c.hx * c.hy * c.hz, h->src_scale);
         VD_CK(h, cudaGetLastError());
+        if (c.free_surface)   // sources on the surface plane do nothing
+            for (int q = 0; q < c.nsrc; ++q)
+                if (h->src[3 * q + 2] == 0) VD_CK(h, cudaMemsetAsync(h->src_scale + q, 0, sizeof(float), s));
     }
     VD_CK(h, cudaStreamSynchronize(s));
     h->model_set = true;
@@ -1290,6 +1332,7 @@ MMOD_API mmod_status mmod_vd_set_state(mmod_vd *h, const float *state, mmod_stre
             VD_CK(h, cudaMemsetAsync(dst[f], 0, sizeof(float) * (size_t)h->vol, s));
         }
     }
+    if (c.free_surface) VD_CK(h, cudaMemsetAsync(h->p, 0, sizeof(float) * (size_t)h->plane, s));   // p = 0 on k = 0
     h->state_pending = true;
     return MMOD_OK;
 }

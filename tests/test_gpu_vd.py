@@ -36,7 +36,7 @@ def run_vd(p, kernel=M.KERNEL_AUTO, state=None, pdl=None):
 def run_oracle_vd(orc, p, state0=None):
     return orc.forward_vd(p.vel, p.rho, p.h, p.dt, p.nt, nbl=p.nbl, refl=p.refl, cpml=p.cpml, f0=p.cpml_f0,
                           src_ijk=p.src_ijk, wavelet=p.wavelet, rec_ijk=p.rec_ijk, state0=state0,
-                          want_state=True)
+                          want_state=True, free_surface=p.free_surface)
 
 
 def check(tr_g, st_g, tr_o, st_o, tol):
@@ -173,8 +173,9 @@ def test_error_paths():
     import ctypes
     out = ctypes.c_void_p()
     assert M.load().mmod_vd_create(ctypes.byref(cfg), 0, ctypes.byref(out)) == -7     # order 6
-    cfg = M._config(22, 21, 20, p.h, p.dt, p.nt, 2, p.src_ijk, p.rec_ijk, 8, 1e-3, free_surface=True)
-    assert M.load().mmod_vd_create(ctypes.byref(cfg), 0, ctypes.byref(out)) == -7     # free surface
+    cfg = M._config(22, 21, 4, p.h, p.dt, p.nt, 1, np.zeros((0, 3), np.int32), np.zeros((0, 3), np.int32), 8, 1e-3,
+                    free_surface=True)
+    assert M.load().mmod_vd_create(ctypes.byref(cfg), 0, ctypes.byref(out)) == -1     # surface with nz < 5
     prop = M.StaggeredPropagator(p.vel.shape, p.h, p.dt, p.nt, **base)
     wav = torch.zeros((2, p.nt), device="cuda")
     tr = torch.zeros((p.nt, len(p.rec_ijk)), device="cuda")
@@ -199,3 +200,75 @@ def test_error_paths():
     prop.forward(wav, tr)
     torch.cuda.synchronize()
     assert prop.loop_ms() > 0
+
+
+FS_SHAPES = [((13, 17, 35), 2), ((70, 33, 65), 5), ((5, 40, 3), 1), ((37, 45, 131), 9), ((6, 20, 70), 0)]
+
+
+@pytest.mark.parametrize("cpml", [False, True], ids=["damping", "cpml"])
+@pytest.mark.parametrize("shape,nbl", FS_SHAPES, ids=[f"{s}-L{n}" for s, n in FS_SHAPES])
+def test_free_surface_ragged_shapes(orc, shape, nbl, cpml):
+    """With the surface option: sources on, just under and far below the
+    surface, receivers on it (they read 0) and under it; TMA = plain bits."""
+    nz, ny, nx = shape
+    p = W.tiny_problem_vd(shape=shape, nt=60, nbl=nbl, nsrc=3, nrec=9, seed=nx * 5 + ny * 3 + nz)
+    p.cpml, p.cpml_f0, p.free_surface = cpml, 25.0, True
+    p.src_ijk[0] = [nx // 2, ny // 2, 0]
+    p.src_ijk[1] = [nx - 1, 0, 1]
+    p.rec_ijk[0] = [0, 0, 0]
+    p.rec_ijk[1] = [nx // 2, ny - 1, 1]
+    tr_o, st_o = run_oracle_vd(orc, p)
+    tr_g, st_g, prop = run_vd(p)
+    assert prop.uses_tma
+    check(tr_g, st_g, tr_o, st_o, 1e-5)
+    assert not tr_g[:, 0].any() and not st_g[0][0].any()
+    tr_s, st_s, _ = run_vd(p, kernel=M.KERNEL_SIMPLE)
+    assert np.array_equal(tr_s, tr_g) and np.array_equal(st_s, st_g)
+
+
+def test_free_surface_layered_240_1000_steps(orc):
+    """The 240^3 Gardner-density workload with the surface on and the
+    receivers one plane under it, over 1000 steps."""
+    p = W.layered_240_vd(1000)
+    p.free_surface = True
+    p.rec_ijk[:, 2] = 1
+    tr_o, st_o = run_oracle_vd(orc, p)
+    tr_g, st_g, _ = run_vd(p)
+    check(tr_g, st_g, tr_o, st_o, 1e-4)
+
+
+def test_free_surface_standing_wave_fp32():
+    """cos(kx x) cos(ky y) sin(kz z): exact with the images up to the surface."""
+    shape, h, v, rho, dt = (60, 70, 74), (10.0, 12.0, 9.0), 2200.0, 1800.0, 0.9e-3
+    K, b = rho * v * v, 1.0 / rho
+    k = np.array([2 * np.pi / 97.0, 2 * np.pi / 61.0, 2 * np.pi / 143.0])
+    a8 = [1225 / 1024, -245 / 3072, 49 / 5120, -5 / 7168]
+    S = np.array([sum(2.0 / h[ax] * a8[m - 1] * np.sin((2 * m - 1) * k[ax] * h[ax] / 2) for m in range(1, 5))
+                  for ax in range(3)])
+    nz, ny, nx = shape
+    x, y, z = np.arange(nx) * h[0], np.arange(ny) * h[1], np.arange(nz) * h[2]
+
+    def prod(fz, fy, fx):
+        return fz[:, None, None] * fy[None, :, None] * fx[None, None, :]
+
+    cx, cy = np.cos(k[0] * x + 0.3), np.cos(k[1] * y + 1.1)
+    f = [prod(np.sin(k[2] * z), cy, cx), prod(np.sin(k[2] * z), cy, np.sin(k[0] * (x + 0.5 * h[0]) + 0.3)),
+         prod(np.sin(k[2] * z), np.sin(k[1] * (y + 0.5 * h[1]) + 1.1), cx),
+         prod(np.cos(k[2] * (z + 0.5 * h[2])), cy, cx)]
+    sgn = np.array([1.0, 1.0, -1.0])
+    V0 = 0.5 * dt * b * S * sgn
+    st = np.stack([f[0]] + [V0[a] * f[1 + a] for a in range(3)])
+    nsteps = 4
+    p = W.Problem("standing-fs", np.full(shape, v, np.float32), h, dt, nsteps, 0, np.zeros((0, 3), np.int32),
+                  np.zeros((0, nsteps), np.float32), np.zeros((0, 3), np.int32), rho=np.full(shape, rho, np.float32),
+                  free_surface=True)
+    _, out, _ = run_vd(p, state=st)
+    P, V = 1.0, V0.copy()
+    for _ in range(nsteps):
+        V = V - dt * b * S * sgn * P
+        P = P + dt * K * float(np.dot(S * sgn, V))
+    m = 7 * nsteps + 1
+    near = (slice(0, nz - m), slice(m, -m), slice(m, -m))
+    assert rel_l2(out[0][near], (P * f[0])[near]) < 2e-6
+    for a in range(3):
+        assert rel_l2(out[1 + a][near], (V[a] * f[1 + a])[near]) < 2e-6
