@@ -320,7 +320,7 @@ def run_mmod(args):
     extra = {}
     fwd_gpts = value / ws
     measures = {"adjoint": lambda: measure_adjoint(M, prop, p, dev, stream, fwd_gpts),
-                "gradient": lambda: measure_gradient(M, dev, stream, fwd_gpts),
+                "gradient": lambda: measure_gradient(M, dev, stream, fwd_gpts, args.nt or 1000),
                 "batched": lambda: measure_batched(M, dev, stream, fwd_gpts),
                 "large": lambda: measure_large(M, dev, stream, peak),
                 "free_surface": lambda: measure_free_surface(M, dev, stream, fwd_gpts),
@@ -381,12 +381,12 @@ def measure_adjoint(M, prop, p, dev, stream, fwd_gpts, reps=3):
             "what": "mmod_adjoint: nt adjoint steps, receivers injected, sources gathered"}
 
 
-def measure_gradient(M, dev, stream, fwd_gpts, reps=2):
+def measure_gradient(M, dev, stream, fwd_gpts, nt=1000, reps=2):
     """mmod_gradient on the 200^3 smooth-gradient workload: 20 FP32 or BF16
     checkpoints, and FP32 with every state kept (no replay)."""
     import torch
     import workloads as W
-    p = W.smooth_gradient_200(1000)
+    p = W.smooth_gradient_200(nt)
     prop = M.Propagator.from_problem(p, device=dev.index or 0)
     prop.set_model(torch.from_numpy(p.vel).to(dev), stream)
     wav = torch.from_numpy(np.ascontiguousarray(p.wavelet)).to(dev)
