@@ -435,7 +435,9 @@ mmod_status mmod_batch_autotune(mmod_batch *b, int steps, mmod_stream stream, in
  * mmod_vd_set_option: MMOD_OPT_PDL 0 / 1 (default 0): launch the TMA
  *   kernels as programmatic dependents, so that each requests the data its
  *   predecessor does not write (own velocities and buoyancy; p and dt K)
- *   while the predecessor finishes; the same bits either way.  ARG otherwise.
+ *   while the predecessor finishes; MMOD_OPT_ZLEN >= 0: planes per z range
+ *   of a CTA (0 = the plan's choice).  The same bits for every value.  ARG
+ *   otherwise.
  * mmod_vd_get_plan: 6 ints {tiles_x, tiles_y, z_chunks, planes_per_chunk,
  *   CTAs per kernel, threads per CTA}; UNSUPPORTED when no TMA plan.
  * mmod_vd_last_loop_ms / mmod_vd_last_launch_count: as for mmod_forward. */

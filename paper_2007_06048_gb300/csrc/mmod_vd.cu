@@ -125,11 +125,15 @@ __device__ __forceinline__ float cpml_mem(float *m, float B, float G, float d) {
 
 __device__ __forceinline__ int zero_clip(int v, int n) { return v < 0 ? 0 : (v >= n ? n - 1 : v); }
 
-// Wait for the previous kernel of the stream (no-op without programmatic
-// dependent launch), then allow the next one to start.
+// Programmatic dependent launch (no-ops without it): wait for the previous
+// kernel of the stream; allow the next one to start.  The step kernels
+// release their dependents after their plane loop, so that the next kernel's
+// CTAs take SM slots only as this kernel's CTAs finish.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait_then_release() {
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    pdl_wait();
+    pdl_release();
 }
 
 // ---------------------------------------------------------------------------
@@ -489,7 +493,7 @@ __global__ void __launch_bounds__(NT, 2)
             for (int q = 0; q < VNSB && q < nseq_b; ++q) issue_b(q);
         }
     }
-    pdl_wait_then_release();   // p^n of the pressure kernel and the source add
+    pdl_wait();   // p^n of the pressure kernel and the source add
     if (tid == 0 && T > 0)
         for (int q = 0; q < VNSP && q < nseq_p; ++q) issue_p(q);
     // receivers of the previous step: p^n, read-only in this kernel
@@ -557,6 +561,7 @@ __global__ void __launch_bounds__(NT, 2)
         }
     }
 #undef VD_VSTEP
+    pdl_release();
     if (*c.abort_flag && tid == 0) {
         drain(c.bar_p, hi_p, VNSP);
         drain(c.bar_o, hi_o, VNSO);
@@ -696,7 +701,7 @@ __global__ void __launch_bounds__(NT, 2)
         if (T > 0)
             for (int q = 0; q < PNSC && q < T; ++q) issue_c_own(q);
     }
-    pdl_wait_then_release();   // the velocities of the velocity kernel
+    pdl_wait();   // the velocities of the velocity kernel
     if (tid == 0 && T > 0) {
         for (int q = 0; q < PNSC && q < T; ++q) issue_c_vel(q);
         for (int q = 0; q < PNSZ && q < nseq_z; ++q) issue_z(q);
@@ -750,6 +755,7 @@ __global__ void __launch_bounds__(NT, 2)
         }
     }
 #undef VD_PSTEP
+    pdl_release();
     if (*c.abort_flag && tid == 0) {
         drain(c.bar_c, hi_c, PNSC);
         drain(c.bar_z, hi_z, PNSZ);
@@ -852,8 +858,10 @@ struct mmod_vd {
     VdMaps maps{};
     VdGeom geom{};
     int kernel = MMOD_KERNEL_AUTO;
-    int pdl = 0;                      // programmatic dependent launch of the TMA step kernels
-                                      // (measured slower on 240^3: 180 vs 166 us per step)
+    int pdl = 0;                      // programmatic dependent launch of the TMA step kernels (measured
+                                      // equal on 240^3 with the release after the plane loop)
+    int zlen = 0;                     // planes per z range (0: the plan's choice)
+    VdGeom geom_plan{};               // the plan's decomposition
     bool model_set = false, ran = false, state_pending = false;
     double vmax = 0.0, veff = 0.0;
     cudaError_t latched = cudaSuccess;
@@ -994,7 +1002,7 @@ cudaError_t enqueue_vd_step(mmod_vd *h, int n, const float *wav, float *traces_p
 
 mmod_status vd_loop(mmod_vd *h, const float *wav, float *tr, cudaStream_t s, long long *launches) {
     const mmod_config &c = h->cfg;
-    const int kern = (vd_use_tma(h) ? 1 : 0) + 2 * h->pdl;
+    const int kern = (vd_use_tma(h) ? 1 : 0) + 2 * h->pdl + 4 * h->zlen;
     const void *key[2] = {wav, tr};
     if (!h->exec || std::memcmp(h->gkey, key, sizeof(key)) != 0 || h->gkernel != kern) {
         if (h->exec) cudaGraphExecDestroy(h->exec);
@@ -1220,6 +1228,7 @@ MMOD_API mmod_status mmod_vd_create(const mmod_config *cfg, int device, mmod_vd 
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     h->geom = plan_geom(c.nx, c.ny, c.nz, sms);
+    h->geom_plan = h->geom;
     bool ok = cudaFuncSetAttribute(vd_velocity_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, V_SMEM) == cudaSuccess &&
               cudaFuncSetAttribute(vd_pressure_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM) == cudaSuccess;
     ok = ok && encode_box(&h->maps.p_halo, h->p, c.nx, c.ny, c.nz, h->nxp, PHX, PHY);
@@ -1387,6 +1396,15 @@ MMOD_API mmod_status mmod_vd_set_option(mmod_vd *h, int option, int value) {
     if (!h) return MMOD_ERR_ARG;
     if (option == MMOD_OPT_PDL && (value == 0 || value == 1)) {
         h->pdl = value;
+        return MMOD_OK;
+    }
+    if (option == MMOD_OPT_ZLEN && value >= 0) {
+        h->zlen = value;
+        h->geom = h->geom_plan;
+        if (value > 0) {
+            h->geom.zlen = std::min(value, h->cfg.nz);
+            h->geom.zchunks = (h->cfg.nz + h->geom.zlen - 1) / h->geom.zlen;
+        }
         return MMOD_OK;
     }
     return vd_fail(h, MMOD_ERR_ARG, "unknown option or value");

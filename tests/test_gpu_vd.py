@@ -13,13 +13,15 @@ from _gpu_util import rel_l2, torch_cuda
 pytestmark = pytest.mark.gpu
 
 
-def run_vd(p, kernel=M.KERNEL_AUTO, state=None, pdl=None):
+def run_vd(p, kernel=M.KERNEL_AUTO, state=None, pdl=None, zlen=None):
     torch = torch_cuda()
     prop = M.StaggeredPropagator.from_problem(p)
     if kernel != M.KERNEL_AUTO:
         prop.set_kernel(kernel)
     if pdl is not None:
         prop.set_option(M.OPT_PDL, pdl)
+    if zlen is not None:
+        prop.set_option(M.OPT_ZLEN, zlen)
     prop.set_model(torch.from_numpy(np.ascontiguousarray(p.vel)).cuda(),
                    torch.from_numpy(np.ascontiguousarray(p.rho)).cuda())
     nsrc, nrec = len(p.src_ijk), len(p.rec_ijk)
@@ -113,6 +115,8 @@ def test_tma_kernels_are_bitwise_the_plain_kernels(shape, nbl, cpml):
     assert np.array_equal(st_t, st_s)
     tr_n, st_n, _ = run_vd(p, pdl=1)           # with programmatic dependent launch
     assert np.array_equal(tr_n, tr_s) and np.array_equal(st_n, st_s)
+    tr_z, st_z, _ = run_vd(p, zlen=7)          # z ranges of 7 planes
+    assert np.array_equal(tr_z, tr_s) and np.array_equal(st_z, st_s)
 
 
 def test_standing_wave_fp32():
