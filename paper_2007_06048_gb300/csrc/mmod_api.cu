@@ -258,9 +258,8 @@ CpmlArgs cpml_args(const mmod_handle *h) {
     const size_t n3 = (size_t)(c.nx + c.ny + c.nz);
     const int off[3] = {0, c.nx, c.nx + c.ny};
     for (int a = 0; a < 3; ++a) {
-        p.psi[0][a] = h->cpml_mem + (size_t)a * h->vol;
-        p.psi[1][a] = h->cpml_mem + (size_t)(3 + a) * h->vol;
-        p.zeta[a] = h->cpml_mem + (size_t)(6 + a) * h->vol;
+        p.psi[a] = h->cpml_mem + (size_t)a * h->vol;
+        p.zeta[a] = h->cpml_mem + (size_t)(3 + a) * h->vol;
         p.b[a] = h->cpml_bg + off[a];
         p.g[a] = h->cpml_bg + n3 + off[a];
     }
@@ -406,8 +405,8 @@ static mmod_status enqueue_loop(mmod_handle *h, const Geometry &geo, const float
             a.uout = h->u[n & 1];
             a.traces = (n >= 1 && tr && ng > 0) ? tr + (long long)(n - 1) * ng : nullptr;
             MMOD_CK(h, enqueue_step(h, a, &h->cur_map[(n + 1) & 1], &h->prev_map[n & 1], tma, nullptr, s, count));
-            MMOD_CK(h, launch_cpml_layers(cp, n, a.ucur, a.uout, s));
-            *count += 1;
+            MMOD_CK(h, launch_cpml_layers(cp, a.ucur, a.uout, s));
+            *count += 2;
             if (!tma && tr && ng > 0) {
                 MMOD_CK(h, launch_gather(a.uout, geo.gather_off, ng, tr + (long long)n * ng, s));
                 ++*count;
@@ -584,8 +583,8 @@ MMOD_API mmod_status mmod_create(const mmod_config *cfg, int device, mmod_handle
     CKC(cudaMemset(h->c, 0, vbytes));
     CKC(cudaMemset(h->eta, 0, sizeof(float) * (size_t)(nx + ny + nz)));
     if (is_cpml(h)) {
-        CKC(cudaMalloc(&h->cpml_mem, 9 * vbytes));
-        CKC(cudaMemset(h->cpml_mem, 0, 9 * vbytes));
+        CKC(cudaMalloc(&h->cpml_mem, 6 * vbytes));
+        CKC(cudaMemset(h->cpml_mem, 0, 6 * vbytes));
         CKC(cudaMalloc(&h->cpml_bg, sizeof(float) * 2 * (size_t)(nx + ny + nz)));
         CKC(cudaMemset(h->cpml_bg, 0, sizeof(float) * 2 * (size_t)(nx + ny + nz)));
     }
@@ -835,7 +834,7 @@ MMOD_API mmod_status mmod_forward(mmod_handle *h, const float *wavelet, float *t
         MMOD_CK(h, cudaMemsetAsync(h->u[0], 0, sizeof(float) * (size_t)h->vol, s));
         MMOD_CK(h, cudaMemsetAsync(h->u[1], 0, sizeof(float) * (size_t)h->vol, s));
     }
-    if (is_cpml(h)) MMOD_CK(h, cudaMemsetAsync(h->cpml_mem, 0, 9 * sizeof(float) * (size_t)h->vol, s));
+    if (is_cpml(h)) MMOD_CK(h, cudaMemsetAsync(h->cpml_mem, 0, 6 * sizeof(float) * (size_t)h->vol, s));
     h->state_pending = false;
     if (c.nt > 0)
         if (mmod_status st = run_loop_graph(h, h->g_fwd, h->fwd, dwav, c.nrec > 0 ? dtr : nullptr, s, &launches))

@@ -9,35 +9,50 @@
 // kernels' pair form), D1_a the order-8 centred first difference.
 //
 // Each step runs the usual step kernel without damping (u^{n+1} = 2u^n -
-// u^{n-1} + c L u^n + sources) and then one layer kernel over the six layer
-// slabs only, which adds c sum_a (D1_a psi_a^n + zeta_a^n) to u^{n+1}.  The
-// layer kernel needs psi_a^n at the eight neighbours along a; it recomputes
-// them from a 17-point line of u^n and psi_a^{n-1} (every thread performs the
-// same operations for a given cell, so the recomputed values equal the one
-// the cell's own thread stores), which removes a separate psi pass.  psi is
-// ping-ponged: step n reads psi[n & 1] and writes psi[(n + 1) & 1].  u and psi
-// are 0 outside the grid; with a free surface the top layer is absent and the
-// plane k = 0 is left alone (u, psi and zeta stay 0 there).
+// u^{n-1} + c L u^n + sources), then two passes over the six layer slabs
+// only: the psi pass (psi_a^n from u^n, in place) and the correction pass
+// (zeta_a^n, and u^{n+1} += c sum_a (D1_a psi_a^n + zeta_a^n)).  One thread
+// per layer column of up to 16 planes; each cell loads its 9-point lines
+// before the arithmetic, without bounds tests where the line stays inside
+// the grid.  u and psi are 0 outside the grid; with a free surface the top
+// layer is absent and the plane k = 0 is left alone (u, psi and zeta stay 0).
 #include "mmod_cpml.h"
 #include "mmod_internal.h"
 
 namespace mmod {
 namespace {
 
-constexpr int kLine = 4 * kRadius + 1;   // u^n from -8 to +8 along the axis
+constexpr int kLine = 2 * kRadius + 1;   // -4..4 along the axis
 
 // First-difference weights (unit spacing): 4/5, -1/5, 4/105, -1/280.
-__device__ __forceinline__ float d1_at(const float *x, int c, float inv_h) {
+__device__ __forceinline__ float d1_of(const float (&x)[kLine], float inv_h) {
     constexpr float w[4] = {4.0f / 5.0f, -1.0f / 5.0f, 4.0f / 105.0f, -1.0f / 280.0f};
     float s = 0.0f;
 #pragma unroll
-    for (int m = 1; m <= kRadius; ++m) s = __fmaf_rn(w[m - 1], __fsub_rn(x[c + m], x[c - m]), s);
+    for (int m = 1; m <= kRadius; ++m) s = __fmaf_rn(w[m - 1], __fsub_rn(x[kRadius + m], x[kRadius - m]), s);
     return __fmul_rn(s, inv_h);
 }
 
+// The 9 values of f along an axis (stride st) centred on offset o, index q0
+// of n along the axis; 0 outside the grid.
+__device__ __forceinline__ void line9(const float *__restrict__ f, long long o, long long st, int q0, int n,
+                                      float (&x)[kLine]) {
+    if (q0 >= kRadius && q0 + kRadius < n) {
+        const float *fp = f + o - kRadius * st;
+#pragma unroll
+        for (int m = 0; m < kLine; ++m, fp += st) x[m] = __ldg(fp);
+    } else {
+#pragma unroll
+        for (int m = 0; m < kLine; ++m) {
+            const int q = q0 - kRadius + m;
+            x[m] = ((unsigned)q < (unsigned)n) ? __ldg(f + o + (m - kRadius) * st) : 0.0f;
+        }
+    }
+}
+
 struct Box {
-    int x0, y0, z0, ex, ey, ez, tx, ty;
-    int first;   // first block of this box
+    int x0, y0, z0, ex, ey, ez, tx, ty, tz;   // tz: z chunks of kZC planes
+    int first;                                // first block of this box
 };
 struct Boxes {
     Box b[6];
@@ -45,68 +60,12 @@ struct Boxes {
     long long blocks;
 };
 
-constexpr int kBX = 32, kBY = 4;
+constexpr int kBX = 32, kBY = 4, kZC = 16;   // a block: 32 x 4 cells over up to kZC planes
 
-// The layer terms of axis A at cell (idx, o): psi^n at the nine cells along A
-// recomputed from u^n (-8..8) and psi^{n-1} (-4..4), the own psi^n stored,
-// zeta advanced; returns D1 psi^n + zeta^n.  Lines that stay inside the grid
-// take unchecked loads.
-template <int A>
-__device__ __forceinline__ float axis_term(const CpmlArgs &p, const float *__restrict__ u, const float *psi_old,
-                                           float *psi_new, float *zeta, int q0, int n, long long o, long long st,
-                                           float g0) {
-    float x[kLine], po[2 * kRadius + 1], bb[2 * kRadius + 1], gg[2 * kRadius + 1];
-    const float *bA = p.b[A], *gA = p.g[A];
-    if (q0 >= 2 * kRadius && q0 + 2 * kRadius < n) {
-        const float *up = u + o - 2 * kRadius * st;
-#pragma unroll
-        for (int m = 0; m < kLine; ++m) x[m] = __ldg(up + m * st);
-        const float *pp = psi_old + o - kRadius * st;
-#pragma unroll
-        for (int m = 0; m <= 2 * kRadius; ++m) {
-            po[m] = pp[m * st];
-            bb[m] = __ldg(bA + q0 - kRadius + m);
-            gg[m] = __ldg(gA + q0 - kRadius + m);
-        }
-    } else {
-#pragma unroll
-        for (int m = 0; m < kLine; ++m) {
-            const int q = q0 - 2 * kRadius + m;
-            x[m] = ((unsigned)q < (unsigned)n) ? __ldg(u + o + (m - 2 * kRadius) * st) : 0.0f;
-        }
-#pragma unroll
-        for (int m = 0; m <= 2 * kRadius; ++m) {
-            const int q = q0 - kRadius + m;
-            const bool in = (unsigned)q < (unsigned)n;
-            po[m] = in ? psi_old[o + (m - kRadius) * st] : 0.0f;
-            bb[m] = in ? __ldg(bA + q) : 1.0f;
-            gg[m] = in ? __ldg(gA + q) : 0.0f;
-        }
-    }
-    // psi_a^n at the nine cells: b psi^{n-1} + g D1 u^n (0 outside the grid)
-    float pn[2 * kRadius + 1];
-#pragma unroll
-    for (int m = 0; m <= 2 * kRadius; ++m) {
-        const int q = q0 - kRadius + m;
-        const float d1 = d1_at(x, m + kRadius, p.inv_h[A]);
-        pn[m] = ((unsigned)q < (unsigned)n) ? __fmaf_rn(bb[m], po[m], __fmul_rn(gg[m], d1)) : 0.0f;
-    }
-    psi_new[o] = pn[kRadius];
-    const float c2 = x[2 * kRadius];
-    const float two_p = __fadd_rn(c2, c2);
-    float d2 = pair_first(p.w[A][0], x[2 * kRadius + 1], x[2 * kRadius - 1], two_p);
-#pragma unroll
-    for (int m = 2; m <= kRadius; ++m) d2 = pair_acc(d2, p.w[A][m - 1], x[2 * kRadius + m], x[2 * kRadius - m], two_p);
-    const float dpsi = d1_at(pn, kRadius, p.inv_h[A]);
-    const float z = __fmaf_rn(bb[kRadius], zeta[o], __fmul_rn(g0, __fadd_rn(d2, dpsi)));
-    zeta[o] = z;
-    return __fadd_rn(dpsi, z);
-}
-
-__global__ void __launch_bounds__(kBX *kBY)
-    cpml_layer_kernel(const CpmlArgs p, const Boxes boxes, const float *__restrict__ u, float *__restrict__ uout,
-                      const float *psi_old0, const float *psi_old1, const float *psi_old2, float *psi_new0,
-                      float *psi_new1, float *psi_new2) {
+// Column of this thread in the layer slabs and its planes [k0, k1); false
+// when outside its box.
+__device__ __forceinline__ bool layer_column(const CpmlArgs &p, const Boxes &boxes, int &i, int &j, int &k0,
+                                             int &k1) {
     const int blk = blockIdx.x;
     int bi = 0;
     while (bi + 1 < boxes.n && blk >= boxes.b[bi + 1].first) ++bi;
@@ -117,26 +76,80 @@ __global__ void __launch_bounds__(kBX *kBY)
     const int ty = local % B.ty;
     const int tz = local / B.ty;
     const int li = tx * kBX + threadIdx.x, lj = ty * kBY + threadIdx.y;
-    if (li >= B.ex || lj >= B.ey) return;
-    const int i = B.x0 + li, j = B.y0 + lj, k = B.z0 + tz;
-    if (p.fs && k == 0) return;   // the free-surface plane stays 0
-    const long long o = (long long)k * p.plane + (long long)j * p.nxp + i;
-    float acc = 0.0f;
-    bool any = false;
-    const float gx = __ldg(p.g[0] + i), gy = __ldg(p.g[1] + j), gz = __ldg(p.g[2] + k);
-    if (gx != 0.0f) {
-        acc = __fadd_rn(acc, axis_term<0>(p, u, psi_old0, psi_new0, p.zeta[0], i, p.nx, o, 1, gx));
-        any = true;
+    if (li >= B.ex || lj >= B.ey) return false;
+    i = B.x0 + li;
+    j = B.y0 + lj;
+    k0 = B.z0 + tz * kZC;
+    k1 = min(k0 + kZC, B.z0 + B.ez);
+    if (p.fs && k0 == 0) k0 = 1;   // the free-surface plane stays 0
+    return true;
+}
+
+template <int A>
+__device__ __forceinline__ void psi_axis(const CpmlArgs &p, const float *__restrict__ u, long long o, long long st,
+                                         int q0, int n, float g) {
+    float x[kLine];
+    line9(u, o, st, q0, n, x);
+    float *ps = p.psi[A] + o;
+    *ps = __fmaf_rn(__ldg(p.b[A] + q0), *ps, __fmul_rn(g, d1_of(x, p.inv_h[A])));
+}
+
+__global__ void __launch_bounds__(kBX *kBY)
+    cpml_psi_kernel(const CpmlArgs p, const Boxes boxes, const float *__restrict__ u) {
+    int i, j, k0, k1;
+    if (!layer_column(p, boxes, i, j, k0, k1)) return;
+    const float gx = __ldg(p.g[0] + i), gy = __ldg(p.g[1] + j);
+    long long o = (long long)k0 * p.plane + (long long)j * p.nxp + i;
+    for (int k = k0; k < k1; ++k, o += p.plane) {
+        const float gz = __ldg(p.g[2] + k);
+        if (gx != 0.0f) psi_axis<0>(p, u, o, 1, i, p.nx, gx);
+        if (gy != 0.0f) psi_axis<1>(p, u, o, p.nxp, j, p.ny, gy);
+        if (gz != 0.0f) psi_axis<2>(p, u, o, p.plane, k, p.nz, gz);
     }
-    if (gy != 0.0f) {
-        acc = __fadd_rn(acc, axis_term<1>(p, u, psi_old1, psi_new1, p.zeta[1], j, p.ny, o, p.nxp, gy));
-        any = true;
+}
+
+// zeta_a^n and the axis's term D1_a psi_a^n + zeta_a^n.
+template <int A>
+__device__ __forceinline__ float correct_axis(const CpmlArgs &p, const float *__restrict__ u, long long o,
+                                              long long st, int q0, int n, float g) {
+    float x[kLine], q[kLine];
+    line9(u, o, st, q0, n, x);
+    line9(p.psi[A], o, st, q0, n, q);
+    const float two_p = __fadd_rn(x[kRadius], x[kRadius]);
+    float d2 = pair_first(p.w[A][0], x[kRadius + 1], x[kRadius - 1], two_p);
+#pragma unroll
+    for (int m = 2; m <= kRadius; ++m) d2 = pair_acc(d2, p.w[A][m - 1], x[kRadius + m], x[kRadius - m], two_p);
+    const float dpsi = d1_of(q, p.inv_h[A]);
+    float *ze = p.zeta[A] + o;
+    const float z = __fmaf_rn(__ldg(p.b[A] + q0), *ze, __fmul_rn(g, __fadd_rn(d2, dpsi)));
+    *ze = z;
+    return __fadd_rn(dpsi, z);
+}
+
+__global__ void __launch_bounds__(kBX *kBY)
+    cpml_correct_kernel(const CpmlArgs p, const Boxes boxes, const float *__restrict__ u, float *__restrict__ uout) {
+    int i, j, k0, k1;
+    if (!layer_column(p, boxes, i, j, k0, k1)) return;
+    const float gx = __ldg(p.g[0] + i), gy = __ldg(p.g[1] + j);
+    long long o = (long long)k0 * p.plane + (long long)j * p.nxp + i;
+    for (int k = k0; k < k1; ++k, o += p.plane) {
+        const float gz = __ldg(p.g[2] + k);
+        float acc = 0.0f;
+        bool any = false;
+        if (gx != 0.0f) {
+            acc = __fadd_rn(acc, correct_axis<0>(p, u, o, 1, i, p.nx, gx));
+            any = true;
+        }
+        if (gy != 0.0f) {
+            acc = __fadd_rn(acc, correct_axis<1>(p, u, o, p.nxp, j, p.ny, gy));
+            any = true;
+        }
+        if (gz != 0.0f) {
+            acc = __fadd_rn(acc, correct_axis<2>(p, u, o, p.plane, k, p.nz, gz));
+            any = true;
+        }
+        if (any) uout[o] = __fmaf_rn(__ldg(p.c + o), acc, uout[o]);
     }
-    if (gz != 0.0f) {
-        acc = __fadd_rn(acc, axis_term<2>(p, u, psi_old2, psi_new2, p.zeta[2], k, p.nz, o, p.plane, gz));
-        any = true;
-    }
-    if (any) uout[o] = __fmaf_rn(__ldg(p.c + o), acc, uout[o]);
 }
 
 void add_box(Boxes &bx, int x0, int y0, int z0, int ex, int ey, int ez) {
@@ -145,8 +158,9 @@ void add_box(Boxes &bx, int x0, int y0, int z0, int ex, int ey, int ez) {
     b.x0 = x0; b.y0 = y0; b.z0 = z0; b.ex = ex; b.ey = ey; b.ez = ez;
     b.tx = (ex + kBX - 1) / kBX;
     b.ty = (ey + kBY - 1) / kBY;
+    b.tz = (ez + kZC - 1) / kZC;
     b.first = (int)bx.blocks;
-    bx.blocks += (long long)b.tx * b.ty * ez;
+    bx.blocks += (long long)b.tx * b.ty * b.tz;
 }
 
 // The layer cells as six disjoint slabs: z layers (whole planes), y layers
@@ -168,14 +182,14 @@ Boxes layer_boxes(const CpmlArgs &p) {
 
 }  // namespace
 
-cudaError_t launch_cpml_layers(const CpmlArgs &p, int n, const float *u, float *uout, cudaStream_t s) {
+cudaError_t launch_cpml_layers(const CpmlArgs &p, const float *u, float *uout, cudaStream_t s) {
     const Boxes bx = layer_boxes(p);
     if (bx.blocks == 0) return cudaSuccess;
     if (bx.blocks >= (1LL << 31)) return cudaErrorInvalidConfiguration;
-    float *const *po = p.psi[n & 1];
-    float *const *pn = p.psi[(n + 1) & 1];
-    cpml_layer_kernel<<<(unsigned)bx.blocks, dim3(kBX, kBY, 1), 0, s>>>(p, bx, u, uout, po[0], po[1], po[2], pn[0],
-                                                                          pn[1], pn[2]);
+    cpml_psi_kernel<<<(unsigned)bx.blocks, dim3(kBX, kBY, 1), 0, s>>>(p, bx, u);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    cpml_correct_kernel<<<(unsigned)bx.blocks, dim3(kBX, kBY, 1), 0, s>>>(p, bx, u, uout);
     return cudaGetLastError();
 }
 

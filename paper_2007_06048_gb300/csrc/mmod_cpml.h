@@ -6,22 +6,21 @@
 
 namespace mmod {
 
-// CPML layers (mmod_cpml.cu): memory variables psi_a (two sets, used in
-// turn) and zeta_a (padded volumes), per-cell coefficients b_a, g_a of each
-// axis (g = 0 outside the layers), the layer width, the step kernels'
-// weights and 1 / h_a.
+// CPML layers (mmod_cpml.cu): memory variables psi_a and zeta_a (padded
+// volumes), per-cell coefficients b_a, g_a of each axis (g = 0 outside the
+// layers), the layer width, the step kernels' weights and 1 / h_a.
 struct CpmlArgs {
     int nx, ny, nz, nxp;
     long long plane;
     int fs, nbl;
-    float *psi[2][3], *zeta[3];
+    float *psi[3], *zeta[3];
     const float *b[3], *g[3];
     float inv_h[3];
     float w[3][kRadius];
     const float *c;
 };
-// After the undamped step n (u = u^n, uout = u^{n+1}): the layer terms of
-// step n on the layer cells (reads psi[n & 1], writes psi[(n + 1) & 1]).
-cudaError_t launch_cpml_layers(const CpmlArgs &p, int n, const float *u, float *uout, cudaStream_t s);
+// After the undamped step (u = u^n, uout = u^{n+1}): the layer terms on the
+// layer cells, a psi pass and a correction pass.
+cudaError_t launch_cpml_layers(const CpmlArgs &p, const float *u, float *uout, cudaStream_t s);
 
 }  // namespace mmod
