@@ -76,6 +76,13 @@ struct VdArgs {
     // predecessor ends; it reads the predecessor's output after
     // griddepcontrol.wait and lets its own dependents start only after that
     int pdl;
+    // sources added by the pressure kernel of the TMA path (ngrp = 0: by the
+    // separate injection kernel): groups of sources on one grid point
+    int ngrp, nt, n;
+    const int *grp_ijk;        // [ngrp][3]
+    const long long *grp_off;
+    const int *grp_first, *src_id;
+    const float *src_scale, *wavelet;
     // receivers of the previous step, gathered by the velocity kernel
     int nrec;
     const long long *rec_off;
@@ -755,6 +762,25 @@ __global__ void __launch_bounds__(NT, 2)
         }
     }
 #undef VD_PSTEP
+    // Sources of this CTA's tile and planes, once its whole z range is stored
+    // (the block barrier makes the stores visible); one thread per group,
+    // sources in their order: the separate injection kernel's operations.
+    if (a.ngrp > 0) {
+        __syncthreads();
+        if (!*c.abort_flag)
+            for (int gi = tid; gi < a.ngrp; gi += NT) {
+                const int *q = a.grp_ijk + 3 * gi;
+                if (q[0] < x0 || q[0] >= x0 + TX || q[1] < y0 || q[1] >= y0 + TY || q[2] < z0 || q[2] >= z0 + T)
+                    continue;
+                float *dst = a.p + a.grp_off[gi];
+                float v = *dst;
+                for (int m = a.grp_first[gi]; m < a.grp_first[gi + 1]; ++m) {
+                    const int sid = a.src_id[m];
+                    v = __fmaf_rn(a.src_scale[sid], a.wavelet[(long long)sid * a.nt + a.n], v);
+                }
+                *dst = v;
+            }
+    }
     pdl_release();
     if (*c.abort_flag && tid == 0) {
         drain(c.bar_c, hi_c, PNSC);
@@ -821,6 +847,9 @@ __global__ void vd_source_scale(const float *vel, const float *rho, int nx, int 
 
 int grid_for(long long n, int block) { return (int)std::min<long long>((n + block - 1) / block, 152LL * 32); }
 
+// Source groups the pressure kernel adds itself (each CTA scans the list).
+constexpr int kFoldSources = 1024;
+
 }  // namespace
 }  // namespace mmod
 
@@ -839,6 +868,7 @@ struct mmod_vd {
     float w[3][kRadius] = {};
     // sources grouped by point, receivers
     long long *grp_off = nullptr;
+    int *grp_ijk = nullptr;           // [ngrp][3] grid point of each source group
     int *grp_first = nullptr, *src_id = nullptr, *src_ijk_d = nullptr;
     double *src_eps = nullptr;
     float *src_scale = nullptr;
@@ -961,6 +991,20 @@ bool vd_use_tma(const mmod_vd *h) { return h->tma_ok && h->kernel != MMOD_KERNEL
 cudaError_t enqueue_vd_step(mmod_vd *h, int n, const float *wav, float *traces_prev, cudaStream_t s, long long *cnt) {
     VdArgs a = vd_args(h);
     a.traces = traces_prev;
+    // the pressure kernel adds the sources when the TMA path runs and the
+    // source list is short (each CTA scans it); else the injection kernel
+    const bool fold = vd_use_tma(h) && h->ngrp > 0 && h->ngrp <= kFoldSources;
+    if (fold) {
+        a.ngrp = h->ngrp;
+        a.nt = h->cfg.nt;
+        a.n = n;
+        a.grp_ijk = h->grp_ijk;
+        a.grp_off = h->grp_off;
+        a.grp_first = h->grp_first;
+        a.src_id = h->src_id;
+        a.src_scale = h->src_scale;
+        a.wavelet = wav;
+    }
     cudaError_t e;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -986,7 +1030,7 @@ cudaError_t enqueue_vd_step(mmod_vd *h, int n, const float *wav, float *traces_p
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     *cnt += 2;
-    if (h->ngrp > 0) {
+    if (h->ngrp > 0 && !fold) {
         lc.gridDim = dim3((h->ngrp + 127) / 128);
         lc.blockDim = dim3(128);
         lc.dynamicSmemBytes = 0;
@@ -1063,7 +1107,7 @@ VdGeom plan_geom(int nx, int ny, int nz, int sms) {
 
 void vd_free(mmod_vd *h) {
     if (h->exec) cudaGraphExecDestroy(h->exec);
-    void *ptrs[] = {h->mem, h->prof, h->grp_off, h->grp_first, h->src_id, h->src_ijk_d, h->src_eps, h->src_scale,
+    void *ptrs[] = {h->mem, h->prof, h->grp_off, h->grp_ijk, h->grp_first, h->src_id, h->src_ijk_d, h->src_eps, h->src_scale,
                     h->rec_off, h->maxbits, h->bad, h->st_dense};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -1198,6 +1242,11 @@ MMOD_API mmod_status mmod_vd_create(const mmod_config *cfg, int device, mmod_vd 
             gfirst.push_back((int)sid.size());
         }
         h->ngrp = (int)goff.size();
+        std::vector<int> gijk;
+        for (auto &m : members) gijk.insert(gijk.end(), &h->src[3 * m[0]], &h->src[3 * m[0]] + 3);
+        VD_CREATE(cudaMalloc(&h->grp_ijk, sizeof(int) * gijk.size()), "source table");
+        VD_CREATE(cudaMemcpy(h->grp_ijk, gijk.data(), sizeof(int) * gijk.size(), cudaMemcpyHostToDevice),
+                  "source table");
         VD_CREATE(cudaMalloc(&h->grp_off, sizeof(long long) * goff.size()), "source table");
         VD_CREATE(cudaMalloc(&h->grp_first, sizeof(int) * gfirst.size()), "source table");
         VD_CREATE(cudaMalloc(&h->src_id, sizeof(int) * sid.size()), "source table");
