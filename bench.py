@@ -425,6 +425,10 @@ def measure_batched(M, dev, stream, fwd_gpts, reps=3):
     fused_variant = b.autotune(10, stream)
     b.forward(wav, trs, stream)
     ms_fused = time_calls(lambda: b.forward(wav, trs, stream), reps, stream)
+    b.set_mode(M.BATCH_PERSISTENT)            # one cooperative launch for every shot's loop
+    b.set_variant(2)
+    b.forward(wav, trs, stream)
+    ms_persist = time_calls(lambda: b.forward(wav, trs, stream), reps, stream)
     b.set_mode(M.BATCH_STREAMS)               # the default mode
     variant = b.autotune(10, stream)
     b.forward(wav, trs, stream)
@@ -443,11 +447,13 @@ def measure_batched(M, dev, stream, fwd_gpts, reps=3):
     return {"value": v, "unit": UNIT, "ms": ms, "loop_ms": loop_ms, "vs_forward": v / fwd_gpts,
             "hbm_frac": BYTES_PER_POINT * v / load_peaks()[0],
             "one_by_one": work / (ms_single * 1e-3) / 1e9, "fused": work / (ms_fused * 1e-3) / 1e9,
+            "persistent": work / (ms_persist * 1e-3) / 1e9,
             "fused_variant": M.mmod_tma_variant_name(fused_variant),
             "shots": len(shots), "nt": shots[0].nt,
             "points": int(sum(p.npoints for p in shots)), "variant": M.mmod_tma_variant_name(variant),
             "what": "mmod_batch_forward, streams mode: the shots' graphs overlap on four streams; "
-                    "fused: one launch per step for all shots"}
+                    "fused: one launch per step for all shots; persistent: one cooperative launch for every "
+                    "shot's whole loop"}
 
 
 def measure_free_surface(M, dev, stream, fwd_gpts, reps=3):

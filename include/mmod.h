@@ -347,7 +347,12 @@ mmod_status mmod_forward_noalloc(const mmod_config *cfg, int device, const float
  *     from and joined back to the caller's stream, so the shots' kernels
  *     overlap;
  *   MMOD_BATCH_FUSED: one kernel launch per time step covers all shots, the
- *     nt launches captured once into a CUDA graph.
+ *     nt launches captured once into a CUDA graph;
+ *   MMOD_BATCH_PERSISTENT: one cooperative launch runs every shot's whole
+ *     time loop: each work unit (a shot's 64 x 16 tile and z range) starts a
+ *     step once the neighbouring units of its shot have finished the
+ *     previous one (per-unit counters, waits bounded at 100 ms: a give-up
+ *     is reported as MMOD_ERR_TIMEOUT); TMA variants 2 and 5 only.
  * Both give every shot the bits it gets alone.  The batch refers to the
  * handles (they keep their buffers, models and geometry); destroy the batch
  * before its handles.  Each handle's buffers hold its shot's final state
@@ -372,7 +377,7 @@ mmod_status mmod_batch_forward(mmod_batch *b, const float *const *wavelets, floa
 mmod_status mmod_batch_set_variant(mmod_batch *b, int v);
 
 /* MMOD_BATCH_STREAMS or MMOD_BATCH_FUSED.  Errors: ARG. */
-enum { MMOD_BATCH_STREAMS = 0, MMOD_BATCH_FUSED = 1 };
+enum { MMOD_BATCH_STREAMS = 0, MMOD_BATCH_FUSED = 1, MMOD_BATCH_PERSISTENT = 2 };
 mmod_status mmod_batch_set_mode(mmod_batch *b, int mode);
 
 /* Device time (ms) of the last mmod_batch_forward's loop; waits for it. */

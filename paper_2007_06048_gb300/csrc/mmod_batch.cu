@@ -11,7 +11,11 @@
 //     tensor maps from a descriptor table in device memory.  The nt launches
 //     are captured once into a CUDA graph; the descriptor table is uploaded
 //     per call, so new wavelet / trace buffers need no new capture.  CTAs are
-//     ordered longest first so the last wave is made of short ones.
+//     ordered longest first so the last wave is made of short ones;
+//   persistent: one cooperative launch runs every shot's whole time loop; a
+//     work unit (a shot's tile and z range) starts a step when the
+//     neighbouring units of its shot have finished the previous one
+//     (per-unit counters, bounded waits).
 //
 // The autotuner times each compiled TMA variant (points per thread, z
 // unroll, ring depths) for a few steps on the real problem and keeps the
@@ -42,6 +46,9 @@ struct mmod_batch {
     ShotDesc *d_desc = nullptr;
     int *d_cta_shot = nullptr, *d_cta_local = nullptr;
     int nctas = 0;
+    // persistent mode: units in shot order, counters per unit, counter base per shot
+    int *d_unit_shot = nullptr, *d_unit_local = nullptr, *d_counter_base = nullptr, *d_counters = nullptr;
+    int units = 0;
     GraphSlot graph;
     cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;
     bool ran = false;
@@ -90,6 +97,10 @@ void free_batch(mmod_batch *b) {
     if (b->d_desc) cudaFree(b->d_desc);
     if (b->d_cta_shot) cudaFree(b->d_cta_shot);
     if (b->d_cta_local) cudaFree(b->d_cta_local);
+    if (b->d_unit_shot) cudaFree(b->d_unit_shot);
+    if (b->d_unit_local) cudaFree(b->d_unit_local);
+    if (b->d_counter_base) cudaFree(b->d_counter_base);
+    if (b->d_counters) cudaFree(b->d_counters);
     if (b->ev_t0) cudaEventDestroy(b->ev_t0);
     if (b->ev_t1) cudaEventDestroy(b->ev_t1);
 }
@@ -199,11 +210,14 @@ MMOD_API mmod_status mmod_batch_create(mmod_handle *const *shots, int nshots, mm
     b->nt = shots[0]->cfg.nt;
     DeviceGuard guard(b->device);
     b->desc.resize(nshots);
-    std::vector<int> cta_shot, cta_local, cta_len;
+    std::vector<int> cta_shot, cta_local, cta_len, counter_base;
     for (int i = 0; i < nshots; ++i) {
         mmod_handle *h = shots[i];
         ShotDesc &d = b->desc[i];
         std::memset(&d, 0, sizeof(d));
+        d.rec_start = h->fwd.g_start;
+        d.rec_idx = h->fwd.g_idx;
+        d.rec_boff = h->fwd.g_off;
         for (int k = 0; k < 2; ++k) {
             d.cur[k] = h->cur_map[k];
             d.prev[k] = h->prev_map[k];
@@ -216,6 +230,7 @@ MMOD_API mmod_status mmod_batch_create(mmod_handle *const *shots, int nshots, mm
         const int zlen = (h->cfg.nz + zchunks - 1) / zchunks;
         d.geom = Geom{p.tiles_x, p.tiles_y, (h->cfg.nz + zlen - 1) / zlen, zlen};
         d.nblocks = d.geom.tiles_x * d.geom.tiles_y * d.geom.zchunks;
+        counter_base.push_back((int)cta_shot.size());
         for (int lb = 0; lb < d.nblocks; ++lb) {
             const int chunk = lb / (d.geom.tiles_x * d.geom.tiles_y);
             cta_shot.push_back(i);
@@ -223,6 +238,8 @@ MMOD_API mmod_status mmod_batch_create(mmod_handle *const *shots, int nshots, mm
             cta_len.push_back(std::min(zlen, h->cfg.nz - chunk * zlen));
         }
     }
+    // persistent mode: units in shot order (unit = counter index)
+    const std::vector<int> unit_shot = cta_shot, unit_local = cta_local;
     // longest z ranges first: the last wave holds the short ones
     std::vector<int> order(cta_shot.size());
     std::iota(order.begin(), order.end(), 0);
@@ -249,6 +266,14 @@ MMOD_API mmod_status mmod_batch_create(mmod_handle *const *shots, int nshots, mm
     CKB(cudaMalloc(&b->d_cta_local, sizeof(int) * cl.size()));
     CKB(cudaMemcpy(b->d_cta_shot, cs.data(), sizeof(int) * cs.size(), cudaMemcpyHostToDevice));
     CKB(cudaMemcpy(b->d_cta_local, cl.data(), sizeof(int) * cl.size(), cudaMemcpyHostToDevice));
+    b->units = (int)unit_shot.size();
+    CKB(cudaMalloc(&b->d_unit_shot, sizeof(int) * unit_shot.size()));
+    CKB(cudaMalloc(&b->d_unit_local, sizeof(int) * unit_local.size()));
+    CKB(cudaMalloc(&b->d_counter_base, sizeof(int) * counter_base.size()));
+    CKB(cudaMalloc(&b->d_counters, sizeof(int) * unit_shot.size()));
+    CKB(cudaMemcpy(b->d_unit_shot, unit_shot.data(), sizeof(int) * unit_shot.size(), cudaMemcpyHostToDevice));
+    CKB(cudaMemcpy(b->d_unit_local, unit_local.data(), sizeof(int) * unit_local.size(), cudaMemcpyHostToDevice));
+    CKB(cudaMemcpy(b->d_counter_base, counter_base.data(), sizeof(int) * counter_base.size(), cudaMemcpyHostToDevice));
     CKB(cudaEventCreate(&b->ev_t0));
     CKB(cudaEventCreate(&b->ev_t1));
     CKB(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
@@ -286,7 +311,8 @@ MMOD_API mmod_status mmod_batch_set_variant(mmod_batch *b, int v) {
 
 MMOD_API mmod_status mmod_batch_set_mode(mmod_batch *b, int mode) {
     if (!b) return MMOD_ERR_ARG;
-    if (mode != MMOD_BATCH_STREAMS && mode != MMOD_BATCH_FUSED) return bfail(b, MMOD_ERR_ARG, "unknown batch mode");
+    if (mode != MMOD_BATCH_STREAMS && mode != MMOD_BATCH_FUSED && mode != MMOD_BATCH_PERSISTENT)
+        return bfail(b, MMOD_ERR_ARG, "unknown batch mode");
     b->mode = mode;
     return MMOD_OK;
 }
@@ -340,9 +366,38 @@ MMOD_API mmod_status mmod_batch_forward(mmod_batch *b, const float *const *wavel
     }
     for (int i = 0; i < ns; ++i)
         if (is_cpml(b->shots[i]))
-            return bfail(b, MMOD_ERR_UNSUPPORTED, "the fused batch kernel has no CPML; use MMOD_BATCH_STREAMS");
+            return bfail(b, MMOD_ERR_UNSUPPORTED, "the fused batch kernels have no CPML; use MMOD_BATCH_STREAMS");
+    int pgrid = 0;
+    if (b->mode == MMOD_BATCH_PERSISTENT) {
+        pgrid = batch_persistent_grid(b->variant, b->units);
+        if (pgrid < 1)
+            return bfail(b, MMOD_ERR_UNSUPPORTED, "the persistent batch kernel needs TMA variant 2 or 5");
+    }
     BCK(b, cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(ShotDesc) * ns, cudaMemcpyHostToDevice, s));
     if (mmod_status st = zero_states(b, s)) return st;
+    if (b->mode == MMOD_BATCH_PERSISTENT) {
+        // every shot's loop in one cooperative launch (no graph: one node)
+        BCK(b, cudaMemsetAsync(b->d_counters, 0, sizeof(int) * (size_t)b->units, s));
+        BCK(b, cudaEventRecord(b->ev_t0, s));
+        if (b->nt > 0) {
+            BatchPersistArgs pa{};
+            pa.n0 = 0;
+            pa.n1 = b->nt;
+            pa.units = b->units;
+            pa.unit_shot = b->d_unit_shot;
+            pa.unit_local = b->d_unit_local;
+            pa.counter_base = b->d_counter_base;
+            pa.counters = b->d_counters;
+            BCK(b, launch_step_tma_batch_persistent(b->variant, b->d_desc, pa, pgrid, s));
+        }
+        BCK(b, cudaEventRecord(b->ev_t1, s));
+        b->ran = b->nt > 0;
+        for (mmod_handle *h : b->shots) {
+            if (mmod_status st = check_latched(h)) return bfail(b, st, h->err);
+            h->ran = true;
+        }
+        return MMOD_OK;
+    }
     if (b->nt > 0) {
         GraphSlot &g = b->graph;
         if (!g.exec || g.kernel != b->variant || g.opts != b->pdl) {
@@ -399,6 +454,8 @@ MMOD_API float mmod_batch_last_loop_ms(mmod_batch *b) {
 
 MMOD_API mmod_status mmod_batch_autotune(mmod_batch *b, int steps, mmod_stream stream, int *variant_out) {
     if (!b || steps < 1) return MMOD_ERR_ARG;
+    if (b->mode == MMOD_BATCH_PERSISTENT)
+        return bfail(b, MMOD_ERR_UNSUPPORTED, "the persistent batch runs TMA variant 2 or 5; tune another mode");
     DeviceGuard guard(b->device);
     cudaStream_t s = (cudaStream_t)stream;
     const int ns = (int)b->shots.size();

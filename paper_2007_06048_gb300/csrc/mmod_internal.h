@@ -116,7 +116,23 @@ struct ShotDesc {
     float *traces;   // [nt][nrec] or null
     Geom geom;
     int nblocks;     // CTAs of this shot per step
+    // receivers bucketed per (64 x 16 tile, plane), for the persistent batch
+    const int *rec_start, *rec_idx;
+    const long long *rec_boff;
 };
+
+// Persistent batch run: steps n0 .. n1-1 of every shot in one cooperative
+// launch; unit u serves shot unit_shot[u] as its block unit_local[u]; the
+// shot's units signal counters[counter_base[shot] + block].
+struct BatchPersistArgs {
+    int n0, n1, units;
+    const int *unit_shot, *unit_local, *counter_base;
+    int *counters;
+};
+cudaError_t launch_step_tma_batch_persistent(int variant, const ShotDesc *shots, const BatchPersistArgs &pa, int grid,
+                                             cudaStream_t s);
+// CTAs of the persistent batch kernel of variant v that fit at once (0: none).
+int batch_persistent_grid(int variant, int units);
 cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap *cur_map,
                             const CUtensorMap *prev_map, const CUtensorMap *c_map,
                             const TmaPlan &plan, cudaStream_t s);

@@ -550,6 +550,63 @@ __global__ void __launch_bounds__(S::NT, S::MINB2)
     }
 }
 
+// Persistent batch run: every shot's time loop in one cooperative launch.
+// Unit u (the batch decomposition: shot unit_shot[u], block unit_local[u])
+// is always served by CTA u mod gridDim.x, so its own u^{n-1} are its own
+// earlier writes; it starts step n when the 26 neighbouring units of its
+// shot have completed step n-1 (bounded polls), then records its receivers
+// and signals its counter.  The shot's arguments are staged in shared
+// memory per unit, as in the one-launch-per-step batch kernel.
+template <class S>
+__global__ void __launch_bounds__(S::NT, S::MINB2)
+    step_tma_batch_persistent_kernel(const ShotDesc *__restrict__ shots, const BatchPersistArgs pa) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    StepArgs &sa = *reinterpret_cast<StepArgs *>(smem + batch_args_offset<S>());
+    const int *abort_flag = reinterpret_cast<const int *>(smem + (S::NSU * S::CUR + S::NSC * 2 * S::PC) * 4 +
+                                                          (S::NSU + S::NSC) * 8);
+    bool first = true;
+    for (int n = pa.n0; n < pa.n1; ++n) {
+        for (int unit = blockIdx.x; unit < pa.units; unit += gridDim.x) {
+            const int shot = __ldg(pa.unit_shot + unit), local = __ldg(pa.unit_local + unit);
+            const ShotDesc *d = shots + shot;
+            __syncthreads();   // the previous unit is done with the staged arguments
+            {
+                const int *src = reinterpret_cast<const int *>(&d->args);
+                int *dst = reinterpret_cast<int *>(&sa);
+                for (int i = threadIdx.x; i < (int)(sizeof(StepArgs) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+            }
+            __syncthreads();
+            float *uout = d->u[n & 1];
+            int *counters = pa.counters + __ldg(pa.counter_base + shot);
+            step_tma_body<S>(sa, StepVar{n, uout, nullptr, nullptr}, &d->cur[(n + 1) & 1], &d->prev[n & 1], &d->cmap,
+                             d->geom, local, d->nblocks, NeighborDep{counters, local, n, d->geom, first});
+            first = false;
+            __syncthreads();
+            if (*abort_flag) return;   // the body drained its copies; waiters give up on the error word
+            // receivers of this unit: u^{n+1} after its sources
+            if (d->traces && sa.nrec > 0) {
+                int b = local;
+                const int tx = b % d->geom.tiles_x;
+                b /= d->geom.tiles_x;
+                const int ty = b % d->geom.tiles_y;
+                const int z0 = (b / d->geom.tiles_y) * d->geom.zlen;
+                const int T = min(sa.nz - z0, d->geom.zlen);
+                const long long q = ((long long)ty * d->geom.tiles_x + tx) * sa.nz + z0;
+                const int lo = __ldg(d->rec_start + q), hi = __ldg(d->rec_start + q + T);
+                float *row = d->traces + (long long)n * sa.nrec;
+                for (int p = lo + threadIdx.x; p < hi; p += blockDim.x)
+                    row[__ldg(d->rec_idx + p)] = uout[__ldg(d->rec_boff + p)];
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                fence_proxy_async_global();
+                __threadfence();
+                st_release_gpu(counters + local, n + 1);
+            }
+        }
+    }
+}
+
 using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -771,6 +828,40 @@ cudaError_t launch_step_tma_persistent(const StepArgs &a, const TmaMaps &maps, c
         case 5: e = cudaLaunchKernelEx(&lc, step_tma_persistent_kernel<V24_2s>, a, maps, g, pa); break;
         default: return cudaErrorInvalidValue;
     }
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+int batch_persistent_grid(int variant, int units) {
+    const void *fn = variant == 2 ? (const void *)step_tma_batch_persistent_kernel<V22_4>
+                                  : (variant == 5 ? (const void *)step_tma_batch_persistent_kernel<V24_2s> : nullptr);
+    if (!fn || units < 1) return 0;
+    const int smem = kVariants[variant].batch_smem;
+    int dev = 0, sms = 0, occ = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kVariants[variant].nt, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return (int)std::min<long long>((long long)sms * occ, units);
+}
+
+cudaError_t launch_step_tma_batch_persistent(int variant, const ShotDesc *shots, const BatchPersistArgs &pa, int grid,
+                                             cudaStream_t s) {
+    if ((variant != 2 && variant != 5) || grid < 1) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(grid);
+    lc.blockDim = dim3(kVariants[variant].nt);
+    lc.dynamicSmemBytes = kVariants[variant].batch_smem;
+    lc.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;   // all CTAs resident: units wait on one another
+    attr[0].val.cooperative = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    cudaError_t e = variant == 2 ? cudaLaunchKernelEx(&lc, step_tma_batch_persistent_kernel<V22_4>, shots, pa)
+                                 : cudaLaunchKernelEx(&lc, step_tma_batch_persistent_kernel<V24_2s>, shots, pa);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

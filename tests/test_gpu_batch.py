@@ -1,7 +1,8 @@
 """Batched shots and the autotuner on the GPU.
 
 A batch advances shots of uneven grid sizes and damping widths together, on
-overlapping streams or in one fused launch per step; every shot must come
+overlapping streams, in one fused launch per step or in one persistent
+launch for the whole run; every shot must come
 out bit for bit as when it runs alone through mmod_forward (same per-point
 arithmetic, only the CTA decomposition differs).  The autotuner must pick a valid variant and leave
 results unchanged.
@@ -45,7 +46,7 @@ def _run_batch(shots, autotune=False, mode=M.BATCH_STREAMS):
     return [t.cpu().numpy() for t in tr], finals, v
 
 
-@pytest.mark.parametrize("mode", [M.BATCH_STREAMS, M.BATCH_FUSED])
+@pytest.mark.parametrize("mode", [M.BATCH_STREAMS, M.BATCH_FUSED, M.BATCH_PERSISTENT])
 def test_batch_matches_single_shots_bitwise(mode):
     shots = _shots()
     tr_b, u_b, _ = _run_batch(shots, mode=mode)
