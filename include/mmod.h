@@ -263,7 +263,8 @@ mmod_status mmod_set_tma_variant(mmod_handle *h, int v);
  *                         run (0 = as many as fit at once; a small value makes
  *                         each CTA serve many units, for tests);
  *   MMOD_OPT_TEST_STALL   1: test hook of the failure path.  The next
- *                         persistent run waits for neighbour counters that
+ *                         persistent run (of this handle, or of a persistent
+ *                         batch holding it) waits for neighbour counters that
  *                         nothing sets; every wait gives up after 100 ms, the
  *                         kernel returns and the call reports MMOD_ERR_TIMEOUT
  *                         (the handle stays in that state; the device and

@@ -381,7 +381,15 @@ MMOD_API mmod_status mmod_batch_forward(mmod_batch *b, const float *const *wavel
         BCK(b, cudaEventRecord(b->ev_t0, s));
         if (b->nt > 0) {
             BatchPersistArgs pa{};
+            // MMOD_OPT_TEST_STALL on any shot: start at step 1 with the
+            // counters at 0, so every unit waits for neighbours that never
+            // signal and gives up (bounded); the shots then report TIMEOUT
             pa.n0 = 0;
+            for (mmod_handle *h : b->shots)
+                if (h->test_stall) {
+                    pa.n0 = 1;
+                    h->test_stall = 0;
+                }
             pa.n1 = b->nt;
             pa.units = b->units;
             pa.unit_shot = b->d_unit_shot;

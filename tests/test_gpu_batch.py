@@ -100,3 +100,35 @@ def test_batch_mode_rejects_unknown():
     with pytest.raises(M.MmodError):
         b.set_mode(7)
     b.close()
+
+
+def test_persistent_batch_stall_reports_timeout_and_device_stays_usable():
+    """The failure path of the persistent batch: a shot's test hook makes
+    every unit wait for neighbour counters that nothing sets; the bounded
+    waits give up, the shots report MMOD_ERR_TIMEOUT, and a new batch on the
+    same device still gives every shot its single-run bits."""
+    torch = torch_cuda()
+    shots = _shots(nt=10)
+    props = [M.Propagator.from_problem(p) for p in shots]
+    for pr, p in zip(props, shots):
+        pr.set_model(torch.from_numpy(p.vel).cuda())
+    b = M.Batch(props)
+    b.set_mode(M.BATCH_PERSISTENT)
+    wav = [torch.from_numpy(p.wavelet).cuda() for p in shots]
+    tr = [torch.zeros((p.nt, len(p.rec_ijk)), device="cuda") for p in shots]
+    props[1].set_option(M.OPT_TEST_STALL, 1)
+    try:
+        b.forward(wav, tr)
+    except M.MmodError as e:
+        assert e.status == -5
+    torch.cuda.synchronize()
+    with pytest.raises(M.MmodError) as ei:
+        b.forward(wav, tr)
+    assert ei.value.status == -5             # latched on the shots' handles
+    b.close()
+    for pr in props:
+        pr.close()
+    tr_b, u_b, _ = _run_batch(shots, mode=M.BATCH_PERSISTENT)
+    for i, p in enumerate(shots):
+        tr_s, u_s, _ = run_gpu(p)
+        assert np.array_equal(tr_b[i], tr_s) and np.array_equal(u_b[i], u_s), i
