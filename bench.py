@@ -491,8 +491,8 @@ def measure_cpml(M, dev, stream, fwd_gpts, reps=3):
     prop.close()
     v = p.npoints * p.nt / (ms * 1e-3) / 1e9
     return {"value": v, "unit": UNIT, "ms": ms, "vs_forward": v / fwd_gpts, "workload": p.name + " + CPML (L=20)",
-            "what": "per step: the undamped step kernel, then one layer kernel over the six layer slabs "
-                    "(psi recomputed along each axis, zeta advanced, u^{n+1} corrected)"}
+            "what": "per step: the undamped step kernel, then two passes over the six layer slabs "
+                    "(psi_a^n from u^n; then zeta_a^n and the u^{n+1} correction)"}
 
 
 VD_BYTES_PER_POINT = 56   # velocity kernel 32 B + pressure kernel 24 B (FP32)

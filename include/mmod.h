@@ -262,6 +262,10 @@ mmod_status mmod_set_tma_variant(mmod_handle *h, int v);
  *   MMOD_OPT_PERSISTENT_CTAS  >= 0: at most this many CTAs for the persistent
  *                         run (0 = as many as fit at once; a small value makes
  *                         each CTA serve many units, for tests);
+ *   MMOD_OPT_CPML_PLANES  0..4096: planes per thread of the CPML layer
+ *                         passes (0 = the default); each layer slab's depth
+ *                         is split into equal ranges of at most this many
+ *                         planes; the same bits for any value;
  *   MMOD_OPT_TEST_STALL   1: test hook of the failure path.  The next
  *                         persistent run (of this handle, or of a persistent
  *                         batch holding it) waits for neighbour counters that
@@ -271,7 +275,7 @@ mmod_status mmod_set_tma_variant(mmod_handle *h, int v);
  *                         other handles stay usable).
  * Errors: ARG (unknown option or value). */
 enum { MMOD_OPT_PDL = 2, MMOD_OPT_CKPT_SCHEME = 3, MMOD_OPT_PERSISTENT = 4, MMOD_OPT_PERSISTENT_CTAS = 5,
-       MMOD_OPT_TEST_STALL = 6, MMOD_OPT_ZLEN = 7 };
+       MMOD_OPT_TEST_STALL = 6, MMOD_OPT_ZLEN = 7, MMOD_OPT_CPML_PLANES = 8 };
 enum { MMOD_SCHEME_SEGMENTS = 0, MMOD_SCHEME_REVOLVE = 1 };
 mmod_status mmod_set_option(mmod_handle *h, int option, int value);
 

@@ -32,6 +32,7 @@ OPT_PERSISTENT = 4
 OPT_PERSISTENT_CTAS = 5
 OPT_TEST_STALL = 6
 OPT_ZLEN = 7
+OPT_CPML_PLANES = 8
 BOUNDARY_DAMPING, BOUNDARY_CPML = 0, 1
 BATCH_STREAMS, BATCH_FUSED, BATCH_PERSISTENT = 0, 1, 2
 SCHEME_SEGMENTS, SCHEME_REVOLVE = 0, 1

@@ -268,6 +268,7 @@ CpmlArgs cpml_args(const mmod_handle *h) {
         p.w[0][m] = h->w.x[m]; p.w[1][m] = h->w.y[m]; p.w[2][m] = h->w.z[m];
     }
     p.c = h->c;
+    p.zc = h->cpml_planes > 0 ? h->cpml_planes : kCpmlPlanes;
     return p;
 }
 
@@ -481,7 +482,7 @@ mmod_status run_loop_graph(mmod_handle *h, GraphSlot &g, const Geometry &geo, co
         return MMOD_OK;
     }
     const int kern = use_tma(h) ? 100 + active_plan(h).variant : MMOD_KERNEL_SIMPLE;
-    const int opts = h->pdl + 2 * h->zlen_override;
+    const long long opts = h->pdl + 2LL * h->zlen_override + (1LL << 40) * h->cpml_planes;
     const void *key[4] = {wav, tr, &geo, nullptr};
     if (!g.exec || std::memcmp(g.key, key, sizeof(key)) != 0 || g.kernel != kern || g.opts != opts) {
         free_graph(g);
@@ -657,6 +658,11 @@ MMOD_API mmod_status mmod_set_option(mmod_handle *h, int option, int value) {
     if (option == MMOD_OPT_ZLEN) {
         if (value < 0) return fail(h, MMOD_ERR_ARG, "MMOD_OPT_ZLEN must be >= 0");
         h->zlen_override = value;
+        return MMOD_OK;
+    }
+    if (option == MMOD_OPT_CPML_PLANES) {
+        if (value < 0 || value > 4096) return fail(h, MMOD_ERR_ARG, "MMOD_OPT_CPML_PLANES must be in [0, 4096]");
+        h->cpml_planes = value;
         return MMOD_OK;
     }
     if (option == MMOD_OPT_PERSISTENT_CTAS) {

@@ -12,7 +12,8 @@
 // u^{n-1} + c L u^n + sources), then two passes over the six layer slabs
 // only: the psi pass (psi_a^n from u^n, in place) and the correction pass
 // (zeta_a^n, and u^{n+1} += c sum_a (D1_a psi_a^n + zeta_a^n)).  One thread
-// per layer column of up to 16 planes; each cell loads its 9-point lines
+// per layer column over a z range of at most CpmlArgs::zc planes (a block
+// takes 128 consecutive columns of one slab); each cell loads its 9-point lines
 // before the arithmetic, without bounds tests where the line stays inside
 // the grid.  u and psi are 0 outside the grid; with a free surface the top
 // layer is absent and the plane k = 0 is left alone (u, psi and zeta stay 0).
@@ -51,8 +52,10 @@ __device__ __forceinline__ void line9(const float *__restrict__ f, long long o, 
 }
 
 struct Box {
-    int x0, y0, z0, ex, ey, ez, tx, ty, tz;   // tz: z chunks of kZC planes
-    int first;                                // first block of this box
+    int x0, y0, z0, ex, ey, ez;
+    int ncb;      // blocks over the ex * ey columns of the box
+    int zc, tz;   // planes per z range, z ranges
+    int first;    // first block of this box
 };
 struct Boxes {
     Box b[6];
@@ -60,27 +63,27 @@ struct Boxes {
     long long blocks;
 };
 
-constexpr int kBX = 32, kBY = 4, kZC = 16;   // a block: 32 x 4 cells over up to kZC planes
+constexpr int kBT = 128;   // a block: 128 consecutive columns of one box (row-major in x, y)
 
 // Column of this thread in the layer slabs and its planes [k0, k1); false
-// when outside its box.
+// when outside its box.  Consecutive threads take consecutive columns of the
+// box's rows, so a 20-wide x slab fills whole warps (1.6 rows per warp).
 __device__ __forceinline__ bool layer_column(const CpmlArgs &p, const Boxes &boxes, int &i, int &j, int &k0,
                                              int &k1) {
     const int blk = blockIdx.x;
     int bi = 0;
     while (bi + 1 < boxes.n && blk >= boxes.b[bi + 1].first) ++bi;
     const Box &B = boxes.b[bi];
-    int local = blk - B.first;
-    const int tx = local % B.tx;
-    local /= B.tx;
-    const int ty = local % B.ty;
-    const int tz = local / B.ty;
-    const int li = tx * kBX + threadIdx.x, lj = ty * kBY + threadIdx.y;
-    if (li >= B.ex || lj >= B.ey) return false;
-    i = B.x0 + li;
+    const int local = blk - B.first;
+    const int cb = local % B.ncb;
+    const int tz = local / B.ncb;
+    const int col = cb * kBT + threadIdx.x;
+    if (col >= B.ex * B.ey) return false;
+    const int lj = col / B.ex;
+    i = B.x0 + (col - lj * B.ex);
     j = B.y0 + lj;
-    k0 = B.z0 + tz * kZC;
-    k1 = min(k0 + kZC, B.z0 + B.ez);
+    k0 = B.z0 + tz * B.zc;
+    k1 = min(k0 + B.zc, B.z0 + B.ez);
     if (p.fs && k0 == 0) k0 = 1;   // the free-surface plane stays 0
     return true;
 }
@@ -94,7 +97,7 @@ __device__ __forceinline__ void psi_axis(const CpmlArgs &p, const float *__restr
     *ps = __fmaf_rn(__ldg(p.b[A] + q0), *ps, __fmul_rn(g, d1_of(x, p.inv_h[A])));
 }
 
-__global__ void __launch_bounds__(kBX *kBY)
+__global__ void __launch_bounds__(kBT)
     cpml_psi_kernel(const CpmlArgs p, const Boxes boxes, const float *__restrict__ u) {
     int i, j, k0, k1;
     if (!layer_column(p, boxes, i, j, k0, k1)) return;
@@ -126,7 +129,7 @@ __device__ __forceinline__ float correct_axis(const CpmlArgs &p, const float *__
     return __fadd_rn(dpsi, z);
 }
 
-__global__ void __launch_bounds__(kBX *kBY)
+__global__ void __launch_bounds__(kBT)
     cpml_correct_kernel(const CpmlArgs p, const Boxes boxes, const float *__restrict__ u, float *__restrict__ uout) {
     int i, j, k0, k1;
     if (!layer_column(p, boxes, i, j, k0, k1)) return;
@@ -152,15 +155,16 @@ __global__ void __launch_bounds__(kBX *kBY)
     }
 }
 
-void add_box(Boxes &bx, int x0, int y0, int z0, int ex, int ey, int ez) {
+void add_box(Boxes &bx, int x0, int y0, int z0, int ex, int ey, int ez, int zc_max) {
     if (ex <= 0 || ey <= 0 || ez <= 0) return;
     Box &b = bx.b[bx.n++];
     b.x0 = x0; b.y0 = y0; b.z0 = z0; b.ex = ex; b.ey = ey; b.ez = ez;
-    b.tx = (ex + kBX - 1) / kBX;
-    b.ty = (ey + kBY - 1) / kBY;
-    b.tz = (ez + kZC - 1) / kZC;
+    b.ncb = (int)(((long long)ex * ey + kBT - 1) / kBT);
+    b.tz = (ez + zc_max - 1) / zc_max;    // equal ranges of at most zc_max planes
+    b.zc = (ez + b.tz - 1) / b.tz;
+    b.tz = (ez + b.zc - 1) / b.zc;
     b.first = (int)bx.blocks;
-    bx.blocks += (long long)b.tx * b.ty * b.tz;
+    bx.blocks += (long long)b.ncb * b.tz;
 }
 
 // The layer cells as six disjoint slabs: z layers (whole planes), y layers
@@ -170,13 +174,13 @@ Boxes layer_boxes(const CpmlArgs &p) {
     Boxes bx{};
     const int L = p.nbl;
     if (L <= 0) return bx;
-    const int zlo = p.fs ? 0 : L, zhi = p.nz - L;
-    if (!p.fs) add_box(bx, 0, 0, 0, p.nx, p.ny, L);
-    add_box(bx, 0, 0, p.nz - L, p.nx, p.ny, L);
-    add_box(bx, 0, 0, zlo, p.nx, L, zhi - zlo);
-    add_box(bx, 0, p.ny - L, zlo, p.nx, L, zhi - zlo);
-    add_box(bx, 0, L, zlo, L, p.ny - 2 * L, zhi - zlo);
-    add_box(bx, p.nx - L, L, zlo, L, p.ny - 2 * L, zhi - zlo);
+    const int zlo = p.fs ? 0 : L, zhi = p.nz - L, zc = p.zc > 0 ? p.zc : kCpmlPlanes;
+    if (!p.fs) add_box(bx, 0, 0, 0, p.nx, p.ny, L, zc);
+    add_box(bx, 0, 0, p.nz - L, p.nx, p.ny, L, zc);
+    add_box(bx, 0, 0, zlo, p.nx, L, zhi - zlo, zc);
+    add_box(bx, 0, p.ny - L, zlo, p.nx, L, zhi - zlo, zc);
+    add_box(bx, 0, L, zlo, L, p.ny - 2 * L, zhi - zlo, zc);
+    add_box(bx, p.nx - L, L, zlo, L, p.ny - 2 * L, zhi - zlo, zc);
     return bx;
 }
 
@@ -186,10 +190,10 @@ cudaError_t launch_cpml_layers(const CpmlArgs &p, const float *u, float *uout, c
     const Boxes bx = layer_boxes(p);
     if (bx.blocks == 0) return cudaSuccess;
     if (bx.blocks >= (1LL << 31)) return cudaErrorInvalidConfiguration;
-    cpml_psi_kernel<<<(unsigned)bx.blocks, dim3(kBX, kBY, 1), 0, s>>>(p, bx, u);
+    cpml_psi_kernel<<<(unsigned)bx.blocks, kBT, 0, s>>>(p, bx, u);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    cpml_correct_kernel<<<(unsigned)bx.blocks, dim3(kBX, kBY, 1), 0, s>>>(p, bx, u, uout);
+    cpml_correct_kernel<<<(unsigned)bx.blocks, kBT, 0, s>>>(p, bx, u, uout);
     return cudaGetLastError();
 }
 

@@ -18,7 +18,11 @@ struct CpmlArgs {
     float inv_h[3];
     float w[3][kRadius];
     const float *c;
+    int zc;   // planes per thread (the last z range of a slab may be shorter)
 };
+
+// Default planes per thread of the layer passes.
+constexpr int kCpmlPlanes = 5;
 // After the undamped step (u = u^n, uout = u^{n+1}): the layer terms on the
 // layer cells, a psi pass and a correction pass.
 cudaError_t launch_cpml_layers(const CpmlArgs &p, const float *u, float *uout, cudaStream_t s);

@@ -44,7 +44,8 @@ struct Geometry {
 struct GraphSlot {
     cudaGraphExec_t exec = nullptr;
     const void *key[4] = {nullptr, nullptr, nullptr, nullptr};
-    int kernel = -1, opts = -1;
+    int kernel = -1;
+    long long opts = -1;
     long long launches = 0;
 };
 
@@ -89,6 +90,7 @@ struct mmod_handle {
     int persistent_ctas = 0;            // MMOD_OPT_PERSISTENT_CTAS (0: as many as fit)
     int test_stall = 0;                 // MMOD_OPT_TEST_STALL (one run)
     int zlen_override = 0;              // MMOD_OPT_ZLEN (0: the plan's z ranges)
+    int cpml_planes = 0;                // MMOD_OPT_CPML_PLANES (0: the default)
     float *cpml_mem = nullptr;          // CPML: psi_x, psi_y, psi_z, zeta_x, zeta_y, zeta_z volumes
     float *cpml_bg = nullptr;           // CPML: b_x | b_y | b_z | g_x | g_y | g_z per cell
     mutable mmod::TmaPlan plan_tmp;     // active_plan() with the override applied

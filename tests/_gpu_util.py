@@ -10,7 +10,8 @@ def torch_cuda():
     return torch
 
 
-def run_gpu(p, kernel=M.KERNEL_AUTO, want_final=True, state=None, want_state=False, variant=None, pdl=None):
+def run_gpu(p, kernel=M.KERNEL_AUTO, want_final=True, state=None, want_state=False, variant=None, pdl=None,
+            options=None):
     """Forward p on cuda:0; returns traces (np), final u (np) and the propagator."""
     torch = torch_cuda()
     prop = M.Propagator.from_problem(p)
@@ -20,6 +21,8 @@ def run_gpu(p, kernel=M.KERNEL_AUTO, want_final=True, state=None, want_state=Fal
         prop.set_variant(variant)
     if pdl is not None:
         prop.set_option(M.OPT_PDL, pdl)
+    for opt, val in (options or {}).items():
+        prop.set_option(opt, val)
     prop.set_model(torch.from_numpy(np.ascontiguousarray(p.vel)).cuda())
     wav = torch.from_numpy(np.ascontiguousarray(p.wavelet, np.float32)).cuda()
     tr = torch.zeros((p.nt, len(p.rec_ijk)), device="cuda", dtype=torch.float32)

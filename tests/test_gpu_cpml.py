@@ -72,6 +72,17 @@ def test_cpml_interior_tiles_bitwise(orc, fs):
     assert trace_err(tr_t, tr_o, u_o) <= 1e-5
 
 
+@pytest.mark.parametrize("fs", [False, True])
+def test_cpml_planes_per_thread_keep_bits(fs):
+    """MMOD_OPT_CPML_PLANES only regroups the layer passes' work (z ranges of
+    1 to 100 planes per thread, slabs of 8 and 193 planes): the same bits."""
+    p = _cpml(W.tiny_problem(shape=(70, 45, 209), nt=30, nbl=8, nsrc=2, nrec=20, seed=14), fs=fs)
+    tr_d, u_d, _ = run_gpu(p)
+    for planes in (1, 3, 7, 100):
+        tr_p, u_p, _ = run_gpu(p, options={M.OPT_CPML_PLANES: planes})
+        assert np.array_equal(u_p, u_d) and np.array_equal(tr_p, tr_d), planes
+
+
 def test_cpml_absorbs_on_the_gpu():
     """Against a GPU run on a grid large enough that nothing returns in the
     window: the CPML of 10 cells leaves < 2 %, the damping layer much more."""
