@@ -101,6 +101,10 @@ void free_all(mmod_handle *h) {
     if (h->bad) cudaFree(h->bad);
     if (h->ev_t0) cudaEventDestroy(h->ev_t0);
     if (h->ev_t1) cudaEventDestroy(h->ev_t1);
+    for (cudaEvent_t e : h->ev_rows)
+        if (e) cudaEventDestroy(e);
+    if (h->ev_copied) cudaEventDestroy(h->ev_copied);
+    if (h->st_copy) cudaStreamDestroy(h->st_copy);
     if (h->cap) cudaStreamDestroy(h->cap);
     if (h->err_host) cudaFreeHost(h->err_host);
 }
@@ -393,6 +397,16 @@ static mmod_status enqueue_loop(mmod_handle *h, const Geometry &geo, const float
     const bool tma = use_tma(h);
     *count = 0;
     MMOD_CK(h, cudaEventRecordWithFlags(h->ev_t0, s, cudaEventRecordExternal));
+    // trace rows [0, done) are final: record the chunk events that wait for them
+    const bool marks = tr && ng > 0 && &geo == &h->fwd;
+    int next_mark = 0;
+    auto mark = [&](long long done) -> cudaError_t {
+        for (; marks && next_mark < mmod_handle::kTraceChunks && h->rows_at[next_mark] <= done; ++next_mark)
+            if (cudaError_t e = cudaEventRecordWithFlags(h->ev_rows[next_mark], s, cudaEventRecordExternal))
+                return e;
+        return cudaSuccess;
+    };
+    MMOD_CK(h, mark(0));
     StepArgs a = base_args(h, geo, wav);
     if (is_cpml(h)) {
         // CPML: the undamped step (sources included), the layer terms of
@@ -412,11 +426,13 @@ static mmod_status enqueue_loop(mmod_handle *h, const Geometry &geo, const float
                 MMOD_CK(h, launch_gather(a.uout, geo.gather_off, ng, tr + (long long)n * ng, s));
                 ++*count;
             }
+            MMOD_CK(h, mark(tma ? n : n + 1));
         }
         if (tma && nt > 0 && ng > 0 && tr) {
             MMOD_CK(h, launch_gather(h->u[(nt - 1) & 1], geo.gather_off, ng, tr + (long long)(nt - 1) * ng, s));
             ++*count;
         }
+        MMOD_CK(h, mark(nt));
         MMOD_CK(h, cudaEventRecordWithFlags(h->ev_t1, s, cudaEventRecordExternal));
         return MMOD_OK;
     }
@@ -431,12 +447,14 @@ static mmod_status enqueue_loop(mmod_handle *h, const Geometry &geo, const float
         a.traces = (n >= 1 && tr && ng > 0) ? tr + (long long)(n - 1) * ng : nullptr;
         MMOD_CK(h, enqueue_step(h, a, &h->cur_map[(n + 1) & 1], &h->prev_map[n & 1], tma,
                                 (tr && ng > 0) ? tr + (long long)n * ng : nullptr, s, count));
+        MMOD_CK(h, mark(tma ? n : n + 1));   // the TMA kernel of step n gathers row n - 1
     }
     if (tma && nt > 0 && ng > 0 && tr) {
         // u^{nt} sits in u[(nt - 1) & 1]; the last step kernel had no successor
         MMOD_CK(h, launch_gather(h->u[(nt - 1) & 1], geo.gather_off, ng, tr + (long long)(nt - 1) * ng, s));
         ++*count;
     }
+    MMOD_CK(h, mark(nt));
     MMOD_CK(h, cudaEventRecordWithFlags(h->ev_t1, s, cudaEventRecordExternal));
     return MMOD_OK;
 }
@@ -605,6 +623,12 @@ MMOD_API mmod_status mmod_create(const mmod_config *cfg, int device, mmod_handle
     CKC(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
     CKC(cudaEventCreate(&h->ev_t0));
     CKC(cudaEventCreate(&h->ev_t1));
+    CKC(cudaStreamCreateWithFlags(&h->st_copy, cudaStreamNonBlocking));
+    CKC(cudaEventCreateWithFlags(&h->ev_copied, cudaEventDisableTiming));
+    for (int i = 0; i < mmod_handle::kTraceChunks; ++i) {
+        CKC(cudaEventCreateWithFlags(&h->ev_rows[i], cudaEventDisableTiming));
+        h->rows_at[i] = (long long)cfg->nt * (i + 1) / mmod_handle::kTraceChunks;
+    }
     CKC(cudaHostAlloc(&h->err_host, sizeof(int), cudaHostAllocMapped));
     *h->err_host = 0;
     CKC(cudaHostGetDevicePointer(&h->err_dev, h->err_host, 0));
@@ -842,6 +866,9 @@ MMOD_API mmod_status mmod_forward(mmod_handle *h, const float *wavelet, float *t
     }
     if (is_cpml(h)) MMOD_CK(h, cudaMemsetAsync(h->cpml_mem, 0, 6 * sizeof(float) * (size_t)h->vol, s));
     h->state_pending = false;
+    // the loop runs as the captured graph (which records the trace-row
+    // events) unless the persistent kernel takes it
+    const bool looped_graph = c.nt > 0 && persistent_grid_of(h) == 0;
     if (c.nt > 0)
         if (mmod_status st = run_loop_graph(h, h->g_fwd, h->fwd, dwav, c.nrec > 0 ? dtr : nullptr, s, &launches))
             return st;
@@ -857,7 +884,24 @@ MMOD_API mmod_status mmod_forward(mmod_handle *h, const float *wavelet, float *t
         }
         ++launches;
     }
-    if (host_tr) MMOD_CK(h, cudaMemcpyAsync(traces, dtr, sizeof(float) * ntr, cudaMemcpyDeviceToHost, s));
+    if (host_tr) {
+        if (looped_graph) {
+            // rows of each chunk as soon as the loop graph has recorded them final
+            long long r0 = 0;
+            for (int i = 0; i < mmod_handle::kTraceChunks; ++i) {
+                const long long r1 = h->rows_at[i];
+                if (r1 <= r0) continue;
+                MMOD_CK(h, cudaStreamWaitEvent(h->st_copy, h->ev_rows[i], 0));
+                MMOD_CK(h, cudaMemcpyAsync(traces + r0 * c.nrec, dtr + r0 * c.nrec, sizeof(float) * (r1 - r0) * c.nrec,
+                                           cudaMemcpyDeviceToHost, h->st_copy));
+                r0 = r1;
+            }
+            MMOD_CK(h, cudaEventRecord(h->ev_copied, h->st_copy));
+            MMOD_CK(h, cudaStreamWaitEvent(s, h->ev_copied, 0));
+        } else {
+            MMOD_CK(h, cudaMemcpyAsync(traces, dtr, sizeof(float) * ntr, cudaMemcpyDeviceToHost, s));
+        }
+    }
     if (host_tr || (final_u && !is_device_ptr(final_u))) MMOD_CK(h, cudaStreamSynchronize(s));
     h->last_launches = launches;
     return check_latched(h);

@@ -81,6 +81,14 @@ struct mmod_handle {
 
     cudaStream_t cap = nullptr;         // private stream used only for graph capture
     cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;   // bracket the step loop
+    // Host traces download in kTraceChunks pieces while the loop runs: the
+    // forward loop graph records ev_rows[i] once trace rows [0, rows_at[i])
+    // are final; st_copy waits for each and copies the rows.
+    static constexpr int kTraceChunks = 8;
+    cudaEvent_t ev_rows[kTraceChunks] = {};
+    long long rows_at[kTraceChunks] = {};
+    cudaStream_t st_copy = nullptr;
+    cudaEvent_t ev_copied = nullptr;
     mmod::GraphSlot g_fwd, g_adj;
 
     mmod::TmaPlan plans[mmod::kMaxTmaVariants]{};
