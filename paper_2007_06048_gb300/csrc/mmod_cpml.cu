@@ -97,7 +97,9 @@ __device__ __forceinline__ void psi_axis(const CpmlArgs &p, const float *__restr
     *ps = __fmaf_rn(__ldg(p.b[A] + q0), *ps, __fmul_rn(g, d1_of(x, p.inv_h[A])));
 }
 
-__global__ void __launch_bounds__(kBT)
+// 16 blocks per SM: 32 registers, full occupancy for the latency-bound line
+// gathers (the correction pass would spill at that cap and keeps 40)
+__global__ void __launch_bounds__(kBT, 16)
     cpml_psi_kernel(const CpmlArgs p, const Boxes boxes, const float *__restrict__ u) {
     int i, j, k0, k1;
     if (!layer_column(p, boxes, i, j, k0, k1)) return;
