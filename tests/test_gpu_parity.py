@@ -151,6 +151,67 @@ def test_standing_wave_fp32():
     assert np.max(np.abs(u[inner] - expect[inner])) < 2e-5
 
 
+# P = sum of coef * s^a t^b r^c over centred coordinates s = (i - i_c) / 3
+# (t, r alike; off-grid centres): degree up to 8 along each axis, where Sec.
+# 3's order-8 second difference is exact (it is exact up to degree 9)
+_POLY = [(1.0, 8, 0, 0), (-0.7, 0, 8, 0), (0.4, 0, 0, 8), (1.3, 3, 2, 3), (-0.5, 5, 0, 4), (0.9, 2, 6, 0),
+         (0.6, 7, 1, 1), (-0.8, 1, 1, 7), (0.2, 0, 0, 0)]
+_TAYLOR8 = (8 / 5, -1 / 5, 8 / 315, -1 / 560)
+
+
+def _poly_and_laplacian(shape, h, scale=3.0):
+    nz, ny, nx = shape
+    S = (scale * h[0], scale * h[1], scale * h[2])
+    Z, Y, X = np.meshgrid((np.arange(nz) - (nz - 1) / 2 + 0.37) / scale, (np.arange(ny) - (ny - 1) / 2 - 0.21) / scale,
+                          (np.arange(nx) - (nx - 1) / 2 + 0.13) / scale, indexing="ij")
+    P = np.zeros(shape)
+    lap = np.zeros(shape)
+    for coef, a, b, c in _POLY:
+        P += coef * X ** a * Y ** b * Z ** c
+        if a >= 2:
+            lap += coef * a * (a - 1) * X ** (a - 2) * Y ** b * Z ** c / S[0] ** 2
+        if b >= 2:
+            lap += coef * b * (b - 1) * X ** a * Y ** (b - 2) * Z ** c / S[1] ** 2
+        if c >= 2:
+            lap += coef * c * (c - 1) * X ** a * Y ** b * Z ** (c - 2) / S[2] ** 2
+    return P, lap
+
+
+def _pair_rounding_bound(U, h):
+    """2^-24 times the sum over the stencil's pairs of |w| (|u(+m)| + |u(-m)| +
+    2|u|): the size of one FP32 rounding of every pair term, per point."""
+    U = np.abs(U.astype(np.float64))
+    out = np.zeros(U.shape)
+    for ax, hh in zip((2, 1, 0), h):
+        for m in range(1, 5):
+            out += abs(_TAYLOR8[m - 1]) / hh ** 2 * (np.roll(U, -m, axis=ax) + np.roll(U, m, axis=ax) + 2 * U)
+    return out * 2.0 ** -24
+
+
+@pytest.mark.parametrize("kernel", [M.KERNEL_TMA, M.KERNEL_SIMPLE])
+def test_polynomial_laplacian_fp32(kernel):
+    """The polynomial pin on the GPU: with u^{-1} = 2 u^0 = 2P (exact in FP32)
+    one undamped step leaves u^1 = c * L_h P, and L_h is exact on P (degree
+    <= 8 per axis; unequal spacings, heterogeneous velocity) at every point 4
+    cells inside the grid.  Per point the difference from c * Laplacian(P)
+    stays within 8 FP32 roundings of the stencil's pair terms (plus the
+    rounding of the product): an order-6 stencil, a dropped m = 4 pair or a
+    1 % error in its weight exceed that bound by factors of 10^3 to 10^5."""
+    shape, h, dt = (40, 36, 44), (9.0, 12.0, 10.0), 1.0e-3
+    rng = np.random.default_rng(31)
+    vel = rng.uniform(1500.0, 3000.0, shape).astype(np.float32)
+    P, lap = _poly_and_laplacian(shape, h)
+    P32 = P.astype(np.float32)
+    p = W.Problem("poly", vel, h, dt, 1, 0, np.zeros((0, 3), np.int32), np.zeros((0, 1), np.float32),
+                  np.zeros((0, 3), np.int32))
+    _, u1, _ = run_gpu(p, kernel=kernel, state=(2 * P32, P32))
+    c = (dt * dt) * vel.astype(np.float64) ** 2
+    inner = (slice(4, -4),) * 3
+    err = np.abs(u1.astype(np.float64) - c * lap)[inner]
+    bound = (8 * c * _pair_rounding_bound(P32, h) + 2.0 ** -22 * np.abs(c * lap))[inner]
+    assert np.all(err <= bound), float(np.max(err / bound))
+
+
 def test_error_paths():
     torch = torch_cuda()
     p = W.tiny_problem(shape=(16, 16, 16), nt=10, nbl=2)
