@@ -7,7 +7,8 @@
 //     D psi^n = 2 psi^{n+1} - E psi^{n+2} + C L psi^{n+1} + C R^T r^{n-1},
 // so the adjoint reuses the forward step kernels run backward in time: the
 // receivers become injection points (scale c, no cell volume), the residual
-// reversed in time is their wavelet, and the sources are gathered; the
+// read backward in time is their wavelet (rows [nt][nrec] as given: one
+// contiguous row per step), and the sources are gathered; the
 // adjoint source is a[s][n] = psi^{n+1}(x_s) / (hx hy hz).
 //
 // Gradient.  dJ/dc(x) = sum_n mu^{n+1}(x) (L u^n + s^n)(x); with
@@ -231,7 +232,7 @@ MMOD_API mmod_status mmod_adjoint(mmod_handle *h, const float *resid, float *adj
     if (mmod_status st = device_input(h, resid, nres, &h->st_tr, &dres, s)) return st;
     if (!h->st_adjw) MMOD_CK(h, cudaMalloc(&h->st_adjw, sizeof(float) * std::max<size_t>(nres, 1)));
     if (!h->st_adjg) MMOD_CK(h, cudaMalloc(&h->st_adjg, sizeof(float) * std::max<size_t>(nadj, 1)));
-    if (nres) MMOD_CK(h, launch_reverse_transpose(dres, c.nt, c.nrec, h->st_adjw, s));
+    if (nres) MMOD_CK(h, cudaMemcpyAsync(h->st_adjw, dres, sizeof(float) * nres, cudaMemcpyDeviceToDevice, s));
     MMOD_CK(h, cudaMemsetAsync(h->u[0], 0, sizeof(float) * (size_t)h->vol, s));
     MMOD_CK(h, cudaMemsetAsync(h->u[1], 0, sizeof(float) * (size_t)h->vol, s));
     h->state_pending = false;
@@ -254,7 +255,7 @@ MMOD_API mmod_status mmod_adjoint(mmod_handle *h, const float *resid, float *adj
             MMOD_CK(h, cudaStreamSynchronize(s));
         }
     }
-    h->last_launches = launches + (nres ? 1 : 0);
+    h->last_launches = launches;
     return check_latched(h);
 }
 
@@ -287,7 +288,7 @@ MMOD_API mmod_status mmod_gradient(mmod_handle *h, const float *wavelet, const f
     if (mmod_status st = device_input(h, resid, (size_t)c.nrec * nt, &h->st_tr, &dres, s)) return st;
     const size_t nres = (size_t)nt * c.nrec;
     if (!h->st_adjw) MMOD_CK(h, cudaMalloc(&h->st_adjw, sizeof(float) * std::max<size_t>(nres, 1)));
-    if (nres) MMOD_CK(h, launch_reverse_transpose(dres, nt, c.nrec, h->st_adjw, s));
+    if (nres) MMOD_CK(h, cudaMemcpyAsync(h->st_adjw, dres, sizeof(float) * nres, cudaMemcpyDeviceToDevice, s));
 
     MMOD_CK(h, cudaMemsetAsync(h->u[0], 0, vb, s));
     MMOD_CK(h, cudaMemsetAsync(h->u[1], 0, vb, s));

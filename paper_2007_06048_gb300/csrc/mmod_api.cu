@@ -354,6 +354,15 @@ StepArgs base_args(mmod_handle *h, const Geometry &geo, const float *wavelet) {
     a.ex = h->eta; a.ey = h->eta + h->cfg.nx; a.ez = h->eta + h->cfg.nx + h->cfg.ny;
     a.inj = geo.inj.view();
     a.wavelet = wavelet;
+    a.wrs = h->cfg.nt;
+    a.wcs = 1;
+    if (&geo == &h->adj && wavelet) {
+        // the adjoint's injection points are the receivers and its wavelet
+        // the residual [nt][nrec] in time order: step n reads row nt-1-n
+        a.wavelet = wavelet + (long long)(h->cfg.nt - 1) * h->cfg.nrec;
+        a.wrs = 1;
+        a.wcs = -(long long)h->cfg.nrec;
+    }
     a.nrec = geo.ngather; a.rec_off = geo.gather_off;
     a.traces = nullptr;
     a.err = h->err_dev;

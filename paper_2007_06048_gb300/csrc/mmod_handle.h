@@ -73,7 +73,7 @@ struct mmod_handle {
     float *st_vol = nullptr;            // dense [nz][ny][nx] staging (lazy)
     float *st_wav = nullptr;            // [nsrc][nt] staging (lazy)
     float *st_tr = nullptr;             // [nt][nrec] staging (lazy)
-    float *st_adjw = nullptr;           // adjoint injection rows [nrec][nt] (lazy)
+    float *st_adjw = nullptr;           // adjoint residual [nt][nrec], the copy the graph reads (lazy)
     float *st_adjg = nullptr;           // adjoint gathers [nt][nsrc] (lazy)
     float *st_adjo = nullptr;           // adjoint output staging [nsrc][nt] (lazy)
     int *err_host = nullptr;            // mapped pinned word: a kernel gave up waiting

@@ -35,7 +35,7 @@ struct StepArgs {
     int nxp;                   // padded row length (floats), multiple of 32
     long long plane;           // nxp * ny
     int nbl;                   // damping width: inner region is [nbl, n - 1 - nbl]
-    int nt;                    // steps of the run (wavelet row length)
+    int nt;                    // steps of the run
     int n;                     // this step: computes u^{n+1}
     Weights w;                 // c_m / h_a^2
     const float *ucur;         // u^n       (padded layout)
@@ -44,7 +44,9 @@ struct StepArgs {
     const float *c;            // dt^2 v^2  (padded layout)
     const float *ex, *ey, *ez; // dt * eta per axis
     InjTable inj;              // sources of this run
-    const float *wavelet;      // [rows][nt]
+    const float *wavelet;      // w(row, n) = wavelet[row * wrs + n * wcs]
+    long long wrs, wcs;        // [rows][nt]: (nt, 1); the adjoint reads its residual
+                               // [nt][nrec] backward in time: (1, -nrec)
     // receivers: the kernel of step n copies u^n (its ucur) into traces[n-1]
     int nrec;
     const long long *rec_off;             // padded offsets
@@ -66,11 +68,59 @@ __device__ __forceinline__ void inject_point_at(const StepArgs &a, float *uout, 
     float v = *dst;
     for (int s = __ldg(a.inj.pt_first + p); s < __ldg(a.inj.pt_first + p + 1); ++s)
         v = add_source(v, __ldg(a.inj.src_scale + s),
-                       __ldg(a.wavelet + (long long)__ldg(a.inj.src_row + s) * a.nt + n), r);
+                       __ldg(a.wavelet + (long long)__ldg(a.inj.src_row + s) * a.wrs + (long long)n * a.wcs), r);
     *dst = v;
 }
 
 __device__ __forceinline__ void inject_point(const StepArgs &a, int p) { inject_point_at(a, a.uout, a.n, p); }
+
+// The same for injection points [lo, hi), thread t of nthreads: each thread
+// takes up to four points at a time and issues the table, profile, wavefield
+// and wavelet loads of all four before it applies any, so the dependent loads
+// of different points overlap (a receiver plane injected by the adjoint gives
+// a CTA about a thousand points).  Per point: the same operations in the same
+// order as inject_point_at.
+__device__ __forceinline__ void inject_points(const StepArgs &a, float *uout, int n, int lo, int hi, int t,
+                                              int nthreads) {
+    constexpr int G = 4;
+    for (int base = lo + t; base < hi; base += G * nthreads) {
+        int p[G], s0[G], s1[G];
+        long long off[G];
+        float e[G], v[G], sc[G], w[G];
+        bool ok[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            p[q] = base + q * nthreads;
+            ok[q] = p[q] < hi;
+            if (!ok[q]) p[q] = lo;   // a valid entry, not applied
+        }
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            const int i = __ldg(a.inj.pt_i + p[q]), j = __ldg(a.inj.pt_j + p[q]), k = __ldg(a.inj.pt_k + p[q]);
+            e[q] = __fadd_rn(__fadd_rn(__ldg(a.ex + i), __ldg(a.ey + j)), __ldg(a.ez + k));
+            off[q] = __ldg(a.inj.pt_off + p[q]);
+            s0[q] = __ldg(a.inj.pt_first + p[q]);
+            s1[q] = __ldg(a.inj.pt_first + p[q] + 1);
+        }
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            v[q] = uout[off[q]];
+            sc[q] = __ldg(a.inj.src_scale + s0[q]);
+            w[q] = __ldg(a.wavelet + (long long)__ldg(a.inj.src_row + s0[q]) * a.wrs + (long long)n * a.wcs);
+        }
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            if (!ok[q]) continue;
+            const float r = damp_factor(e[q]);
+            float x = add_source(v[q], sc[q], w[q], r);   // every point has at least one source
+            for (int s = s0[q] + 1; s < s1[q]; ++s)
+                x = add_source(x, __ldg(a.inj.src_scale + s),
+                               __ldg(a.wavelet + (long long)__ldg(a.inj.src_row + s) * a.wrs + (long long)n * a.wcs),
+                               r);
+            uout[off[q]] = x;
+        }
+    }
+}
 
 // Host helpers shared by the entry points (mmod_api.cu).
 void damping_profile(int n, int nbl, double h, double vmax, double R, double dt, float *out);
@@ -183,7 +233,6 @@ cudaError_t launch_source_scale(const float *vel, int nx, int ny, int nsrc, cons
                                 float *scale, cudaStream_t s);
 // Adjoint helpers: resid [nt][nrec] -> out [nrec][nt] reversed in time;
 // g [nt][nsrc] -> adj [nsrc][nt], adj[s][n] = g[nt-1-n][s] * scale.
-cudaError_t launch_reverse_transpose(const float *in, int nt, int ncol, float *out, cudaStream_t s);
 cudaError_t launch_unreverse_transpose(const float *g, int nt, int ncol, double scale, float *out,
                                        cudaStream_t s);
 // Gradient helpers (mmod_setup.cu).

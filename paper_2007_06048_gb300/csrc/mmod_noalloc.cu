@@ -313,6 +313,8 @@ extern "C" __attribute__((visibility("default"))) mmod_status mmod_forward_noall
     a.inj.pt_off = pt_off_d; a.inj.src_scale = src_scale;
     a.inj.tiles_x = tiles_x; a.inj.tiles_y = tiles_y; a.inj.npts = npt;
     a.wavelet = wavelet;
+    a.wrs = c.nt;
+    a.wcs = 1;
     a.fs = c.free_surface;
     a.pdl = 0;
     a.nrec = c.nrec; a.rec_off = rec_off;

@@ -165,17 +165,6 @@ extern "C" __attribute__((visibility("default"))) int mmod_check_recip(int n, un
 namespace mmod {
 namespace {
 
-// out[c][m] = in[nt-1-m][c]: the residual, reversed in time, as one row per
-// injection point (the wavelet layout of the adjoint run).
-__global__ void reverse_transpose_kernel(const float *__restrict__ in, int nt, int ncol, float *__restrict__ out) {
-    const long long total = (long long)nt * ncol;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
-         q += (long long)gridDim.x * blockDim.x) {
-        const int col = (int)(q / nt), m = (int)(q % nt);
-        out[q] = in[(long long)(nt - 1 - m) * ncol + col];
-    }
-}
-
 // adj[s][n] = g[nt-1-n][s] * scale.
 __global__ void unreverse_transpose_kernel(const float *__restrict__ g, int nt, int ncol, double scale,
                                            float *__restrict__ adj) {
@@ -270,12 +259,6 @@ inline int grid2(long long n) {
 }
 
 }  // namespace
-
-cudaError_t launch_reverse_transpose(const float *in, int nt, int ncol, float *out, cudaStream_t s) {
-    if ((long long)nt * ncol == 0) return cudaSuccess;
-    reverse_transpose_kernel<<<grid2((long long)nt * ncol), 256, 0, s>>>(in, nt, ncol, out);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_unreverse_transpose(const float *g, int nt, int ncol, double scale, float *out,
                                        cudaStream_t s) {

@@ -445,7 +445,7 @@ __device__ __forceinline__ void step_tma_body(const StepArgs &a, const StepVar &
     if (!*c.abort_flag && a.inj.npts > 0) {
         const long long b = ((long long)(c.y0 / kInjTileY) * a.inj.tiles_x + c.x0 / kInjTileX) * a.nz + c.z0;
         const int lo = __ldg(a.inj.tile_start + b), hi = __ldg(a.inj.tile_start + b + T);
-        for (int p = lo + tid; p < hi; p += S::NT) inject_point_at(a, v.uout, v.n, p);
+        inject_points(a, v.uout, v.n, lo, hi, tid, S::NT);
     }
     // After a give-up, wait (bounded) for the copies this CTA still has in
     // flight (the latest sequence of every slot) before its shared memory is
