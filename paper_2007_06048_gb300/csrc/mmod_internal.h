@@ -231,8 +231,8 @@ cudaError_t launch_model_fill(const float *vel, int nx, int ny, int nz, int nxp,
 cudaError_t launch_source_scale(const float *vel, int nx, int ny, int nsrc, const int *src_i,
                                 const int *src_j, const int *src_k, double dt, double cell,
                                 float *scale, cudaStream_t s);
-// Adjoint helpers: resid [nt][nrec] -> out [nrec][nt] reversed in time;
-// g [nt][nsrc] -> adj [nsrc][nt], adj[s][n] = g[nt-1-n][s] * scale.
+// Adjoint output: the gathers g [nt][nsrc] of the backward run ->
+// adj [nsrc][nt], adj[s][n] = g[nt-1-n][s] * scale.
 cudaError_t launch_unreverse_transpose(const float *g, int nt, int ncol, double scale, float *out,
                                        cudaStream_t s);
 // Gradient helpers (mmod_setup.cu).
