@@ -93,8 +93,8 @@ struct mmod_handle {
 
     mmod::TmaPlan plans[mmod::kMaxTmaVariants]{};
     int variant = -1;                   // -1: automatic choice
-    int pdl = 1;                        // MMOD_OPT_PDL
-    int persistent = 1;                 // MMOD_OPT_PERSISTENT
+    int pdl = 1;                        // MMOD_OPT_PDL (set at create)
+    int persistent = 0;                 // MMOD_OPT_PERSISTENT (set at create)
     int persistent_ctas = 0;            // MMOD_OPT_PERSISTENT_CTAS (0: as many as fit)
     int test_stall = 0;                 // MMOD_OPT_TEST_STALL (one run)
     int zlen_override = 0;              // MMOD_OPT_ZLEN (0: the plan's z ranges)
