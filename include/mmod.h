@@ -124,6 +124,10 @@ mmod_status mmod_set_model(mmod_handle *h, const float *vel, mmod_stream stream)
  *   traces   [nt][nrec] FP32 output, traces[n][r] = u^{n+1}(x_r); may be
  *            NULL when nrec == 0
  *   final_u  optional [nz][ny][nx] FP32 output u^{nt}
+ * Each pointer may be host or device memory.  Host traces are downloaded
+ * in eight row chunks on an internal stream while the time loop still runs
+ * (each chunk once the steps that finish its rows are done); with any host
+ * output the call returns after the data is in host memory.
  * Errors: STATE (no model), ARG, CUDA, TIMEOUT. */
 mmod_status mmod_forward(mmod_handle *h, const float *wavelet, float *traces,
                          float *final_u, mmod_stream stream);
