@@ -153,6 +153,87 @@ def test_standing_wave_fp32():
         assert rel_l2(out[1 + a][inner], (V[a] / V0[a] * st[1 + a])[inner]) < 2e-6
 
 
+# P = sum of coef * s^a t^b r^c, s = (i - i_c + 0.13) / 3 (t, r alike with
+# other offsets): degree <= 8 per axis, where the order-8 staggered
+# differences are exact (Sec. 3 system; see the oracle's pins)
+_POLY = [(1.0, 8, 0, 0), (-0.7, 0, 8, 0), (0.4, 0, 0, 8), (1.3, 3, 2, 3), (-0.5, 5, 0, 4), (0.9, 2, 6, 0),
+         (0.6, 7, 1, 1), (-0.8, 1, 1, 7), (0.2, 0, 0, 0)]
+_A8 = (1225 / 1024, -245 / 3072, 49 / 5120, -5 / 7168)
+_NP_AXIS = (2, 1, 0)   # array axis of x, y, z
+
+
+def _poly_terms(shape, h, half_axis, deriv, scale=3.0):
+    """sum over _POLY of d^deriv/dx_a^deriv (a = each axis in turn when
+    deriv > 0, summed) at the grid points, shifted half a cell along
+    half_axis; deriv 0: P itself."""
+    nz, ny, nx = shape
+    off = (0.13, -0.21, 0.37)
+    t = [(np.arange(n) - (n - 1) / 2 + off[a] + (0.5 if a == half_axis else 0.0)) / scale
+         for a, n in enumerate((nx, ny, nz))]
+    Z, Y, X = np.meshgrid(t[2], t[1], t[0], indexing="ij")
+    base = (X, Y, Z)
+    out = np.zeros(shape)
+    for coef, *pw in _POLY:
+        axes = [None] if deriv == 0 else ([half_axis] if deriv == 1 else [0, 1, 2])
+        for ax in axes:
+            f = [base[a] ** pw[a] for a in range(3)]
+            if ax is not None:
+                k = pw[ax]
+                if k < deriv:
+                    continue
+                f[ax] = (k if deriv == 1 else k * (k - 1)) * base[ax] ** (k - deriv) / (scale * h[ax]) ** deriv
+            out += coef * f[0] * f[1] * f[2]
+    return out
+
+
+def _pair_sum(U, axis, h, shift_plus, shift_minus):
+    """sum_m |a_m| (|U(i + m + shift_plus)| + |U(i - m + shift_minus)|) / h."""
+    U = np.abs(U.astype(np.float64))
+    ax = _NP_AXIS[axis]
+    out = np.zeros(U.shape)
+    for m in range(1, 5):
+        out += abs(_A8[m - 1]) * (np.roll(U, -(m + shift_plus), axis=ax) + np.roll(U, m - shift_minus, axis=ax))
+    return out / h[axis]
+
+
+@pytest.mark.parametrize("kernel", [M.KERNEL_TMA, M.KERNEL_SIMPLE])
+def test_polynomial_step_fp32(kernel):
+    """The staggered polynomial pin on the GPU: from p^0 = P (degree <= 8 per
+    axis), v^{-1/2} = 0 and a constant density, one step gives
+    v_a^{1/2} = dt b dP/dx_a at the half points (D+ exact) and
+    p^1 = P + dt^2 v^2 Laplacian(P) (D- D+ exact), per point within 8 FP32
+    roundings of the pair terms (plus the products' rounding); a 1 % error
+    in a_4 or order-6 weights exceed the bounds 400 to 10^5 times."""
+    shape, h, dt, rho = (44, 40, 48), (9.0, 12.0, 10.0), 1.0e-3, 1800.0
+    rng = np.random.default_rng(31)
+    vel = rng.uniform(1500.0, 3000.0, shape).astype(np.float32)
+    P = _poly_terms(shape, h, None, 0)
+    P32 = P.astype(np.float32)
+    st = np.zeros((4,) + shape, np.float32)
+    st[0] = P32
+    p = W.Problem("poly", vel, h, dt, 1, 0, np.zeros((0, 3), np.int32), np.zeros((0, 1), np.float32),
+                  np.zeros((0, 3), np.int32), rho=np.full(shape, rho, np.float32))
+    _, out, _ = run_vd(p, kernel=kernel, state=st)
+    eps = 2.0 ** -24
+    dtb = dt / rho
+    inner_v = (slice(4, -5),) * 3
+    vbound = []
+    for a in range(3):
+        exact = dtb * _poly_terms(shape, h, a, 1)
+        bound = 8 * eps * dtb * _pair_sum(P32, a, h, 0, 1) + 4 * eps * np.abs(exact)
+        vbound.append(bound)
+        err = np.abs(out[1 + a].astype(np.float64) - exact)
+        assert np.all(err[inner_v] <= bound[inner_v]), (a, float(np.max(err[inner_v] / bound[inner_v])))
+    dtK = dt * rho * vel.astype(np.float64) ** 2
+    update = dt * dt * vel.astype(np.float64) ** 2 * _poly_terms(shape, h, None, 2)
+    bound = 2 * eps * np.abs(P) + 4 * eps * np.abs(update)
+    for a in range(3):
+        bound += dtK * (8 * eps * _pair_sum(out[1 + a], a, h, -1, 0) + _pair_sum(vbound[a], a, h, -1, 0))
+    inner_p = (slice(8, -8),) * 3
+    err = np.abs(out[0].astype(np.float64) - (P + update))
+    assert np.all(err[inner_p] <= bound[inner_p]), float(np.max(err[inner_p] / bound[inner_p]))
+
+
 def test_zero_steps_and_no_sources_or_receivers(orc):
     p = W.tiny_problem_vd(shape=(20, 21, 22), nt=0, nbl=2, nsrc=1, nrec=2)
     tr, st, _ = run_vd(p)
