@@ -306,20 +306,49 @@ MMOD_API mmod_status mmod_gradient(mmod_handle *h, const float *wavelet, const f
         fa.uout = h->u[n & 1];
         return enqueue_step(h, fa, &h->cur_map[(n + 1) & 1], &h->prev_map[n & 1], tma, nullptr, s, &launches);
     };
-    // adjoint step of forward step n, then the imaging term of step n from
-    // u^{n+1}, u^n, u^{n-1}
-    auto adj_step_and_image = [&](int n, const float *un, const float *uc, const float *up) {
-        const int m = nt - 1 - n;   // adjoint step m produces psi^{n+1}
+    // adjoint step of forward step n: adjoint step m = nt-1-n produces
+    // psi^{n+1} in psi[m & 1] (psi^{n+2} stays in the other buffer until the
+    // next adjoint step)
+    auto adj_step = [&](int n) {
+        const int m = nt - 1 - n;
         aa.n = m;
         aa.ucur = gw.psi[(m + 1) & 1];
         aa.uprev = gw.psi[m & 1];
         aa.uout = gw.psi[m & 1];
-        cudaError_t e = enqueue_step(h, aa, tma ? &gw.psi_cur[(m + 1) & 1] : nullptr,
-                                     tma ? &gw.psi_prev[m & 1] : nullptr, tma, nullptr, s, &launches);
-        if (e != cudaSuccess) return e;
+        return enqueue_step(h, aa, tma ? &gw.psi_cur[(m + 1) & 1] : nullptr, tma ? &gw.psi_prev[m & 1] : nullptr,
+                            tma, nullptr, s, &launches);
+    };
+    // imaging terms of forward steps n (and n - 1 when pair) from u[t] =
+    // u^{n+1-t}, after their adjoint steps: psi^{n+1} in psi[(nt-1-n) & 1],
+    // psi^n in the other buffer
+    auto image = [&](int n, const float *const *u, bool pair) {
+        const int m = nt - 1 - n;
+        const float *ps[2] = {gw.psi[m & 1], gw.psi[(m + 1) & 1]};
         ++launches;
-        return launch_imaging(gw.psi[m & 1], un, uc, up, h->c, aa.ex, aa.ey, aa.ez, c.nx, c.ny, c.nz, h->nxp,
-                              gw.gradc, s);
+        return launch_imaging(pair ? 2 : 1, ps, u, h->c, aa.ex, aa.ey, aa.ez, c.nx, c.ny, c.nz, h->nxp, gw.gradc,
+                              s);
+    };
+    auto adj_step_and_image = [&](int n, const float *un, const float *uc, const float *up) {
+        cudaError_t e = adj_step(n);
+        if (e != cudaSuccess) return e;
+        const float *u[3] = {un, uc, up};
+        return image(n, u, false);
+    };
+    // steps hi down to lo with their states in st(j) = u^{j-1} (j = lo .. hi
+    // + 2): two adjoint steps, then one imaging pass over both (the same
+    // accumulation order as one pass per step, u^n, u^{n-1}, c and grad_c
+    // read once per pair)
+    auto backward_range = [&](int hi, int lo, auto st) -> cudaError_t {
+        int n = hi;
+        for (; n - 1 >= lo; n -= 2) {
+            cudaError_t e = adj_step(n);
+            if (e == cudaSuccess) e = adj_step(n - 1);
+            if (e != cudaSuccess) return e;
+            const float *u[4] = {st(n + 2), st(n + 1), st(n), st(n - 1)};
+            if ((e = image(n, u, true)) != cudaSuccess) return e;
+        }
+        if (n == lo) return adj_step_and_image(n, st(n + 2), st(n + 1), st(n));
+        return cudaSuccess;
     };
 
     if (seglen == 0 && nslot == 0) {
@@ -337,7 +366,7 @@ MMOD_API mmod_status mmod_gradient(mmod_handle *h, const float *wavelet, const f
         MMOD_CK(h, cudaMemsetAsync(gw.psi[0], 0, vb, s));
         MMOD_CK(h, cudaMemsetAsync(gw.psi[1], 0, vb, s));
         MMOD_CK(h, cudaMemsetAsync(gw.gradc, 0, vb, s));
-        for (int n = nt - 1; n >= 0; --n) MMOD_CK(h, adj_step_and_image(n, gw.seg[n + 2], gw.seg[n + 1], gw.seg[n]));
+        MMOD_CK(h, backward_range(nt - 1, 0, [&](int j) { return gw.seg[j]; }));
     } else if (h->ckpt_scheme == MMOD_SCHEME_REVOLVE) {
         std::vector<RevAction> sched;
         revolve_schedule(nt, nslot, &sched);
@@ -405,10 +434,7 @@ MMOD_API mmod_status mmod_gradient(mmod_handle *h, const float *wavelet, const f
                 MMOD_CK(h, enqueue_step(h, fa, tma ? &gw.seg_cur[j + 1] : nullptr, tma ? &gw.seg_prev[j] : nullptr,
                                         tma, nullptr, s, &launches));
             }
-            for (int n = b0 - 1; n >= a0; --n) {
-                const int j = n - a0;
-                MMOD_CK(h, adj_step_and_image(n, gw.seg[j + 2], gw.seg[j + 1], gw.seg[j]));
-            }
+            MMOD_CK(h, backward_range(b0 - 1, a0, [&](int j) { return gw.seg[j - a0]; }));
         }
     }
     h->ran = false;

@@ -236,9 +236,12 @@ cudaError_t launch_source_scale(const float *vel, int nx, int ny, int nsrc, cons
 cudaError_t launch_unreverse_transpose(const float *g, int nt, int ncol, double scale, float *out,
                                        cudaStream_t s);
 // Gradient helpers (mmod_setup.cu).
-cudaError_t launch_imaging(const float *psi, const float *u_next, const float *u_cur, const float *u_prev,
-                           const float *c, const float *ex, const float *ey, const float *ez, int nx, int ny,
-                           int nz, int nxp, float *grad_c, cudaStream_t s);
+// Imaging condition of nsteps (1 or 2) forward steps n, n-1: psi[t] =
+// psi^{n+1-t}, u[t] = u^{n+1-t} (t = 0 .. nsteps + 1), grad_c accumulated in
+// the order of the steps.
+cudaError_t launch_imaging(int nsteps, const float *const *psi, const float *const *u, const float *c,
+                           const float *ex, const float *ey, const float *ez, int nx, int ny, int nz, int nxp,
+                           float *grad_c, cudaStream_t s);
 cudaError_t launch_grad_to_velocity(const float *grad_c, const float *vel, int nx, int ny, int nz, int nxp,
                                     double dt, float *grad_v, cudaStream_t s);
 cudaError_t launch_dot(const float *a, const float *b, long long n, double *out, cudaStream_t s);

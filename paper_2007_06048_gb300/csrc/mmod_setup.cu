@@ -188,38 +188,54 @@ __device__ __forceinline__ float imaging_term(float psi, float un, float uc, flo
 
 // Four consecutive x of one row per thread (16-byte loads; rows are padded to
 // 32 floats, so a group never straddles rows); columns past nx are loaded
-// (in bounds of the padded row) but not stored.
-__global__ void imaging_kernel(const float4 *__restrict__ psi, const float4 *__restrict__ un,
-                               const float4 *__restrict__ uc, const float4 *__restrict__ up,
-                               const float4 *__restrict__ c, const float *__restrict__ ex,
-                               const float *__restrict__ ey, const float *__restrict__ ez, int nx, int ny, int nz,
-                               int nxp, float4 *__restrict__ grad) {
-    const int per_row = nxp >> 2;
-    const long long total = (long long)per_row * ny * nz;
+// (in bounds of the padded row) but not stored.  NS = 1: forward step n
+// (psi[0] = psi^{n+1}; u[0..2] = u^{n+1}, u^n, u^{n-1}); NS = 2: steps n and
+// n - 1 in that order (psi[1] = psi^n, u[3] = u^{n-2}), the same operations
+// as two single-step passes but u^n, u^{n-1}, c and grad_c read once.
+struct ImagingArgs {
+    const float4 *psi[2];
+    const float4 *u[4];
+    const float4 *c;
+    const float *ex, *ey, *ez;
+    int nx, ny, nz, nxp;
+    float4 *grad;
+};
+
+template <int NS>
+__global__ void imaging_kernel(const ImagingArgs a) {
+    const int per_row = a.nxp >> 2;
+    const long long total = (long long)per_row * a.ny * a.nz;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
          q += (long long)gridDim.x * blockDim.x) {
         const int row = total <= 0xffffffffLL ? (int)((unsigned)q / (unsigned)per_row) : (int)(q / per_row);
         const int i0 = (int)(q - (long long)row * per_row) * 4;
-        if (i0 >= nx) continue;
-        const int j = row % ny, k = row / ny;
-        const float eyj = __ldg(ey + j), ezk = __ldg(ez + k);
-        const float4 ps = psi[q], a = un[q], b = uc[q], d = up[q], cc = c[q];
-        float4 g = grad[q];
+        if (i0 >= a.nx) continue;
+        const int j = row % a.ny, k = row / a.ny;
+        const float eyj = __ldg(a.ey + j), ezk = __ldg(a.ez + k);
+        float4 ps[NS], u[NS + 2];
+#pragma unroll
+        for (int t = 0; t < NS; ++t) ps[t] = a.psi[t][q];
+#pragma unroll
+        for (int t = 0; t < NS + 2; ++t) u[t] = a.u[t][q];
+        const float4 cc = a.c[q];
+        float4 g = a.grad[q];
         float e[4];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) e[t] = __fadd_rn(__fadd_rn(__ldg(ex + min(i0 + t, nx - 1)), eyj), ezk);
-        float4 r;
-        r.x = imaging_term(ps.x, a.x, b.x, d.x, cc.x, e[0], g.x);
-        r.y = imaging_term(ps.y, a.y, b.y, d.y, cc.y, e[1], g.y);
-        r.z = imaging_term(ps.z, a.z, b.z, d.z, cc.z, e[2], g.z);
-        r.w = imaging_term(ps.w, a.w, b.w, d.w, cc.w, e[3], g.w);
-        if (i0 + 3 < nx) {
-            grad[q] = r;
+        for (int t = 0; t < 4; ++t) e[t] = __fadd_rn(__fadd_rn(__ldg(a.ex + min(i0 + t, a.nx - 1)), eyj), ezk);
+#pragma unroll
+        for (int t = 0; t < NS; ++t) {
+            g.x = imaging_term(ps[t].x, u[t].x, u[t + 1].x, u[t + 2].x, cc.x, e[0], g.x);
+            g.y = imaging_term(ps[t].y, u[t].y, u[t + 1].y, u[t + 2].y, cc.y, e[1], g.y);
+            g.z = imaging_term(ps[t].z, u[t].z, u[t + 1].z, u[t + 2].z, cc.z, e[2], g.z);
+            g.w = imaging_term(ps[t].w, u[t].w, u[t + 1].w, u[t + 2].w, cc.w, e[3], g.w);
+        }
+        if (i0 + 3 < a.nx) {
+            a.grad[q] = g;
         } else {   // the row's last group: keep the padding untouched
-            float *gp = reinterpret_cast<float *>(grad + q);
-            gp[0] = r.x;
-            if (i0 + 1 < nx) gp[1] = r.y;
-            if (i0 + 2 < nx) gp[2] = r.z;
+            float *gp = reinterpret_cast<float *>(a.grad + q);
+            gp[0] = g.x;
+            if (i0 + 1 < a.nx) gp[1] = g.y;
+            if (i0 + 2 < a.nx) gp[2] = g.z;
         }
     }
 }
@@ -267,14 +283,23 @@ cudaError_t launch_unreverse_transpose(const float *g, int nt, int ncol, double 
     return cudaGetLastError();
 }
 
-cudaError_t launch_imaging(const float *psi, const float *u_next, const float *u_cur, const float *u_prev,
-                           const float *c, const float *ex, const float *ey, const float *ez, int nx, int ny,
-                           int nz, int nxp, float *grad_c, cudaStream_t s) {
+cudaError_t launch_imaging(int nsteps, const float *const *psi, const float *const *u, const float *c,
+                           const float *ex, const float *ey, const float *ez, int nx, int ny, int nz, int nxp,
+                           float *grad_c, cudaStream_t s) {
+    if (nsteps != 1 && nsteps != 2) return cudaErrorInvalidValue;
+    ImagingArgs a{};
+    for (int t = 0; t < nsteps; ++t) a.psi[t] = reinterpret_cast<const float4 *>(psi[t]);
+    for (int t = 0; t < nsteps + 2; ++t) a.u[t] = reinterpret_cast<const float4 *>(u[t]);
+    a.c = reinterpret_cast<const float4 *>(c);
+    a.ex = ex; a.ey = ey; a.ez = ez;
+    a.nx = nx; a.ny = ny; a.nz = nz; a.nxp = nxp;
+    a.grad = reinterpret_cast<float4 *>(grad_c);
     const long long groups = (long long)(nxp / 4) * ny * nz;
-    imaging_kernel<<<(int)std::min<long long>((groups + 255) / 256, 152LL * 8), 256, 0, s>>>(
-        reinterpret_cast<const float4 *>(psi), reinterpret_cast<const float4 *>(u_next),
-        reinterpret_cast<const float4 *>(u_cur), reinterpret_cast<const float4 *>(u_prev),
-        reinterpret_cast<const float4 *>(c), ex, ey, ez, nx, ny, nz, nxp, reinterpret_cast<float4 *>(grad_c));
+    const int grid = (int)std::min<long long>((groups + 255) / 256, 152LL * 8);
+    if (nsteps == 1)
+        imaging_kernel<1><<<grid, 256, 0, s>>>(a);
+    else
+        imaging_kernel<2><<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
