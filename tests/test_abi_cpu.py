@@ -34,6 +34,33 @@ def test_header_and_library_agree():
     assert exported_symbols() == decl
 
 
+def header_constants():
+    """Every NAME = value of the header's enums (comments stripped)."""
+    consts = {}
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = re.sub(r"/\*.*?\*/", "", open(hdr).read(), flags=re.S)
+        for body in re.findall(r"enum\s*\{(.*?)\}", text, flags=re.S):
+            for name, value in re.findall(r"\b(MMOD_\w+)\s*=\s*(-?\d+)", body):
+                consts[name] = int(value)
+    return consts
+
+
+def test_binding_constants_match_the_header():
+    """The binding's option, mode and status numbers are the header's."""
+    consts = header_constants()
+    pairs = {name[len("MMOD_"):]: value for name, value in consts.items()}
+    checked = 0
+    for py_name, value in pairs.items():
+        if hasattr(M, py_name):
+            assert getattr(M, py_name) == value, py_name
+            checked += 1
+    assert checked >= 20
+    for status, text in M.STATUS.items():
+        assert consts["MMOD_" + text] == status
+    for needed in ("OPT_PDL", "OPT_ZLEN", "OPT_CPML_PLANES", "OPT_TEST_STALL", "BATCH_PERSISTENT", "KERNEL_TMA"):
+        assert hasattr(M, needed), needed
+
+
 def test_every_symbol_loads():
     lib = M.load()
     for name in M.EXPORTED:
