@@ -255,6 +255,8 @@ def run_mmod(args):
         prop.set_variant(args.variant)
     if args.pdl is not None:
         prop.set_option(M.OPT_PDL, args.pdl)
+    if args.claim is not None:
+        prop.set_option(M.OPT_CLAIM, args.claim)
     stream = torch.cuda.current_stream(dev)
     vel_d = torch.from_numpy(p.vel).to(dev)
     wav_d = torch.from_numpy(np.ascontiguousarray(p.wavelet)).to(dev)
@@ -340,18 +342,81 @@ def run_mmod(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": describe(p, {"parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                                       "kernel": kernel_tag, "plan": plan,
-                                       "variant": None if plan is None else
-                                       M.mmod_tma_variant_name(plan["variant"])}),
+                "config": describe(p),
+                "launch": {"parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                           "kernel": kernel_tag, "plan": plan,
+                           "variant": None if plan is None else M.mmod_tma_variant_name(plan["variant"])},
                 "hbm_roofline_pct": 100.0 * BYTES_PER_POINT * value / ws / peak,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clocks, **extra}
+        if extra:   # last, so that a reader of the line's tail sees every headline figure
+            line["summary"] = summarize(value, roofline, extra)
         print(json.dumps(line), flush=True)
     prop.close()
     if ws > 1:
         dist.destroy_process_group()
     return 0
+
+
+def _r(x, nd=3):
+    return None if x is None else round(float(x), nd)
+
+
+def summarize(value, roofline, extra):
+    """Headline figures of the main line and of every extra measurement."""
+    out = {"forward_gpts": _r(value, 1), "forward_frac": _r(roofline["frac"])}
+    if "adjoint" in extra:
+        a = extra["adjoint"]
+        out["adjoint"] = {"gpts": _r(a["value"], 1), "vs_fwd": _r(a["vs_forward"]), "frac": _r(a["roofline"]["frac"])}
+    if "gradient" in extra:
+        g = extra["gradient"]
+        out["gradient"] = {k: {"ms": _r(g[k]["ms"], 1), "vs_fwd": _r(g[k]["vs_forward"]),
+                               "frac": _r(g[k]["roofline"]["frac"])}
+                           for k in ("fp32", "bf16", "fp32_every_state") if k in g}
+    if "batched" in extra:
+        b = extra["batched"]
+        out["batched"] = {"gpts": _r(b["value"], 1), "vs_fwd": _r(b["vs_forward"]), "fused": _r(b["fused"], 1),
+                          "persistent": _r(b["persistent"], 1), "one_by_one": _r(b["one_by_one"], 1)}
+    if "large" in extra:
+        lg = extra["large"]
+        out["large"] = {"gpts": _r(lg["forward"]["value"], 1), "frac": _r(lg["forward"]["roofline"]["frac"]),
+                        "grad_fp16_ms": _r(lg["gradient_fp16"]["ms"], 1),
+                        "grad_gb": _r(lg["gradient_fp16"]["device_gb"], 1)}
+    if "free_surface" in extra:
+        out["free_surface"] = {"gpts": _r(extra["free_surface"]["value"], 1)}
+    if "cpml" in extra:
+        c = extra["cpml"]
+        out["cpml"] = {"gpts": _r(c["value"], 1), "vs_fwd": _r(c["vs_forward"]), "frac": _r(c["roofline"]["frac"])}
+    if "variable_density" in extra:
+        v = extra["variable_density"]
+        out["variable_density"] = {"gpts": _r(v["value"], 1), "frac": _r(v["roofline"]["frac"]),
+                                   "frac_512": _r(v["large"]["roofline"]["frac"])}
+    return out
+
+
+def roofline_of(bytes_per_call, ms, peak, what):
+    achieved = bytes_per_call / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "bytes_per_call": bytes_per_call, "what": what}
+
+
+def cpml_layer_bytes(nx, ny, nz, L, free_surface=False):
+    """Algorithmic bytes of the two CPML layer passes per step.  A layer cell
+    with k axes in their layers: psi pass reads u (4 B) and updates psi_a
+    (8k B); the correction pass reads u (4) and psi_a (4k), updates zeta_a
+    (8k) and u^{n+1} (8) and reads c (4): 20 + 20k bytes per cell."""
+    def inside(n, lo_layer=True):
+        m = np.zeros(n, bool)
+        if lo_layer:
+            m[:L] = True
+        m[n - L:] = True
+        return m
+    ax = inside(nx)
+    ay = inside(ny)
+    az = inside(nz, not free_surface)
+    cells = int(np.logical_or.outer(np.logical_or.outer(az, ay), ax).sum())
+    axes = int(ax.sum()) * ny * nz + int(ay.sum()) * nx * nz + int(az.sum()) * nx * ny
+    return 20 * cells + 20 * axes, cells, axes
 
 
 def time_calls(fn, reps, stream):
@@ -377,7 +442,9 @@ def measure_adjoint(M, prop, p, dev, stream, fwd_gpts, reps=3):
     prop.adjoint(r, a, stream)
     ms = time_calls(lambda: prop.adjoint(r, a, stream), reps, stream)
     v = p.npoints * p.nt / (ms * 1e-3) / 1e9
-    return {"value": v, "unit": UNIT, "ms": ms, "vs_forward": v / fwd_gpts, "workload": p.name,
+    roof = roofline_of(BYTES_PER_POINT * p.npoints * p.nt, ms, load_peaks()[0],
+                       "16 B per point and adjoint step (the forward step kernel on psi), whole call")
+    return {"value": v, "unit": UNIT, "ms": ms, "vs_forward": v / fwd_gpts, "workload": p.name, "roofline": roof,
             "what": "mmod_adjoint: nt adjoint steps, receivers injected, sources gathered"}
 
 
@@ -396,15 +463,27 @@ def measure_gradient(M, dev, stream, fwd_gpts, nt=1000, reps=2):
     out = {"workload": p.name, "unit": UNIT,
            "what": "mmod_gradient: forward sweep with checkpoints, segment replay, adjoint, imaging; "
                    "value counts nt forward-equivalent steps per call"}
+    peak = load_peaks()[0]
     for name, dtype, ck in (("fp32", M.CKPT_FP32, 20), ("bf16", M.CKPT_BF16, 20),
                             ("fp32_every_state", M.CKPT_FP32, p.nt)):
         prop.gradient(wav, r, g, ck, dtype, stream)
         ms = time_calls(lambda: prop.gradient(wav, r, g, ck, dtype, stream), reps, stream)
         v = p.npoints * p.nt / (ms * 1e-3) / 1e9
+        bpp, what = gradient_bytes_per_point_step(ck >= p.nt and dtype == M.CKPT_FP32)
         out[name] = {"value": v, "ms": ms, "vs_forward": v / fwd_gpts, "checkpoints": ck,
-                     "memory_gb": prop.gradient_memory(ck, dtype) / 1e9}
+                     "memory_gb": prop.gradient_memory(ck, dtype) / 1e9,
+                     "roofline": roofline_of(bpp * p.npoints * p.nt, ms, peak, what)}
     prop.close()
     return out
+
+
+def gradient_bytes_per_point_step(every_state):
+    """Algorithmic bytes per grid point and time step of mmod_gradient
+    (checkpoint saves and restores, once per segment, left out)."""
+    if every_state:
+        return 50, ("forward sweep 16 B (u^{n+1} out of place), adjoint step 16 B, paired imaging 18 B "
+                    "(psi^{n+1}, psi^n, u^{n+1}..u^{n-2}, c, grad_c read-modify-write per two steps)")
+    return 66, ("forward sweep 16 B, segment replay 16 B, adjoint step 16 B, paired imaging 18 B per point and step")
 
 
 def measure_batched(M, dev, stream, fwd_gpts, reps=3):
@@ -490,7 +569,13 @@ def measure_cpml(M, dev, stream, fwd_gpts, reps=3):
     ms = time_calls(lambda: prop.forward(wav, tr, None, stream), reps, stream)
     prop.close()
     v = p.npoints * p.nt / (ms * 1e-3) / 1e9
+    nz, ny, nx = p.vel.shape
+    lb, cells, axes = cpml_layer_bytes(nx, ny, nz, p.nbl)
+    roof = roofline_of((BYTES_PER_POINT * p.npoints + lb) * p.nt, ms, load_peaks()[0],
+                       f"per step 16 B per point (step kernel) + 20 + 20k B per layer cell with k axes in their "
+                       f"layers (psi and correction passes): {cells} layer cells, {axes} cell-axes")
     return {"value": v, "unit": UNIT, "ms": ms, "vs_forward": v / fwd_gpts, "workload": p.name + " + CPML (L=20)",
+            "roofline": roof, "layer_bytes_per_step": lb,
             "what": "per step: the undamped step kernel, then two passes over the six layer slabs "
                     "(psi_a^n from u^n; then zeta_a^n and the u^{n+1} correction)"}
 
@@ -643,6 +728,8 @@ def main():
     ap.add_argument("--kernel", choices=["auto", "simple", "tma"], default="auto")
     ap.add_argument("--variant", type=int, default=-1, help="TMA kernel variant (-1 = automatic)")
     ap.add_argument("--pdl", type=int, choices=[0, 1], default=None, help="override MMOD_OPT_PDL")
+    ap.add_argument("--claim", type=int, default=None,
+                    help="override MMOD_OPT_CLAIM (planes per claimed work unit; 0 = the static plan)")
     ap.add_argument("--ref-seconds", type=float, default=20.0,
                     help="CPU seconds per oracle sample (cpu_baseline / reference arm)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
