@@ -19,14 +19,15 @@
 // threads) race on it — serialise them.
 //
 // In host code the array's name is only a stand-in for the device object, so
-// the device address is looked up with cudaGetSymbolAddress, once per device,
-// by the first call on that device (with the device current).  Make that
-// first call before any stream capture.
+// every call looks up the device address with cudaGetSymbolAddress, with the
+// call's device current (the lookup allocates nothing).  Looking it up per
+// call keeps the address right when the array is instantiated again, e.g.
+// after cudaDeviceReset or in another context.  The first call on a device
+// may load the library's device code; make it before any stream capture.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
-#include <mutex>
 
 #include "mmod_internal.h"
 #include "tma_plan.h"
@@ -39,15 +40,16 @@ constexpr long long kMaxVolume = 1LL << 21;   // padded points (nx rounded up to
 constexpr int kMaxAxis = 4096;                // points per axis
 constexpr int kMaxSrc = 64;
 constexpr int kMaxRec = 65536;
-constexpr int kMaxDevices = 64;
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t kOffU0 = 0;
 constexpr size_t kOffU1 = kOffU0 + align256(kMaxVolume * 4);
 constexpr size_t kOffC = kOffU1 + align256(kMaxVolume * 4);
-// Injection buckets (planes x 64x16 tiles) never exceed 32768 within the
-// limits above: the worst case is ny = 1, nz * nx / 64 <= 2^21 / 64.
-constexpr int kMaxBuckets = 32768;
+// Injection buckets: nz * ceil(nx / 64) * ceil(ny / 16).  ceil(nx / 64) <=
+// nxp / 32 and ceil(ny / 16) <= ny, so the count never exceeds
+// nxp * ny * nz / 32 <= 2^21 / 32 within the volume limit above (nx <= 32
+// and ny = 1 reach it).
+constexpr int kMaxBuckets = (int)(kMaxVolume / 32);
 constexpr size_t kOffEta = kOffC + align256(kMaxVolume * 4);
 constexpr size_t kOffTiles = kOffEta + align256(3 * kMaxAxis * 4);
 constexpr size_t kOffTab = kOffTiles + align256((kMaxBuckets + 1) * 4);   // point and source tables
@@ -60,30 +62,25 @@ constexpr size_t kScratchBytes = kOffMisc + 256;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-std::mutex g_setup_mutex;
-unsigned char *g_dev_scratch[kMaxDevices] = {};
-
-// Device address of the block on the current device (looked up once).
-cudaError_t scratch_address(int dev, unsigned char **out) {
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_dev_scratch[dev]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess) return e;
-        g_dev_scratch[dev] = static_cast<unsigned char *>(p);
-    }
-    *out = g_dev_scratch[dev];
+// Device address of the block in the current context.
+cudaError_t scratch_address(unsigned char **out) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess) return e;
+    *out = static_cast<unsigned char *>(p);
     return cudaSuccess;
 }
 
-bool on_device(const void *p) {
+// Memory the kernels on `device` can dereference: device memory of that
+// device, or managed memory.
+bool on_device(const void *p, int device) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == device;
 }
 
 mmod_status fail(mmod_status st, const char *msg) {
@@ -102,6 +99,19 @@ mmod_status fail_cuda(cudaError_t e, const char *what) {
     do {                                               \
         cudaError_t _e = (call);                       \
         if (_e != cudaSuccess) return fail_cuda(_e, #call); \
+    } while (0)
+
+// After the first enqueue: on a failure, wait (ignoring its status) for the
+// work already queued on `s`, which still uses the block, before returning,
+// so that a following call finds it idle.
+#define CKS(call)                                      \
+    do {                                               \
+        cudaError_t _e = (call);                       \
+        if (_e != cudaSuccess) {                       \
+            cudaStreamSynchronize(s);                  \
+            cudaGetLastError();                        \
+            return fail_cuda(_e, #call);               \
+        }                                              \
     } while (0)
 
 struct DeviceGuard {
@@ -162,15 +172,16 @@ extern "C" __attribute__((visibility("default"))) mmod_status mmod_forward_noall
         return fail(MMOD_ERR_CUDA, "CUDA device not available");
     }
     DeviceGuard guard(device);
-    if (!vel || !on_device(vel)) return fail(MMOD_ERR_ARG, "vel must be a device pointer");
-    if (c.nsrc > 0 && c.nt > 0 && (!wavelet || !on_device(wavelet)))
-        return fail(MMOD_ERR_ARG, "wavelet must be a device pointer");
-    if (c.nrec > 0 && c.nt > 0 && (!traces || !on_device(traces)))
-        return fail(MMOD_ERR_ARG, "traces must be a device pointer");
-    if (final_u && !on_device(final_u)) return fail(MMOD_ERR_ARG, "final_u must be a device pointer");
+    if (!vel || !on_device(vel, device)) return fail(MMOD_ERR_ARG, "vel must be a pointer to memory of `device`");
+    if (c.nsrc > 0 && c.nt > 0 && (!wavelet || !on_device(wavelet, device)))
+        return fail(MMOD_ERR_ARG, "wavelet must be a pointer to memory of `device`");
+    if (c.nrec > 0 && c.nt > 0 && (!traces || !on_device(traces, device)))
+        return fail(MMOD_ERR_ARG, "traces must be a pointer to memory of `device`");
+    if (final_u && !on_device(final_u, device))
+        return fail(MMOD_ERR_ARG, "final_u must be a pointer to memory of `device`");
 
     unsigned char *base = nullptr;
-    CKN(scratch_address(device, &base));
+    CKN(scratch_address(&base));
     cudaStream_t s = (cudaStream_t)stream;
     float *u[2] = {reinterpret_cast<float *>(base + kOffU0), reinterpret_cast<float *>(base + kOffU1)};
     float *cvol = reinterpret_cast<float *>(base + kOffC);
@@ -235,9 +246,9 @@ extern "C" __attribute__((visibility("default"))) mmod_status mmod_forward_noall
         }
     }
     pt_first[npt] = nkeep;
-    CKN(cudaMemcpyAsync(tab_d, tab, sizeof(tab), cudaMemcpyHostToDevice, s));
-    CKN(cudaMemcpyAsync(pt_off_d, pt_off, sizeof(pt_off), cudaMemcpyHostToDevice, s));
-    CKN(cudaStreamSynchronize(s));   // the host tables above live on the stack
+    CKS(cudaMemcpyAsync(tab_d, tab, sizeof(tab), cudaMemcpyHostToDevice, s));
+    CKS(cudaMemcpyAsync(pt_off_d, pt_off, sizeof(pt_off), cudaMemcpyHostToDevice, s));
+    CKS(cudaStreamSynchronize(s));   // the host tables above live on the stack
     {
         int chunk[1024];   // tile_start[b] = points in buckets < b
         int ptr = 0;
@@ -247,8 +258,8 @@ extern "C" __attribute__((visibility("default"))) mmod_status mmod_forward_noall
                 while (ptr < npt && pt_bucket[ptr] < b0 + q) ++ptr;
                 chunk[q] = ptr;
             }
-            CKN(cudaMemcpyAsync(tiles_d + b0, chunk, sizeof(int) * n, cudaMemcpyHostToDevice, s));
-            CKN(cudaStreamSynchronize(s));   // the chunk buffer is reused
+            CKS(cudaMemcpyAsync(tiles_d + b0, chunk, sizeof(int) * n, cudaMemcpyHostToDevice, s));
+            CKS(cudaStreamSynchronize(s));   // the chunk buffer is reused
         }
     }
     {
@@ -259,30 +270,30 @@ extern "C" __attribute__((visibility("default"))) mmod_status mmod_forward_noall
                 const int *p = c.rec_ijk + 3 * (r0 + r);
                 chunk[r] = (long long)p[2] * plane + (long long)p[1] * nxp + p[0];
             }
-            CKN(cudaMemcpyAsync(rec_off + r0, chunk, sizeof(long long) * n, cudaMemcpyHostToDevice, s));
-            CKN(cudaStreamSynchronize(s));   // the chunk buffer is reused
+            CKS(cudaMemcpyAsync(rec_off + r0, chunk, sizeof(long long) * n, cudaMemcpyHostToDevice, s));
+            CKS(cudaStreamSynchronize(s));   // the chunk buffer is reused
         }
     }
 
     // ---- model: scan, stability check, c = dt^2 v^2, profiles, source scales
     const long long npts = (long long)c.nx * c.ny * c.nz;
-    CKN(cudaMemsetAsync(base + kOffMisc, 0, 256, s));
-    CKN(launch_model_scan(vel, npts, vmax_bits, bad, s));
+    CKS(cudaMemsetAsync(base + kOffMisc, 0, 256, s));
+    CKS(launch_model_scan(vel, npts, vmax_bits, bad, s));
     unsigned int vbits = 0;
     unsigned long long nbad = 0;
-    CKN(cudaMemcpyAsync(&vbits, vmax_bits, sizeof(vbits), cudaMemcpyDeviceToHost, s));
-    CKN(cudaMemcpyAsync(&nbad, bad, sizeof(nbad), cudaMemcpyDeviceToHost, s));
-    CKN(cudaStreamSynchronize(s));
+    CKS(cudaMemcpyAsync(&vbits, vmax_bits, sizeof(vbits), cudaMemcpyDeviceToHost, s));
+    CKS(cudaMemcpyAsync(&nbad, bad, sizeof(nbad), cudaMemcpyDeviceToHost, s));
+    CKS(cudaStreamSynchronize(s));
     if (nbad) return fail(MMOD_ERR_ARG, "velocities must be positive and finite");
     float vmaxf;
     std::memcpy(&vmaxf, &vbits, sizeof(vmaxf));
     const double vmax = vmaxf;
     const double ksum = kSymbolMax8 * (1.0 / (c.hx * c.hx) + 1.0 / (c.hy * c.hy) + 1.0 / (c.hz * c.hz));
     if (c.dt * vmax * std::sqrt(ksum) > 2.0) return fail(MMOD_ERR_UNSTABLE, "dt too large for the model (CFL bound)");
-    CKN(launch_model_fill(vel, c.nx, c.ny, c.nz, nxp, c.dt, cvol, s));
+    CKS(launch_model_fill(vel, c.nx, c.ny, c.nz, nxp, c.dt, cvol, s));
     {
         int *tab_src_i = tab_d + 4 * kMaxSrc + 1 + kMaxSrc;
-        CKN(launch_source_scale(vel, c.nx, c.ny, nkeep, tab_src_i, tab_src_i + kMaxSrc, tab_src_i + 2 * kMaxSrc,
+        CKS(launch_source_scale(vel, c.nx, c.ny, nkeep, tab_src_i, tab_src_i + kMaxSrc, tab_src_i + 2 * kMaxSrc,
                                 c.dt, c.hx * c.hy * c.hz, src_scale, s));
     }
     float eta_h[3 * kMaxAxis];
@@ -290,11 +301,11 @@ extern "C" __attribute__((visibility("default"))) mmod_status mmod_forward_noall
     damping_profile(c.ny, c.nbl, c.hy, vmax, c.damp_R, c.dt, eta_h + c.nx);
     damping_profile(c.nz, c.nbl, c.hz, vmax, c.damp_R, c.dt, eta_h + c.nx + c.ny);
     if (c.free_surface) clear_surface_layer(c.nz, c.nbl, eta_h + c.nx + c.ny);
-    CKN(cudaMemcpyAsync(eta, eta_h, sizeof(float) * (c.nx + c.ny + c.nz), cudaMemcpyHostToDevice, s));
+    CKS(cudaMemcpyAsync(eta, eta_h, sizeof(float) * (c.nx + c.ny + c.nz), cudaMemcpyHostToDevice, s));
 
     // ---- time loop: u^{-1} = u^0 = 0, one step kernel per step
-    CKN(cudaMemsetAsync(u[0], 0, sizeof(float) * vol, s));
-    CKN(cudaMemsetAsync(u[1], 0, sizeof(float) * vol, s));
+    CKS(cudaMemsetAsync(u[0], 0, sizeof(float) * vol, s));
+    CKS(cudaMemsetAsync(u[1], 0, sizeof(float) * vol, s));
     CUtensorMap cur_map[2], prev_map[2], c_map;
     TmaPlan plans[kMaxTmaVariants];
     const bool tma = make_tma_plan(c, nxp, u, cvol, cur_map, prev_map, &c_map, plans);
@@ -327,20 +338,20 @@ extern "C" __attribute__((visibility("default"))) mmod_status mmod_forward_noall
         a.uout = u[n & 1];
         if (tma) {
             a.traces = (n >= 1 && want_tr) ? traces + (long long)(n - 1) * c.nrec : nullptr;
-            CKN(launch_step_tma(a, &cur_map[(n + 1) & 1], &prev_map[n & 1], &c_map, plans[kTmaDefaultVariant], s));
+            CKS(launch_step_tma(a, &cur_map[(n + 1) & 1], &prev_map[n & 1], &c_map, plans[kTmaDefaultVariant], s));
         } else {
             a.traces = nullptr;
-            CKN(launch_step_simple(a, s));
-            if (npt > 0) CKN(launch_inject(a, s));
-            if (want_tr) CKN(launch_gather(u[n & 1], rec_off, c.nrec, traces + (long long)n * c.nrec, s));
+            CKS(launch_step_simple(a, s));
+            if (npt > 0) CKS(launch_inject(a, s));
+            if (want_tr) CKS(launch_gather(u[n & 1], rec_off, c.nrec, traces + (long long)n * c.nrec, s));
         }
     }
     if (tma && c.nt > 0 && want_tr)
-        CKN(launch_gather(u[(c.nt - 1) & 1], rec_off, c.nrec, traces + (long long)(c.nt - 1) * c.nrec, s));
-    if (final_u) CKN(launch_unpack(u[(c.nt + 1) & 1], c.nx, c.ny, c.nz, nxp, final_u, s));
+        CKS(launch_gather(u[(c.nt - 1) & 1], rec_off, c.nrec, traces + (long long)(c.nt - 1) * c.nrec, s));
+    if (final_u) CKS(launch_unpack(u[(c.nt + 1) & 1], c.nx, c.ny, c.nz, nxp, final_u, s));
     int err_h = 0;
-    CKN(cudaMemcpyAsync(&err_h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CKN(cudaStreamSynchronize(s));
+    CKS(cudaMemcpyAsync(&err_h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CKS(cudaStreamSynchronize(s));
     if (err_h) return fail(MMOD_ERR_TIMEOUT, "a step kernel gave up waiting for its copies (device-side timeout)");
     return MMOD_OK;
 }
