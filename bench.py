@@ -257,6 +257,10 @@ def run_mmod(args):
         prop.set_option(M.OPT_PDL, args.pdl)
     if args.claim is not None:
         prop.set_option(M.OPT_CLAIM, args.claim)
+    if args.persistent is not None:
+        prop.set_option(M.OPT_PERSISTENT, args.persistent)
+    if args.zlen is not None:
+        prop.set_option(M.OPT_ZLEN, args.zlen)
     stream = torch.cuda.current_stream(dev)
     vel_d = torch.from_numpy(p.vel).to(dev)
     wav_d = torch.from_numpy(np.ascontiguousarray(p.wavelet)).to(dev)
@@ -372,7 +376,7 @@ def summarize(value, roofline, extra):
         g = extra["gradient"]
         out["gradient"] = {k: {"ms": _r(g[k]["ms"], 1), "vs_fwd": _r(g[k]["vs_forward"]),
                                "frac": _r(g[k]["roofline"]["frac"])}
-                           for k in ("fp32", "bf16", "fp32_every_state") if k in g}
+                           for k in ("fp32", "bf16", "bfp16", "fp32_every_state") if k in g}
     if "batched" in extra:
         b = extra["batched"]
         out["batched"] = {"gpts": _r(b["value"], 1), "vs_fwd": _r(b["vs_forward"]), "fused": _r(b["fused"], 1),
@@ -464,7 +468,7 @@ def measure_gradient(M, dev, stream, fwd_gpts, nt=1000, reps=2):
            "what": "mmod_gradient: forward sweep with checkpoints, segment replay, adjoint, imaging; "
                    "value counts nt forward-equivalent steps per call"}
     peak = load_peaks()[0]
-    for name, dtype, ck in (("fp32", M.CKPT_FP32, 20), ("bf16", M.CKPT_BF16, 20),
+    for name, dtype, ck in (("fp32", M.CKPT_FP32, 20), ("bf16", M.CKPT_BF16, 20), ("bfp16", M.CKPT_BFP16, 20),
                             ("fp32_every_state", M.CKPT_FP32, p.nt)):
         prop.gradient(wav, r, g, ck, dtype, stream)
         ms = time_calls(lambda: prop.gradient(wav, r, g, ck, dtype, stream), reps, stream)
@@ -481,9 +485,11 @@ def gradient_bytes_per_point_step(every_state):
     """Algorithmic bytes per grid point and time step of mmod_gradient
     (checkpoint saves and restores, once per segment, left out)."""
     if every_state:
-        return 50, ("forward sweep 16 B (u^{n+1} out of place), adjoint step 16 B, paired imaging 18 B "
-                    "(psi^{n+1}, psi^n, u^{n+1}..u^{n-2}, c, grad_c read-modify-write per two steps)")
-    return 66, ("forward sweep 16 B, segment replay 16 B, adjoint step 16 B, paired imaging 18 B per point and step")
+        return 48, ("forward sweep 20 B (u^{n-1}, u^n, c read, u^{n+1} and g^n = L u^n + s^n written), adjoint "
+                    "step 16 B, paired imaging 12 B (psi^{n+1}, psi^n, g^n, g^{n-1} read, accumulator "
+                    "read and written per two steps)")
+    return 64, ("forward sweep 16 B, segment replay 20 B (g^n written as well), adjoint step 16 B, paired "
+                "imaging 12 B per point and step")
 
 
 def measure_batched(M, dev, stream, fwd_gpts, reps=3):
@@ -728,6 +734,8 @@ def main():
     ap.add_argument("--kernel", choices=["auto", "simple", "tma"], default="auto")
     ap.add_argument("--variant", type=int, default=-1, help="TMA kernel variant (-1 = automatic)")
     ap.add_argument("--pdl", type=int, choices=[0, 1], default=None, help="override MMOD_OPT_PDL")
+    ap.add_argument("--persistent", type=int, choices=[0, 1], default=None, help="override MMOD_OPT_PERSISTENT")
+    ap.add_argument("--zlen", type=int, default=None, help="override MMOD_OPT_ZLEN (planes per z range)")
     ap.add_argument("--claim", type=int, default=None,
                     help="override MMOD_OPT_CLAIM (planes per claimed work unit; 0 = the static plan)")
     ap.add_argument("--ref-seconds", type=float, default=20.0,

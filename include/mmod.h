@@ -143,29 +143,42 @@ mmod_status mmod_forward(mmod_handle *h, const float *wavelet, float *traces,
 mmod_status mmod_adjoint(mmod_handle *h, const float *resid, float *adj_src, mmod_stream stream);
 
 /* Checkpoint storage of mmod_gradient. */
-enum { MMOD_CKPT_FP32 = 0, MMOD_CKPT_BF16 = 1, MMOD_CKPT_FP16 = 2 };
+/* MMOD_CKPT_BF16 / MMOD_CKPT_FP16: the value divided by max |u| over its z
+ * plane, rounded to BF16 / FP16 (one FP32 scale per plane).
+ * MMOD_CKPT_BFP16: block floating point, one FP32 scale s = max |u| over each
+ * block of 32 consecutive x values and round(u * 32767 / s) as int16 per
+ * value (error <= s / 65534; 2.125 bytes per value). */
+enum { MMOD_CKPT_FP32 = 0, MMOD_CKPT_BF16 = 1, MMOD_CKPT_FP16 = 2, MMOD_CKPT_BFP16 = 3 };
 
 /* Gradient of J = 1/2 sum_n |traces^n - d_obs^n|^2 with respect to the
  * velocity, for the current model, given wavelet [nsrc][nt] and the residual
  * resid [nt][nrec] = traces - d_obs of that model.  Writes grad_v
  * [nz][ny][nx] (FP32, dJ/dv in J-units per m/s):
- *   dJ/dv = 2 dt^2 v sum_n psi^{n+1} (D u^{n+1} - 2 u^n + E u^{n-1}) / c^2,
- * psi the adjoint wavefield (zero-lag imaging condition).  The forward
- * states are recomputed from ckpt_count checkpoints, by the handle's scheme
- * (mmod_set_option MMOD_OPT_CKPT_SCHEME):
+ *   dJ/dv = 2 dt^2 v sum_n mu^{n+1} (L u^n + s^n) = (2 / v) sum_n psi^{n+1} g^n,
+ * mu = psi / c the adjoint state (zero-lag imaging condition), g^n = L u^n +
+ * s^n written by the step kernel that advances u^n (FP32); the sum over n is
+ * a compensated FP32 sum (the accurate dot product "Dot2" of Ogita, Rump and
+ * Oishi, 2005), the final scaling FP32.  The forward states are recomputed from
+ * ckpt_count checkpoints, by the handle's scheme (mmod_set_option
+ * MMOD_OPT_CKPT_SCHEME):
  *   MMOD_SCHEME_SEGMENTS (default): the run is cut into ckpt_count segments;
- *     each is replayed once into ceil(nt / ckpt_count) + 2 FP32 volumes, so
- *     the cost is two forward runs and one adjoint run; with FP32 storage and
- *     ckpt_count >= nt every state is kept instead (nt + 2 volumes, one
- *     forward run and one adjoint run);
+ *     each is replayed once, writing g^n of its ceil(nt / ckpt_count) steps
+ *     into FP32 volumes (plus two for the replayed state), so the cost is two
+ *     forward runs and one adjoint run; with FP32 storage and ckpt_count >= nt
+ *     g^n of every step is kept instead (nt + 2 volumes, one forward run and
+ *     one adjoint run);
  *   MMOD_SCHEME_REVOLVE: binomial checkpointing (mmod_revolve_schedule) with
- *     ckpt_count slots and three FP32 work volumes; the forward steps
- *     replayed are the fewest any schedule with that many slots needs
- *     (about r forward runs when C(ckpt_count + 1 + r, r) >= nt).
- * A checkpoint holds (u^{n-1}, u^n), stored as MMOD_CKPT_FP32 (exact replay:
- * both schemes give the same bits) or BF16 / FP16 with one scale per z plane
- * (stepping stays FP32).  Device memory: mmod_gradient_memory().  Errors:
- * STATE, ARG, OOM, CUDA, TIMEOUT. */
+ *     ckpt_count slots and two FP32 work volumes; the forward steps replayed
+ *     are the fewest any schedule with that many slots needs (about r forward
+ *     runs when C(ckpt_count + 1 + r, r) >= nt).
+ * Every scheme also holds two adjoint volumes and the FP32 accumulator.  A
+ * checkpoint holds (u^{n-1}, u^n), stored as MMOD_CKPT_FP32 (exact replay:
+ * both schemes give the same bits) or in 16 bits per value (BF16 / FP16 with
+ * one scale per z plane, BFP16 with one per 32 values; stepping stays FP32).  The rounding of a 16-bit checkpoint is noise at the
+ * grid scale, which L in g^n amplifies by the ratio of the stencil's largest
+ * symbol to the wavefield's: the gradient error grows with the points per
+ * wavelength.  Device memory: mmod_gradient_memory().  Errors: STATE, ARG,
+ * OOM, CUDA, TIMEOUT. */
 mmod_status mmod_gradient(mmod_handle *h, const float *wavelet, const float *resid, float *grad_v,
                           int ckpt_count, int ckpt_dtype, mmod_stream stream);
 
@@ -261,15 +274,26 @@ mmod_status mmod_set_tma_variant(mmod_handle *h, int v);
  *                         measured grids; the same bits either way; variants
  *                         without a persistent form ignore it);
  *   MMOD_OPT_ZLEN         >= 0: planes per z range of a CTA (0 = the plan's
- *                         choice, which fills one wave of resident CTAs); the
- *                         same bits for any value;
+ *                         choice, which fills one wave of resident CTAs; in a
+ *                         batch created after it is set: the shot's z ranges,
+ *                         at least 4 planes, 0 = 96); the same bits for any
+ *                         value;
  *   MMOD_OPT_PERSISTENT_CTAS  >= 0: at most this many CTAs for the persistent
  *                         run (0 = as many as fit at once; a small value makes
  *                         each CTA serve many units, for tests);
- *   MMOD_OPT_CPML_PLANES  0..4096: planes per thread of the CPML layer
- *                         passes (0 = the default); each layer slab's depth
- *                         is split into equal ranges of at most this many
- *                         planes; the same bits for any value;
+ *   MMOD_OPT_CLAIM        0..2^20: planes per work unit of a work-claiming
+ *                         step launch (0 = off: one CTA per unit of the
+ *                         plan).  At most one wave of CTAs serves the units
+ *                         (64 x 16 tile x this many planes): each CTA takes
+ *                         its first unit by its index, then claims the next
+ *                         free unit from a per-launch counter until none is
+ *                         left, so early finishers take the remaining work
+ *                         (TMA variants 1, 2 and 6; others ignore it); the
+ *                         same bits for any value;
+ *   MMOD_OPT_CPML_PLANES  0..4096: about this many layer lines per thread
+ *                         (row segments per warp along x) in the CPML
+ *                         layer passes (0 = the default, 1); the same bits
+ *                         for any value;
  *   MMOD_OPT_TEST_STALL   1: test hook of the failure path.  The next
  *                         persistent run (of this handle, or of a persistent
  *                         batch holding it) waits for neighbour counters that
@@ -279,7 +303,7 @@ mmod_status mmod_set_tma_variant(mmod_handle *h, int v);
  *                         other handles stay usable).
  * Errors: ARG (unknown option or value). */
 enum { MMOD_OPT_PDL = 2, MMOD_OPT_CKPT_SCHEME = 3, MMOD_OPT_PERSISTENT = 4, MMOD_OPT_PERSISTENT_CTAS = 5,
-       MMOD_OPT_TEST_STALL = 6, MMOD_OPT_ZLEN = 7, MMOD_OPT_CPML_PLANES = 8 };
+       MMOD_OPT_TEST_STALL = 6, MMOD_OPT_ZLEN = 7, MMOD_OPT_CPML_PLANES = 8, MMOD_OPT_CLAIM = 9 };
 enum { MMOD_SCHEME_SEGMENTS = 0, MMOD_SCHEME_REVOLVE = 1 };
 mmod_status mmod_set_option(mmod_handle *h, int option, int value);
 
@@ -336,14 +360,17 @@ int mmod_check_recip(int n, unsigned int *max_ulp_out);
  *   Limits: nx, ny, nz <= 4096; (nx rounded up to 32) * ny * nz <= 2097152;
  *   nsrc <= 64; nrec <= 65536; order 8.  Larger problems are rejected with
  *   MMOD_ERR_ARG (use the handle API).
- *   vel, wavelet, traces, final_u: device pointers (layouts as in
- *   mmod_set_model / mmod_forward); final_u may be NULL.
- * Synchronous: returns after the work on `stream` has finished.  Every call
- * shares the block (each call clears what must start at zero), so calls that
- * overlap on the GPU race: serialise them.  The first call on a device looks
- * up the block's device address (cudaGetSymbolAddress); make it before any
- * stream capture.  Errors: ARG, UNSTABLE, UNSUPPORTED, CUDA, TIMEOUT; the
- * message is available from mmod_last_error(NULL) on the calling thread. */
+ *   vel, wavelet, traces, final_u: memory of `device` (or managed memory),
+ *   layouts as in mmod_set_model / mmod_forward; final_u may be NULL.
+ * Synchronous: returns after the work on `stream` has finished, also when a
+ * call fails after enqueuing work.  Every call shares the block (each call
+ * clears what must start at zero), so calls that overlap on the GPU race:
+ * serialise them.  Each call looks up the block's device address
+ * (cudaGetSymbolAddress, which allocates nothing) with `device` current; the
+ * first call on a device may load the library's device code, so make it
+ * before any stream capture.  Errors: ARG, UNSTABLE, UNSUPPORTED, CUDA,
+ * TIMEOUT; the message is available from mmod_last_error(NULL) on the
+ * calling thread. */
 mmod_status mmod_forward_noalloc(const mmod_config *cfg, int device, const float *vel,
                                  const float *wavelet, float *traces, float *final_u,
                                  mmod_stream stream);

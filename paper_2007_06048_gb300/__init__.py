@@ -33,6 +33,7 @@ OPT_PERSISTENT_CTAS = 5
 OPT_TEST_STALL = 6
 OPT_ZLEN = 7
 OPT_CPML_PLANES = 8
+OPT_CLAIM = 9
 BOUNDARY_DAMPING, BOUNDARY_CPML = 0, 1
 BATCH_STREAMS, BATCH_FUSED, BATCH_PERSISTENT = 0, 1, 2
 SCHEME_SEGMENTS, SCHEME_REVOLVE = 0, 1
@@ -51,7 +52,7 @@ EXPORTED = ["mmod_create", "mmod_destroy", "mmod_set_model", "mmod_forward", "mm
             "mmod_set_fd_coefficients", "mmod_vd_create", "mmod_vd_destroy", "mmod_vd_set_model",
             "mmod_vd_set_state", "mmod_vd_forward", "mmod_vd_set_kernel", "mmod_vd_uses_tma", "mmod_vd_set_option",
             "mmod_vd_last_loop_ms", "mmod_vd_last_launch_count", "mmod_vd_last_error", "mmod_vd_get_plan"]
-CKPT_FP32, CKPT_BF16, CKPT_FP16 = 0, 1, 2
+CKPT_FP32, CKPT_BF16, CKPT_FP16, CKPT_BFP16 = 0, 1, 2, 3
 
 
 class MmodError(RuntimeError):

@@ -11,22 +11,24 @@
 // contiguous row per step), and the sources are gathered; the
 // adjoint source is a[s][n] = psi^{n+1}(x_s) / (hx hy hz).
 //
-// Gradient.  dJ/dc(x) = sum_n mu^{n+1}(x) (L u^n + s^n)(x); with
-// C (L u^n + s^n) = D u^{n+1} - 2 u^n + E u^{n-1} this is the zero-lag
-// imaging condition sum_n psi^{n+1} (D u^{n+1} - 2 u^n + E u^{n-1}) / c^2,
-// and dJ/dv = 2 dt^2 v dJ/dc.  The forward states are recovered from
-// checkpoints (u^{a-1}, u^a) (FP32, or BF16 / FP16 with one scale per z
-// plane) by one of two schemes:
+// Gradient.  dJ/dc(x) = sum_n mu^{n+1}(x) g^n(x), g^n = L u^n + s^n, so
+// with mu = psi / c the kernels accumulate A = sum_n psi^{n+1} g^n (a
+// compensated FP32 sum, see the imaging kernel) and dJ/dv = 2 dt^2 v A / c =
+// 2 A / v.  g^n is written by the step kernel that
+// advances u^n (the Laplacian it already holds, plus w[n] / (hx hy hz) at the
+// sources): no difference of nearly equal wavefields is formed.  The forward
+// states are recovered from checkpoints (u^{a-1}, u^a) (FP32, or BF16 / FP16
+// with one scale per z plane) by one of two schemes:
 //   segments: the first sweep stores a checkpoint at the start of each of S
 //     segments of K steps; the backward sweep replays each segment from its
-//     checkpoint into K+2 stored volumes and runs the segment's adjoint steps
-//     against them.  Memory: 2 S checkpoint volumes + K + 2; work: two
-//     forward sweeps and one adjoint;
+//     checkpoint, in place in two volumes, writing g^n into K more, and runs
+//     the segment's adjoint steps against them.  Memory: 2 S checkpoint
+//     volumes + K + 2; work: two forward sweeps and one adjoint;
 //   revolve: the binomial schedule of mmod_revolve.cu over S slots, with the
-//     working state in the handle's two buffers and one more volume for
-//     u^{n+1}; the fewest replayed steps for S slots;
-//   segments with S >= nt and FP32 storage keeps every state (nt + 2
-//     volumes, written out of place by the first sweep): no replay.
+//     working state in the handle's two buffers, u^{n+1} and g^n of a
+//     reversed step in two more volumes; the fewest replayed steps for S slots;
+//   segments with S >= nt and FP32 storage keeps g^n of every step (nt + 2
+//     volumes, written by the first sweep): no replay.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -88,7 +90,49 @@ __global__ void decompress_kernel(const T *__restrict__ in, const float *__restr
     for (long long q = threadIdx.x; q < plane; q += blockDim.x) u[base + q] = from_store(in[base + q]) * s;
 }
 
+// Block floating point (MMOD_CKPT_BFP16): per block of 32 consecutive x
+// values of a padded row (rows are padded to 32, so blocks never straddle
+// rows), scale s = max |u| over the block and q = round(u * 32767 / s) as
+// int16; u is restored as q * (s / 32767), within s / 65534 of the stored
+// value.  One warp per block, grid-stride over the volume's blocks.
+constexpr int kBfpBlock = 32;
+constexpr float kBfpMax = 32767.0f;
+
+__global__ void compress_bfp_kernel(const float *__restrict__ u, long long nblocks, short *__restrict__ out,
+                                    float *__restrict__ scale) {
+    const int lane = threadIdx.x & 31;
+    const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long b = warp0; b < nblocks; b += nwarps) {
+        const float v = u[b * kBfpBlock + lane];
+        float m = fabsf(v);
+        for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+        int q = 0;
+        if (m > 0.0f) q = max(-32767, min(32767, __float2int_rn(v * (kBfpMax / m))));
+        out[b * kBfpBlock + lane] = (short)q;
+        if (lane == 0) scale[b] = m;
+    }
+}
+
+__global__ void decompress_bfp_kernel(const short *__restrict__ in, const float *__restrict__ scale, long long nblocks,
+                                      float *__restrict__ u) {
+    const int lane = threadIdx.x & 31;
+    const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long b = warp0; b < nblocks; b += nwarps)
+        u[b * kBfpBlock + lane] = (float)in[b * kBfpBlock + lane] * (scale[b] / kBfpMax);
+}
+
+int bfp_grid(long long nblocks) { return (int)std::min<long long>((nblocks + 7) / 8, 152LL * 16); }
+
 size_t ckpt_elem_bytes(int dtype) { return dtype == MMOD_CKPT_FP32 ? 4 : 2; }
+
+// Scales per checkpoint volume: one per z plane (BF16 / FP16), one per
+// 32-value block (BFP16), none (FP32).
+size_t ckpt_scales(const mmod_handle *h, int dtype) {
+    if (dtype == MMOD_CKPT_BFP16) return (size_t)h->vol / kBfpBlock;
+    return dtype == MMOD_CKPT_FP32 ? 0 : (size_t)h->cfg.nz;
+}
 
 // Save the volume u as checkpoint volume slot (FP32: copy; 16-bit: compress).
 cudaError_t save_volume(mmod_handle *h, const float *u, int slot, cudaStream_t s) {
@@ -97,8 +141,11 @@ cudaError_t save_volume(mmod_handle *h, const float *u, int slot, cudaStream_t s
     char *dst = static_cast<char *>(gw.ckpt) + (size_t)slot * h->vol * eb;
     if (gw.dtype == MMOD_CKPT_FP32)
         return cudaMemcpyAsync(dst, u, sizeof(float) * (size_t)h->vol, cudaMemcpyDeviceToDevice, s);
-    float *sc = gw.ckpt_scale + (size_t)slot * h->cfg.nz;
-    if (gw.dtype == MMOD_CKPT_BF16)
+    float *sc = gw.ckpt_scale + (size_t)slot * ckpt_scales(h, gw.dtype);
+    if (gw.dtype == MMOD_CKPT_BFP16) {
+        const long long nb = h->vol / kBfpBlock;
+        compress_bfp_kernel<<<bfp_grid(nb), 256, 0, s>>>(u, nb, reinterpret_cast<short *>(dst), sc);
+    } else if (gw.dtype == MMOD_CKPT_BF16)
         compress_kernel<__nv_bfloat16><<<h->cfg.nz, 256, 0, s>>>(u, h->plane, reinterpret_cast<__nv_bfloat16 *>(dst), sc);
     else
         compress_kernel<__half><<<h->cfg.nz, 256, 0, s>>>(u, h->plane, reinterpret_cast<__half *>(dst), sc);
@@ -111,8 +158,11 @@ cudaError_t restore_volume(mmod_handle *h, int slot, float *u, cudaStream_t s) {
     const char *src = static_cast<const char *>(gw.ckpt) + (size_t)slot * h->vol * eb;
     if (gw.dtype == MMOD_CKPT_FP32)
         return cudaMemcpyAsync(u, src, sizeof(float) * (size_t)h->vol, cudaMemcpyDeviceToDevice, s);
-    const float *sc = gw.ckpt_scale + (size_t)slot * h->cfg.nz;
-    if (gw.dtype == MMOD_CKPT_BF16)
+    const float *sc = gw.ckpt_scale + (size_t)slot * ckpt_scales(h, gw.dtype);
+    if (gw.dtype == MMOD_CKPT_BFP16) {
+        const long long nb = h->vol / kBfpBlock;
+        decompress_bfp_kernel<<<bfp_grid(nb), 256, 0, s>>>(reinterpret_cast<const short *>(src), sc, nb, u);
+    } else if (gw.dtype == MMOD_CKPT_BF16)
         decompress_kernel<__nv_bfloat16><<<h->cfg.nz, 256, 0, s>>>(reinterpret_cast<const __nv_bfloat16 *>(src), sc,
                                                                     h->plane, u);
     else
@@ -142,10 +192,11 @@ mmod_status ensure_grad_work(mmod_handle *h, int nslot, int nwork, int dtype) {
             return fail(h, MMOD_ERR_CUDA, "tensor map encoding failed for an adjoint buffer");
     }
     MMOD_CK(h, cudaMalloc(&gw.gradc, vb));
+    MMOD_CK(h, cudaMalloc(&gw.gcomp, vb));
     gw.ckpt_bytes = (size_t)nslot * 2 * (size_t)h->vol * ckpt_elem_bytes(dtype);
     if (nslot > 0) MMOD_CK(h, cudaMalloc(&gw.ckpt, gw.ckpt_bytes));
     if (nslot > 0 && dtype != MMOD_CKPT_FP32)
-        MMOD_CK(h, cudaMalloc(&gw.ckpt_scale, sizeof(float) * (size_t)nslot * 2 * h->cfg.nz));
+        MMOD_CK(h, cudaMalloc(&gw.ckpt_scale, sizeof(float) * (size_t)nslot * 2 * ckpt_scales(h, dtype)));
     gw.nslot = nslot;
     gw.nwork = nwork;
     gw.dtype = dtype;
@@ -166,7 +217,7 @@ void grad_layout(const mmod_handle *h, int ckpt_count, int dtype, int *nslot, in
     if (h->ckpt_scheme == MMOD_SCHEME_REVOLVE) {
         *seglen = 0;
         *nslot = std::max(1, std::min(ckpt_count, nt - 1));
-        *nwork = 1;
+        *nwork = 2;
     } else {
         *seglen = std::max(1, (nt + ckpt_count - 1) / ckpt_count);
         *nslot = nt > 0 ? (nt + *seglen - 1) / *seglen : 1;
@@ -204,6 +255,8 @@ void free_grad_work(mmod_handle *h) {
         p = nullptr;
     }
     if (gw.gradc) cudaFree(gw.gradc);
+    if (gw.gcomp) cudaFree(gw.gcomp);
+    gw.gcomp = nullptr;
     if (gw.ckpt) cudaFree(gw.ckpt);
     if (gw.ckpt_scale) cudaFree(gw.ckpt_scale);
     gw.gradc = nullptr;
@@ -268,7 +321,8 @@ MMOD_API mmod_status mmod_gradient(mmod_handle *h, const float *wavelet, const f
     const auto &c = h->cfg;
     if (!grad_v) return fail(h, MMOD_ERR_ARG, "null gradient output");
     if (ckpt_count < 1) return fail(h, MMOD_ERR_ARG, "ckpt_count must be >= 1");
-    if (ckpt_dtype != MMOD_CKPT_FP32 && ckpt_dtype != MMOD_CKPT_BF16 && ckpt_dtype != MMOD_CKPT_FP16)
+    if (ckpt_dtype != MMOD_CKPT_FP32 && ckpt_dtype != MMOD_CKPT_BF16 && ckpt_dtype != MMOD_CKPT_FP16 &&
+        ckpt_dtype != MMOD_CKPT_BFP16)
         return fail(h, MMOD_ERR_ARG, "unknown checkpoint type");
     if (c.nsrc > 0 && c.nt > 0 && !wavelet) return fail(h, MMOD_ERR_ARG, "null wavelet with nsrc > 0");
     if (c.nrec > 0 && c.nt > 0 && !resid) return fail(h, MMOD_ERR_ARG, "null residual with nrec > 0");
@@ -295,6 +349,7 @@ MMOD_API mmod_status mmod_gradient(mmod_handle *h, const float *wavelet, const f
     h->state_pending = false;
     StepArgs fa = base_args(h, h->fwd, dwav);
     fa.nrec = 0;   // no receivers in the gradient's forward sweeps
+    fa.inv_cell = (float)(1.0 / (c.hx * c.hy * c.hz));
     StepArgs aa = base_args(h, h->adj, h->st_adjw);
     aa.nrec = 0;
     // forward step n in place on the handle's buffers: u^{n-1} in u[n & 1],
@@ -305,6 +360,19 @@ MMOD_API mmod_status mmod_gradient(mmod_handle *h, const float *wavelet, const f
         fa.uprev = h->u[n & 1];
         fa.uout = h->u[n & 1];
         return enqueue_step(h, fa, &h->cur_map[(n + 1) & 1], &h->prev_map[n & 1], tma, nullptr, s, &launches);
+    };
+    // forward step n of a replay in the work volumes w0, w1 (u^{n-1} in w0,
+    // u^n in w1, u^{n+1} over u^{n-1}), also writing g^n into gout
+    auto fwd_step_g = [&](int n, int w0, int w1, float *gout) {
+        fa.n = n;
+        fa.ucur = gw.seg[w1];
+        fa.uprev = gw.seg[w0];
+        fa.uout = gw.seg[w0];
+        fa.gout = gout;
+        const cudaError_t e = enqueue_step(h, fa, tma ? &gw.seg_cur[w1] : nullptr, tma ? &gw.seg_prev[w0] : nullptr,
+                                           tma, nullptr, s, &launches);
+        fa.gout = nullptr;
+        return e;
     };
     // adjoint step of forward step n: adjoint step m = nt-1-n produces
     // psi^{n+1} in psi[m & 1] (psi^{n+2} stays in the other buffer until the
@@ -318,62 +386,55 @@ MMOD_API mmod_status mmod_gradient(mmod_handle *h, const float *wavelet, const f
         return enqueue_step(h, aa, tma ? &gw.psi_cur[(m + 1) & 1] : nullptr, tma ? &gw.psi_prev[m & 1] : nullptr,
                             tma, nullptr, s, &launches);
     };
-    // imaging terms of forward steps n (and n - 1 when pair) from u[t] =
-    // u^{n+1-t}, after their adjoint steps: psi^{n+1} in psi[(nt-1-n) & 1],
+    // imaging terms of forward steps n (and n - 1 when ns = 2) from g[t] =
+    // g^{n-t}, after their adjoint steps: psi^{n+1} in psi[(nt-1-n) & 1],
     // psi^n in the other buffer
-    auto image = [&](int n, const float *const *u, bool pair) {
+    auto image = [&](int n, const float *const *g, int ns) {
         const int m = nt - 1 - n;
         const float *ps[2] = {gw.psi[m & 1], gw.psi[(m + 1) & 1]};
         ++launches;
-        return launch_imaging(pair ? 2 : 1, ps, u, h->c, aa.ex, aa.ey, aa.ez, c.nx, c.ny, c.nz, h->nxp, gw.gradc,
-                              s);
+        return launch_imaging(ns, ps, g, c.nx, c.ny, c.nz, h->nxp, gw.gradc, gw.gcomp, s);
     };
-    auto adj_step_and_image = [&](int n, const float *un, const float *uc, const float *up) {
-        cudaError_t e = adj_step(n);
-        if (e != cudaSuccess) return e;
-        const float *u[3] = {un, uc, up};
-        return image(n, u, false);
-    };
-    // steps hi down to lo with their states in st(j) = u^{j-1} (j = lo .. hi
-    // + 2): two adjoint steps, then one imaging pass over both (the same
-    // accumulation order as one pass per step, u^n, u^{n-1}, c and grad_c
-    // read once per pair)
-    auto backward_range = [&](int hi, int lo, auto st) -> cudaError_t {
+    // steps hi down to lo with g^j in gof(j): two adjoint steps, then one
+    // imaging pass over both (the same accumulation order as one pass per
+    // step, the accumulator read and written once per pair)
+    auto backward_range = [&](int hi, int lo, auto gof) -> cudaError_t {
         int n = hi;
         for (; n - 1 >= lo; n -= 2) {
             cudaError_t e = adj_step(n);
             if (e == cudaSuccess) e = adj_step(n - 1);
             if (e != cudaSuccess) return e;
-            const float *u[4] = {st(n + 2), st(n + 1), st(n), st(n - 1)};
-            if ((e = image(n, u, true)) != cudaSuccess) return e;
+            const float *g[2] = {gof(n), gof(n - 1)};
+            if ((e = image(n, g, 2)) != cudaSuccess) return e;
         }
-        if (n == lo) return adj_step_and_image(n, st(n + 2), st(n + 1), st(n));
+        if (n == lo) {
+            cudaError_t e = adj_step(n);
+            if (e != cudaSuccess) return e;
+            const float *g[1] = {gof(n)};
+            return image(n, g, 1);
+        }
         return cudaSuccess;
     };
 
     if (seglen == 0 && nslot == 0) {
-        // every state kept: seg[m] = u^{m-1}, the sweep writes out of place
+        // every step's g^n kept: seg[0], seg[1] hold the stepped state,
+        // seg[2 + n] = g^n
         MMOD_CK(h, cudaMemsetAsync(gw.seg[0], 0, vb, s));
         MMOD_CK(h, cudaMemsetAsync(gw.seg[1], 0, vb, s));
-        for (int n = 0; n < nt; ++n) {
-            fa.n = n;
-            fa.ucur = gw.seg[n + 1];
-            fa.uprev = gw.seg[n];
-            fa.uout = gw.seg[n + 2];
-            MMOD_CK(h, enqueue_step(h, fa, tma ? &gw.seg_cur[n + 1] : nullptr, tma ? &gw.seg_prev[n] : nullptr, tma,
-                                    nullptr, s, &launches));
-        }
+        for (int n = 0; n < nt; ++n) MMOD_CK(h, fwd_step_g(n, n & 1, (n + 1) & 1, gw.seg[2 + n]));
         MMOD_CK(h, cudaMemsetAsync(gw.psi[0], 0, vb, s));
         MMOD_CK(h, cudaMemsetAsync(gw.psi[1], 0, vb, s));
         MMOD_CK(h, cudaMemsetAsync(gw.gradc, 0, vb, s));
-        MMOD_CK(h, backward_range(nt - 1, 0, [&](int j) { return gw.seg[j]; }));
+        MMOD_CK(h, cudaMemsetAsync(gw.gcomp, 0, vb, s));
+        MMOD_CK(h, backward_range(nt - 1, 0, [&](int j) { return gw.seg[2 + j]; }));
     } else if (h->ckpt_scheme == MMOD_SCHEME_REVOLVE) {
         std::vector<RevAction> sched;
         revolve_schedule(nt, nslot, &sched);
         MMOD_CK(h, cudaMemsetAsync(gw.psi[0], 0, vb, s));
         MMOD_CK(h, cudaMemsetAsync(gw.psi[1], 0, vb, s));
         MMOD_CK(h, cudaMemsetAsync(gw.gradc, 0, vb, s));
-        float *unext = gw.seg[0];
+        MMOD_CK(h, cudaMemsetAsync(gw.gcomp, 0, vb, s));
+        float *unext = gw.seg[0], *gn = gw.seg[1];
         for (const RevAction &act : sched) {
             switch (act.kind) {
                 case MMOD_REV_ADVANCE:
@@ -392,15 +453,20 @@ MMOD_API mmod_status mmod_gradient(mmod_handle *h, const float *wavelet, const f
                         MMOD_CK(h, restore_volume(h, 2 * act.a + 1, h->u[(act.b + 1) & 1], s));
                     }
                     break;
-                case MMOD_REV_REVERSE: {
+                case MMOD_REV_REVERSE: {   // g^n from the working state, then the adjoint step and its term
                     const int n = act.a;
                     fa.n = n;
                     fa.ucur = h->u[(n + 1) & 1];
                     fa.uprev = h->u[n & 1];
                     fa.uout = unext;
-                    MMOD_CK(h, enqueue_step(h, fa, &h->cur_map[(n + 1) & 1], &h->prev_map[n & 1], tma, nullptr, s,
-                                            &launches));
-                    MMOD_CK(h, adj_step_and_image(n, unext, h->u[(n + 1) & 1], h->u[n & 1]));
+                    fa.gout = gn;
+                    const cudaError_t e = enqueue_step(h, fa, &h->cur_map[(n + 1) & 1], &h->prev_map[n & 1], tma,
+                                                       nullptr, s, &launches);
+                    fa.gout = nullptr;
+                    MMOD_CK(h, e);
+                    MMOD_CK(h, adj_step(n));
+                    const float *g[1] = {gn};
+                    MMOD_CK(h, image(n, g, 1));
                     break;
                 }
                 default:
@@ -417,28 +483,25 @@ MMOD_API mmod_status mmod_gradient(mmod_handle *h, const float *wavelet, const f
             MMOD_CK(h, save_volume(h, h->u[(a0 + 1) & 1], 2 * sg + 1, s));
             for (int n = a0; n < b0; ++n) MMOD_CK(h, fwd_step_in_place(n));
         }
-        // ---- backward: replay each segment, then its adjoint steps + imaging
+        // ---- backward: replay each segment (g^n of its steps), then its
+        // adjoint steps + imaging
         MMOD_CK(h, cudaMemsetAsync(gw.psi[0], 0, vb, s));
         MMOD_CK(h, cudaMemsetAsync(gw.psi[1], 0, vb, s));
         MMOD_CK(h, cudaMemsetAsync(gw.gradc, 0, vb, s));
+        MMOD_CK(h, cudaMemsetAsync(gw.gcomp, 0, vb, s));
         for (int sg = nseg - 1; sg >= 0; --sg) {
             const int a0 = sg * seglen, b0 = std::min(nt, a0 + seglen);
             MMOD_CK(h, restore_volume(h, 2 * sg, gw.seg[0], s));
             MMOD_CK(h, restore_volume(h, 2 * sg + 1, gw.seg[1], s));
-            for (int n = a0; n < b0; ++n) {   // seg[j] holds u^{a0-1+j}
+            for (int n = a0; n < b0; ++n) {   // seg[2 + n - a0] receives g^n
                 const int j = n - a0;
-                fa.n = n;
-                fa.ucur = gw.seg[j + 1];
-                fa.uprev = gw.seg[j];
-                fa.uout = gw.seg[j + 2];
-                MMOD_CK(h, enqueue_step(h, fa, tma ? &gw.seg_cur[j + 1] : nullptr, tma ? &gw.seg_prev[j] : nullptr,
-                                        tma, nullptr, s, &launches));
+                MMOD_CK(h, fwd_step_g(n, j & 1, (j + 1) & 1, gw.seg[2 + j]));
             }
-            MMOD_CK(h, backward_range(b0 - 1, a0, [&](int j) { return gw.seg[j - a0]; }));
+            MMOD_CK(h, backward_range(b0 - 1, a0, [&](int j) { return gw.seg[2 + j - a0]; }));
         }
     }
     h->ran = false;
-    // ---- dJ/dv = 2 dt^2 v dJ/dc
+    // ---- dJ/dv = 2 dt^2 v dJ/dc = 2 A / v (FP32)
     const size_t npts = (size_t)h->npts;
     const bool dev_out = is_device_ptr(grad_v);
     float *dst = grad_v;
@@ -446,7 +509,7 @@ MMOD_API mmod_status mmod_gradient(mmod_handle *h, const float *wavelet, const f
         if (!h->st_vol) MMOD_CK(h, cudaMalloc(&h->st_vol, sizeof(float) * npts));
         dst = h->st_vol;
     }
-    MMOD_CK(h, launch_grad_to_velocity(gw.gradc, h->vel_copy, c.nx, c.ny, c.nz, h->nxp, c.dt, dst, s));
+    MMOD_CK(h, launch_grad_to_velocity(gw.gradc, gw.gcomp, h->vel_copy, c.nx, c.ny, c.nz, h->nxp, dst, s));
     ++launches;
     if (!dev_out) {
         MMOD_CK(h, cudaMemcpyAsync(grad_v, dst, sizeof(float) * npts, cudaMemcpyDeviceToHost, s));
@@ -458,13 +521,15 @@ MMOD_API mmod_status mmod_gradient(mmod_handle *h, const float *wavelet, const f
 
 MMOD_API long long mmod_gradient_memory(const mmod_handle *h, int ckpt_count, int ckpt_dtype) {
     if (!h || ckpt_count < 1) return -1;
-    if (ckpt_dtype != MMOD_CKPT_FP32 && ckpt_dtype != MMOD_CKPT_BF16 && ckpt_dtype != MMOD_CKPT_FP16) return -1;
+    if (ckpt_dtype != MMOD_CKPT_FP32 && ckpt_dtype != MMOD_CKPT_BF16 && ckpt_dtype != MMOD_CKPT_FP16 &&
+        ckpt_dtype != MMOD_CKPT_BFP16)
+        return -1;
     int nslot = 0, nwork = 0, seglen = 0;
     grad_layout(h, ckpt_count, ckpt_dtype, &nslot, &nwork, &seglen);
     const long long vb = 4LL * h->vol;
     const long long eb = ckpt_dtype == MMOD_CKPT_FP32 ? 4 : 2;
-    return (long long)(nwork + 3) * vb + (long long)nslot * 2 * h->vol * eb +
-           (ckpt_dtype == MMOD_CKPT_FP32 ? 0 : 4LL * nslot * 2 * h->cfg.nz);
+    return (long long)(nwork + 4) * vb + (long long)nslot * 2 * h->vol * eb +
+           4LL * nslot * 2 * (long long)ckpt_scales(h, ckpt_dtype);
 }
 
 MMOD_API mmod_status mmod_dot(const float *a, const float *b, long long n, double *out, mmod_stream stream) {

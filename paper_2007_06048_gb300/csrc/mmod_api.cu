@@ -95,6 +95,8 @@ void free_all(mmod_handle *h) {
         if (g->g_off) cudaFree(g->g_off);
     }
     if (h->counters) cudaFree(h->counters);
+    if (h->claim_ctr) cudaFree(h->claim_ctr);
+    if (h->queue) cudaFree(h->queue);
     if (h->cpml_mem) cudaFree(h->cpml_mem);
     if (h->cpml_bg) cudaFree(h->cpml_bg);
     if (h->vmax_bits) cudaFree(h->vmax_bits);
@@ -331,17 +333,27 @@ int persistent_grid_of(const mmod_handle *h) {
     return persistent_grid(plan, h->cfg.nz, h->persistent_ctas);
 }
 
-const TmaPlan &active_plan(const mmod_handle *h) {
-    const TmaPlan &p = h->plans[h->variant >= 0 ? h->variant : kTmaDefaultVariant];
-    if (h->zlen_override <= 0) return p;
-    // MMOD_OPT_ZLEN: the same tiles, z ranges of the requested thickness
-    TmaPlan &q = h->plan_tmp;
+// The plan of variant v with the handle's z-range and work-claiming options.
+static const TmaPlan &plan_with_options(const mmod_handle *h, int v, TmaPlan &q) {
+    const TmaPlan &p = h->plans[v];
+    if (h->zlen_override <= 0 && h->claim_planes <= 0) return p;
     q = p;
-    q.zlen = std::min(h->zlen_override, h->cfg.nz);
-    q.zchunks = (h->cfg.nz + q.zlen - 1) / q.zlen;
-    q.grid = q.tiles_x * q.tiles_y * q.zchunks;
+    if (h->zlen_override > 0) {   // MMOD_OPT_ZLEN: the same tiles, z ranges of the requested thickness
+        q.zlen = std::min(h->zlen_override, h->cfg.nz);
+        q.zchunks = (h->cfg.nz + q.zlen - 1) / q.zlen;
+        q.grid = q.tiles_x * q.tiles_y * q.zchunks;
+    }
+    q.claim = h->claim_planes;   // MMOD_OPT_CLAIM: units of this many planes, claimed by one wave of CTAs
     return q;
 }
+
+const TmaPlan &active_plan(const mmod_handle *h) {
+    return plan_with_options(h, h->variant >= 0 ? h->variant : kTmaDefaultVariant, h->plan_tmp);
+}
+
+// Steps that also write g^n run the variant compiled with that output (the
+// same bits as every other variant).
+static const TmaPlan &g_plan(const mmod_handle *h) { return plan_with_options(h, kTmaGVariant, h->plan_tmp_g); }
 
 // Step arguments shared by every step of a run (n, buffers and gathers are
 // filled per step).
@@ -368,6 +380,7 @@ StepArgs base_args(mmod_handle *h, const Geometry &geo, const float *wavelet) {
     a.err = h->err_dev;
     a.fs = h->cfg.free_surface;
     a.pdl = h->pdl;
+    a.claim = h->claim_ctr;
     return a;
 }
 
@@ -378,7 +391,7 @@ cudaError_t enqueue_step(mmod_handle *h, const StepArgs &a, const CUtensorMap *c
                          bool tma, float *plain_gather_dst, cudaStream_t s, long long *count) {
     cudaError_t e;
     if (tma) {
-        e = launch_step_tma(a, cur, prev, &h->c_map, active_plan(h), s);
+        e = launch_step_tma(a, cur, prev, &h->c_map, a.gout ? g_plan(h) : active_plan(h), s);
         ++*count;
         return e;
     }
@@ -479,6 +492,7 @@ mmod_status run_loop_graph(mmod_handle *h, GraphSlot &g, const Geometry &geo, co
         const Geom pg = persistent_geom(plan, h->cfg.nz);
         const int units = pg.tiles_x * pg.tiles_y * pg.zchunks;
         MMOD_CK(h, cudaMemsetAsync(h->counters, 0, sizeof(int) * (size_t)units, s));
+        MMOD_CK(h, cudaMemsetAsync(h->queue, 0, sizeof(unsigned long long), s));
         MMOD_CK(h, cudaEventRecord(h->ev_t0, s));
         StepArgs a = base_args(h, geo, wav);
         a.pdl = 0;
@@ -490,6 +504,7 @@ mmod_status run_loop_graph(mmod_handle *h, GraphSlot &g, const Geometry &geo, co
         pa.n1 = h->cfg.nt;
         pa.units = units;
         pa.counters = h->counters;
+        pa.queue = h->queue;
         pa.rec_start = geo.g_start;
         pa.rec_idx = geo.g_idx;
         pa.rec_off = geo.g_off;
@@ -509,7 +524,8 @@ mmod_status run_loop_graph(mmod_handle *h, GraphSlot &g, const Geometry &geo, co
         return MMOD_OK;
     }
     const int kern = use_tma(h) ? 100 + active_plan(h).variant : MMOD_KERNEL_SIMPLE;
-    const long long opts = h->pdl + 2LL * h->zlen_override + (1LL << 40) * h->cpml_planes;
+    const long long opts = h->pdl + 2LL * h->zlen_override + (1LL << 20) * h->claim_planes +
+                           (1LL << 40) * h->cpml_planes;
     const void *key[4] = {wav, tr, &geo, nullptr};
     if (!g.exec || std::memcmp(g.key, key, sizeof(key)) != 0 || g.kernel != kern || g.opts != opts) {
         free_graph(g);
@@ -647,6 +663,9 @@ MMOD_API mmod_status mmod_create(const mmod_config *cfg, int device, mmod_handle
             h->ncounters = std::max<long long>(h->ncounters, (long long)h->plans[v].tiles_x * h->plans[v].tiles_y *
                                                                  h->plans[v].zchunks);
         CKC(cudaMalloc(&h->counters, sizeof(int) * (size_t)h->ncounters));
+        CKC(cudaMalloc(&h->queue, sizeof(unsigned long long)));
+        CKC(cudaMalloc(&h->claim_ctr, 2 * sizeof(int)));
+        CKC(cudaMemset(h->claim_ctr, 0, 2 * sizeof(int)));
     }
 #undef CKC
     *out = h;
@@ -698,6 +717,11 @@ MMOD_API mmod_status mmod_set_option(mmod_handle *h, int option, int value) {
         h->cpml_planes = value;
         return MMOD_OK;
     }
+    if (option == MMOD_OPT_CLAIM) {
+        if (value < 0 || value > 1 << 20) return fail(h, MMOD_ERR_ARG, "MMOD_OPT_CLAIM must be in [0, 2^20]");
+        h->claim_planes = value;
+        return MMOD_OK;
+    }
     if (option == MMOD_OPT_PERSISTENT_CTAS) {
         if (value < 0) return fail(h, MMOD_ERR_ARG, "MMOD_OPT_PERSISTENT_CTAS must be >= 0");
         h->persistent_ctas = value;
@@ -728,7 +752,14 @@ MMOD_API mmod_status mmod_get_plan(const mmod_handle *h, int *out8) {
     if (!h || !out8) return MMOD_ERR_ARG;
     if (!h->tma_ok) return MMOD_ERR_UNSUPPORTED;
     const TmaPlan &p = active_plan(h);
-    const int v[8] = {p.variant, p.tiles_x, p.tiles_y, p.zchunks, p.zlen, p.grid, p.block, p.occupancy};
+    int v[8] = {p.variant, p.tiles_x, p.tiles_y, p.zchunks, p.zlen, p.grid, p.block, p.occupancy};
+    Geom cg;
+    int units = 0, cgrid = 0;
+    if (claim_geom(p, h->cfg.nz, &cg, &units, &cgrid)) {   // a work-claiming launch: its units and grid
+        v[3] = cg.zchunks;
+        v[4] = cg.zlen;
+        v[5] = cgrid;
+    }
     for (int i = 0; i < 8; ++i) out8[i] = v[i];
     return MMOD_OK;
 }

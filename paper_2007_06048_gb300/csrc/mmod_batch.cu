@@ -12,9 +12,10 @@
 //     are captured once into a CUDA graph; the descriptor table is uploaded
 //     per call, so new wavelet / trace buffers need no new capture.  CTAs are
 //     ordered longest first so the last wave is made of short ones;
-//   persistent: one cooperative launch runs every shot's whole time loop; a
-//     work unit (a shot's tile and z range) starts a step when the
-//     neighbouring units of its shot have finished the previous one
+//   persistent: one cooperative launch runs every shot's whole time loop as
+//     a work list: CTAs claim (step, unit) items in step-major order, a unit
+//     being a shot's tile and z range; an item starts when the unit and its
+//     neighbouring units of the same shot have finished the previous step
 //     (per-unit counters, bounded waits).
 //
 // The autotuner times each compiled TMA variant (points per thread, z
@@ -48,6 +49,7 @@ struct mmod_batch {
     int nctas = 0;
     // persistent mode: units in shot order, counters per unit, counter base per shot
     int *d_unit_shot = nullptr, *d_unit_local = nullptr, *d_counter_base = nullptr, *d_counters = nullptr;
+    unsigned long long *d_queue = nullptr;   // next (step, unit) item of the persistent work list
     int units = 0;
     GraphSlot graph;
     cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;
@@ -101,6 +103,7 @@ void free_batch(mmod_batch *b) {
     if (b->d_unit_local) cudaFree(b->d_unit_local);
     if (b->d_counter_base) cudaFree(b->d_counter_base);
     if (b->d_counters) cudaFree(b->d_counters);
+    if (b->d_queue) cudaFree(b->d_queue);
     if (b->ev_t0) cudaEventDestroy(b->ev_t0);
     if (b->ev_t1) cudaEventDestroy(b->ev_t1);
 }
@@ -226,7 +229,10 @@ MMOD_API mmod_status mmod_batch_create(mmod_handle *const *shots, int nshots, mm
         d.cmap = h->c_map;
         d.args = base_args(h, h->fwd, nullptr);
         const TmaPlan &p = h->plans[0];
-        const int zchunks = (h->cfg.nz + kBatchZlen - 1) / kBatchZlen;
+        // MMOD_OPT_ZLEN of the shot, at least the stencil radius (a persistent
+        // unit's halo then reaches only the adjacent z ranges)
+        const int zt = h->zlen_override > 0 ? std::max(h->zlen_override, kRadius) : kBatchZlen;
+        const int zchunks = (h->cfg.nz + zt - 1) / zt;
         const int zlen = (h->cfg.nz + zchunks - 1) / zchunks;
         d.geom = Geom{p.tiles_x, p.tiles_y, (h->cfg.nz + zlen - 1) / zlen, zlen};
         d.nblocks = d.geom.tiles_x * d.geom.tiles_y * d.geom.zchunks;
@@ -271,6 +277,7 @@ MMOD_API mmod_status mmod_batch_create(mmod_handle *const *shots, int nshots, mm
     CKB(cudaMalloc(&b->d_unit_local, sizeof(int) * unit_local.size()));
     CKB(cudaMalloc(&b->d_counter_base, sizeof(int) * counter_base.size()));
     CKB(cudaMalloc(&b->d_counters, sizeof(int) * unit_shot.size()));
+    CKB(cudaMalloc(&b->d_queue, sizeof(unsigned long long)));
     CKB(cudaMemcpy(b->d_unit_shot, unit_shot.data(), sizeof(int) * unit_shot.size(), cudaMemcpyHostToDevice));
     CKB(cudaMemcpy(b->d_unit_local, unit_local.data(), sizeof(int) * unit_local.size(), cudaMemcpyHostToDevice));
     CKB(cudaMemcpy(b->d_counter_base, counter_base.data(), sizeof(int) * counter_base.size(), cudaMemcpyHostToDevice));
@@ -378,6 +385,7 @@ MMOD_API mmod_status mmod_batch_forward(mmod_batch *b, const float *const *wavel
     if (b->mode == MMOD_BATCH_PERSISTENT) {
         // every shot's loop in one cooperative launch (no graph: one node)
         BCK(b, cudaMemsetAsync(b->d_counters, 0, sizeof(int) * (size_t)b->units, s));
+        BCK(b, cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned long long), s));
         BCK(b, cudaEventRecord(b->ev_t0, s));
         if (b->nt > 0) {
             BatchPersistArgs pa{};
@@ -396,6 +404,7 @@ MMOD_API mmod_status mmod_batch_forward(mmod_batch *b, const float *const *wavel
             pa.unit_local = b->d_unit_local;
             pa.counter_base = b->d_counter_base;
             pa.counters = b->d_counters;
+            pa.queue = b->d_queue;
             BCK(b, launch_step_tma_batch_persistent(b->variant, b->d_desc, pa, pgrid, s));
         }
         BCK(b, cudaEventRecord(b->ev_t1, s));

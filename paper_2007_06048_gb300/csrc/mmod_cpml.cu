@@ -6,17 +6,27 @@
 //     zeta_a^n = b_a zeta_a^{n-1} + g_a (D2_a u^n + D1_a psi_a^n),
 // b = exp(-(d + alpha) dt), g = d (b - 1) / (d + alpha) per cell of the axis
 // (zero outside the layers), D2_a the order-8 second difference (the step
-// kernels' pair form), D1_a the order-8 centred first difference.
+// kernels' pair form), D1_a the order-8 centred first difference.  The terms
+// D1_a psi_a + zeta_a exist only where axis a's profile is on (g_a != 0);
+// psi_a is zero elsewhere.
 //
 // Each step runs the usual step kernel without damping (u^{n+1} = 2u^n -
-// u^{n-1} + c L u^n + sources), then two passes over the six layer slabs
-// only: the psi pass (psi_a^n from u^n, in place) and the correction pass
-// (zeta_a^n, and u^{n+1} += c sum_a (D1_a psi_a^n + zeta_a^n)).  One thread
-// per layer column over a z range of at most CpmlArgs::zc planes (a block
-// takes 128 consecutive columns of one slab); each cell loads its 9-point lines
-// before the arithmetic, without bounds tests where the line stays inside
-// the grid.  u and psi are 0 outside the grid; with a free surface the top
-// layer is absent and the plane k = 0 is left alone (u, psi and zeta stay 0).
+// u^{n-1} + c L u^n + sources), then one pass per axis over that axis's
+// layer cells: psi_a^n, zeta_a^n and u^{n+1} += c (D1_a psi_a^n + zeta_a^n).
+// A pass works on lines along its axis and on the layer ranges of a line
+// ([0, L) and [n - L, n), or the whole line where the two ranges' stencils
+// meet), so every psi_a value it needs is computed by the same thread or warp
+// in the same pass and no gathers are needed:
+//   x: one warp per row segment (lane = cell, 24 cells and a 4-cell margin
+//      each side), neighbours by warp shuffles;
+//   y, z (and x for ranges wider than 24): one thread per line range,
+//      consecutive threads on consecutive x (coalesced), marching along the
+//      axis with a 13-value window of u^n and a 9-value window of psi^n, the
+//      correction trailing psi by the stencil radius.
+// Per cell, psi and zeta take the same FP32 operations as before; u^{n+1}
+// gains one fused multiply-add per axis whose profile is on.  u and psi are
+// 0 outside the grid; with a free surface the top layer is absent and the
+// plane k = 0 is left alone (u, psi and zeta stay 0).
 #include "mmod_cpml.h"
 #include "mmod_internal.h"
 
@@ -24,179 +34,220 @@ namespace mmod {
 namespace {
 
 constexpr int kLine = 2 * kRadius + 1;   // -4..4 along the axis
+constexpr int kWarpCells = 32 - 2 * kRadius;   // cells per warp row segment
 
-// First-difference weights (unit spacing): 4/5, -1/5, 4/105, -1/280.
-__device__ __forceinline__ float d1_of(const float (&x)[kLine], float inv_h) {
-    constexpr float w[4] = {4.0f / 5.0f, -1.0f / 5.0f, 4.0f / 105.0f, -1.0f / 280.0f};
+__device__ __forceinline__ float d1_w(int m) {   // first-difference weights: 4/5, -1/5, 4/105, -1/280
+    return m == 1 ? 4.0f / 5.0f : (m == 2 ? -1.0f / 5.0f : (m == 3 ? 4.0f / 105.0f : -1.0f / 280.0f));
+}
+
+// D1 of the 9 values x[0..8] (centre x[4]), unit spacing times inv_h.
+__device__ __forceinline__ float d1_of(const float *x, float inv_h) {
     float s = 0.0f;
 #pragma unroll
-    for (int m = 1; m <= kRadius; ++m) s = __fmaf_rn(w[m - 1], __fsub_rn(x[kRadius + m], x[kRadius - m]), s);
+    for (int m = 1; m <= kRadius; ++m) s = __fmaf_rn(d1_w(m), __fsub_rn(x[kRadius + m], x[kRadius - m]), s);
     return __fmul_rn(s, inv_h);
 }
 
-// The 9 values of f along an axis (stride st) centred on offset o, index q0
-// of n along the axis; 0 outside the grid.
-__device__ __forceinline__ void line9(const float *__restrict__ f, long long o, long long st, int q0, int n,
-                                      float (&x)[kLine]) {
-    if (q0 >= kRadius && q0 + kRadius < n) {
-        const float *fp = f + o - kRadius * st;
-#pragma unroll
-        for (int m = 0; m < kLine; ++m, fp += st) x[m] = __ldg(fp);
-    } else {
-#pragma unroll
-        for (int m = 0; m < kLine; ++m) {
-            const int q = q0 - kRadius + m;
-            x[m] = ((unsigned)q < (unsigned)n) ? __ldg(f + o + (m - kRadius) * st) : 0.0f;
-        }
-    }
-}
-
-struct Box {
-    int x0, y0, z0, ex, ey, ez;
-    int ncb;      // blocks over the ex * ey columns of the box
-    int zc, tz;   // planes per z range, z ranges
-    int first;    // first block of this box
-};
-struct Boxes {
-    Box b[6];
-    int n;
-    long long blocks;
-};
-
-constexpr int kBT = 128;   // a block: 128 consecutive columns of one box (row-major in x, y)
-
-// Column of this thread in the layer slabs and its planes [k0, k1); false
-// when outside its box.  Consecutive threads take consecutive columns of the
-// box's rows, so a 20-wide x slab fills whole warps (1.6 rows per warp).
-__device__ __forceinline__ bool layer_column(const CpmlArgs &p, const Boxes &boxes, int &i, int &j, int &k0,
-                                             int &k1) {
-    const int blk = blockIdx.x;
-    int bi = 0;
-    while (bi + 1 < boxes.n && blk >= boxes.b[bi + 1].first) ++bi;
-    const Box &B = boxes.b[bi];
-    const int local = blk - B.first;
-    const int cb = local % B.ncb;
-    const int tz = local / B.ncb;
-    const int col = cb * kBT + threadIdx.x;
-    if (col >= B.ex * B.ey) return false;
-    const int lj = col / B.ex;
-    i = B.x0 + (col - lj * B.ex);
-    j = B.y0 + lj;
-    k0 = B.z0 + tz * B.zc;
-    k1 = min(k0 + B.zc, B.z0 + B.ez);
-    if (p.fs && k0 == 0) k0 = 1;   // the free-surface plane stays 0
-    return true;
-}
-
-template <int A>
-__device__ __forceinline__ void psi_axis(const CpmlArgs &p, const float *__restrict__ u, long long o, long long st,
-                                         int q0, int n, float g) {
-    float x[kLine];
-    line9(u, o, st, q0, n, x);
-    float *ps = p.psi[A] + o;
-    *ps = __fmaf_rn(__ldg(p.b[A] + q0), *ps, __fmul_rn(g, d1_of(x, p.inv_h[A])));
-}
-
-// 16 blocks per SM: 32 registers, full occupancy for the latency-bound line
-// gathers (the correction pass would spill at that cap and keeps 40)
-__global__ void __launch_bounds__(kBT, 16)
-    cpml_psi_kernel(const CpmlArgs p, const Boxes boxes, const float *__restrict__ u) {
-    int i, j, k0, k1;
-    if (!layer_column(p, boxes, i, j, k0, k1)) return;
-    const float gx = __ldg(p.g[0] + i), gy = __ldg(p.g[1] + j);
-    long long o = (long long)k0 * p.plane + (long long)j * p.nxp + i;
-    for (int k = k0; k < k1; ++k, o += p.plane) {
-        const float gz = __ldg(p.g[2] + k);
-        if (gx != 0.0f) psi_axis<0>(p, u, o, 1, i, p.nx, gx);
-        if (gy != 0.0f) psi_axis<1>(p, u, o, p.nxp, j, p.ny, gy);
-        if (gz != 0.0f) psi_axis<2>(p, u, o, p.plane, k, p.nz, gz);
-    }
-}
-
-// zeta_a^n and the axis's term D1_a psi_a^n + zeta_a^n.
-template <int A>
-__device__ __forceinline__ float correct_axis(const CpmlArgs &p, const float *__restrict__ u, long long o,
-                                              long long st, int q0, int n, float g) {
-    float x[kLine], q[kLine];
-    line9(u, o, st, q0, n, x);
-    line9(p.psi[A], o, st, q0, n, q);
+// D2 of the 9 values x[0..8] in the step kernels' pair form.
+__device__ __forceinline__ float d2_of(const float *x, const float (&w)[kRadius]) {
     const float two_p = __fadd_rn(x[kRadius], x[kRadius]);
-    float d2 = pair_first(p.w[A][0], x[kRadius + 1], x[kRadius - 1], two_p);
+    float d2 = pair_first(w[0], x[kRadius + 1], x[kRadius - 1], two_p);
 #pragma unroll
-    for (int m = 2; m <= kRadius; ++m) d2 = pair_acc(d2, p.w[A][m - 1], x[kRadius + m], x[kRadius - m], two_p);
-    const float dpsi = d1_of(q, p.inv_h[A]);
-    float *ze = p.zeta[A] + o;
-    const float z = __fmaf_rn(__ldg(p.b[A] + q0), *ze, __fmul_rn(g, __fadd_rn(d2, dpsi)));
-    *ze = z;
-    return __fadd_rn(dpsi, z);
+    for (int m = 2; m <= kRadius; ++m) d2 = pair_acc(d2, w[m - 1], x[kRadius + m], x[kRadius - m], two_p);
+    return d2;
 }
 
-__global__ void __launch_bounds__(kBT)
-    cpml_correct_kernel(const CpmlArgs p, const Boxes boxes, const float *__restrict__ u, float *__restrict__ uout) {
-    int i, j, k0, k1;
-    if (!layer_column(p, boxes, i, j, k0, k1)) return;
-    const float gx = __ldg(p.g[0] + i), gy = __ldg(p.g[1] + j);
-    long long o = (long long)k0 * p.plane + (long long)j * p.nxp + i;
-    for (int k = k0; k < k1; ++k, o += p.plane) {
-        const float gz = __ldg(p.g[2] + k);
-        float acc = 0.0f;
-        bool any = false;
-        if (gx != 0.0f) {
-            acc = __fadd_rn(acc, correct_axis<0>(p, u, o, 1, i, p.nx, gx));
-            any = true;
+// Layer ranges of one axis of n points with layer width L (low_absent: no
+// low layer, the z axis under a free surface).  The ranges are merged into
+// one when the stencil of one reaches the other.
+struct Ranges {
+    int n, lo[2], hi[2];
+};
+
+Ranges axis_ranges(int n, int L, bool low_absent) {
+    Ranges r{};
+    if (L <= 0) return r;
+    if (!low_absent && n - L < L + kRadius) {
+        r.lo[0] = 0;
+        r.hi[0] = n;
+        r.n = 1;
+        return r;
+    }
+    if (!low_absent) {
+        r.lo[r.n] = 0;
+        r.hi[r.n] = L;
+        ++r.n;
+    }
+    r.lo[r.n] = n - L;
+    r.hi[r.n] = n;
+    ++r.n;
+    return r;
+}
+
+// One layer range [lo, hi) of the line at offset o0 (axis stride st, n points
+// along the axis) for axis A: psi_a, zeta_a and the u^{n+1} correction.
+template <int A>
+__device__ __forceinline__ void march_range(const CpmlArgs &p, long long o0, long long st, int n, int lo, int hi,
+                                            const float *__restrict__ u, float *__restrict__ uout) {
+    const float *B = p.b[A], *G = p.g[A];
+    float *psi = p.psi[A], *zeta = p.zeta[A];
+    const float ih = p.inv_h[A];
+    float uw[2 * kRadius + kLine - kRadius];   // u at q-8 .. q+4 (13 values)
+    float pw[kLine];                           // psi at q-8 .. q
+#pragma unroll
+    for (int m = 0; m < 13; ++m) {
+        const int q = lo - 13 + m;
+        uw[m] = (q >= 0 && q < n) ? __ldg(u + o0 + q * st) : 0.0f;
+    }
+#pragma unroll
+    for (int m = 0; m < kLine; ++m) pw[m] = 0.0f;
+    for (int q = lo - kRadius; q < hi + kRadius; ++q) {
+#pragma unroll
+        for (int m = 0; m < 12; ++m) uw[m] = uw[m + 1];
+        const int qa = q + kRadius;
+        uw[12] = (qa >= 0 && qa < n) ? __ldg(u + o0 + (long long)qa * st) : 0.0f;
+#pragma unroll
+        for (int m = 0; m < kLine - 1; ++m) pw[m] = pw[m + 1];
+        float ps = 0.0f;   // psi outside the range is 0 (outside the grid or g = 0)
+        if (q >= lo && q < hi) {
+            const float g = __ldg(G + q);
+            if (g != 0.0f) {
+                float *pp = psi + o0 + (long long)q * st;
+                ps = __fmaf_rn(__ldg(B + q), *pp, __fmul_rn(g, d1_of(uw + kRadius, ih)));
+                *pp = ps;
+            }
         }
-        if (gy != 0.0f) {
-            acc = __fadd_rn(acc, correct_axis<1>(p, u, o, p.nxp, j, p.ny, gy));
-            any = true;
+        pw[kLine - 1] = ps;
+        const int pc = q - kRadius;   // the correction trails psi by the radius
+        if (pc >= lo && pc < hi) {
+            const float g = __ldg(G + pc);
+            if (g != 0.0f) {
+                const long long o = o0 + (long long)pc * st;
+                const float d2 = d2_of(uw, p.w[A]);
+                const float dpsi = d1_of(pw, ih);
+                const float z = __fmaf_rn(__ldg(B + pc), zeta[o], __fmul_rn(g, __fadd_rn(d2, dpsi)));
+                zeta[o] = z;
+                uout[o] = __fmaf_rn(__ldg(p.c + o), __fadd_rn(dpsi, z), uout[o]);
+            }
         }
-        if (gz != 0.0f) {
-            acc = __fadd_rn(acc, correct_axis<2>(p, u, o, p.plane, k, p.nz, gz));
-            any = true;
-        }
-        if (any) uout[o] = __fmaf_rn(__ldg(p.c + o), acc, uout[o]);
     }
 }
 
-void add_box(Boxes &bx, int x0, int y0, int z0, int ex, int ey, int ez, int zc_max) {
-    if (ex <= 0 || ey <= 0 || ez <= 0) return;
-    Box &b = bx.b[bx.n++];
-    b.x0 = x0; b.y0 = y0; b.z0 = z0; b.ex = ex; b.ey = ey; b.ez = ez;
-    b.ncb = (int)(((long long)ex * ey + kBT - 1) / kBT);
-    b.tz = (ez + zc_max - 1) / zc_max;    // equal ranges of at most zc_max planes
-    b.zc = (ez + b.tz - 1) / b.tz;
-    b.tz = (ez + b.zc - 1) / b.zc;
-    b.first = (int)bx.blocks;
-    bx.blocks += (long long)b.ncb * b.tz;
+// y and z passes (and the x pass for ranges wider than a warp row segment):
+// work item t is line t % lines of range t / lines (consecutive t on
+// consecutive x for y and z); grid-stride over the items, so each thread
+// takes about `per` of them and neighbouring threads stay on neighbouring
+// lines.
+template <int A>
+__global__ void __launch_bounds__(128) cpml_line_kernel(const CpmlArgs p, const Ranges rg, const float *__restrict__ u,
+                                                        float *__restrict__ uout) {
+    const int n = A == 0 ? p.nx : (A == 1 ? p.ny : p.nz);
+    // the other two coordinates: (x, z) for y lines, (x, y) for z lines, (y, z) for x lines
+    const int n1 = A == 0 ? p.ny : p.nx, n2 = A == 2 ? p.ny : p.nz;
+    const long long lines = (long long)n1 * n2;
+    const long long st = A == 0 ? 1 : (A == 1 ? p.nxp : p.plane);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < lines * rg.n; t += stride) {
+        const int r = (int)(t / lines);
+        const long long l = t - (long long)r * lines;
+        const int c1 = (int)(l % n1), c2 = (int)(l / n1);
+        long long o0;
+        if (A == 0) {
+            if (p.fs && c2 == 0) continue;   // the free-surface plane stays 0
+            o0 = (long long)c2 * p.plane + (long long)c1 * p.nxp;
+        } else if (A == 1) {
+            if (p.fs && c2 == 0) continue;
+            o0 = (long long)c2 * p.plane + c1;
+        } else {
+            o0 = (long long)c2 * p.nxp + c1;
+        }
+        march_range<A>(p, o0, st, n, rg.lo[r], rg.hi[r], u, uout);
+    }
 }
 
-// The layer cells as six disjoint slabs: z layers (whole planes), y layers
-// between them, x layers between those.  With a free surface the top z layer
-// is absent and the y and x slabs reach the surface.
-Boxes layer_boxes(const CpmlArgs &p) {
-    Boxes bx{};
-    const int L = p.nbl;
-    if (L <= 0) return bx;
-    const int zlo = p.fs ? 0 : L, zhi = p.nz - L, zc = p.zc > 0 ? p.zc : kCpmlPlanes;
-    if (!p.fs) add_box(bx, 0, 0, 0, p.nx, p.ny, L, zc);
-    add_box(bx, 0, 0, p.nz - L, p.nx, p.ny, L, zc);
-    add_box(bx, 0, 0, zlo, p.nx, L, zhi - zlo, zc);
-    add_box(bx, 0, p.ny - L, zlo, p.nx, L, zhi - zlo, zc);
-    add_box(bx, 0, L, zlo, L, p.ny - 2 * L, zhi - zlo, zc);
-    add_box(bx, p.nx - L, L, zlo, L, p.ny - 2 * L, zhi - zlo, zc);
-    return bx;
+// x pass: one warp per row segment of one layer range (at most 24 cells,
+// lanes 4..27 hold them, lanes 0..3 and 28..31 the margins); grid-stride over
+// the segments (about `per` per warp).
+__global__ void __launch_bounds__(128) cpml_x_warp_kernel(const CpmlArgs p, const Ranges rg, const float *__restrict__ u,
+                                                          float *__restrict__ uout) {
+    const int lane = threadIdx.x & 31;
+    const long long rows = (long long)p.ny * p.nz;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const float ih = p.inv_h[0];
+    for (long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < rows * rg.n; t += nwarps) {
+        const int r = (int)(t / rows);
+        const long long l = t - (long long)r * rows;
+        const int j = (int)(l % p.ny), k = (int)(l / p.ny);
+        if (p.fs && k == 0) continue;   // the free-surface plane stays 0 (uniform over the warp)
+        const long long row = (long long)k * p.plane + (long long)j * p.nxp;
+        const int i = rg.lo[r] - kRadius + lane;
+        const bool in_grid = i >= 0 && i < p.nx;
+        const bool mine = i >= rg.lo[r] && i < rg.hi[r];
+        const float uu = in_grid ? __ldg(u + row + i) : 0.0f;
+        const float g = mine ? __ldg(p.g[0] + i) : 0.0f;
+        float x[kLine];
+#pragma unroll
+        for (int m = 1; m <= kRadius; ++m) {
+            x[kRadius + m] = __shfl_down_sync(0xffffffffu, uu, m);
+            x[kRadius - m] = __shfl_up_sync(0xffffffffu, uu, m);
+        }
+        x[kRadius] = uu;
+        float ps = 0.0f;
+        if (g != 0.0f) {
+            float *pp = p.psi[0] + row + i;
+            ps = __fmaf_rn(__ldg(p.b[0] + i), *pp, __fmul_rn(g, d1_of(x, ih)));
+            *pp = ps;
+        }
+        float q[kLine];
+#pragma unroll
+        for (int m = 1; m <= kRadius; ++m) {
+            q[kRadius + m] = __shfl_down_sync(0xffffffffu, ps, m);
+            q[kRadius - m] = __shfl_up_sync(0xffffffffu, ps, m);
+        }
+        q[kRadius] = ps;
+        if (g != 0.0f) {
+            const long long o = row + i;
+            const float d2 = d2_of(x, p.w[0]);
+            const float dpsi = d1_of(q, ih);
+            const float z = __fmaf_rn(__ldg(p.b[0] + i), p.zeta[0][o], __fmul_rn(g, __fadd_rn(d2, dpsi)));
+            p.zeta[0][o] = z;
+            uout[o] = __fmaf_rn(__ldg(p.c + o), __fadd_rn(dpsi, z), uout[o]);
+        }
+    }
+}
+
+int blocks_for(long long threads) {
+    const long long b = (threads + 127) / 128;
+    return (int)(b < 1 ? 1 : b);
 }
 
 }  // namespace
 
 cudaError_t launch_cpml_layers(const CpmlArgs &p, const float *u, float *uout, cudaStream_t s) {
-    const Boxes bx = layer_boxes(p);
-    if (bx.blocks == 0) return cudaSuccess;
-    if (bx.blocks >= (1LL << 31)) return cudaErrorInvalidConfiguration;
-    cpml_psi_kernel<<<(unsigned)bx.blocks, kBT, 0, s>>>(p, bx, u);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    cpml_correct_kernel<<<(unsigned)bx.blocks, kBT, 0, s>>>(p, bx, u, uout);
-    return cudaGetLastError();
+    if (p.nbl <= 0) return cudaSuccess;
+    const int per = p.zc > 0 ? p.zc : kCpmlPlanes;
+    const Ranges rx = axis_ranges(p.nx, p.nbl, false), ry = axis_ranges(p.ny, p.nbl, false),
+                 rz = axis_ranges(p.nz, p.nbl, p.fs != 0);
+    bool x_warp = true;
+    for (int r = 0; r < rx.n; ++r) x_warp = x_warp && rx.hi[r] - rx.lo[r] <= kWarpCells;
+    const long long xl = (long long)p.ny * p.nz * rx.n, yl = (long long)p.nx * p.nz * ry.n,
+                    zl = (long long)p.nx * p.ny * rz.n;
+    if (rx.n > 0) {
+        if (x_warp)
+            cpml_x_warp_kernel<<<blocks_for(((xl + per - 1) / per) * 32), 128, 0, s>>>(p, rx, u, uout);
+        else
+            cpml_line_kernel<0><<<blocks_for((xl + per - 1) / per), 128, 0, s>>>(p, rx, u, uout);
+        if (cudaError_t e = cudaGetLastError()) return e;
+    }
+    if (ry.n > 0) {
+        cpml_line_kernel<1><<<blocks_for((yl + per - 1) / per), 128, 0, s>>>(p, ry, u, uout);
+        if (cudaError_t e = cudaGetLastError()) return e;
+    }
+    if (rz.n > 0) {
+        cpml_line_kernel<2><<<blocks_for((zl + per - 1) / per), 128, 0, s>>>(p, rz, u, uout);
+        if (cudaError_t e = cudaGetLastError()) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace mmod

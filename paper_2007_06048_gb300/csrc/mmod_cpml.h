@@ -18,13 +18,13 @@ struct CpmlArgs {
     float inv_h[3];
     float w[3][kRadius];
     const float *c;
-    int zc;   // planes per thread (the last z range of a slab may be shorter)
+    int zc;   // layer lines per thread (y, z passes) or row segments per warp (x pass), about
 };
 
-// Default planes per thread of the layer passes.
-constexpr int kCpmlPlanes = 5;
+// Default lines per thread of the layer passes.
+constexpr int kCpmlPlanes = 1;
 // After the undamped step (u = u^n, uout = u^{n+1}): the layer terms on the
-// layer cells, a psi pass and a correction pass.
+// layer cells, one pass per axis.
 cudaError_t launch_cpml_layers(const CpmlArgs &p, const float *u, float *uout, cudaStream_t s);
 
 }  // namespace mmod

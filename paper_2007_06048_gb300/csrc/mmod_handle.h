@@ -99,10 +99,14 @@ struct mmod_handle {
     int test_stall = 0;                 // MMOD_OPT_TEST_STALL (one run)
     int zlen_override = 0;              // MMOD_OPT_ZLEN (0: the plan's z ranges)
     int cpml_planes = 0;                // MMOD_OPT_CPML_PLANES (0: the default)
+    int claim_planes = 0;               // MMOD_OPT_CLAIM (0: the static plan)
+    int *claim_ctr = nullptr;           // {next unit, CTAs done} of work-claiming step launches
     float *cpml_mem = nullptr;          // CPML: psi_x, psi_y, psi_z, zeta_x, zeta_y, zeta_z volumes
     float *cpml_bg = nullptr;           // CPML: b_x | b_y | b_z | g_x | g_y | g_z per cell
     mutable mmod::TmaPlan plan_tmp;     // active_plan() with the override applied
+    mutable mmod::TmaPlan plan_tmp_g;   // the same for the steps that write g^n
     int *counters = nullptr;            // per work unit of the persistent kernel
+    unsigned long long *queue = nullptr;   // the persistent kernel's next (step, unit) item
     long long ncounters = 0;
     int ckpt_scheme = MMOD_SCHEME_SEGMENTS;   // MMOD_OPT_CKPT_SCHEME
     bool tma_ok = false;
@@ -115,9 +119,11 @@ struct mmod_handle {
         std::vector<CUtensorMap> seg_cur, seg_prev;
         float *psi[2] = {nullptr, nullptr};
         CUtensorMap psi_cur[2], psi_prev[2];
-        float *gradc = nullptr;             // padded FP32 accumulator
+        float *gradc = nullptr;             // padded FP32 sum of psi^{n+1} g^n ...
+        float *gcomp = nullptr;             // ... and its compensation term
         void *ckpt = nullptr;               // nslot * 2 volumes (FP32 or 16-bit)
-        float *ckpt_scale = nullptr;        // nslot * 2 * nz per-plane scales (16-bit storage)
+        float *ckpt_scale = nullptr;        // 16-bit storage: per-plane (BF16, FP16) or per-32-value
+                                            // (BFP16) scales of the nslot * 2 volumes
         size_t ckpt_bytes = 0;
     } gw;
 

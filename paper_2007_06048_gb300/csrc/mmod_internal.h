@@ -56,6 +56,11 @@ struct StepArgs {
     int pdl;                              // 0: plain launch; 1: programmatic dependent launch;
                                           // 2: the same, and the previous kernel in the stream
                                           //    is the previous step of this run
+    int *claim;                           // work-claiming launches: {next unit, CTAs done},
+                                          // 0 between launches (null: the static plan)
+    float *gout;                          // gradient replay: also write g^n = L u^n + s^n here
+                                          // (padded layout; null: not written)
+    float inv_cell;                       // 1 / (hx hy hz): s^n = w[n] / (hx hy hz) at a source
 };
 
 // Adds the sources of injection point p to u^{n+1} (already stored): the
@@ -122,6 +127,20 @@ __device__ __forceinline__ void inject_points(const StepArgs &a, float *uout, in
     }
 }
 
+// The source term of g^n = L u^n + s^n at injection points [lo, hi) of the
+// step's g^n (already holding L u^n): + w[n] / (hx hy hz) per source, in table
+// order; thread t of nthreads.
+__device__ __forceinline__ void inject_g_points(const StepArgs &a, int n, int lo, int hi, int t, int nthreads) {
+    for (int p = lo + t; p < hi; p += nthreads) {
+        float *dst = a.gout + __ldg(a.inj.pt_off + p);
+        float v = *dst;
+        for (int s = __ldg(a.inj.pt_first + p); s < __ldg(a.inj.pt_first + p + 1); ++s)
+            v = __fmaf_rn(__ldg(a.wavelet + (long long)__ldg(a.inj.src_row + s) * a.wrs + (long long)n * a.wcs),
+                          a.inv_cell, v);
+        *dst = v;
+    }
+}
+
 // Host helpers shared by the entry points (mmod_api.cu).
 void damping_profile(int n, int nbl, double h, double vmax, double R, double dt, float *out);
 // With a free surface the z axis has no layer under the surface plane.
@@ -178,6 +197,7 @@ struct BatchPersistArgs {
     int n0, n1, units;
     const int *unit_shot, *unit_local, *counter_base;
     int *counters;
+    unsigned long long *queue;   // next (step, unit) item of the work list, zeroed before the launch
 };
 cudaError_t launch_step_tma_batch_persistent(int variant, const ShotDesc *shots, const BatchPersistArgs &pa, int grid,
                                              cudaStream_t s);
@@ -187,9 +207,9 @@ cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap *cur_map,
                             const CUtensorMap *prev_map, const CUtensorMap *c_map,
                             const TmaPlan &plan, cudaStream_t s);
 
-// Persistent run: one cooperative launch advances steps n0 .. n1-1.  Each CTA
-// owns the work units (tile x z range) unit = blockIdx.x + k * gridDim.x;
-// a unit starts step n once its 26 neighbours have completed step n-1
+// Persistent run: one cooperative launch advances steps n0 .. n1-1.  CTAs
+// claim (step, work unit) items in step-major order from a queue; an item
+// starts once its unit and the unit's 26 neighbours have completed step n-1
 // (counters[v] >= n: they wrote the u^n it reads and finished reading the
 // u^{n-1} it overwrites), so no launch boundary separates the steps.  The
 // receivers of a unit (bucketed like the injection table: entries
@@ -201,6 +221,7 @@ struct TmaMaps {
 struct PersistArgs {
     int n0, n1, units;
     int *counters;                    // per unit: steps completed, zeroed before the run
+    unsigned long long *queue;        // next (step, unit) item of the work list, zeroed before the run
     const int *rec_start, *rec_idx;   // receivers bucketed per (tile, plane); original index
     const long long *rec_off;         // padded offset of each bucketed receiver
     float *traces;                    // [nt][nrec] or null
@@ -237,13 +258,13 @@ cudaError_t launch_unreverse_transpose(const float *g, int nt, int ncol, double 
                                        cudaStream_t s);
 // Gradient helpers (mmod_setup.cu).
 // Imaging condition of nsteps (1 or 2) forward steps n, n-1: psi[t] =
-// psi^{n+1-t}, u[t] = u^{n+1-t} (t = 0 .. nsteps + 1), grad_c accumulated in
-// the order of the steps.
-cudaError_t launch_imaging(int nsteps, const float *const *psi, const float *const *u, const float *c,
-                           const float *ex, const float *ey, const float *ez, int nx, int ny, int nz, int nxp,
-                           float *grad_c, cudaStream_t s);
-cudaError_t launch_grad_to_velocity(const float *grad_c, const float *vel, int nx, int ny, int nz, int nxp,
-                                    double dt, float *grad_v, cudaStream_t s);
+// psi^{n+1-t}, g[t] = g^{n-t} = L u^{n-t} + s^{n-t}; the compensated sum
+// (acc, comp) gains psi[t] g[t] in the order of the steps.
+cudaError_t launch_imaging(int nsteps, const float *const *psi, const float *const *g, int nx, int ny, int nz,
+                           int nxp, float *acc, float *comp, cudaStream_t s);
+// grad_v = 2 (acc + comp) / v (dJ/dv from the sum of psi^{n+1} g^n), dense output.
+cudaError_t launch_grad_to_velocity(const float *acc, const float *comp, const float *vel, int nx, int ny, int nz,
+                                    int nxp, float *grad_v, cudaStream_t s);
 cudaError_t launch_dot(const float *a, const float *b, long long n, double *out, cudaStream_t s);
 cudaError_t launch_pack(const float *dense, int nx, int ny, int nz, int nxp, float *padded,
                         cudaStream_t s);

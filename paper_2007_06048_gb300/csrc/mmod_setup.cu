@@ -176,30 +176,41 @@ __global__ void unreverse_transpose_kernel(const float *__restrict__ g, int nt, 
     }
 }
 
-// Zero-lag imaging condition of forward step n:
-//   grad_c += psi^{n+1} (D u^{n+1} - 2 u^n + E u^{n-1}) / c^2,
-// psi = c mu the adjoint wavefield, D = 1 + e, E = 1 - e.  Padding columns
-// are left untouched.
-__device__ __forceinline__ float imaging_term(float psi, float un, float uc, float up, float cc, float e,
-                                              float g) {
-    const float d2 = __fmaf_rn(__fadd_rn(1.0f, e), un, __fmaf_rn(-2.0f, uc, __fmul_rn(__fsub_rn(1.0f, e), up)));
-    return __fmaf_rn(psi, __fdiv_rn(d2, __fmul_rn(cc, cc)), g);
-}
-
+// Zero-lag imaging condition: with mu = psi / c the adjoint state,
+//   dJ/dc = sum_n mu^{n+1} g^n,  g^n = L u^n + s^n (written by the replay's
+// step kernel), so the kernel accumulates A = sum_n psi^{n+1} g^n and the
+// factor 1 / c is applied once at the end (dJ/dv = 2 dt^2 v A / c = 2 A / v).
+// The terms of a point change sign from step to step (two oscillating fields
+// correlated at zero lag), so their sum is much smaller than the sum of their
+// magnitudes; a plain FP32 running sum loses about a digit per decade of
+// that ratio.  The sum is therefore compensated, in FP32: the accurate dot
+// product of Ogita, Rump and Oishi (2005, "Dot2"): each product split exactly
+// into h + r (r from a fused multiply-add), added to the running sum p by
+// Knuth's error-free TwoSum (p + h = p' + q exactly), and q + r collected in a
+// second sum s; the result p + s is as accurate as a sum in twice the working
+// precision followed by one rounding.
 // Four consecutive x of one row per thread (16-byte loads; rows are padded to
 // 32 floats, so a group never straddles rows); columns past nx are loaded
 // (in bounds of the padded row) but not stored.  NS = 1: forward step n
-// (psi[0] = psi^{n+1}; u[0..2] = u^{n+1}, u^n, u^{n-1}); NS = 2: steps n and
-// n - 1 in that order (psi[1] = psi^n, u[3] = u^{n-2}), the same operations
-// as two single-step passes but u^n, u^{n-1}, c and grad_c read once.
+// (psi[0] = psi^{n+1}, g[0] = g^n); NS = 2: steps n and n - 1 in that order
+// (psi[1] = psi^n, g[1] = g^{n-1}), the same operations as two single-step
+// passes with p and s read and written once.
 struct ImagingArgs {
     const float4 *psi[2];
-    const float4 *u[4];
-    const float4 *c;
-    const float *ex, *ey, *ez;
+    const float4 *g[2];
     int nx, ny, nz, nxp;
-    float4 *grad;
+    float4 *acc, *comp;   // p and s of the compensated sum
 };
+
+__device__ __forceinline__ void dot2_step(float x, float y, float &p, float &s) {
+    const float h = __fmul_rn(x, y);
+    const float r = __fmaf_rn(x, y, -h);        // x y = h + r exactly
+    const float pn = __fadd_rn(p, h);
+    const float z = __fsub_rn(pn, p);
+    const float q = __fadd_rn(__fsub_rn(p, __fsub_rn(pn, z)), __fsub_rn(h, z));   // p + h = pn + q exactly
+    p = pn;
+    s = __fadd_rn(s, __fadd_rn(q, r));
+}
 
 template <int NS>
 __global__ void imaging_kernel(const ImagingArgs a) {
@@ -210,45 +221,45 @@ __global__ void imaging_kernel(const ImagingArgs a) {
         const int row = total <= 0xffffffffLL ? (int)((unsigned)q / (unsigned)per_row) : (int)(q / per_row);
         const int i0 = (int)(q - (long long)row * per_row) * 4;
         if (i0 >= a.nx) continue;
-        const int j = row % a.ny, k = row / a.ny;
-        const float eyj = __ldg(a.ey + j), ezk = __ldg(a.ez + k);
-        float4 ps[NS], u[NS + 2];
-#pragma unroll
-        for (int t = 0; t < NS; ++t) ps[t] = a.psi[t][q];
-#pragma unroll
-        for (int t = 0; t < NS + 2; ++t) u[t] = a.u[t][q];
-        const float4 cc = a.c[q];
-        float4 g = a.grad[q];
-        float e[4];
-#pragma unroll
-        for (int t = 0; t < 4; ++t) e[t] = __fadd_rn(__fadd_rn(__ldg(a.ex + min(i0 + t, a.nx - 1)), eyj), ezk);
+        float4 ps[NS], gg[NS];
 #pragma unroll
         for (int t = 0; t < NS; ++t) {
-            g.x = imaging_term(ps[t].x, u[t].x, u[t + 1].x, u[t + 2].x, cc.x, e[0], g.x);
-            g.y = imaging_term(ps[t].y, u[t].y, u[t + 1].y, u[t + 2].y, cc.y, e[1], g.y);
-            g.z = imaging_term(ps[t].z, u[t].z, u[t + 1].z, u[t + 2].z, cc.z, e[2], g.z);
-            g.w = imaging_term(ps[t].w, u[t].w, u[t + 1].w, u[t + 2].w, cc.w, e[3], g.w);
+            ps[t] = a.psi[t][q];
+            gg[t] = a.g[t][q];
+        }
+        float4 p = a.acc[q], c = a.comp[q];
+#pragma unroll
+        for (int t = 0; t < NS; ++t) {
+            dot2_step(ps[t].x, gg[t].x, p.x, c.x);
+            dot2_step(ps[t].y, gg[t].y, p.y, c.y);
+            dot2_step(ps[t].z, gg[t].z, p.z, c.z);
+            dot2_step(ps[t].w, gg[t].w, p.w, c.w);
         }
         if (i0 + 3 < a.nx) {
-            a.grad[q] = g;
+            a.acc[q] = p;
+            a.comp[q] = c;
         } else {   // the row's last group: keep the padding untouched
-            float *gp = reinterpret_cast<float *>(a.grad + q);
-            gp[0] = g.x;
-            if (i0 + 1 < a.nx) gp[1] = g.y;
-            if (i0 + 2 < a.nx) gp[2] = g.z;
+            float *pp = reinterpret_cast<float *>(a.acc + q), *cp = reinterpret_cast<float *>(a.comp + q);
+            pp[0] = p.x;
+            cp[0] = c.x;
+            if (i0 + 1 < a.nx) pp[1] = p.y, cp[1] = c.y;
+            if (i0 + 2 < a.nx) pp[2] = p.z, cp[2] = c.z;
         }
     }
 }
 
-// grad_v = 2 dt^2 v grad_c (c = dt^2 v^2), dense output.
-__global__ void grad_to_velocity_kernel(const float *__restrict__ gc, const float *__restrict__ vel, int nx,
-                                        int ny, int nz, int nxp, double dt, float *__restrict__ gv) {
+// grad_v = 2 (p + s) / v (p + s = sum_n psi^{n+1} g^n, c = dt^2 v^2), dense
+// output, FP32 (correctly rounded division).
+__global__ void grad_to_velocity_kernel(const float *__restrict__ acc, const float *__restrict__ comp,
+                                        const float *__restrict__ vel, int nx, int ny, int nz, int nxp,
+                                        float *__restrict__ gv) {
     const long long total = (long long)nx * ny * nz;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
          q += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(q % nx);
-        const long long row = q / nx;
-        gv[q] = (float)(2.0 * dt * dt * (double)vel[q] * (double)gc[row * nxp + i]);
+        const long long o = (q / nx) * nxp + i;
+        const float sum = __fadd_rn(acc[o], comp[o]);
+        gv[q] = __fdiv_rn(__fmul_rn(2.0f, sum), vel[q]);
     }
 }
 
@@ -283,17 +294,17 @@ cudaError_t launch_unreverse_transpose(const float *g, int nt, int ncol, double 
     return cudaGetLastError();
 }
 
-cudaError_t launch_imaging(int nsteps, const float *const *psi, const float *const *u, const float *c,
-                           const float *ex, const float *ey, const float *ez, int nx, int ny, int nz, int nxp,
-                           float *grad_c, cudaStream_t s) {
-    if (nsteps != 1 && nsteps != 2) return cudaErrorInvalidValue;
+cudaError_t launch_imaging(int nsteps, const float *const *psi, const float *const *g, int nx, int ny, int nz,
+                           int nxp, float *acc, float *comp, cudaStream_t s) {
+    if (nsteps < 1 || nsteps > 2) return cudaErrorInvalidValue;
     ImagingArgs a{};
-    for (int t = 0; t < nsteps; ++t) a.psi[t] = reinterpret_cast<const float4 *>(psi[t]);
-    for (int t = 0; t < nsteps + 2; ++t) a.u[t] = reinterpret_cast<const float4 *>(u[t]);
-    a.c = reinterpret_cast<const float4 *>(c);
-    a.ex = ex; a.ey = ey; a.ez = ez;
+    for (int t = 0; t < nsteps; ++t) {
+        a.psi[t] = reinterpret_cast<const float4 *>(psi[t]);
+        a.g[t] = reinterpret_cast<const float4 *>(g[t]);
+    }
     a.nx = nx; a.ny = ny; a.nz = nz; a.nxp = nxp;
-    a.grad = reinterpret_cast<float4 *>(grad_c);
+    a.acc = reinterpret_cast<float4 *>(acc);
+    a.comp = reinterpret_cast<float4 *>(comp);
     const long long groups = (long long)(nxp / 4) * ny * nz;
     const int grid = (int)std::min<long long>((groups + 255) / 256, 152LL * 8);
     if (nsteps == 1)
@@ -303,10 +314,9 @@ cudaError_t launch_imaging(int nsteps, const float *const *psi, const float *con
     return cudaGetLastError();
 }
 
-cudaError_t launch_grad_to_velocity(const float *grad_c, const float *vel, int nx, int ny, int nz, int nxp,
-                                    double dt, float *grad_v, cudaStream_t s) {
-    grad_to_velocity_kernel<<<grid2((long long)nx * ny * nz), 256, 0, s>>>(grad_c, vel, nx, ny, nz, nxp, dt,
-                                                                           grad_v);
+cudaError_t launch_grad_to_velocity(const float *acc, const float *comp, const float *vel, int nx, int ny, int nz,
+                                    int nxp, float *grad_v, cudaStream_t s) {
+    grad_to_velocity_kernel<<<grid2((long long)nx * ny * nz), 256, 0, s>>>(acc, comp, vel, nx, ny, nz, nxp, grad_v);
     return cudaGetLastError();
 }
 

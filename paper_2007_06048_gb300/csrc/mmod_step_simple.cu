@@ -42,12 +42,15 @@ __global__ void __launch_bounds__(128) step_simple_kernel(const StepArgs a) {
     const float e = __fadd_rn(__fadd_rn(__ldg(a.ex + i), __ldg(a.ey + j)), __ldg(a.ez + k));
     const float out = __fmul_rn(num_damped(two_p, a.uprev[o], __ldg(a.c + o), lap, e), damp_factor(e));
     a.uout[o] = (a.fs && k == 0) ? 0.0f : out;   // p = 0 on a free surface
+    if (a.gout) a.gout[o] = (a.fs && k == 0) ? 0.0f : lap;   // g^n = L u^n (sources: inject_kernel)
 }
 
 // Sources, after the step: one thread per injection point (stencil order).
 __global__ void inject_kernel(const StepArgs a) {
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < a.inj.npts; p += gridDim.x * blockDim.x)
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < a.inj.npts; p += gridDim.x * blockDim.x) {
         inject_point(a, p);
+        if (a.gout) inject_g_points(a, a.n, p, p + 1, 0, 1);
+    }
 }
 
 __global__ void gather_kernel(const float *__restrict__ u, const long long *__restrict__ off, int nrec,

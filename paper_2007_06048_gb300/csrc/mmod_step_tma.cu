@@ -130,10 +130,11 @@ __device__ __forceinline__ PlaneInfo plane_info(const StepArgs &a, int k) {
 
 // One z step computing plane z0 + t.  The queue window of this step is
 // q[J .. J+8] (planes k-4 .. k+4); the leading plane k+4 lands in q[J+8].
-template <class S, int J>
+template <class S, int J, bool G>
 __device__ __forceinline__ void step(const StepArgs &a, const Ctx &c, int t, float2 (&q)[S::QD][S::RY],
                                      const Wts &w, float2 exr, const float (&eyr)[S::RY], bool xy_damped,
-                                     const PlaneInfo &pi, float *const (&out_row)[S::RY]) {
+                                     const PlaneInfo &pi, float *const (&out_row)[S::RY],
+                                     float *const (&g_row)[S::RY]) {
     constexpr int RY = S::RY;
     const int k = c.z0 + t;
     // 1. the leading plane k+4 (sequence t+8) enters the queue
@@ -195,6 +196,16 @@ __device__ __forceinline__ void step(const StepArgs &a, const Ctx &c, int t, flo
             else
                 dst[0] = num.x;
         }
+        if constexpr (G) {   // g^n = L u^n (sources added after the z range), 0 on a free surface
+            if (g_row[r]) {
+                const float2 gv = (a.fs && k == 0) ? make_float2(0.0f, 0.0f) : lap;
+                float *dst = g_row[r] + koff;
+                if (c.x0 + 2 * c.lane + 1 < a.nx)
+                    *reinterpret_cast<float2 *>(dst) = gv;
+                else
+                    dst[0] = gv.x;
+            }
+        }
     }
 }
 
@@ -229,25 +240,25 @@ struct PdlDep {
 };
 
 // Persistent run: the 26 neighbouring units (x-y tiles and z ranges, with
-// diagonals: the u^n halo box touches all of them) must have completed step
-// n-1.  One thread polls each neighbour's counter (acquire, bounded by
-// kWaitNs; a give-up sets the abort flag and the error word).  The unit's
-// own u^{n-1} and c are its own earlier writes or constant, so they are
-// requested before the wait.  Barriers of an earlier unit are invalidated
-// and set up again.
+// diagonals: the u^n halo box touches all of them) and the unit itself must
+// have completed step n-1 (the unit's own u^n and u^{n-1} may have been
+// written by another CTA).  One thread polls each counter (acquire, bounded
+// by kWaitNs; a give-up sets the abort flag and the error word).  Nothing is
+// requested before the wait.  Barriers of an earlier unit are invalidated and
+// set up again.
 struct NeighborDep {
     const int *counters;
     int unit, n;
     Geom g;
     bool first;
     static constexpr bool kProxyFence = true;
-    __device__ bool early() const { return true; }
+    __device__ bool early() const { return false; }
     __device__ bool reinit() const { return !first; }
     __device__ void wait(int tid, int *abort_flag, int *err) const;
 };
 
 __device__ __noinline__ void NeighborDep::wait(int tid, int *abort_flag, int *err) const {
-    if (tid >= 27 || tid == 13) return;   // 13: the unit itself
+    if (tid >= 27) return;   // 27 units: the unit (13) and its neighbours
     int b = unit;
     const int tx = b % g.tiles_x;
     b /= g.tiles_x;
@@ -272,7 +283,7 @@ __device__ __noinline__ void NeighborDep::wait(int tid, int *abort_flag, int *er
 // shot).  The single-shot kernel passes its parameters; the batch kernel a
 // shot's arguments staged in shared memory and that shot's tensor maps in
 // global memory.
-template <class S, class Dep>
+template <class S, class Dep, bool G = false>
 __device__ __forceinline__ void step_tma_body(const StepArgs &a, const StepVar &v, const CUtensorMap *cur_map,
                                               const CUtensorMap *prev_map, const CUtensorMap *c_map, const Geom &g,
                                               int bid, int nbid, const Dep &dep) {
@@ -353,11 +364,13 @@ __device__ __forceinline__ void step_tma_body(const StepArgs &a, const StepVar &
     exr.y = x + 1 < a.nx ? __ldg(a.ex + x + 1) : 0.0f;
     float eyr[RY];
     float *out_row[RY];   // u^{n+1} row pointers at plane 0; null outside the grid
+    float *g_row[RY];     // the same rows of g^n (G only)
 #pragma unroll
     for (int r = 0; r < RY; ++r) {
         const int y = c.y0 + RY * c.warp + r;
         eyr[r] = y < a.ny ? __ldg(a.ey + y) : 0.0f;
         out_row[r] = (y < a.ny && x < a.nx) ? v.uout + (long long)y * a.nxp + x : nullptr;
+        g_row[r] = (G && y < a.ny && x < a.nx) ? a.gout + (long long)y * a.nxp + x : nullptr;
     }
     const bool xy_damped = c.x0 < a.nbl || c.x0 + TX - 1 > a.nx - 1 - a.nbl || c.y0 < a.nbl ||
                            c.y0 + S::TY - 1 > a.ny - 1 - a.nbl;
@@ -412,7 +425,7 @@ __device__ __forceinline__ void step_tma_body(const StepArgs &a, const StepVar &
 #define MMOD_STEP(J)                                                                        \
     if (t + (J) < T) {                                                                      \
         const PlaneInfo pi_next = plane_info(a, c.z0 + t + (J) + 1);                        \
-        step<S, (J)>(a, c, t + (J), q, w, exr, eyr, xy_damped, pi, out_row);               \
+        step<S, (J), G>(a, c, t + (J), q, w, exr, eyr, xy_damped, pi, out_row, g_row);     \
         pi = pi_next;                                                                       \
         __syncthreads();                                                                    \
         if (*c.abort_flag) break;                                                           \
@@ -446,6 +459,7 @@ __device__ __forceinline__ void step_tma_body(const StepArgs &a, const StepVar &
         const long long b = ((long long)(c.y0 / kInjTileY) * a.inj.tiles_x + c.x0 / kInjTileX) * a.nz + c.z0;
         const int lo = __ldg(a.inj.tile_start + b), hi = __ldg(a.inj.tile_start + b + T);
         inject_points(a, v.uout, v.n, lo, hi, tid, S::NT);
+        if constexpr (G) inject_g_points(a, v.n, lo, hi, tid, S::NT);
     }
     // After a give-up, wait (bounded) for the copies this CTA still has in
     // flight (the latest sequence of every slot) before its shared memory is
@@ -456,13 +470,69 @@ __device__ __forceinline__ void step_tma_body(const StepArgs &a, const StepVar &
     }
 }
 
-template <class S>
+// G: also write g^n = L u^n + s^n into a.gout (the gradient's imaging factor).
+template <class S, bool G = false>
 __global__ void __launch_bounds__(S::NT, S::MINB)
     step_tma_kernel(const StepArgs a, const __grid_constant__ CUtensorMap cur_map,
                     const __grid_constant__ CUtensorMap prev_map, const __grid_constant__ CUtensorMap c_map,
                     const Geom g) {
-    step_tma_body<S>(a, StepVar{a.n, a.uout, a.ucur, a.traces}, &cur_map, &prev_map, &c_map, g, blockIdx.x,
-                     gridDim.x, PdlDep{a.pdl});
+    step_tma_body<S, PdlDep, G>(a, StepVar{a.n, a.uout, a.ucur, a.traces}, &cur_map, &prev_map, &c_map, g,
+                                blockIdx.x, gridDim.x, PdlDep{a.pdl});
+}
+
+// Work-claiming step (StepArgs::claim set): at most one wave of CTAs covers
+// the grid's units (64 x TY tile x g.zlen planes).  CTA b serves unit b, then
+// claims the next unserved unit from the launch's counter (claim[0]) until
+// none is left, so a CTA that finishes early takes more work and every SM
+// keeps its CTAs busy until the last units; the units are independent within
+// a step (each reads u^n, its own u^{n-1} and c, and writes its own u^{n+1}),
+// so the order does not matter and the bits are those of the static plan.
+// Only a CTA's first unit waits for the previous step (PDL); later units
+// request their planes at once.  The last CTA to stop claiming (claim[1]
+// counts them) clears both counters for the next launch, which reads them
+// only after its own griddepcontrol.wait or stream order.
+struct ClaimDep {
+    int pdl;
+    bool first;
+    static constexpr bool kProxyFence = false;
+    __device__ bool early() const { return first ? pdl == 2 : true; }
+    __device__ bool reinit() const { return !first; }
+    __device__ void wait(int, int *, int *) const {
+        if (first && pdl) {
+            asm volatile("griddepcontrol.wait;" ::: "memory");
+            asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+        }
+    }
+};
+
+template <class S, bool G = false>
+__global__ void __launch_bounds__(S::NT, S::MINB2)
+    step_tma_claim_kernel(const StepArgs a, const __grid_constant__ CUtensorMap cur_map,
+                          const __grid_constant__ CUtensorMap prev_map, const __grid_constant__ CUtensorMap c_map,
+                          const Geom g, int units) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    // the body's abort flag and, next to it, the claimed unit
+    int *abort_flag = reinterpret_cast<int *>(smem + (S::NSU * S::CUR + S::NSC * 2 * S::PC) * 4 +
+                                              (S::NSU + S::NSC) * 8);
+    int *next = abort_flag + 1;
+    bool first = true;
+    for (int unit = blockIdx.x; unit < units;) {
+        step_tma_body<S, ClaimDep, G>(a, StepVar{a.n, a.uout, a.ucur, a.traces}, &cur_map, &prev_map, &c_map, g,
+                                      unit, units, ClaimDep{a.pdl, first});
+        first = false;
+        __syncthreads();
+        if (*abort_flag) break;   // the body drained its copies
+        if (threadIdx.x == 0) *next = (int)gridDim.x + atomicAdd(a.claim, 1);
+        __syncthreads();
+        unit = *next;
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(a.claim + 1, 1) == (int)gridDim.x - 1) {   // every CTA has stopped claiming
+            atomicExch(a.claim, 0);
+            atomicExch(a.claim + 1, 0);
+        }
+    }
 }
 
 // Batch: every shot of the batch advances one step in one launch.  CTA b
@@ -506,103 +576,123 @@ __global__ void __launch_bounds__(S::NT, S::MINB2)
                      &d->cmap, d->geom, __ldg(cta_local + blockIdx.x), d->nblocks, PdlDep{sa.pdl});
 }
 
-// Persistent run (PersistArgs): steps n0 .. n1-1 in one cooperative launch.
-// StepArgs stay in the kernel's constant parameters (a.pdl is ignored); the
-// step and the buffer roles go in a StepVar; each unit signals its counter
-// once its u^{n+1} (sources and receivers included) is complete.
+// Persistent run (PersistArgs): steps n0 .. n1-1 in one cooperative launch,
+// as a work list.  Item i is step n0 + i / units of unit i % units (step
+// major); CTAs claim items from pa.queue in that order, one at a time, so
+// every item before a claimed one is held by a resident CTA and the waits of
+// NeighborDep always end.  StepArgs stay in the kernel's constant parameters
+// (a.pdl is ignored); the step and the buffer roles go in a StepVar; each
+// unit signals its counter once its u^{n+1} (sources and receivers included)
+// is complete.
+__device__ __forceinline__ unsigned long long *claimed_item(unsigned char *smem_reserved) {
+    return reinterpret_cast<unsigned long long *>(smem_reserved + 8);   // next to the abort flag
+}
+
 template <class S>
 __global__ void __launch_bounds__(S::NT, S::MINB2)
     step_tma_persistent_kernel(const StepArgs a, const __grid_constant__ TmaMaps maps, const Geom g,
                                const PersistArgs pa) {
     extern __shared__ __align__(128) unsigned char smem[];
-    const int *abort_flag = reinterpret_cast<const int *>(smem + (S::NSU * S::CUR + S::NSC * 2 * S::PC) * 4 +
-                                                          (S::NSU + S::NSC) * 8);
+    unsigned char *reserved = smem + (S::NSU * S::CUR + S::NSC * 2 * S::PC) * 4 + (S::NSU + S::NSC) * 8;
+    const int *abort_flag = reinterpret_cast<const int *>(reserved);
+    unsigned long long *claimed = claimed_item(reserved);
+    const unsigned long long total = (unsigned long long)(pa.n1 - pa.n0) * pa.units;
     bool first = true;
-    for (int n = pa.n0; n < pa.n1; ++n) {
+    for (;;) {
+        __syncthreads();   // every thread has read the previous claim
+        if (threadIdx.x == 0) *claimed = atomicAdd(pa.queue, 1ULL);
+        __syncthreads();
+        const unsigned long long item = *claimed;
+        if (item >= total) break;
+        const int n = pa.n0 + (int)(item / pa.units), unit = (int)(item % pa.units);
         float *uout = pa.u[n & 1];
-        for (int unit = blockIdx.x; unit < pa.units; unit += gridDim.x) {
-            step_tma_body<S>(a, StepVar{n, uout, nullptr, nullptr}, &maps.cur[(n + 1) & 1], &maps.prev[n & 1],
-                             &maps.c, g, unit, pa.units, NeighborDep{pa.counters, unit, n, g, first});
-            first = false;
-            __syncthreads();
-            if (*abort_flag) return;   // the body drained its copies; waiters give up on the error word
-            // receivers of this unit: u^{n+1} after its sources
-            if (pa.traces && pa.nrec > 0) {
-                int b = unit;
-                const int tx = b % g.tiles_x;
-                b /= g.tiles_x;
-                const int ty = b % g.tiles_y;
-                const int z0 = (b / g.tiles_y) * g.zlen;
-                const int T = min(a.nz - z0, g.zlen);
-                const long long q = ((long long)ty * g.tiles_x + tx) * a.nz + z0;
-                const int lo = __ldg(pa.rec_start + q), hi = __ldg(pa.rec_start + q + T);
-                float *row = pa.traces + (long long)n * pa.nrec;
-                for (int p = lo + threadIdx.x; p < hi; p += blockDim.x)
-                    row[__ldg(pa.rec_idx + p)] = uout[__ldg(pa.rec_off + p)];
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                fence_proxy_async_global();
-                __threadfence();
-                st_release_gpu(pa.counters + unit, n + 1);
-            }
+        step_tma_body<S>(a, StepVar{n, uout, nullptr, nullptr}, &maps.cur[(n + 1) & 1], &maps.prev[n & 1], &maps.c,
+                         g, unit, pa.units, NeighborDep{pa.counters, unit, n, g, first});
+        first = false;
+        __syncthreads();
+        if (*abort_flag) return;   // the body drained its copies; waiters give up on the error word
+        // receivers of this unit: u^{n+1} after its sources
+        if (pa.traces && pa.nrec > 0) {
+            int b = unit;
+            const int tx = b % g.tiles_x;
+            b /= g.tiles_x;
+            const int ty = b % g.tiles_y;
+            const int z0 = (b / g.tiles_y) * g.zlen;
+            const int T = min(a.nz - z0, g.zlen);
+            const long long q = ((long long)ty * g.tiles_x + tx) * a.nz + z0;
+            const int lo = __ldg(pa.rec_start + q), hi = __ldg(pa.rec_start + q + T);
+            float *row = pa.traces + (long long)n * pa.nrec;
+            for (int p = lo + threadIdx.x; p < hi; p += blockDim.x)
+                row[__ldg(pa.rec_idx + p)] = uout[__ldg(pa.rec_off + p)];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            fence_proxy_async_global();
+            __threadfence();
+            st_release_gpu(pa.counters + unit, n + 1);
         }
     }
 }
 
-// Persistent batch run: every shot's time loop in one cooperative launch.
-// Unit u (the batch decomposition: shot unit_shot[u], block unit_local[u])
-// is always served by CTA u mod gridDim.x, so its own u^{n-1} are its own
-// earlier writes; it starts step n when the 26 neighbouring units of its
-// shot have completed step n-1 (bounded polls), then records its receivers
-// and signals its counter.  The shot's arguments are staged in shared
-// memory per unit, as in the one-launch-per-step batch kernel.
+// Persistent batch run: every shot's time loop in one cooperative launch,
+// as a work list over all shots' units (the batch decomposition: unit u is
+// shot unit_shot[u], block unit_local[u]).  Item i is step n0 + i / units of
+// unit i % units; CTAs claim items in that order from pa.queue, one at a
+// time, wait until the unit and its 26 neighbours of the same shot have
+// completed step n-1 (bounded polls), run the step, record the unit's
+// receivers and signal its counter.  The shot's arguments are staged in
+// shared memory per item, as in the one-launch-per-step batch kernel.
 template <class S>
 __global__ void __launch_bounds__(S::NT, S::MINB2)
     step_tma_batch_persistent_kernel(const ShotDesc *__restrict__ shots, const BatchPersistArgs pa) {
     extern __shared__ __align__(128) unsigned char smem[];
     StepArgs &sa = *reinterpret_cast<StepArgs *>(smem + batch_args_offset<S>());
-    const int *abort_flag = reinterpret_cast<const int *>(smem + (S::NSU * S::CUR + S::NSC * 2 * S::PC) * 4 +
-                                                          (S::NSU + S::NSC) * 8);
+    unsigned char *reserved = smem + (S::NSU * S::CUR + S::NSC * 2 * S::PC) * 4 + (S::NSU + S::NSC) * 8;
+    const int *abort_flag = reinterpret_cast<const int *>(reserved);
+    unsigned long long *claimed = claimed_item(reserved);
+    const unsigned long long total = (unsigned long long)(pa.n1 - pa.n0) * pa.units;
     bool first = true;
-    for (int n = pa.n0; n < pa.n1; ++n) {
-        for (int unit = blockIdx.x; unit < pa.units; unit += gridDim.x) {
-            const int shot = __ldg(pa.unit_shot + unit), local = __ldg(pa.unit_local + unit);
-            const ShotDesc *d = shots + shot;
-            __syncthreads();   // the previous unit is done with the staged arguments
-            {
-                const int *src = reinterpret_cast<const int *>(&d->args);
-                int *dst = reinterpret_cast<int *>(&sa);
-                for (int i = threadIdx.x; i < (int)(sizeof(StepArgs) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
-            }
-            __syncthreads();
-            float *uout = d->u[n & 1];
-            int *counters = pa.counters + __ldg(pa.counter_base + shot);
-            step_tma_body<S>(sa, StepVar{n, uout, nullptr, nullptr}, &d->cur[(n + 1) & 1], &d->prev[n & 1], &d->cmap,
-                             d->geom, local, d->nblocks, NeighborDep{counters, local, n, d->geom, first});
-            first = false;
-            __syncthreads();
-            if (*abort_flag) return;   // the body drained its copies; waiters give up on the error word
-            // receivers of this unit: u^{n+1} after its sources
-            if (d->traces && sa.nrec > 0) {
-                int b = local;
-                const int tx = b % d->geom.tiles_x;
-                b /= d->geom.tiles_x;
-                const int ty = b % d->geom.tiles_y;
-                const int z0 = (b / d->geom.tiles_y) * d->geom.zlen;
-                const int T = min(sa.nz - z0, d->geom.zlen);
-                const long long q = ((long long)ty * d->geom.tiles_x + tx) * sa.nz + z0;
-                const int lo = __ldg(d->rec_start + q), hi = __ldg(d->rec_start + q + T);
-                float *row = d->traces + (long long)n * sa.nrec;
-                for (int p = lo + threadIdx.x; p < hi; p += blockDim.x)
-                    row[__ldg(d->rec_idx + p)] = uout[__ldg(d->rec_boff + p)];
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                fence_proxy_async_global();
-                __threadfence();
-                st_release_gpu(counters + local, n + 1);
-            }
+    for (;;) {
+        __syncthreads();   // the previous item is done with the staged arguments and the claim
+        if (threadIdx.x == 0) *claimed = atomicAdd(pa.queue, 1ULL);
+        __syncthreads();
+        const unsigned long long item = *claimed;
+        if (item >= total) break;
+        const int n = pa.n0 + (int)(item / pa.units), unit = (int)(item % pa.units);
+        const int shot = __ldg(pa.unit_shot + unit), local = __ldg(pa.unit_local + unit);
+        const ShotDesc *d = shots + shot;
+        {
+            const int *src = reinterpret_cast<const int *>(&d->args);
+            int *dst = reinterpret_cast<int *>(&sa);
+            for (int i = threadIdx.x; i < (int)(sizeof(StepArgs) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+        }
+        __syncthreads();
+        float *uout = d->u[n & 1];
+        int *counters = pa.counters + __ldg(pa.counter_base + shot);
+        step_tma_body<S>(sa, StepVar{n, uout, nullptr, nullptr}, &d->cur[(n + 1) & 1], &d->prev[n & 1], &d->cmap,
+                         d->geom, local, d->nblocks, NeighborDep{counters, local, n, d->geom, first});
+        first = false;
+        __syncthreads();
+        if (*abort_flag) return;   // the body drained its copies; waiters give up on the error word
+        // receivers of this unit: u^{n+1} after its sources
+        if (d->traces && sa.nrec > 0) {
+            int b = local;
+            const int tx = b % d->geom.tiles_x;
+            b /= d->geom.tiles_x;
+            const int ty = b % d->geom.tiles_y;
+            const int z0 = (b / d->geom.tiles_y) * d->geom.zlen;
+            const int T = min(sa.nz - z0, d->geom.zlen);
+            const long long q = ((long long)ty * d->geom.tiles_x + tx) * sa.nz + z0;
+            const int lo = __ldg(d->rec_start + q), hi = __ldg(d->rec_start + q + T);
+            float *row = d->traces + (long long)n * sa.nrec;
+            for (int p = lo + threadIdx.x; p < hi; p += blockDim.x)
+                row[__ldg(d->rec_idx + p)] = uout[__ldg(d->rec_boff + p)];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            fence_proxy_async_global();
+            __threadfence();
+            st_release_gpu(counters + local, n + 1);
         }
     }
 }
@@ -652,30 +742,34 @@ using V24_2s = Shape<kTY, 4, 2, 6, 2>;
 using V22_4s = Shape<kTY, 2, 4, 6, 2>;
 using V22_4s3 = Shape<kTY, 2, 4, 6, 2, 3>;
 using V22_2s3 = Shape<kTY, 2, 2, 6, 2, 3>;
+static_assert(kTmaGVariant == 2, "the g^n forms are compiled for V22_4, variant 2");
 
 struct Variant {
     const char *name;
     const void *fn;
     const void *batch_fn;
     const void *persist_fn;   // null: no persistent form compiled
+    const void *claim_fn;     // null: no work-claiming form compiled
     int nt, smem, batch_smem;
 };
 
-#define MMOD_VARIANT(V, desc, P) \
-    {desc, (const void *)step_tma_kernel<V>, (const void *)step_tma_batch_kernel<V>, P, V::NT, V::SMEM, \
+#define MMOD_VARIANT(V, desc, P, C) \
+    {desc, (const void *)step_tma_kernel<V>, (const void *)step_tma_batch_kernel<V>, P, C, V::NT, V::SMEM, \
      batch_smem<V>()}
 const Variant kVariants[] = {
-    MMOD_VARIANT(V22_1, "64x16 tile, 2x2 points/thread, z unroll 1", nullptr),
-    MMOD_VARIANT(V22_2, "64x16 tile, 2x2 points/thread, z unroll 2", nullptr),
+    MMOD_VARIANT(V22_1, "64x16 tile, 2x2 points/thread, z unroll 1", nullptr, nullptr),
+    MMOD_VARIANT(V22_2, "64x16 tile, 2x2 points/thread, z unroll 2", nullptr,
+                 (const void *)step_tma_claim_kernel<V22_2>),
     MMOD_VARIANT(V22_4, "64x16 tile, 2x2 points/thread, z unroll 4",
-                 (const void *)step_tma_persistent_kernel<V22_4>),
-    MMOD_VARIANT(V24_1, "64x16 tile, 2x4 points/thread, z unroll 1", nullptr),
-    MMOD_VARIANT(V24_2, "64x16 tile, 2x4 points/thread, z unroll 2", nullptr),
+                 (const void *)step_tma_persistent_kernel<V22_4>, (const void *)step_tma_claim_kernel<V22_4>),
+    MMOD_VARIANT(V24_1, "64x16 tile, 2x4 points/thread, z unroll 1", nullptr, nullptr),
+    MMOD_VARIANT(V24_2, "64x16 tile, 2x4 points/thread, z unroll 2", nullptr, nullptr),
     MMOD_VARIANT(V24_2s, "64x16 tile, 2x4 points/thread, z unroll 2, shallow rings",
-                 (const void *)step_tma_persistent_kernel<V24_2s>),
-    MMOD_VARIANT(V22_4s, "64x16 tile, 2x2 points/thread, z unroll 4, shallow rings", nullptr),
-    MMOD_VARIANT(V22_4s3, "64x16 tile, 2x2 points/thread, z unroll 4, shallow rings, 3 CTAs/SM", nullptr),
-    MMOD_VARIANT(V22_2s3, "64x16 tile, 2x2 points/thread, z unroll 2, shallow rings, 3 CTAs/SM", nullptr),
+                 (const void *)step_tma_persistent_kernel<V24_2s>, nullptr),
+    MMOD_VARIANT(V22_4s, "64x16 tile, 2x2 points/thread, z unroll 4, shallow rings", nullptr,
+                 (const void *)step_tma_claim_kernel<V22_4s>),
+    MMOD_VARIANT(V22_4s3, "64x16 tile, 2x2 points/thread, z unroll 4, shallow rings, 3 CTAs/SM", nullptr, nullptr),
+    MMOD_VARIANT(V22_2s3, "64x16 tile, 2x2 points/thread, z unroll 2, shallow rings, 3 CTAs/SM", nullptr, nullptr),
 };
 #undef MMOD_VARIANT
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
@@ -715,10 +809,21 @@ bool make_tma_plan(const mmod_config &cfg, int nxp, float *const u[2], const flo
         int occ = 0;
         if (cudaFuncSetAttribute(var.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, var.smem) != cudaSuccess ||
             cudaFuncSetAttribute(var.batch_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, var.batch_smem) != cudaSuccess ||
+            (var.claim_fn &&
+             cudaFuncSetAttribute(var.claim_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, var.smem) !=
+                 cudaSuccess) ||
             (var.persist_fn &&
              cudaFuncSetAttribute(var.persist_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, var.smem) !=
                  cudaSuccess) ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, var.fn, var.nt, var.smem) != cudaSuccess || occ < 1) {
+            cudaGetLastError();
+            return false;
+        }
+        if (v == kTmaGVariant &&
+            (cudaFuncSetAttribute((const void *)step_tma_kernel<V22_4, true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, var.smem) != cudaSuccess ||
+             cudaFuncSetAttribute((const void *)step_tma_claim_kernel<V22_4, true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, var.smem) != cudaSuccess)) {
             cudaGetLastError();
             return false;
         }
@@ -748,12 +853,70 @@ bool make_tma_plan(const mmod_config &cfg, int nxp, float *const u[2], const flo
         p.block = var.nt;
         p.smem = var.smem;
         p.occupancy = occ;
+        p.slots = (int)std::min<long long>(slots, 1LL << 30);
+        p.claim = 0;
     }
+    return true;
+}
+
+bool claim_geom(const TmaPlan &plan, int nz, Geom *g, int *units, int *grid) {
+    if (plan.claim <= 0 || plan.variant < 0 || plan.variant >= kNumVariants || !kVariants[plan.variant].claim_fn ||
+        plan.slots < 1 || nz < 1)
+        return false;
+    const int zlen = std::min(plan.claim, nz);
+    *g = Geom{plan.tiles_x, plan.tiles_y, (nz + zlen - 1) / zlen, zlen};
+    const long long u = (long long)g->tiles_x * g->tiles_y * g->zchunks;
+    if (u > (1LL << 30)) return false;
+    *units = (int)u;
+    *grid = (int)std::min<long long>(u, plan.slots);
     return true;
 }
 
 cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap *cur_map, const CUtensorMap *prev_map,
                             const CUtensorMap *c_map, const TmaPlan &plan, cudaStream_t s) {
+    Geom cg;
+    int units = 0, cgrid = 0;
+    const bool claim = a.claim && claim_geom(plan, a.nz, &cg, &units, &cgrid);
+    if (a.gout) {   // g^n as well: variant 2 only (the caller passes its plan)
+        if (plan.variant != kTmaGVariant) return cudaErrorInvalidValue;
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3(claim ? cgrid : plan.grid);
+        lc.blockDim = dim3(plan.block);
+        lc.dynamicSmemBytes = plan.smem;
+        lc.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        lc.attrs = attr;
+        lc.numAttrs = a.pdl ? 1 : 0;
+        const Geom g{plan.tiles_x, plan.tiles_y, plan.zchunks, plan.zlen};
+        const cudaError_t e =
+            claim ? cudaLaunchKernelEx(&lc, step_tma_claim_kernel<V22_4, true>, a, *cur_map, *prev_map, *c_map, cg, units)
+                  : cudaLaunchKernelEx(&lc, step_tma_kernel<V22_4, true>, a, *cur_map, *prev_map, *c_map, g);
+        if (e != cudaSuccess) return e;
+        return cudaGetLastError();
+    }
+    if (claim) {
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3(cgrid);
+        lc.blockDim = dim3(plan.block);
+        lc.dynamicSmemBytes = plan.smem;
+        lc.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        lc.attrs = attr;
+        lc.numAttrs = a.pdl ? 1 : 0;
+        cudaError_t e;
+        switch (plan.variant) {
+            case 1: e = cudaLaunchKernelEx(&lc, step_tma_claim_kernel<V22_2>, a, *cur_map, *prev_map, *c_map, cg, units); break;
+            case 2: e = cudaLaunchKernelEx(&lc, step_tma_claim_kernel<V22_4>, a, *cur_map, *prev_map, *c_map, cg, units); break;
+            case 6: e = cudaLaunchKernelEx(&lc, step_tma_claim_kernel<V22_4s>, a, *cur_map, *prev_map, *c_map, cg, units); break;
+            default: return cudaErrorInvalidValue;
+        }
+        if (e != cudaSuccess) return e;
+        return cudaGetLastError();
+    }
     const Geom g{plan.tiles_x, plan.tiles_y, plan.zchunks, plan.zlen};
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3(plan.grid);

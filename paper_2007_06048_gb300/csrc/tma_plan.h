@@ -10,6 +10,8 @@ constexpr int kMaxTmaVariants = 12;
 // Variant used unless a handle selects another: the fastest measured on the
 // 240^3 workload (64x16 tile, 2x2 points per thread, z unroll 4).
 constexpr int kTmaDefaultVariant = 2;
+// The variant whose step kernels can also write g^n = L u^n + s^n (StepArgs::gout).
+constexpr int kTmaGVariant = 2;
 
 struct TmaPlan {
     int variant = 0;                // index into the compiled variants
@@ -20,7 +22,14 @@ struct TmaPlan {
     int block = 0;                  // threads per CTA
     int smem = 0;                   // dynamic shared memory per CTA, bytes
     int occupancy = 0;              // resident CTAs per SM
+    int slots = 0;                  // resident CTAs on the device (SMs x occupancy)
+    int claim = 0;                  // > 0: work-claiming launch with units of this many planes
 };
+
+struct Geom;
+// Units and grid of a work-claiming launch of plan (false: the plan's variant
+// has no work-claiming form or claim is off).
+bool claim_geom(const TmaPlan &plan, int nz, Geom *g, int *units, int *grid);
 
 int tma_variant_count();
 const char *tma_variant_name(int v);

@@ -3,13 +3,14 @@
 Tolerances (relative L2 over the whole array, FP64 norms):
   adjoint source (transpose of the forward map), <= 100 steps: 1e-5, as the
   forward parity gate (the adjoint runs the same FP32 step kernels);
-  gradient, FP32 checkpoints: 1e-4 — the imaging condition subtracts nearly
-  equal FP32 wavefields (D u^{n+1} - 2 u^n + E u^{n-1}), which costs about
-  two decimal digits against the oracle's L u^n + s^n; the measured error
-  is reported by test_gradient_checkpoint_precision;
+  gradient, FP32 checkpoints, <= 100 steps: 1e-5, the forward gate (the
+  imaging factor g^n = L u^n + s^n comes from the step kernel's own FP32
+  Laplacian, so no difference of nearly equal wavefields is formed);
   16-bit checkpoints: the replayed forward starts from rounded states, so the
   gradient moves by ~ the storage precision (BF16 8 bits, FP16 11 bits of
-  mantissa after per-plane scaling): gates 2e-2 (BF16) and 3e-3 (FP16).
+  mantissa after per-plane scaling, BFP16 15 bits below each 32-value
+  block's maximum) times the stencil's amplification of grid-scale noise:
+  gates 2e-2 (BF16), 3e-3 (FP16) and 1e-3 (BFP16) on this 30 Hz case.
 Dot-product test: <F w, r> = <w, F^T r> with FP32 operators and FP64 sums
 (mmod_dot) to 1e-6 relative.
 """
@@ -128,7 +129,9 @@ def test_gradient_fp32_checkpoints_matches_oracle(grad_ref):
     p, resid, g_o = grad_ref
     g = _gpu_gradient(p, resid, 8, M.CKPT_FP32)
     assert np.abs(g_o).max() > 0
-    assert rel_l2(g, g_o) <= 1e-4
+    err = rel_l2(g, g_o)
+    print(f"FP32 checkpoints: gradient rel L2 vs FP64 oracle {err:.3e}")
+    assert err <= 1e-5
 
 
 def test_gradient_fp32_is_independent_of_the_checkpoint_count(grad_ref):
@@ -138,7 +141,7 @@ def test_gradient_fp32_is_independent_of_the_checkpoint_count(grad_ref):
         assert np.array_equal(_gpu_gradient(p, resid, ck, M.CKPT_FP32), ref), ck
 
 
-@pytest.mark.parametrize("dtype,gate", [(M.CKPT_BF16, 2e-2), (M.CKPT_FP16, 3e-3)])
+@pytest.mark.parametrize("dtype,gate", [(M.CKPT_BF16, 2e-2), (M.CKPT_FP16, 3e-3), (M.CKPT_BFP16, 1e-3)])
 def test_gradient_checkpoint_precision(grad_ref, dtype, gate):
     p, resid, g_o = grad_ref
     g = _gpu_gradient(p, resid, 8, dtype)
@@ -153,7 +156,8 @@ def test_gradient_memory_accounting():
     prop = M.Propagator.from_problem(p)
     m32 = prop.gradient_memory(10, M.CKPT_FP32)
     m16 = prop.gradient_memory(10, M.CKPT_BF16)
-    assert 0 < m16 < m32
+    mb = prop.gradient_memory(10, M.CKPT_BFP16)
+    assert 0 < m16 < mb < m32
     torch.cuda.synchronize()
 
 
@@ -165,7 +169,7 @@ def test_gradient_revolve_fp32_matches_segments_bitwise(grad_ref):
         assert np.array_equal(_gpu_gradient(p, resid, ck, M.CKPT_FP32, M.SCHEME_REVOLVE), ref), ck
 
 
-@pytest.mark.parametrize("dtype,gate", [(M.CKPT_BF16, 2e-2), (M.CKPT_FP16, 3e-3)])
+@pytest.mark.parametrize("dtype,gate", [(M.CKPT_BF16, 2e-2), (M.CKPT_FP16, 3e-3), (M.CKPT_BFP16, 1e-3)])
 def test_gradient_revolve_16bit_checkpoints(grad_ref, dtype, gate):
     p, resid, g_o = grad_ref
     g = _gpu_gradient(p, resid, 4, dtype, M.SCHEME_REVOLVE)
@@ -201,7 +205,7 @@ def test_autograd_function_matches_gradient_and_adjoint(grad_ref):
     assert np.array_equal(wav.grad.cpu().numpy(), a_ref)
 
 
-@pytest.mark.parametrize("dtype,gate", [(M.CKPT_BF16, 2e-2), (M.CKPT_FP16, 3e-3)])
+@pytest.mark.parametrize("dtype,gate", [(M.CKPT_BF16, 2e-2), (M.CKPT_FP16, 3e-3), (M.CKPT_BFP16, 1e-3)])
 def test_gradient_16bit_checkpoints_with_quiet_planes(dtype, gate):
     """A deep grid run for few steps: far planes hold only zeros and the
     wave's leading edge only FP32 subnormals, so a checkpoint plane's scale

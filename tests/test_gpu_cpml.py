@@ -23,8 +23,11 @@ def trace_err(tr_g, tr_o, u_o):
     return float(np.linalg.norm(tr_g.astype(np.float64) - tr_o) / max(np.linalg.norm(tr_o), floor))
 
 
+# the layer passes work on ranges along each axis: 26-cell x layers take the
+# line march (wider than a warp segment), 18 points with 8-cell layers merge
+# both x ranges into one, 18-cell layers leave a 4-cell gap
 CASES = [((40, 36, 70), 6, False), ((33, 64, 131), 8, False), ((9, 20, 9), 2, False), ((30, 28, 70), 5, True),
-         ((64, 20, 40), 0, False)]
+         ((64, 20, 40), 0, False), ((60, 60, 70), 26, False), ((30, 40, 18), 8, False), ((36, 40, 40), 18, True)]
 
 
 @pytest.mark.parametrize("shape,nbl,fs", CASES, ids=[f"{s}-L{n}-fs{int(f)}" for s, n, f in CASES])
@@ -74,8 +77,8 @@ def test_cpml_interior_tiles_bitwise(orc, fs):
 
 @pytest.mark.parametrize("fs", [False, True])
 def test_cpml_planes_per_thread_keep_bits(fs):
-    """MMOD_OPT_CPML_PLANES only regroups the layer passes' work (z ranges of
-    1 to 100 planes per thread, slabs of 8 and 193 planes): the same bits."""
+    """MMOD_OPT_CPML_PLANES only regroups the layer passes' work (1 to 100
+    layer lines per thread or row segments per warp): the same bits."""
     p = _cpml(W.tiny_problem(shape=(70, 45, 209), nt=30, nbl=8, nsrc=2, nrec=20, seed=14), fs=fs)
     tr_d, u_d, _ = run_gpu(p)
     for planes in (1, 3, 7, 100):

@@ -123,7 +123,9 @@ def test_free_surface_adjoint_and_gradient(orc):
     g_o = orc.gradient(p.vel, p.h, p.dt, p.nt, nbl=p.nbl, src_ijk=p.src_ijk, wavelet=p.wavelet,
                        rec_ijk=p.rec_ijk, resid=resid, free_surface=True)
     torch.cuda.synchronize()
-    assert rel_l2(g.cpu().numpy(), g_o) <= 1e-4
+    err = rel_l2(g.cpu().numpy(), g_o)
+    print(f"free surface, FP32 checkpoints: gradient rel L2 vs FP64 oracle {err:.3e}")
+    assert err <= 1e-5
     assert not np.any(g.cpu().numpy()[0])
 
 

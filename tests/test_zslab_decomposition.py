@@ -81,7 +81,7 @@ def _worker(rank, world, port, out):
 
 
 def test_two_z_slabs_equal_one_domain_bit_for_bit(orc):
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()   # the oracle fixture has started OpenMP threads
     out = mgr.dict()
     mp.start_processes(_worker, args=(2, _free_port(), out), nprocs=2, join=True, start_method="spawn")
     p = _problem()
