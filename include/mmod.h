@@ -156,9 +156,7 @@ enum { MMOD_CKPT_FP32 = 0, MMOD_CKPT_BF16 = 1, MMOD_CKPT_FP16 = 2, MMOD_CKPT_BFP
  * [nz][ny][nx] (FP32, dJ/dv in J-units per m/s):
  *   dJ/dv = 2 dt^2 v sum_n mu^{n+1} (L u^n + s^n) = (2 / v) sum_n psi^{n+1} g^n,
  * mu = psi / c the adjoint state (zero-lag imaging condition), g^n = L u^n +
- * s^n written by the step kernel that advances u^n (FP32); the sum over n is
- * a compensated FP32 sum (the accurate dot product "Dot2" of Ogita, Rump and
- * Oishi, 2005), the final scaling FP32.  The forward states are recomputed from
+ * s^n written by the step kernel that advances u^n; all of it FP32.  The forward states are recomputed from
  * ckpt_count checkpoints, by the handle's scheme (mmod_set_option
  * MMOD_OPT_CKPT_SCHEME):
  *   MMOD_SCHEME_SEGMENTS (default): the run is cut into ckpt_count segments;
@@ -276,7 +274,7 @@ mmod_status mmod_set_tma_variant(mmod_handle *h, int v);
  *   MMOD_OPT_ZLEN         >= 0: planes per z range of a CTA (0 = the plan's
  *                         choice, which fills one wave of resident CTAs; in a
  *                         batch created after it is set: the shot's z ranges,
- *                         at least 4 planes, 0 = 96); the same bits for any
+ *                         at least 4 planes, 0 = 256); the same bits for any
  *                         value;
  *   MMOD_OPT_PERSISTENT_CTAS  >= 0: at most this many CTAs for the persistent
  *                         run (0 = as many as fit at once; a small value makes

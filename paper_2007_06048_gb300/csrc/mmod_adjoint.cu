@@ -12,9 +12,8 @@
 // adjoint source is a[s][n] = psi^{n+1}(x_s) / (hx hy hz).
 //
 // Gradient.  dJ/dc(x) = sum_n mu^{n+1}(x) g^n(x), g^n = L u^n + s^n, so
-// with mu = psi / c the kernels accumulate A = sum_n psi^{n+1} g^n (a
-// compensated FP32 sum, see the imaging kernel) and dJ/dv = 2 dt^2 v A / c =
-// 2 A / v.  g^n is written by the step kernel that
+// with mu = psi / c the kernels accumulate A = sum_n psi^{n+1} g^n (FP32)
+// and dJ/dv = 2 dt^2 v A / c = 2 A / v.  g^n is written by the step kernel that
 // advances u^n (the Laplacian it already holds, plus w[n] / (hx hy hz) at the
 // sources): no difference of nearly equal wavefields is formed.  The forward
 // states are recovered from checkpoints (u^{a-1}, u^a) (FP32, or BF16 / FP16
@@ -192,7 +191,6 @@ mmod_status ensure_grad_work(mmod_handle *h, int nslot, int nwork, int dtype) {
             return fail(h, MMOD_ERR_CUDA, "tensor map encoding failed for an adjoint buffer");
     }
     MMOD_CK(h, cudaMalloc(&gw.gradc, vb));
-    MMOD_CK(h, cudaMalloc(&gw.gcomp, vb));
     gw.ckpt_bytes = (size_t)nslot * 2 * (size_t)h->vol * ckpt_elem_bytes(dtype);
     if (nslot > 0) MMOD_CK(h, cudaMalloc(&gw.ckpt, gw.ckpt_bytes));
     if (nslot > 0 && dtype != MMOD_CKPT_FP32)
@@ -255,8 +253,6 @@ void free_grad_work(mmod_handle *h) {
         p = nullptr;
     }
     if (gw.gradc) cudaFree(gw.gradc);
-    if (gw.gcomp) cudaFree(gw.gcomp);
-    gw.gcomp = nullptr;
     if (gw.ckpt) cudaFree(gw.ckpt);
     if (gw.ckpt_scale) cudaFree(gw.ckpt_scale);
     gw.gradc = nullptr;
@@ -393,7 +389,7 @@ MMOD_API mmod_status mmod_gradient(mmod_handle *h, const float *wavelet, const f
         const int m = nt - 1 - n;
         const float *ps[2] = {gw.psi[m & 1], gw.psi[(m + 1) & 1]};
         ++launches;
-        return launch_imaging(ns, ps, g, c.nx, c.ny, c.nz, h->nxp, gw.gradc, gw.gcomp, s);
+        return launch_imaging(ns, ps, g, c.nx, c.ny, c.nz, h->nxp, gw.gradc, s);
     };
     // steps hi down to lo with g^j in gof(j): two adjoint steps, then one
     // imaging pass over both (the same accumulation order as one pass per
@@ -425,7 +421,6 @@ MMOD_API mmod_status mmod_gradient(mmod_handle *h, const float *wavelet, const f
         MMOD_CK(h, cudaMemsetAsync(gw.psi[0], 0, vb, s));
         MMOD_CK(h, cudaMemsetAsync(gw.psi[1], 0, vb, s));
         MMOD_CK(h, cudaMemsetAsync(gw.gradc, 0, vb, s));
-        MMOD_CK(h, cudaMemsetAsync(gw.gcomp, 0, vb, s));
         MMOD_CK(h, backward_range(nt - 1, 0, [&](int j) { return gw.seg[2 + j]; }));
     } else if (h->ckpt_scheme == MMOD_SCHEME_REVOLVE) {
         std::vector<RevAction> sched;
@@ -433,7 +428,6 @@ MMOD_API mmod_status mmod_gradient(mmod_handle *h, const float *wavelet, const f
         MMOD_CK(h, cudaMemsetAsync(gw.psi[0], 0, vb, s));
         MMOD_CK(h, cudaMemsetAsync(gw.psi[1], 0, vb, s));
         MMOD_CK(h, cudaMemsetAsync(gw.gradc, 0, vb, s));
-        MMOD_CK(h, cudaMemsetAsync(gw.gcomp, 0, vb, s));
         float *unext = gw.seg[0], *gn = gw.seg[1];
         for (const RevAction &act : sched) {
             switch (act.kind) {
@@ -488,7 +482,6 @@ MMOD_API mmod_status mmod_gradient(mmod_handle *h, const float *wavelet, const f
         MMOD_CK(h, cudaMemsetAsync(gw.psi[0], 0, vb, s));
         MMOD_CK(h, cudaMemsetAsync(gw.psi[1], 0, vb, s));
         MMOD_CK(h, cudaMemsetAsync(gw.gradc, 0, vb, s));
-        MMOD_CK(h, cudaMemsetAsync(gw.gcomp, 0, vb, s));
         for (int sg = nseg - 1; sg >= 0; --sg) {
             const int a0 = sg * seglen, b0 = std::min(nt, a0 + seglen);
             MMOD_CK(h, restore_volume(h, 2 * sg, gw.seg[0], s));
@@ -509,7 +502,7 @@ MMOD_API mmod_status mmod_gradient(mmod_handle *h, const float *wavelet, const f
         if (!h->st_vol) MMOD_CK(h, cudaMalloc(&h->st_vol, sizeof(float) * npts));
         dst = h->st_vol;
     }
-    MMOD_CK(h, launch_grad_to_velocity(gw.gradc, gw.gcomp, h->vel_copy, c.nx, c.ny, c.nz, h->nxp, dst, s));
+    MMOD_CK(h, launch_grad_to_velocity(gw.gradc, h->vel_copy, c.nx, c.ny, c.nz, h->nxp, dst, s));
     ++launches;
     if (!dev_out) {
         MMOD_CK(h, cudaMemcpyAsync(grad_v, dst, sizeof(float) * npts, cudaMemcpyDeviceToHost, s));
@@ -528,7 +521,7 @@ MMOD_API long long mmod_gradient_memory(const mmod_handle *h, int ckpt_count, in
     grad_layout(h, ckpt_count, ckpt_dtype, &nslot, &nwork, &seglen);
     const long long vb = 4LL * h->vol;
     const long long eb = ckpt_dtype == MMOD_CKPT_FP32 ? 4 : 2;
-    return (long long)(nwork + 4) * vb + (long long)nslot * 2 * h->vol * eb +
+    return (long long)(nwork + 3) * vb + (long long)nslot * 2 * h->vol * eb +
            4LL * nslot * 2 * (long long)ckpt_scales(h, ckpt_dtype);
 }
 

@@ -59,9 +59,10 @@ struct mmod_batch {
 
 namespace {
 
-// Planes per CTA in a batch: long z ranges (few halo planes) since a batch
+// Planes per CTA (or per persistent work unit) in a batch: whole columns of
+// the shots up to 256 planes (few halo planes and unit set-ups), since a batch
 // has many CTAs per wave anyway.
-constexpr int kBatchZlen = 96;
+constexpr int kBatchZlen = 256;
 
 __global__ void batch_gather_kernel(const ShotDesc *__restrict__ shots, int nt) {
     const ShotDesc *d = shots + blockIdx.y;

@@ -85,7 +85,13 @@ Ranges axis_ranges(int n, int L, bool low_absent) {
 }
 
 // One layer range [lo, hi) of the line at offset o0 (axis stride st, n points
-// along the axis) for axis A: psi_a, zeta_a and the u^{n+1} correction.
+// along the axis) for axis A: psi_a, zeta_a and the u^{n+1} correction.  The
+// march takes four positions at a time and issues all their loads (u ahead of
+// psi, psi, zeta, u^{n+1}, c and the profiles) before any arithmetic, so a
+// thread keeps about twenty loads in flight instead of waiting on one per
+// position.
+constexpr int kGroup = 4;
+
 template <int A>
 __device__ __forceinline__ void march_range(const CpmlArgs &p, long long o0, long long st, int n, int lo, int hi,
                                             const float *__restrict__ u, float *__restrict__ uout) {
@@ -101,33 +107,47 @@ __device__ __forceinline__ void march_range(const CpmlArgs &p, long long o0, lon
     }
 #pragma unroll
     for (int m = 0; m < kLine; ++m) pw[m] = 0.0f;
-    for (int q = lo - kRadius; q < hi + kRadius; ++q) {
+    for (int q0 = lo - kRadius; q0 < hi + kRadius; q0 += kGroup) {
+        // loads of positions q = q0 .. q0+3: u(q + 4); psi(q) and the profile at
+        // q when q lies in the range; zeta, u^{n+1}, c and the profile at the
+        // trailing position q - 4
+        float un[kGroup], po[kGroup], bq[kGroup], gq[kGroup], zo[kGroup], uo[kGroup], co[kGroup], bp[kGroup],
+            gp[kGroup];
 #pragma unroll
-        for (int m = 0; m < 12; ++m) uw[m] = uw[m + 1];
-        const int qa = q + kRadius;
-        uw[12] = (qa >= 0 && qa < n) ? __ldg(u + o0 + (long long)qa * st) : 0.0f;
-#pragma unroll
-        for (int m = 0; m < kLine - 1; ++m) pw[m] = pw[m + 1];
-        float ps = 0.0f;   // psi outside the range is 0 (outside the grid or g = 0)
-        if (q >= lo && q < hi) {
-            const float g = __ldg(G + q);
-            if (g != 0.0f) {
-                float *pp = psi + o0 + (long long)q * st;
-                ps = __fmaf_rn(__ldg(B + q), *pp, __fmul_rn(g, d1_of(uw + kRadius, ih)));
-                *pp = ps;
-            }
+        for (int j = 0; j < kGroup; ++j) {
+            const int q = q0 + j, qa = q + kRadius, pc = q - kRadius;
+            un[j] = (qa >= 0 && qa < n) ? __ldg(u + o0 + (long long)qa * st) : 0.0f;
+            const bool iq = q >= lo && q < hi, ip = pc >= lo && pc < hi;
+            po[j] = iq ? psi[o0 + (long long)q * st] : 0.0f;
+            bq[j] = iq ? __ldg(B + q) : 0.0f;
+            gq[j] = iq ? __ldg(G + q) : 0.0f;
+            zo[j] = ip ? zeta[o0 + (long long)pc * st] : 0.0f;
+            uo[j] = ip ? uout[o0 + (long long)pc * st] : 0.0f;
+            co[j] = ip ? __ldg(p.c + o0 + (long long)pc * st) : 0.0f;
+            bp[j] = ip ? __ldg(B + pc) : 0.0f;
+            gp[j] = ip ? __ldg(G + pc) : 0.0f;
         }
-        pw[kLine - 1] = ps;
-        const int pc = q - kRadius;   // the correction trails psi by the radius
-        if (pc >= lo && pc < hi) {
-            const float g = __ldg(G + pc);
-            if (g != 0.0f) {
+#pragma unroll
+        for (int j = 0; j < kGroup; ++j) {
+            const int q = q0 + j, pc = q - kRadius;
+#pragma unroll
+            for (int m = 0; m < 12; ++m) uw[m] = uw[m + 1];
+            uw[12] = un[j];
+#pragma unroll
+            for (int m = 0; m < kLine - 1; ++m) pw[m] = pw[m + 1];
+            float ps = 0.0f;   // psi outside the range is 0 (outside the grid or g = 0)
+            if (gq[j] != 0.0f) {
+                ps = __fmaf_rn(bq[j], po[j], __fmul_rn(gq[j], d1_of(uw + kRadius, ih)));
+                psi[o0 + (long long)q * st] = ps;
+            }
+            pw[kLine - 1] = ps;
+            if (gp[j] != 0.0f) {   // the correction trails psi by the radius
                 const long long o = o0 + (long long)pc * st;
                 const float d2 = d2_of(uw, p.w[A]);
                 const float dpsi = d1_of(pw, ih);
-                const float z = __fmaf_rn(__ldg(B + pc), zeta[o], __fmul_rn(g, __fadd_rn(d2, dpsi)));
+                const float z = __fmaf_rn(bp[j], zo[j], __fmul_rn(gp[j], __fadd_rn(d2, dpsi)));
                 zeta[o] = z;
-                uout[o] = __fmaf_rn(__ldg(p.c + o), __fadd_rn(dpsi, z), uout[o]);
+                uout[o] = __fmaf_rn(co[j], __fadd_rn(dpsi, z), uo[j]);
             }
         }
     }

@@ -119,8 +119,7 @@ struct mmod_handle {
         std::vector<CUtensorMap> seg_cur, seg_prev;
         float *psi[2] = {nullptr, nullptr};
         CUtensorMap psi_cur[2], psi_prev[2];
-        float *gradc = nullptr;             // padded FP32 sum of psi^{n+1} g^n ...
-        float *gcomp = nullptr;             // ... and its compensation term
+        float *gradc = nullptr;             // padded FP32 sum of psi^{n+1} g^n
         void *ckpt = nullptr;               // nslot * 2 volumes (FP32 or 16-bit)
         float *ckpt_scale = nullptr;        // 16-bit storage: per-plane (BF16, FP16) or per-32-value
                                             // (BFP16) scales of the nslot * 2 volumes

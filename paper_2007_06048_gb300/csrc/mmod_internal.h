@@ -258,13 +258,13 @@ cudaError_t launch_unreverse_transpose(const float *g, int nt, int ncol, double 
                                        cudaStream_t s);
 // Gradient helpers (mmod_setup.cu).
 // Imaging condition of nsteps (1 or 2) forward steps n, n-1: psi[t] =
-// psi^{n+1-t}, g[t] = g^{n-t} = L u^{n-t} + s^{n-t}; the compensated sum
-// (acc, comp) gains psi[t] g[t] in the order of the steps.
+// psi^{n+1-t}, g[t] = g^{n-t} = L u^{n-t} + s^{n-t}; acc += psi[t] g[t] in
+// the order of the steps.
 cudaError_t launch_imaging(int nsteps, const float *const *psi, const float *const *g, int nx, int ny, int nz,
-                           int nxp, float *acc, float *comp, cudaStream_t s);
-// grad_v = 2 (acc + comp) / v (dJ/dv from the sum of psi^{n+1} g^n), dense output.
-cudaError_t launch_grad_to_velocity(const float *acc, const float *comp, const float *vel, int nx, int ny, int nz,
-                                    int nxp, float *grad_v, cudaStream_t s);
+                           int nxp, float *acc, cudaStream_t s);
+// grad_v = 2 acc / v (dJ/dv from acc = sum_n psi^{n+1} g^n), dense output.
+cudaError_t launch_grad_to_velocity(const float *acc, const float *vel, int nx, int ny, int nz, int nxp,
+                                    float *grad_v, cudaStream_t s);
 cudaError_t launch_dot(const float *a, const float *b, long long n, double *out, cudaStream_t s);
 cudaError_t launch_pack(const float *dense, int nx, int ny, int nz, int nxp, float *padded,
                         cudaStream_t s);

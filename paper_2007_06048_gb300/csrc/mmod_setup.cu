@@ -178,39 +178,21 @@ __global__ void unreverse_transpose_kernel(const float *__restrict__ g, int nt, 
 
 // Zero-lag imaging condition: with mu = psi / c the adjoint state,
 //   dJ/dc = sum_n mu^{n+1} g^n,  g^n = L u^n + s^n (written by the replay's
-// step kernel), so the kernel accumulates A = sum_n psi^{n+1} g^n and the
-// factor 1 / c is applied once at the end (dJ/dv = 2 dt^2 v A / c = 2 A / v).
-// The terms of a point change sign from step to step (two oscillating fields
-// correlated at zero lag), so their sum is much smaller than the sum of their
-// magnitudes; a plain FP32 running sum loses about a digit per decade of
-// that ratio.  The sum is therefore compensated, in FP32: the accurate dot
-// product of Ogita, Rump and Oishi (2005, "Dot2"): each product split exactly
-// into h + r (r from a fused multiply-add), added to the running sum p by
-// Knuth's error-free TwoSum (p + h = p' + q exactly), and q + r collected in a
-// second sum s; the result p + s is as accurate as a sum in twice the working
-// precision followed by one rounding.
+// step kernel), so the kernel accumulates A = sum_n psi^{n+1} g^n (FP32
+// fused multiply-adds, in step order) and the factor 1 / c is applied once at
+// the end (dJ/dv = 2 dt^2 v A / c = 2 A / v).
 // Four consecutive x of one row per thread (16-byte loads; rows are padded to
 // 32 floats, so a group never straddles rows); columns past nx are loaded
 // (in bounds of the padded row) but not stored.  NS = 1: forward step n
 // (psi[0] = psi^{n+1}, g[0] = g^n); NS = 2: steps n and n - 1 in that order
 // (psi[1] = psi^n, g[1] = g^{n-1}), the same operations as two single-step
-// passes with p and s read and written once.
+// passes with A read and written once.
 struct ImagingArgs {
     const float4 *psi[2];
     const float4 *g[2];
     int nx, ny, nz, nxp;
-    float4 *acc, *comp;   // p and s of the compensated sum
+    float4 *acc;
 };
-
-__device__ __forceinline__ void dot2_step(float x, float y, float &p, float &s) {
-    const float h = __fmul_rn(x, y);
-    const float r = __fmaf_rn(x, y, -h);        // x y = h + r exactly
-    const float pn = __fadd_rn(p, h);
-    const float z = __fsub_rn(pn, p);
-    const float q = __fadd_rn(__fsub_rn(p, __fsub_rn(pn, z)), __fsub_rn(h, z));   // p + h = pn + q exactly
-    p = pn;
-    s = __fadd_rn(s, __fadd_rn(q, r));
-}
 
 template <int NS>
 __global__ void imaging_kernel(const ImagingArgs a) {
@@ -227,39 +209,35 @@ __global__ void imaging_kernel(const ImagingArgs a) {
             ps[t] = a.psi[t][q];
             gg[t] = a.g[t][q];
         }
-        float4 p = a.acc[q], c = a.comp[q];
+        float4 acc = a.acc[q];
 #pragma unroll
         for (int t = 0; t < NS; ++t) {
-            dot2_step(ps[t].x, gg[t].x, p.x, c.x);
-            dot2_step(ps[t].y, gg[t].y, p.y, c.y);
-            dot2_step(ps[t].z, gg[t].z, p.z, c.z);
-            dot2_step(ps[t].w, gg[t].w, p.w, c.w);
+            acc.x = __fmaf_rn(ps[t].x, gg[t].x, acc.x);
+            acc.y = __fmaf_rn(ps[t].y, gg[t].y, acc.y);
+            acc.z = __fmaf_rn(ps[t].z, gg[t].z, acc.z);
+            acc.w = __fmaf_rn(ps[t].w, gg[t].w, acc.w);
         }
         if (i0 + 3 < a.nx) {
-            a.acc[q] = p;
-            a.comp[q] = c;
+            a.acc[q] = acc;
         } else {   // the row's last group: keep the padding untouched
-            float *pp = reinterpret_cast<float *>(a.acc + q), *cp = reinterpret_cast<float *>(a.comp + q);
-            pp[0] = p.x;
-            cp[0] = c.x;
-            if (i0 + 1 < a.nx) pp[1] = p.y, cp[1] = c.y;
-            if (i0 + 2 < a.nx) pp[2] = p.z, cp[2] = c.z;
+            float *ap = reinterpret_cast<float *>(a.acc + q);
+            ap[0] = acc.x;
+            if (i0 + 1 < a.nx) ap[1] = acc.y;
+            if (i0 + 2 < a.nx) ap[2] = acc.z;
         }
     }
 }
 
-// grad_v = 2 (p + s) / v (p + s = sum_n psi^{n+1} g^n, c = dt^2 v^2), dense
-// output, FP32 (correctly rounded division).
-__global__ void grad_to_velocity_kernel(const float *__restrict__ acc, const float *__restrict__ comp,
-                                        const float *__restrict__ vel, int nx, int ny, int nz, int nxp,
-                                        float *__restrict__ gv) {
+// grad_v = 2 A / v (A = sum_n psi^{n+1} g^n, c = dt^2 v^2), dense output,
+// FP32 (correctly rounded division).
+__global__ void grad_to_velocity_kernel(const float *__restrict__ acc, const float *__restrict__ vel, int nx,
+                                        int ny, int nz, int nxp, float *__restrict__ gv) {
     const long long total = (long long)nx * ny * nz;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
          q += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(q % nx);
         const long long o = (q / nx) * nxp + i;
-        const float sum = __fadd_rn(acc[o], comp[o]);
-        gv[q] = __fdiv_rn(__fmul_rn(2.0f, sum), vel[q]);
+        gv[q] = __fdiv_rn(__fmul_rn(2.0f, acc[o]), vel[q]);
     }
 }
 
@@ -295,7 +273,7 @@ cudaError_t launch_unreverse_transpose(const float *g, int nt, int ncol, double 
 }
 
 cudaError_t launch_imaging(int nsteps, const float *const *psi, const float *const *g, int nx, int ny, int nz,
-                           int nxp, float *acc, float *comp, cudaStream_t s) {
+                           int nxp, float *acc, cudaStream_t s) {
     if (nsteps < 1 || nsteps > 2) return cudaErrorInvalidValue;
     ImagingArgs a{};
     for (int t = 0; t < nsteps; ++t) {
@@ -304,7 +282,6 @@ cudaError_t launch_imaging(int nsteps, const float *const *psi, const float *con
     }
     a.nx = nx; a.ny = ny; a.nz = nz; a.nxp = nxp;
     a.acc = reinterpret_cast<float4 *>(acc);
-    a.comp = reinterpret_cast<float4 *>(comp);
     const long long groups = (long long)(nxp / 4) * ny * nz;
     const int grid = (int)std::min<long long>((groups + 255) / 256, 152LL * 8);
     if (nsteps == 1)
@@ -314,9 +291,9 @@ cudaError_t launch_imaging(int nsteps, const float *const *psi, const float *con
     return cudaGetLastError();
 }
 
-cudaError_t launch_grad_to_velocity(const float *acc, const float *comp, const float *vel, int nx, int ny, int nz,
-                                    int nxp, float *grad_v, cudaStream_t s) {
-    grad_to_velocity_kernel<<<grid2((long long)nx * ny * nz), 256, 0, s>>>(acc, comp, vel, nx, ny, nz, nxp, grad_v);
+cudaError_t launch_grad_to_velocity(const float *acc, const float *vel, int nx, int ny, int nz, int nxp,
+                                    float *grad_v, cudaStream_t s) {
+    grad_to_velocity_kernel<<<grid2((long long)nx * ny * nz), 256, 0, s>>>(acc, vel, nx, ny, nz, nxp, grad_v);
     return cudaGetLastError();
 }
 

@@ -78,8 +78,19 @@ def grad200(orc):
     return p, resid, g
 
 
-# provisional gates until the 1000-step errors are measured
-GATES = {M.CKPT_FP32: 1e-4, M.CKPT_BF16: 20.0, M.CKPT_FP16: 2.0, M.CKPT_BFP16: 0.5}
+# Gates: about twice the errors measured on GB300 (whole volume; beyond 4
+# cells of the source), per checkpoint type and scheme.  FP32: the source
+# point dominates the whole-volume error: there L u^n and s^n nearly cancel,
+# and around it the static near field of the point source is harmonic, so
+# the Laplacian's axis terms nearly cancel too; FP32 loses digits in both
+# (the FP64 oracle does not).  16-bit checkpoints: the rounding of the
+# replayed states is grid-scale noise that L amplifies ~100x against this
+# smooth 10 Hz field on a 10 m grid (15-40 points per wavelength); revolve
+# restores states saved from restored states, so its errors compound.
+GATES = {(M.CKPT_FP32, M.SCHEME_SEGMENTS): (2e-3, 3e-4), (M.CKPT_FP32, M.SCHEME_REVOLVE): (2e-3, 3e-4),
+         (M.CKPT_BF16, M.SCHEME_SEGMENTS): (5.0, 2.0), (M.CKPT_BF16, M.SCHEME_REVOLVE): (17.0, 5.0),
+         (M.CKPT_FP16, M.SCHEME_SEGMENTS): (0.6, 0.25), (M.CKPT_FP16, M.SCHEME_REVOLVE): (2.0, 0.6),
+         (M.CKPT_BFP16, M.SCHEME_SEGMENTS): (0.1, 0.1), (M.CKPT_BFP16, M.SCHEME_REVOLVE): (0.35, 0.35)}
 
 
 @pytest.mark.parametrize("scheme", [M.SCHEME_SEGMENTS, M.SCHEME_REVOLVE])
@@ -107,7 +118,8 @@ def test_gradient_200_geometry_matches_oracle(grad200, scheme, dtype):
           f"beyond 4 cells of the source {err_far:.3e}; largest difference at (k, j, i) = {big}, "
           f"|g| max {np.abs(g_o).max():.3e} at {np.unravel_index(np.argmax(np.abs(g_o)), gg.shape)}")
     assert np.abs(g_o).max() > 0
-    assert err <= GATES[dtype]
+    gate, gate_far = GATES[(dtype, scheme)]
+    assert err <= gate and err_far <= gate_far
 
 
 def _fd_problem(nt=300):
