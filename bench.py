@@ -405,10 +405,9 @@ def roofline_of(bytes_per_call, ms, peak, what):
 
 
 def cpml_layer_bytes(nx, ny, nz, L, free_surface=False):
-    """Algorithmic bytes of the two CPML layer passes per step.  A layer cell
-    with k axes in their layers: psi pass reads u (4 B) and updates psi_a
-    (8k B); the correction pass reads u (4) and psi_a (4k), updates zeta_a
-    (8k) and u^{n+1} (8) and reads c (4): 20 + 20k bytes per cell."""
+    """Algorithmic bytes of the CPML layer terms per step: a layer cell with k
+    axes in their layers reads u^n and c and updates u^{n+1} once (16 B), and
+    updates psi_a and zeta_a of each of its k axes (16k B)."""
     def inside(n, lo_layer=True):
         m = np.zeros(n, bool)
         if lo_layer:
@@ -420,7 +419,7 @@ def cpml_layer_bytes(nx, ny, nz, L, free_surface=False):
     az = inside(nz, not free_surface)
     cells = int(np.logical_or.outer(np.logical_or.outer(az, ay), ax).sum())
     axes = int(ax.sum()) * ny * nz + int(ay.sum()) * nx * nz + int(az.sum()) * nx * ny
-    return 20 * cells + 20 * axes, cells, axes
+    return 16 * cells + 16 * axes, cells, axes
 
 
 def time_calls(fn, reps, stream):
@@ -578,12 +577,12 @@ def measure_cpml(M, dev, stream, fwd_gpts, reps=3):
     nz, ny, nx = p.vel.shape
     lb, cells, axes = cpml_layer_bytes(nx, ny, nz, p.nbl)
     roof = roofline_of((BYTES_PER_POINT * p.npoints + lb) * p.nt, ms, load_peaks()[0],
-                       f"per step 16 B per point (step kernel) + 20 + 20k B per layer cell with k axes in their "
-                       f"layers (psi and correction passes): {cells} layer cells, {axes} cell-axes")
+                       f"per step 16 B per point (step kernel) + 16 + 16k B per layer cell with k axes in their "
+                       f"layers (u^n, c, u^{{n+1}} once; psi_a, zeta_a per axis): {cells} layer cells, {axes} cell-axes")
     return {"value": v, "unit": UNIT, "ms": ms, "vs_forward": v / fwd_gpts, "workload": p.name + " + CPML (L=20)",
             "roofline": roof, "layer_bytes_per_step": lb,
-            "what": "per step: the undamped step kernel, then two passes over the six layer slabs "
-                    "(psi_a^n from u^n; then zeta_a^n and the u^{n+1} correction)"}
+            "what": "per step: the undamped step kernel, then one pass per axis over the layer ranges of the "
+                    "lines along it (psi_a^n, zeta_a^n and the u^{n+1} correction)"}
 
 
 VD_BYTES_PER_POINT = 56   # velocity kernel 32 B + pressure kernel 24 B (FP32)

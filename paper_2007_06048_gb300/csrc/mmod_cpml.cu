@@ -86,13 +86,12 @@ Ranges axis_ranges(int n, int L, bool low_absent) {
 
 // One layer range [lo, hi) of the line at offset o0 (axis stride st, n points
 // along the axis) for axis A: psi_a, zeta_a and the u^{n+1} correction.  The
-// march takes four positions at a time and issues all their loads (u ahead of
+// march takes kGroup positions at a time (7: a 20-cell layer's 28 positions
+// in four groups) and issues all their loads (u ahead of
 // psi, psi, zeta, u^{n+1}, c and the profiles) before any arithmetic, so a
-// thread keeps about twenty loads in flight instead of waiting on one per
+// thread keeps 5 kGroup loads in flight instead of waiting on one per
 // position.
-constexpr int kGroup = 4;
-
-template <int A>
+template <int A, int kGroup>
 __device__ __forceinline__ void march_range(const CpmlArgs &p, long long o0, long long st, int n, int lo, int hi,
                                             const float *__restrict__ u, float *__restrict__ uout) {
     const float *B = p.b[A], *G = p.g[A];
@@ -158,7 +157,7 @@ __device__ __forceinline__ void march_range(const CpmlArgs &p, long long o0, lon
 // consecutive x for y and z); grid-stride over the items, so each thread
 // takes about `per` of them and neighbouring threads stay on neighbouring
 // lines.
-template <int A>
+template <int A, int kGroup = 7>
 __global__ void __launch_bounds__(128) cpml_line_kernel(const CpmlArgs p, const Ranges rg, const float *__restrict__ u,
                                                         float *__restrict__ uout) {
     const int n = A == 0 ? p.nx : (A == 1 ? p.ny : p.nz);
@@ -181,57 +180,75 @@ __global__ void __launch_bounds__(128) cpml_line_kernel(const CpmlArgs p, const 
         } else {
             o0 = (long long)c2 * p.nxp + c1;
         }
-        march_range<A>(p, o0, st, n, rg.lo[r], rg.hi[r], u, uout);
+        march_range<A, kGroup>(p, o0, st, n, rg.lo[r], rg.hi[r], u, uout);
     }
 }
 
 // x pass: one warp per row segment of one layer range (at most 24 cells,
-// lanes 4..27 hold them, lanes 0..3 and 28..31 the margins); grid-stride over
-// the segments (about `per` per warp).
+// lanes 4..27 hold them, lanes 0..3 and 28..31 the margins); a warp takes
+// kRows consecutive segments at a time and issues all their loads before the
+// shuffles and arithmetic; grid-stride over the groups.
+constexpr int kRows = 4;
+
 __global__ void __launch_bounds__(128) cpml_x_warp_kernel(const CpmlArgs p, const Ranges rg, const float *__restrict__ u,
                                                           float *__restrict__ uout) {
     const int lane = threadIdx.x & 31;
-    const long long rows = (long long)p.ny * p.nz;
+    const long long rows = (long long)p.ny * p.nz, total = rows * rg.n;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const float ih = p.inv_h[0];
-    for (long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < rows * rg.n; t += nwarps) {
-        const int r = (int)(t / rows);
-        const long long l = t - (long long)r * rows;
-        const int j = (int)(l % p.ny), k = (int)(l / p.ny);
-        if (p.fs && k == 0) continue;   // the free-surface plane stays 0 (uniform over the warp)
-        const long long row = (long long)k * p.plane + (long long)j * p.nxp;
-        const int i = rg.lo[r] - kRadius + lane;
-        const bool in_grid = i >= 0 && i < p.nx;
-        const bool mine = i >= rg.lo[r] && i < rg.hi[r];
-        const float uu = in_grid ? __ldg(u + row + i) : 0.0f;
-        const float g = mine ? __ldg(p.g[0] + i) : 0.0f;
-        float x[kLine];
+    for (long long t0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kRows; t0 < total;
+         t0 += nwarps * kRows) {
+        float uu[kRows], po[kRows], zo[kRows], uo[kRows], co[kRows], bb[kRows], gg[kRows];
+        long long off[kRows];
 #pragma unroll
-        for (int m = 1; m <= kRadius; ++m) {
-            x[kRadius + m] = __shfl_down_sync(0xffffffffu, uu, m);
-            x[kRadius - m] = __shfl_up_sync(0xffffffffu, uu, m);
+        for (int rr = 0; rr < kRows; ++rr) {
+            const long long t = t0 + rr;
+            const int r = t < total ? (int)(t / rows) : 0;
+            const long long l = t - (long long)r * rows;
+            const int j = (int)(l % p.ny), k = (int)(l / p.ny);
+            // rows past the end and the free-surface plane take no part (uniform over the warp)
+            const bool live = t < total && !(p.fs && k == 0);
+            const int i = rg.lo[r] - kRadius + lane;
+            const bool in_grid = live && i >= 0 && i < p.nx;
+            const bool mine = live && i >= rg.lo[r] && i < rg.hi[r];
+            off[rr] = (long long)k * p.plane + (long long)j * p.nxp + i;
+            uu[rr] = in_grid ? __ldg(u + off[rr]) : 0.0f;
+            gg[rr] = mine ? __ldg(p.g[0] + i) : 0.0f;
+            bb[rr] = mine ? __ldg(p.b[0] + i) : 0.0f;
+            po[rr] = mine ? p.psi[0][off[rr]] : 0.0f;
+            zo[rr] = mine ? p.zeta[0][off[rr]] : 0.0f;
+            uo[rr] = mine ? uout[off[rr]] : 0.0f;
+            co[rr] = mine ? __ldg(p.c + off[rr]) : 0.0f;
         }
-        x[kRadius] = uu;
-        float ps = 0.0f;
-        if (g != 0.0f) {
-            float *pp = p.psi[0] + row + i;
-            ps = __fmaf_rn(__ldg(p.b[0] + i), *pp, __fmul_rn(g, d1_of(x, ih)));
-            *pp = ps;
-        }
-        float q[kLine];
 #pragma unroll
-        for (int m = 1; m <= kRadius; ++m) {
-            q[kRadius + m] = __shfl_down_sync(0xffffffffu, ps, m);
-            q[kRadius - m] = __shfl_up_sync(0xffffffffu, ps, m);
-        }
-        q[kRadius] = ps;
-        if (g != 0.0f) {
-            const long long o = row + i;
-            const float d2 = d2_of(x, p.w[0]);
-            const float dpsi = d1_of(q, ih);
-            const float z = __fmaf_rn(__ldg(p.b[0] + i), p.zeta[0][o], __fmul_rn(g, __fadd_rn(d2, dpsi)));
-            p.zeta[0][o] = z;
-            uout[o] = __fmaf_rn(__ldg(p.c + o), __fadd_rn(dpsi, z), uout[o]);
+        for (int rr = 0; rr < kRows; ++rr) {
+            float x[kLine];
+#pragma unroll
+            for (int m = 1; m <= kRadius; ++m) {
+                x[kRadius + m] = __shfl_down_sync(0xffffffffu, uu[rr], m);
+                x[kRadius - m] = __shfl_up_sync(0xffffffffu, uu[rr], m);
+            }
+            x[kRadius] = uu[rr];
+            const float g = gg[rr];
+            float ps = 0.0f;
+            if (g != 0.0f) {
+                ps = __fmaf_rn(bb[rr], po[rr], __fmul_rn(g, d1_of(x, ih)));
+                p.psi[0][off[rr]] = ps;
+            }
+            float q[kLine];
+#pragma unroll
+            for (int m = 1; m <= kRadius; ++m) {
+                q[kRadius + m] = __shfl_down_sync(0xffffffffu, ps, m);
+                q[kRadius - m] = __shfl_up_sync(0xffffffffu, ps, m);
+            }
+            q[kRadius] = ps;
+            if (g != 0.0f) {
+                const float d2 = d2_of(x, p.w[0]);
+                const float dpsi = d1_of(q, ih);
+                const float z = __fmaf_rn(bb[rr], zo[rr], __fmul_rn(g, __fadd_rn(d2, dpsi)));
+                p.zeta[0][off[rr]] = z;
+                uout[off[rr]] = __fmaf_rn(co[rr], __fadd_rn(dpsi, z), uo[rr]);
+            }
         }
     }
 }
@@ -254,7 +271,8 @@ cudaError_t launch_cpml_layers(const CpmlArgs &p, const float *u, float *uout, c
                     zl = (long long)p.nx * p.ny * rz.n;
     if (rx.n > 0) {
         if (x_warp)
-            cpml_x_warp_kernel<<<blocks_for(((xl + per - 1) / per) * 32), 128, 0, s>>>(p, rx, u, uout);
+            cpml_x_warp_kernel<<<blocks_for(((xl + (long long)per * kRows - 1) / ((long long)per * kRows)) * 32), 128,
+                                 0, s>>>(p, rx, u, uout);
         else
             cpml_line_kernel<0><<<blocks_for((xl + per - 1) / per), 128, 0, s>>>(p, rx, u, uout);
         if (cudaError_t e = cudaGetLastError()) return e;
