@@ -330,7 +330,7 @@ def run_mmod(args):
                 "batched": lambda: measure_batched(M, dev, stream, fwd_gpts),
                 "large": lambda: measure_large(M, dev, stream, peak),
                 "free_surface": lambda: measure_free_surface(M, dev, stream, fwd_gpts),
-                "cpml": lambda: measure_cpml(M, dev, stream, fwd_gpts),
+                "cpml": lambda: measure_cpml(M, dev, stream, fwd_gpts, args.nt or 1000),
                 "variable_density": lambda: measure_vd(M, dev, stream, fwd_gpts, peak, args.nt or 1000)}
     for name in extras_of(args):
         extra[name] = measures[name]()
@@ -559,12 +559,12 @@ def measure_free_surface(M, dev, stream, fwd_gpts, reps=3):
     return {"value": v, "unit": UNIT, "ms": ms, "vs_forward": v / fwd_gpts, "workload": p.name + " + free surface"}
 
 
-def measure_cpml(M, dev, stream, fwd_gpts, reps=3):
+def measure_cpml(M, dev, stream, fwd_gpts, nt=1000, reps=3):
     """The bench workload with CPML layers (20 cells, 10 Hz shift) instead of
     damping layers: the memory variables' cost."""
     import torch
     import workloads as W
-    p = W.layered_240(1000)
+    p = W.layered_240(nt)
     p.cpml, p.cpml_f0 = True, 10.0
     prop = M.Propagator.from_problem(p, device=dev.index or 0)
     prop.set_model(torch.from_numpy(p.vel).to(dev), stream)
