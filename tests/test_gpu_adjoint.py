@@ -220,3 +220,24 @@ def test_gradient_16bit_checkpoints_with_quiet_planes(dtype, gate):
     assert np.isfinite(g16).all()
     assert rel_l2(g16, g32) <= gate
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("scheme", [M.SCHEME_SEGMENTS, M.SCHEME_REVOLVE])
+@pytest.mark.parametrize("nt", [1, 2, 3, 7])
+def test_gradient_of_short_runs_matches_oracle(orc, nt, scheme):
+    """Runs of a few steps, where the checkpoint layouts degenerate (one slot,
+    a slot per step, every state kept): random wavelets, receivers on and next
+    to the sources so that the gradient is not identically zero."""
+    rng = np.random.default_rng(50 + nt)
+    p = W.tiny_problem(shape=(14, 15, 16), nt=nt, nbl=2, nsrc=2, nrec=6, seed=60 + nt)
+    p.wavelet = rng.standard_normal((2, nt)).astype(np.float32)
+    s0, s1 = p.src_ijk
+    top = np.array([16 - 1, 15 - 1, 14 - 1])
+    p.rec_ijk[:] = np.clip([s0, s1, s0 + [1, 0, 0], s1 + [0, 1, 0], s0 + [0, 0, 1], s1 - [1, 0, 0]], 0, top)
+    resid = rng.standard_normal((nt, 6)).astype(np.float32)
+    g_o = orc.gradient(p.vel, p.h, p.dt, p.nt, nbl=p.nbl, src_ijk=p.src_ijk, wavelet=p.wavelet,
+                       rec_ijk=p.rec_ijk, resid=resid)
+    assert np.abs(g_o).max() > 0
+    for ck, dtype, gate in ((1, M.CKPT_FP32, 1e-5), (nt, M.CKPT_FP32, 1e-5), (1, M.CKPT_BFP16, 1e-3)):
+        g = _gpu_gradient(p, resid, ck, dtype, scheme)
+        assert rel_l2(g, g_o) <= gate, (ck, dtype)

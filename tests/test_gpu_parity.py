@@ -52,8 +52,10 @@ def test_layered_240_1000_steps_full_size(orc):
     assert rel_l2(tr_g, tr_o) <= 1e-4
 
 
+# ragged tiles and z ranges, one-point and one-wide grids, and layers that fill
+# an axis (2 nbl = n: no inner point along z)
 SHAPES = [((9, 9, 9), 0), ((13, 17, 35), 2), ((70, 33, 65), 5), ((5, 40, 3), 1), ((1, 1, 1), 0),
-          ((2, 67, 129), 0), ((40, 1, 30), 0), ((37, 45, 131), 9)]
+          ((2, 67, 129), 0), ((40, 1, 30), 0), ((37, 45, 131), 9), ((8, 10, 12), 4)]
 
 
 @pytest.mark.parametrize("shape,nbl", SHAPES, ids=[f"{s}-L{n}" for s, n in SHAPES])
