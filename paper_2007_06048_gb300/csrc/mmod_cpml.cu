@@ -91,9 +91,12 @@ Ranges axis_ranges(int n, int L, bool low_absent) {
 // psi, psi, zeta, u^{n+1}, c and the profiles) before any arithmetic, so a
 // thread keeps 5 kGroup loads in flight instead of waiting on one per
 // position.
-template <int A, int kGroup>
+// kLen > 0: the range is known to hold kLen cells, so the march is unrolled in
+// full and the windows are fixed registers (no shifting moves).
+template <int A, int kGroup, int kLen = 0>
 __device__ __forceinline__ void march_range(const CpmlArgs &p, long long o0, long long st, int n, int lo, int hi,
                                             const float *__restrict__ u, float *__restrict__ uout) {
+    if (kLen > 0) hi = lo + kLen;
     const float *B = p.b[A], *G = p.g[A];
     float *psi = p.psi[A], *zeta = p.zeta[A];
     const float ih = p.inv_h[A];
@@ -106,7 +109,10 @@ __device__ __forceinline__ void march_range(const CpmlArgs &p, long long o0, lon
     }
 #pragma unroll
     for (int m = 0; m < kLine; ++m) pw[m] = 0.0f;
-    for (int q0 = lo - kRadius; q0 < hi + kRadius; q0 += kGroup) {
+    constexpr int kGroups = kLen > 0 ? (kLen + 2 * kRadius + kGroup - 1) / kGroup : 1;
+#pragma unroll
+    for (int gi = 0; kLen > 0 ? gi < kGroups : lo - kRadius + gi * kGroup < hi + kRadius; ++gi) {
+        const int q0 = lo - kRadius + gi * kGroup;
         // loads of positions q = q0 .. q0+3: u(q + 4); psi(q) and the profile at
         // q when q lies in the range; zeta, u^{n+1}, c and the profile at the
         // trailing position q - 4
@@ -152,6 +158,9 @@ __device__ __forceinline__ void march_range(const CpmlArgs &p, long long o0, lon
     }
 }
 
+// Layer width whose march is compiled fully unrolled (the workloads' 20 cells).
+constexpr int kCommonLayer = 20;
+
 // y and z passes (and the x pass for ranges wider than a warp row segment):
 // work item t is line t % lines of range t / lines (consecutive t on
 // consecutive x for y and z); grid-stride over the items, so each thread
@@ -180,7 +189,10 @@ __global__ void __launch_bounds__(128) cpml_line_kernel(const CpmlArgs p, const 
         } else {
             o0 = (long long)c2 * p.nxp + c1;
         }
-        march_range<A, kGroup>(p, o0, st, n, rg.lo[r], rg.hi[r], u, uout);
+        if (rg.hi[r] - rg.lo[r] == kCommonLayer)
+            march_range<A, kGroup, kCommonLayer>(p, o0, st, n, rg.lo[r], rg.hi[r], u, uout);
+        else
+            march_range<A, kGroup>(p, o0, st, n, rg.lo[r], rg.hi[r], u, uout);
     }
 }
 
