@@ -292,6 +292,12 @@ mmod_status mmod_set_tma_variant(mmod_handle *h, int v);
  *                         (row segments per warp along x) in the CPML
  *                         layer passes (0 = the default, 1); the same bits
  *                         for any value;
+ *   MMOD_OPT_CPML_TILES   0 / 1 (default 1): run the CPML layer pass of an
+ *                         axis as tiles of 128 lines loaded whole into shared
+ *                         memory by bulk-tensor copies, where the axis allows
+ *                         it (layer width 8 or 20, the two layer ranges
+ *                         apart; along x also nx a multiple of 4); 0: the
+ *                         marching passes only.  The same bits either way;
  *   MMOD_OPT_TEST_STALL   1: test hook of the failure path.  The next
  *                         persistent run (of this handle, or of a persistent
  *                         batch holding it) waits for neighbour counters that
@@ -301,7 +307,8 @@ mmod_status mmod_set_tma_variant(mmod_handle *h, int v);
  *                         other handles stay usable).
  * Errors: ARG (unknown option or value). */
 enum { MMOD_OPT_PDL = 2, MMOD_OPT_CKPT_SCHEME = 3, MMOD_OPT_PERSISTENT = 4, MMOD_OPT_PERSISTENT_CTAS = 5,
-       MMOD_OPT_TEST_STALL = 6, MMOD_OPT_ZLEN = 7, MMOD_OPT_CPML_PLANES = 8, MMOD_OPT_CLAIM = 9 };
+       MMOD_OPT_TEST_STALL = 6, MMOD_OPT_ZLEN = 7, MMOD_OPT_CPML_PLANES = 8, MMOD_OPT_CLAIM = 9,
+       MMOD_OPT_CPML_TILES = 10 };
 enum { MMOD_SCHEME_SEGMENTS = 0, MMOD_SCHEME_REVOLVE = 1 };
 mmod_status mmod_set_option(mmod_handle *h, int option, int value);
 

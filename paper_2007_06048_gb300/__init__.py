@@ -34,6 +34,7 @@ OPT_TEST_STALL = 6
 OPT_ZLEN = 7
 OPT_CPML_PLANES = 8
 OPT_CLAIM = 9
+OPT_CPML_TILES = 10
 BOUNDARY_DAMPING, BOUNDARY_CPML = 0, 1
 BATCH_STREAMS, BATCH_FUSED, BATCH_PERSISTENT = 0, 1, 2
 SCHEME_SEGMENTS, SCHEME_REVOLVE = 0, 1

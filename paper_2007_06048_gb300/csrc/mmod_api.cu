@@ -99,6 +99,7 @@ void free_all(mmod_handle *h) {
     if (h->queue) cudaFree(h->queue);
     if (h->cpml_mem) cudaFree(h->cpml_mem);
     if (h->cpml_bg) cudaFree(h->cpml_bg);
+    if (h->cpml_xc) cudaFree(h->cpml_xc);
     if (h->vmax_bits) cudaFree(h->vmax_bits);
     if (h->bad) cudaFree(h->bad);
     if (h->ev_t0) cudaEventDestroy(h->ev_t0);
@@ -275,6 +276,9 @@ CpmlArgs cpml_args(const mmod_handle *h) {
     }
     p.c = h->c;
     p.zc = h->cpml_planes > 0 ? h->cpml_planes : kCpmlPlanes;
+    p.tiles = h->cpml_tiles_on;
+    p.err = h->err_dev;
+    p.xc = h->cpml_xc;
     return p;
 }
 
@@ -442,8 +446,9 @@ static mmod_status enqueue_loop(mmod_handle *h, const Geometry &geo, const float
             a.uout = h->u[n & 1];
             a.traces = (n >= 1 && tr && ng > 0) ? tr + (long long)(n - 1) * ng : nullptr;
             MMOD_CK(h, enqueue_step(h, a, &h->cur_map[(n + 1) & 1], &h->prev_map[n & 1], tma, nullptr, s, count));
-            MMOD_CK(h, launch_cpml_layers(cp, a.ucur, a.uout, s));
-            *count += 2;
+            int passes = 0;
+            MMOD_CK(h, launch_cpml_layers(cp, &h->cpml_tiles, (n + 1) & 1, a.ucur, a.uout, s, &passes));
+            *count += passes;
             if (!tma && tr && ng > 0) {
                 MMOD_CK(h, launch_gather(a.uout, geo.gather_off, ng, tr + (long long)n * ng, s));
                 ++*count;
@@ -631,6 +636,11 @@ MMOD_API mmod_status mmod_create(const mmod_config *cfg, int device, mmod_handle
         CKC(cudaMemset(h->cpml_mem, 0, 6 * vbytes));
         CKC(cudaMalloc(&h->cpml_bg, sizeof(float) * 2 * (size_t)(nx + ny + nz)));
         CKC(cudaMemset(h->cpml_bg, 0, sizeof(float) * 2 * (size_t)(nx + ny + nz)));
+        h->cpml_xc_floats = cpml_x_compact_floats(cpml_args(h));
+        if (h->cpml_xc_floats > 0) {
+            CKC(cudaMalloc(&h->cpml_xc, sizeof(float) * (size_t)h->cpml_xc_floats));
+            CKC(cudaMemset(h->cpml_xc, 0, sizeof(float) * (size_t)h->cpml_xc_floats));
+        }
     }
     CKC(cudaMalloc(&h->vmax_bits, sizeof(unsigned int)));
     CKC(cudaMalloc(&h->bad, sizeof(unsigned long long)));
@@ -657,6 +667,8 @@ MMOD_API mmod_status mmod_create(const mmod_config *cfg, int device, mmod_handle
     CKC(cudaHostAlloc(&h->err_host, sizeof(int), cudaHostAllocMapped));
     *h->err_host = 0;
     CKC(cudaHostGetDevicePointer(&h->err_dev, h->err_host, 0));
+    if (is_cpml(h) && !make_cpml_tiles(cpml_args(h), h->u, &h->cpml_tiles))
+        CKC(cudaErrorInvalidValue);   // a tensor map of the tiled layer passes could not be encoded
     h->tma_ok = make_tma_plan(h->cfg, h->nxp, h->u, h->c, h->cur_map, h->prev_map, &h->c_map, h->plans);
     if (h->tma_ok) {   // counters of the persistent kernel, sized for the plan with the most units
         for (int v = 0; v < tma_variant_count(); ++v)
@@ -715,6 +727,11 @@ MMOD_API mmod_status mmod_set_option(mmod_handle *h, int option, int value) {
     if (option == MMOD_OPT_CPML_PLANES) {
         if (value < 0 || value > 4096) return fail(h, MMOD_ERR_ARG, "MMOD_OPT_CPML_PLANES must be in [0, 4096]");
         h->cpml_planes = value;
+        return MMOD_OK;
+    }
+    if (option == MMOD_OPT_CPML_TILES) {
+        if (value != 0 && value != 1) return fail(h, MMOD_ERR_ARG, "MMOD_OPT_CPML_TILES must be 0 or 1");
+        h->cpml_tiles_on = value;
         return MMOD_OK;
     }
     if (option == MMOD_OPT_CLAIM) {
@@ -796,6 +813,7 @@ MMOD_API mmod_status mmod_set_model(mmod_handle *h, const float *vel, mmod_strea
                                               std::to_string(c.dt * vmax * std::sqrt(ksum)) + " > 2");
     }
     MMOD_CK(h, launch_model_fill(dvel, c.nx, c.ny, c.nz, h->nxp, c.dt, h->c, s));
+    if (is_cpml(h)) MMOD_CK(h, launch_cpml_pack_c(cpml_args(h), s));
     for (Geometry *g : {&h->fwd, &h->adj})
         MMOD_CK(h, launch_source_scale(dvel, c.nx, c.ny, g->inj.nsrc, g->inj.src_i, g->inj.src_j, g->inj.src_k,
                                        c.dt, g->cell, g->inj.src_scale, s));
@@ -905,6 +923,8 @@ MMOD_API mmod_status mmod_forward(mmod_handle *h, const float *wavelet, float *t
         MMOD_CK(h, cudaMemsetAsync(h->u[1], 0, sizeof(float) * (size_t)h->vol, s));
     }
     if (is_cpml(h)) MMOD_CK(h, cudaMemsetAsync(h->cpml_mem, 0, 6 * sizeof(float) * (size_t)h->vol, s));
+    if (h->cpml_xc)   // psi_x and zeta_x of the compact x layers (c_x stays)
+        MMOD_CK(h, cudaMemsetAsync(h->cpml_xc, 0, sizeof(float) * (size_t)(h->cpml_xc_floats / 3 * 2), s));
     h->state_pending = false;
     // the loop runs as the captured graph (which records the trace-row
     // events) unless the persistent kernel takes it

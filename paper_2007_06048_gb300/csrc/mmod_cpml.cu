@@ -29,6 +29,7 @@
 // plane k = 0 is left alone (u, psi and zeta stay 0).
 #include "mmod_cpml.h"
 #include "mmod_internal.h"
+#include "tma_ptx.cuh"
 
 namespace mmod {
 namespace {
@@ -265,6 +266,343 @@ __global__ void __launch_bounds__(128) cpml_x_warp_kernel(const CpmlArgs p, cons
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Tiled passes.  A block takes 128 lines of one layer range (z: 64 x 2 lines
+// over (x, y); y: 64 x 2 over (x, z); x: 32 x 4 rows over (y, z)) and loads
+// the whole unit with five bulk-tensor copies on one mbarrier: u^n over the
+// range and its 4-cell margins (zeros outside the grid), psi_a, zeta_a,
+// u^{n+1} and c over the range.  Each thread then marches its line from
+// shared memory (the same FP32 operations as march_range), updates psi,
+// zeta and u^{n+1} in place, and the three boxes go back by bulk-tensor
+// stores.  All of a unit's bytes are in flight at once, which the per-thread
+// marches over global memory cannot reach.
+// ---------------------------------------------------------------------------
+
+constexpr int kTileLines = 128;
+
+// Orders this thread's shared-memory writes before later bulk copies.
+__device__ __forceinline__ void fence_tile_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Tiled bulk-tensor store of a shared-memory box; elements outside the
+// tensor are not written.
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, int x, int y, int z, const float *src) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(z), "r"(smem_u32(src))
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+// Until every committed bulk store of this thread has completed.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// Until every committed bulk store of this thread has read its source.
+__device__ __forceinline__ void bulk_wait_read_all() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+template <int kLen>
+struct TileGeom {
+    static constexpr int kU = kLen + 2 * kRadius;        // u positions of a line
+    static constexpr int kUF = kU * kTileLines;          // floats of the u box
+    static constexpr int kOF = kLen * kTileLines;        // floats of each layer box
+    static constexpr int kBytes = (kUF + 4 * kOF) * 4;   // bytes of the five boxes
+};
+
+// Box shape of axis A's pass: lines (x extent, y extent, z extent) with the
+// axis extent set to `len`.
+__host__ __device__ constexpr int box_x(int A, int len) { return A == 0 ? len : 64; }
+__host__ __device__ constexpr int box_y(int A, int len) { return A == 0 ? 32 : (A == 1 ? len : 2); }
+__host__ __device__ constexpr int box_z(int A, int len) { return A == 0 ? 4 : (A == 1 ? 2 : len); }
+
+// Line t's element at position j of a box with `len` positions per line.
+template <int A, int len>
+__device__ __forceinline__ int tile_index(int t, int j) {
+    if (A == 0) return t * len + j;                               // [z][y][x]: row t, x = j
+    if (A == 1) return ((t >> 6) * len + j) * 64 + (t & 63);      // [z][y][x]: z = t >> 6, y = j
+    return j * kTileLines + t;                                    // [z][y][x]: z = j
+}
+
+// Positions [start, start + N) of line t of a box with `len` positions per
+// line into v (0 outside [0, len)); rows of the x pass in 16- or 8-byte
+// vectors where the positions allow (a row is 16-byte aligned).
+template <int A, int len, int N, int start>
+__device__ __forceinline__ void tile_get(const float *s, int t, float (&v)[N]) {
+    constexpr int lo = start < 0 ? 0 : start, hi = start + N > len ? len : start + N;
+#pragma unroll
+    for (int j = 0; j < N; ++j) v[j] = 0.0f;
+    if constexpr (A == 0 && lo % 4 == 0 && (hi - lo) % 4 == 0) {
+        const float4 *q = reinterpret_cast<const float4 *>(s + t * len + lo);
+#pragma unroll
+        for (int k = 0; k < (hi - lo) / 4; ++k) {
+            const float4 f = q[k];
+            v[lo - start + 4 * k] = f.x; v[lo - start + 4 * k + 1] = f.y;
+            v[lo - start + 4 * k + 2] = f.z; v[lo - start + 4 * k + 3] = f.w;
+        }
+    } else if constexpr (A == 0 && lo % 2 == 0 && (hi - lo) % 2 == 0) {
+        const float2 *q = reinterpret_cast<const float2 *>(s + t * len + lo);
+#pragma unroll
+        for (int k = 0; k < (hi - lo) / 2; ++k) {
+            const float2 f = q[k];
+            v[lo - start + 2 * k] = f.x; v[lo - start + 2 * k + 1] = f.y;
+        }
+    } else {
+#pragma unroll
+        for (int j = lo; j < hi; ++j) v[j - start] = s[tile_index<A, len>(t, j)];
+    }
+}
+
+// v into positions [start, start + N) of line t (all inside [0, len)).
+template <int A, int len, int N, int start>
+__device__ __forceinline__ void tile_put(float *s, int t, const float (&v)[N]) {
+    static_assert(start >= 0 && start + N <= len, "a store stays inside the line");
+    if constexpr (A == 0 && start % 4 == 0 && N % 4 == 0) {
+        float4 *q = reinterpret_cast<float4 *>(s + t * len + start);
+#pragma unroll
+        for (int k = 0; k < N / 4; ++k) q[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+    } else if constexpr (A == 0 && start % 2 == 0 && N % 2 == 0) {
+        float2 *q = reinterpret_cast<float2 *>(s + t * len + start);
+#pragma unroll
+        for (int k = 0; k < N / 2; ++k) q[k] = make_float2(v[2 * k], v[2 * k + 1]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < N; ++j) s[tile_index<A, len>(t, start + j)] = v[j];
+    }
+}
+
+// Global coordinate of line t along the slowest line axis (z for the x and y
+// passes), for the free-surface plane.
+template <int A>
+__device__ __forceinline__ int tile_line_z(int i2, int t) {
+    return A == 0 ? i2 * 4 + (t >> 5) : i2 * 2 + (t >> 6);
+}
+
+// One thread per line: psi_a, zeta_a and u^{n+1} of line t, in place, with
+// the same FP32 operations as march_range.  The range's profiles are loaded
+// once per warp (lane i holds cell i) and broadcast by shuffles; where g = 0
+// the results are selected away (psi taken as 0, the stored values kept).
+// Called by whole warps.
+template <int A, int kLen>
+__device__ __forceinline__ void tile_unit(const CpmlArgs &p, float *base, int t, int lo) {
+    static_assert(kLen <= 32, "one profile value per lane");
+    using G = TileGeom<kLen>;
+    float *su = base, *sp = su + G::kUF, *sz = sp + G::kOF, *so = sz + G::kOF, *sc = so + G::kOF;
+    const int lane = t & 31;
+    const float gl = lane < kLen ? __ldg(p.g[A] + lo + lane) : 0.0f;
+    const float bl = lane < kLen ? __ldg(p.b[A] + lo + lane) : 0.0f;
+    const float ih = p.inv_h[A];
+    float uu[G::kU], ps[kLen], v[kLen];
+    tile_get<A, G::kU, G::kU, 0>(su, t, uu);
+    tile_get<A, kLen, kLen, 0>(sp, t, v);
+    // psi^n at each cell of the range
+#pragma unroll
+    for (int i = 0; i < kLen; ++i) {
+        const float g = __shfl_sync(0xffffffffu, gl, i), b = __shfl_sync(0xffffffffu, bl, i);
+        const float nv = __fmaf_rn(b, v[i], __fmul_rn(g, d1_of(uu + i, ih)));
+        ps[i] = g != 0.0f ? nv : 0.0f;
+        v[i] = g != 0.0f ? nv : v[i];
+    }
+    tile_put<A, kLen, kLen, 0>(sp, t, v);
+    // zeta^n and the u^{n+1} term, psi taken as 0 outside the range
+    float zo[kLen], uo[kLen], co[kLen];
+    tile_get<A, kLen, kLen, 0>(sz, t, zo);
+    tile_get<A, kLen, kLen, 0>(so, t, uo);
+    tile_get<A, kLen, kLen, 0>(sc, t, co);
+#pragma unroll
+    for (int i = 0; i < kLen; ++i) {
+        const float g = __shfl_sync(0xffffffffu, gl, i), b = __shfl_sync(0xffffffffu, bl, i);
+        float pw[kLine];
+#pragma unroll
+        for (int k = 0; k < kLine; ++k) {
+            const int j = i - kRadius + k;
+            pw[k] = (j >= 0 && j < kLen) ? ps[j] : 0.0f;
+        }
+        const float d2 = d2_of(uu + i, p.w[A]);
+        const float dpsi = d1_of(pw, ih);
+        const float zn = __fmaf_rn(b, zo[i], __fmul_rn(g, __fadd_rn(d2, dpsi)));
+        const float un = __fmaf_rn(co[i], __fadd_rn(dpsi, zn), uo[i]);
+        zo[i] = g != 0.0f ? zn : zo[i];
+        uo[i] = g != 0.0f ? un : uo[i];
+    }
+    tile_put<A, kLen, kLen, 0>(sz, t, zo);
+    tile_put<A, kLen, kLen, 0>(so, t, uo);
+}
+
+// Unit -> layer-box origin (x, y, z), the range's first cell lo and the
+// slowest line-axis tile i2; r the range.
+template <int A>
+__device__ __forceinline__ void tile_origin(const Ranges &rg, int n1, int n2, int unit, int &x, int &y, int &z,
+                                            int &lo, int &i2, int &r) {
+    const int per_range = n1 * n2, rem = unit - (unit / per_range) * per_range;
+    r = unit / per_range;
+    const int i1 = rem % n1;
+    i2 = rem / n1;
+    lo = rg.lo[r];
+    x = A == 0 ? lo : i1 * 64;
+    y = A == 0 ? i1 * 32 : (A == 1 ? lo : i2 * 2);
+    z = A == 0 ? i2 * 4 : (A == 1 ? i2 * 2 : lo);
+}
+
+// Planes per range of the compact x-layer arrays: nz rounded up to the x
+// pass's 4-plane boxes, so that no box reaches into the next range.
+__host__ __device__ constexpr int compact_planes(int nz) { return (nz + 3) / 4 * 4; }
+
+// Origin of the psi, zeta and c boxes: the volumes' layer box, or for the x
+// pass the compact arrays' box (x = 0, z = r * nzp + z).
+template <int A>
+__device__ __forceinline__ void tile_aux_origin(int nz, int r, int x, int y, int z, int &ax, int &ay, int &az) {
+    ax = A == 0 ? 0 : x;
+    ay = y;
+    az = A == 0 ? r * compact_planes(nz) + z : z;
+}
+
+// Persistent over the units (unit = block + k * grid), two shared-memory
+// stages: the loads of unit k + 1 are in flight while unit k is computed;
+// a stage is refilled once the bulk stores of its previous unit have read
+// it.
+constexpr int kTileThreads = kTileLines;   // one thread per line
+
+template <int A, int kLen>
+__global__ void __launch_bounds__(kTileThreads, 2)
+    cpml_tile_kernel(const __grid_constant__ CpmlTileMaps m, const CpmlArgs p, const Ranges rg, int n1, int n2,
+                     int units) {
+    using G = TileGeom<kLen>;
+    constexpr int kStage = G::kBytes / 4;   // floats per stage
+    extern __shared__ __align__(128) float tile_smem[];
+    __shared__ __align__(8) uint64_t full[2];
+    __shared__ int abort_flag;
+    const int t = threadIdx.x;
+    auto issue = [&](int unit, int st) {   // thread 0
+        int x, y, z, lo, i2, r, ax, ay, az;
+        tile_origin<A>(rg, n1, n2, unit, x, y, z, lo, i2, r);
+        tile_aux_origin<A>(p.nz, r, x, y, z, ax, ay, az);
+        float *su = tile_smem + st * kStage, *sp = su + G::kUF, *sz = sp + G::kOF, *so = sz + G::kOF,
+              *sc = so + G::kOF;
+        mbar_expect_tx(&full[st], G::kBytes);
+        tma_load_3d(su, &m.u, A == 0 ? x - kRadius : x, A == 1 ? y - kRadius : y, A == 2 ? z - kRadius : z,
+                    &full[st]);
+        tma_load_3d(sp, &m.psi, ax, ay, az, &full[st]);
+        tma_load_3d(sz, &m.zeta, ax, ay, az, &full[st]);
+        tma_load_3d(so, &m.uout, x, y, z, &full[st]);
+        tma_load_3d(sc, &m.c, ax, ay, az, &full[st]);
+    };
+    if (t == 0) {
+        abort_flag = 0;
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_tile_shared();
+    }
+    __syncthreads();
+    if (t == 0) {
+        if ((int)blockIdx.x < units) issue(blockIdx.x, 0);
+        if ((int)(blockIdx.x + gridDim.x) < units) issue(blockIdx.x + gridDim.x, 1);
+    }
+    int k = 0;
+    for (int unit = blockIdx.x; unit < units; unit += gridDim.x, ++k) {
+        const int st = k & 1;
+        float *base = tile_smem + st * kStage;
+        const bool ready = mbar_wait(&full[st], (k >> 1) & 1, &abort_flag, p.err);
+        int x, y, z, lo, i2, r;
+        tile_origin<A>(rg, n1, n2, unit, x, y, z, lo, i2, r);
+        // the free-surface plane stays as it is (whole warps: a warp's lines share z)
+        const bool live = ready && !(A != 2 && p.fs && tile_line_z<A>(i2, t) == 0);
+        if (__all_sync(0xffffffffu, live)) tile_unit<A, kLen>(p, base, t, lo);
+        fence_tile_shared();   // this thread's shared-memory writes before the bulk stores
+        __syncthreads();
+        if (abort_flag) {      // uniform: read after the barrier
+            if (t == 0) {      // no copy may still be landing when the block exits
+                mbar_drain(&full[st], (k >> 1) & 1);
+                if (unit + (int)gridDim.x < units) mbar_drain(&full[st ^ 1], ((k + 1) >> 1) & 1);
+            }
+            break;
+        }
+        if (t == 0) {
+            float *sp = base + G::kUF, *sz = sp + G::kOF, *so = sz + G::kOF;
+            int ax, ay, az;
+            tile_aux_origin<A>(p.nz, r, x, y, z, ax, ay, az);
+            tma_store_3d(&m.psi, ax, ay, az, sp);
+            tma_store_3d(&m.zeta, ax, ay, az, sz);
+            tma_store_3d(&m.uout, x, y, z, so);
+            bulk_commit();
+            const int next = unit + 2 * (int)gridDim.x;
+            if (next < units) {
+                bulk_wait_read_all();   // the stage's stores have read it
+                issue(next, st);
+            }
+        }
+    }
+    if (t == 0) bulk_wait_all();
+}
+
+// Compiled layer widths of the tiled passes.
+constexpr int kTileWidths[] = {8, 20};
+
+template <int A, int kLen>
+cudaError_t tile_attr() {
+    return cudaFuncSetAttribute(cpml_tile_kernel<A, kLen>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                2 * TileGeom<kLen>::kBytes);
+}
+
+// Resident blocks of the persistent tiled pass on the current device.
+template <int A, int kLen>
+int tile_blocks() {
+    int dev = 0, sms = 0, occ = 0;
+    if (cudaGetDevice(&dev) || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cpml_tile_kernel<A, kLen>, kTileThreads,
+                                                      2 * TileGeom<kLen>::kBytes)) {
+        cudaGetLastError();
+        return 0;
+    }
+    return sms * occ;
+}
+
+template <int A>
+void tile_grid(const CpmlArgs &p, int *n1, int *n2) {
+    if (A == 0) {
+        *n1 = (p.ny + 31) / 32;
+        *n2 = (p.nz + 3) / 4;
+    } else {
+        *n1 = (p.nx + 63) / 64;
+        *n2 = ((A == 1 ? p.nz : p.ny) + 1) / 2;
+    }
+}
+
+template <int A, int kLen>
+cudaError_t launch_tile(const CpmlTileMaps &m, const CpmlArgs &p, const Ranges &rg, int resident, cudaStream_t s) {
+    int n1, n2;
+    tile_grid<A>(p, &n1, &n2);
+    const int units = rg.n * n1 * n2;
+    const int grid = resident > 0 && resident < units ? resident : units;
+    cpml_tile_kernel<A, kLen><<<grid, kTileThreads, 2 * TileGeom<kLen>::kBytes, s>>>(m, p, rg, n1, n2, units);
+    return cudaGetLastError();
+}
+
+template <int A>
+cudaError_t launch_tile_axis(const CpmlTiles &tl, int buffer, const CpmlArgs &p, const Ranges &rg, cudaStream_t s) {
+    return p.nbl == 8 ? launch_tile<A, 8>(tl.maps[buffer][A], p, rg, tl.resident[A], s)
+                      : launch_tile<A, 20>(tl.maps[buffer][A], p, rg, tl.resident[A], s);
+}
+
+// c_x[r][z][y][i] = c(lo_r + i, y, z) over the x layer ranges (z < nz of
+// each range's nzp planes).
+__global__ void cpml_pack_c_kernel(const CpmlArgs p, const Ranges rg, float *__restrict__ cx) {
+    const int L = p.nbl, nzp = compact_planes(p.nz);
+    const long long per = (long long)p.nz * p.ny * L, n = per * rg.n;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / per);
+        long long q = e - (long long)r * per;
+        const int i = (int)(q % L);
+        q /= L;
+        const int y = (int)(q % p.ny), z = (int)(q / p.ny);
+        cx[(((long long)r * nzp + z) * p.ny + y) * L + i] =
+            p.c[(long long)z * p.plane + (long long)y * p.nxp + rg.lo[r] + i];
+    }
+}
+
 int blocks_for(long long threads) {
     const long long b = (threads + 127) / 128;
     return (int)(b < 1 ? 1 : b);
@@ -272,30 +610,167 @@ int blocks_for(long long threads) {
 
 }  // namespace
 
-cudaError_t launch_cpml_layers(const CpmlArgs &p, const float *u, float *uout, cudaStream_t s) {
+namespace {
+
+using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                              const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn tile_encoder() {
+    static EncodeFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeFn>(f);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// A 3-D FP32 array of dims (nx, ny, nz), row and plane pitches in floats,
+// with a box of (bx, by, bz).
+bool encode_array(CUtensorMap *map, const float *base, long long nx, long long ny, long long nz, long long row,
+                  long long plane, int bx, int by, int bz) {
+    const EncodeFn fn = tile_encoder();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)row * 4, (cuuint64_t)plane * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// A padded volume (x pitch nxp, plane pitch `plane`) with a box of (bx, by, bz).
+bool encode_tile(CUtensorMap *map, const float *base, const CpmlArgs &p, int bx, int by, int bz) {
+    return encode_array(map, base, p.nx, p.ny, p.nz, p.nxp, p.plane, bx, by, bz);
+}
+
+// The x pass can run tiled: a compiled width, two layer ranges of L cells,
+// 16-byte aligned row segments (lo = 0 or nx - L, and lo - 4).
+bool x_tileable(const CpmlArgs &p, Ranges *rx) {
+    const int L = p.nbl;
+    bool width = false;
+    for (int w : kTileWidths) width = width || w == L;
+    *rx = axis_ranges(p.nx, L, false);
+    bool ok = width && rx->n > 0 && L % 4 == 0 && p.nx % 4 == 0;
+    for (int r = 0; r < rx->n; ++r) ok = ok && rx->hi[r] - rx->lo[r] == L;
+    return ok;
+}
+
+template <int A>
+bool encode_axis(const CpmlArgs &p, const float *u, const float *uout, CpmlTileMaps *m) {
+    const int L = p.nbl, lu = L + 2 * kRadius;
+    if (!encode_tile(&m->u, u, p, box_x(A, lu), box_y(A, lu), box_z(A, lu)) ||
+        !encode_tile(&m->uout, uout, p, box_x(A, L), box_y(A, L), box_z(A, L)))
+        return false;
+    if (A == 0) {   // compact [range][z][y][L] arrays: rows of L, planes of ny rows
+        Ranges rx;
+        x_tileable(p, &rx);
+        const long long zr = (long long)rx.n * compact_planes(p.nz), cnt = zr * p.ny * L;
+        return encode_array(&m->psi, p.xc, L, p.ny, zr, L, (long long)L * p.ny, L, 32, 4) &&
+               encode_array(&m->zeta, p.xc + cnt, L, p.ny, zr, L, (long long)L * p.ny, L, 32, 4) &&
+               encode_array(&m->c, p.xc + 2 * cnt, L, p.ny, zr, L, (long long)L * p.ny, L, 32, 4);
+    }
+    return encode_tile(&m->psi, p.psi[A], p, box_x(A, L), box_y(A, L), box_z(A, L)) &&
+           encode_tile(&m->zeta, p.zeta[A], p, box_x(A, L), box_y(A, L), box_z(A, L)) &&
+           encode_tile(&m->c, p.c, p, box_x(A, L), box_y(A, L), box_z(A, L));
+}
+
+}  // namespace
+
+long long cpml_x_compact_floats(const CpmlArgs &p) {
+    Ranges rx;
+    if (!x_tileable(p, &rx)) return 0;
+    return 3LL * rx.n * compact_planes(p.nz) * p.ny * p.nbl;
+}
+
+cudaError_t launch_cpml_pack_c(const CpmlArgs &p, cudaStream_t s) {
+    Ranges rx;
+    if (!p.xc || !x_tileable(p, &rx)) return cudaSuccess;
+    const long long cnt = (long long)rx.n * compact_planes(p.nz) * p.ny * p.nbl;
+    const long long blocks = ((long long)rx.n * p.nz * p.ny * p.nbl + 255) / 256;
+    cpml_pack_c_kernel<<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(p, rx, p.xc + 2 * cnt);
+    return cudaGetLastError();
+}
+
+bool make_cpml_tiles(const CpmlArgs &p, float *const u[2], CpmlTiles *t) {
+    for (int a = 0; a < 3; ++a) t->ok[a] = false;
+    const int L = p.nbl;
+    bool width = false;
+    for (int w : kTileWidths) width = width || w == L;
+    if (!width) return true;
+    const Ranges rr[3] = {axis_ranges(p.nx, L, false), axis_ranges(p.ny, L, false), axis_ranges(p.nz, L, p.fs != 0)};
+    bool ok[3];
+    for (int a = 0; a < 3; ++a) {
+        ok[a] = rr[a].n > 0;
+        for (int r = 0; r < rr[a].n; ++r) ok[a] = ok[a] && rr[a].hi[r] - rr[a].lo[r] == L;
+    }
+    // x: row segments start on 16-byte boundaries, and the compact arrays exist
+    Ranges rx;
+    ok[0] = ok[0] && x_tileable(p, &rx) && p.xc != nullptr;
+    for (int b = 0; b < 2; ++b) {
+        if (ok[0] && !encode_axis<0>(p, u[b], u[1 - b], &t->maps[b][0])) return false;
+        if (ok[1] && !encode_axis<1>(p, u[b], u[1 - b], &t->maps[b][1])) return false;
+        if (ok[2] && !encode_axis<2>(p, u[b], u[1 - b], &t->maps[b][2])) return false;
+    }
+    if (tile_attr<0, 8>() || tile_attr<1, 8>() || tile_attr<2, 8>() || tile_attr<0, 20>() || tile_attr<1, 20>() ||
+        tile_attr<2, 20>())
+        return false;
+    const bool w8 = L == 8;
+    t->resident[0] = w8 ? tile_blocks<0, 8>() : tile_blocks<0, 20>();
+    t->resident[1] = w8 ? tile_blocks<1, 8>() : tile_blocks<1, 20>();
+    t->resident[2] = w8 ? tile_blocks<2, 8>() : tile_blocks<2, 20>();
+    for (int a = 0; a < 3; ++a) ok[a] = ok[a] && t->resident[a] > 0;
+    for (int a = 0; a < 3; ++a) t->ok[a] = ok[a];
+    return true;
+}
+
+cudaError_t launch_cpml_layers(const CpmlArgs &p, const CpmlTiles *tiles, int buffer, const float *u, float *uout,
+                               cudaStream_t s, int *launches) {
+    *launches = 0;
     if (p.nbl <= 0) return cudaSuccess;
     const int per = p.zc > 0 ? p.zc : kCpmlPlanes;
     const Ranges rx = axis_ranges(p.nx, p.nbl, false), ry = axis_ranges(p.ny, p.nbl, false),
                  rz = axis_ranges(p.nz, p.nbl, p.fs != 0);
+    const bool use = tiles && p.tiles && (buffer == 0 || buffer == 1);
     bool x_warp = true;
     for (int r = 0; r < rx.n; ++r) x_warp = x_warp && rx.hi[r] - rx.lo[r] <= kWarpCells;
     const long long xl = (long long)p.ny * p.nz * rx.n, yl = (long long)p.nx * p.nz * ry.n,
                     zl = (long long)p.nx * p.ny * rz.n;
     if (rx.n > 0) {
-        if (x_warp)
+        if (use && tiles->ok[0])
+            launch_tile_axis<0>(*tiles, buffer, p, rx, s);
+        else if (x_warp)
             cpml_x_warp_kernel<<<blocks_for(((xl + (long long)per * kRows - 1) / ((long long)per * kRows)) * 32), 128,
                                  0, s>>>(p, rx, u, uout);
         else
             cpml_line_kernel<0><<<blocks_for((xl + per - 1) / per), 128, 0, s>>>(p, rx, u, uout);
         if (cudaError_t e = cudaGetLastError()) return e;
+        ++*launches;
     }
     if (ry.n > 0) {
-        cpml_line_kernel<1><<<blocks_for((yl + per - 1) / per), 128, 0, s>>>(p, ry, u, uout);
+        if (use && tiles->ok[1])
+            launch_tile_axis<1>(*tiles, buffer, p, ry, s);
+        else
+            cpml_line_kernel<1><<<blocks_for((yl + per - 1) / per), 128, 0, s>>>(p, ry, u, uout);
         if (cudaError_t e = cudaGetLastError()) return e;
+        ++*launches;
     }
     if (rz.n > 0) {
-        cpml_line_kernel<2><<<blocks_for((zl + per - 1) / per), 128, 0, s>>>(p, rz, u, uout);
+        if (use && tiles->ok[2])
+            launch_tile_axis<2>(*tiles, buffer, p, rz, s);
+        else
+            cpml_line_kernel<2><<<blocks_for((zl + per - 1) / per), 128, 0, s>>>(p, rz, u, uout);
         if (cudaError_t e = cudaGetLastError()) return e;
+        ++*launches;
     }
     return cudaSuccess;
 }

@@ -103,6 +103,10 @@ struct mmod_handle {
     int *claim_ctr = nullptr;           // {next unit, CTAs done} of work-claiming step launches
     float *cpml_mem = nullptr;          // CPML: psi_x, psi_y, psi_z, zeta_x, zeta_y, zeta_z volumes
     float *cpml_bg = nullptr;           // CPML: b_x | b_y | b_z | g_x | g_y | g_z per cell
+    float *cpml_xc = nullptr;           // CPML: compact x layers of the tiled pass (psi_x | zeta_x | c_x)
+    long long cpml_xc_floats = 0;
+    mmod::CpmlTiles cpml_tiles{};       // CPML: tensor maps of the tiled layer passes
+    int cpml_tiles_on = 1;              // MMOD_OPT_CPML_TILES
     mutable mmod::TmaPlan plan_tmp;     // active_plan() with the override applied
     mutable mmod::TmaPlan plan_tmp_g;   // the same for the steps that write g^n
     int *counters = nullptr;            // per work unit of the persistent kernel

@@ -26,8 +26,11 @@ def trace_err(tr_g, tr_o, u_o):
 # the layer passes work on ranges along each axis: 26-cell x layers take the
 # line march (wider than a warp segment), 18 points with 8-cell layers merge
 # both x ranges into one, 18-cell layers leave a 4-cell gap
+# both ranges apart; 20- and 8-cell layers (with nx a multiple of 4) run the
+# tiled passes, over tiles that are ragged along every line axis
 CASES = [((40, 36, 70), 6, False), ((33, 64, 131), 8, False), ((9, 20, 9), 2, False), ((30, 28, 70), 5, True),
-         ((64, 20, 40), 0, False), ((60, 60, 70), 26, False), ((30, 40, 18), 8, False), ((36, 40, 40), 18, True)]
+         ((64, 20, 40), 0, False), ((60, 60, 70), 26, False), ((30, 40, 18), 8, False), ((36, 40, 40), 18, True),
+         ((47, 71, 100), 20, False), ((47, 71, 100), 20, True), ((40, 37, 68), 8, True)]
 
 
 @pytest.mark.parametrize("shape,nbl,fs", CASES, ids=[f"{s}-L{n}-fs{int(f)}" for s, n, f in CASES])
@@ -84,6 +87,27 @@ def test_cpml_planes_per_thread_keep_bits(fs):
     for planes in (1, 3, 7, 100):
         tr_p, u_p, _ = run_gpu(p, options={M.OPT_CPML_PLANES: planes})
         assert np.array_equal(u_p, u_d) and np.array_equal(tr_p, tr_d), planes
+
+
+TILE_CASES = [((47, 71, 100), 20, False), ((47, 71, 100), 20, True), ((40, 37, 68), 8, False),
+              ((41, 37, 68), 8, True), ((33, 64, 131), 8, False)]
+
+
+@pytest.mark.parametrize("shape,nbl,fs", TILE_CASES, ids=[f"{s}-L{n}-fs{int(f)}" for s, n, f in TILE_CASES])
+def test_cpml_tiled_passes_keep_bits(shape, nbl, fs):
+    """The tiled layer passes (whole units in shared memory by bulk-tensor
+    copies) take the marching passes' FP32 operations: the same bits, with
+    sources and receivers inside the layers."""
+    nz, ny, nx = shape
+    p = _cpml(W.tiny_problem(shape=shape, nt=50, nbl=nbl, nsrc=3, nrec=16, seed=nx + nbl), fs=fs)
+    p.src_ijk[0] = [2, ny - 3, nz - 2]
+    p.src_ijk[1] = [nx - 5, 4, nz // 2]
+    p.rec_ijk[0] = [0, 0, nz - 1]
+    p.rec_ijk[1] = [nx - 1, ny // 2, 1]
+    tr_m, u_m, _ = run_gpu(p, options={M.OPT_CPML_TILES: 0})
+    tr_t, u_t, _ = run_gpu(p, options={M.OPT_CPML_TILES: 1})
+    assert np.abs(u_m).max() > 0
+    assert np.array_equal(u_t, u_m) and np.array_equal(tr_t, tr_m)
 
 
 def test_cpml_absorbs_on_the_gpu():
