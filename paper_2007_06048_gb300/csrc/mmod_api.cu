@@ -437,8 +437,12 @@ static mmod_status enqueue_loop(mmod_handle *h, const Geometry &geo, const float
     if (is_cpml(h)) {
         // CPML: the undamped step (sources included), the layer terms of
         // u^{n+1}, then (plain kernel) the receivers of u^{n+1}
-        const CpmlArgs cp = cpml_args(h);
-        a.pdl = 0;
+        // with PDL each kernel requests the data its predecessors do not
+        // write before its wait: the step kernel c and u^{n-1} (the layer
+        // passes only read u^n), a tiled pass u^n, psi_a, zeta_a and c
+        CpmlArgs cp = cpml_args(h);
+        cp.pdl = h->pdl;
+        a.pdl = h->pdl ? 2 : 0;
         for (int n = 0; n < nt; ++n) {
             a.n = n;
             a.ucur = h->u[(n + 1) & 1];

@@ -268,8 +268,8 @@ __global__ void __launch_bounds__(128) cpml_x_warp_kernel(const CpmlArgs p, cons
 
 
 // ---------------------------------------------------------------------------
-// Tiled passes.  A block takes 128 lines of one layer range (z: 64 x 2 lines
-// over (x, y); y: 64 x 2 over (x, z); x: 32 x 4 rows over (y, z)) and loads
+// Tiled passes.  A unit is 2 W lines of one layer range (z: W x 2 lines over
+// (x, y); y: W x 2 over (x, z); x: W x 2 rows over (y, z)) and a block loads
 // the whole unit with five bulk-tensor copies on one mbarrier: u^n over the
 // range and its 4-cell margins (zeros outside the grid), psi_a, zeta_a,
 // u^{n+1} and c over the range.  Each thread then marches its line from
@@ -279,7 +279,8 @@ __global__ void __launch_bounds__(128) cpml_x_warp_kernel(const CpmlArgs p, cons
 // marches over global memory cannot reach.
 // ---------------------------------------------------------------------------
 
-constexpr int kTileLines = 128;
+constexpr int kTileW = 32;                 // line-box width W
+constexpr int kTileLines = 2 * kTileW;     // lines per unit
 
 // Orders this thread's shared-memory writes before later bulk copies.
 __device__ __forceinline__ void fence_tile_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -313,15 +314,15 @@ struct TileGeom {
 
 // Box shape of axis A's pass: lines (x extent, y extent, z extent) with the
 // axis extent set to `len`.
-__host__ __device__ constexpr int box_x(int A, int len) { return A == 0 ? len : 64; }
-__host__ __device__ constexpr int box_y(int A, int len) { return A == 0 ? 32 : (A == 1 ? len : 2); }
-__host__ __device__ constexpr int box_z(int A, int len) { return A == 0 ? 4 : (A == 1 ? 2 : len); }
+__host__ __device__ constexpr int box_x(int A, int len) { return A == 0 ? len : kTileW; }
+__host__ __device__ constexpr int box_y(int A, int len) { return A == 0 ? kTileW : (A == 1 ? len : 2); }
+__host__ __device__ constexpr int box_z(int A, int len) { return A == 2 ? len : 2; }
 
 // Line t's element at position j of a box with `len` positions per line.
 template <int A, int len>
 __device__ __forceinline__ int tile_index(int t, int j) {
     if (A == 0) return t * len + j;                               // [z][y][x]: row t, x = j
-    if (A == 1) return ((t >> 6) * len + j) * 64 + (t & 63);      // [z][y][x]: z = t >> 6, y = j
+    if (A == 1) return ((t / kTileW) * len + j) * kTileW + t % kTileW;   // [z][y][x]: z = t / W, y = j
     return j * kTileLines + t;                                    // [z][y][x]: z = j
 }
 
@@ -376,16 +377,16 @@ __device__ __forceinline__ void tile_put(float *s, int t, const float (&v)[N]) {
 // passes), for the free-surface plane.
 template <int A>
 __device__ __forceinline__ int tile_line_z(int i2, int t) {
-    return A == 0 ? i2 * 4 + (t >> 5) : i2 * 2 + (t >> 6);
+    return i2 * 2 + t / kTileW;
 }
 
 // One thread per line: psi_a, zeta_a and u^{n+1} of line t, in place, with
 // the same FP32 operations as march_range.  The range's profiles are loaded
 // once per warp (lane i holds cell i) and broadcast by shuffles; where g = 0
 // the results are selected away (psi taken as 0, the stored values kept).
-// Called by whole warps.
+// Called by whole warps; lines that are not live write nothing back.
 template <int A, int kLen>
-__device__ __forceinline__ void tile_unit(const CpmlArgs &p, float *base, int t, int lo) {
+__device__ __forceinline__ void tile_unit(const CpmlArgs &p, float *base, int t, int lo, bool live) {
     static_assert(kLen <= 32, "one profile value per lane");
     using G = TileGeom<kLen>;
     float *su = base, *sp = su + G::kUF, *sz = sp + G::kOF, *so = sz + G::kOF, *sc = so + G::kOF;
@@ -404,7 +405,7 @@ __device__ __forceinline__ void tile_unit(const CpmlArgs &p, float *base, int t,
         ps[i] = g != 0.0f ? nv : 0.0f;
         v[i] = g != 0.0f ? nv : v[i];
     }
-    tile_put<A, kLen, kLen, 0>(sp, t, v);
+    if (live) tile_put<A, kLen, kLen, 0>(sp, t, v);
     // zeta^n and the u^{n+1} term, psi taken as 0 outside the range
     float zo[kLen], uo[kLen], co[kLen];
     tile_get<A, kLen, kLen, 0>(sz, t, zo);
@@ -426,8 +427,10 @@ __device__ __forceinline__ void tile_unit(const CpmlArgs &p, float *base, int t,
         zo[i] = g != 0.0f ? zn : zo[i];
         uo[i] = g != 0.0f ? un : uo[i];
     }
-    tile_put<A, kLen, kLen, 0>(sz, t, zo);
-    tile_put<A, kLen, kLen, 0>(so, t, uo);
+    if (live) {
+        tile_put<A, kLen, kLen, 0>(sz, t, zo);
+        tile_put<A, kLen, kLen, 0>(so, t, uo);
+    }
 }
 
 // Unit -> layer-box origin (x, y, z), the range's first cell lo and the
@@ -440,14 +443,14 @@ __device__ __forceinline__ void tile_origin(const Ranges &rg, int n1, int n2, in
     const int i1 = rem % n1;
     i2 = rem / n1;
     lo = rg.lo[r];
-    x = A == 0 ? lo : i1 * 64;
-    y = A == 0 ? i1 * 32 : (A == 1 ? lo : i2 * 2);
-    z = A == 0 ? i2 * 4 : (A == 1 ? i2 * 2 : lo);
+    x = A == 0 ? lo : i1 * kTileW;
+    y = A == 0 ? i1 * kTileW : (A == 1 ? lo : i2 * 2);
+    z = A == 2 ? lo : i2 * 2;
 }
 
 // Planes per range of the compact x-layer arrays: nz rounded up to the x
-// pass's 4-plane boxes, so that no box reaches into the next range.
-__host__ __device__ constexpr int compact_planes(int nz) { return (nz + 3) / 4 * 4; }
+// pass's 2-plane boxes, so that no box reaches into the next range.
+__host__ __device__ constexpr int compact_planes(int nz) { return (nz + 1) / 2 * 2; }
 
 // Origin of the psi, zeta and c boxes: the volumes' layer box, or for the x
 // pass the compact arrays' box (x = 0, z = r * nzp + z).
@@ -474,19 +477,23 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     __shared__ __align__(8) uint64_t full[2];
     __shared__ int abort_flag;
     const int t = threadIdx.x;
-    auto issue = [&](int unit, int st) {   // thread 0
+    // thread 0: a unit's copies into stage st; `stable` the four that no
+    // earlier pass of the step writes (u^n, psi_a, zeta_a, c), `after` u^{n+1}
+    auto issue = [&](int unit, int st, bool stable, bool after) {
         int x, y, z, lo, i2, r, ax, ay, az;
         tile_origin<A>(rg, n1, n2, unit, x, y, z, lo, i2, r);
         tile_aux_origin<A>(p.nz, r, x, y, z, ax, ay, az);
         float *su = tile_smem + st * kStage, *sp = su + G::kUF, *sz = sp + G::kOF, *so = sz + G::kOF,
               *sc = so + G::kOF;
-        mbar_expect_tx(&full[st], G::kBytes);
-        tma_load_3d(su, &m.u, A == 0 ? x - kRadius : x, A == 1 ? y - kRadius : y, A == 2 ? z - kRadius : z,
-                    &full[st]);
-        tma_load_3d(sp, &m.psi, ax, ay, az, &full[st]);
-        tma_load_3d(sz, &m.zeta, ax, ay, az, &full[st]);
-        tma_load_3d(so, &m.uout, x, y, z, &full[st]);
-        tma_load_3d(sc, &m.c, ax, ay, az, &full[st]);
+        if (stable) {
+            mbar_expect_tx(&full[st], G::kBytes);
+            tma_load_3d(su, &m.u, A == 0 ? x - kRadius : x, A == 1 ? y - kRadius : y, A == 2 ? z - kRadius : z,
+                        &full[st]);
+            tma_load_3d(sp, &m.psi, ax, ay, az, &full[st]);
+            tma_load_3d(sz, &m.zeta, ax, ay, az, &full[st]);
+            tma_load_3d(sc, &m.c, ax, ay, az, &full[st]);
+        }
+        if (after) tma_load_3d(so, &m.uout, x, y, z, &full[st]);
     };
     if (t == 0) {
         abort_flag = 0;
@@ -496,9 +503,20 @@ __global__ void __launch_bounds__(kTileThreads, 2)
         fence_tile_shared();
     }
     __syncthreads();
+    // the first two units' copies of data the previous kernels of the step do
+    // not write go out before the programmatic-launch wait, u^{n+1} after it
+    const bool have0 = (int)blockIdx.x < units, have1 = (int)(blockIdx.x + gridDim.x) < units;
     if (t == 0) {
-        if ((int)blockIdx.x < units) issue(blockIdx.x, 0);
-        if ((int)(blockIdx.x + gridDim.x) < units) issue(blockIdx.x + gridDim.x, 1);
+        if (have0) issue(blockIdx.x, 0, true, false);
+        if (have1) issue(blockIdx.x + gridDim.x, 1, true, false);
+    }
+    if (p.pdl) {
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    }
+    if (t == 0) {
+        if (have0) issue(blockIdx.x, 0, false, true);
+        if (have1) issue(blockIdx.x + gridDim.x, 1, false, true);
     }
     int k = 0;
     for (int unit = blockIdx.x; unit < units; unit += gridDim.x, ++k) {
@@ -507,9 +525,10 @@ __global__ void __launch_bounds__(kTileThreads, 2)
         const bool ready = mbar_wait(&full[st], (k >> 1) & 1, &abort_flag, p.err);
         int x, y, z, lo, i2, r;
         tile_origin<A>(rg, n1, n2, unit, x, y, z, lo, i2, r);
-        // the free-surface plane stays as it is (whole warps: a warp's lines share z)
+        // every lane computes (the profiles are shuffled across the warp); the
+        // free-surface plane keeps its values
         const bool live = ready && !(A != 2 && p.fs && tile_line_z<A>(i2, t) == 0);
-        if (__all_sync(0xffffffffu, live)) tile_unit<A, kLen>(p, base, t, lo);
+        tile_unit<A, kLen>(p, base, t, lo, live);
         fence_tile_shared();   // this thread's shared-memory writes before the bulk stores
         __syncthreads();
         if (abort_flag) {      // uniform: read after the barrier
@@ -530,7 +549,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
             const int next = unit + 2 * (int)gridDim.x;
             if (next < units) {
                 bulk_wait_read_all();   // the stage's stores have read it
-                issue(next, st);
+                issue(next, st, true, true);
             }
         }
     }
@@ -562,10 +581,10 @@ int tile_blocks() {
 template <int A>
 void tile_grid(const CpmlArgs &p, int *n1, int *n2) {
     if (A == 0) {
-        *n1 = (p.ny + 31) / 32;
-        *n2 = (p.nz + 3) / 4;
+        *n1 = (p.ny + kTileW - 1) / kTileW;
+        *n2 = (p.nz + 1) / 2;
     } else {
-        *n1 = (p.nx + 63) / 64;
+        *n1 = (p.nx + kTileW - 1) / kTileW;
         *n2 = ((A == 1 ? p.nz : p.ny) + 1) / 2;
     }
 }
@@ -574,10 +593,22 @@ template <int A, int kLen>
 cudaError_t launch_tile(const CpmlTileMaps &m, const CpmlArgs &p, const Ranges &rg, int resident, cudaStream_t s) {
     int n1, n2;
     tile_grid<A>(p, &n1, &n2);
+    // as many units per block everywhere: ceil(units / resident) rounds, and
+    // only as many blocks as those rounds need
     const int units = rg.n * n1 * n2;
-    const int grid = resident > 0 && resident < units ? resident : units;
-    cpml_tile_kernel<A, kLen><<<grid, kTileThreads, 2 * TileGeom<kLen>::kBytes, s>>>(m, p, rg, n1, n2, units);
-    return cudaGetLastError();
+    const int rounds = resident > 0 ? (units + resident - 1) / resident : 1;
+    const int grid = (units + rounds - 1) / rounds;
+    cudaLaunchConfig_t lc{};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.gridDim = dim3(grid);
+    lc.blockDim = dim3(kTileThreads);
+    lc.dynamicSmemBytes = 2 * TileGeom<kLen>::kBytes;
+    lc.stream = s;
+    lc.attrs = at;
+    lc.numAttrs = p.pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&lc, cpml_tile_kernel<A, kLen>, m, p, rg, n1, n2, units);
 }
 
 template <int A>
@@ -675,9 +706,9 @@ bool encode_axis(const CpmlArgs &p, const float *u, const float *uout, CpmlTileM
         Ranges rx;
         x_tileable(p, &rx);
         const long long zr = (long long)rx.n * compact_planes(p.nz), cnt = zr * p.ny * L;
-        return encode_array(&m->psi, p.xc, L, p.ny, zr, L, (long long)L * p.ny, L, 32, 4) &&
-               encode_array(&m->zeta, p.xc + cnt, L, p.ny, zr, L, (long long)L * p.ny, L, 32, 4) &&
-               encode_array(&m->c, p.xc + 2 * cnt, L, p.ny, zr, L, (long long)L * p.ny, L, 32, 4);
+        return encode_array(&m->psi, p.xc, L, p.ny, zr, L, (long long)L * p.ny, L, kTileW, 2) &&
+               encode_array(&m->zeta, p.xc + cnt, L, p.ny, zr, L, (long long)L * p.ny, L, kTileW, 2) &&
+               encode_array(&m->c, p.xc + 2 * cnt, L, p.ny, zr, L, (long long)L * p.ny, L, kTileW, 2);
     }
     return encode_tile(&m->psi, p.psi[A], p, box_x(A, L), box_y(A, L), box_z(A, L)) &&
            encode_tile(&m->zeta, p.zeta[A], p, box_x(A, L), box_y(A, L), box_z(A, L)) &&

@@ -21,6 +21,7 @@ struct CpmlArgs {
     const float *c;
     int zc;      // layer lines per thread (y, z passes) or row segments per warp (x pass), about
     int tiles;   // 1: tiled passes on the axes that allow them
+    int pdl;     // 1: tiled passes as programmatic dependent launches
     int *err;    // device view of the handle's error word (a bounded wait gave up)
     // x layers of the tiled pass in compact form, each [range][nzp][y][L]
     // with nzp = nz rounded up to a multiple of 4: psi_x | zeta_x | c_x

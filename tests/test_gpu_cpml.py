@@ -104,10 +104,11 @@ def test_cpml_tiled_passes_keep_bits(shape, nbl, fs):
     p.src_ijk[1] = [nx - 5, 4, nz // 2]
     p.rec_ijk[0] = [0, 0, nz - 1]
     p.rec_ijk[1] = [nx - 1, ny // 2, 1]
-    tr_m, u_m, _ = run_gpu(p, options={M.OPT_CPML_TILES: 0})
-    tr_t, u_t, _ = run_gpu(p, options={M.OPT_CPML_TILES: 1})
+    tr_m, u_m, _ = run_gpu(p, options={M.OPT_CPML_TILES: 0}, pdl=0)
     assert np.abs(u_m).max() > 0
-    assert np.array_equal(u_t, u_m) and np.array_equal(tr_t, tr_m)
+    for pdl in (0, 1):   # chained by programmatic dependent launch, or in stream order
+        tr_t, u_t, _ = run_gpu(p, options={M.OPT_CPML_TILES: 1}, pdl=pdl)
+        assert np.array_equal(u_t, u_m) and np.array_equal(tr_t, tr_m), pdl
 
 
 def test_cpml_absorbs_on_the_gpu():
