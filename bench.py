@@ -390,7 +390,8 @@ def summarize(value, roofline, extra):
         out["free_surface"] = {"gpts": _r(extra["free_surface"]["value"], 1)}
     if "cpml" in extra:
         c = extra["cpml"]
-        out["cpml"] = {"gpts": _r(c["value"], 1), "vs_fwd": _r(c["vs_forward"]), "frac": _r(c["roofline"]["frac"])}
+        out["cpml"] = {"gpts": _r(c["value"], 1), "vs_fwd": _r(c["vs_forward"]), "frac": _r(c["roofline"]["frac"]),
+                       "passes_frac": c["layer_passes"]["frac"]}
     if "variable_density" in extra:
         v = extra["variable_density"]
         out["variable_density"] = {"gpts": _r(v["value"], 1), "frac": _r(v["roofline"]["frac"]),
@@ -579,10 +580,22 @@ def measure_cpml(M, dev, stream, fwd_gpts, nt=1000, reps=3):
     roof = roofline_of((BYTES_PER_POINT * p.npoints + lb) * p.nt, ms, load_peaks()[0],
                        f"per step 16 B per point (step kernel) + 16 + 16k B per layer cell with k axes in their "
                        f"layers (u^n, c, u^{{n+1}} once; psi_a, zeta_a per axis): {cells} layer cells, {axes} cell-axes")
+    # the layer passes alone: the step's time less the forward run's time per
+    # step (the same step kernel), against their own algorithmic bytes
+    step_us = 1e3 * ms / p.nt
+    fwd_us = 1e6 * p.npoints / (fwd_gpts * 1e9)
+    pass_us = step_us - fwd_us
+    peak = load_peaks()[0]
+    passes = {"bytes_per_step": lb, "us_per_step": _r(pass_us, 2),
+              "gbs": _r(lb / (pass_us * 1e-6) / 1e9, 1) if pass_us > 0 else None,
+              "frac": _r(lb / (pass_us * 1e-6) / 1e9 / peak) if pass_us > 0 and peak else None,
+              "note": "us per step less the forward run's us per step"}
     return {"value": v, "unit": UNIT, "ms": ms, "vs_forward": v / fwd_gpts, "workload": p.name + " + CPML (L=20)",
-            "roofline": roof, "layer_bytes_per_step": lb,
-            "what": "per step: the undamped step kernel, then one pass per axis over the layer ranges of the "
-                    "lines along it (psi_a^n, zeta_a^n and the u^{n+1} correction)"}
+            "roofline": roof, "layer_bytes_per_step": lb, "layer_passes": passes,
+            "what": "per step: the undamped step kernel, then one tiled pass per axis (units of 64 lines of a "
+                    "layer range loaded whole into shared memory by bulk-tensor copies, two stages per block; "
+                    "psi_a^n, zeta_a^n and the u^{n+1} correction), the four kernels chained by programmatic "
+                    "dependent launch"}
 
 
 VD_BYTES_PER_POINT = 56   # velocity kernel 32 B + pressure kernel 24 B (FP32)
