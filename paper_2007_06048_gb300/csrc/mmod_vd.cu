@@ -361,7 +361,7 @@ __device__ __forceinline__ void v_read_q(const VCtx &c, int seq, float2 (&dst)[R
     for (int r = 0; r < RY; ++r) dst[r] = *reinterpret_cast<const float2 *>(base + r * PHX);
 }
 
-template <int J>
+template <int J, bool C>
 __device__ __forceinline__ bool v_plane(const VdArgs &a, const VCtx &c, int t, float2 (&q)[2 * kRadius][RY]) {
     const int k = c.z0 + t;
     if (!(mbar_wait(&c.bar_p[(t + 7) % VNSP], ((t + 7) / VNSP) & 1, c.abort_flag, a.err) &&
@@ -374,8 +374,8 @@ __device__ __forceinline__ bool v_plane(const VdArgs &a, const VCtx &c, int t, f
     const float *own = c.ring_o + (t % VNSO) * V_SLOT_O;
     const float *bk = c.ring_b + (t % VNSB) * V_SLOT_B;
     const float *bk1 = c.ring_b + ((t + 1) % VNSB) * V_SLOT_B;
-    const bool zl = !a.cpml && (k < a.nbl || k >= a.nz - 1 - a.nbl);
-    const float egz = a.cpml ? 0.0f : a.eg[2][k], ehz = a.cpml ? 0.0f : a.eh[2][k];
+    const bool zl = !C && (k < a.nbl || k >= a.nz - 1 - a.nbl);
+    const float egz = C ? 0.0f : a.eg[2][k], ehz = C ? 0.0f : a.eh[2][k];
     const bool zin = k + 1 < a.nz;
     // y neighbours: rows 2w+1 .. 2w+9 of the centre tile, columns xl+4, xl+5
     float2 yc[RY + 2 * kRadius - 1];
@@ -417,7 +417,7 @@ __device__ __forceinline__ bool v_plane(const VdArgs &a, const VCtx &c, int t, f
         const bool in0 = c.in0 && y < a.ny, in1 = c.in1 && y < a.ny;
         const long long o = (long long)k * a.plane + (long long)y * a.nxp + c.x;
         float2 nx_, ny_, nz_;
-        if (!a.cpml && (c.lay_xy[r] || zl)) {
+        if (!C && (c.lay_xy[r] || zl)) {
             // eps = (e_x + e_y) + e_z at each component's own position
             const float2 ex = __fadd2_rn(__fadd2_rn(c.ehx, bc2(c.egy[r])), bc2(egz));
             const float2 ey = __fadd2_rn(__fadd2_rn(c.egx, bc2(c.ehy[r])), bc2(egz));
@@ -425,7 +425,7 @@ __device__ __forceinline__ bool v_plane(const VdArgs &a, const VCtx &c, int t, f
             nx_ = relax2(vx, bhx, dx, ex);
             ny_ = relax2(vy, bhy, dy, ey);
             nz_ = relax2(vz, bhz, dz, ez);
-        } else if (a.cpml) {
+        } else if (C) {
             const float2 ddx = cpml_pair(a.psi[0] + o, a.Bh[0], a.Gh[0], c.x, c.x + 1, a.nx, in0, in1, dx);
             const float2 ddy = cpml_pair(a.psi[1] + o, a.Bh[1], a.Gh[1], y, y, a.ny, in0, in1, dy);
             const float2 ddz = cpml_pair(a.psi[2] + o, a.Bh[2], a.Gh[2], k, k, a.nz, in0, in1, dz);
@@ -444,6 +444,7 @@ __device__ __forceinline__ bool v_plane(const VdArgs &a, const VCtx &c, int t, f
     return true;
 }
 
+template <bool C>
 __global__ void __launch_bounds__(NT, 2)
     vd_velocity_tma(const __grid_constant__ VdArgs a, const __grid_constant__ VdMaps maps, VdGeom g) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -513,15 +514,15 @@ __global__ void __launch_bounds__(NT, 2)
     c.x = x0 + c.xl;
     c.in0 = c.x < a.nx;
     c.in1 = c.x + 1 < a.nx;
-    c.egx = a.cpml ? bc2(0.0f) : make_float2(a.eg[0][zero_clip(c.x, a.nx)], a.eg[0][zero_clip(c.x + 1, a.nx)]);
-    c.ehx = a.cpml ? bc2(0.0f) : make_float2(a.eh[0][zero_clip(c.x, a.nx)], a.eh[0][zero_clip(c.x + 1, a.nx)]);
+    c.egx = C ? bc2(0.0f) : make_float2(a.eg[0][zero_clip(c.x, a.nx)], a.eg[0][zero_clip(c.x + 1, a.nx)]);
+    c.ehx = C ? bc2(0.0f) : make_float2(a.eh[0][zero_clip(c.x, a.nx)], a.eh[0][zero_clip(c.x + 1, a.nx)]);
     // the half point after the last inner index (n - 1 - nbl) already lies in the layer
     const bool lay_x = x0 < a.nbl || x0 + TX - 1 >= a.nx - 1 - a.nbl;
 #pragma unroll
     for (int r = 0; r < RY; ++r) {
         const int y = y0 + RY * c.warp + r, yi = zero_clip(y, a.ny);
-        c.egy[r] = a.cpml ? 0.0f : a.eg[1][yi];
-        c.ehy[r] = a.cpml ? 0.0f : a.eh[1][yi];
+        c.egy[r] = C ? 0.0f : a.eg[1][yi];
+        c.ehy[r] = C ? 0.0f : a.eh[1][yi];
         c.lay_xy[r] = lay_x || y < a.nbl || y >= a.ny - 1 - a.nbl;
     }
 
@@ -552,7 +553,7 @@ __global__ void __launch_bounds__(NT, 2)
     // end of step t: the centre tile (seq t+3), the own tile and b plane k are free
 #define VD_VSTEP(J)                                                                   \
     if (t + (J) < T) {                                                                \
-        v_plane<(J)>(a, c, t + (J), q);                                               \
+        v_plane<(J), C>(a, c, t + (J), q);                                               \
         __syncthreads();                                                              \
         if (*c.abort_flag) break;                                                     \
         if (tid == 0) {                                                               \
@@ -598,7 +599,7 @@ __device__ __forceinline__ void p_read_q(const PCtx &c, int seq, float2 (&dst)[R
     for (int r = 0; r < RY; ++r) dst[r] = *reinterpret_cast<const float2 *>(base + r * TX);
 }
 
-template <int J>
+template <int J, bool C>
 __device__ __forceinline__ bool p_plane(const VdArgs &a, const PCtx &c, int t, float2 (&q)[2 * kRadius][RY]) {
     const int k = c.z0 + t;
     if (!(mbar_wait(&c.bar_z[(t + 7) % PNSZ], ((t + 7) / PNSZ) & 1, c.abort_flag, a.err) &&
@@ -607,8 +608,8 @@ __device__ __forceinline__ bool p_plane(const VdArgs &a, const PCtx &c, int t, f
     p_read_q(c, t + 7, q[(J + 7) % 8]);
     const float *base = c.ring_c + (t % PNSC) * P_SLOT_C;
     const float *tvx = base, *tvy = base + P_VX, *tp = base + P_VX + P_VY, *tk = tp + OWN;
-    const bool zl = !a.cpml && (k < a.nbl || k > a.nz - 1 - a.nbl);
-    const float egz = a.cpml ? 0.0f : a.eg[2][k];
+    const bool zl = !C && (k < a.nbl || k > a.nz - 1 - a.nbl);
+    const float egz = C ? 0.0f : a.eg[2][k];
     // vy rows 2w .. 2w+8 at columns xl, xl+1
     float2 yc[RY + 2 * kRadius - 1];
 #pragma unroll
@@ -632,7 +633,7 @@ __device__ __forceinline__ bool p_plane(const VdArgs &a, const PCtx &c, int t, f
                                q[(J + 6) % 8][r], q[(J + 1) % 8][r], q[(J + 7) % 8][r], q[(J + 0) % 8][r]);
         const bool in0 = c.in0 && y < a.ny, in1 = c.in1 && y < a.ny;
         const long long o = (long long)k * a.plane + (long long)y * a.nxp + c.x;
-        if (a.cpml) {
+        if (C) {
             dx = cpml_pair(a.phi[0] + o, a.Bg[0], a.Gg[0], c.x, c.x + 1, a.nx, in0, in1, dx);
             dy = cpml_pair(a.phi[1] + o, a.Bg[1], a.Gg[1], y, y, a.ny, in0, in1, dy);
             dz = cpml_pair(a.phi[2] + o, a.Bg[2], a.Gg[2], k, k, a.nz, in0, in1, dz);
@@ -643,7 +644,7 @@ __device__ __forceinline__ bool p_plane(const VdArgs &a, const PCtx &c, int t, f
         float2 pn;
         if (a.fs && k == 0)
             pn = make_float2(0.0f, 0.0f);   // p = 0 on the free surface
-        else if (!a.cpml && (c.lay_xy[r] || zl))
+        else if (!C && (c.lay_xy[r] || zl))
             pn = relax2(po, ko, div, __fadd2_rn(__fadd2_rn(c.egx, bc2(c.egy[r])), bc2(egz)));
         else
             pn = undamped2(po, ko, div);
@@ -652,6 +653,7 @@ __device__ __forceinline__ bool p_plane(const VdArgs &a, const PCtx &c, int t, f
     return true;
 }
 
+template <bool C>
 __global__ void __launch_bounds__(NT, 2)
     vd_pressure_tma(const __grid_constant__ VdArgs a, const __grid_constant__ VdMaps maps, VdGeom g) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -720,12 +722,12 @@ __global__ void __launch_bounds__(NT, 2)
     c.x = x0 + c.xl;
     c.in0 = c.x < a.nx;
     c.in1 = c.x + 1 < a.nx;
-    c.egx = a.cpml ? bc2(0.0f) : make_float2(a.eg[0][zero_clip(c.x, a.nx)], a.eg[0][zero_clip(c.x + 1, a.nx)]);
+    c.egx = C ? bc2(0.0f) : make_float2(a.eg[0][zero_clip(c.x, a.nx)], a.eg[0][zero_clip(c.x + 1, a.nx)]);
     const bool lay_x = x0 < a.nbl || x0 + TX - 1 > a.nx - 1 - a.nbl;
 #pragma unroll
     for (int r = 0; r < RY; ++r) {
         const int y = y0 + RY * c.warp + r;
-        c.egy[r] = a.cpml ? 0.0f : a.eg[1][zero_clip(y, a.ny)];
+        c.egy[r] = C ? 0.0f : a.eg[1][zero_clip(y, a.ny)];
         c.lay_xy[r] = lay_x || y < a.nbl || y > a.ny - 1 - a.nbl;
     }
 
@@ -747,7 +749,7 @@ __global__ void __launch_bounds__(NT, 2)
     // end of step t: the vz tile read into the queue (seq t+7) and the centre slot are free
 #define VD_PSTEP(J)                                                                   \
     if (t + (J) < T) {                                                                \
-        p_plane<(J)>(a, c, t + (J), q);                                               \
+        p_plane<(J), C>(a, c, t + (J), q);                                               \
         __syncthreads();                                                              \
         if (*c.abort_flag) break;                                                     \
         if (tid == 0) {                                                               \
@@ -1018,10 +1020,14 @@ cudaError_t enqueue_vd_step(mmod_vd *h, int n, const float *wav, float *traces_p
         lc.gridDim = dim3(h->geom.tiles_x * h->geom.tiles_y * h->geom.zchunks);
         lc.blockDim = dim3(NT);
         lc.dynamicSmemBytes = V_SMEM;
-        if ((e = cudaLaunchKernelEx(&lc, vd_velocity_tma, a, h->maps, h->geom)) != cudaSuccess) return e;
+        if ((e = cudaLaunchKernelEx(&lc, a.cpml ? vd_velocity_tma<true> : vd_velocity_tma<false>, a, h->maps,
+                                    h->geom)) != cudaSuccess)
+            return e;
         a.traces = nullptr;
         lc.dynamicSmemBytes = P_SMEM;
-        if ((e = cudaLaunchKernelEx(&lc, vd_pressure_tma, a, h->maps, h->geom)) != cudaSuccess) return e;
+        if ((e = cudaLaunchKernelEx(&lc, a.cpml ? vd_pressure_tma<true> : vd_pressure_tma<false>, a, h->maps,
+                                    h->geom)) != cudaSuccess)
+            return e;
     } else {
         const dim3 blk(32, 8, 1), grd((h->cfg.nx + 31) / 32, (h->cfg.ny + 7) / 8, h->cfg.nz);
         vd_velocity_simple<<<grd, blk, 0, s>>>(a);
@@ -1278,8 +1284,11 @@ MMOD_API mmod_status mmod_vd_create(const mmod_config *cfg, int device, mmod_vd 
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     h->geom = plan_geom(c.nx, c.ny, c.nz, sms);
     h->geom_plan = h->geom;
-    bool ok = cudaFuncSetAttribute(vd_velocity_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, V_SMEM) == cudaSuccess &&
-              cudaFuncSetAttribute(vd_pressure_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM) == cudaSuccess;
+    bool ok = true;
+    for (const void *f : {(const void *)vd_velocity_tma<false>, (const void *)vd_velocity_tma<true>})
+        ok = ok && cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, V_SMEM) == cudaSuccess;
+    for (const void *f : {(const void *)vd_pressure_tma<false>, (const void *)vd_pressure_tma<true>})
+        ok = ok && cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM) == cudaSuccess;
     ok = ok && encode_box(&h->maps.p_halo, h->p, c.nx, c.ny, c.nz, h->nxp, PHX, PHY);
     for (int ax = 0; ax < 3; ++ax) ok = ok && encode_box(&h->maps.own[ax], h->v[ax], c.nx, c.ny, c.nz, h->nxp, TX, TY);
     ok = ok && encode_box(&h->maps.b_box, h->bd, c.nx, c.ny, c.nz, h->nxp, BX, BY);
