@@ -341,9 +341,15 @@ __device__ __forceinline__ void store_pair(float *dst, float2 v, bool in0, bool 
 // Velocity kernel.  Rings (sequence -> plane): p halo tiles, seq s -> z0-3+s
 // (the queue window of plane k is p(k-3 .. k+4), the centre tile is seq t+3);
 // own velocity tiles and buoyancy tiles, seq s -> z0+s (planes k and k+1 of
-// b are resident during step t).  The plane loop is unrolled 8x so queue
-// slot (J + i) % 8 holds p(k - 3 + i) at step J of a block: no shifts.
+// b are resident during step t).  The plane loop is unrolled kVU times: at
+// step J of a group queue slot J + i holds p(k - 3 + i) (kVQ = 7 + kVU slots),
+// and after each group the queue shifts down by kVU.  With kVU = 8 the
+// slots are used modulo 8 instead and nothing shifts (more code per loop).
 // ---------------------------------------------------------------------------
+constexpr int kVU = 4;
+constexpr int kVQ = kVU == 8 ? 8 : 2 * kRadius - 1 + kVU;
+__host__ __device__ constexpr int vq(int J, int i) { return kVU == 8 ? (J + i) % 8 : J + i; }
+
 struct VCtx {
     float *ring_p, *ring_o, *ring_b;
     uint64_t *bar_p, *bar_o, *bar_b;
@@ -362,14 +368,14 @@ __device__ __forceinline__ void v_read_q(const VCtx &c, int seq, float2 (&dst)[R
 }
 
 template <int J, bool C>
-__device__ __forceinline__ bool v_plane(const VdArgs &a, const VCtx &c, int t, float2 (&q)[2 * kRadius][RY]) {
+__device__ __forceinline__ bool v_plane(const VdArgs &a, const VCtx &c, int t, float2 (&q)[kVQ][RY]) {
     const int k = c.z0 + t;
     if (!(mbar_wait(&c.bar_p[(t + 7) % VNSP], ((t + 7) / VNSP) & 1, c.abort_flag, a.err) &&
           mbar_wait(&c.bar_o[t % VNSO], (t / VNSO) & 1, c.abort_flag, a.err) &&
           mbar_wait(&c.bar_b[t % VNSB], (t / VNSB) & 1, c.abort_flag, a.err) &&
           mbar_wait(&c.bar_b[(t + 1) % VNSB], ((t + 1) / VNSB) & 1, c.abort_flag, a.err)))
         return false;
-    v_read_q(c, t + 7, q[(J + 7) % 8]);
+    v_read_q(c, t + 7, q[vq(J, 7)]);
     const float *ctr = c.ring_p + ((t + 3) % VNSP) * V_SLOT_P;
     const float *own = c.ring_o + (t % VNSO) * V_SLOT_O;
     const float *bk = c.ring_b + (t % VNSB) * V_SLOT_B;
@@ -397,9 +403,8 @@ __device__ __forceinline__ bool v_plane(const VdArgs &a, const VCtx &c, int t, f
         const float2 dy = stag_diff2(a.w[1], yc[r + 4], yc[r + 3], yc[r + 5], yc[r + 2], yc[r + 6], yc[r + 1],
                                      yc[r + 7], yc[r + 0]);
         // D+_z: planes k+m and k-m+1 -> queue entries 3+m and 4-m
-        const float2 dz = stag_diff2(a.w[2], q[(J + 4) % 8][r], q[(J + 3) % 8][r], q[(J + 5) % 8][r],
-                                     q[(J + 2) % 8][r], q[(J + 6) % 8][r], q[(J + 1) % 8][r], q[(J + 7) % 8][r],
-                                     q[(J + 0) % 8][r]);
+        const float2 dz = stag_diff2(a.w[2], q[vq(J, 4)][r], q[vq(J, 3)][r], q[vq(J, 5)][r], q[vq(J, 2)][r],
+                                     q[vq(J, 6)][r], q[vq(J, 1)][r], q[vq(J, 7)][r], q[vq(J, 0)][r]);
         // dt b at the half points
         const float *brow = bk + yl * BX + c.xl;
         const float2 b01 = *reinterpret_cast<const float2 *>(brow);
@@ -526,7 +531,7 @@ __global__ void __launch_bounds__(NT, 2)
         c.lay_xy[r] = lay_x || y < a.nbl || y >= a.ny - 1 - a.nbl;
     }
 
-    float2 q[2 * kRadius][RY];
+    float2 q[kVQ][RY];
     bool ok = true;
     for (int s = 0; s < 2 * kRadius - 1 && ok; ++s) {
         ok = mbar_wait(&c.bar_p[s % VNSP], (s / VNSP) & 1, c.abort_flag, a.err);
@@ -564,8 +569,17 @@ __global__ void __launch_bounds__(NT, 2)
     }
     if (!*c.abort_flag) {
 #pragma unroll 1
-        for (int t = 0; t < T; t += 8) {
-            VD_VSTEP(0) VD_VSTEP(1) VD_VSTEP(2) VD_VSTEP(3) VD_VSTEP(4) VD_VSTEP(5) VD_VSTEP(6) VD_VSTEP(7)
+        for (int t = 0; t < T; t += kVU) {
+            VD_VSTEP(0) VD_VSTEP(1) VD_VSTEP(2) VD_VSTEP(3)
+            if constexpr (kVU == 8) {
+                VD_VSTEP(4) VD_VSTEP(5) VD_VSTEP(6) VD_VSTEP(7)
+            } else {
+#pragma unroll
+                for (int i = 0; i < 2 * kRadius - 1; ++i) {
+#pragma unroll
+                    for (int r = 0; r < RY; ++r) q[i][r] = q[i + kVU][r];
+                }
+            }
         }
     }
 #undef VD_VSTEP
