@@ -473,7 +473,8 @@ def measure_gradient(M, dev, stream, fwd_gpts, nt=1000, reps=2):
         prop.gradient(wav, r, g, ck, dtype, stream)
         ms = time_calls(lambda: prop.gradient(wav, r, g, ck, dtype, stream), reps, stream)
         v = p.npoints * p.nt / (ms * 1e-3) / 1e9
-        bpp, what = gradient_bytes_per_point_step(ck >= p.nt and dtype == M.CKPT_FP32)
+        bpp, what = gradient_bytes_per_point_step(ck >= p.nt and dtype == M.CKPT_FP32,
+                                                  ck if dtype == M.CKPT_FP32 else 0)
         out[name] = {"value": v, "ms": ms, "vs_forward": v / fwd_gpts, "checkpoints": ck,
                      "memory_gb": prop.gradient_memory(ck, dtype) / 1e9,
                      "roofline": roofline_of(bpp * p.npoints * p.nt, ms, peak, what)}
@@ -481,15 +482,21 @@ def measure_gradient(M, dev, stream, fwd_gpts, nt=1000, reps=2):
     return out
 
 
-def gradient_bytes_per_point_step(every_state):
+def gradient_bytes_per_point_step(every_state, fp32_segments=0):
     """Algorithmic bytes per grid point and time step of mmod_gradient
-    (checkpoint saves and restores, once per segment, left out)."""
+    (checkpoint saves and restores, once per segment, left out).  With S FP32
+    segments the first sweep writes g^n of the last segment (+4 B on 1/S of
+    the steps) and that segment is not replayed (-20 B on 1/S of the steps)."""
     if every_state:
         return 48, ("forward sweep 20 B (u^{n-1}, u^n, c read, u^{n+1} and g^n = L u^n + s^n written), adjoint "
                     "step 16 B, paired imaging 12 B (psi^{n+1}, psi^n, g^n, g^{n-1} read, accumulator "
                     "read and written per two steps)")
-    return 64, ("forward sweep 16 B, segment replay 20 B (g^n written as well), adjoint step 16 B, paired "
-                "imaging 12 B per point and step")
+    what = ("forward sweep 16 B, segment replay 20 B (g^n written as well), adjoint step 16 B, paired "
+            "imaging 12 B per point and step")
+    if fp32_segments > 0:
+        return 64 - 16.0 / fp32_segments, what + (f"; the last of {fp32_segments} FP32 segments keeps g^n from the "
+                                                 f"first sweep (+4 B) and is not replayed (-20 B)")
+    return 64, what
 
 
 def measure_batched(M, dev, stream, fwd_gpts, reps=3):

@@ -22,7 +22,9 @@
 //     segments of K steps; the backward sweep replays each segment from its
 //     checkpoint, in place in two volumes, writing g^n into K more, and runs
 //     the segment's adjoint steps against them.  Memory: 2 S checkpoint
-//     volumes + K + 2; work: two forward sweeps and one adjoint;
+//     volumes + K + 2; work: two forward sweeps and one adjoint (with FP32
+//     checkpoints the first sweep writes g^n of the last segment itself,
+//     which is then not replayed);
 //   revolve: the binomial schedule of mmod_revolve.cu over S slots, with the
 //     working state in the handle's two buffers, u^{n+1} and g^n of a
 //     reversed step in two more volumes; the fewest replayed steps for S slots;
@@ -469,13 +471,25 @@ MMOD_API mmod_status mmod_gradient(mmod_handle *h, const float *wavelet, const f
         }
     } else {
         const int nseg = nt > 0 ? nslot : 0;
+        // With FP32 checkpoints a replay reproduces the first sweep bit for
+        // bit, so the first sweep writes g^n of the last segment straight into
+        // the segment buffer and that segment is neither saved nor replayed.
+        // (A 16-bit checkpoint would start its replay from the rounded state.)
+        const bool keep_last = ckpt_dtype == MMOD_CKPT_FP32;
         // ---- sweep 1: forward with a checkpoint at the start of every segment
         for (int sg = 0; sg < nseg; ++sg) {
             const int a0 = sg * seglen, b0 = std::min(nt, a0 + seglen);
-            // at step a0: u^{a0-1} in u[a0 & 1], u^{a0} in u[(a0 + 1) & 1]
-            MMOD_CK(h, save_volume(h, h->u[a0 & 1], 2 * sg, s));
-            MMOD_CK(h, save_volume(h, h->u[(a0 + 1) & 1], 2 * sg + 1, s));
-            for (int n = a0; n < b0; ++n) MMOD_CK(h, fwd_step_in_place(n));
+            const bool last = keep_last && sg == nseg - 1;
+            if (!last) {   // at step a0: u^{a0-1} in u[a0 & 1], u^{a0} in u[(a0 + 1) & 1]
+                MMOD_CK(h, save_volume(h, h->u[a0 & 1], 2 * sg, s));
+                MMOD_CK(h, save_volume(h, h->u[(a0 + 1) & 1], 2 * sg + 1, s));
+            }
+            for (int n = a0; n < b0; ++n) {
+                fa.gout = last ? gw.seg[2 + n - a0] : nullptr;
+                const cudaError_t e = fwd_step_in_place(n);
+                fa.gout = nullptr;
+                MMOD_CK(h, e);
+            }
         }
         // ---- backward: replay each segment (g^n of its steps), then its
         // adjoint steps + imaging
@@ -484,11 +498,13 @@ MMOD_API mmod_status mmod_gradient(mmod_handle *h, const float *wavelet, const f
         MMOD_CK(h, cudaMemsetAsync(gw.gradc, 0, vb, s));
         for (int sg = nseg - 1; sg >= 0; --sg) {
             const int a0 = sg * seglen, b0 = std::min(nt, a0 + seglen);
-            MMOD_CK(h, restore_volume(h, 2 * sg, gw.seg[0], s));
-            MMOD_CK(h, restore_volume(h, 2 * sg + 1, gw.seg[1], s));
-            for (int n = a0; n < b0; ++n) {   // seg[2 + n - a0] receives g^n
-                const int j = n - a0;
-                MMOD_CK(h, fwd_step_g(n, j & 1, (j + 1) & 1, gw.seg[2 + j]));
+            if (!(keep_last && sg == nseg - 1)) {
+                MMOD_CK(h, restore_volume(h, 2 * sg, gw.seg[0], s));
+                MMOD_CK(h, restore_volume(h, 2 * sg + 1, gw.seg[1], s));
+                for (int n = a0; n < b0; ++n) {   // seg[2 + n - a0] receives g^n
+                    const int j = n - a0;
+                    MMOD_CK(h, fwd_step_g(n, j & 1, (j + 1) & 1, gw.seg[2 + j]));
+                }
             }
             MMOD_CK(h, backward_range(b0 - 1, a0, [&](int j) { return gw.seg[2 + j - a0]; }));
         }
