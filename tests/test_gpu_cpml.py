@@ -89,8 +89,10 @@ def test_cpml_planes_per_thread_keep_bits(fs):
         assert np.array_equal(u_p, u_d) and np.array_equal(tr_p, tr_d), planes
 
 
+# (45, 50, 98): nx not a multiple of 4, so x takes the marching pass while y
+# and z run tiled in the same step
 TILE_CASES = [((47, 71, 100), 20, False), ((47, 71, 100), 20, True), ((40, 37, 68), 8, False),
-              ((41, 37, 68), 8, True), ((33, 64, 131), 8, False)]
+              ((41, 37, 68), 8, True), ((33, 64, 131), 8, False), ((45, 50, 98), 20, True)]
 
 
 @pytest.mark.parametrize("shape,nbl,fs", TILE_CASES, ids=[f"{s}-L{n}-fs{int(f)}" for s, n, f in TILE_CASES])
