@@ -671,8 +671,7 @@ MMOD_API mmod_status mmod_create(const mmod_config *cfg, int device, mmod_handle
     CKC(cudaHostAlloc(&h->err_host, sizeof(int), cudaHostAllocMapped));
     *h->err_host = 0;
     CKC(cudaHostGetDevicePointer(&h->err_dev, h->err_host, 0));
-    if (is_cpml(h) && !make_cpml_tiles(cpml_args(h), h->u, &h->cpml_tiles))
-        CKC(cudaErrorInvalidValue);   // a tensor map of the tiled layer passes could not be encoded
+    if (is_cpml(h)) make_cpml_tiles(cpml_args(h), h->u, &h->cpml_tiles);   // axes it cannot tile keep the march
     h->tma_ok = make_tma_plan(h->cfg, h->nxp, h->u, h->c, h->cur_map, h->prev_map, &h->c_map, h->plans);
     if (h->tma_ok) {   // counters of the persistent kernel, sized for the plan with the most units
         for (int v = 0; v < tma_variant_count(); ++v)

@@ -747,14 +747,17 @@ bool make_cpml_tiles(const CpmlArgs &p, float *const u[2], CpmlTiles *t) {
     // x: row segments start on 16-byte boundaries, and the compact arrays exist
     Ranges rx;
     ok[0] = ok[0] && x_tileable(p, &rx) && p.xc != nullptr;
+    // an axis whose maps cannot be encoded keeps the marching pass
     for (int b = 0; b < 2; ++b) {
-        if (ok[0] && !encode_axis<0>(p, u[b], u[1 - b], &t->maps[b][0])) return false;
-        if (ok[1] && !encode_axis<1>(p, u[b], u[1 - b], &t->maps[b][1])) return false;
-        if (ok[2] && !encode_axis<2>(p, u[b], u[1 - b], &t->maps[b][2])) return false;
+        ok[0] = ok[0] && encode_axis<0>(p, u[b], u[1 - b], &t->maps[b][0]);
+        ok[1] = ok[1] && encode_axis<1>(p, u[b], u[1 - b], &t->maps[b][1]);
+        ok[2] = ok[2] && encode_axis<2>(p, u[b], u[1 - b], &t->maps[b][2]);
     }
     if (tile_attr<0, 8>() || tile_attr<1, 8>() || tile_attr<2, 8>() || tile_attr<0, 20>() || tile_attr<1, 20>() ||
-        tile_attr<2, 20>())
-        return false;
+        tile_attr<2, 20>()) {
+        cudaGetLastError();
+        return true;   // no tiled pass: the marching passes serve every axis
+    }
     const bool w8 = L == 8;
     t->resident[0] = w8 ? tile_blocks<0, 8>() : tile_blocks<0, 20>();
     t->resident[1] = w8 ? tile_blocks<1, 8>() : tile_blocks<1, 20>();

@@ -53,8 +53,9 @@ struct CpmlTiles {
 // where the x pass cannot run tiled.
 long long cpml_x_compact_floats(const CpmlArgs &p);
 
-// Builds the tile maps for the wavefield buffers u[0], u[1]; false on an
-// encoding failure (ok[] then all false).
+// Builds the tile maps for the wavefield buffers u[0], u[1] and sets ok[]
+// for the axes whose tiled pass can run (an axis whose maps cannot be
+// encoded keeps the marching pass).  Returns true.
 bool make_cpml_tiles(const CpmlArgs &p, float *const u[2], CpmlTiles *t);
 
 // c_x of the compact x layers from c (after set_model's fill); no-op
