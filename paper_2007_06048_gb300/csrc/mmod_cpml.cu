@@ -461,11 +461,16 @@ __device__ __forceinline__ void tile_aux_origin(int nz, int r, int x, int y, int
     az = A == 0 ? r * compact_planes(nz) + z : z;
 }
 
-// Persistent over the units (unit = block + k * grid), two shared-memory
-// stages: the loads of unit k + 1 are in flight while unit k is computed;
+// Persistent over the units (unit = block + k * grid), kTileStages
+// shared-memory stages: the loads of the next units are in flight while unit
+// k is computed;
 // a stage is refilled once the bulk stores of its previous unit have read
 // it.
 constexpr int kTileThreads = kTileLines;   // one thread per line
+// Shared-memory stages per block.  Measured on 240^3 (us per CPML step):
+// 32-cell boxes with 2 / 3 / 4 stages 85.5 / 89.2 / 91.0, 16-cell boxes
+// 86.4 / 87.8 / 90.0.
+constexpr int kTileStages = 2;
 
 template <int A, int kLen>
 __global__ void __launch_bounds__(kTileThreads, 2)
@@ -474,7 +479,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     using G = TileGeom<kLen>;
     constexpr int kStage = G::kBytes / 4;   // floats per stage
     extern __shared__ __align__(128) float tile_smem[];
-    __shared__ __align__(8) uint64_t full[2];
+    __shared__ __align__(8) uint64_t full[kTileStages];
     __shared__ int abort_flag;
     const int t = threadIdx.x;
     // thread 0: a unit's copies into stage st; `stable` the four that no
@@ -497,32 +502,28 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     };
     if (t == 0) {
         abort_flag = 0;
-        mbar_init(&full[0], 1);
-        mbar_init(&full[1], 1);
+        for (int s = 0; s < kTileStages; ++s) mbar_init(&full[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_tile_shared();
     }
     __syncthreads();
-    // the first two units' copies of data the previous kernels of the step do
-    // not write go out before the programmatic-launch wait, u^{n+1} after it
-    const bool have0 = (int)blockIdx.x < units, have1 = (int)(blockIdx.x + gridDim.x) < units;
-    if (t == 0) {
-        if (have0) issue(blockIdx.x, 0, true, false);
-        if (have1) issue(blockIdx.x + gridDim.x, 1, true, false);
-    }
+    // the first units' copies of data the previous kernels of the step do not
+    // write go out before the programmatic-launch wait, u^{n+1} after it
+    if (t == 0)
+        for (int s = 0; s < kTileStages; ++s)
+            if ((int)(blockIdx.x + s * gridDim.x) < units) issue(blockIdx.x + s * gridDim.x, s, true, false);
     if (p.pdl) {
         asm volatile("griddepcontrol.wait;" ::: "memory");
         asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     }
-    if (t == 0) {
-        if (have0) issue(blockIdx.x, 0, false, true);
-        if (have1) issue(blockIdx.x + gridDim.x, 1, false, true);
-    }
+    if (t == 0)
+        for (int s = 0; s < kTileStages; ++s)
+            if ((int)(blockIdx.x + s * gridDim.x) < units) issue(blockIdx.x + s * gridDim.x, s, false, true);
     int k = 0;
     for (int unit = blockIdx.x; unit < units; unit += gridDim.x, ++k) {
-        const int st = k & 1;
+        const int st = k % kTileStages;
         float *base = tile_smem + st * kStage;
-        const bool ready = mbar_wait(&full[st], (k >> 1) & 1, &abort_flag, p.err);
+        const bool ready = mbar_wait(&full[st], (k / kTileStages) & 1, &abort_flag, p.err);
         int x, y, z, lo, i2, r;
         tile_origin<A>(rg, n1, n2, unit, x, y, z, lo, i2, r);
         // every lane computes (the profiles are shuffled across the warp); the
@@ -532,10 +533,10 @@ __global__ void __launch_bounds__(kTileThreads, 2)
         fence_tile_shared();   // this thread's shared-memory writes before the bulk stores
         __syncthreads();
         if (abort_flag) {      // uniform: read after the barrier
-            if (t == 0) {      // no copy may still be landing when the block exits
-                mbar_drain(&full[st], (k >> 1) & 1);
-                if (unit + (int)gridDim.x < units) mbar_drain(&full[st ^ 1], ((k + 1) >> 1) & 1);
-            }
+            if (t == 0)        // no copy may still be landing when the block exits
+                for (int j = 0; j < kTileStages; ++j)
+                    if (unit + j * (int)gridDim.x < units)
+                        mbar_drain(&full[(k + j) % kTileStages], ((k + j) / kTileStages) & 1);
             break;
         }
         if (t == 0) {
@@ -546,7 +547,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
             tma_store_3d(&m.zeta, ax, ay, az, sz);
             tma_store_3d(&m.uout, x, y, z, so);
             bulk_commit();
-            const int next = unit + 2 * (int)gridDim.x;
+            const int next = unit + kTileStages * (int)gridDim.x;
             if (next < units) {
                 bulk_wait_read_all();   // the stage's stores have read it
                 issue(next, st, true, true);
@@ -562,7 +563,7 @@ constexpr int kTileWidths[] = {8, 20};
 template <int A, int kLen>
 cudaError_t tile_attr() {
     return cudaFuncSetAttribute(cpml_tile_kernel<A, kLen>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                2 * TileGeom<kLen>::kBytes);
+                                kTileStages * TileGeom<kLen>::kBytes);
 }
 
 // Resident blocks of the persistent tiled pass on the current device.
@@ -571,7 +572,7 @@ int tile_blocks() {
     int dev = 0, sms = 0, occ = 0;
     if (cudaGetDevice(&dev) || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cpml_tile_kernel<A, kLen>, kTileThreads,
-                                                      2 * TileGeom<kLen>::kBytes)) {
+                                                      kTileStages * TileGeom<kLen>::kBytes)) {
         cudaGetLastError();
         return 0;
     }
@@ -604,7 +605,7 @@ cudaError_t launch_tile(const CpmlTileMaps &m, const CpmlArgs &p, const Ranges &
     at[0].val.programmaticStreamSerializationAllowed = 1;
     lc.gridDim = dim3(grid);
     lc.blockDim = dim3(kTileThreads);
-    lc.dynamicSmemBytes = 2 * TileGeom<kLen>::kBytes;
+    lc.dynamicSmemBytes = kTileStages * TileGeom<kLen>::kBytes;
     lc.stream = s;
     lc.attrs = at;
     lc.numAttrs = p.pdl ? 1 : 0;
