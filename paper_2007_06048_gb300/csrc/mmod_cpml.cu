@@ -468,8 +468,8 @@ __device__ __forceinline__ void tile_aux_origin(int nz, int r, int x, int y, int
 // it.
 constexpr int kTileThreads = kTileLines;   // one thread per line
 // Shared-memory stages per block.  Measured on 240^3 (us per CPML step):
-// 32-cell boxes with 2 / 3 / 4 stages 85.5 / 89.2 / 91.0, 16-cell boxes
-// 86.4 / 87.8 / 90.0.
+// 32-cell boxes with 1 / 2 / 3 / 4 stages 95.0 / 85.5 / 89.2 / 91.0, 16-cell
+// boxes with 2 / 3 / 4 stages 86.4 / 87.8 / 90.0.
 constexpr int kTileStages = 2;
 
 template <int A, int kLen>
