@@ -16,17 +16,21 @@
 // A pass works on lines along its axis and on the layer ranges of a line
 // ([0, L) and [n - L, n), or the whole line where the two ranges' stencils
 // meet), so every psi_a value it needs is computed by the same thread or warp
-// in the same pass and no gathers are needed:
-//   x: one warp per row segment (lane = cell, 24 cells and a 4-cell margin
-//      each side), neighbours by warp shuffles;
-//   y, z (and x for ranges wider than 24): one thread per line range,
-//      consecutive threads on consecutive x (coalesced), marching along the
-//      axis with a 13-value window of u^n and a 9-value window of psi^n, the
-//      correction trailing psi by the stencil radius.
-// Per cell, psi and zeta take the same FP32 operations as before; u^{n+1}
-// gains one fused multiply-add per axis whose profile is on.  u and psi are
-// 0 outside the grid; with a free surface the top layer is absent and the
-// plane k = 0 is left alone (u, psi and zeta stay 0).
+// in the same pass and no gathers are needed.  Two forms, with the same FP32
+// operations per cell (the same bits):
+//   tiled (the default where the axis allows it, see below): units of 64
+//      lines of a range loaded whole into shared memory by bulk-tensor
+//      copies, one thread per line, results stored back by bulk-tensor
+//      stores; the x layers' psi, zeta and c in compact arrays;
+//   marching: x — one warp per row segment (lane = cell, 24 cells and a
+//      4-cell margin each side), neighbours by warp shuffles; y, z (and x
+//      for ranges wider than 24) — one thread per line range, consecutive
+//      threads on consecutive x (coalesced), marching along the axis with a
+//      13-value window of u^n and a 9-value window of psi^n, the correction
+//      trailing psi by the stencil radius.
+// u^{n+1} gains one fused multiply-add per axis whose profile is on.  u and
+// psi are 0 outside the grid; with a free surface the top layer is absent
+// and the plane k = 0 is left alone (u, psi and zeta stay 0).
 #include "mmod_cpml.h"
 #include "mmod_internal.h"
 #include "tma_ptx.cuh"
